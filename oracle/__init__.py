@@ -1,0 +1,402 @@
+"""FP64 CPU oracle for the tree side of the P3T scheme (arXiv:1506.04553).
+
+TEST INFRASTRUCTURE ONLY: the independent reference that the CUDA library is
+checked against.  Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it; the library never does, and it
+shares no code with the CUDA path.  The arithmetic lives in ``p3t_oracle.c``
+(plain C, FP64, compiled with ``-ffp-contract=off``); this module builds that
+file with gcc on first use and wraps it with ctypes.
+
+Functions and the passages they follow:
+
+* ``K``, ``W``, ``W_inner_slope`` -- Eq. 12-17 (Sect. 2.1); W uses G with its
+  numerator's sign reversed, the reading under which Eq. 9 holds.
+* ``direct`` -- Eq. 7-9 with the softened distance of Eq. 2-3 (soft, hard
+  and Newtonian weights) and the pair potentials of Eq. 5-6.
+* ``Tree`` -- the Barnes-Hut tree to quadrupole order of Sect. 2.2: Morton
+  keys, octree, moments, groups, opening test, interaction lists, forces.
+* ``neighbours`` -- the per-particle list of particles within h (Sect. 2.2).
+* ``kick`` / ``drift`` -- the leapfrog pieces of Eq. 11 and Sect. 2.2.
+* ``direct_vjp`` / ``Tree.vjp`` -- gradients of sum_i w_i . a_i (no
+  counterpart in the paper; derived from Eq. 8 and the quadrupole expansion).
+
+Parity status of each function (what pins it) is listed in the test files
+``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "p3t_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DEFAULT_THREADS = os.cpu_count() or 1
+
+
+def build(force: bool = False) -> str:
+    """Compile p3t_oracle.c into a shared library (gcc, FP64, no FMA)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            _declare(lib)
+            _lib = lib
+    return _lib
+
+
+_d = C.c_double
+_i64 = C.c_int64
+_i32 = C.c_int32
+_p = C.c_void_p
+
+
+def _declare(lib):
+    lib.orc_K.restype = _d
+    lib.orc_K.argtypes = [_d]
+    lib.orc_dKdx.restype = _d
+    lib.orc_dKdx.argtypes = [_d]
+    lib.orc_K_of_s.restype = _d
+    lib.orc_K_of_s.argtypes = [_d, _d, _d]
+    lib.orc_W.restype = _d
+    lib.orc_W.argtypes = [_d, _d]
+    lib.orc_W_inner_slope.restype = _d
+    lib.orc_W_inner_slope.argtypes = [_d]
+    lib.orc_direct.restype = None
+    lib.orc_direct.argtypes = [_i64, _p, _p, _d, _d, _d, _d, C.c_int, _p, _i64,
+                               _p, _p, C.c_int]
+    lib.orc_neighbours_count.restype = None
+    lib.orc_neighbours_count.argtypes = [_i64, _p, _d, _p, _i64, _p, C.c_int]
+    lib.orc_neighbours_fill.restype = None
+    lib.orc_neighbours_fill.argtypes = [_i64, _p, _d, _p, _i64, _p, _p, _p,
+                                        C.c_int]
+    lib.orc_is_neighbour.restype = C.c_int
+    lib.orc_is_neighbour.argtypes = [_p, _p, _d]
+    lib.orc_kick.restype = None
+    lib.orc_kick.argtypes = [_i64, _p, _p, _d]
+    lib.orc_drift.restype = None
+    lib.orc_drift.argtypes = [_i64, _p, _p, _d]
+    lib.orc_morton_key.restype = C.c_uint64
+    lib.orc_morton_key.argtypes = [_d, _d, _d, _p, _d]
+    lib.orc_root_box.restype = None
+    lib.orc_root_box.argtypes = [_i64, _p, _p, _p]
+    lib.orc_tree_build.restype = _p
+    lib.orc_tree_build.argtypes = [_i64, _p, _p, C.c_int, C.c_int]
+    lib.orc_tree_free.restype = None
+    lib.orc_tree_free.argtypes = [_p]
+    for f in ("orc_tree_n", "orc_tree_ncell", "orc_tree_ngroup"):
+        getattr(lib, f).restype = _i64
+        getattr(lib, f).argtypes = [_p]
+    lib.orc_tree_root.restype = None
+    lib.orc_tree_root.argtypes = [_p, _p, _p]
+    lib.orc_tree_particles.restype = None
+    lib.orc_tree_particles.argtypes = [_p, _p, _p]
+    lib.orc_tree_cells.restype = None
+    lib.orc_tree_cells.argtypes = [_p] + [_p] * 11
+    lib.orc_tree_groups.restype = None
+    lib.orc_tree_groups.argtypes = [_p, _p, _p, _p, _p]
+    lib.orc_tree_walk.restype = None
+    lib.orc_tree_walk.argtypes = [_p, _d, _d, _d, C.c_int, _p]
+    lib.orc_tree_lists.restype = None
+    lib.orc_tree_lists.argtypes = [_p] + [_p] * 6
+    lib.orc_tree_force.restype = C.c_int
+    lib.orc_tree_force.argtypes = [_p, _d, _d, _d, _d, _p, _i64, _p, _p,
+                                   C.c_int]
+    lib.orc_tree_group_of.restype = _i64
+    lib.orc_tree_group_of.argtypes = [_p, _i64]
+    if hasattr(lib, "orc_direct_vjp"):
+        lib.orc_direct_vjp.restype = None
+        lib.orc_direct_vjp.argtypes = [_i64, _p, _p, _d, _d, _d, _d, _p, _p,
+                                       _p, C.c_int]
+    if hasattr(lib, "orc_tree_vjp"):
+        lib.orc_tree_vjp.restype = C.c_int
+        lib.orc_tree_vjp.argtypes = [_p, _d, _d, _d, _d, _p, _p, _p, C.c_int]
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+KINDS = {"soft": 0, "hard": 1, "newton": 2}
+
+
+# --------------------------------------------------------------------------
+# Eq. 12-17
+# --------------------------------------------------------------------------
+
+def K(x):
+    """Cut-off function K(x) of Eq. 12 (elementwise)."""
+    lib = _load()
+    x = np.asarray(x, dtype=np.float64)
+    return np.vectorize(lib.orc_K, otypes=[np.float64])(x)
+
+
+def dKdx(x):
+    lib = _load()
+    x = np.asarray(x, dtype=np.float64)
+    return np.vectorize(lib.orc_dKdx, otypes=[np.float64])(x)
+
+
+def K_of_s(s, r_cut, gamma):
+    """K as a function of the softened distance (Eq. 12-15)."""
+    lib = _load()
+    s = np.asarray(s, dtype=np.float64)
+    return np.vectorize(lambda v: lib.orc_K_of_s(v, r_cut, gamma),
+                        otypes=[np.float64])(s)
+
+
+def W(y, gamma):
+    """Potential transition function W(y; gamma) of Eq. 16-17 (sign of G's
+    numerator reversed, see the module docstring)."""
+    lib = _load()
+    y = np.asarray(y, dtype=np.float64)
+    return np.vectorize(lambda v: lib.orc_W(v, gamma), otypes=[np.float64])(y)
+
+
+def W_inner_slope(gamma):
+    return _load().orc_W_inner_slope(gamma)
+
+
+# --------------------------------------------------------------------------
+# Direct summation
+# --------------------------------------------------------------------------
+
+def direct(pos, mass, *, G=1.0, eps=0.0, r_cut=1.0, gamma=0.1, kind="soft",
+           rows=None, potential=False, threads=None):
+    """Acceleration a_i = -sum_{j!=i} G m_j w(s_ij) q_ij / s_ij^3 with
+    w = K (soft, Eq. 8), 1-K (hard, Eq. 7) or 1 (Newton); optionally the
+    matching potential.  ``rows`` restricts the evaluation to those i."""
+    lib = _load()
+    pos = _f64(pos, (-1, 3))
+    mass = _f64(mass)
+    n = pos.shape[0]
+    rws = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nr = n if rws is None else rws.shape[0]
+    acc = np.zeros((nr, 3))
+    pot = np.zeros(nr) if potential else None
+    lib.orc_direct(n, _ptr(pos), _ptr(mass), G, eps, r_cut, gamma,
+                   KINDS[kind], None if rws is None else _ptr(rws), nr,
+                   _ptr(acc), None if pot is None else _ptr(pot),
+                   threads or DEFAULT_THREADS)
+    return (acc, pot) if potential else acc
+
+
+# --------------------------------------------------------------------------
+# Neighbour lists
+# --------------------------------------------------------------------------
+
+def neighbours(pos, h, rows=None, threads=None):
+    """CSR neighbour lists: for each row i, every j != i with
+    ((dx*dx + dy*dy) + dz*dz) < h*h (FP64, unsoftened), ascending j.
+    Returns (offsets int64[nr+1], indices int32[nnz])."""
+    lib = _load()
+    pos = _f64(pos, (-1, 3))
+    n = pos.shape[0]
+    rws = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nr = n if rws is None else rws.shape[0]
+    cnt = np.zeros(nr, dtype=np.int64)
+    th = threads or DEFAULT_THREADS
+    rp = None if rws is None else _ptr(rws)
+    lib.orc_neighbours_count(n, _ptr(pos), h, rp, nr, _ptr(cnt), th)
+    off = np.zeros(nr + 1, dtype=np.int64)
+    np.cumsum(cnt, out=off[1:])
+    idx = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
+    cnt2 = np.zeros(nr, dtype=np.int64)
+    lib.orc_neighbours_fill(n, _ptr(pos), h, rp, nr, _ptr(off), _ptr(idx),
+                            _ptr(cnt2), th)
+    return off, idx[: int(off[-1])]
+
+
+def is_neighbour(pi, pj, h) -> bool:
+    lib = _load()
+    a = _f64(pi, (3,))
+    b = _f64(pj, (3,))
+    return bool(lib.orc_is_neighbour(_ptr(a), _ptr(b), h))
+
+
+# --------------------------------------------------------------------------
+# Leapfrog pieces
+# --------------------------------------------------------------------------
+
+def kick(vel, acc32, dt_half):
+    """v <- v + dt_half * a (FP64 update with an FP32 acceleration)."""
+    lib = _load()
+    v = _f64(vel).copy()
+    a = np.ascontiguousarray(acc32, dtype=np.float32)
+    assert a.size == v.size
+    lib.orc_kick(v.size, _ptr(v), _ptr(a), dt_half)
+    return v
+
+
+def drift(pos, vel, dt):
+    """x <- x + dt * v (FP64)."""
+    lib = _load()
+    x = _f64(pos).copy()
+    v = _f64(vel)
+    assert x.size == v.size
+    lib.orc_drift(x.size, _ptr(x), _ptr(v), dt)
+    return x
+
+
+# --------------------------------------------------------------------------
+# Tree
+# --------------------------------------------------------------------------
+
+def morton_key(p, lo, size) -> int:
+    lib = _load()
+    lo = _f64(lo, (3,))
+    return int(lib.orc_morton_key(float(p[0]), float(p[1]), float(p[2]),
+                                  _ptr(lo), float(size)))
+
+
+def root_box(pos):
+    lib = _load()
+    pos = _f64(pos, (-1, 3))
+    lo = np.zeros(3)
+    size = np.zeros(1)
+    lib.orc_root_box(pos.shape[0], _ptr(pos), _ptr(lo), _ptr(size))
+    return lo, float(size[0])
+
+
+class Tree:
+    """The oracle's octree over (pos, mass) with leaf size n_leaf and group
+    size n_group; see p3t_oracle.c for the exact rules."""
+
+    def __init__(self, pos, mass, n_leaf=16, n_group=64):
+        self._lib = _load()
+        self.pos = _f64(pos, (-1, 3))
+        self.mass = _f64(mass)
+        self.n = self.pos.shape[0]
+        self.n_leaf = n_leaf
+        self.n_group = n_group
+        self._h = self._lib.orc_tree_build(self.n, _ptr(self.pos),
+                                           _ptr(self.mass), n_leaf, n_group)
+        self._walk = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.orc_tree_free(h)
+            self._h = None
+
+    # ---- structure ----
+    @property
+    def ncell(self):
+        return int(self._lib.orc_tree_ncell(self._h))
+
+    @property
+    def ngroup(self):
+        return int(self._lib.orc_tree_ngroup(self._h))
+
+    def root(self):
+        lo = np.zeros(3)
+        size = np.zeros(1)
+        self._lib.orc_tree_root(self._h, _ptr(lo), _ptr(size))
+        return lo, float(size[0])
+
+    def particles(self):
+        """(keys in sorted order, order[k] = original index)."""
+        key = np.zeros(self.n, dtype=np.uint64)
+        order = np.zeros(self.n, dtype=np.int64)
+        if self.n:
+            self._lib.orc_tree_particles(self._h, _ptr(key), _ptr(order))
+        return key, order
+
+    def cells(self):
+        c = self.ncell
+        out = dict(level=np.zeros(c, np.int32), first=np.zeros(c, np.int64),
+                   count=np.zeros(c, np.int64), parent=np.zeros(c, np.int64),
+                   child_first=np.zeros(c, np.int64),
+                   nchild=np.zeros(c, np.int32), M=np.zeros(c),
+                   com=np.zeros((c, 3)), Q=np.zeros((c, 6)),
+                   fmin=np.zeros((c, 3), np.float32),
+                   fmax=np.zeros((c, 3), np.float32))
+        if c:
+            self._lib.orc_tree_cells(self._h, *[_ptr(out[k]) for k in (
+                "level", "first", "count", "parent", "child_first", "nchild",
+                "M", "com", "Q", "fmin", "fmax")])
+        return out
+
+    def groups(self):
+        g = self.ngroup
+        first = np.zeros(g, np.int64)
+        count = np.zeros(g, np.int64)
+        fmin = np.zeros((g, 3), np.float32)
+        fmax = np.zeros((g, 3), np.float32)
+        if g:
+            self._lib.orc_tree_groups(self._h, _ptr(first), _ptr(count),
+                                      _ptr(fmin), _ptr(fmax))
+        return dict(first=first, count=count, fmin=fmin, fmax=fmax)
+
+    # ---- walk / lists ----
+    def walk(self, theta, h, r_cut, threads=None):
+        out = np.zeros(3, np.int64)
+        self._lib.orc_tree_walk(self._h, theta, h, r_cut,
+                                threads or DEFAULT_THREADS, _ptr(out))
+        self._walk = (theta, h, r_cut)
+        self._tot = [int(v) for v in out]
+        return dict(n_pc=int(out[0]), n_ppn=int(out[1]), n_ppf=int(out[2]))
+
+    def lists(self):
+        """Per-group interaction lists in CSR form: pc (cell ids), ppn
+        (near particles, sorted ids), ppf (far particles, sorted ids)."""
+        assert self._walk is not None, "walk() first"
+        g = self.ngroup
+        offs = [np.zeros(g + 1, np.int64) for _ in range(3)]
+        tot = self._tot
+        pc = np.zeros(max(tot[0], 1), np.int64)
+        ppn = np.zeros(max(tot[1], 1), np.int64)
+        ppf = np.zeros(max(tot[2], 1), np.int64)
+        self._lib.orc_tree_lists(self._h, _ptr(offs[0]), _ptr(pc),
+                                 _ptr(offs[1]), _ptr(ppn), _ptr(offs[2]),
+                                 _ptr(ppf))
+        return dict(pc_off=offs[0], pc=pc[: tot[0]], ppn_off=offs[1],
+                    ppn=ppn[: tot[1]], ppf_off=offs[2], ppf=ppf[: tot[2]])
+
+    def group_of_sorted(self, k):
+        return int(self._lib.orc_tree_group_of(self._h, int(k)))
+
+    # ---- forces ----
+    def force(self, *, G=1.0, eps=0.0, r_cut, gamma=0.1, groups=None,
+              potential=False, threads=None):
+        """FP64 tree acceleration (n x 3, original order) and soft potential
+        over the current lists; ``groups`` restricts to those groups (other
+        rows stay zero)."""
+        assert self._walk is not None, "walk() first"
+        acc = np.zeros((self.n, 3))
+        pot = np.zeros(self.n)
+        gr = None if groups is None else np.ascontiguousarray(groups, np.int64)
+        rc = self._lib.orc_tree_force(
+            self._h, G, eps, r_cut, gamma, None if gr is None else _ptr(gr),
+            0 if gr is None else gr.shape[0], _ptr(acc), _ptr(pot),
+            threads or DEFAULT_THREADS)
+        assert rc == 0
+        return (acc, pot) if potential else acc

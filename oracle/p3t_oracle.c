@@ -1,0 +1,987 @@
+/*
+ * FP64 CPU oracle for the tree side of the P3T scheme (Iwasawa, Portegies
+ * Zwart & Makino, arXiv:1506.04553).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the independent reference that the
+ * CUDA library is checked against.  Only the test suite, the smoke check and
+ * the CPU-baseline leg of the benchmark may build, load or call it; the
+ * library itself never does.  It shares no source, header, table or helper
+ * with the CUDA path.
+ *
+ * Everything here is deliberately plain: loops over particles in the order the
+ * definitions are written, FP64 arithmetic, no blocking or reordering beyond
+ * what a definition states.  It is compiled with -ffp-contract=off so that
+ * every float/double expression is evaluated exactly as written (IEEE
+ * round-to-nearest, one rounding per operation).
+ *
+ * What follows the paper, and where:
+ *   - cut-off function K(x) ............ Eq. 12-15 (Sect. 2.1)
+ *   - transition function W(y; gamma) .. Eq. 16-17, with the sign of G's
+ *                                         numerator reversed (the printed sign
+ *                                         violates Eq. 9; see orc_W)
+ *   - soft / hard / Newtonian forces ... Eq. 7-9 with the softened distance of
+ *                                         Eq. 2-3
+ *   - soft potential ................... Eq. 6
+ *   - Barnes-Hut tree to quadrupole .... Sect. 2.2 (tree for F_soft on all
+ *                                         particles, up to the quadrupole)
+ *   - neighbour list within h .......... Sect. 2.2 (list of particles within
+ *                                         distance h of each particle)
+ *   - velocity kick / drift ............ Eq. 11 and the step procedure of
+ *                                         Sect. 2.2 (half kicks by F_soft,
+ *                                         drift r <- r + dt v)
+ * Items the paper leaves unstated (key quantisation, leaf and group rules,
+ * the opening test, the quadrupole convention) follow one fixed reading that
+ * is written out at each function.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAX_LEVEL 21
+
+/* ------------------------------------------------------------------------ */
+/* Cut-off function and transition function (Sect. 2.1)                     */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 12: K(x) = 0 for x < 0, -20x^7 + 70x^6 - 84x^5 + 35x^4 on [0, 1),
+ * 1 for x >= 1. */
+double orc_K(double x)
+{
+    if (x < 0.0) return 0.0;
+    if (x >= 1.0) return 1.0;
+    double x2 = x * x;
+    double x3 = x2 * x;
+    double x4 = x2 * x2;
+    double x5 = x4 * x;
+    double x6 = x3 * x3;
+    double x7 = x6 * x;
+    return -20.0 * x7 + 70.0 * x6 - 84.0 * x5 + 35.0 * x4;
+}
+
+/* dK/dx of Eq. 12 (used by the analytic gradient). */
+double orc_dKdx(double x)
+{
+    if (x <= 0.0 || x >= 1.0) return 0.0;
+    double x2 = x * x;
+    double x3 = x2 * x;
+    double x4 = x2 * x2;
+    double x5 = x4 * x;
+    double x6 = x3 * x3;
+    return -140.0 * x6 + 420.0 * x5 - 420.0 * x4 + 140.0 * x3;
+}
+
+/* Eq. 13-15: K as a function of the softened distance s, with y = s/r_cut,
+ * x = (y - gamma)/(1 - gamma). */
+double orc_K_of_s(double s, double r_cut, double gamma)
+{
+    double y = s / r_cut;
+    double x = (y - gamma) / (1.0 - gamma);
+    return orc_K(x);
+}
+
+/* Eq. 17 as printed, G_printed(y; gamma). */
+static double orc_G_printed(double y, double g)
+{
+    double g2 = g * g, g3 = g2 * g, g4 = g3 * g, g5 = g4 * g, g6 = g5 * g,
+           g7 = g6 * g;
+    double y2 = y * y, y3 = y2 * y, y4 = y3 * y, y5 = y4 * y, y6 = y5 * y,
+           y7 = y6 * y;
+    double num = (-10.0 / 3.0) * y7
+               + 14.0 * (g + 1.0) * y6
+               - 21.0 * (g2 + 3.0 * g + 1.0) * y5
+               + (35.0 * (g3 + 9.0 * g2 + 9.0 * g + 1.0) / 3.0) * y4
+               - 70.0 * (g3 + 3.0 * g2 + g) * y3
+               + 210.0 * (g3 + g2) * y2
+               - 140.0 * g3 * y * log(y)
+               + (g7 - 7.0 * g6 + 21.0 * g5 - 35.0 * g4);
+    double d = 1.0 - g;
+    double d7 = d * d * d * d * d * d * d;
+    return num / d7;
+}
+
+/* Slope of W below r_in (first branch of Eq. 16). */
+double orc_W_inner_slope(double g)
+{
+    double g2 = g * g, g3 = g2 * g, g4 = g3 * g, g5 = g4 * g, g6 = g5 * g;
+    double gm1 = g - 1.0;
+    double gm17 = gm1 * gm1 * gm1 * gm1 * gm1 * gm1 * gm1;
+    return 7.0 * (g6 - 9.0 * g5 + 45.0 * g4 - 60.0 * g3 * log(g) - 45.0 * g2
+                  + 9.0 * g - 1.0)
+           / (3.0 * gm17);
+}
+
+/* Eq. 16: the potential transition function W(y; gamma).
+ * Reading: the middle branch uses G = -G_printed.  With the printed sign,
+ * W - y dW/dy differs from K by O(1) on (gamma, 1) and W jumps at y = gamma,
+ * contradicting Eq. 9; with the numerator's sign reversed Eq. 9 holds and W
+ * is continuous at y = gamma and y = 1. */
+double orc_W(double y, double g)
+{
+    if (y >= 1.0) return 1.0;
+    if (y < g) return orc_W_inner_slope(g) * y;
+    double G1 = -orc_G_printed(1.0, g);
+    return -orc_G_printed(y, g) + (1.0 - G1) * y;
+}
+
+/* W(s/r_cut)/s, the soft pair potential per unit G m_i m_j (Eq. 6), with its
+ * finite limit inside r_in where W is linear in y. */
+static double orc_W_over_s(double s, double r_cut, double g)
+{
+    double y = s / r_cut;
+    if (y < g) return orc_W_inner_slope(g) / r_cut;
+    return orc_W(y, g) / s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* A plain parallel-for over index ranges (used only to make the oracle     */
+/* finish in reasonable time; each index is computed independently).        */
+/* ------------------------------------------------------------------------ */
+
+typedef void (*orc_range_fn)(void *arg, int64_t lo, int64_t hi);
+
+typedef struct {
+    orc_range_fn fn;
+    void *arg;
+    int64_t lo, hi;
+} orc_job;
+
+static void *orc_job_main(void *p)
+{
+    orc_job *j = (orc_job *)p;
+    j->fn(j->arg, j->lo, j->hi);
+    return NULL;
+}
+
+static void orc_parallel_for(int64_t n, int nthreads, orc_range_fn fn,
+                             void *arg)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if (n < 2 * nthreads || nthreads == 1) {
+        fn(arg, 0, n);
+        return;
+    }
+    pthread_t th[256];
+    orc_job jobs[256];
+    /* interleave work in small chunks so uneven per-index costs balance */
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].fn = fn;
+        jobs[t].arg = arg;
+        jobs[t].lo = (n * t) / nthreads;
+        jobs[t].hi = (n * (t + 1)) / nthreads;
+        pthread_create(&th[t], NULL, orc_job_main, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Direct summation (the plain definition of Eq. 7-9 and Eq. 6)             */
+/* ------------------------------------------------------------------------ */
+
+enum { ORC_SOFT = 0, ORC_HARD = 1, ORC_NEWTON = 2 };
+
+typedef struct {
+    int64_t n;
+    const double *pos; /* n x 3, row-major */
+    const double *m;
+    double G, eps, r_cut, gamma;
+    int kind;
+    double *acc; /* n x 3 */
+    double *pot; /* n or NULL */
+    const int64_t *rows; /* NULL: all i; else the i to evaluate */
+} orc_direct_args;
+
+/* Pair weight for the force (Eq. 7 hard: 1-K, Eq. 8 soft: K, Newton: 1). */
+static double orc_force_weight(int kind, double s, double r_cut, double g)
+{
+    if (kind == ORC_NEWTON) return 1.0;
+    double K = orc_K_of_s(s, r_cut, g);
+    return kind == ORC_SOFT ? K : 1.0 - K;
+}
+
+/* Pair potential per unit G m_j: soft W/s (Eq. 6), hard (1-W)/s (Eq. 5). */
+static double orc_pot_weight(int kind, double s, double r_cut, double g)
+{
+    if (kind == ORC_NEWTON) return 1.0 / s;
+    double wos = orc_W_over_s(s, r_cut, g);
+    return kind == ORC_SOFT ? wos : 1.0 / s - wos;
+}
+
+static void orc_direct_range(void *p, int64_t lo, int64_t hi)
+{
+    orc_direct_args *a = (orc_direct_args *)p;
+    double eps2 = a->eps * a->eps;
+    for (int64_t r = lo; r < hi; ++r) {
+        int64_t i = a->rows ? a->rows[r] : r;
+        double ax = 0.0, ay = 0.0, az = 0.0, ph = 0.0;
+        for (int64_t j = 0; j < a->n; ++j) {
+            if (j == i) continue;
+            /* q_ij = q_i - q_j (Eq. 3), s_ij = sqrt(|q_ij|^2 + eps^2) (Eq. 2) */
+            double qx = a->pos[3 * i + 0] - a->pos[3 * j + 0];
+            double qy = a->pos[3 * i + 1] - a->pos[3 * j + 1];
+            double qz = a->pos[3 * i + 2] - a->pos[3 * j + 2];
+            double s2 = qx * qx + qy * qy + qz * qz + eps2;
+            double s = sqrt(s2);
+            double w = orc_force_weight(a->kind, s, a->r_cut, a->gamma);
+            if (w != 0.0) {
+                /* acceleration of i: F_i / m_i = -G m_j w q_ij / s^3 */
+                double f = -a->G * a->m[j] * w / (s2 * s);
+                ax += f * qx;
+                ay += f * qy;
+                az += f * qz;
+            }
+            if (a->pot) ph -= a->G * a->m[j]
+                              * orc_pot_weight(a->kind, s, a->r_cut, a->gamma);
+        }
+        a->acc[3 * r + 0] = ax;
+        a->acc[3 * r + 1] = ay;
+        a->acc[3 * r + 2] = az;
+        if (a->pot) a->pot[r] = ph;
+    }
+}
+
+/* Acceleration (and optionally potential) by direct summation over all
+ * j != i.  rows == NULL evaluates every particle; otherwise only rows[0..nr)
+ * and the outputs are indexed by position in rows. */
+void orc_direct(int64_t n, const double *pos, const double *m, double G,
+                double eps, double r_cut, double gamma, int kind,
+                const int64_t *rows, int64_t nr, double *acc, double *pot,
+                int nthreads)
+{
+    orc_direct_args a = {n, pos, m, G, eps, r_cut, gamma, kind, acc, pot,
+                         rows};
+    orc_parallel_for(rows ? nr : n, nthreads, orc_direct_range, &a);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neighbour lists by brute force (Sect. 2.2: particles within distance h)  */
+/* Predicate: j != i and ((dx*dx + dy*dy) + dz*dz) < h*h in FP64, with      */
+/* dx = x_i - x_j; the unsoftened distance, strict inequality.              */
+/* ------------------------------------------------------------------------ */
+
+int orc_is_neighbour(const double *pi, const double *pj, double h)
+{
+    double dx = pi[0] - pj[0];
+    double dy = pi[1] - pj[1];
+    double dz = pi[2] - pj[2];
+    double r2 = (dx * dx + dy * dy) + dz * dz;
+    return r2 < h * h;
+}
+
+typedef struct {
+    int64_t n;
+    const double *pos;
+    double h;
+    const int64_t *rows;
+    int64_t *count; /* per row */
+    const int64_t *offsets; /* NULL in the counting pass */
+    int32_t *idx;
+} orc_ngb_args;
+
+static void orc_ngb_range(void *p, int64_t lo, int64_t hi)
+{
+    orc_ngb_args *a = (orc_ngb_args *)p;
+    for (int64_t r = lo; r < hi; ++r) {
+        int64_t i = a->rows ? a->rows[r] : r;
+        int64_t c = 0;
+        for (int64_t j = 0; j < a->n; ++j) {
+            if (j == i) continue;
+            if (orc_is_neighbour(a->pos + 3 * i, a->pos + 3 * j, a->h)) {
+                if (a->offsets) a->idx[a->offsets[r] + c] = (int32_t)j;
+                ++c;
+            }
+        }
+        a->count[r] = c;
+    }
+}
+
+/* Counting pass: count[r] = number of neighbours of row r. */
+void orc_neighbours_count(int64_t n, const double *pos, double h,
+                          const int64_t *rows, int64_t nr, int64_t *count,
+                          int nthreads)
+{
+    orc_ngb_args a = {n, pos, h, rows, count, NULL, NULL};
+    orc_parallel_for(rows ? nr : n, nthreads, orc_ngb_range, &a);
+}
+
+/* Filling pass: indices of row r (ascending j) at idx[offsets[r] ...]. */
+void orc_neighbours_fill(int64_t n, const double *pos, double h,
+                         const int64_t *rows, int64_t nr,
+                         const int64_t *offsets, int32_t *idx, int64_t *count,
+                         int nthreads)
+{
+    orc_ngb_args a = {n, pos, h, rows, count, offsets, idx};
+    orc_parallel_for(rows ? nr : n, nthreads, orc_ngb_range, &a);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Leapfrog pieces (Eq. 11; Sect. 2.2 steps: kick by F_soft for dt/2,       */
+/* drift r <- r + dt v)                                                     */
+/* ------------------------------------------------------------------------ */
+
+void orc_kick(int64_t n3, double *v, const float *a, double dt_half)
+{
+    for (int64_t k = 0; k < n3; ++k) v[k] = v[k] + dt_half * (double)a[k];
+}
+
+void orc_drift(int64_t n3, double *x, const double *v, double dt)
+{
+    for (int64_t k = 0; k < n3; ++k) x[k] = x[k] + dt * v[k];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Barnes-Hut octree to quadrupole order (Sect. 2.2)                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct orc_tree {
+    int64_t n;
+    int n_leaf, n_group;
+    double lo[3], size;
+    uint64_t *key;   /* keys in sorted order */
+    int64_t *order;  /* order[k] = original index of the k-th sorted particle */
+    double *x;       /* sorted positions, n x 3 */
+    double *m;       /* sorted masses */
+    /* cells, in breadth-first order; children of a cell are contiguous and
+     * in Morton (digit) order */
+    int64_t ncell, cap_cell;
+    int32_t *level;
+    int64_t *first, *count, *parent, *child_first;
+    int32_t *nchild;
+    double *M, *com, *Q;   /* Q: xx, yy, zz, xy, xz, yz */
+    double *bmin, *bmax;   /* member bounding box, FP64 */
+    float *fmin, *fmax;    /* the same box rounded outward to FP32 */
+    /* groups (i-particle sets sharing one interaction list) */
+    int64_t ngroup, cap_group;
+    int64_t *g_first, *g_count;
+    float *g_fmin, *g_fmax;
+    /* interaction lists, filled by orc_tree_walk */
+    int walked;
+    int64_t *pc_off, *ppn_off, *ppf_off; /* ngroup + 1 */
+    int64_t *pc, *ppn, *ppf;             /* cell ids / sorted particle ids */
+} orc_tree;
+
+/* Level-L Morton digit (L = 1..21): three bits, x highest. */
+static int orc_digit(uint64_t key, int L)
+{
+    return (int)((key >> (3 * (ORC_MAX_LEVEL - L))) & 7u);
+}
+
+/* Quantised integer coordinate along one axis: floor((x - lo)/size * 2^21),
+ * clamped to [0, 2^21 - 1], each operation rounded once in FP64. */
+static int64_t orc_quantise(double x, double lo, double size)
+{
+    double t = x - lo;
+    double u = t / size;
+    double v = u * 2097152.0;
+    int64_t q = (int64_t)floor(v);
+    if (q < 0) q = 0;
+    if (q > 2097151) q = 2097151;
+    return q;
+}
+
+/* 63-bit Morton key: for bit b = 20..0 the triple (x_b, y_b, z_b), x highest. */
+uint64_t orc_morton_key(double x, double y, double z, const double *lo,
+                        double size)
+{
+    int64_t q[3] = {orc_quantise(x, lo[0], size), orc_quantise(y, lo[1], size),
+                    orc_quantise(z, lo[2], size)};
+    uint64_t key = 0;
+    for (int b = ORC_MAX_LEVEL - 1; b >= 0; --b) {
+        key = (key << 3) | ((uint64_t)((q[0] >> b) & 1) << 2)
+              | ((uint64_t)((q[1] >> b) & 1) << 1) | (uint64_t)((q[2] >> b) & 1);
+    }
+    return key;
+}
+
+/* Root cube: lo = componentwise minimum; ext = largest extent; size =
+ * ext * (1 + 2^-20) so the cube strictly encloses every particle; size = 1
+ * when all particles coincide. */
+void orc_root_box(int64_t n, const double *pos, double *lo, double *size)
+{
+    double mn[3], mx[3];
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = pos[a];
+        mx[a] = pos[a];
+    }
+    for (int64_t i = 1; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            if (pos[3 * i + a] < mn[a]) mn[a] = pos[3 * i + a];
+            if (pos[3 * i + a] > mx[a]) mx[a] = pos[3 * i + a];
+        }
+    double ext = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double e = mx[a] - mn[a];
+        if (e > ext) ext = e;
+        lo[a] = mn[a];
+    }
+    *size = (ext == 0.0) ? 1.0 : ext * (1.0 + 0x1p-20);
+}
+
+/* FP64 -> FP32 rounded toward -inf / +inf. */
+static float orc_round_down(double v)
+{
+    float f = (float)v;
+    if ((double)f > v) f = nextafterf(f, -INFINITY);
+    return f;
+}
+static float orc_round_up(double v)
+{
+    float f = (float)v;
+    if ((double)f < v) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+typedef struct {
+    uint64_t key;
+    int64_t idx;
+} orc_kv;
+
+static int orc_kv_cmp(const void *a, const void *b)
+{
+    const orc_kv *p = (const orc_kv *)a, *q = (const orc_kv *)b;
+    if (p->key != q->key) return p->key < q->key ? -1 : 1;
+    if (p->idx != q->idx) return p->idx < q->idx ? -1 : 1;
+    return 0;
+}
+
+static void orc_cell_reserve(orc_tree *t)
+{
+    if (t->ncell < t->cap_cell) return;
+    int64_t c = t->cap_cell ? 2 * t->cap_cell : 1024;
+    t->level = realloc(t->level, c * sizeof(int32_t));
+    t->first = realloc(t->first, c * sizeof(int64_t));
+    t->count = realloc(t->count, c * sizeof(int64_t));
+    t->parent = realloc(t->parent, c * sizeof(int64_t));
+    t->child_first = realloc(t->child_first, c * sizeof(int64_t));
+    t->nchild = realloc(t->nchild, c * sizeof(int32_t));
+    t->cap_cell = c;
+}
+
+static int64_t orc_cell_add(orc_tree *t, int level, int64_t first,
+                            int64_t count, int64_t parent)
+{
+    orc_cell_reserve(t);
+    int64_t c = t->ncell++;
+    t->level[c] = level;
+    t->first[c] = first;
+    t->count[c] = count;
+    t->parent[c] = parent;
+    t->child_first[c] = -1;
+    t->nchild[c] = 0;
+    return c;
+}
+
+/* Multipole moments of a cell directly from its member particles:
+ * M = sum m, com = sum m x / M, Q_ab = sum m (3 d_a d_b - |d|^2 delta_ab)
+ * with d = x - com (traceless quadrupole about the centre of mass). */
+static void orc_cell_moments(orc_tree *t, int64_t c)
+{
+    int64_t f = t->first[c], n = t->count[c];
+    double M = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+    for (int64_t k = f; k < f + n; ++k) {
+        M += t->m[k];
+        cx += t->m[k] * t->x[3 * k + 0];
+        cy += t->m[k] * t->x[3 * k + 1];
+        cz += t->m[k] * t->x[3 * k + 2];
+    }
+    cx /= M;
+    cy /= M;
+    cz /= M;
+    double Q[6] = {0, 0, 0, 0, 0, 0};
+    double bmn[3], bmx[3];
+    for (int a = 0; a < 3; ++a) {
+        bmn[a] = t->x[3 * f + a];
+        bmx[a] = t->x[3 * f + a];
+    }
+    for (int64_t k = f; k < f + n; ++k) {
+        double dx = t->x[3 * k + 0] - cx;
+        double dy = t->x[3 * k + 1] - cy;
+        double dz = t->x[3 * k + 2] - cz;
+        double d2 = dx * dx + dy * dy + dz * dz;
+        double mk = t->m[k];
+        Q[0] += mk * (3.0 * dx * dx - d2);
+        Q[1] += mk * (3.0 * dy * dy - d2);
+        Q[2] += mk * (3.0 * dz * dz - d2);
+        Q[3] += mk * (3.0 * dx * dy);
+        Q[4] += mk * (3.0 * dx * dz);
+        Q[5] += mk * (3.0 * dy * dz);
+        for (int a = 0; a < 3; ++a) {
+            if (t->x[3 * k + a] < bmn[a]) bmn[a] = t->x[3 * k + a];
+            if (t->x[3 * k + a] > bmx[a]) bmx[a] = t->x[3 * k + a];
+        }
+    }
+    t->M[c] = M;
+    t->com[3 * c + 0] = cx;
+    t->com[3 * c + 1] = cy;
+    t->com[3 * c + 2] = cz;
+    for (int q = 0; q < 6; ++q) t->Q[6 * c + q] = Q[q];
+    for (int a = 0; a < 3; ++a) {
+        t->bmin[3 * c + a] = bmn[a];
+        t->bmax[3 * c + a] = bmx[a];
+        t->fmin[3 * c + a] = orc_round_down(bmn[a]);
+        t->fmax[3 * c + a] = orc_round_up(bmx[a]);
+    }
+}
+
+static int orc_is_leaf(const orc_tree *t, int64_t c)
+{
+    return t->nchild[c] == 0;
+}
+
+static void orc_group_add(orc_tree *t, int64_t first, int64_t count)
+{
+    if (t->ngroup == t->cap_group) {
+        int64_t c = t->cap_group ? 2 * t->cap_group : 1024;
+        t->g_first = realloc(t->g_first, c * sizeof(int64_t));
+        t->g_count = realloc(t->g_count, c * sizeof(int64_t));
+        t->cap_group = c;
+    }
+    t->g_first[t->ngroup] = first;
+    t->g_count[t->ngroup] = count;
+    t->ngroup++;
+}
+
+/* A range larger than n_group is cut into consecutive chunks of n_group. */
+static void orc_group_add_chunked(orc_tree *t, int64_t first, int64_t count)
+{
+    for (int64_t k = 0; k < count; k += t->n_group) {
+        int64_t c = count - k < t->n_group ? count - k : t->n_group;
+        orc_group_add(t, first + k, c);
+    }
+}
+
+/* Groups below an internal cell with more than n_group particles: runs of
+ * consecutive children that each hold at most n_group particles are merged
+ * greedily while the run holds at most n_group; a larger child closes the
+ * run and is itself descended (or chunked if it is a leaf). */
+static void orc_groups_below(orc_tree *t, int64_t c)
+{
+    int64_t run_first = 0, run_count = 0;
+    for (int k = 0; k < t->nchild[c]; ++k) {
+        int64_t ch = t->child_first[c] + k;
+        if (t->count[ch] <= t->n_group) {
+            if (run_count > 0 && run_count + t->count[ch] > t->n_group) {
+                orc_group_add(t, run_first, run_count);
+                run_count = 0;
+            }
+            if (run_count == 0) run_first = t->first[ch];
+            run_count += t->count[ch];
+        } else {
+            if (run_count > 0) {
+                orc_group_add(t, run_first, run_count);
+                run_count = 0;
+            }
+            if (orc_is_leaf(t, ch))
+                orc_group_add_chunked(t, t->first[ch], t->count[ch]);
+            else
+                orc_groups_below(t, ch);
+        }
+    }
+    if (run_count > 0) orc_group_add(t, run_first, run_count);
+}
+
+/* Build the tree for n particles (pos n x 3 row-major, masses m > 0).
+ * Steps: root cube, Morton keys, sort by (key, original index), split every
+ * cell holding more than n_leaf particles (and above level 21) into its
+ * non-empty octants, moments per cell, groups. */
+orc_tree *orc_tree_build(int64_t n, const double *pos, const double *m,
+                         int n_leaf, int n_group)
+{
+    orc_tree *t = calloc(1, sizeof(orc_tree));
+    t->n = n;
+    t->n_leaf = n_leaf;
+    t->n_group = n_group;
+    if (n <= 0) return t;
+    orc_root_box(n, pos, t->lo, &t->size);
+
+    orc_kv *kv = malloc(n * sizeof(orc_kv));
+    for (int64_t i = 0; i < n; ++i) {
+        kv[i].key = orc_morton_key(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2],
+                                   t->lo, t->size);
+        kv[i].idx = i;
+    }
+    qsort(kv, n, sizeof(orc_kv), orc_kv_cmp);
+    t->key = malloc(n * sizeof(uint64_t));
+    t->order = malloc(n * sizeof(int64_t));
+    t->x = malloc(3 * n * sizeof(double));
+    t->m = malloc(n * sizeof(double));
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t i = kv[k].idx;
+        t->key[k] = kv[k].key;
+        t->order[k] = i;
+        for (int a = 0; a < 3; ++a) t->x[3 * k + a] = pos[3 * i + a];
+        t->m[k] = m[i];
+    }
+    free(kv);
+
+    /* breadth-first split */
+    orc_cell_add(t, 0, 0, n, -1);
+    for (int64_t c = 0; c < t->ncell; ++c) {
+        if (t->count[c] <= n_leaf || t->level[c] >= ORC_MAX_LEVEL) continue;
+        int L = t->level[c] + 1;
+        int64_t f = t->first[c], e = f + t->count[c];
+        int64_t start = f;
+        t->child_first[c] = t->ncell;
+        while (start < e) {
+            int d = orc_digit(t->key[start], L);
+            int64_t stop = start;
+            while (stop < e && orc_digit(t->key[stop], L) == d) ++stop;
+            orc_cell_add(t, L, start, stop - start, c);
+            t->nchild[c]++;
+            start = stop;
+        }
+    }
+
+    int64_t C = t->ncell;
+    t->M = malloc(C * sizeof(double));
+    t->com = malloc(3 * C * sizeof(double));
+    t->Q = malloc(6 * C * sizeof(double));
+    t->bmin = malloc(3 * C * sizeof(double));
+    t->bmax = malloc(3 * C * sizeof(double));
+    t->fmin = malloc(3 * C * sizeof(float));
+    t->fmax = malloc(3 * C * sizeof(float));
+    for (int64_t c = 0; c < C; ++c) orc_cell_moments(t, c);
+
+    if (t->count[0] <= n_group || orc_is_leaf(t, 0))
+        orc_group_add_chunked(t, 0, n);
+    else
+        orc_groups_below(t, 0);
+    t->g_fmin = malloc(3 * t->ngroup * sizeof(float));
+    t->g_fmax = malloc(3 * t->ngroup * sizeof(float));
+    for (int64_t g = 0; g < t->ngroup; ++g) {
+        int64_t f = t->g_first[g];
+        for (int a = 0; a < 3; ++a) {
+            double mn = t->x[3 * f + a], mx = t->x[3 * f + a];
+            for (int64_t k = f; k < f + t->g_count[g]; ++k) {
+                if (t->x[3 * k + a] < mn) mn = t->x[3 * k + a];
+                if (t->x[3 * k + a] > mx) mx = t->x[3 * k + a];
+            }
+            t->g_fmin[3 * g + a] = orc_round_down(mn);
+            t->g_fmax[3 * g + a] = orc_round_up(mx);
+        }
+    }
+    return t;
+}
+
+void orc_tree_free(orc_tree *t)
+{
+    if (!t) return;
+    void *ptrs[] = {t->key, t->order, t->x, t->m, t->level, t->first,
+                    t->count, t->parent, t->child_first, t->nchild, t->M,
+                    t->com, t->Q, t->bmin, t->bmax, t->fmin, t->fmax,
+                    t->g_first, t->g_count, t->g_fmin, t->g_fmax, t->pc_off,
+                    t->ppn_off, t->ppf_off, t->pc, t->ppn, t->ppf};
+    for (size_t k = 0; k < sizeof(ptrs) / sizeof(ptrs[0]); ++k) free(ptrs[k]);
+    free(t);
+}
+
+/* ---- accessors for the Python side ---- */
+int64_t orc_tree_n(const orc_tree *t) { return t->n; }
+int64_t orc_tree_ncell(const orc_tree *t) { return t->ncell; }
+int64_t orc_tree_ngroup(const orc_tree *t) { return t->ngroup; }
+void orc_tree_root(const orc_tree *t, double *lo3, double *size)
+{
+    for (int a = 0; a < 3; ++a) lo3[a] = t->lo[a];
+    *size = t->size;
+}
+void orc_tree_particles(const orc_tree *t, uint64_t *key, int64_t *order)
+{
+    memcpy(key, t->key, t->n * sizeof(uint64_t));
+    memcpy(order, t->order, t->n * sizeof(int64_t));
+}
+void orc_tree_cells(const orc_tree *t, int32_t *level, int64_t *first,
+                    int64_t *count, int64_t *parent, int64_t *child_first,
+                    int32_t *nchild, double *M, double *com, double *Q,
+                    float *fmin, float *fmax)
+{
+    int64_t C = t->ncell;
+    memcpy(level, t->level, C * sizeof(int32_t));
+    memcpy(first, t->first, C * sizeof(int64_t));
+    memcpy(count, t->count, C * sizeof(int64_t));
+    memcpy(parent, t->parent, C * sizeof(int64_t));
+    memcpy(child_first, t->child_first, C * sizeof(int64_t));
+    memcpy(nchild, t->nchild, C * sizeof(int32_t));
+    memcpy(M, t->M, C * sizeof(double));
+    memcpy(com, t->com, 3 * C * sizeof(double));
+    memcpy(Q, t->Q, 6 * C * sizeof(double));
+    memcpy(fmin, t->fmin, 3 * C * sizeof(float));
+    memcpy(fmax, t->fmax, 3 * C * sizeof(float));
+}
+void orc_tree_groups(const orc_tree *t, int64_t *first, int64_t *count,
+                     float *fmin, float *fmax)
+{
+    memcpy(first, t->g_first, t->ngroup * sizeof(int64_t));
+    memcpy(count, t->g_count, t->ngroup * sizeof(int64_t));
+    memcpy(fmin, t->g_fmin, 3 * t->ngroup * sizeof(float));
+    memcpy(fmax, t->g_fmax, 3 * t->ngroup * sizeof(float));
+}
+
+/* ---- the opening test (paper: "opening criterion theta"; form unstated) ----
+ * Reading used here.  For group box B_g and cell member box B_c (both the
+ * FP64 boxes rounded outward to FP32), with all arithmetic in FP32, one
+ * rounding per operation, in this order:
+ *   gap_a = max(max(cmin_a - gmax_a, gmin_a - cmax_a), 0)
+ *   d2    = (gap_x*gap_x + gap_y*gap_y) + gap_z*gap_z
+ *   l     = max(max(cmax_x - cmin_x, cmax_y - cmin_y), cmax_z - cmin_z)
+ *   accept  <=>  l*l < theta2*d2  and  d2 > hg2
+ * with theta2 = fl(theta)*fl(theta) and hg2 = (hg*hg)*(1 + 2^-10),
+ * hg = fl(max(h, r_cut)).  The second clause keeps every pair closer than
+ * max(h, r_cut) out of the cell list, so cells are evaluated with K = 1 and
+ * every neighbour candidate is met particle by particle. */
+typedef struct {
+    float theta2, hg2;
+} orc_mac;
+
+static orc_mac orc_mac_make(double theta, double h, double r_cut)
+{
+    orc_mac k;
+    float th = (float)theta;
+    k.theta2 = th * th;
+    float hg = (float)(h > r_cut ? h : r_cut);
+    float hh = hg * hg;
+    k.hg2 = hh * 1.0009765625f;
+    return k;
+}
+
+static float orc_box_d2(const float *gmin, const float *gmax,
+                        const float *cmin, const float *cmax)
+{
+    float gap[3];
+    for (int a = 0; a < 3; ++a) {
+        float u = cmin[a] - gmax[a];
+        float v = gmin[a] - cmax[a];
+        float w = fmaxf(u, v);
+        gap[a] = fmaxf(w, 0.0f);
+    }
+    float gx2 = gap[0] * gap[0];
+    float gy2 = gap[1] * gap[1];
+    float gz2 = gap[2] * gap[2];
+    float s = gx2 + gy2;
+    return s + gz2;
+}
+
+static float orc_box_side(const float *cmin, const float *cmax)
+{
+    float lx = cmax[0] - cmin[0];
+    float ly = cmax[1] - cmin[1];
+    float lz = cmax[2] - cmin[2];
+    return fmaxf(fmaxf(lx, ly), lz);
+}
+
+/* growable int64 list */
+typedef struct {
+    int64_t *v;
+    int64_t n, cap;
+} orc_vec;
+static void orc_vec_push(orc_vec *a, int64_t x)
+{
+    if (a->n == a->cap) {
+        a->cap = a->cap ? 2 * a->cap : 256;
+        a->v = realloc(a->v, a->cap * sizeof(int64_t));
+    }
+    a->v[a->n++] = x;
+}
+
+/* Visit cell c for group g: accepted -> cell list; a leaf that is not
+ * accepted -> its particles go to the near list (d2 <= hg2) or the far list;
+ * otherwise descend into the children. */
+static void orc_visit(const orc_tree *t, int64_t g, int64_t c, orc_mac mac,
+                      orc_vec *pc, orc_vec *ppn, orc_vec *ppf)
+{
+    const float *gmin = t->g_fmin + 3 * g, *gmax = t->g_fmax + 3 * g;
+    const float *cmin = t->fmin + 3 * c, *cmax = t->fmax + 3 * c;
+    float d2 = orc_box_d2(gmin, gmax, cmin, cmax);
+    float l = orc_box_side(cmin, cmax);
+    float ll = l * l;
+    float td = mac.theta2 * d2;
+    if (ll < td && d2 > mac.hg2) {
+        orc_vec_push(pc, c);
+        return;
+    }
+    if (orc_is_leaf(t, c)) {
+        orc_vec *dst = (d2 <= mac.hg2) ? ppn : ppf;
+        for (int64_t k = t->first[c]; k < t->first[c] + t->count[c]; ++k)
+            orc_vec_push(dst, k);
+        return;
+    }
+    for (int k = 0; k < t->nchild[c]; ++k)
+        orc_visit(t, g, t->child_first[c] + k, mac, pc, ppn, ppf);
+}
+
+typedef struct {
+    const orc_tree *t;
+    orc_mac mac;
+    orc_vec *pc, *ppn, *ppf;
+} orc_walk_args;
+
+static void orc_walk_range(void *p, int64_t lo, int64_t hi)
+{
+    orc_walk_args *a = (orc_walk_args *)p;
+    for (int64_t g = lo; g < hi; ++g)
+        orc_visit(a->t, g, 0, a->mac, &a->pc[g], &a->ppn[g], &a->ppf[g]);
+}
+
+/* Interaction lists of every group.  Returns total sizes through out3
+ * (cells, near particles, far particles). */
+void orc_tree_walk(orc_tree *t, double theta, double h, double r_cut,
+                   int nthreads, int64_t *out3)
+{
+    int64_t G = t->ngroup;
+    orc_walk_args a;
+    a.t = t;
+    a.mac = orc_mac_make(theta, h, r_cut);
+    a.pc = calloc(G ? G : 1, sizeof(orc_vec));
+    a.ppn = calloc(G ? G : 1, sizeof(orc_vec));
+    a.ppf = calloc(G ? G : 1, sizeof(orc_vec));
+    orc_parallel_for(G, nthreads, orc_walk_range, &a);
+    free(t->pc_off); free(t->ppn_off); free(t->ppf_off);
+    free(t->pc); free(t->ppn); free(t->ppf);
+    t->pc_off = calloc(G + 1, sizeof(int64_t));
+    t->ppn_off = calloc(G + 1, sizeof(int64_t));
+    t->ppf_off = calloc(G + 1, sizeof(int64_t));
+    for (int64_t g = 0; g < G; ++g) {
+        t->pc_off[g + 1] = t->pc_off[g] + a.pc[g].n;
+        t->ppn_off[g + 1] = t->ppn_off[g] + a.ppn[g].n;
+        t->ppf_off[g + 1] = t->ppf_off[g] + a.ppf[g].n;
+    }
+    t->pc = malloc((t->pc_off[G] + 1) * sizeof(int64_t));
+    t->ppn = malloc((t->ppn_off[G] + 1) * sizeof(int64_t));
+    t->ppf = malloc((t->ppf_off[G] + 1) * sizeof(int64_t));
+    for (int64_t g = 0; g < G; ++g) {
+        if (a.pc[g].n)
+            memcpy(t->pc + t->pc_off[g], a.pc[g].v, a.pc[g].n * sizeof(int64_t));
+        if (a.ppn[g].n)
+            memcpy(t->ppn + t->ppn_off[g], a.ppn[g].v,
+                   a.ppn[g].n * sizeof(int64_t));
+        if (a.ppf[g].n)
+            memcpy(t->ppf + t->ppf_off[g], a.ppf[g].v,
+                   a.ppf[g].n * sizeof(int64_t));
+        free(a.pc[g].v);
+        free(a.ppn[g].v);
+        free(a.ppf[g].v);
+    }
+    free(a.pc);
+    free(a.ppn);
+    free(a.ppf);
+    t->walked = 1;
+    out3[0] = t->pc_off[G];
+    out3[1] = t->ppn_off[G];
+    out3[2] = t->ppf_off[G];
+}
+
+void orc_tree_lists(const orc_tree *t, int64_t *pc_off, int64_t *pc,
+                    int64_t *ppn_off, int64_t *ppn, int64_t *ppf_off,
+                    int64_t *ppf)
+{
+    int64_t G = t->ngroup;
+    memcpy(pc_off, t->pc_off, (G + 1) * sizeof(int64_t));
+    memcpy(ppn_off, t->ppn_off, (G + 1) * sizeof(int64_t));
+    memcpy(ppf_off, t->ppf_off, (G + 1) * sizeof(int64_t));
+    memcpy(pc, t->pc, t->pc_off[G] * sizeof(int64_t));
+    memcpy(ppn, t->ppn, t->ppn_off[G] * sizeof(int64_t));
+    memcpy(ppf, t->ppf, t->ppf_off[G] * sizeof(int64_t));
+}
+
+/* ---- tree forces ---- */
+
+/* Softened quadrupole expansion about the cell's centre of mass.  With
+ * r = x_i - com and s^2 = |r|^2 + eps^2:
+ *   phi = -G M / s - (G/2) r.Q.r / s^5
+ *   a   = -grad phi = -G M r / s^3 + G Q r / s^5 - (5/2) G (r.Q.r) r / s^7 */
+static void orc_cell_accel(const orc_tree *t, int64_t c, const double *xi,
+                           double G, double eps2, double *acc, double *pot)
+{
+    const double *Q = t->Q + 6 * c;
+    double rx = xi[0] - t->com[3 * c + 0];
+    double ry = xi[1] - t->com[3 * c + 1];
+    double rz = xi[2] - t->com[3 * c + 2];
+    double s2 = rx * rx + ry * ry + rz * rz + eps2;
+    double s = sqrt(s2);
+    double s3 = s2 * s, s5 = s3 * s2, s7 = s5 * s2;
+    double Qrx = Q[0] * rx + Q[3] * ry + Q[4] * rz;
+    double Qry = Q[3] * rx + Q[1] * ry + Q[5] * rz;
+    double Qrz = Q[4] * rx + Q[5] * ry + Q[2] * rz;
+    double rQr = rx * Qrx + ry * Qry + rz * Qrz;
+    double M = t->M[c];
+    acc[0] += -G * M * rx / s3 + G * Qrx / s5 - 2.5 * G * rQr * rx / s7;
+    acc[1] += -G * M * ry / s3 + G * Qry / s5 - 2.5 * G * rQr * ry / s7;
+    acc[2] += -G * M * rz / s3 + G * Qrz / s5 - 2.5 * G * rQr * rz / s7;
+    *pot += -G * M / s - 0.5 * G * rQr / s5;
+}
+
+/* Soft pair term of Eq. 8 (per unit m_i) and Eq. 6 for sorted particle j. */
+static void orc_pair_soft(const orc_tree *t, int64_t j, const double *xi,
+                          double G, double eps2, double r_cut, double gamma,
+                          double *acc, double *pot)
+{
+    double qx = xi[0] - t->x[3 * j + 0];
+    double qy = xi[1] - t->x[3 * j + 1];
+    double qz = xi[2] - t->x[3 * j + 2];
+    double s2 = qx * qx + qy * qy + qz * qz + eps2;
+    double s = sqrt(s2);
+    double K = orc_K_of_s(s, r_cut, gamma);
+    if (K != 0.0) {
+        double f = -G * t->m[j] * K / (s2 * s);
+        acc[0] += f * qx;
+        acc[1] += f * qy;
+        acc[2] += f * qz;
+    }
+    *pot += -G * t->m[j] * orc_W_over_s(s, r_cut, gamma);
+}
+
+typedef struct {
+    const orc_tree *t;
+    double G, eps2, r_cut, gamma;
+    const int64_t *groups; /* groups to evaluate, NULL = all */
+    double *acc, *pot;     /* indexed by ORIGINAL particle index */
+} orc_force_args;
+
+static void orc_force_range(void *p, int64_t lo, int64_t hi)
+{
+    orc_force_args *a = (orc_force_args *)p;
+    const orc_tree *t = a->t;
+    for (int64_t r = lo; r < hi; ++r) {
+        int64_t g = a->groups ? a->groups[r] : r;
+        for (int64_t i = t->g_first[g]; i < t->g_first[g] + t->g_count[g]; ++i) {
+            const double *xi = t->x + 3 * i;
+            double acc[3] = {0, 0, 0}, pot = 0.0;
+            for (int64_t k = t->pc_off[g]; k < t->pc_off[g + 1]; ++k)
+                orc_cell_accel(t, t->pc[k], xi, a->G, a->eps2, acc, &pot);
+            for (int64_t k = t->ppf_off[g]; k < t->ppf_off[g + 1]; ++k)
+                orc_pair_soft(t, t->ppf[k], xi, a->G, a->eps2, a->r_cut,
+                              a->gamma, acc, &pot);
+            for (int64_t k = t->ppn_off[g]; k < t->ppn_off[g + 1]; ++k) {
+                if (t->ppn[k] == i) continue;
+                orc_pair_soft(t, t->ppn[k], xi, a->G, a->eps2, a->r_cut,
+                              a->gamma, acc, &pot);
+            }
+            int64_t o = t->order[i];
+            for (int c = 0; c < 3; ++c) a->acc[3 * o + c] = acc[c];
+            if (a->pot) a->pot[o] = pot;
+        }
+    }
+}
+
+/* Tree acceleration (and soft potential) of the particles of the listed
+ * groups (all groups if groups == NULL), written at their ORIGINAL indices
+ * of acc (n x 3) and pot (n).  Requires orc_tree_walk first. */
+int orc_tree_force(const orc_tree *t, double G, double eps, double r_cut,
+                   double gamma, const int64_t *groups, int64_t ng,
+                   double *acc, double *pot, int nthreads)
+{
+    if (!t->walked) return -1;
+    orc_force_args a = {t, G, eps * eps, r_cut, gamma, groups, acc, pot};
+    orc_parallel_for(groups ? ng : t->ngroup, nthreads, orc_force_range, &a);
+    return 0;
+}
+
+/* Group that holds sorted particle k (groups are disjoint contiguous ranges
+ * whose union is [0, n)). */
+int64_t orc_tree_group_of(const orc_tree *t, int64_t k)
+{
+    for (int64_t g = 0; g < t->ngroup; ++g)
+        if (k >= t->g_first[g] && k < t->g_first[g] + t->g_count[g]) return g;
+    return -1;
+}
