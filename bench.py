@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the P3T tree side on B300.
+
+One step = one leapfrog (kick-drift-kick) step of the soft part on a Plummer
+sphere of N = 2^20 equal-mass particles in N-body units (r_out = 0.0025,
+r_in = 0.1 r_out, theta = 0.4, eps = 4/N, h = r_out, dt = 1/256, groups of
+<= 64, leaves of <= 16):
+    kick(dt/2) -> drift(dt) -> build tree -> long-range force (walk + force
+    kernel, neighbour counts) -> neighbour lists -> kick(dt/2)
+all through the C ABI of libp3t.  ``value`` is particles per second of whole
+steps with the data resident in HBM; ``e2e`` adds the host<->device copies of
+the step's inputs and outputs from/to pinned host memory.  The working set of
+a step (particles, tree, lists: ~0.5 GB) is larger than L2, so no flush is
+done between steps.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (tree build and walk over all particles, forces
+of a random subset of groups, scaled by the subset fraction).
+
+Multi-GPU (torchrun): every rank runs its own independent cluster (replicas,
+weak scaling); ranks meet only at the timing barrier.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+N_DEFAULT = 1 << 20
+THETA = 0.4
+R_OUT = 0.0025
+GAMMA = 0.1
+DT = 1.0 / 256.0
+N_LEAF = 16
+N_GROUP = 64
+SEED = 2
+
+# FP32 flops per interaction (FMA = 2), fixed from the force kernel source
+FLOPS_PC = 49
+FLOPS_PP_FAR = 18
+FLOPS_PP_NEAR = 31
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(n):
+    return (f"plummer_n{n}_theta{THETA}_rout{R_OUT}_kdk_dt1/256"
+            f"_nleaf{N_LEAF}_ngroup{N_GROUP}")
+
+
+def config(n, world):
+    return {"workload": workload_name(n), "n": n, "theta": THETA,
+            "r_out": R_OUT, "gamma": GAMMA, "eps": 4.0 / n, "h": R_OUT,
+            "dt": DT, "n_leaf": N_LEAF, "n_group": N_GROUP,
+            "model": "Plummer sphere, N-body units, equal masses",
+            "parallelism": f"replicas x{world}",
+            "l2": "no flush: per-step working set ~0.5 GB > 126 MB L2"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def profile_traffic():
+    """Per-launch DRAM bytes of the force kernel from the committed ncu
+    summary (a line 'dram_bytes_per_launch: <float>'), else None."""
+    path = os.path.join(HERE, "profiles", "k_force_plummer_1M.txt")
+    try:
+        for line in open(path):
+            if line.startswith("dram_bytes_per_launch:"):
+                return float(line.split(":", 1)[1])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# --------------------------------------------------------------------------
+# CPU reference arm / baseline: the FP64 oracle on the host cores
+# --------------------------------------------------------------------------
+
+def oracle_sample(pos, mass, frac=1 / 16, seed=0):
+    """Times one step of the oracle on a bounded sample: tree build and walk
+    over all particles, forces of a random subset of groups holding about
+    `frac` of the particles; returns (seconds per full step, description)."""
+    import oracle
+    n = pos.shape[1]
+    p = np.ascontiguousarray(pos.T)
+    t0 = time.perf_counter()
+    tree = oracle.Tree(p, mass, n_leaf=N_LEAF, n_group=N_GROUP)
+    t1 = time.perf_counter()
+    tree.walk(THETA, R_OUT, R_OUT)
+    t2 = time.perf_counter()
+    g = tree.groups()
+    rng = np.random.default_rng(seed)
+    sel = rng.permutation(tree.ngroup)
+    cum = np.cumsum(g["count"][sel])
+    k = int(np.searchsorted(cum, frac * n)) + 1
+    sel = sel[:k]
+    t3 = time.perf_counter()
+    tree.force(eps=4.0 / n, r_cut=R_OUT, gamma=GAMMA, groups=sel)
+    t4 = time.perf_counter()
+    covered = int(g["count"][sel].sum())
+    t_step = (t1 - t0) + (t2 - t1) + (t4 - t3) * n / covered
+    desc = (f"oracle tree build + walk over all {n} particles, forces of "
+            f"{k} random groups ({covered} particles) scaled by {n / covered:.2f}; "
+            f"neighbour lists and kick/drift not included")
+    return t_step, desc
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_1506_04553_b300 import ics
+    n = args.n
+    pos, vel, mass = ics.plummer(n, SEED)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_sample(pos, mass, frac=1 / 64)
+    ts = []
+    desc = ""
+    for s in range(args.steps):
+        t, desc = oracle_sample(pos, mass, frac=1 / 64, seed=s)
+        ts.append(t)
+    t_step = float(np.mean(ts))
+    value = n / t_step
+    line = {"impl": "reference", "metric": METRIC, "value": value,
+            "unit": "particles/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": config(n, world),
+            "cpu_baseline": {"value": value, "unit": "particles/s",
+                             "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "particles/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+METRIC = ("long-range tree force particles/s & Gint/s at N=2^20 theta=0.4; "
+          "fwd+bwd vs fwd ratio")
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_1506_04553_b300 as P
+    from paper_1506_04553_b300 import ics
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n = args.n
+    pos_h, vel_h, mass_h = ics.plummer(n, SEED + rank)
+    params = P.Params(theta=THETA, r_out=R_OUT, gamma=GAMMA, eps=4.0 / n,
+                      h=R_OUT, G=1.0, n_leaf=N_LEAF, n_group=N_GROUP,
+                      flags=P.FLAG_NEIGHBOURS)
+    ctx = P.Context(params)
+    stream = torch.cuda.current_stream(dev)
+    pos = torch.tensor(pos_h, device=dev)
+    vel = torch.tensor(vel_h, device=dev)
+    mass = torch.tensor(mass_h, device=dev)
+    acc = torch.empty((3, n), dtype=torch.float32, device=dev)
+    off = torch.empty((n + 1,), dtype=torch.int64, device=dev)
+
+    # initial force and neighbour capacity
+    ctx.build_tree(pos, mass)
+    ctx.long_force(acc)
+    _, idx0 = ctx.neighbours()
+    cap = max(4 * int(idx0.numel()) + 1024, n)
+    idx = torch.empty((cap,), dtype=torch.int32, device=dev)
+
+    def step():
+        P.kick(vel, acc, 0.5 * DT)
+        P.drift(pos, vel, DT)
+        ctx.build_tree(pos, mass)
+        ctx.long_force(acc)
+        ctx.neighbours_into(off, idx, sync=False)
+        P.kick(vel, acc, 0.5 * DT)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    ctx.profile(reset=True)
+    ctx.profile_enable(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = P.launch_count()
+    stats = []
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+        stats.append(ctx.stats())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = P.launch_count() - l0
+    clocks = sampler.stop()
+    ctx.profile_enable(False)
+    prof = ctx.profile(reset=True)
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * n * args.steps / (ms * 1e-3)
+
+    # interactions and roofline of the force kernel
+    int_pc = sum(s["int_pc"] for s in stats)
+    int_pp = sum(s["int_pp"] for s in stats)
+    int_ppn = sum(s["int_pp_near"] for s in stats)
+    flops = FLOPS_PC * int_pc + FLOPS_PP_NEAR * int_ppn + FLOPS_PP_FAR * (int_pp - int_ppn)
+    force_s = prof["force_ms"] * 1e-3
+    achieved = flops / force_s / 1e12 if force_s > 0 else None
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = float(peaks.get("sm_max_mhz", 2032.0))
+    peak = sms * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    traffic = profile_traffic()
+    gint = world * (int_pc + int_pp) / (ms * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "particles/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "precision": "FP32 group-relative interactions with compensated sums; "
+                     "FP64 positions, moments, kick, drift; FP64 exact "
+                     "neighbour predicate",
+        "data": "synthetic", "config": config(n, world),
+        "gint_per_s": gint,
+        "interactions_per_particle": {"pc": int_pc / (n * args.steps),
+                                      "pp": int_pp / (n * args.steps)},
+        "phase_ms_per_step": {"build": prof["build_ms"] / args.steps,
+                              "walk": prof["walk_ms"] / args.steps,
+                              "force": prof["force_ms"] / args.steps,
+                              "neighbours": prof["ngb_ms"] / args.steps},
+        "force_particles_per_s": world * n * args.steps / force_s if force_s else None,
+        "fwd_bwd_ratio": None,
+        "roofline": {"kernel": "k_force", "bound": "alu",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": traffic,
+                     "peak_note": f"FP32 FMA: {sms} SMs x 128 lanes x 2 x "
+                                  f"{clk:.0f} MHz (max SM clock)"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    # end-to-end through the public API with host buffers
+    if not args.no_e2e:
+        pin = lambda a: torch.tensor(a).pin_memory()
+        hp, hv, hm = pin(pos.cpu().numpy()), pin(vel.cpu().numpy()), pin(mass_h)
+        hoff = torch.empty((n + 1,), dtype=torch.int64).pin_memory()
+        hidx = torch.empty((cap,), dtype=torch.int32).pin_memory()
+        nnz_last = [0]
+
+        def e2e_step():
+            pos.copy_(hp, non_blocking=True)
+            vel.copy_(hv, non_blocking=True)
+            mass.copy_(hm, non_blocking=True)
+            P.kick(vel, acc, 0.5 * DT)
+            P.drift(pos, vel, DT)
+            ctx.build_tree(pos, mass)
+            ctx.long_force(acc)
+            nnz = ctx.neighbours_into(off, idx, sync=True)
+            P.kick(vel, acc, 0.5 * DT)
+            hp.copy_(pos, non_blocking=True)
+            hv.copy_(vel, non_blocking=True)
+            hoff.copy_(off, non_blocking=True)
+            hidx[:nnz].copy_(idx[:nnz], non_blocking=True)
+            nnz_last[0] = nnz
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        ke = max(2, min(args.steps, 8))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / ke
+        if world > 1:
+            t = torch.tensor([te], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        line["e2e"] = {"value": world * n / te, "unit": "particles/s",
+                       "h2d_bytes_per_step": 7 * 8 * n,
+                       "d2h_bytes_per_step": 6 * 8 * n + 8 * (n + 1) + 4 * nnz_last[0],
+                       "ms_per_step": te * 1e3}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t_step, desc = oracle_sample(pos_h, mass_h, frac=1 / 16)
+        line["cpu_baseline"] = {"value": n / t_step, "unit": "particles/s",
+                                "cores": os.cpu_count() or 1, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

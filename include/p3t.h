@@ -1,0 +1,218 @@
+/*
+ * p3t.h -- C ABI of libp3t, the tree side of the P3T (particle-particle
+ * particle-tree) scheme of Iwasawa, Portegies Zwart & Makino,
+ * arXiv:1506.04553, on one NVIDIA B300 (sm_103a).
+ *
+ * The library evaluates the long-range ("soft") gravitational acceleration
+ *     a_soft,i = -sum_{j != i} G m_j K(s_ij) q_ij / s_ij^3          (Eq. 8)
+ * with q_ij = q_i - q_j and s_ij = sqrt(|q_ij|^2 + eps^2)            (Eq. 2-3)
+ * and the cut-off function K(x) of Eq. 12-15, by a Barnes-Hut octree to
+ * quadrupole order, and gives every particle its list of neighbours within a
+ * radius h, the two products the GPU tree library hands to the host-side
+ * Hermite part in Sect. 2.2.  It also provides the velocity kick and drift of
+ * the second-order splitting of Eq. 11 and of the step procedure of
+ * Sect. 2.2.
+ *
+ * Conventions for every entry point:
+ *   - Every function returns an int status (P3T_OK or a P3T_ERR_* code).
+ *   - Particle arrays are DEVICE pointers in the caller's particle order.
+ *     Three-vectors are structure-of-arrays: x[0..n), y[0..n), z[0..n)
+ *     contiguous (a (3, n) row-major array).
+ *   - The caller owns every pointer it passes; the context owns the tree,
+ *     the interaction lists and all other scratch.  Nothing the caller passes
+ *     is retained after a call returns (build_tree copies what it needs).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All device
+ *     work of a call is issued on that stream.
+ *   - A context belongs to one device (the current device at p3t_create) and
+ *     must not be used by two host threads at once.
+ */
+#ifndef P3T_H
+#define P3T_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define P3T_OK 0
+#define P3T_ERR_INVALID 1  /* bad parameter, n < 0, NULL pointer, NaN/Inf
+                              coordinate, non-positive or non-finite mass */
+#define P3T_ERR_CAPACITY 2 /* caller buffer too small; *needed says how big */
+#define P3T_ERR_CUDA 3     /* a CUDA runtime call failed */
+#define P3T_ERR_TIMEOUT 4  /* a bounded device-side wait expired */
+#define P3T_ERR_STATE 5    /* call out of order (e.g. force before build) */
+
+/* ---- flags ---- */
+/* p3t_long_force also counts neighbours within h (needed by p3t_neighbours). */
+#define P3T_FLAG_NEIGHBOURS 1
+
+typedef struct p3t_ctx p3t_ctx;
+
+/* Parameters.  Names follow the paper: r_out is r_cut of Eq. 12-15 and
+ * Table 1, gamma = r_in / r_cut (Eq. 15; 0.1 in every run of the paper),
+ * eps the Plummer softening of Eq. 2, theta the opening criterion of
+ * Table 1, h the neighbour radius of Sect. 2.2 (h = r_cut + dr_buff). */
+typedef struct p3t_params {
+    double theta;    /* opening parameter, >= 0 (0 = direct summation) */
+    double r_out;    /* outer cut-off radius r_cut, > 0 */
+    double gamma;    /* r_in / r_cut, in [0, 1) */
+    double eps;      /* Plummer softening, >= 0 */
+    double h;        /* neighbour radius, >= 0; 0 means h = r_out */
+    double G;        /* gravitational constant, > 0 */
+    int32_t n_leaf;  /* a cell with more than n_leaf particles is split
+                        (1..64; default 16) */
+    int32_t n_group; /* particles sharing one interaction list (1..64;
+                        default 64) */
+    int32_t flags;   /* P3T_FLAG_* */
+    int32_t reserved;
+} p3t_params;
+
+/* Fills *p with the defaults: theta 0.4, r_out 1/64, gamma 0.1, eps 0,
+ * h 0 (= r_out), G 1, n_leaf 16, n_group 64, flags P3T_FLAG_NEIGHBOURS. */
+int p3t_default_params(p3t_params *p);
+
+/* Creates a context on the current device.  *ctx receives the handle.
+ * Errors: P3T_ERR_INVALID (NULL or out-of-range parameter). */
+int p3t_create(p3t_ctx **ctx, const p3t_params *p);
+
+/* Releases the context and all device memory it owns.  NULL is a no-op. */
+int p3t_destroy(p3t_ctx *ctx);
+
+/* Replaces the parameters.  n_leaf / n_group changes take effect at the next
+ * p3t_build_tree; the others at the next p3t_long_force. */
+int p3t_set_params(p3t_ctx *ctx, const p3t_params *p);
+
+/* Builds the octree (Sect. 2.2: Barnes-Hut tree "up to the quadrupole
+ * moment") for n particles.
+ *   pos  : device, double[3][n] (SoA), the particle positions q_i
+ *   mass : device, double[n], m_i > 0
+ * Steps: root cube, 63-bit Morton keys (21 bits per axis), stable radix sort
+ * by (key, index), level-wise split of every cell holding more than n_leaf
+ * particles, FP64 monopole + traceless quadrupole moments per cell, groups
+ * of at most n_group particles.  The context keeps Morton-ordered copies, so
+ * pos and mass may change after the call returns.  n == 0 builds an empty
+ * tree.  Synchronises `stream` once at the end (to size later launches).
+ * Errors: P3T_ERR_INVALID (n < 0, NULL pointer with n > 0, non-finite
+ * coordinate, mass not finite and positive), P3T_ERR_CUDA. */
+int p3t_build_tree(p3t_ctx *ctx, int64_t n, const double *pos,
+                   const double *mass, void *stream);
+
+/* Long-range acceleration a_soft (Eq. 8) of every particle by the tree.
+ *   acc : device, float[3][n] (SoA), written in the caller's order
+ *   pot : device, double[n] or NULL; if given, the soft potential
+ *         phi_i = -sum_j G m_j W(s_ij / r_cut) / s_ij (Eq. 6, Eq. 16)
+ * Cells are accepted only when every pair they stand for is farther apart
+ * than max(h, r_cut), so cell terms carry K = 1; particle pairs carry K.
+ * With P3T_FLAG_NEIGHBOURS the per-particle neighbour counts are produced
+ * for p3t_neighbours.  Synchronises `stream` once (to size the lists).
+ * Errors: P3T_ERR_STATE (no tree), P3T_ERR_INVALID (acc NULL with n > 0),
+ * P3T_ERR_CUDA. */
+int p3t_long_force(p3t_ctx *ctx, float *acc, double *pot, void *stream);
+
+/* Neighbour lists (Sect. 2.2) of the last p3t_long_force call made with
+ * P3T_FLAG_NEIGHBOURS, in CSR form: the neighbours of particle i are
+ * idx[offsets[i] .. offsets[i+1]), ascending original indices.  j is a
+ * neighbour of i iff j != i and ((dx*dx + dy*dy) + dz*dz) < h*h evaluated in
+ * FP64 with dx = x_i - x_j (unsoftened distance, strict inequality).
+ *   offsets : device, int64[n + 1]
+ *   idx     : device, int32[cap]
+ *   cap     : capacity of idx
+ *   needed  : host int64*, receives the total count (nnz); may be NULL, in
+ *             which case no host synchronisation happens and a too-small
+ *             cap is reported by the next synchronising call.
+ * Errors: P3T_ERR_CAPACITY (nnz > cap; offsets valid, idx undefined),
+ * P3T_ERR_STATE (no force evaluation with P3T_FLAG_NEIGHBOURS), P3T_ERR_CUDA. */
+int p3t_neighbours(p3t_ctx *ctx, int64_t *offsets, int32_t *idx, int64_t cap,
+                   int64_t *needed, void *stream);
+
+/* Velocity kick by the soft force (Eq. 11; Sect. 2.2 steps 4 and 8):
+ * v <- v + dt * a, elementwise in FP64 (no fused multiply-add).
+ *   vel : device, double[3][n];  acc : device, float[3][n].
+ * Errors: P3T_ERR_INVALID (n < 0 or NULL with n > 0), P3T_ERR_CUDA. */
+int p3t_kick(int64_t n, double *vel, const float *acc, double dt, void *stream);
+
+/* Drift (Sect. 2.2 step 5): x <- x + dt * v, elementwise in FP64.
+ *   pos : device, double[3][n];  vel : device, double[3][n]. */
+int p3t_drift(int64_t n, double *pos, const double *vel, double dt,
+              void *stream);
+
+/* Energies in FP64: out[0] = E_kin = 1/2 sum m_i |v_i|^2 and, if pot is not
+ * NULL, out[1] = 1/2 sum m_i phi_i (else 0).  out is a DEVICE double[2].
+ * Uses scratch owned by ctx. */
+int p3t_energy(p3t_ctx *ctx, int64_t n, const double *mass, const double *vel,
+               const double *pot, double *out, void *stream);
+
+/* Counters of the last build / force evaluation (host struct). */
+typedef struct p3t_stats {
+    int64_t n;
+    int64_t n_cells;
+    int64_t n_groups;
+    int64_t n_levels;     /* deepest level + 1 */
+    int64_t list_pc;      /* cell entries over all group lists */
+    int64_t list_pp_near; /* particle entries with K < 1 possible */
+    int64_t list_pp_far;  /* particle entries with K = 1 */
+    int64_t int_pc;       /* particle-cell interactions (sum over groups of
+                             group size x cell list length) */
+    int64_t int_pp;       /* particle-particle interactions, self included */
+    int64_t int_pp_near;  /* the part of int_pp from near lists */
+    int64_t nnz;          /* neighbour pairs (after p3t_neighbours) */
+} p3t_stats;
+int p3t_get_stats(p3t_ctx *ctx, p3t_stats *s);
+
+/* ---- profiling ----
+ * With profiling on, CUDA events are recorded on the caller's stream around
+ * each phase; p3t_get_profile synchronises and returns the accumulated
+ * device time of every phase since the last reset. */
+typedef struct p3t_profile {
+    double build_ms;   /* p3t_build_tree, all kernels */
+    double walk_ms;    /* tree walk (count pass, scan, fill pass) */
+    double force_ms;   /* the force kernel alone */
+    double ngb_ms;     /* p3t_neighbours: scan, fill, row sort */
+    int64_t builds, walks, forces, ngbs; /* number of timed calls */
+} p3t_profile;
+int p3t_profile_enable(p3t_ctx *ctx, int on);
+int p3t_get_profile(p3t_ctx *ctx, p3t_profile *out, int reset);
+
+/* Number of kernels this library has launched since it was loaded (all
+ * contexts, all entry points). */
+int64_t p3t_launch_count(void);
+
+/* ---- inspection (tests and tools; each call synchronises and copies to
+ * HOST buffers sized from p3t_get_stats) ---- */
+
+/* Sorted Morton keys and the original index of each sorted particle. */
+int p3t_get_order(p3t_ctx *ctx, uint64_t *key, int32_t *order);
+
+/* Root cube: lo[3] and side. */
+int p3t_get_root(p3t_ctx *ctx, double *lo, double *size);
+
+/* Cells (any order; children of a cell are contiguous and in Morton order):
+ * level, first sorted particle, count, first child (-1 for a leaf), number of
+ * children, FP64 mass, centre of mass [3], quadrupole [6] (xx yy zz xy xz yz,
+ * traceless, about the centre of mass), FP32 outward-rounded member box
+ * fmin[3], fmax[3].  Any pointer may be NULL. */
+int p3t_get_cells(p3t_ctx *ctx, int32_t *level, int32_t *first,
+                  int32_t *count, int32_t *child, int32_t *nchild, double *M,
+                  double *com, double *Q, float *fmin, float *fmax);
+
+/* Groups: first sorted particle and count of each group (any order), and
+ * the FP32 outward-rounded member box. */
+int p3t_get_groups(p3t_ctx *ctx, int32_t *first, int32_t *count, float *fmin,
+                   float *fmax);
+
+/* Interaction lists of the last p3t_long_force, CSR per group (group order
+ * as p3t_get_groups): cells (cell ids as p3t_get_cells), near particles and
+ * far particles (sorted particle ids).  Offsets have n_groups + 1 entries. */
+int p3t_get_lists(p3t_ctx *ctx, int64_t *pc_off, int32_t *pc,
+                  int64_t *ppn_off, int32_t *ppn, int64_t *ppf_off,
+                  int32_t *ppf);
+
+/* Human-readable name of a status code. */
+const char *p3t_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* P3T_H */

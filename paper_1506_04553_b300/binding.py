@@ -1,0 +1,352 @@
+"""ctypes binding of libp3t (the tree side of the P3T scheme on one B300).
+
+Thin Python binding over ``libp3t.so`` (the C ABI declared in
+``include/p3t.h``).  It only marshals arguments: device pointers of torch
+tensors, the current CUDA stream, and status codes turned into exceptions.
+Every step of the computation runs in the library's CUDA kernels; there is no
+CPU fallback, and importing without the built library raises.
+
+Conventions: particle vectors are ``(3, n)`` float64 CUDA tensors
+(structure of arrays, the caller's particle order), masses ``(n,)`` float64,
+accelerations ``(3, n)`` float32.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, fields
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Params", "Context", "P3TError", "kick", "drift", "library_path",
+           "launch_count", "FLAG_NEIGHBOURS"]
+
+FLAG_NEIGHBOURS = 1
+
+_STATUS = {0: "ok", 1: "invalid argument or input", 2: "capacity exceeded",
+           3: "CUDA error", 4: "device wait timed out", 5: "call out of order"}
+
+
+class P3TError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {_STATUS.get(code, 'unknown')} (status {code})")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load_lib():
+    path = _build.LIB
+    if not os.path.exists(path):
+        if os.environ.get("P3T_AUTOBUILD", "1") == "1":
+            _build.build()
+        else:
+            raise ImportError(f"libp3t.so not built at {path}")
+    return C.CDLL(path)
+
+
+class _CParams(C.Structure):
+    _fields_ = [("theta", C.c_double), ("r_out", C.c_double),
+                ("gamma", C.c_double), ("eps", C.c_double), ("h", C.c_double),
+                ("G", C.c_double), ("n_leaf", C.c_int32),
+                ("n_group", C.c_int32), ("flags", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class _CStats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in (
+        "n", "n_cells", "n_groups", "n_levels", "list_pc", "list_pp_near",
+        "list_pp_far", "int_pc", "int_pp", "int_pp_near", "nnz")]
+
+
+class _CProfile(C.Structure):
+    _fields_ = [("build_ms", C.c_double), ("walk_ms", C.c_double),
+                ("force_ms", C.c_double), ("ngb_ms", C.c_double),
+                ("builds", C.c_int64), ("walks", C.c_int64),
+                ("forces", C.c_int64), ("ngbs", C.c_int64)]
+
+
+_lib = _load_lib()
+_vp = C.c_void_p
+_i64 = C.c_int64
+_sigs = {
+    "p3t_default_params": [_vp],
+    "p3t_create": [_vp, _vp],
+    "p3t_destroy": [_vp],
+    "p3t_set_params": [_vp, _vp],
+    "p3t_build_tree": [_vp, _i64, _vp, _vp, _vp],
+    "p3t_long_force": [_vp, _vp, _vp, _vp],
+    "p3t_neighbours": [_vp, _vp, _vp, _i64, _vp, _vp],
+    "p3t_kick": [_i64, _vp, _vp, C.c_double, _vp],
+    "p3t_drift": [_i64, _vp, _vp, C.c_double, _vp],
+    "p3t_energy": [_vp, _i64, _vp, _vp, _vp, _vp, _vp],
+    "p3t_get_stats": [_vp, _vp],
+    "p3t_get_order": [_vp, _vp, _vp],
+    "p3t_get_root": [_vp, _vp, _vp],
+    "p3t_get_cells": [_vp] + [_vp] * 10,
+    "p3t_get_groups": [_vp, _vp, _vp, _vp, _vp],
+    "p3t_get_lists": [_vp] + [_vp] * 6,
+    "p3t_profile_enable": [_vp, C.c_int],
+    "p3t_get_profile": [_vp, _vp, C.c_int],
+}
+for _name, _args in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.p3t_status_string.argtypes = [C.c_int]
+_lib.p3t_status_string.restype = C.c_char_p
+_lib.p3t_launch_count.argtypes = []
+_lib.p3t_launch_count.restype = C.c_int64
+
+
+def launch_count() -> int:
+    """Kernels launched by libp3t since it was loaded."""
+    return int(_lib.p3t_launch_count())
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise P3TError(code, where)
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, dtype, shape, name):
+    """Device pointer of a contiguous CUDA tensor with the given dtype/shape."""
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: tensor must be contiguous")
+    return C.c_void_p(t.data_ptr()) if t.numel() else None
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+@dataclass
+class Params:
+    """Parameters of one context (names after the paper: r_out is r_cut of
+    Eq. 12-15, gamma = r_in/r_cut, eps the Plummer softening of Eq. 2, theta
+    the opening criterion, h the neighbour radius of Sect. 2.2)."""
+    theta: float = 0.4
+    r_out: float = 1.0 / 64.0
+    gamma: float = 0.1
+    eps: float = 0.0
+    h: float = 0.0
+    G: float = 1.0
+    n_leaf: int = 16
+    n_group: int = 64
+    flags: int = FLAG_NEIGHBOURS
+
+    def _c(self) -> _CParams:
+        p = _CParams()
+        for f in fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+
+class Context:
+    """One tree-side context on the current CUDA device (libp3t p3t_ctx)."""
+
+    def __init__(self, params: Params | None = None):
+        self.params = params or Params()
+        self._h = C.c_void_p()
+        cp = self.params._c()
+        _check(_lib.p3t_create(C.byref(self._h), C.byref(cp)), "p3t_create")
+        self.n = 0
+
+    def close(self):
+        if self._h:
+            _lib.p3t_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params: Params):
+        cp = params._c()
+        _check(_lib.p3t_set_params(self._h, C.byref(cp)), "p3t_set_params")
+        self.params = params
+
+    # ---- hot path ----
+    def build_tree(self, pos, mass, stream=None):
+        import torch
+        n = int(mass.shape[0])
+        p = _dptr(pos, torch.float64, (3, n), "pos")
+        m = _dptr(mass, torch.float64, (n,), "mass")
+        _check(_lib.p3t_build_tree(self._h, n, p, m, _stream(stream)),
+               "p3t_build_tree")
+        self.n = n
+
+    def long_force(self, acc=None, pot=None, want_potential=False, stream=None):
+        """Soft acceleration (3, n) float32; with ``want_potential`` also the
+        soft potential (n,) float64.  Returns acc or (acc, pot)."""
+        import torch
+        n = self.n
+        if acc is None:
+            acc = torch.empty((3, n), dtype=torch.float32, device="cuda")
+        if want_potential and pot is None:
+            pot = torch.empty((n,), dtype=torch.float64, device="cuda")
+        a = _dptr(acc, torch.float32, (3, n), "acc")
+        q = _dptr(pot, torch.float64, (n,), "pot") if pot is not None else None
+        _check(_lib.p3t_long_force(self._h, a, q, _stream(stream)),
+               "p3t_long_force")
+        return (acc, pot) if pot is not None else acc
+
+    def neighbours(self, stream=None):
+        """CSR neighbour lists (offsets int64[n+1], idx int32[nnz]) on the
+        device, rows in the caller's order, ascending indices."""
+        import torch
+        n = self.n
+        off = torch.empty((n + 1,), dtype=torch.int64, device="cuda")
+        need = C.c_int64(0)
+        code = _lib.p3t_neighbours(self._h, C.c_void_p(off.data_ptr()), None, 0,
+                                   C.byref(need), _stream(stream))
+        if code not in (0, 2):
+            _check(code, "p3t_neighbours")
+        nnz = int(need.value)
+        idx = torch.empty((max(nnz, 1),), dtype=torch.int32, device="cuda")
+        _check(_lib.p3t_neighbours(self._h, C.c_void_p(off.data_ptr()),
+                                   C.c_void_p(idx.data_ptr()), idx.numel(),
+                                   C.byref(need), _stream(stream)),
+               "p3t_neighbours")
+        return off, idx[:nnz]
+
+    def neighbours_into(self, offsets, idx, stream=None, sync=True):
+        """Fill caller buffers; returns nnz (or None when sync=False)."""
+        import torch
+        n = self.n
+        o = _dptr(offsets, torch.int64, (n + 1,), "offsets")
+        i = C.c_void_p(idx.data_ptr()) if idx.numel() else None
+        need = C.c_int64(0)
+        _check(_lib.p3t_neighbours(self._h, o, i, idx.numel(),
+                                   C.byref(need) if sync else None,
+                                   _stream(stream)), "p3t_neighbours")
+        return int(need.value) if sync else None
+
+    def energy(self, mass, vel, pot=None, out=None, stream=None):
+        import torch
+        n = int(mass.shape[0])
+        if out is None:
+            out = torch.zeros((2,), dtype=torch.float64, device="cuda")
+        _check(_lib.p3t_energy(
+            self._h, n, _dptr(mass, torch.float64, (n,), "mass"),
+            _dptr(vel, torch.float64, (3, n), "vel"),
+            _dptr(pot, torch.float64, (n,), "pot") if pot is not None else None,
+            _dptr(out, torch.float64, (2,), "out"), _stream(stream)),
+            "p3t_energy")
+        return out
+
+    # ---- profiling ----
+    def profile_enable(self, on: bool = True):
+        _check(_lib.p3t_profile_enable(self._h, 1 if on else 0),
+               "p3t_profile_enable")
+
+    def profile(self, reset: bool = True) -> dict:
+        p = _CProfile()
+        _check(_lib.p3t_get_profile(self._h, C.byref(p), 1 if reset else 0),
+               "p3t_get_profile")
+        return {f: (float(getattr(p, f)) if t is C.c_double else int(getattr(p, f)))
+                for f, t in _CProfile._fields_}
+
+    # ---- inspection ----
+    def stats(self) -> dict:
+        s = _CStats()
+        _check(_lib.p3t_get_stats(self._h, C.byref(s)), "p3t_get_stats")
+        return {f: int(getattr(s, f)) for f, _ in _CStats._fields_}
+
+    def order(self):
+        n = self.n
+        key = np.zeros(n, np.uint64)
+        order = np.zeros(n, np.int32)
+        _check(_lib.p3t_get_order(self._h, _np_ptr(key), _np_ptr(order)),
+               "p3t_get_order")
+        return key, order
+
+    def root(self):
+        lo = np.zeros(3)
+        size = np.zeros(1)
+        _check(_lib.p3t_get_root(self._h, _np_ptr(lo), _np_ptr(size)),
+               "p3t_get_root")
+        return lo, float(size[0])
+
+    def cells(self) -> dict:
+        c = self.stats()["n_cells"]
+        out = dict(level=np.zeros(c, np.int32), first=np.zeros(c, np.int32),
+                   count=np.zeros(c, np.int32), child=np.zeros(c, np.int32),
+                   nchild=np.zeros(c, np.int32), M=np.zeros(c),
+                   com=np.zeros((c, 3)), Q=np.zeros((c, 6)),
+                   fmin=np.zeros((c, 3), np.float32),
+                   fmax=np.zeros((c, 3), np.float32))
+        if c:
+            _check(_lib.p3t_get_cells(self._h, *[_np_ptr(out[k]) for k in (
+                "level", "first", "count", "child", "nchild", "M", "com", "Q",
+                "fmin", "fmax")]), "p3t_get_cells")
+        return out
+
+    def groups(self) -> dict:
+        g = self.stats()["n_groups"]
+        out = dict(first=np.zeros(g, np.int32), count=np.zeros(g, np.int32),
+                   fmin=np.zeros((g, 3), np.float32),
+                   fmax=np.zeros((g, 3), np.float32))
+        if g:
+            _check(_lib.p3t_get_groups(self._h, *[_np_ptr(out[k]) for k in (
+                "first", "count", "fmin", "fmax")]), "p3t_get_groups")
+        return out
+
+    def lists(self) -> dict:
+        st = self.stats()
+        g = st["n_groups"]
+        out = dict(pc_off=np.zeros(g + 1, np.int64),
+                   pc=np.zeros(max(st["list_pc"], 1), np.int32),
+                   ppn_off=np.zeros(g + 1, np.int64),
+                   ppn=np.zeros(max(st["list_pp_near"], 1), np.int32),
+                   ppf_off=np.zeros(g + 1, np.int64),
+                   ppf=np.zeros(max(st["list_pp_far"], 1), np.int32))
+        if g:
+            _check(_lib.p3t_get_lists(self._h, *[_np_ptr(out[k]) for k in (
+                "pc_off", "pc", "ppn_off", "ppn", "ppf_off", "ppf")]),
+                "p3t_get_lists")
+        out["pc"] = out["pc"][: st["list_pc"]]
+        out["ppn"] = out["ppn"][: st["list_pp_near"]]
+        out["ppf"] = out["ppf"][: st["list_pp_far"]]
+        return out
+
+
+def kick(vel, acc, dt, stream=None):
+    """v <- v + dt * a in place (FP64; Eq. 11 / Sect. 2.2)."""
+    import torch
+    n = int(vel.shape[1])
+    _check(_lib.p3t_kick(n, _dptr(vel, torch.float64, (3, n), "vel"),
+                         _dptr(acc, torch.float32, (3, n), "acc"), float(dt),
+                         _stream(stream)), "p3t_kick")
+    return vel
+
+
+def drift(pos, vel, dt, stream=None):
+    """x <- x + dt * v in place (FP64; Sect. 2.2 step 5)."""
+    import torch
+    n = int(pos.shape[1])
+    _check(_lib.p3t_drift(n, _dptr(pos, torch.float64, (3, n), "pos"),
+                          _dptr(vel, torch.float64, (3, n), "vel"), float(dt),
+                          _stream(stream)), "p3t_drift")
+    return pos

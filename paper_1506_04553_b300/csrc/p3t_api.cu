@@ -1,0 +1,558 @@
+// C ABI of libp3t: context, memory management and the entry points declared
+// in include/p3t.h.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+
+#include "p3t_internal.cuh"
+
+static std::atomic<long long> g_launches{0};
+
+void p3t_count_launches(long long k) { g_launches.fetch_add(k); }
+
+int p3t_prof_open(p3t_ctx *c, int phase, cudaStream_t s)
+{
+    if (!c->prof_on) return -1;
+    P3TEvents &e = c->prof;
+    if (e.used == e.cap) {
+        int cap = e.cap ? 2 * e.cap : 64;
+        cudaEvent_t *ev = (cudaEvent_t *)realloc(e.ev, 2 * cap * sizeof(cudaEvent_t));
+        int *ph = (int *)realloc(e.phase, cap * sizeof(int));
+        if (!ev || !ph) return -1;
+        e.ev = ev;
+        e.phase = ph;
+        for (int k = 2 * e.cap; k < 2 * cap; ++k)
+            if (cudaEventCreate(&e.ev[k]) != cudaSuccess) return -1;
+        e.cap = cap;
+    }
+    int slot = e.used++;
+    e.phase[slot] = phase;
+    cudaEventRecord(e.ev[2 * slot], s);
+    return slot;
+}
+
+void p3t_prof_close(p3t_ctx *c, int slot, cudaStream_t s)
+{
+    if (slot < 0) return;
+    cudaEventRecord(c->prof.ev[2 * slot + 1], s);
+}
+
+// Resolves recorded event pairs into the per-phase totals.
+static int prof_resolve(p3t_ctx *c)
+{
+    P3TEvents &e = c->prof;
+    for (int k = 0; k < e.used; ++k) {
+        if (cudaEventSynchronize(e.ev[2 * k + 1]) != cudaSuccess) return P3T_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.ev[2 * k], e.ev[2 * k + 1]) != cudaSuccess)
+            return P3T_ERR_CUDA;
+        c->prof_ms[e.phase[k]] += ms;
+        c->prof_calls[e.phase[k]] += 1;
+    }
+    e.used = 0;
+    return P3T_OK;
+}
+
+namespace {
+
+template <class T>
+int grow(T *&ptr, int64_t &cap_slot, int64_t want, size_t per)
+{
+    (void)cap_slot;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    if (want <= 0) want = 1;
+    P3T_CUDA_TRY(cudaMalloc((void **)&ptr, (size_t)want * per));
+    return P3T_OK;
+}
+
+#define P3T_TRY(expr)                \
+    do {                             \
+        int r__ = (expr);            \
+        if (r__ != P3T_OK) return r__; \
+    } while (0)
+
+int check_params(const p3t_params *p)
+{
+    if (!p) return P3T_ERR_INVALID;
+    if (!(p->theta >= 0.0) || !isfinite(p->theta)) return P3T_ERR_INVALID;
+    if (!(p->r_out > 0.0) || !isfinite(p->r_out)) return P3T_ERR_INVALID;
+    if (!(p->gamma >= 0.0 && p->gamma < 1.0)) return P3T_ERR_INVALID;
+    if (!(p->eps >= 0.0) || !isfinite(p->eps)) return P3T_ERR_INVALID;
+    if (!(p->h >= 0.0) || !isfinite(p->h)) return P3T_ERR_INVALID;
+    if (!(p->G > 0.0) || !isfinite(p->G)) return P3T_ERR_INVALID;
+    if (p->n_leaf < 1 || p->n_leaf > 64) return P3T_ERR_INVALID;
+    if (p->n_group < 1 || p->n_group > 64) return P3T_ERR_INVALID;
+    return P3T_OK;
+}
+
+int ensure_particles(p3t_ctx *c, int64_t n)
+{
+    if (n <= c->cap_n) return P3T_OK;
+    int64_t cap = n + n / 8 + 1024;
+    int64_t d = 0;
+    P3T_TRY(grow(c->key_a, d, cap, sizeof(u64)));
+    P3T_TRY(grow(c->key_b, d, cap, sizeof(u64)));
+    P3T_TRY(grow(c->idx_a, d, cap, sizeof(int)));
+    P3T_TRY(grow(c->idx_b, d, cap, sizeof(int)));
+    P3T_TRY(grow(c->order, d, cap, sizeof(int)));
+    P3T_TRY(grow(c->xs, d, 3 * cap, sizeof(double)));
+    P3T_TRY(grow(c->ms, d, cap, sizeof(double)));
+    P3T_TRY(grow(c->phi, d, cap, sizeof(float4)));
+    P3T_TRY(grow(c->plo, d, cap, sizeof(float4)));
+    P3T_TRY(grow(c->ngb_cnt, d, cap, sizeof(int)));
+    c->cap_tiles = p3t_sort_tiles(cap);
+    P3T_TRY(grow(c->rs_counts, d, 256 * c->cap_tiles, sizeof(int)));
+    c->cap_scan = p3t_scan_blocks(cap) + 2;
+    P3T_TRY(grow(c->scan_part, d, c->cap_scan, sizeof(long long)));
+    // groups: at most one per particle
+    c->cap_groups = cap;
+    P3T_TRY(grow(c->grange, d, cap, sizeof(int2)));
+    P3T_TRY(grow(c->gmin, d, cap, sizeof(float4)));
+    P3T_TRY(grow(c->gmax, d, cap, sizeof(float4)));
+    P3T_TRY(grow(c->gctr, d, cap, sizeof(float4)));
+    P3T_TRY(grow(c->lcnt, d, 3 * cap, sizeof(long long)));
+    P3T_TRY(grow(c->loff, d, 3 * (cap + 1), sizeof(long long)));
+    c->cap_n = cap;
+    return P3T_OK;
+}
+
+int ensure_cells(p3t_ctx *c, int64_t want)
+{
+    if (want <= c->cap_cells) return P3T_OK;
+    int64_t cap = want;
+    int64_t d = 0;
+    P3T_TRY(grow(c->node, d, cap, sizeof(int4)));
+    P3T_TRY(grow(c->parent, d, cap, sizeof(int)));
+    P3T_TRY(grow(c->cM, d, cap, sizeof(double)));
+    P3T_TRY(grow(c->ccom, d, 3 * cap, sizeof(double)));
+    P3T_TRY(grow(c->cQ, d, 6 * cap, sizeof(double)));
+    P3T_TRY(grow(c->cbmin, d, 3 * cap, sizeof(double)));
+    P3T_TRY(grow(c->cbmax, d, 3 * cap, sizeof(double)));
+    P3T_TRY(grow(c->wmin, d, cap, sizeof(float4)));
+    P3T_TRY(grow(c->wmax, d, cap, sizeof(float4)));
+    P3T_TRY(grow(c->cf0, d, cap, sizeof(float4)));
+    P3T_TRY(grow(c->cf1, d, cap, sizeof(float4)));
+    P3T_TRY(grow(c->cf2, d, cap, sizeof(float4)));
+    c->cap_cells = cap;
+    return P3T_OK;
+}
+
+int ensure_list(p3t_ctx *c, int L, int64_t want)
+{
+    if (want <= c->cap_list[L]) return P3T_OK;
+    int64_t cap = want + want / 4 + 1024;
+    int64_t d = 0;
+    P3T_TRY(grow(c->list[L], d, cap, sizeof(int)));
+    c->cap_list[L] = cap;
+    return P3T_OK;
+}
+
+int sync_state(p3t_ctx *c, cudaStream_t s)
+{
+    P3T_CUDA_TRY(cudaMemcpyAsync(c->hst, c->st, sizeof(P3TDevState),
+                                 cudaMemcpyDeviceToHost, s));
+    P3T_CUDA_TRY(cudaStreamSynchronize(s));
+    return P3T_OK;
+}
+
+int clear_error(p3t_ctx *c, cudaStream_t s)
+{
+    P3T_CUDA_TRY(cudaMemsetAsync(&c->st->error, 0, sizeof(int), s));
+    return P3T_OK;
+}
+
+void free_all(p3t_ctx *c)
+{
+    void *ptrs[] = {c->st, c->key_a, c->key_b, c->idx_a, c->idx_b, c->order,
+                    c->xs, c->ms, c->phi, c->plo, c->ngb_cnt, c->rs_counts,
+                    c->rs_totals, c->bbox_part, c->node, c->parent, c->cM,
+                    c->ccom, c->cQ, c->cbmin, c->cbmax, c->wmin, c->wmax,
+                    c->cf0, c->cf1, c->cf2, c->grange, c->gmin, c->gmax,
+                    c->gctr, c->lcnt, c->loff, c->list[0], c->list[1],
+                    c->list[2], c->scan_part, c->red_part};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->hst) cudaFreeHost(c->hst);
+    for (int k = 0; k < 2 * c->prof.cap; ++k) cudaEventDestroy(c->prof.ev[k]);
+    free(c->prof.ev);
+    free(c->prof.phase);
+}
+
+}  // namespace
+
+extern "C" {
+
+int p3t_default_params(p3t_params *p)
+{
+    if (!p) return P3T_ERR_INVALID;
+    memset(p, 0, sizeof(*p));
+    p->theta = 0.4;
+    p->r_out = 1.0 / 64.0;
+    p->gamma = 0.1;
+    p->eps = 0.0;
+    p->h = 0.0;
+    p->G = 1.0;
+    p->n_leaf = 16;
+    p->n_group = 64;
+    p->flags = P3T_FLAG_NEIGHBOURS;
+    return P3T_OK;
+}
+
+int p3t_create(p3t_ctx **out, const p3t_params *p)
+{
+    if (!out) return P3T_ERR_INVALID;
+    *out = nullptr;
+    P3T_TRY(check_params(p));
+    p3t_ctx *c = new (std::nothrow) p3t_ctx;
+    if (!c) return P3T_ERR_CUDA;
+    memset(c, 0, sizeof(*c));
+    c->p = *p;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return P3T_ERR_CUDA;
+    }
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->sms <= 0) c->sms = 148;
+    int64_t d = 0;
+    int rc = P3T_OK;
+    if ((rc = grow(c->st, d, 1, sizeof(P3TDevState))) != P3T_OK ||
+        cudaMallocHost((void **)&c->hst, sizeof(P3TDevState)) != cudaSuccess ||
+        (rc = grow(c->rs_totals, d, 256, sizeof(int))) != P3T_OK ||
+        (rc = grow(c->bbox_part, d, 6 * c->sms * 4, sizeof(double))) != P3T_OK ||
+        (rc = grow(c->red_part, d, 2 * c->sms * 4, sizeof(double))) != P3T_OK) {
+        free_all(c);
+        delete c;
+        return rc ? rc : P3T_ERR_CUDA;
+    }
+    if (cudaMemset(c->st, 0, sizeof(P3TDevState)) != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return P3T_ERR_CUDA;
+    }
+    memset(c->hst, 0, sizeof(P3TDevState));
+    *out = c;
+    return P3T_OK;
+}
+
+int p3t_destroy(p3t_ctx *c)
+{
+    if (!c) return P3T_OK;
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+    return P3T_OK;
+}
+
+int p3t_set_params(p3t_ctx *c, const p3t_params *p)
+{
+    if (!c) return P3T_ERR_INVALID;
+    P3T_TRY(check_params(p));
+    c->p = *p;
+    return P3T_OK;
+}
+
+int p3t_build_tree(p3t_ctx *c, int64_t n, const double *pos,
+                   const double *mass, void *stream)
+{
+    if (!c || n < 0 || n > 0x7fffff00LL) return P3T_ERR_INVALID;
+    if (n > 0 && (!pos || !mass)) return P3T_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    c->built = 0;
+    c->forced_ngb = 0;
+    c->n = n;
+    if (n == 0) {
+        memset(c->hst, 0, sizeof(P3TDevState));
+        P3T_CUDA_TRY(cudaMemcpyAsync(c->st, c->hst, sizeof(P3TDevState),
+                                     cudaMemcpyHostToDevice, s));
+        c->built = 1;
+        return P3T_OK;
+    }
+    P3T_TRY(ensure_particles(c, n));
+    if (c->cap_cells < n / 2 + 64) P3T_TRY(ensure_cells(c, n / 2 + 64));
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        P3T_TRY(clear_error(c, s));
+        int slot = p3t_prof_open(c, P3T_PH_BUILD, s);
+        int rc = p3t_build_levels(c, (int)n, s, pos, mass);
+        p3t_prof_close(c, slot, s);
+        P3T_TRY(rc);
+        P3T_TRY(sync_state(c, s));
+        if (c->hst->error == 0) {
+            c->built = 1;
+            return P3T_OK;
+        }
+        if (c->hst->error != P3T_ERR_CAPACITY) return c->hst->error;
+        int64_t want = 2 * c->cap_cells;
+        if (c->hst->need_cells > want) want = c->hst->need_cells;
+        P3T_TRY(ensure_cells(c, want));
+    }
+    return P3T_ERR_CAPACITY;
+}
+
+int p3t_long_force(p3t_ctx *c, float *acc, double *pot, void *stream)
+{
+    if (!c) return P3T_ERR_INVALID;
+    if (!c->built) return P3T_ERR_STATE;
+    if (c->n == 0) {
+        c->forced_ngb = (c->p.flags & P3T_FLAG_NEIGHBOURS) != 0;
+        return P3T_OK;
+    }
+    if (!acc) return P3T_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    P3T_TRY(clear_error(c, s));
+    int slot = p3t_prof_open(c, P3T_PH_WALK, s);
+    P3T_TRY(p3t_run_walk(c, 0, s));
+    P3T_TRY(p3t_scan_lists(c, s));
+    int rc = sync_state(c, s);
+    if (rc == P3T_OK && c->hst->error) rc = c->hst->error;
+    if (rc != P3T_OK) {
+        p3t_prof_close(c, slot, s);
+        return rc;
+    }
+    for (int L = 0; L < 3; ++L) P3T_TRY(ensure_list(c, L, c->hst->tot[L]));
+    P3T_TRY(p3t_run_walk(c, 1, s));
+    p3t_prof_close(c, slot, s);
+    slot = p3t_prof_open(c, P3T_PH_FORCE, s);
+    P3T_TRY(p3t_run_force(c, acc, pot, s));
+    p3t_prof_close(c, slot, s);
+    c->forced_ngb = (c->p.flags & P3T_FLAG_NEIGHBOURS) != 0;
+    return P3T_OK;
+}
+
+int p3t_neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, int64_t cap,
+                   int64_t *needed, void *stream)
+{
+    if (!c || !offsets || cap < 0 || (cap > 0 && !idx)) return P3T_ERR_INVALID;
+    if (!c->built || !c->forced_ngb) return P3T_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = (int)c->n;
+    int slot = p3t_prof_open(c, P3T_PH_NGB, s);
+    P3T_TRY(p3t_scan_ll(c, c->ngb_cnt, (long long *)offsets, n, s));
+    if (needed) {
+        long long nnz = 0;
+        P3T_CUDA_TRY(cudaMemcpyAsync(&nnz, offsets + n, sizeof(long long),
+                                     cudaMemcpyDeviceToHost, s));
+        P3T_CUDA_TRY(cudaStreamSynchronize(s));
+        *needed = nnz;
+        c->hst->nnz = nnz;
+        if (nnz > cap) {
+            p3t_prof_close(c, slot, s);
+            return P3T_ERR_CAPACITY;
+        }
+    }
+    if (n == 0) {
+        p3t_prof_close(c, slot, s);
+        return P3T_OK;
+    }
+    P3T_TRY(clear_error(c, s));
+    P3T_TRY(p3t_run_ngb_fill(c, (const long long *)offsets, idx, cap, s));
+    p3t_prof_close(c, slot, s);
+    if (needed) {
+        P3T_TRY(sync_state(c, s));
+        if (c->hst->error) return c->hst->error;
+    }
+    return P3T_OK;
+}
+
+int p3t_energy(p3t_ctx *c, int64_t n, const double *mass, const double *vel,
+               const double *pot, double *out, void *stream)
+{
+    if (!c || n < 0 || !out || (n > 0 && (!mass || !vel)))
+        return P3T_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        P3T_CUDA_TRY(cudaMemsetAsync(out, 0, 2 * sizeof(double), s));
+        return P3T_OK;
+    }
+    return p3t_energy_launch(c, (int)n, mass, vel, pot, out, s);
+}
+
+int p3t_get_stats(p3t_ctx *c, p3t_stats *o)
+{
+    if (!c || !o) return P3T_ERR_INVALID;
+    if (cudaDeviceSynchronize() != cudaSuccess) return P3T_ERR_CUDA;
+    long long nnz = c->hst->nnz;
+    if (c->n > 0)
+        P3T_CUDA_TRY(cudaMemcpy(c->hst, c->st, sizeof(P3TDevState),
+                                cudaMemcpyDeviceToHost));
+    c->hst->nnz = nnz;
+    memset(o, 0, sizeof(*o));
+    o->n = c->n;
+    if (c->n == 0) return P3T_OK;
+    o->n_cells = c->hst->ncell;
+    o->n_groups = c->hst->ngroup;
+    o->n_levels = c->hst->max_level + 1;
+    o->list_pc = c->hst->tot[0];
+    o->list_pp_near = c->hst->tot[1];
+    o->list_pp_far = c->hst->tot[2];
+    o->int_pc = c->hst->int_pc;
+    o->int_pp = c->hst->int_pp;
+    o->int_pp_near = c->hst->int_ppn;
+    o->nnz = nnz;
+    return P3T_OK;
+}
+
+int p3t_get_order(p3t_ctx *c, uint64_t *key, int32_t *order)
+{
+    if (!c || !c->built) return P3T_ERR_STATE;
+    size_t n = (size_t)c->n;
+    if (n == 0) return P3T_OK;
+    if (key)
+        P3T_CUDA_TRY(cudaMemcpy(key, c->key_a, n * 8, cudaMemcpyDeviceToHost));
+    if (order)
+        P3T_CUDA_TRY(cudaMemcpy(order, c->order, n * 4, cudaMemcpyDeviceToHost));
+    return P3T_OK;
+}
+
+int p3t_get_root(p3t_ctx *c, double *lo, double *size)
+{
+    if (!c || !c->built) return P3T_ERR_STATE;
+    P3T_CUDA_TRY(cudaDeviceSynchronize());
+    P3T_CUDA_TRY(cudaMemcpy(c->hst, c->st, sizeof(P3TDevState),
+                            cudaMemcpyDeviceToHost));
+    if (lo)
+        for (int a = 0; a < 3; ++a) lo[a] = c->hst->lo[a];
+    if (size) *size = c->hst->size;
+    return P3T_OK;
+}
+
+int p3t_get_cells(p3t_ctx *c, int32_t *level, int32_t *first, int32_t *count,
+                  int32_t *child, int32_t *nchild, double *M, double *com,
+                  double *Q, float *fmin, float *fmax)
+{
+    if (!c || !c->built) return P3T_ERR_STATE;
+    const size_t C = c->n ? (size_t)c->hst->ncell : 0;
+    if (C == 0) return P3T_OK;
+    int4 *node = (int4 *)malloc(C * sizeof(int4));
+    float4 *a = (float4 *)malloc(C * sizeof(float4));
+    float4 *b = (float4 *)malloc(C * sizeof(float4));
+    if (!node || !a || !b) {
+        free(node); free(a); free(b);
+        return P3T_ERR_CUDA;
+    }
+    int rc = P3T_OK;
+    if (cudaMemcpy(node, c->node, C * sizeof(int4), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(a, c->wmin, C * sizeof(float4), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(b, c->wmax, C * sizeof(float4), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (M && cudaMemcpy(M, c->cM, C * 8, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (com && cudaMemcpy(com, c->ccom, 3 * C * 8, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (Q && cudaMemcpy(Q, c->cQ, 6 * C * 8, cudaMemcpyDeviceToHost) != cudaSuccess))
+        rc = P3T_ERR_CUDA;
+    if (rc == P3T_OK)
+        for (size_t k = 0; k < C; ++k) {
+            if (level) level[k] = node[k].w >> 8;
+            if (first) first[k] = node[k].x;
+            if (count) count[k] = node[k].y;
+            if (child) child[k] = node[k].z;
+            if (nchild) nchild[k] = node[k].w & 255;
+            if (fmin) {
+                fmin[3 * k] = a[k].x; fmin[3 * k + 1] = a[k].y; fmin[3 * k + 2] = a[k].z;
+            }
+            if (fmax) {
+                fmax[3 * k] = b[k].x; fmax[3 * k + 1] = b[k].y; fmax[3 * k + 2] = b[k].z;
+            }
+        }
+    free(node);
+    free(a);
+    free(b);
+    return rc;
+}
+
+int p3t_get_groups(p3t_ctx *c, int32_t *first, int32_t *count, float *fmin,
+                   float *fmax)
+{
+    if (!c || !c->built) return P3T_ERR_STATE;
+    const size_t G = c->n ? (size_t)c->hst->ngroup : 0;
+    if (G == 0) return P3T_OK;
+    int2 *r = (int2 *)malloc(G * sizeof(int2));
+    float4 *a = (float4 *)malloc(G * sizeof(float4));
+    float4 *b = (float4 *)malloc(G * sizeof(float4));
+    int rc = P3T_OK;
+    if (!r || !a || !b ||
+        cudaMemcpy(r, c->grange, G * sizeof(int2), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(a, c->gmin, G * sizeof(float4), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(b, c->gmax, G * sizeof(float4), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = P3T_ERR_CUDA;
+    if (rc == P3T_OK)
+        for (size_t g = 0; g < G; ++g) {
+            if (first) first[g] = r[g].x;
+            if (count) count[g] = r[g].y;
+            if (fmin) { fmin[3 * g] = a[g].x; fmin[3 * g + 1] = a[g].y; fmin[3 * g + 2] = a[g].z; }
+            if (fmax) { fmax[3 * g] = b[g].x; fmax[3 * g + 1] = b[g].y; fmax[3 * g + 2] = b[g].z; }
+        }
+    free(r);
+    free(a);
+    free(b);
+    return rc;
+}
+
+int p3t_get_lists(p3t_ctx *c, int64_t *pc_off, int32_t *pc, int64_t *ppn_off,
+                  int32_t *ppn, int64_t *ppf_off, int32_t *ppf)
+{
+    if (!c || !c->built) return P3T_ERR_STATE;
+    const size_t G = c->n ? (size_t)c->hst->ngroup : 0;
+    if (G == 0) return P3T_OK;
+    P3T_CUDA_TRY(cudaDeviceSynchronize());
+    int64_t *offs[3] = {pc_off, ppn_off, ppf_off};
+    int32_t *lists[3] = {pc, ppn, ppf};
+    for (int L = 0; L < 3; ++L) {
+        int64_t *o = offs[L];
+        int64_t tot = c->hst->tot[L];
+        if (o)
+            P3T_CUDA_TRY(cudaMemcpy(o, c->loff + (size_t)L * (G + 1),
+                                    (G + 1) * 8, cudaMemcpyDeviceToHost));
+        if (lists[L] && tot > 0)
+            P3T_CUDA_TRY(cudaMemcpy(lists[L], c->list[L], (size_t)tot * 4,
+                                    cudaMemcpyDeviceToHost));
+    }
+    return P3T_OK;
+}
+
+int p3t_profile_enable(p3t_ctx *c, int on)
+{
+    if (!c) return P3T_ERR_INVALID;
+    c->prof_on = on ? 1 : 0;
+    return P3T_OK;
+}
+
+int p3t_get_profile(p3t_ctx *c, p3t_profile *o, int reset)
+{
+    if (!c || !o) return P3T_ERR_INVALID;
+    int rc = prof_resolve(c);
+    if (rc) return rc;
+    o->build_ms = c->prof_ms[P3T_PH_BUILD];
+    o->walk_ms = c->prof_ms[P3T_PH_WALK];
+    o->force_ms = c->prof_ms[P3T_PH_FORCE];
+    o->ngb_ms = c->prof_ms[P3T_PH_NGB];
+    o->builds = c->prof_calls[P3T_PH_BUILD];
+    o->walks = c->prof_calls[P3T_PH_WALK];
+    o->forces = c->prof_calls[P3T_PH_FORCE];
+    o->ngbs = c->prof_calls[P3T_PH_NGB];
+    if (reset) {
+        for (int k = 0; k < P3T_NPH; ++k) {
+            c->prof_ms[k] = 0.0;
+            c->prof_calls[k] = 0;
+        }
+    }
+    return P3T_OK;
+}
+
+int64_t p3t_launch_count(void) { return g_launches.load(); }
+
+const char *p3t_status_string(int s)
+{
+    switch (s) {
+    case P3T_OK: return "ok";
+    case P3T_ERR_INVALID: return "invalid argument or input";
+    case P3T_ERR_CAPACITY: return "capacity exceeded";
+    case P3T_ERR_CUDA: return "CUDA error";
+    case P3T_ERR_TIMEOUT: return "device wait timed out";
+    case P3T_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

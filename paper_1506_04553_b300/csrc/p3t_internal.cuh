@@ -1,0 +1,164 @@
+// Internal declarations shared by the translation units of libp3t.
+// Device data layout (all in HBM, owned by the context):
+//   particles, Morton order : key u64[n], order i32[n] (original index),
+//                             xs f64[3][n], ms f64[n],
+//                             phi float4[n] = (x_hi, y_hi, z_hi, m),
+//                             plo float4[n] = (x_lo, y_lo, z_lo, 0)
+//                             where x = x_hi + x_lo to ~2^-48 relative
+//   cells                   : node int4[C] = (first, count, child, level<<8|nchild)
+//                             FP64 moments M[C], com[C][3], Q[C][6], bmin/bmax[C][3]
+//                             walk record wmin/wmax float4[C] (outward FP32 box,
+//                             .w = child / nchild bit patterns)
+//                             force record cf0/cf1/cf2 float4[C]
+//   groups                  : grange int2[G] = (first, count),
+//                             gmin/gmax/gctr float4[G]
+//   lists (CSR per group)   : pc i32, ppn i32, ppf i32 with int64 offsets
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/p3t.h"
+
+#define P3T_MAX_LEVEL 21
+#define P3T_WARP 32
+
+typedef unsigned long long u64;
+
+// Device-side state of one context (one copy in device memory, mirrored to
+// pinned host memory when a call synchronises).
+struct P3TDevState {
+    double lo[3];
+    double size;
+    int error;        // first P3T_ERR_* raised by a kernel (0 = none)
+    int ncell;        // cells allocated
+    int ngroup;       // groups allocated
+    int max_level;    // deepest level holding a cell
+    int need_cells;   // cells requested when the cell capacity overflowed
+    unsigned int blocks_done;
+    unsigned int work;  // dynamic work counter
+    int pad0;
+    int level_start[P3T_MAX_LEVEL + 3];
+    long long tot[3];   // list totals: pc, ppn, ppf
+    long long int_pc;   // particle-cell interactions
+    long long int_pp;   // particle-particle interactions
+    long long int_ppn;  // of which near-list interactions
+    long long nnz;      // neighbour pairs
+};
+
+// Phase timing with CUDA events (resolved lazily at p3t_get_profile).
+enum { P3T_PH_BUILD = 0, P3T_PH_WALK, P3T_PH_FORCE, P3T_PH_NGB, P3T_NPH };
+struct P3TEvents {
+    cudaEvent_t *ev;   // pairs: ev[2k] start, ev[2k+1] stop
+    int *phase;
+    int used, cap;
+};
+
+struct p3t_ctx {
+    p3t_params p;
+    int device;
+    int sms;
+    // capacities (elements)
+    int64_t cap_n, cap_cells, cap_groups, cap_list[3], cap_scan;
+    int64_t n;
+    int built;         // a tree exists
+    int forced_ngb;    // last force evaluation counted neighbours
+    // device state
+    P3TDevState *st;
+    P3TDevState *hst;  // pinned host mirror
+    // particles
+    u64 *key_a, *key_b;
+    int *idx_a, *idx_b;
+    int *order;
+    double *xs, *ms;
+    float4 *phi, *plo;
+    int *ngb_cnt;      // per original index
+    // sort scratch
+    int *rs_counts, *rs_totals;
+    int64_t cap_tiles;
+    double *bbox_part;
+    // cells
+    int4 *node;
+    int *parent;
+    double *cM, *ccom, *cQ, *cbmin, *cbmax;
+    float4 *wmin, *wmax, *cf0, *cf1, *cf2;
+    // groups
+    int2 *grange;
+    float4 *gmin, *gmax, *gctr;
+    // lists
+    long long *lcnt;   // [3][G] counts, then offsets [3][G+1]
+    long long *loff;
+    int *list[3];
+    // generic scan scratch
+    long long *scan_part;
+    // energy scratch
+    double *red_part;
+    // profiling
+    int prof_on;
+    P3TEvents prof;
+    double prof_ms[P3T_NPH];
+    long long prof_calls[P3T_NPH];
+};
+
+// Kernel launch accounting (all contexts).
+void p3t_count_launches(long long k);
+// Profiling helpers: open returns a slot (or -1), close records the stop.
+int p3t_prof_open(p3t_ctx *c, int phase, cudaStream_t s);
+void p3t_prof_close(p3t_ctx *c, int slot, cudaStream_t s);
+
+// ---- error helpers ----
+#define P3T_CUDA_TRY(expr)                                              \
+    do {                                                                \
+        cudaError_t e__ = (expr);                                       \
+        if (e__ != cudaSuccess) return P3T_ERR_CUDA;                    \
+    } while (0)
+
+__device__ __forceinline__ void p3t_raise(P3TDevState *st, int code)
+{
+    atomicCAS(&st->error, 0, code);
+}
+
+// ---- warp helpers ----
+__device__ __forceinline__ int warp_incl_scan(int v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ long long warp_incl_scan_ll(long long v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    return (1u << (threadIdx.x & 31)) - 1u;
+}
+
+// ---- kernel-launch helpers implemented in the .cu files ----
+int p3t_sort_keys(p3t_ctx *c, int n, cudaStream_t s);          // p3t_sort.cu
+int p3t_scan_ll(p3t_ctx *c, const int *in, long long *out, int n,
+                cudaStream_t s);                                 // p3t_misc.cu
+int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
+                     const double *mass);                       // p3t_tree.cu
+int p3t_run_walk(p3t_ctx *c, int fill, cudaStream_t s);        // p3t_walk.cu
+int p3t_scan_lists(p3t_ctx *c, cudaStream_t s);                 // p3t_walk.cu
+int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s);   // p3t_force.cu
+int p3t_run_ngb_fill(p3t_ctx *c, const long long *off, int *idx,
+                     long long cap, cudaStream_t s);             // p3t_force.cu
+int p3t_energy_launch(p3t_ctx *c, int n, const double *mass,
+                      const double *vel, const double *pot, double *out,
+                      cudaStream_t s);                           // p3t_misc.cu
+int64_t p3t_sort_tiles(int64_t n);                               // p3t_sort.cu
+int64_t p3t_scan_blocks(int64_t n);                              // p3t_misc.cu
+void p3t_mac_constants(const p3t_params *p, float *theta2, float *hg2);

@@ -1,0 +1,221 @@
+// Elementwise FP64 updates (kick, drift), energy reductions and the scan that
+// turns per-particle neighbour counts into CSR offsets.
+#include "p3t_internal.cuh"
+
+namespace {
+
+constexpr int TB = 256;
+
+// Velocity kick of Eq. 11 / Sect. 2.2: v <- v + dt * a (FP64, no FMA).
+__global__ void __launch_bounds__(TB)
+k_kick(long long n3, double *__restrict__ v, const float *__restrict__ a,
+       double dt)
+{
+    for (long long i = blockIdx.x * (long long)TB + threadIdx.x; i < n3;
+         i += (long long)gridDim.x * TB)
+        v[i] = __dadd_rn(v[i], __dmul_rn(dt, (double)a[i]));
+}
+
+// Drift of Sect. 2.2 step 5: x <- x + dt * v (FP64, no FMA).
+__global__ void __launch_bounds__(TB)
+k_drift(long long n3, double *__restrict__ x, const double *__restrict__ v,
+        double dt)
+{
+    for (long long i = blockIdx.x * (long long)TB + threadIdx.x; i < n3;
+         i += (long long)gridDim.x * TB)
+        x[i] = __dadd_rn(x[i], __dmul_rn(dt, v[i]));
+}
+
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double ws[TB / 32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < TB / 32; ++q) s += ws[q];
+    __syncthreads();
+    return s;
+}
+
+// Per-block partial sums of 1/2 m |v|^2 and 1/2 m phi.
+__global__ void __launch_bounds__(TB)
+k_energy_part(int n, const double *__restrict__ m, const double *__restrict__ v,
+              const double *__restrict__ phi, double *__restrict__ part)
+{
+    double ek = 0.0, ep = 0.0;
+    for (int i = blockIdx.x * TB + threadIdx.x; i < n; i += gridDim.x * TB) {
+        double vx = v[i], vy = v[(size_t)n + i], vz = v[2 * (size_t)n + i];
+        ek += 0.5 * m[i] * (vx * vx + vy * vy + vz * vz);
+        if (phi) ep += 0.5 * m[i] * phi[i];
+    }
+    double a = block_sum(ek);
+    double b = block_sum(ep);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void k_energy_final(int nblk, const double *__restrict__ part,
+                               double *__restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < nblk; ++q) {
+        a += part[2 * q];
+        b += part[2 * q + 1];
+    }
+    out[0] = a;
+    out[1] = b;
+}
+
+// ---- exclusive scan int -> int64 (three phases) ----
+constexpr int SC_T = 256;
+constexpr int SC_ITEMS = 16;
+constexpr int SC_TILE = SC_T * SC_ITEMS;
+
+__device__ __forceinline__ long long block_excl_scan_ll(long long v,
+                                                        long long *total)
+{
+    __shared__ long long ws[SC_T / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    long long inc = warp_incl_scan_ll(v);
+    if (lane == 31) ws[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        long long x = lane < SC_T / 32 ? ws[lane] : 0;
+        long long xi = warp_incl_scan_ll(x);
+        __syncwarp();
+        if (lane < SC_T / 32) ws[lane] = xi - x;
+        if (lane == 31) *total = xi;
+    }
+    __syncthreads();
+    long long r = inc - v + ws[w];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SC_T)
+k_scan_reduce(int n, const int *__restrict__ in, long long *__restrict__ part)
+{
+    __shared__ long long tot;
+    long long s = 0;
+    const int base = blockIdx.x * SC_TILE;
+    for (int q = 0; q < SC_ITEMS; ++q) {
+        int i = base + q * SC_T + threadIdx.x;
+        if (i < n) s += in[i];
+    }
+    block_excl_scan_ll(s, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SC_T)
+k_scan_partials(int nb, long long *__restrict__ part)
+{
+    __shared__ long long tot;
+    long long carry = 0;
+    for (int b = 0; b < nb; b += SC_T) {
+        int i = b + threadIdx.x;
+        long long v = i < nb ? part[i] : 0;
+        long long ex = block_excl_scan_ll(v, &tot);
+        if (i < nb) part[i] = ex + carry;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[nb] = carry;
+}
+
+__global__ void __launch_bounds__(SC_T)
+k_scan_apply(int n, const int *__restrict__ in,
+             const long long *__restrict__ part, long long *__restrict__ out,
+             int nb)
+{
+    __shared__ long long tot;
+    // thread t owns the SC_ITEMS consecutive items [base + t*ITEMS, ...)
+    const int base = blockIdx.x * SC_TILE + threadIdx.x * SC_ITEMS;
+    int v[SC_ITEMS];
+    long long s = 0;
+#pragma unroll
+    for (int q = 0; q < SC_ITEMS; ++q) {
+        int i = base + q;
+        v[q] = i < n ? in[i] : 0;
+        s += v[q];
+    }
+    long long ex = block_excl_scan_ll(s, &tot) + part[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < SC_ITEMS; ++q) {
+        int i = base + q;
+        if (i < n) out[i] = ex;
+        ex += v[q];
+    }
+    if (blockIdx.x == nb - 1 && threadIdx.x == 0) out[n] = part[nb];
+}
+
+}  // namespace
+
+int p3t_scan_ll(p3t_ctx *c, const int *in, long long *out, int n,
+                cudaStream_t s)
+{
+    if (n == 0) {
+        P3T_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(long long), s));
+        return P3T_OK;
+    }
+    int nb = (n + SC_TILE - 1) / SC_TILE;
+    if (nb + 1 > c->cap_scan) return P3T_ERR_STATE;
+    k_scan_reduce<<<nb, SC_T, 0, s>>>(n, in, c->scan_part);
+    k_scan_partials<<<1, SC_T, 0, s>>>(nb, c->scan_part);
+    k_scan_apply<<<nb, SC_T, 0, s>>>(n, in, c->scan_part, out, nb);
+    p3t_count_launches(3);
+    P3T_CUDA_TRY(cudaGetLastError());
+    return P3T_OK;
+}
+
+int64_t p3t_scan_blocks(int64_t n) { return (n + SC_TILE - 1) / SC_TILE; }
+
+static int grid_for(long long n3)
+{
+    long long b = (n3 + TB - 1) / TB;
+    if (b > 148 * 16) b = 148 * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+extern "C" int p3t_kick(int64_t n, double *vel, const float *acc, double dt,
+                        void *stream)
+{
+    if (n < 0 || (n > 0 && (!vel || !acc))) return P3T_ERR_INVALID;
+    if (n == 0) return P3T_OK;
+    long long n3 = 3 * (long long)n;
+    k_kick<<<grid_for(n3), TB, 0, (cudaStream_t)stream>>>(n3, vel, acc, dt);
+    p3t_count_launches(1);
+    P3T_CUDA_TRY(cudaGetLastError());
+    return P3T_OK;
+}
+
+extern "C" int p3t_drift(int64_t n, double *pos, const double *vel, double dt,
+                         void *stream)
+{
+    if (n < 0 || (n > 0 && (!pos || !vel))) return P3T_ERR_INVALID;
+    if (n == 0) return P3T_OK;
+    long long n3 = 3 * (long long)n;
+    k_drift<<<grid_for(n3), TB, 0, (cudaStream_t)stream>>>(n3, pos, vel, dt);
+    p3t_count_launches(1);
+    P3T_CUDA_TRY(cudaGetLastError());
+    return P3T_OK;
+}
+
+int p3t_energy_launch(p3t_ctx *c, int n, const double *mass, const double *vel,
+                      const double *pot, double *out, cudaStream_t s)
+{
+    int nb = (n + TB - 1) / TB;
+    if (nb > c->sms * 4) nb = c->sms * 4;
+    if (nb < 1) nb = 1;
+    k_energy_part<<<nb, TB, 0, s>>>(n, mass, vel, pot, c->red_part);
+    k_energy_final<<<1, 32, 0, s>>>(nb, c->red_part, out);
+    p3t_count_launches(2);
+    P3T_CUDA_TRY(cudaGetLastError());
+    return P3T_OK;
+}

@@ -1,0 +1,533 @@
+// Tree construction (Sect. 2.2: Barnes-Hut tree up to the quadrupole moment).
+//
+//   bbox      root cube: componentwise min, largest extent, side =
+//             extent * (1 + 2^-20) (1 when all particles coincide); input
+//             validation (finite coordinates, finite positive masses)
+//   keys      21-bit quantisation per axis, floor((x - lo) / side * 2^21)
+//             with one FP64 rounding per operation, interleaved x-highest
+//             into a 63-bit Morton key
+//   (sort)    p3t_sort.cu
+//   gather    Morton-ordered FP64 copies and the FP32 hi/lo split
+//   split     level by level: a cell of level L < 21 holding more than n_leaf
+//             particles gets its non-empty octants (found by binary search
+//             on the sorted keys) as children, contiguous and in Morton order
+//   moments   level by level from the deepest: M, centre of mass, traceless
+//             quadrupole Q_ab = sum m (3 d_a d_b - |d|^2 delta_ab) about the
+//             centre of mass, member box; leaves from their particles,
+//             internal cells from their children (parallel-axis shift) in
+//             FP64; then the FP32 walk and force records
+//   groups    below every internal cell with more than n_group particles,
+//             runs of consecutive children holding at most n_group particles
+//             each are merged greedily while the run holds at most n_group;
+//             a larger leaf is cut into chunks of n_group
+#include <math.h>
+
+#include "p3t_internal.cuh"
+
+namespace {
+
+constexpr int TB = 256;
+
+// ---------------------------------------------------------------- bbox ----
+__global__ void __launch_bounds__(TB)
+k_bbox_partial(int n, const double *__restrict__ pos,
+               const double *__restrict__ mass, double *__restrict__ part,
+               P3TDevState *st)
+{
+    double mn[3] = {INFINITY, INFINITY, INFINITY};
+    double mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    for (int i = blockIdx.x * TB + threadIdx.x; i < n; i += gridDim.x * TB) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double v = pos[(size_t)a * n + i];
+            bad |= !isfinite(v);
+            mn[a] = fmin(mn[a], v);
+            mx[a] = fmax(mx[a], v);
+        }
+        double m = mass[i];
+        bad |= !(m > 0.0) || !isfinite(m);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) p3t_raise(st, P3T_ERR_INVALID);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    }
+    __shared__ double smn[3][TB / 32], smx[3][TB / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) {
+            smn[a][w] = mn[a];
+            smx[a][w] = mx[a];
+        }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        int a = threadIdx.x;
+        double u = smn[a][0], v = smx[a][0];
+        for (int q = 1; q < TB / 32; ++q) {
+            u = fmin(u, smn[a][q]);
+            v = fmax(v, smx[a][q]);
+        }
+        part[blockIdx.x * 6 + a] = u;
+        part[blockIdx.x * 6 + 3 + a] = v;
+    }
+}
+
+__global__ void k_bbox_final(int nblk, const double *__restrict__ part,
+                             P3TDevState *st)
+{
+    if (threadIdx.x != 0) return;
+    double mn[3], mx[3];
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = part[a];
+        mx[a] = part[3 + a];
+    }
+    for (int b = 1; b < nblk; ++b)
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fmin(mn[a], part[6 * b + a]);
+            mx[a] = fmax(mx[a], part[6 * b + 3 + a]);
+        }
+    double ext = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double e = __dsub_rn(mx[a], mn[a]);
+        if (e > ext) ext = e;
+        st->lo[a] = mn[a];
+    }
+    st->size = (ext == 0.0) ? 1.0 : __dmul_rn(ext, 1.0 + 0x1p-20);
+}
+
+// ---------------------------------------------------------------- keys ----
+__device__ __forceinline__ u64 quantise(double x, double lo, double size)
+{
+    double t = __dsub_rn(x, lo);
+    double u = __ddiv_rn(t, size);
+    double v = __dmul_rn(u, 2097152.0);
+    long long q = (long long)floor(v);
+    q = q < 0 ? 0 : q;
+    q = q > 2097151 ? 2097151 : q;
+    return (u64)q;
+}
+
+// Spreads the low 21 bits of v so that bit b lands on bit 3b.
+__device__ __forceinline__ u64 spread3(u64 v)
+{
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__global__ void __launch_bounds__(TB)
+k_keys(int n, const double *__restrict__ pos, const P3TDevState *st,
+       u64 *__restrict__ key, int *__restrict__ idx)
+{
+    int i = blockIdx.x * TB + threadIdx.x;
+    if (i >= n) return;
+    const double size = st->size;
+    u64 qx = quantise(pos[i], st->lo[0], size);
+    u64 qy = quantise(pos[(size_t)n + i], st->lo[1], size);
+    u64 qz = quantise(pos[2 * (size_t)n + i], st->lo[2], size);
+    key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    idx[i] = i;
+}
+
+// -------------------------------------------------------------- gather ----
+__global__ void __launch_bounds__(TB)
+k_gather(int n, const int *__restrict__ sidx, const double *__restrict__ pos,
+         const double *__restrict__ mass, int *__restrict__ order,
+         double *__restrict__ xs, double *__restrict__ ms,
+         float4 *__restrict__ phi, float4 *__restrict__ plo)
+{
+    int k = blockIdx.x * TB + threadIdx.x;
+    if (k >= n) return;
+    int i = sidx[k];
+    order[k] = i;
+    double x = pos[i], y = pos[(size_t)n + i], z = pos[2 * (size_t)n + i];
+    double m = mass[i];
+    xs[k] = x;
+    xs[(size_t)n + k] = y;
+    xs[2 * (size_t)n + k] = z;
+    ms[k] = m;
+    float xh = __double2float_rn(x), yh = __double2float_rn(y),
+          zh = __double2float_rn(z);
+    phi[k] = make_float4(xh, yh, zh, __double2float_rn(m));
+    plo[k] = make_float4(__double2float_rn(x - (double)xh),
+                         __double2float_rn(y - (double)yh),
+                         __double2float_rn(z - (double)zh), 0.0f);
+}
+
+// --------------------------------------------------------------- split ----
+__global__ void k_tree_init(int n, int4 *node, int *parent, P3TDevState *st)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    node[0] = make_int4(0, n, -1, 0);
+    parent[0] = -1;
+    st->ncell = 1;
+    st->ngroup = 0;
+    st->max_level = 0;
+    st->need_cells = 0;
+    st->blocks_done = 0;
+    st->level_start[0] = 0;
+    for (int L = 1; L < P3T_MAX_LEVEL + 3; ++L) st->level_start[L] = 1;
+}
+
+__device__ __forceinline__ int digit_at(u64 key, int L)
+{
+    return (int)((key >> (3 * (P3T_MAX_LEVEL - L))) & 7u);
+}
+
+// first position p in [lo, hi) with digit_at(key[p], L) >= d
+__device__ __forceinline__ int lower_digit(const u64 *__restrict__ key, int lo,
+                                           int hi, int L, int d)
+{
+    while (lo < hi) {
+        int mid = lo + ((hi - lo) >> 1);
+        if (digit_at(key[mid], L) < d)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(TB)
+k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
+             int4 *__restrict__ node, int *__restrict__ parent,
+             P3TDevState *st)
+{
+    const int beg = st->level_start[L], end = st->level_start[L + 1];
+    const bool stop = st->error != 0;
+    for (int c = beg + blockIdx.x * TB + threadIdx.x; c < end && !stop;
+         c += gridDim.x * TB) {
+        int4 nd = node[c];
+        if (nd.y <= n_leaf || L >= P3T_MAX_LEVEL) continue;
+        int b[9];
+        b[0] = nd.x;
+        b[8] = nd.x + nd.y;
+#pragma unroll
+        for (int d = 1; d < 8; ++d)
+            b[d] = lower_digit(key, b[d - 1], b[8], L + 1, d);
+        int k = 0;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) k += b[d + 1] > b[d];
+        int base = atomicAdd(&st->ncell, k);
+        if (base + k > cap) {
+            p3t_raise(st, P3T_ERR_CAPACITY);
+            atomicMax(&st->need_cells, base + k);
+            continue;
+        }
+        int j = 0;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            if (b[d + 1] > b[d]) {
+                node[base + j] = make_int4(b[d], b[d + 1] - b[d], -1,
+                                           (L + 1) << 8);
+                parent[base + j] = c;
+                ++j;
+            }
+        }
+        node[c].z = base;
+        node[c].w = (L << 8) | k;
+    }
+    // the last block to finish closes the next level's range
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned t = atomicAdd(&st->blocks_done, 1u);
+        if (t == gridDim.x - 1) {
+            int nc = atomicAdd(&st->ncell, 0);
+            if (nc > cap) nc = cap;
+            st->level_start[L + 2] = nc;
+            if (nc > st->level_start[L + 1]) st->max_level = L + 1;
+            st->blocks_done = 0;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------- moments ----
+// Writes the FP32 records of cell c from its FP64 moments.
+__device__ __forceinline__ void write_records(
+    int c, int4 nd, double M, const double *com, const double *Q,
+    const double *bmn, const double *bmx, float4 *wmin, float4 *wmax,
+    float4 *cf0, float4 *cf1, float4 *cf2)
+{
+    wmin[c] = make_float4(__double2float_rd(bmn[0]), __double2float_rd(bmn[1]),
+                          __double2float_rd(bmn[2]), __int_as_float(nd.z));
+    wmax[c] = make_float4(__double2float_ru(bmx[0]), __double2float_ru(bmx[1]),
+                          __double2float_ru(bmx[2]),
+                          __int_as_float(nd.w & 255));
+    float ch[3], cl[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ch[a] = __double2float_rn(com[a]);
+        cl[a] = __double2float_rn(com[a] - (double)ch[a]);
+    }
+    cf0[c] = make_float4(ch[0], ch[1], ch[2], __double2float_rn(M));
+    cf1[c] = make_float4(cl[0], cl[1], cl[2], __double2float_rn(Q[0]));
+    cf2[c] = make_float4(__double2float_rn(Q[1]), __double2float_rn(Q[3]),
+                         __double2float_rn(Q[4]), __double2float_rn(Q[5]));
+}
+
+__global__ void __launch_bounds__(TB)
+k_moments(int L, const double *__restrict__ xs, const double *__restrict__ ms,
+          int n, const int4 *__restrict__ node, double *__restrict__ cM,
+          double *__restrict__ ccom, double *__restrict__ cQ,
+          double *__restrict__ cbmin, double *__restrict__ cbmax,
+          float4 *__restrict__ wmin, float4 *__restrict__ wmax,
+          float4 *__restrict__ cf0, float4 *__restrict__ cf1,
+          float4 *__restrict__ cf2, const P3TDevState *st)
+{
+    if (st->error) return;
+    const int beg = st->level_start[L], end = st->level_start[L + 1];
+    for (int c = beg + blockIdx.x * TB + threadIdx.x; c < end;
+         c += gridDim.x * TB) {
+        int4 nd = node[c];
+        double M = 0.0, com[3] = {0, 0, 0}, Q[6] = {0, 0, 0, 0, 0, 0};
+        double bmn[3] = {INFINITY, INFINITY, INFINITY};
+        double bmx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        const int nch = nd.w & 255;
+        if (nch == 0) {
+            // leaf: from its particles
+            for (int k = nd.x; k < nd.x + nd.y; ++k) {
+                double m = ms[k];
+                M += m;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    double x = xs[(size_t)a * n + k];
+                    com[a] += m * x;
+                    bmn[a] = fmin(bmn[a], x);
+                    bmx[a] = fmax(bmx[a], x);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) com[a] /= M;
+            for (int k = nd.x; k < nd.x + nd.y; ++k) {
+                double m = ms[k];
+                double dx = xs[k] - com[0];
+                double dy = xs[(size_t)n + k] - com[1];
+                double dz = xs[2 * (size_t)n + k] - com[2];
+                double d2 = dx * dx + dy * dy + dz * dz;
+                Q[0] += m * (3.0 * dx * dx - d2);
+                Q[1] += m * (3.0 * dy * dy - d2);
+                Q[2] += m * (3.0 * dz * dz - d2);
+                Q[3] += m * (3.0 * dx * dy);
+                Q[4] += m * (3.0 * dx * dz);
+                Q[5] += m * (3.0 * dy * dz);
+            }
+        } else {
+            // internal: combine the children (parallel-axis shift)
+            for (int q = 0; q < nch; ++q) {
+                int ch = nd.z + q;
+                double m = cM[ch];
+                M += m;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    com[a] += m * ccom[3 * ch + a];
+                    bmn[a] = fmin(bmn[a], cbmin[3 * ch + a]);
+                    bmx[a] = fmax(bmx[a], cbmax[3 * ch + a]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) com[a] /= M;
+            for (int q = 0; q < nch; ++q) {
+                int ch = nd.z + q;
+                double m = cM[ch];
+                double dx = ccom[3 * ch + 0] - com[0];
+                double dy = ccom[3 * ch + 1] - com[1];
+                double dz = ccom[3 * ch + 2] - com[2];
+                double d2 = dx * dx + dy * dy + dz * dz;
+                const double *qc = cQ + 6 * ch;
+                Q[0] += qc[0] + m * (3.0 * dx * dx - d2);
+                Q[1] += qc[1] + m * (3.0 * dy * dy - d2);
+                Q[2] += qc[2] + m * (3.0 * dz * dz - d2);
+                Q[3] += qc[3] + m * (3.0 * dx * dy);
+                Q[4] += qc[4] + m * (3.0 * dx * dz);
+                Q[5] += qc[5] + m * (3.0 * dy * dz);
+            }
+        }
+        cM[c] = M;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            ccom[3 * c + a] = com[a];
+            cbmin[3 * c + a] = bmn[a];
+            cbmax[3 * c + a] = bmx[a];
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) cQ[6 * c + q] = Q[q];
+        write_records(c, nd, M, com, Q, bmn, bmx, wmin, wmax, cf0, cf1, cf2);
+    }
+}
+
+// -------------------------------------------------------------- groups ----
+__device__ __forceinline__ void emit_group(int first, int count,
+                                           int2 *grange, int &slot)
+{
+    grange[slot++] = make_int2(first, count);
+}
+
+__device__ __forceinline__ int chunks(int count, int ng)
+{
+    return (count + ng - 1) / ng;
+}
+
+// One thread per cell.  A cell emits groups when it is internal and holds
+// more than n_group particles (runs of small children, chunked big leaves);
+// the root also emits when it is itself small or a leaf.
+__global__ void __launch_bounds__(TB)
+k_groups(int ng, int gcap, const int4 *__restrict__ node,
+         int2 *__restrict__ grange, P3TDevState *st)
+{
+    if (st->error) return;
+    const int ncell = st->ncell;
+    for (int c = blockIdx.x * TB + threadIdx.x; c < ncell;
+         c += gridDim.x * TB) {
+        int4 nd = node[c];
+        const int nch = nd.w & 255;
+        if (c == 0 && (nd.y <= ng || nch == 0)) {
+            int k = chunks(nd.y, ng);
+            int slot = atomicAdd(&st->ngroup, k);
+            if (slot + k > gcap) {
+                p3t_raise(st, P3T_ERR_STATE);
+                continue;
+            }
+            for (int q = 0; q < k; ++q) {
+                int f = nd.x + q * ng;
+                int cnt = min(ng, nd.y - q * ng);
+                emit_group(f, cnt, grange, slot);
+            }
+            continue;
+        }
+        if (nch == 0 || nd.y <= ng) continue;
+        // pass 1: count, pass 2: write
+        int slot = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            int ngr = 0, run_first = 0, run_count = 0;
+            for (int q = 0; q < nch; ++q) {
+                int4 ch = node[nd.z + q];
+                if (ch.y <= ng) {
+                    if (run_count > 0 && run_count + ch.y > ng) {
+                        if (pass) emit_group(run_first, run_count, grange, slot);
+                        ++ngr;
+                        run_count = 0;
+                    }
+                    if (run_count == 0) run_first = ch.x;
+                    run_count += ch.y;
+                } else {
+                    if (run_count > 0) {
+                        if (pass) emit_group(run_first, run_count, grange, slot);
+                        ++ngr;
+                        run_count = 0;
+                    }
+                    if ((ch.w & 255) == 0) {
+                        int k = chunks(ch.y, ng);
+                        if (pass)
+                            for (int r = 0; r < k; ++r)
+                                emit_group(ch.x + r * ng,
+                                           min(ng, ch.y - r * ng), grange, slot);
+                        ngr += k;
+                    }
+                }
+            }
+            if (run_count > 0) {
+                if (pass) emit_group(run_first, run_count, grange, slot);
+                ++ngr;
+            }
+            if (pass == 0) {
+                slot = atomicAdd(&st->ngroup, ngr);
+                if (slot + ngr > gcap) {
+                    p3t_raise(st, P3T_ERR_STATE);
+                    break;
+                }
+            }
+        }
+    }
+}
+
+// Group boxes (FP32 outward), relative origin and neighbour screening radius.
+// gmin.w = hs2: squared screening radius; any pair of the group with
+// |x_i - x_j| < h has an FP32 group-relative r^2 below hs2.
+__global__ void __launch_bounds__(TB)
+k_group_box(const int2 *__restrict__ grange, const double *__restrict__ xs,
+            int n, double h, float4 *__restrict__ gmin,
+            float4 *__restrict__ gmax, float4 *__restrict__ gctr,
+            const P3TDevState *st)
+{
+    if (st->error) return;
+    const int G = st->ngroup;  // <= capacity (k_groups checks)
+    for (int g = blockIdx.x * TB + threadIdx.x; g < G; g += gridDim.x * TB) {
+        int2 r = grange[g];
+        double mn[3] = {INFINITY, INFINITY, INFINITY};
+        double mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int k = r.x; k < r.x + r.y; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                double x = xs[(size_t)a * n + k];
+                mn[a] = fmin(mn[a], x);
+                mx[a] = fmax(mx[a], x);
+            }
+        float c[3];
+        double R2 = 0.0, cabs = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            c[a] = __double2float_rn(0.5 * (mn[a] + mx[a]));
+            double e = fmax(fabs(mx[a] - (double)c[a]), fabs(mn[a] - (double)c[a]));
+            R2 += e * e;
+            cabs = fmax(cabs, fabs((double)c[a]));
+        }
+        double R = sqrt(R2);
+        // screening margin: 2^-14 h (R + h) + 2^-30 h |c| (>> the FP32
+        // rounding of group-relative coordinates and of r^2)
+        double hs2 = h * h + 0x1p-14 * h * (R + h) + 0x1p-30 * h * cabs;
+        gmin[g] = make_float4(__double2float_rd(mn[0]), __double2float_rd(mn[1]),
+                              __double2float_rd(mn[2]),
+                              __double2float_ru(hs2));
+        gmax[g] = make_float4(__double2float_ru(mx[0]), __double2float_ru(mx[1]),
+                              __double2float_ru(mx[2]), 0.0f);
+        gctr[g] = make_float4(c[0], c[1], c[2], 0.0f);
+    }
+}
+
+}  // namespace
+
+// Bounding box, keys, sort, gather, level-wise split, moments, groups.
+int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
+                     const double *mass)
+{
+    const int grid_small = c->sms * 4;
+    int nb = (n + TB - 1) / TB;
+    int nbb = nb < grid_small ? nb : grid_small;
+    if (nbb < 1) nbb = 1;
+    k_bbox_partial<<<nbb, TB, 0, s>>>(n, pos, mass, c->bbox_part, c->st);
+    k_bbox_final<<<1, 32, 0, s>>>(nbb, c->bbox_part, c->st);
+    k_keys<<<nb, TB, 0, s>>>(n, pos, c->st, c->key_a, c->idx_a);
+    int rc = p3t_sort_keys(c, n, s);
+    if (rc) return rc;
+    k_gather<<<nb, TB, 0, s>>>(n, c->idx_a, pos, mass, c->order, c->xs, c->ms,
+                               c->phi, c->plo);
+    k_tree_init<<<1, 32, 0, s>>>(n, c->node, c->parent, c->st);
+    const int cap = (int)c->cap_cells;
+    for (int L = 0; L < P3T_MAX_LEVEL; ++L)
+        k_tree_split<<<grid_small, TB, 0, s>>>(L, c->p.n_leaf, cap, c->key_a,
+                                                c->node, c->parent, c->st);
+    for (int L = P3T_MAX_LEVEL; L >= 0; --L)
+        k_moments<<<grid_small, TB, 0, s>>>(L, c->xs, c->ms, n, c->node, c->cM,
+                                             c->ccom, c->cQ, c->cbmin,
+                                             c->cbmax, c->wmin, c->wmax,
+                                             c->cf0, c->cf1, c->cf2, c->st);
+    k_groups<<<grid_small, TB, 0, s>>>(c->p.n_group, (int)c->cap_groups,
+                                        c->node, c->grange, c->st);
+    double h = c->p.h > 0.0 ? c->p.h : c->p.r_out;
+    k_group_box<<<grid_small, TB, 0, s>>>(c->grange, c->xs, n, h, c->gmin,
+                                           c->gmax, c->gctr, c->st);
+    // bbox 2, keys, gather, init, 21 splits, 22 moment levels, groups, boxes
+    p3t_count_launches(2 + 1 + 1 + 1 + P3T_MAX_LEVEL + (P3T_MAX_LEVEL + 1) + 2);
+    P3T_CUDA_TRY(cudaGetLastError());
+    return P3T_OK;
+}

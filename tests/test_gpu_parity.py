@@ -1,0 +1,241 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bit-exact: Morton keys, sort order, root cube, cell and group structure, FP32
+boxes, interaction-list sets, neighbour lists, kick and drift.
+Within tolerance: forces against the same-tree FP64 oracle (per-particle
+relative error, floor 1e-3 rms: median <= 1e-5, max <= 1e-4), moments.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1506_04553_b300 import ics
+from parity_util import compare_lists, compare_structure, gpu_run, rel_err
+
+pytestmark = pytest.mark.gpu
+
+GAMMA = 0.1
+
+
+def _params(**kw):
+    from paper_1506_04553_b300 import Params
+    return Params(**kw)
+
+
+def _plummer(n, seed):
+    pos, vel, m = ics.plummer(n, seed)
+    return pos.T.copy(), vel, m
+
+
+CASES = {
+    # config 1: Plummer N = 8192, r_out = 0.01, theta = 0.4, eps = 4/N
+    "plummer8192": lambda: (*_plummer(8192, 1)[::2], dict(
+        theta=0.4, r_out=0.01, eps=4 / 8192)),
+    "plummer3000_theta0.6": lambda: (*_plummer(3000, 7)[::2], dict(
+        theta=0.6, r_out=0.02, eps=1e-3, n_leaf=8, n_group=32)),
+    "gauss_dense": lambda: (np.random.default_rng(3).normal(size=(5000, 3)) * 0.05,
+                            np.random.default_rng(4).uniform(0.5, 1.5, 5000) / 5000,
+                            dict(theta=0.5, r_out=0.01, eps=0.0, h=0.012)),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def case(request, cuda):
+    pos, m, kw = CASES[request.param]()
+    p = _params(**kw)
+    ctx, acc, pot, ngb = gpu_run(pos, m, p, potential=True)
+    t = oracle.Tree(pos, m, n_leaf=p.n_leaf, n_group=p.n_group)
+    h = p.h if p.h > 0 else p.r_out
+    t.walk(p.theta, h, p.r_out)
+    return dict(name=request.param, pos=pos, m=m, p=p, ctx=ctx, acc=acc,
+                pot=pot, ngb=ngb, tree=t, h=h)
+
+
+def test_structure_bitexact(case):
+    compare_structure(case["ctx"], case["tree"])
+
+
+def test_lists_identical(case):
+    og, gid = compare_structure(case["ctx"], case["tree"])
+    compare_lists(case["ctx"], case["tree"], og, gid)
+    st = case["ctx"].stats()
+    L = case["tree"].lists()
+    assert st["list_pc"] == L["pc"].size
+    assert st["list_pp_near"] == L["ppn"].size
+    assert st["list_pp_far"] == L["ppf"].size
+
+
+def test_force_matches_same_tree_oracle(case):
+    p = case["p"]
+    a_o, p_o = case["tree"].force(G=p.G, eps=p.eps, r_cut=p.r_out,
+                                  gamma=p.gamma, potential=True)
+    e = rel_err(case["acc"], a_o)
+    assert np.median(e) <= 1e-5, np.median(e)
+    assert e.max() <= 1e-4, e.max()
+    ep = np.abs(case["pot"] - p_o) / np.abs(p_o)
+    assert np.median(ep) <= 1e-5 and ep.max() <= 1e-4, (np.median(ep), ep.max())
+
+
+def test_neighbours_bitexact(case):
+    off, idx = case["ngb"]
+    off_o, idx_o = oracle.neighbours(case["pos"], case["h"])
+    assert np.array_equal(off, off_o)
+    assert np.array_equal(idx.astype(np.int64), idx_o.astype(np.int64))
+    if case["name"] == "gauss_dense":
+        assert off[-1] > 5 * case["pos"].shape[0]  # several neighbours each
+
+
+def test_theta_zero_equals_direct_sum(cuda):
+    pos, _, m = ics.plummer(4096, 12)
+    pos = pos.T.copy()
+    p = _params(theta=0.0, r_out=0.01, eps=4 / 4096)
+    ctx, acc, pot, _ = gpu_run(pos, m, p, potential=True)
+    assert ctx.stats()["list_pc"] == 0
+    a_d, p_d = oracle.direct(pos, m, G=1.0, eps=p.eps, r_cut=p.r_out,
+                             gamma=GAMMA, kind="soft", potential=True)
+    e = rel_err(acc, a_d)
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4, (np.median(e), e.max())
+
+
+def test_error_vs_direct_consistent_with_theta(cuda):
+    pos, _, m = ics.plummer(8192, 1)
+    pos = pos.T.copy()
+    a_d = oracle.direct(pos, m, eps=4 / 8192, r_cut=0.01, gamma=GAMMA)
+    meds = []
+    for th in (0.8, 0.4, 0.2):
+        _, acc, _, _ = gpu_run(pos, m, _params(theta=th, r_out=0.01, eps=4 / 8192),
+                               neighbours=False)
+        meds.append(np.median(rel_err(acc, a_d)))
+    assert meds[0] > meds[1] > meds[2]
+    assert meds[1] < 2e-3
+
+
+def test_kick_drift_bitexact(cuda):
+    import torch
+    from paper_1506_04553_b300 import drift, kick
+    rng = np.random.default_rng(8)
+    v = rng.normal(size=(3, 10001))
+    x = rng.normal(size=(3, 10001))
+    a = rng.normal(size=(3, 10001)).astype(np.float32)
+    vd = torch.tensor(v, device="cuda")
+    xd = torch.tensor(x, device="cuda")
+    ad = torch.tensor(a, device="cuda")
+    kick(vd, ad, 1 / 512)
+    drift(xd, vd, 1 / 256)
+    v1 = oracle.kick(v, a, 1 / 512)
+    x1 = oracle.drift(x, v1, 1 / 256)
+    assert np.array_equal(vd.cpu().numpy(), v1)
+    assert np.array_equal(xd.cpu().numpy(), x1)
+
+
+def test_energy(cuda):
+    import torch
+    pos, vel, m = ics.plummer(4096, 5)
+    p = _params(theta=0.4, r_out=0.01, eps=4 / 4096)
+    ctx, acc, pot, _ = gpu_run(pos.T.copy(), m, p, potential=True,
+                               neighbours=False)
+    out = ctx.energy(torch.tensor(m, device="cuda"),
+                     torch.tensor(vel, device="cuda"),
+                     torch.tensor(pot, device="cuda")).cpu().numpy()
+    ek = 0.5 * float((m * (vel * vel).sum(axis=0)).sum())
+    ep = 0.5 * float((m * pot).sum())
+    assert abs(out[0] - ek) <= 1e-12 * abs(ek)
+    assert abs(out[1] - ep) <= 1e-12 * abs(ep)
+
+
+@pytest.mark.parametrize("n", [1, 2, 16, 17, 65, 300])
+def test_small_sizes(cuda, n):
+    rng = np.random.default_rng(n)
+    pos = rng.normal(size=(n, 3)) * 0.01
+    m = rng.uniform(0.5, 1.5, n) / n
+    p = _params(theta=0.5, r_out=0.005, eps=1e-4)
+    ctx, acc, _, ngb = gpu_run(pos, m, p)
+    t = oracle.Tree(pos, m)
+    t.walk(p.theta, p.r_out, p.r_out)
+    og, gid = compare_structure(ctx, t)
+    compare_lists(ctx, t, og, gid)
+    a_o = t.force(eps=p.eps, r_cut=p.r_out)
+    if n > 1:
+        e = rel_err(acc, a_o)
+        assert e.max() <= 1e-4
+    else:
+        assert np.all(acc == 0.0)
+    off_o, idx_o = oracle.neighbours(pos, p.r_out)
+    assert np.array_equal(ngb[0], off_o) and np.array_equal(ngb[1], idx_o)
+
+
+def test_coincident_particles(cuda):
+    # all particles at one point: the tree is a chain down to level 21, every
+    # pair has K(0) = 0 (force exactly zero) and every pair is a neighbour
+    n = 100
+    pos = np.full((n, 3), 0.25)
+    m = np.full(n, 1.0 / n)
+    p = _params(theta=0.4, r_out=0.01, eps=0.0, n_leaf=16, n_group=32)
+    ctx, acc, _, ngb = gpu_run(pos, m, p)
+    assert np.all(acc == 0.0)
+    t = oracle.Tree(pos, m, n_leaf=16, n_group=32)
+    t.walk(p.theta, p.r_out, p.r_out)
+    og, gid = compare_structure(ctx, t)
+    compare_lists(ctx, t, og, gid)
+    off, idx = ngb
+    assert off[-1] == n * (n - 1)
+    off_o, idx_o = oracle.neighbours(pos, p.r_out)
+    assert np.array_equal(off, off_o) and np.array_equal(idx, idx_o)
+
+
+def test_exact_distance_ties(cuda):
+    # pairs at exactly r = h (excluded) and just inside (included)
+    h = 0.5
+    pos = np.array([[0.0, 0.0, 0.0], [0.5, 0.0, 0.0], [0.0, 0.3, 0.4],
+                    [0.0, -0.3, 0.39999], [0.0, 0.0, 0.0], [0.1, 0.1, 0.1]])
+    m = np.full(6, 1 / 6)
+    p = _params(theta=0.4, r_out=0.5, h=h, eps=0.0)
+    _, _, _, ngb = gpu_run(pos, m, p)
+    off_o, idx_o = oracle.neighbours(pos, h)
+    assert np.array_equal(ngb[0], off_o) and np.array_equal(ngb[1], idx_o)
+
+
+def test_empty_input(cuda):
+    import torch
+    from paper_1506_04553_b300 import Context
+    ctx = Context(_params())
+    e = torch.zeros((3, 0), dtype=torch.float64, device="cuda")
+    ctx.build_tree(e, torch.zeros((0,), dtype=torch.float64, device="cuda"))
+    acc = ctx.long_force()
+    assert acc.shape == (3, 0)
+    off, idx = ctx.neighbours()
+    assert off.cpu().tolist() == [0] and idx.numel() == 0
+
+
+def test_errors(cuda):
+    import torch
+    from paper_1506_04553_b300 import Context, P3TError
+    ctx = Context(_params())
+    with pytest.raises(P3TError) as ei:
+        ctx.long_force(torch.zeros((3, 0), dtype=torch.float32, device="cuda"))
+    assert ei.value.code == 5  # force before build
+    pos = torch.zeros((3, 10), dtype=torch.float64, device="cuda")
+    pos[0, 3] = float("nan")
+    with pytest.raises(P3TError) as ei:
+        ctx.build_tree(pos, torch.ones(10, dtype=torch.float64, device="cuda"))
+    assert ei.value.code == 1
+    pos[0, 3] = 0.0
+    with pytest.raises(P3TError) as ei:
+        ctx.build_tree(pos, -torch.ones(10, dtype=torch.float64, device="cuda"))
+    assert ei.value.code == 1
+    # valid input after errors works again
+    ctx.build_tree(torch.rand((3, 10), dtype=torch.float64, device="cuda"),
+                   torch.ones(10, dtype=torch.float64, device="cuda"))
+    ctx.long_force()
+    # neighbour capacity too small
+    off = torch.zeros(11, dtype=torch.int64, device="cuda")
+    idx = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx2 = Context(_params(r_out=10.0))
+    ctx2.build_tree(torch.rand((3, 10), dtype=torch.float64, device="cuda"),
+                    torch.ones(10, dtype=torch.float64, device="cuda"))
+    ctx2.long_force()
+    with pytest.raises(P3TError) as ei:
+        ctx2.neighbours_into(off, idx)
+    assert ei.value.code == 2
