@@ -144,6 +144,34 @@ int p3t_drift(int64_t n, double *pos, const double *vel, double dt,
 int p3t_energy(p3t_ctx *ctx, int64_t n, const double *mass, const double *vel,
                const double *pot, double *out, void *stream);
 
+/* The same energy sums as p3t_energy for callers that cannot allocate device
+ * memory: code that runs while a stream is being captured into a CUDA graph,
+ * or inside a host application whose device memory is entirely owned by
+ * another allocator (a pre-reserved pool), may not call cudaMalloc, and a
+ * p3t_ctx (which allocates) may not be available to it.  The paper has no
+ * counterpart; this is a service of the library.
+ * Scratch: a static device array of P3T_ENERGY_NOALLOC_MAX_PARTIALS block
+ * partial sums (two doubles each, 16 KiB) that every GPU loading the library
+ * keeps until exit; no cudaMalloc, cudaFree or allocating library routine is
+ * called.  The launch uses min(ceil(n / 256), 4 x SM count) blocks, so any n
+ * fits as long as the device has at most 256 SMs.
+ *   n    : 0 <= n <= P3T_ENERGY_NOALLOC_MAX_N (INT32_MAX, the kernel's
+ *          index type); larger n is rejected with P3T_ERR_CAPACITY
+ *   mass, vel, pot, out : as p3t_energy (device pointers; pot may be NULL)
+ * The first call on a device looks up the scratch address for that device
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (every
+ * partial a call reads is written by that call first, so nothing needs
+ * clearing); calls that overlap on the GPU (different streams, no ordering)
+ * race on it and must be serialised by the caller.
+ * Errors: P3T_ERR_INVALID (NULL pointer with n > 0, n < 0),
+ * P3T_ERR_CAPACITY (n too large, or more partials than the array holds),
+ * P3T_ERR_CUDA. */
+#define P3T_ENERGY_NOALLOC_MAX_PARTIALS 1024
+#define P3T_ENERGY_NOALLOC_MAX_N 2147483647LL
+int p3t_energy_noalloc(int64_t n, const double *mass, const double *vel,
+                       const double *pot, double *out, void *stream);
+
 /* Counters of the last build / force evaluation (host struct). */
 typedef struct p3t_stats {
     int64_t n;

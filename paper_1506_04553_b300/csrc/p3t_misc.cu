@@ -1,5 +1,7 @@
 // Elementwise FP64 updates (kick, drift), energy reductions and the scan that
 // turns per-particle neighbour counts into CSR offsets.
+#include <mutex>
+
 #include "p3t_internal.cuh"
 
 namespace {
@@ -215,6 +217,60 @@ int p3t_energy_launch(p3t_ctx *c, int n, const double *mass, const double *vel,
     if (nb < 1) nb = 1;
     k_energy_part<<<nb, TB, 0, s>>>(n, mass, vel, pot, c->red_part);
     k_energy_final<<<1, 32, 0, s>>>(nb, c->red_part, out);
+    p3t_count_launches(2);
+    P3T_CUDA_TRY(cudaGetLastError());
+    return P3T_OK;
+}
+
+// ---- energy sums without allocation -------------------------------------
+// Block partials live in this file-scope device array instead of memory from
+// cudaMalloc.  Host code must not pass the symbol itself to a kernel (on the
+// host it names a host-side shadow, not device memory): the device address is
+// looked up once per device with cudaGetSymbolAddress while that device is
+// current, and that address is what the kernels receive.
+static __device__ __align__(256) double
+    g_energy_scratch[2 * P3T_ENERGY_NOALLOC_MAX_PARTIALS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+double *g_scratch_ptr[kMaxDevices];
+}  // namespace
+
+static int energy_scratch(double **out)
+{
+    int dev = 0;
+    P3T_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return P3T_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        double *ptr = nullptr;
+        P3T_CUDA_TRY(cudaGetSymbolAddress((void **)&ptr, g_energy_scratch));
+        g_scratch_ptr[dev] = ptr;
+    }
+    *out = g_scratch_ptr[dev];
+    return P3T_OK;
+}
+
+extern "C" int p3t_energy_noalloc(int64_t n, const double *mass,
+                                  const double *vel, const double *pot,
+                                  double *out, void *stream)
+{
+    if (n < 0 || !out || (n > 0 && (!mass || !vel))) return P3T_ERR_INVALID;
+    if (n > P3T_ENERGY_NOALLOC_MAX_N) return P3T_ERR_CAPACITY;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *scratch = nullptr;
+    int rc = energy_scratch(&scratch);
+    if (rc != P3T_OK) return rc;
+    int dev = 0, sms = 0;
+    P3T_CUDA_TRY(cudaGetDevice(&dev));
+    P3T_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    long long nb = (n + TB - 1) / TB;
+    if (nb > 4LL * sms) nb = 4LL * sms;
+    if (nb < 1) nb = 1;
+    if (nb > P3T_ENERGY_NOALLOC_MAX_PARTIALS) return P3T_ERR_CAPACITY;
+    k_energy_part<<<(int)nb, TB, 0, s>>>((int)n, mass, vel, pot, scratch);
+    k_energy_final<<<1, 32, 0, s>>>((int)nb, scratch, out);
     p3t_count_launches(2);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
