@@ -89,7 +89,7 @@ def measured_peaks():
 def profile_traffic():
     """Per-launch DRAM bytes of the force kernel from the committed ncu
     summary (a line 'dram_bytes_per_launch: <float>'), else None."""
-    path = os.path.join(HERE, "profiles", "k_force_plummer_1M.txt")
+    path = os.path.join(HERE, "profiles", "k_walk_force_plummer_1M.txt")
     try:
         for line in open(path):
             if line.startswith("dram_bytes_per_launch:"):
@@ -239,8 +239,7 @@ def run_ours(args, world, rank, local):
     n = args.n
     pos_h, vel_h, mass_h = ics.plummer(n, SEED + rank)
     params = P.Params(theta=THETA, r_out=R_OUT, gamma=GAMMA, eps=4.0 / n,
-                      h=R_OUT, G=1.0, n_leaf=N_LEAF, n_group=N_GROUP,
-                      flags=P.FLAG_NEIGHBOURS)
+                      h=R_OUT, G=1.0, n_leaf=N_LEAF, n_group=N_GROUP)
     ctx = P.Context(params)
     stream = torch.cuda.current_stream(dev)
     pos = torch.tensor(pos_h, device=dev)
@@ -251,7 +250,7 @@ def run_ours(args, world, rank, local):
 
     # initial force and neighbour capacity
     ctx.build_tree(pos, mass)
-    ctx.long_force(acc)
+    ctx.long_force(acc, check=True)
     _, idx0 = ctx.neighbours()
     cap = max(4 * int(idx0.numel()) + 1024, n)
     idx = torch.empty((cap,), dtype=torch.int32, device=dev)
@@ -260,7 +259,7 @@ def run_ours(args, world, rank, local):
         P.kick(vel, acc, 0.5 * DT)
         P.drift(pos, vel, DT)
         ctx.build_tree(pos, mass)
-        ctx.long_force(acc)
+        ctx.long_force(acc, check=False)
         ctx.neighbours_into(off, idx, sync=False)
         P.kick(vel, acc, 0.5 * DT)
 
@@ -275,16 +274,15 @@ def run_ours(args, world, rank, local):
     sampler = ClockSampler(local)
     sampler.start()
     l0 = P.launch_count()
-    stats = []
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         step()
-        stats.append(ctx.stats())
     e1.record(stream)
     torch.cuda.synchronize()
+    ctx.check()  # any error latched on the device during the timed steps
     launches = P.launch_count() - l0
     clocks = sampler.stop()
     ctx.profile_enable(False)
@@ -298,9 +296,7 @@ def run_ours(args, world, rank, local):
     value = world * n * args.steps / (ms * 1e-3)
 
     # interactions and roofline of the force kernel
-    int_pc = sum(s["int_pc"] for s in stats)
-    int_pp = sum(s["int_pp"] for s in stats)
-    int_ppn = sum(s["int_pp_near"] for s in stats)
+    int_pc, int_pp, int_ppn = prof["int_pc"], prof["int_pp"], prof["int_pp_near"]
     flops = FLOPS_PC * int_pc + FLOPS_PP_NEAR * int_ppn + FLOPS_PP_FAR * (int_pp - int_ppn)
     force_s = prof["force_ms"] * 1e-3
     achieved = flops / force_s / 1e12 if force_s > 0 else None
@@ -324,12 +320,11 @@ def run_ours(args, world, rank, local):
         "interactions_per_particle": {"pc": int_pc / (n * args.steps),
                                       "pp": int_pp / (n * args.steps)},
         "phase_ms_per_step": {"build": prof["build_ms"] / args.steps,
-                              "walk": prof["walk_ms"] / args.steps,
-                              "force": prof["force_ms"] / args.steps,
+                              "walk_and_force": prof["force_ms"] / args.steps,
                               "neighbours": prof["ngb_ms"] / args.steps},
         "force_particles_per_s": world * n * args.steps / force_s if force_s else None,
         "fwd_bwd_ratio": None,
-        "roofline": {"kernel": "k_force", "bound": "alu",
+        "roofline": {"kernel": "k_walk_force", "bound": "alu",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if achieved else None,
                      "traffic": traffic,
@@ -353,7 +348,7 @@ def run_ours(args, world, rank, local):
             P.kick(vel, acc, 0.5 * DT)
             P.drift(pos, vel, DT)
             ctx.build_tree(pos, mass)
-            ctx.long_force(acc)
+            ctx.long_force(acc, check=False)
             nnz = ctx.neighbours_into(off, idx, sync=True)
             P.kick(vel, acc, 0.5 * DT)
             hp.copy_(pos, non_blocking=True)

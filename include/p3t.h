@@ -44,10 +44,6 @@ extern "C" {
 #define P3T_ERR_TIMEOUT 4  /* a bounded device-side wait expired */
 #define P3T_ERR_STATE 5    /* call out of order (e.g. force before build) */
 
-/* ---- flags ---- */
-/* p3t_long_force also counts neighbours within h (needed by p3t_neighbours). */
-#define P3T_FLAG_NEIGHBOURS 1
-
 typedef struct p3t_ctx p3t_ctx;
 
 /* Parameters.  Names follow the paper: r_out is r_cut of Eq. 12-15 and
@@ -65,12 +61,12 @@ typedef struct p3t_params {
                         (1..64; default 16) */
     int32_t n_group; /* particles sharing one interaction list (1..64;
                         default 64) */
-    int32_t flags;   /* P3T_FLAG_* */
+    int32_t flags;   /* reserved, 0 */
     int32_t reserved;
 } p3t_params;
 
 /* Fills *p with the defaults: theta 0.4, r_out 1/64, gamma 0.1, eps 0,
- * h 0 (= r_out), G 1, n_leaf 16, n_group 64, flags P3T_FLAG_NEIGHBOURS. */
+ * h 0 (= r_out), G 1, n_leaf 16, n_group 64, flags 0. */
 int p3t_default_params(p3t_params *p);
 
 /* Creates a context on the current device.  *ctx receives the handle.
@@ -91,7 +87,8 @@ int p3t_set_params(p3t_ctx *ctx, const p3t_params *p);
  * Steps: root cube, 63-bit Morton keys (21 bits per axis), stable radix sort
  * by (key, index), level-wise split of every cell holding more than n_leaf
  * particles, FP64 monopole + traceless quadrupole moments per cell, groups
- * of at most n_group particles.  The context keeps Morton-ordered copies, so
+ * of at most n_group particles (runs of consecutive sibling cells).  The
+ * context keeps Morton-ordered copies, so
  * pos and mass may change after the call returns.  n == 0 builds an empty
  * tree.  Synchronises `stream` once at the end (to size later launches).
  * Errors: P3T_ERR_INVALID (n < 0, NULL pointer with n > 0, non-finite
@@ -103,27 +100,36 @@ int p3t_build_tree(p3t_ctx *ctx, int64_t n, const double *pos,
  *   acc : device, float[3][n] (SoA), written in the caller's order
  *   pot : device, double[n] or NULL; if given, the soft potential
  *         phi_i = -sum_j G m_j W(s_ij / r_cut) / s_ij (Eq. 6, Eq. 16)
- * Cells are accepted only when every pair they stand for is farther apart
- * than max(h, r_cut), so cell terms carry K = 1; particle pairs carry K.
- * With P3T_FLAG_NEIGHBOURS the per-particle neighbour counts are produced
- * for p3t_neighbours.  Synchronises `stream` once (to size the lists).
+ * Each group of particles walks the tree with the opening test (a cell is
+ * accepted only when its box is farther than max(h, r_cut) from the group's
+ * box and its size is below theta times that distance) and its interactions
+ * are evaluated as they are found: cells as softened quadrupoles with K = 1,
+ * leaf particles pair by pair with K.  No host synchronisation: errors found
+ * by the kernels (P3T_ERR_CAPACITY if a walk stack overflows) are latched on
+ * the device and returned by the next p3t_check, p3t_build_tree or
+ * synchronising p3t_neighbours call.
  * Errors: P3T_ERR_STATE (no tree), P3T_ERR_INVALID (acc NULL with n > 0),
  * P3T_ERR_CUDA. */
 int p3t_long_force(p3t_ctx *ctx, float *acc, double *pot, void *stream);
 
-/* Neighbour lists (Sect. 2.2) of the last p3t_long_force call made with
- * P3T_FLAG_NEIGHBOURS, in CSR form: the neighbours of particle i are
- * idx[offsets[i] .. offsets[i+1]), ascending original indices.  j is a
- * neighbour of i iff j != i and ((dx*dx + dy*dy) + dz*dz) < h*h evaluated in
- * FP64 with dx = x_i - x_j (unsoftened distance, strict inequality).
+/* Synchronises `stream` and returns (and clears) the first error latched by
+ * a kernel of this context since the last check, or P3T_OK. */
+int p3t_check(p3t_ctx *ctx, void *stream);
+
+/* Neighbour lists (Sect. 2.2) of the particles of the current tree, in CSR
+ * form: the neighbours of particle i are idx[offsets[i] .. offsets[i+1]),
+ * ascending original indices.  j is a neighbour of i iff j != i and
+ * ((dx*dx + dy*dy) + dz*dz) < h*h evaluated in FP64 with dx = x_i - x_j
+ * (unsoftened distance, strict inequality).
  *   offsets : device, int64[n + 1]
  *   idx     : device, int32[cap]
  *   cap     : capacity of idx
  *   needed  : host int64*, receives the total count (nnz); may be NULL, in
  *             which case no host synchronisation happens and a too-small
- *             cap is reported by the next synchronising call.
+ *             cap is latched (nothing is written past cap) and reported by
+ *             the next p3t_check.
  * Errors: P3T_ERR_CAPACITY (nnz > cap; offsets valid, idx undefined),
- * P3T_ERR_STATE (no force evaluation with P3T_FLAG_NEIGHBOURS), P3T_ERR_CUDA. */
+ * P3T_ERR_STATE (no tree), P3T_ERR_CUDA. */
 int p3t_neighbours(p3t_ctx *ctx, int64_t *offsets, int32_t *idx, int64_t cap,
                    int64_t *needed, void *stream);
 
@@ -195,10 +201,13 @@ int p3t_get_stats(p3t_ctx *ctx, p3t_stats *s);
  * device time of every phase since the last reset. */
 typedef struct p3t_profile {
     double build_ms;   /* p3t_build_tree, all kernels */
-    double walk_ms;    /* tree walk (count pass, scan, fill pass) */
-    double force_ms;   /* the force kernel alone */
-    double ngb_ms;     /* p3t_neighbours: scan, fill, row sort */
+    double walk_ms;    /* unused (the walk runs inside the force kernel) */
+    double force_ms;   /* p3t_long_force: the fused walk + force kernel */
+    double ngb_ms;     /* p3t_neighbours: near walks, scan, row sort */
     int64_t builds, walks, forces, ngbs; /* number of timed calls */
+    int64_t int_pc, int_pp, int_pp_near; /* interactions evaluated by
+                                            p3t_long_force since the last
+                                            reset */
 } p3t_profile;
 int p3t_profile_enable(p3t_ctx *ctx, int on);
 int p3t_get_profile(p3t_ctx *ctx, p3t_profile *out, int reset);
@@ -230,9 +239,13 @@ int p3t_get_cells(p3t_ctx *ctx, int32_t *level, int32_t *first,
 int p3t_get_groups(p3t_ctx *ctx, int32_t *first, int32_t *count, float *fmin,
                    float *fmax);
 
-/* Interaction lists of the last p3t_long_force, CSR per group (group order
- * as p3t_get_groups): cells (cell ids as p3t_get_cells), near particles and
- * far particles (sorted particle ids).  Offsets have n_groups + 1 entries. */
+/* Interaction lists of the current tree and parameters, CSR per group (group
+ * order as p3t_get_groups): cells (cell ids as p3t_get_cells), near particles
+ * and far particles (sorted particle ids).  Offsets have n_groups + 1
+ * entries.  The lists are made by a separate walk with the same traversal
+ * and opening test as the force kernel (run on the first call after a build
+ * or a parameter change); call once with the list pointers NULL to learn the
+ * sizes from the offsets' last entries, then again to copy the lists. */
 int p3t_get_lists(p3t_ctx *ctx, int64_t *pc_off, int32_t *pc,
                   int64_t *ppn_off, int32_t *ppn, int64_t *ppf_off,
                   int32_t *ppf);

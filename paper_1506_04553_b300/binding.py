@@ -21,9 +21,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Params", "Context", "P3TError", "kick", "drift", "library_path",
-           "launch_count", "FLAG_NEIGHBOURS"]
-
-FLAG_NEIGHBOURS = 1
+           "launch_count"]
 
 _STATUS = {0: "ok", 1: "invalid argument or input", 2: "capacity exceeded",
            3: "CUDA error", 4: "device wait timed out", 5: "call out of order"}
@@ -67,7 +65,9 @@ class _CProfile(C.Structure):
     _fields_ = [("build_ms", C.c_double), ("walk_ms", C.c_double),
                 ("force_ms", C.c_double), ("ngb_ms", C.c_double),
                 ("builds", C.c_int64), ("walks", C.c_int64),
-                ("forces", C.c_int64), ("ngbs", C.c_int64)]
+                ("forces", C.c_int64), ("ngbs", C.c_int64),
+                ("int_pc", C.c_int64), ("int_pp", C.c_int64),
+                ("int_pp_near", C.c_int64)]
 
 
 _lib = _load_lib()
@@ -91,6 +91,7 @@ _sigs = {
     "p3t_get_groups": [_vp, _vp, _vp, _vp, _vp],
     "p3t_get_lists": [_vp] + [_vp] * 6,
     "p3t_profile_enable": [_vp, C.c_int],
+    "p3t_check": [_vp, _vp],
     "p3t_get_profile": [_vp, _vp, C.c_int],
 }
 for _name, _args in _sigs.items():
@@ -152,7 +153,7 @@ class Params:
     G: float = 1.0
     n_leaf: int = 16
     n_group: int = 64
-    flags: int = FLAG_NEIGHBOURS
+    flags: int = 0
 
     def _c(self) -> _CParams:
         p = _CParams()
@@ -197,9 +198,11 @@ class Context:
                "p3t_build_tree")
         self.n = n
 
-    def long_force(self, acc=None, pot=None, want_potential=False, stream=None):
+    def long_force(self, acc=None, pot=None, want_potential=False, stream=None,
+                   check=True):
         """Soft acceleration (3, n) float32; with ``want_potential`` also the
-        soft potential (n,) float64.  Returns acc or (acc, pot)."""
+        soft potential (n,) float64.  Returns acc or (acc, pot).  With
+        ``check`` the stream is synchronised and device-side errors raise."""
         import torch
         n = self.n
         if acc is None:
@@ -210,7 +213,13 @@ class Context:
         q = _dptr(pot, torch.float64, (n,), "pot") if pot is not None else None
         _check(_lib.p3t_long_force(self._h, a, q, _stream(stream)),
                "p3t_long_force")
+        if check:
+            self.check(stream)
         return (acc, pot) if pot is not None else acc
+
+    def check(self, stream=None):
+        """Synchronise and raise the first error latched on the device."""
+        _check(_lib.p3t_check(self._h, _stream(stream)), "p3t_check")
 
     def neighbours(self, stream=None):
         """CSR neighbour lists (offsets int64[n+1], idx int32[nnz]) on the
@@ -314,21 +323,22 @@ class Context:
         return out
 
     def lists(self) -> dict:
-        st = self.stats()
-        g = st["n_groups"]
-        out = dict(pc_off=np.zeros(g + 1, np.int64),
-                   pc=np.zeros(max(st["list_pc"], 1), np.int32),
-                   ppn_off=np.zeros(g + 1, np.int64),
-                   ppn=np.zeros(max(st["list_pp_near"], 1), np.int32),
-                   ppf_off=np.zeros(g + 1, np.int64),
-                   ppf=np.zeros(max(st["list_pp_far"], 1), np.int32))
-        if g:
-            _check(_lib.p3t_get_lists(self._h, *[_np_ptr(out[k]) for k in (
-                "pc_off", "pc", "ppn_off", "ppn", "ppf_off", "ppf")]),
-                "p3t_get_lists")
-        out["pc"] = out["pc"][: st["list_pc"]]
-        out["ppn"] = out["ppn"][: st["list_pp_near"]]
-        out["ppf"] = out["ppf"][: st["list_pp_far"]]
+        """Interaction lists (CSR per group) from the inspection walk."""
+        g = self.stats()["n_groups"]
+        offs = {k: np.zeros(g + 1, np.int64) for k in ("pc_off", "ppn_off", "ppf_off")}
+        if g == 0:
+            return dict(**offs, pc=np.zeros(0, np.int32), ppn=np.zeros(0, np.int32),
+                        ppf=np.zeros(0, np.int32))
+        _check(_lib.p3t_get_lists(self._h, _np_ptr(offs["pc_off"]), None,
+                                  _np_ptr(offs["ppn_off"]), None,
+                                  _np_ptr(offs["ppf_off"]), None), "p3t_get_lists")
+        out = dict(offs)
+        for k in ("pc", "ppn", "ppf"):
+            out[k] = np.zeros(max(int(offs[k + "_off"][-1]), 1), np.int32)
+        _check(_lib.p3t_get_lists(self._h, *[_np_ptr(out[k]) for k in (
+            "pc_off", "pc", "ppn_off", "ppn", "ppf_off", "ppf")]), "p3t_get_lists")
+        for k in ("pc", "ppn", "ppf"):
+            out[k] = out[k][: int(offs[k + "_off"][-1])]
         return out
 
 

@@ -198,7 +198,7 @@ int p3t_default_params(p3t_params *p)
     p->G = 1.0;
     p->n_leaf = 16;
     p->n_group = 64;
-    p->flags = P3T_FLAG_NEIGHBOURS;
+    p->flags = 0;
     return P3T_OK;
 }
 
@@ -252,6 +252,7 @@ int p3t_set_params(p3t_ctx *c, const p3t_params *p)
     if (!c) return P3T_ERR_INVALID;
     P3T_TRY(check_params(p));
     c->p = *p;
+    c->lists_valid = 0;
     return P3T_OK;
 }
 
@@ -262,7 +263,7 @@ int p3t_build_tree(p3t_ctx *c, int64_t n, const double *pos,
     if (n > 0 && (!pos || !mass)) return P3T_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     c->built = 0;
-    c->forced_ngb = 0;
+    c->lists_valid = 0;
     c->n = n;
     if (n == 0) {
         memset(c->hst, 0, sizeof(P3TDevState));
@@ -296,65 +297,64 @@ int p3t_long_force(p3t_ctx *c, float *acc, double *pot, void *stream)
 {
     if (!c) return P3T_ERR_INVALID;
     if (!c->built) return P3T_ERR_STATE;
-    if (c->n == 0) {
-        c->forced_ngb = (c->p.flags & P3T_FLAG_NEIGHBOURS) != 0;
-        return P3T_OK;
-    }
+    if (c->n == 0) return P3T_OK;
     if (!acc) return P3T_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
-    P3T_TRY(clear_error(c, s));
-    int slot = p3t_prof_open(c, P3T_PH_WALK, s);
-    P3T_TRY(p3t_run_walk(c, 0, s));
-    P3T_TRY(p3t_scan_lists(c, s));
-    int rc = sync_state(c, s);
-    if (rc == P3T_OK && c->hst->error) rc = c->hst->error;
-    if (rc != P3T_OK) {
-        p3t_prof_close(c, slot, s);
-        return rc;
-    }
-    for (int L = 0; L < 3; ++L) P3T_TRY(ensure_list(c, L, c->hst->tot[L]));
-    P3T_TRY(p3t_run_walk(c, 1, s));
+    int slot = p3t_prof_open(c, P3T_PH_FORCE, s);
+    int rc = p3t_run_force(c, acc, pot, s);
     p3t_prof_close(c, slot, s);
-    slot = p3t_prof_open(c, P3T_PH_FORCE, s);
-    P3T_TRY(p3t_run_force(c, acc, pot, s));
-    p3t_prof_close(c, slot, s);
-    c->forced_ngb = (c->p.flags & P3T_FLAG_NEIGHBOURS) != 0;
-    return P3T_OK;
+    return rc;
+}
+
+int p3t_check(p3t_ctx *c, void *stream)
+{
+    if (!c) return P3T_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    P3T_TRY(sync_state(c, s));
+    int e = c->hst->error;
+    if (e) P3T_TRY(clear_error(c, s));
+    return e;
 }
 
 int p3t_neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, int64_t cap,
                    int64_t *needed, void *stream)
 {
     if (!c || !offsets || cap < 0 || (cap > 0 && !idx)) return P3T_ERR_INVALID;
-    if (!c->built || !c->forced_ngb) return P3T_ERR_STATE;
+    if (!c->built) return P3T_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     const int n = (int)c->n;
-    int slot = p3t_prof_open(c, P3T_PH_NGB, s);
-    P3T_TRY(p3t_scan_ll(c, c->ngb_cnt, (long long *)offsets, n, s));
-    if (needed) {
-        long long nnz = 0;
-        P3T_CUDA_TRY(cudaMemcpyAsync(&nnz, offsets + n, sizeof(long long),
-                                     cudaMemcpyDeviceToHost, s));
-        P3T_CUDA_TRY(cudaStreamSynchronize(s));
-        *needed = nnz;
-        c->hst->nnz = nnz;
-        if (nnz > cap) {
-            p3t_prof_close(c, slot, s);
-            return P3T_ERR_CAPACITY;
-        }
-    }
     if (n == 0) {
-        p3t_prof_close(c, slot, s);
+        P3T_CUDA_TRY(cudaMemsetAsync(offsets, 0, sizeof(int64_t), s));
+        if (needed) *needed = 0;
         return P3T_OK;
     }
-    P3T_TRY(clear_error(c, s));
-    P3T_TRY(p3t_run_ngb_fill(c, (const long long *)offsets, idx, cap, s));
-    p3t_prof_close(c, slot, s);
-    if (needed) {
-        P3T_TRY(sync_state(c, s));
-        if (c->hst->error) return c->hst->error;
+    int slot = p3t_prof_open(c, P3T_PH_NGB, s);
+    int rc = p3t_run_ngb(c, 0, nullptr, nullptr, 0, s);
+    if (rc == P3T_OK)
+        rc = p3t_scan_ll(c, c->ngb_cnt, (long long *)offsets, n, s);
+    if (rc == P3T_OK && needed) {
+        long long nnz = 0;
+        if (cudaMemcpyAsync(&nnz, offsets + n, sizeof(long long),
+                            cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            rc = P3T_ERR_CUDA;
+        *needed = nnz;
+        c->hst->nnz = nnz;
+        if (rc == P3T_OK && nnz > cap) rc = P3T_ERR_CAPACITY;
     }
-    return P3T_OK;
+    if (rc == P3T_OK)
+        rc = p3t_run_ngb(c, 1, (const long long *)offsets, idx, cap, s);
+    p3t_prof_close(c, slot, s);
+    if (rc == P3T_OK && needed) {
+        long long nnz = c->hst->nnz;
+        rc = sync_state(c, s);
+        c->hst->nnz = nnz;
+        if (rc == P3T_OK && c->hst->error) {
+            rc = c->hst->error;
+            clear_error(c, s);
+        }
+    }
+    return rc;
 }
 
 int p3t_energy(p3t_ctx *c, int64_t n, const double *mass, const double *vel,
@@ -495,12 +495,26 @@ int p3t_get_lists(p3t_ctx *c, int64_t *pc_off, int32_t *pc, int64_t *ppn_off,
     if (!c || !c->built) return P3T_ERR_STATE;
     const size_t G = c->n ? (size_t)c->hst->ngroup : 0;
     if (G == 0) return P3T_OK;
-    P3T_CUDA_TRY(cudaDeviceSynchronize());
+    if (!c->lists_valid) {
+        cudaStream_t s = 0;
+        P3T_TRY(clear_error(c, s));
+        P3T_TRY(p3t_run_walk(c, 0, s));
+        P3T_TRY(p3t_scan_lists(c, s));
+        P3T_TRY(sync_state(c, s));
+        if (c->hst->error) return c->hst->error;
+        for (int L = 0; L < 3; ++L) {
+            P3T_TRY(ensure_list(c, L, c->hst->tot[L]));
+            c->list_tot[L] = c->hst->tot[L];
+        }
+        P3T_TRY(p3t_run_walk(c, 1, s));
+        P3T_CUDA_TRY(cudaStreamSynchronize(s));
+        c->lists_valid = 1;
+    }
     int64_t *offs[3] = {pc_off, ppn_off, ppf_off};
     int32_t *lists[3] = {pc, ppn, ppf};
     for (int L = 0; L < 3; ++L) {
         int64_t *o = offs[L];
-        int64_t tot = c->hst->tot[L];
+        int64_t tot = c->list_tot[L];
         if (o)
             P3T_CUDA_TRY(cudaMemcpy(o, c->loff + (size_t)L * (G + 1),
                                     (G + 1) * 8, cudaMemcpyDeviceToHost));
@@ -531,6 +545,18 @@ int p3t_get_profile(p3t_ctx *c, p3t_profile *o, int reset)
     o->walks = c->prof_calls[P3T_PH_WALK];
     o->forces = c->prof_calls[P3T_PH_FORCE];
     o->ngbs = c->prof_calls[P3T_PH_NGB];
+    if (c->built && c->n > 0) {
+        long long cum[3];
+        P3T_CUDA_TRY(cudaMemcpy(cum, c->st->cum_int, sizeof(cum),
+                                cudaMemcpyDeviceToHost));
+        o->int_pc = cum[0];
+        o->int_pp = cum[1];
+        o->int_pp_near = cum[2];
+        if (reset)
+            P3T_CUDA_TRY(cudaMemset(c->st->cum_int, 0, sizeof(cum)));
+    } else {
+        o->int_pc = o->int_pp = o->int_pp_near = 0;
+    }
     if (reset) {
         for (int k = 0; k < P3T_NPH; ++k) {
             c->prof_ms[k] = 0.0;

@@ -10,16 +10,18 @@
 // d = 0 and contribute exactly zero.
 //
 // Layout of the work: one warp per group (groups fetched dynamically), two
-// i-particles per lane (group size <= 64).  Sources are staged 32 at a time
-// in shared memory as group-relative FP32 vectors, (x_hi - c) + x_lo, so that
-// no absolute coordinate enters the FP32 arithmetic; every lane then reads
-// each staged source as a broadcast and applies it to both of its particles.
-// Partial sums of a tile are added into (hi, lo) pairs with an error-free
-// two-sum, so the summation error is that of 32-term FP32 sums.
-//
-// Near pairs also screen for neighbours: r^2 (FP32, group relative) < hs2
-// (the group's screening radius, which bounds the FP32 error) sends the pair
-// to the exact FP64 predicate ((dx*dx + dy*dy) + dz*dz) < h*h.
+// i-particles per lane (group size <= 64).  The warp walks the tree for its
+// group (the same traversal and opening test as the list walk in
+// p3t_walk.cu) and feeds what it finds into three small rings in shared
+// memory: accepted cells, far leaf ranges, near leaf ranges.  Whenever a ring
+// holds 32 sources they are staged in shared memory as group-relative FP32
+// vectors, (x_hi - c) + x_lo, so that no absolute coordinate enters the FP32
+// arithmetic, and every lane applies each staged source (a broadcast read) to
+// both of its particles.  Walking and evaluating in one kernel means the
+// interaction lists never go through HBM and the walk's memory latency hides
+// behind other warps' arithmetic.  Partial sums of a tile are added into
+// (hi, lo) pairs with an error-free two-sum, so the summation error is that
+// of 32-term FP32 sums.
 #include <math.h>
 
 #include "p3t_internal.cuh"
@@ -173,17 +175,6 @@ __device__ double w_over_s(double s, const ForceConsts &k)
     return W / s;
 }
 
-__device__ __forceinline__ bool exact_ngb(const double *__restrict__ xs,
-                                          int n, int ki, int kj, double h2)
-{
-    double dx = __dsub_rn(xs[ki], xs[kj]);
-    double dy = __dsub_rn(xs[(size_t)n + ki], xs[(size_t)n + kj]);
-    double dz = __dsub_rn(xs[2 * (size_t)n + ki], xs[2 * (size_t)n + kj]);
-    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
-                          __dmul_rn(dz, dz));
-    return r2 < h2;
-}
-
 __device__ __forceinline__ float4 rel4(float4 hi, float4 lo, float4 c)
 {
     return make_float4(__fadd_rn(__fsub_rn(hi.x, c.x), lo.x),
@@ -191,267 +182,350 @@ __device__ __forceinline__ float4 rel4(float4 hi, float4 lo, float4 c)
                        __fadd_rn(__fsub_rn(hi.z, c.z), lo.z), hi.w);
 }
 
-template <bool NGB, bool POT>
-__global__ void __launch_bounds__(FW * 32)
-k_force(int G, const int2 *__restrict__ grange,
-        const float4 *__restrict__ gmin, const float4 *__restrict__ gctr,
-        const float4 *__restrict__ phi, const float4 *__restrict__ plo,
-        const float4 *__restrict__ cf0, const float4 *__restrict__ cf1,
-        const float4 *__restrict__ cf2, const long long *__restrict__ off,
-        const int *__restrict__ pc_list, const int *__restrict__ ppn_list,
-        const int *__restrict__ ppf_list, const int *__restrict__ order,
-        const double *__restrict__ xs, int n, ForceConsts k,
-        float *__restrict__ acc, double *__restrict__ pot,
-        int *__restrict__ ngb_cnt, P3TDevState *st)
+
+constexpr int FSTACK = 768;  // walk stack entries per warp (child ranges)
+constexpr int RING = 64;     // ring capacity (entries); never more than 63 used
+
+struct __align__(16) WarpSmem {
+    float4 t0[32], t1[32], t2[32];  // staged sources
+    int stack[FSTACK];              // packed child ranges: child * 8 + nchild-1
+    int cb[32];                     // cells of the current walk batch
+    int pc[RING];                   // accepted cells
+    int2 pf[RING];                  // far leaf ranges (first, count)
+    int2 pn[RING];                  // near leaf ranges
+    int tj[32];                     // sorted ids of staged particles
+};
+
+struct RangeRing {
+    int head, nr, np;  // first entry, ranges held, particles held
+};
+
+// Appends one range per flagged lane to a ring of leaf ranges.
+__device__ __forceinline__ void ring_push_ranges(int2 *ring, RangeRing &r,
+                                                 bool flag, int first,
+                                                 int count, int lane)
 {
-    __shared__ float4 T0[FW][32], T1[FW][32], T2[FW][32];
-    __shared__ int TJ[FW][32];
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if (flag) ring[(r.head + r.nr + __popc(m & lanemask_lt())) & (RING - 1)] =
+        make_int2(first, count);
+    int c = flag ? count : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    r.nr += __popc(m);
+    r.np += c;
+}
+
+// Takes the next `take` (<= 32, <= r.np) particle ids off the front of a
+// ring of ranges into tj[0..take).
+__device__ __forceinline__ void ring_take(int2 *ring, RangeRing &r, int take,
+                                         int *tj, int lane)
+{
+    const bool have = lane < r.nr;
+    int2 g = have ? ring[(r.head + lane) & (RING - 1)] : make_int2(0, 0);
+    int inc = warp_incl_scan(g.y);
+    int exc = inc - g.y;
+    if (have && exc < take) {
+        int stop = min(inc, take);
+        for (int p = exc; p < stop; ++p) tj[p] = g.x + (p - exc);
+    }
+    const unsigned full = __ballot_sync(0xffffffffu, have && inc <= take);
+    const int nfull = __popc(full);
+    // the range straddling the tile boundary keeps its remainder
+    if (lane == nfull && have && exc < take) {
+        int used = take - exc;
+        ring[(r.head + lane) & (RING - 1)] = make_int2(g.x + used, g.y - used);
+    }
+    __syncwarp();
+    r.head = (r.head + nfull) & (RING - 1);
+    r.nr -= nfull;
+    r.np -= take;
+}
+
+template <bool POT>
+struct GroupAcc {
+    Acc3 a0, a1;
+    float ph0, pl0, ph1, pl1;
+};
+
+// One tile of up to 32 accepted cells.
+template <bool POT>
+__device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
+                                          int take, const float4 *cf0,
+                                          const float4 *cf1, const float4 *cf2,
+                                          float4 ct, float4 p0, float4 p1,
+                                          float eps2, GroupAcc<POT> &A, int lane)
+{
+    if (lane < take) {
+        int c = S.pc[(head + lane) & (RING - 1)];
+        float4 a = cf0[c], bb = cf1[c], cc = cf2[c];
+        S.t0[lane] = make_float4(__fadd_rn(__fsub_rn(a.x, ct.x), bb.x),
+                                 __fadd_rn(__fsub_rn(a.y, ct.y), bb.y),
+                                 __fadd_rn(__fsub_rn(a.z, ct.z), bb.z), a.w);
+        S.t1[lane] = make_float4(bb.w, cc.x, -(bb.w + cc.x), cc.y);
+        S.t2[lane] = make_float4(cc.z, cc.w, 0.0f, 0.0f);
+    } else {
+        S.t0[lane] = far_pad();
+        S.t1[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        S.t2[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    head = (head + take) & (RING - 1);
+    n -= take;
+    __syncwarp();
+    float tx0 = 0.f, ty0 = 0.f, tz0 = 0.f, tx1 = 0.f, ty1 = 0.f, tz1 = 0.f,
+          tp0 = 0.f, tp1 = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {
+        const float4 a = S.t0[j], bq = S.t1[j], cq = S.t2[j];
+        pc_term(p0.x, p0.y, p0.z, a, bq, cq, eps2, tx0, ty0, tz0);
+        pc_term(p1.x, p1.y, p1.z, a, bq, cq, eps2, tx1, ty1, tz1);
+        if (POT) {
+            tp0 += pc_pot(p0.x, p0.y, p0.z, a, bq, cq, eps2);
+            tp1 += pc_pot(p1.x, p1.y, p1.z, a, bq, cq, eps2);
+        }
+    }
+    A.a0.add(tx0, ty0, tz0);
+    A.a1.add(tx1, ty1, tz1);
+    if (POT) {
+        two_sum_add(A.ph0, A.pl0, tp0);
+        two_sum_add(A.ph1, A.pl1, tp1);
+    }
+    __syncwarp();
+}
+
+// One tile of up to 32 particles from a ring of leaf ranges.
+template <bool NEAR, bool POT>
+__device__ __forceinline__ void particle_tile(
+    WarpSmem &S, int2 *ring, RangeRing &r, int take, const float4 *phi,
+    const float4 *plo, float4 ct, float4 p0, float4 p1, int k0, int k1,
+    const ForceConsts &k, GroupAcc<POT> &A, int lane)
+{
+    ring_take(ring, r, take, S.tj, lane);
+    if (lane < take) {
+        int j = S.tj[lane];
+        S.t0[lane] = rel4(phi[j], plo[j], ct);
+    } else {
+        S.t0[lane] = far_pad();
+        S.tj[lane] = -1;
+    }
+    __syncwarp();
+    float tx0 = 0.f, ty0 = 0.f, tz0 = 0.f, tx1 = 0.f, ty1 = 0.f, tz1 = 0.f,
+          tp0 = 0.f, tp1 = 0.f;
+    if (NEAR) {
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const float4 a = S.t0[j];
+            float s0, s1;
+            pp_near(p0.x, p0.y, p0.z, a, k, tx0, ty0, tz0, s0);
+            pp_near(p1.x, p1.y, p1.z, a, k, tx1, ty1, tz1, s1);
+            if (POT) {
+                const int kj = S.tj[j];
+                if (kj >= 0 && kj != k0) tp0 -= a.w * (float)w_over_s((double)s0, k);
+                if (kj >= 0 && kj != k1) tp1 -= a.w * (float)w_over_s((double)s1, k);
+            }
+        }
+    } else {
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const float4 a = S.t0[j];
+            pp_far(p0.x, p0.y, p0.z, a, k.eps2, tx0, ty0, tz0);
+            pp_far(p1.x, p1.y, p1.z, a, k.eps2, tx1, ty1, tz1);
+            if (POT) {
+                float dx = a.x - p0.x, dy = a.y - p0.y, dz = a.z - p0.z;
+                tp0 -= a.w * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, k.eps2))));
+                dx = a.x - p1.x; dy = a.y - p1.y; dz = a.z - p1.z;
+                tp1 -= a.w * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, k.eps2))));
+            }
+        }
+    }
+    A.a0.add(tx0, ty0, tz0);
+    A.a1.add(tx1, ty1, tz1);
+    if (POT) {
+        two_sum_add(A.ph0, A.pl0, tp0);
+        two_sum_add(A.ph1, A.pl1, tp1);
+    }
+    __syncwarp();
+}
+
+template <bool POT>
+__global__ void __launch_bounds__(FW * 32)
+k_walk_force(int G, const int2 *__restrict__ grange,
+             const float4 *__restrict__ gmin, const float4 *__restrict__ gmax,
+             const float4 *__restrict__ gctr, const float4 *__restrict__ wmin,
+             const float4 *__restrict__ wmax, const int4 *__restrict__ node,
+             float theta2, float hg2, const float4 *__restrict__ phi,
+             const float4 *__restrict__ plo, const float4 *__restrict__ cf0,
+             const float4 *__restrict__ cf1, const float4 *__restrict__ cf2,
+             const int *__restrict__ order, int n, ForceConsts k,
+             float *__restrict__ acc, double *__restrict__ pot,
+             P3TDevState *st)
+{
+    __shared__ WarpSmem smem[FW];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float eps2 = k.eps2;
+    const unsigned full = 0xffffffffu, lt = lanemask_lt();
+    WarpSmem &S = smem[w];
     for (;;) {
         int g = 0;
         if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
-        g = __shfl_sync(0xffffffffu, g, 0);
+        g = __shfl_sync(full, g, 0);
         if (g >= G) break;
         const int2 gr = grange[g];
         const float4 ct = gctr[g];
-        const float hs2 = gmin[g].w;
+        const float4 gmn = gmin[g], gmx = gmax[g];
         const int k0 = gr.x + lane, k1 = gr.x + 32 + lane;
         const bool v0 = lane < gr.y, v1 = lane + 32 < gr.y;
         const float4 p0 = v0 ? rel4(phi[k0], plo[k0], ct) : far_pad();
         const float4 p1 = v1 ? rel4(phi[k1], plo[k1], ct) : far_pad();
-        Acc3 A0, A1;
-        A0.zero();
-        A1.zero();
-        float ph0 = 0.f, pl0 = 0.f, ph1 = 0.f, pl1 = 0.f;
-        int nc0 = 0, nc1 = 0;
+        GroupAcc<POT> A;
+        A.a0.zero();
+        A.a1.zero();
+        A.ph0 = A.pl0 = A.ph1 = A.pl1 = 0.f;
+        int pc_head = 0, pc_n = 0;
+        RangeRing rf = {0, 0, 0}, rn = {0, 0, 0};
+        long long cnt_pc = 0, cnt_pn = 0, cnt_pf = 0;
 
-        // ---- cells ----
-        {
-            const long long b = off[g], e = off[g + 1];
-            for (long long t = b; t < e; t += 32) {
-                const long long q = t + lane;
-                if (q < e) {
-                    int c = pc_list[q];
-                    float4 a = cf0[c], bb = cf1[c], cc = cf2[c];
-                    T0[w][lane] = make_float4(__fadd_rn(__fsub_rn(a.x, ct.x), bb.x),
-                                              __fadd_rn(__fsub_rn(a.y, ct.y), bb.y),
-                                              __fadd_rn(__fsub_rn(a.z, ct.z), bb.z),
-                                              a.w);
-                    T1[w][lane] = make_float4(bb.w, cc.x, -(bb.w + cc.x), cc.y);
-                    T2[w][lane] = make_float4(cc.z, cc.w, 0.0f, 0.0f);
+        if (lane == 0) S.stack[0] = 0;  // the root: child 0, one cell
+        int top = 1;
+        int iter = 0;
+        bool overflow = false;
+        __syncwarp();
+        while (top > 0) {
+            if (++iter > (1 << 24)) {  // a finite tree never gets here
+                overflow = true;
+                break;
+            }
+            // pop child ranges from the top holding at most 32 cells
+            int rx = 0, ry = 0;
+            if (lane < top) {
+                int e = S.stack[top - 1 - lane];
+                rx = e >> 3;
+                ry = (e & 7) + 1;
+            }
+            int inc = warp_incl_scan(ry);
+            bool take = lane < top && inc <= 32;
+            int ntake = __popc(__ballot_sync(full, take));
+            int total = __shfl_sync(full, inc, ntake - 1);
+            if (take)
+                for (int t = 0; t < ry; ++t) S.cb[inc - ry + t] = rx + t;
+            top -= ntake;
+            __syncwarp();
+            const int c = lane < total ? S.cb[lane] : -1;
+            __syncwarp();
+
+            bool is_pc = false, near = false, farl = false, open = false;
+            int child = 0, nchild = 0, pfirst = 0, pcount = 0;
+            if (c >= 0) {
+                const float4 cmn = wmin[c], cmx = wmax[c];
+                float d2 = box_d2(gmn, gmx, cmn, cmx);
+                float l = box_side(cmn, cmx);
+                if (mac_accept(d2, l, theta2, hg2)) {
+                    is_pc = true;
                 } else {
-                    T0[w][lane] = far_pad();
-                    T1[w][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    T2[w][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-                __syncwarp();
-                float tx0 = 0.f, ty0 = 0.f, tz0 = 0.f, tx1 = 0.f, ty1 = 0.f,
-                      tz1 = 0.f, tp0 = 0.f, tp1 = 0.f;
-#pragma unroll 8
-                for (int j = 0; j < 32; ++j) {
-                    const float4 a = T0[w][j], bq = T1[w][j], cq = T2[w][j];
-                    pc_term(p0.x, p0.y, p0.z, a, bq, cq, eps2, tx0, ty0, tz0);
-                    pc_term(p1.x, p1.y, p1.z, a, bq, cq, eps2, tx1, ty1, tz1);
-                    if (POT) {
-                        tp0 += pc_pot(p0.x, p0.y, p0.z, a, bq, cq, eps2);
-                        tp1 += pc_pot(p1.x, p1.y, p1.z, a, bq, cq, eps2);
+                    child = __float_as_int(cmn.w);
+                    nchild = __float_as_int(cmx.w);
+                    if (nchild == 0) {
+                        int4 nd = node[c];
+                        pfirst = nd.x;
+                        pcount = nd.y;
+                        near = d2 <= hg2;
+                        farl = !near;
+                    } else {
+                        open = true;
                     }
                 }
-                A0.add(tx0, ty0, tz0);
-                A1.add(tx1, ty1, tz1);
-                if (POT) {
-                    two_sum_add(ph0, pl0, tp0);
-                    two_sum_add(ph1, pl1, tp1);
-                }
-                __syncwarp();
             }
-        }
-        // ---- far particles ----
-        {
-            const long long b = off[2 * (G + 1) + g], e = off[2 * (G + 1) + g + 1];
-            for (long long t = b; t < e; t += 32) {
-                const long long q = t + lane;
-                if (q < e) {
-                    int j = ppf_list[q];
-                    T0[w][lane] = rel4(phi[j], plo[j], ct);
-                } else {
-                    T0[w][lane] = far_pad();
-                }
-                __syncwarp();
-                float tx0 = 0.f, ty0 = 0.f, tz0 = 0.f, tx1 = 0.f, ty1 = 0.f,
-                      tz1 = 0.f, tp0 = 0.f, tp1 = 0.f;
-#pragma unroll 8
-                for (int j = 0; j < 32; ++j) {
-                    const float4 a = T0[w][j];
-                    pp_far(p0.x, p0.y, p0.z, a, eps2, tx0, ty0, tz0);
-                    pp_far(p1.x, p1.y, p1.z, a, eps2, tx1, ty1, tz1);
-                    if (POT) {
-                        float dx = a.x - p0.x, dy = a.y - p0.y, dz = a.z - p0.z;
-                        tp0 -= a.w * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2))));
-                        dx = a.x - p1.x; dy = a.y - p1.y; dz = a.z - p1.z;
-                        tp1 -= a.w * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2))));
-                    }
-                }
-                A0.add(tx0, ty0, tz0);
-                A1.add(tx1, ty1, tz1);
-                if (POT) {
-                    two_sum_add(ph0, pl0, tp0);
-                    two_sum_add(ph1, pl1, tp1);
-                }
-                __syncwarp();
+            // accepted cells -> cell ring
+            {
+                unsigned m = __ballot_sync(full, is_pc);
+                if (is_pc) S.pc[(pc_head + pc_n + __popc(m & lt)) & (RING - 1)] = c;
+                pc_n += __popc(m);
+                cnt_pc += __popc(m);
             }
-        }
-        // ---- near particles (cut-off K, neighbour screening) ----
-        {
-            const long long b = off[(G + 1) + g], e = off[(G + 1) + g + 1];
-            for (long long t = b; t < e; t += 32) {
-                const long long q = t + lane;
-                if (q < e) {
-                    int j = ppn_list[q];
-                    T0[w][lane] = rel4(phi[j], plo[j], ct);
-                    TJ[w][lane] = j;
-                } else {
-                    T0[w][lane] = far_pad();
-                    TJ[w][lane] = -1;
-                }
-                __syncwarp();
-                float tx0 = 0.f, ty0 = 0.f, tz0 = 0.f, tx1 = 0.f, ty1 = 0.f,
-                      tz1 = 0.f, tp0 = 0.f, tp1 = 0.f;
-#pragma unroll 4
-                for (int j = 0; j < 32; ++j) {
-                    const float4 a = T0[w][j];
-                    float s0, s1;
-                    float r20 = pp_near(p0.x, p0.y, p0.z, a, k, tx0, ty0, tz0, s0);
-                    float r21 = pp_near(p1.x, p1.y, p1.z, a, k, tx1, ty1, tz1, s1);
-                    if (NGB || POT) {
-                        const int kj = TJ[w][j];
-                        if (NGB) {
-                            if (r20 < hs2 && v0 && kj >= 0 && kj != k0)
-                                nc0 += exact_ngb(xs, n, k0, kj, k.h2);
-                            if (r21 < hs2 && v1 && kj >= 0 && kj != k1)
-                                nc1 += exact_ngb(xs, n, k1, kj, k.h2);
-                        }
-                        if (POT) {
-                            if (kj >= 0 && kj != k0)
-                                tp0 -= a.w * (float)w_over_s((double)s0, k);
-                            if (kj >= 0 && kj != k1)
-                                tp1 -= a.w * (float)w_over_s((double)s1, k);
-                        }
-                    }
-                }
-                A0.add(tx0, ty0, tz0);
-                A1.add(tx1, ty1, tz1);
-                if (POT) {
-                    two_sum_add(ph0, pl0, tp0);
-                    two_sum_add(ph1, pl1, tp1);
-                }
-                __syncwarp();
+            // leaves -> particle rings
+            {
+                int before = rn.np;
+                ring_push_ranges(S.pn, rn, near, pfirst, pcount, lane);
+                cnt_pn += rn.np - before;
+                before = rf.np;
+                ring_push_ranges(S.pf, rf, farl, pfirst, pcount, lane);
+                cnt_pf += rf.np - before;
             }
+            // opened cells -> stack
+            {
+                unsigned mo = __ballot_sync(full, open);
+                int np = __popc(mo);
+                if (top + np > FSTACK) {
+                    overflow = true;
+                    break;
+                }
+                if (open) S.stack[top + __popc(mo & lt)] = child * 8 + (nchild - 1);
+                top += np;
+            }
+            __syncwarp();
+            // evaluate every full tile
+            while (pc_n >= 32)
+                cell_tile<POT>(S, pc_head, pc_n, 32, cf0, cf1, cf2, ct, p0, p1,
+                               k.eps2, A, lane);
+            while (rf.np >= 32)
+                particle_tile<false, POT>(S, S.pf, rf, 32, phi, plo, ct, p0, p1,
+                                          k0, k1, k, A, lane);
+            while (rn.np >= 32)
+                particle_tile<true, POT>(S, S.pn, rn, 32, phi, plo, ct, p0, p1,
+                                         k0, k1, k, A, lane);
         }
+        if (overflow) {
+            if (lane == 0) p3t_raise(st, P3T_ERR_CAPACITY);
+            continue;
+        }
+        // the partial tiles left over
+        if (pc_n > 0)
+            cell_tile<POT>(S, pc_head, pc_n, pc_n, cf0, cf1, cf2, ct, p0, p1,
+                           k.eps2, A, lane);
+        if (rf.np > 0)
+            particle_tile<false, POT>(S, S.pf, rf, rf.np, phi, plo, ct, p0, p1,
+                                      k0, k1, k, A, lane);
+        if (rn.np > 0)
+            particle_tile<true, POT>(S, S.pn, rn, rn.np, phi, plo, ct, p0, p1,
+                                     k0, k1, k, A, lane);
         // ---- write back in the caller's order ----
         const float Gc = k.G;
         if (v0) {
             int o = order[k0];
-            acc[o] = Gc * (A0.hx + A0.lx);
-            acc[(size_t)n + o] = Gc * (A0.hy + A0.ly);
-            acc[2 * (size_t)n + o] = Gc * (A0.hz + A0.lz);
-            if (POT) pot[o] = (double)Gc * ((double)ph0 + (double)pl0);
-            if (NGB) ngb_cnt[o] = nc0;
+            acc[o] = Gc * (A.a0.hx + A.a0.lx);
+            acc[(size_t)n + o] = Gc * (A.a0.hy + A.a0.ly);
+            acc[2 * (size_t)n + o] = Gc * (A.a0.hz + A.a0.lz);
+            if (POT) pot[o] = (double)Gc * ((double)A.ph0 + (double)A.pl0);
         }
         if (v1) {
             int o = order[k1];
-            acc[o] = Gc * (A1.hx + A1.lx);
-            acc[(size_t)n + o] = Gc * (A1.hy + A1.ly);
-            acc[2 * (size_t)n + o] = Gc * (A1.hz + A1.lz);
-            if (POT) pot[o] = (double)Gc * ((double)ph1 + (double)pl1);
-            if (NGB) ngb_cnt[o] = nc1;
+            acc[o] = Gc * (A.a1.hx + A.a1.lx);
+            acc[(size_t)n + o] = Gc * (A.a1.hy + A.a1.ly);
+            acc[2 * (size_t)n + o] = Gc * (A.a1.hz + A.a1.lz);
+            if (POT) pot[o] = (double)Gc * ((double)A.ph1 + (double)A.pl1);
+        }
+        if (lane == 0) {
+            const long long m = gr.y;
+            atomicAdd((unsigned long long *)&st->tot[0], (unsigned long long)cnt_pc);
+            atomicAdd((unsigned long long *)&st->tot[1], (unsigned long long)cnt_pn);
+            atomicAdd((unsigned long long *)&st->tot[2], (unsigned long long)cnt_pf);
+            atomicAdd((unsigned long long *)&st->int_pc, (unsigned long long)(m * cnt_pc));
+            atomicAdd((unsigned long long *)&st->int_pp,
+                      (unsigned long long)(m * (cnt_pn + cnt_pf)));
+            atomicAdd((unsigned long long *)&st->int_ppn, (unsigned long long)(m * cnt_pn));
+            atomicAdd((unsigned long long *)&st->cum_int[0], (unsigned long long)(m * cnt_pc));
+            atomicAdd((unsigned long long *)&st->cum_int[1],
+                      (unsigned long long)(m * (cnt_pn + cnt_pf)));
+            atomicAdd((unsigned long long *)&st->cum_int[2], (unsigned long long)(m * cnt_pn));
         }
     }
 }
 
-// Neighbour fill: the near lists again, writing original indices of the
-// exact neighbours of each particle into its CSR row (unsorted).
-__global__ void __launch_bounds__(FW * 32)
-k_ngb_fill(int G, const int2 *__restrict__ grange,
-           const float4 *__restrict__ gmin, const float4 *__restrict__ gctr,
-           const float4 *__restrict__ phi, const float4 *__restrict__ plo,
-           const long long *__restrict__ off, const int *__restrict__ ppn_list,
-           const int *__restrict__ order, const double *__restrict__ xs,
-           int n, double h2, const long long *__restrict__ row_off,
-           int *__restrict__ idx, long long cap, P3TDevState *st)
+// Resets the per-call counters of a force evaluation.
+__global__ void k_force_reset(P3TDevState *st)
 {
-    __shared__ float4 T0[FW][32];
-    __shared__ int TJ[FW][32];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (;;) {
-        int g = 0;
-        if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= G) break;
-        const int2 gr = grange[g];
-        const float4 ct = gctr[g];
-        const float hs2 = gmin[g].w;
-        const int k0 = gr.x + lane, k1 = gr.x + 32 + lane;
-        const bool v0 = lane < gr.y, v1 = lane + 32 < gr.y;
-        const float4 p0 = v0 ? rel4(phi[k0], plo[k0], ct) : far_pad();
-        const float4 p1 = v1 ? rel4(phi[k1], plo[k1], ct) : far_pad();
-        long long w0 = v0 ? row_off[order[k0]] : 0;
-        long long w1 = v1 ? row_off[order[k1]] : 0;
-        const long long b = off[(G + 1) + g], e = off[(G + 1) + g + 1];
-        for (long long t = b; t < e; t += 32) {
-            const long long q = t + lane;
-            if (q < e) {
-                int j = ppn_list[q];
-                T0[w][lane] = rel4(phi[j], plo[j], ct);
-                TJ[w][lane] = j;
-            } else {
-                T0[w][lane] = far_pad();
-                TJ[w][lane] = -1;
-            }
-            __syncwarp();
-            for (int j = 0; j < 32; ++j) {
-                const float4 a = T0[w][j];
-                const int kj = TJ[w][j];
-                float dx = a.x - p0.x, dy = a.y - p0.y, dz = a.z - p0.z;
-                float r20 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                dx = a.x - p1.x; dy = a.y - p1.y; dz = a.z - p1.z;
-                float r21 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (r20 < hs2 && v0 && kj >= 0 && kj != k0 &&
-                    exact_ngb(xs, n, k0, kj, h2)) {
-                    if (w0 < cap) idx[w0] = order[kj];
-                    else p3t_raise(st, P3T_ERR_CAPACITY);
-                    ++w0;
-                }
-                if (r21 < hs2 && v1 && kj >= 0 && kj != k1 &&
-                    exact_ngb(xs, n, k1, kj, h2)) {
-                    if (w1 < cap) idx[w1] = order[kj];
-                    else p3t_raise(st, P3T_ERR_CAPACITY);
-                    ++w1;
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
-// Sorts each CSR row ascending (rows are short: insertion sort per thread).
-__global__ void k_ngb_sort(int n, const long long *__restrict__ row_off,
-                           int *__restrict__ idx, long long cap)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += gridDim.x * blockDim.x) {
-        long long b = row_off[i], e = row_off[i + 1];
-        if (e > cap) continue;
-        for (long long a = b + 1; a < e; ++a) {
-            int v = idx[a];
-            long long q = a - 1;
-            while (q >= b && idx[q] > v) {
-                idx[q + 1] = idx[q];
-                --q;
-            }
-            idx[q + 1] = v;
-        }
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        st->work = 0;
+        st->tot[0] = st->tot[1] = st->tot[2] = 0;
+        st->int_pc = st->int_pp = st->int_ppn = 0;
     }
 }
 
@@ -479,59 +553,31 @@ ForceConsts make_consts(const p3t_params &p)
     return k;
 }
 
-int force_blocks(const p3t_ctx *c, int G)
-{
-    int blocks = (G + FW - 1) / FW;
-    int maxb = c->sms * 16;
-    return blocks < maxb ? blocks : maxb;
-}
-
 }  // namespace
 
 int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s)
 {
     const int G = c->hst->ngroup;
     const int n = (int)c->n;
+    k_force_reset<<<1, 32, 0, s>>>(c->st);
+    p3t_count_launches(1);
     if (G == 0) return P3T_OK;
     ForceConsts k = make_consts(c->p);
-    const bool ngb = (c->p.flags & P3T_FLAG_NEIGHBOURS) != 0;
-    P3T_CUDA_TRY(cudaMemsetAsync(&c->st->work, 0, sizeof(unsigned), s));
-    const int blocks = force_blocks(c, G);
-#define P3T_LAUNCH_FORCE(NG, PT)                                             \
-    k_force<NG, PT><<<blocks, FW * 32, 0, s>>>(                              \
-        G, c->grange, c->gmin, c->gctr, c->phi, c->plo, c->cf0, c->cf1,      \
-        c->cf2, c->loff, c->list[0], c->list[1], c->list[2], c->order,       \
-        c->xs, n, k, acc, pot, c->ngb_cnt, c->st)
-    if (ngb && pot)
-        P3T_LAUNCH_FORCE(true, true);
-    else if (ngb)
-        P3T_LAUNCH_FORCE(true, false);
-    else if (pot)
-        P3T_LAUNCH_FORCE(false, true);
+    float theta2, hg2;
+    p3t_mac_constants(&c->p, &theta2, &hg2);
+    int blocks = (G + FW - 1) / FW;
+    if (blocks > c->sms * 16) blocks = c->sms * 16;
+    if (pot)
+        k_walk_force<true><<<blocks, FW * 32, 0, s>>>(
+            G, c->grange, c->gmin, c->gmax, c->gctr, c->wmin, c->wmax, c->node,
+            theta2, hg2, c->phi, c->plo, c->cf0, c->cf1, c->cf2, c->order, n, k,
+            acc, pot, c->st);
     else
-        P3T_LAUNCH_FORCE(false, false);
-#undef P3T_LAUNCH_FORCE
+        k_walk_force<false><<<blocks, FW * 32, 0, s>>>(
+            G, c->grange, c->gmin, c->gmax, c->gctr, c->wmin, c->wmax, c->node,
+            theta2, hg2, c->phi, c->plo, c->cf0, c->cf1, c->cf2, c->order, n, k,
+            acc, pot, c->st);
     p3t_count_launches(1);
-    P3T_CUDA_TRY(cudaGetLastError());
-    return P3T_OK;
-}
-
-int p3t_run_ngb_fill(p3t_ctx *c, const long long *row_off, int *idx,
-                     long long cap, cudaStream_t s)
-{
-    const int G = c->hst->ngroup;
-    const int n = (int)c->n;
-    if (G == 0) return P3T_OK;
-    double h = c->p.h > 0.0 ? c->p.h : c->p.r_out;
-    P3T_CUDA_TRY(cudaMemsetAsync(&c->st->work, 0, sizeof(unsigned), s));
-    k_ngb_fill<<<force_blocks(c, G), FW * 32, 0, s>>>(
-        G, c->grange, c->gmin, c->gctr, c->phi, c->plo, c->loff, c->list[1],
-        c->order, c->xs, n, h * h, row_off, idx, cap, c->st);
-    int nb = (n + 255) / 256;
-    if (nb > c->sms * 8) nb = c->sms * 8;
-    if (nb < 1) nb = 1;
-    k_ngb_sort<<<nb, 256, 0, s>>>(n, row_off, idx, cap);
-    p3t_count_launches(2);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
 }

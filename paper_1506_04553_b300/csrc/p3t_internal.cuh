@@ -43,6 +43,9 @@ struct P3TDevState {
     long long int_pp;   // particle-particle interactions
     long long int_ppn;  // of which near-list interactions
     long long nnz;      // neighbour pairs
+    long long cum_int[3];  // pc, pp, pp-near interactions since profile reset
+    int max_stack;      // deepest walk stack seen (ranges)
+    int pad1;
 };
 
 // Phase timing with CUDA events (resolved lazily at p3t_get_profile).
@@ -61,7 +64,8 @@ struct p3t_ctx {
     int64_t cap_n, cap_cells, cap_groups, cap_list[3], cap_scan;
     int64_t n;
     int built;         // a tree exists
-    int forced_ngb;    // last force evaluation counted neighbours
+    int lists_valid;   // inspection lists match the current tree
+    int64_t list_tot[3];
     // device state
     P3TDevState *st;
     P3TDevState *hst;  // pinned host mirror
@@ -145,6 +149,34 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return (1u << (threadIdx.x & 31)) - 1u;
 }
 
+// ---- opening test (identical in every walk) ----
+// Squared gap between two FP32 boxes, one rounding per operation, no FMA.
+__device__ __forceinline__ float box_d2(float4 gmn, float4 gmx, float4 cmn,
+                                        float4 cmx)
+{
+    float gx = fmaxf(fmaxf(__fsub_rn(cmn.x, gmx.x), __fsub_rn(gmn.x, cmx.x)), 0.0f);
+    float gy = fmaxf(fmaxf(__fsub_rn(cmn.y, gmx.y), __fsub_rn(gmn.y, cmx.y)), 0.0f);
+    float gz = fmaxf(fmaxf(__fsub_rn(cmn.z, gmx.z), __fsub_rn(gmn.z, cmx.z)), 0.0f);
+    float s = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
+    return __fadd_rn(s, __fmul_rn(gz, gz));
+}
+
+// Largest side of an FP32 box.
+__device__ __forceinline__ float box_side(float4 cmn, float4 cmx)
+{
+    float lx = __fsub_rn(cmx.x, cmn.x);
+    float ly = __fsub_rn(cmx.y, cmn.y);
+    float lz = __fsub_rn(cmx.z, cmn.z);
+    return fmaxf(fmaxf(lx, ly), lz);
+}
+
+// Cell c is accepted for a group iff l*l < theta2*d2 and d2 > hg2.
+__device__ __forceinline__ bool mac_accept(float d2, float l, float theta2,
+                                           float hg2)
+{
+    return __fmul_rn(l, l) < __fmul_rn(theta2, d2) && d2 > hg2;
+}
+
 // ---- kernel-launch helpers implemented in the .cu files ----
 int p3t_sort_keys(p3t_ctx *c, int n, cudaStream_t s);          // p3t_sort.cu
 int p3t_scan_ll(p3t_ctx *c, const int *in, long long *out, int n,
@@ -154,8 +186,8 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
 int p3t_run_walk(p3t_ctx *c, int fill, cudaStream_t s);        // p3t_walk.cu
 int p3t_scan_lists(p3t_ctx *c, cudaStream_t s);                 // p3t_walk.cu
 int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s);   // p3t_force.cu
-int p3t_run_ngb_fill(p3t_ctx *c, const long long *off, int *idx,
-                     long long cap, cudaStream_t s);             // p3t_force.cu
+int p3t_run_ngb(p3t_ctx *c, int fill, const long long *row_off, int *idx,
+                long long cap, cudaStream_t s);                  // p3t_ngb.cu
 int p3t_energy_launch(p3t_ctx *c, int n, const double *mass,
                       const double *vel, const double *pot, double *out,
                       cudaStream_t s);                           // p3t_misc.cu

@@ -1,0 +1,291 @@
+// Neighbour lists (Sect. 2.2: for every particle, the particles within a
+// distance h; h = r_cut + dr_buff).
+//
+// j is a neighbour of i iff j != i and ((dx*dx + dy*dy) + dz*dz) < h*h in
+// FP64 with dx = x_i - x_j.  Every such pair lies in a leaf whose member box
+// is within the guard distance of the group's box (the opening test never
+// accepts a cell closer than max(h, r_cut), and the guard box distance of an
+// ancestor never exceeds that of its descendants), so a walk that opens only
+// cells with d2 <= hg2 meets every candidate.  Pairs are screened in FP32
+// with group-relative coordinates against the group's radius hs2, which
+// exceeds h^2 by more than the FP32 error of r^2, and the survivors are
+// decided by the FP64 predicate above: the result is exact.
+//
+// Two passes over the same walk: counts per particle (scanned into CSR
+// offsets), then the fill; rows are sorted by original index afterwards.
+#include "p3t_internal.cuh"
+
+namespace {
+
+constexpr int NW = 4;        // warps per block
+constexpr int NSTACK = 768;  // walk stack entries per warp
+constexpr int NRING = 64;
+
+__device__ __forceinline__ bool exact_ngb(const double *__restrict__ xs,
+                                          int n, int ki, int kj, double h2)
+{
+    double dx = __dsub_rn(xs[ki], xs[kj]);
+    double dy = __dsub_rn(xs[(size_t)n + ki], xs[(size_t)n + kj]);
+    double dz = __dsub_rn(xs[2 * (size_t)n + ki], xs[2 * (size_t)n + kj]);
+    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                          __dmul_rn(dz, dz));
+    return r2 < h2;
+}
+
+__device__ __forceinline__ float4 rel4n(float4 hi, float4 lo, float4 c)
+{
+    return make_float4(__fadd_rn(__fsub_rn(hi.x, c.x), lo.x),
+                       __fadd_rn(__fsub_rn(hi.y, c.y), lo.y),
+                       __fadd_rn(__fsub_rn(hi.z, c.z), lo.z), hi.w);
+}
+
+struct __align__(16) NgbSmem {
+    float4 t0[32];
+    int tj[32];
+    int stack[NSTACK];
+    int cb[32];
+    int2 ring[NRING];
+};
+
+// Screens the staged tile against the lane's two particles.
+template <bool FILL>
+__device__ __forceinline__ void ngb_tile(NgbSmem &S, float4 p0, float4 p1,
+                                         bool v0, bool v1, int k0, int k1,
+                                         float hs2, const double *xs, int n,
+                                         double h2, const int *order,
+                                         int &c0, int &c1, long long &w0,
+                                         long long &w1, int *idx,
+                                         long long cap, P3TDevState *st)
+{
+    for (int j = 0; j < 32; ++j) {
+        const float4 a = S.t0[j];
+        const int kj = S.tj[j];
+        float dx = a.x - p0.x, dy = a.y - p0.y, dz = a.z - p0.z;
+        float r20 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        dx = a.x - p1.x; dy = a.y - p1.y; dz = a.z - p1.z;
+        float r21 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (r20 < hs2 && v0 && kj >= 0 && kj != k0 && exact_ngb(xs, n, k0, kj, h2)) {
+            if (FILL) {
+                if (w0 < cap) idx[w0] = order[kj];
+                else p3t_raise(st, P3T_ERR_CAPACITY);
+                ++w0;
+            }
+            ++c0;
+        }
+        if (r21 < hs2 && v1 && kj >= 0 && kj != k1 && exact_ngb(xs, n, k1, kj, h2)) {
+            if (FILL) {
+                if (w1 < cap) idx[w1] = order[kj];
+                else p3t_raise(st, P3T_ERR_CAPACITY);
+                ++w1;
+            }
+            ++c1;
+        }
+    }
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(NW * 32)
+k_ngb_walk(int G, const int2 *__restrict__ grange,
+           const float4 *__restrict__ gmin, const float4 *__restrict__ gmax,
+           const float4 *__restrict__ gctr, const float4 *__restrict__ wmin,
+           const float4 *__restrict__ wmax, const int4 *__restrict__ node,
+           float hg2, const float4 *__restrict__ phi,
+           const float4 *__restrict__ plo, const int *__restrict__ order,
+           const double *__restrict__ xs, int n, double h2,
+           int *__restrict__ cnt, const long long *__restrict__ row_off,
+           int *__restrict__ idx, long long cap, P3TDevState *st)
+{
+    __shared__ NgbSmem smem[NW];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu, lt = lanemask_lt();
+    NgbSmem &S = smem[w];
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
+        g = __shfl_sync(full, g, 0);
+        if (g >= G) break;
+        const int2 gr = grange[g];
+        const float4 ct = gctr[g];
+        const float4 gmn = gmin[g], gmx = gmax[g];
+        const float hs2 = gmn.w;
+        const int k0 = gr.x + lane, k1 = gr.x + 32 + lane;
+        const bool v0 = lane < gr.y, v1 = lane + 32 < gr.y;
+        const float4 p0 = v0 ? rel4n(phi[k0], plo[k0], ct) : make_float4(1e15f, 1e15f, 1e15f, 0.f);
+        const float4 p1 = v1 ? rel4n(phi[k1], plo[k1], ct) : make_float4(1e15f, 1e15f, 1e15f, 0.f);
+        int c0 = 0, c1 = 0;
+        long long w0 = 0, w1 = 0;
+        if (FILL) {
+            if (v0) w0 = row_off[order[k0]];
+            if (v1) w1 = row_off[order[k1]];
+        }
+        int head = 0, nr = 0, np = 0;  // ring of near leaf ranges
+        if (lane == 0) S.stack[0] = 0;
+        int top = 1, iter = 0;
+        bool bad = false;
+        __syncwarp();
+        for (;;) {
+            // drain full tiles (and everything once the walk is done)
+            while (np >= 32 || (top == 0 && np > 0)) {
+                const int take = min(np, 32);
+                const bool have = lane < nr;
+                int2 r = have ? S.ring[(head + lane) & (NRING - 1)] : make_int2(0, 0);
+                int inc = warp_incl_scan(r.y);
+                int exc = inc - r.y;
+                if (have && exc < take) {
+                    int stop = min(inc, take);
+                    for (int q = exc; q < stop; ++q) S.tj[q] = r.x + (q - exc);
+                }
+                const int nfull = __popc(__ballot_sync(full, have && inc <= take));
+                if (lane == nfull && have && exc < take) {
+                    int used = take - exc;
+                    S.ring[(head + lane) & (NRING - 1)] = make_int2(r.x + used, r.y - used);
+                }
+                __syncwarp();
+                head = (head + nfull) & (NRING - 1);
+                nr -= nfull;
+                np -= take;
+                if (lane < take) {
+                    int j = S.tj[lane];
+                    S.t0[lane] = rel4n(phi[j], plo[j], ct);
+                } else {
+                    S.t0[lane] = make_float4(1e15f, 1e15f, 1e15f, 0.f);
+                    S.tj[lane] = -1;
+                }
+                __syncwarp();
+                ngb_tile<FILL>(S, p0, p1, v0, v1, k0, k1, hs2, xs, n, h2, order,
+                               c0, c1, w0, w1, idx, cap, st);
+                __syncwarp();
+            }
+            if (top == 0) break;
+            if (++iter > (1 << 24)) {
+                bad = true;
+                break;
+            }
+            int rx = 0, ry = 0;
+            if (lane < top) {
+                int e = S.stack[top - 1 - lane];
+                rx = e >> 3;
+                ry = (e & 7) + 1;
+            }
+            int inc = warp_incl_scan(ry);
+            bool take = lane < top && inc <= 32;
+            int ntake = __popc(__ballot_sync(full, take));
+            int total = __shfl_sync(full, inc, ntake - 1);
+            if (take)
+                for (int t = 0; t < ry; ++t) S.cb[inc - ry + t] = rx + t;
+            top -= ntake;
+            __syncwarp();
+            const int c = lane < total ? S.cb[lane] : -1;
+            __syncwarp();
+            bool near = false, open = false;
+            int child = 0, nchild = 0, pfirst = 0, pcount = 0;
+            if (c >= 0) {
+                const float4 cmn = wmin[c], cmx = wmax[c];
+                if (box_d2(gmn, gmx, cmn, cmx) <= hg2) {
+                    child = __float_as_int(cmn.w);
+                    nchild = __float_as_int(cmx.w);
+                    if (nchild == 0) {
+                        int4 nd = node[c];
+                        pfirst = nd.x;
+                        pcount = nd.y;
+                        near = true;
+                    } else {
+                        open = true;
+                    }
+                }
+            }
+            {
+                unsigned m = __ballot_sync(full, near);
+                if (near)
+                    S.ring[(head + nr + __popc(m & lt)) & (NRING - 1)] =
+                        make_int2(pfirst, pcount);
+                int x = near ? pcount : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(full, x, o);
+                nr += __popc(m);
+                np += x;
+            }
+            {
+                unsigned mo = __ballot_sync(full, open);
+                int q = __popc(mo);
+                if (top + q > NSTACK) {
+                    bad = true;
+                    break;
+                }
+                if (open) S.stack[top + __popc(mo & lt)] = child * 8 + (nchild - 1);
+                top += q;
+            }
+            __syncwarp();
+        }
+        if (bad) {
+            if (lane == 0) p3t_raise(st, P3T_ERR_CAPACITY);
+            continue;
+        }
+        if (!FILL) {
+            if (v0) cnt[order[k0]] = c0;
+            if (v1) cnt[order[k1]] = c1;
+        }
+    }
+}
+
+// Sorts each CSR row ascending (rows are short: insertion sort per thread).
+__global__ void k_ngb_sort(int n, const long long *__restrict__ row_off,
+                           int *__restrict__ idx, long long cap)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += gridDim.x * blockDim.x) {
+        long long b = row_off[i], e = row_off[i + 1];
+        if (e > cap) continue;
+        for (long long a = b + 1; a < e; ++a) {
+            int v = idx[a];
+            long long q = a - 1;
+            while (q >= b && idx[q] > v) {
+                idx[q + 1] = idx[q];
+                --q;
+            }
+            idx[q + 1] = v;
+        }
+    }
+}
+
+__global__ void k_work_reset(P3TDevState *st)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) st->work = 0;
+}
+
+}  // namespace
+
+// fill == 0: per-particle counts into c->ngb_cnt; fill == 1: CSR rows.
+int p3t_run_ngb(p3t_ctx *c, int fill, const long long *row_off, int *idx,
+                long long cap, cudaStream_t s)
+{
+    const int G = c->hst->ngroup;
+    const int n = (int)c->n;
+    if (G == 0) return P3T_OK;
+    float theta2, hg2;
+    p3t_mac_constants(&c->p, &theta2, &hg2);
+    double h = c->p.h > 0.0 ? c->p.h : c->p.r_out;
+    int blocks = (G + NW - 1) / NW;
+    if (blocks > c->sms * 16) blocks = c->sms * 16;
+    k_work_reset<<<1, 32, 0, s>>>(c->st);
+    if (fill)
+        k_ngb_walk<true><<<blocks, NW * 32, 0, s>>>(
+            G, c->grange, c->gmin, c->gmax, c->gctr, c->wmin, c->wmax, c->node,
+            hg2, c->phi, c->plo, c->order, c->xs, n, h * h, c->ngb_cnt,
+            row_off, idx, cap, c->st);
+    else
+        k_ngb_walk<false><<<blocks, NW * 32, 0, s>>>(
+            G, c->grange, c->gmin, c->gmax, c->gctr, c->wmin, c->wmax, c->node,
+            hg2, c->phi, c->plo, c->order, c->xs, n, h * h, c->ngb_cnt,
+            row_off, idx, cap, c->st);
+    p3t_count_launches(2);
+    if (fill) {
+        int nb = (n + 255) / 256;
+        if (nb > c->sms * 8) nb = c->sms * 8;
+        if (nb < 1) nb = 1;
+        k_ngb_sort<<<nb, 256, 0, s>>>(n, row_off, idx, cap);
+        p3t_count_launches(1);
+    }
+    P3T_CUDA_TRY(cudaGetLastError());
+    return P3T_OK;
+}

@@ -76,25 +76,41 @@ k_bbox_partial(int n, const double *__restrict__ pos,
     }
 }
 
-__global__ void k_bbox_final(int nblk, const double *__restrict__ part,
-                             P3TDevState *st)
+__global__ void __launch_bounds__(TB)
+k_bbox_final(int nblk, const double *__restrict__ part, P3TDevState *st)
 {
-    if (threadIdx.x != 0) return;
-    double mn[3], mx[3];
-    for (int a = 0; a < 3; ++a) {
-        mn[a] = part[a];
-        mx[a] = part[3 + a];
-    }
-    for (int b = 1; b < nblk; ++b)
+    double mn[3] = {INFINITY, INFINITY, INFINITY};
+    double mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int b = threadIdx.x; b < nblk; b += TB)
         for (int a = 0; a < 3; ++a) {
             mn[a] = fmin(mn[a], part[6 * b + a]);
             mx[a] = fmax(mx[a], part[6 * b + 3 + a]);
         }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    __shared__ double smn[3][TB / 32], smx[3][TB / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) {
+            smn[a][w] = mn[a];
+            smx[a][w] = mx[a];
+        }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     double ext = 0.0;
     for (int a = 0; a < 3; ++a) {
-        double e = __dsub_rn(mx[a], mn[a]);
+        double u = smn[a][0], v = smx[a][0];
+        for (int q = 1; q < TB / 32; ++q) {
+            u = fmin(u, smn[a][q]);
+            v = fmax(v, smx[a][q]);
+        }
+        double e = __dsub_rn(v, u);
         if (e > ext) ext = e;
-        st->lo[a] = mn[a];
+        st->lo[a] = u;
     }
     st->size = (ext == 0.0) ? 1.0 : __dmul_rn(ext, 1.0 + 0x1p-20);
 }
@@ -505,7 +521,7 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     int nbb = nb < grid_small ? nb : grid_small;
     if (nbb < 1) nbb = 1;
     k_bbox_partial<<<nbb, TB, 0, s>>>(n, pos, mass, c->bbox_part, c->st);
-    k_bbox_final<<<1, 32, 0, s>>>(nbb, c->bbox_part, c->st);
+    k_bbox_final<<<1, TB, 0, s>>>(nbb, c->bbox_part, c->st);
     k_keys<<<nb, TB, 0, s>>>(n, pos, c->st, c->key_a, c->idx_a);
     int rc = p3t_sort_keys(c, n, s);
     if (rc) return rc;

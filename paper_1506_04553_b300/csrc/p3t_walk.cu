@@ -31,24 +31,6 @@ namespace {
 constexpr int WALK_WARPS = 4;
 constexpr int WALK_STACK = 1024;
 
-__device__ __forceinline__ float box_d2(float4 gmn, float4 gmx, float4 cmn,
-                                        float4 cmx)
-{
-    float gx = fmaxf(fmaxf(__fsub_rn(cmn.x, gmx.x), __fsub_rn(gmn.x, cmx.x)), 0.0f);
-    float gy = fmaxf(fmaxf(__fsub_rn(cmn.y, gmx.y), __fsub_rn(gmn.y, cmx.y)), 0.0f);
-    float gz = fmaxf(fmaxf(__fsub_rn(cmn.z, gmx.z), __fsub_rn(gmn.z, cmx.z)), 0.0f);
-    float s = __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy));
-    return __fadd_rn(s, __fmul_rn(gz, gz));
-}
-
-__device__ __forceinline__ float box_side(float4 cmn, float4 cmx)
-{
-    float lx = __fsub_rn(cmx.x, cmn.x);
-    float ly = __fsub_rn(cmx.y, cmn.y);
-    float lz = __fsub_rn(cmx.z, cmn.z);
-    return fmaxf(fmaxf(lx, ly), lz);
-}
-
 template <bool FILL>
 __global__ void __launch_bounds__(WALK_WARPS * 32)
 k_walk(int ngroup, const int2 *__restrict__ grange,
@@ -105,7 +87,7 @@ k_walk(int ngroup, const int2 *__restrict__ grange,
                 const float4 cmn = wmin[c], cmx = wmax[c];
                 float d2 = box_d2(gmn, gmx, cmn, cmx);
                 float l = box_side(cmn, cmx);
-                if (__fmul_rn(l, l) < __fmul_rn(theta2, d2) && d2 > hg2) {
+                if (mac_accept(d2, l, theta2, hg2)) {
                     is_pc = true;
                 } else {
                     child = __float_as_int(cmn.w);
@@ -155,6 +137,7 @@ k_walk(int ngroup, const int2 *__restrict__ grange,
             }
             if (open) stk[top + __popc(mo & lt)] = make_int2(child, nchild);
             top += np;
+            if (lane == 0 && top > 64) atomicMax(&st->max_stack, top);
             __syncwarp();
         }
         if (overflow) {

@@ -58,9 +58,11 @@ def test_structure_bitexact(case):
 
 
 def test_lists_identical(case):
+    # the fused walk+force kernel's counts (taken before the inspection walk
+    # overwrites them) and the inspection lists both match the oracle
+    st = case["ctx"].stats()
     og, gid = compare_structure(case["ctx"], case["tree"])
     compare_lists(case["ctx"], case["tree"], og, gid)
-    st = case["ctx"].stats()
     L = case["tree"].lists()
     assert st["list_pc"] == L["pc"].size
     assert st["list_pp_near"] == L["ppn"].size
