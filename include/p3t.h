@@ -87,8 +87,9 @@ int p3t_set_params(p3t_ctx *ctx, const p3t_params *p);
  * Steps: root cube, 63-bit Morton keys (21 bits per axis), stable radix sort
  * by (key, index), level-wise split of every cell holding more than n_leaf
  * particles, FP64 monopole + traceless quadrupole moments per cell, groups
- * of at most n_group particles (runs of consecutive sibling cells).  The
- * context keeps Morton-ordered copies, so
+ * of n_group consecutive particles cut from containers (cells of at most
+ * 16 n_group particles whose parent holds more).  The context keeps
+ * Morton-ordered copies, so
  * pos and mass may change after the call returns.  n == 0 builds an empty
  * tree.  Synchronises `stream` once at the end (to size later launches).
  * Errors: P3T_ERR_INVALID (n < 0, NULL pointer with n > 0, non-finite

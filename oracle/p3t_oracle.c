@@ -552,40 +552,27 @@ static void orc_group_add_chunked(orc_tree *t, int64_t first, int64_t count)
     }
 }
 
-/* Groups below an internal cell with more than n_group particles: runs of
- * consecutive children that each hold at most n_group particles are merged
- * greedily while the run holds at most n_group; a larger child closes the
- * run and is itself descended (or chunked if it is a leaf). */
+/* Groups.  A container is a cell holding at most 16 n_group particles whose
+ * parent holds more (or a leaf whose parent holds more, or the root if it
+ * qualifies); the particles of each container are cut into consecutive
+ * chunks of n_group in Morton order, the last one partial.  Containers are
+ * visited depth first in Morton order. */
 static void orc_groups_below(orc_tree *t, int64_t c)
 {
-    int64_t run_first = 0, run_count = 0;
-    for (int k = 0; k < t->nchild[c]; ++k) {
-        int64_t ch = t->child_first[c] + k;
-        if (t->count[ch] <= t->n_group) {
-            if (run_count > 0 && run_count + t->count[ch] > t->n_group) {
-                orc_group_add(t, run_first, run_count);
-                run_count = 0;
-            }
-            if (run_count == 0) run_first = t->first[ch];
-            run_count += t->count[ch];
-        } else {
-            if (run_count > 0) {
-                orc_group_add(t, run_first, run_count);
-                run_count = 0;
-            }
-            if (orc_is_leaf(t, ch))
-                orc_group_add_chunked(t, t->first[ch], t->count[ch]);
-            else
-                orc_groups_below(t, ch);
-        }
+    const int64_t cap = 16 * (int64_t)t->n_group;
+    if (t->count[c] <= cap || orc_is_leaf(t, c)) {
+        orc_group_add_chunked(t, t->first[c], t->count[c]);
+        return;
     }
-    if (run_count > 0) orc_group_add(t, run_first, run_count);
+    for (int k = 0; k < t->nchild[c]; ++k)
+        orc_groups_below(t, t->child_first[c] + k);
 }
 
 /* Build the tree for n particles (pos n x 3 row-major, masses m > 0).
  * Steps: root cube, Morton keys, sort by (key, original index), split every
  * cell holding more than n_leaf particles (and above level 21) into its
- * non-empty octants, moments per cell, groups. */
+ * non-empty octants, moments per cell, groups (chunks of n_group inside
+ * cells of at most 16 n_group particles). */
 orc_tree *orc_tree_build(int64_t n, const double *pos, const double *m,
                          int n_leaf, int n_group)
 {
@@ -644,10 +631,7 @@ orc_tree *orc_tree_build(int64_t n, const double *pos, const double *m,
     t->fmax = malloc(3 * C * sizeof(float));
     for (int64_t c = 0; c < C; ++c) orc_cell_moments(t, c);
 
-    if (t->count[0] <= n_group || orc_is_leaf(t, 0))
-        orc_group_add_chunked(t, 0, n);
-    else
-        orc_groups_below(t, 0);
+    orc_groups_below(t, 0);
     t->g_fmin = malloc(3 * t->ngroup * sizeof(float));
     t->g_fmax = malloc(3 * t->ngroup * sizeof(float));
     for (int64_t g = 0; g < t->ngroup; ++g) {

@@ -16,10 +16,9 @@
 //             centre of mass, member box; leaves from their particles,
 //             internal cells from their children (parallel-axis shift) in
 //             FP64; then the FP32 walk and force records
-//   groups    below every internal cell with more than n_group particles,
-//             runs of consecutive children holding at most n_group particles
-//             each are merged greedily while the run holds at most n_group;
-//             a larger leaf is cut into chunks of n_group
+//   groups    chunks of n_group consecutive particles (Morton order) inside
+//             containers: cells of at most 16 n_group particles whose parent
+//             holds more (leaves of any size whose parent holds more)
 #include <math.h>
 
 #include "p3t_internal.cuh"
@@ -393,76 +392,32 @@ __device__ __forceinline__ int chunks(int count, int ng)
     return (count + ng - 1) / ng;
 }
 
-// One thread per cell.  A cell emits groups when it is internal and holds
-// more than n_group particles (runs of small children, chunked big leaves);
-// the root also emits when it is itself small or a leaf.
+// One thread per cell.  A container is a cell holding at most 16 n_group
+// particles whose parent holds more (or a leaf whose parent holds more, or
+// the root if it qualifies); its particles are cut into consecutive chunks of
+// n_group in Morton order, the last one partial.
 __global__ void __launch_bounds__(TB)
 k_groups(int ng, int gcap, const int4 *__restrict__ node,
-         int2 *__restrict__ grange, P3TDevState *st)
+         const int *__restrict__ parent, int2 *__restrict__ grange,
+         P3TDevState *st)
 {
     if (st->error) return;
     const int ncell = st->ncell;
+    const int cap = 16 * ng;
     for (int c = blockIdx.x * TB + threadIdx.x; c < ncell;
          c += gridDim.x * TB) {
-        int4 nd = node[c];
-        const int nch = nd.w & 255;
-        if (c == 0 && (nd.y <= ng || nch == 0)) {
-            int k = chunks(nd.y, ng);
-            int slot = atomicAdd(&st->ngroup, k);
-            if (slot + k > gcap) {
-                p3t_raise(st, P3T_ERR_STATE);
-                continue;
-            }
-            for (int q = 0; q < k; ++q) {
-                int f = nd.x + q * ng;
-                int cnt = min(ng, nd.y - q * ng);
-                emit_group(f, cnt, grange, slot);
-            }
+        const int4 nd = node[c];
+        const bool small = nd.y <= cap || (nd.w & 255) == 0;
+        if (!small) continue;
+        if (c != 0 && node[parent[c]].y <= cap) continue;
+        const int k = chunks(nd.y, ng);
+        int slot = atomicAdd(&st->ngroup, k);
+        if (slot + k > gcap) {
+            p3t_raise(st, P3T_ERR_STATE);
             continue;
         }
-        if (nch == 0 || nd.y <= ng) continue;
-        // pass 1: count, pass 2: write
-        int slot = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            int ngr = 0, run_first = 0, run_count = 0;
-            for (int q = 0; q < nch; ++q) {
-                int4 ch = node[nd.z + q];
-                if (ch.y <= ng) {
-                    if (run_count > 0 && run_count + ch.y > ng) {
-                        if (pass) emit_group(run_first, run_count, grange, slot);
-                        ++ngr;
-                        run_count = 0;
-                    }
-                    if (run_count == 0) run_first = ch.x;
-                    run_count += ch.y;
-                } else {
-                    if (run_count > 0) {
-                        if (pass) emit_group(run_first, run_count, grange, slot);
-                        ++ngr;
-                        run_count = 0;
-                    }
-                    if ((ch.w & 255) == 0) {
-                        int k = chunks(ch.y, ng);
-                        if (pass)
-                            for (int r = 0; r < k; ++r)
-                                emit_group(ch.x + r * ng,
-                                           min(ng, ch.y - r * ng), grange, slot);
-                        ngr += k;
-                    }
-                }
-            }
-            if (run_count > 0) {
-                if (pass) emit_group(run_first, run_count, grange, slot);
-                ++ngr;
-            }
-            if (pass == 0) {
-                slot = atomicAdd(&st->ngroup, ngr);
-                if (slot + ngr > gcap) {
-                    p3t_raise(st, P3T_ERR_STATE);
-                    break;
-                }
-            }
-        }
+        for (int q = 0; q < k; ++q)
+            emit_group(nd.x + q * ng, min(ng, nd.y - q * ng), grange, slot);
     }
 }
 
@@ -538,7 +493,7 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
                                              c->cbmax, c->wmin, c->wmax,
                                              c->cf0, c->cf1, c->cf2, c->st);
     k_groups<<<grid_small, TB, 0, s>>>(c->p.n_group, (int)c->cap_groups,
-                                        c->node, c->grange, c->st);
+                                        c->node, c->parent, c->grange, c->st);
     double h = c->p.h > 0.0 ? c->p.h : c->p.r_out;
     k_group_box<<<grid_small, TB, 0, s>>>(c->grange, c->xs, n, h, c->gmin,
                                            c->gmax, c->gctr, c->st);

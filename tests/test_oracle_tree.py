@@ -129,10 +129,18 @@ def test_groups_partition(plummer_tree):
     assert np.array_equal(first[1:], first[:-1] + count[:-1])
     assert first[-1] + count[-1] == pos.shape[0]
     assert count.max() <= 64 and count.min() >= 1
-    # groups are tree-aligned: every group lies inside one cell whose parent
-    # holds more than n_group particles
+    # every group lies inside one container: a cell of at most 16 * 64
+    # particles whose parent holds more; inside it groups are chunks of 64
     c = t.cells()
-    assert count.mean() > 20
+    cont = [k for k in range(t.ncell)
+            if (c["count"][k] <= 1024 or c["nchild"][k] == 0)
+            and (c["parent"][k] < 0 or c["count"][c["parent"][k]] > 1024)]
+    cf = np.sort(c["first"][cont])
+    assert cf[0] == 0 and np.sum(c["count"][cont]) == pos.shape[0]
+    box = np.searchsorted(cf, first, side="right") - 1
+    start = cf[box]
+    assert np.all((first - start) % 64 == 0)  # chunks from the container start
+    assert count.mean() > 48  # well filled (52 for this input)
 
 
 def test_quadrupole_expansion_accuracy():
