@@ -125,13 +125,13 @@ def _declare(lib):
                                    C.c_int]
     lib.orc_tree_group_of.restype = _i64
     lib.orc_tree_group_of.argtypes = [_p, _i64]
-    if hasattr(lib, "orc_direct_vjp"):
-        lib.orc_direct_vjp.restype = None
-        lib.orc_direct_vjp.argtypes = [_i64, _p, _p, _d, _d, _d, _d, _p, _p,
-                                       _p, C.c_int]
-    if hasattr(lib, "orc_tree_vjp"):
-        lib.orc_tree_vjp.restype = C.c_int
-        lib.orc_tree_vjp.argtypes = [_p, _d, _d, _d, _d, _p, _p, _p, C.c_int]
+    lib.orc_direct_vjp.restype = None
+    lib.orc_direct_vjp.argtypes = [_i64, _p, _p, _d, _d, _d, _d, _p, _p, _p,
+                                   C.c_int]
+    lib.orc_tree_vjp.restype = C.c_int
+    lib.orc_tree_vjp.argtypes = [_p, _d, _d, _d, _d, _p, _p, _p, C.c_int]
+    lib.orc_tree_update.restype = None
+    lib.orc_tree_update.argtypes = [_p, _p, _p]
 
 
 def _ptr(a: np.ndarray):
@@ -207,6 +207,21 @@ def direct(pos, mass, *, G=1.0, eps=0.0, r_cut=1.0, gamma=0.1, kind="soft",
                    _ptr(acc), None if pot is None else _ptr(pot),
                    threads or DEFAULT_THREADS)
     return (acc, pot) if potential else acc
+
+
+def direct_vjp(pos, mass, w, *, G=1.0, eps=0.0, r_cut=1.0, gamma=0.1):
+    """Gradient of sum_i w_i . a_soft,i (direct summation) with respect to
+    positions (n x 3) and masses (n)."""
+    lib = _load()
+    pos = _f64(pos, (-1, 3))
+    mass = _f64(mass)
+    w = _f64(w, (-1, 3))
+    n = pos.shape[0]
+    gx = np.zeros((n, 3))
+    gm = np.zeros(n)
+    lib.orc_direct_vjp(n, _ptr(pos), _ptr(mass), G, eps, r_cut, gamma, _ptr(w),
+                       _ptr(gx), _ptr(gm), 1)
+    return gx, gm
 
 
 # --------------------------------------------------------------------------
@@ -400,3 +415,24 @@ class Tree:
             threads or DEFAULT_THREADS)
         assert rc == 0
         return (acc, pot) if potential else acc
+
+    # ---- gradients (structure frozen) ----
+    def update(self, pos, mass):
+        """New positions/masses with the same keys, cells, groups and lists;
+        moments are recomputed."""
+        self.pos = _f64(pos, (-1, 3))
+        self.mass = _f64(mass)
+        self._lib.orc_tree_update(self._h, _ptr(self.pos), _ptr(self.mass))
+
+    def vjp(self, w, *, G=1.0, eps=0.0, r_cut, gamma=0.1, threads=None):
+        """Gradient of sum_i w_i . a_i over the current lists with respect
+        to positions (n x 3) and masses (n), original order."""
+        assert self._walk is not None, "walk() first"
+        w = _f64(w, (-1, 3))
+        gx = np.zeros((self.n, 3))
+        gm = np.zeros(self.n)
+        rc = self._lib.orc_tree_vjp(self._h, G, eps, r_cut, gamma, _ptr(w),
+                                    _ptr(gx), _ptr(gm),
+                                    threads or DEFAULT_THREADS)
+        assert rc == 0
+        return gx, gm

@@ -969,3 +969,255 @@ int64_t orc_tree_group_of(const orc_tree *t, int64_t k)
         if (k >= t->g_first[g] && k < t->g_first[g] + t->g_count[g]) return g;
     return -1;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradients of L = sum_i w_i . a_i (no counterpart in the paper)           */
+/*                                                                          */
+/* The tree force is a function of positions and masses once the tree      */
+/* topology, the groups and the interaction lists are held fixed; these     */
+/* functions give its vector-Jacobian product.  Pair term (Eq. 8, per unit  */
+/* m_i) with d = x_j - x_i, s^2 = |d|^2 + eps^2:                            */
+/*     f = G m_j K(s) d / s^3,                                               */
+/*     df/dd = G m_j [ (K / s^3) I + (K'(s) / s^4 - 3 K / s^5) d d^T ],     */
+/* K'(s) = dK/dx / ((1 - gamma) r_cut).  Cell term with d = com - x_i:      */
+/*     f = G [ M d / s^3 - Q d / s^5 + (5/2) (d.Q.d) d / s^7 ].             */
+/* Cell adjoints (dL/dM, dL/dcom, dL/dQ) are pushed to every member k with  */
+/* dM/dm_k = 1, dcom/dx_k = m_k / M, dcom/dm_k = e_k / M and                 */
+/* dQ_ab/dx_k,c = m_k (3 (delta_ac e_b + e_a delta_bc) - 2 e_c delta_ab),   */
+/* dQ_ab/dm_k = 3 e_a e_b - |e|^2 delta_ab, e_k = x_k - com (the dependence */
+/* of Q on com vanishes because sum_k m_k e_k = 0).                          */
+/* ------------------------------------------------------------------------ */
+
+static double orc_dK_ds(double s, double r_cut, double gamma)
+{
+    double x = (s / r_cut - gamma) / (1.0 - gamma);
+    return orc_dKdx(x) / ((1.0 - gamma) * r_cut);
+}
+
+/* Pair contribution: adds -J w to gi, +J w to gj and w.(f/m_j) to gmj. */
+static void orc_pair_vjp(const double *xi, const double *xj, double mj,
+                         const double *w, double G, double eps2, double r_cut,
+                         double gamma, double *gi, double *gj, double *gmj)
+{
+    double d[3] = {xj[0] - xi[0], xj[1] - xi[1], xj[2] - xi[2]};
+    double s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps2;
+    if (s2 == 0.0) return;
+    double s = sqrt(s2);
+    double K = orc_K_of_s(s, r_cut, gamma);
+    double Kp = orc_dK_ds(s, r_cut, gamma);
+    if (K == 0.0 && Kp == 0.0) return;
+    double s3 = s2 * s, s4 = s2 * s2, s5 = s4 * s;
+    double phi = K / s3;
+    double psi = Kp / s4 - 3.0 * K / s5;
+    double wd = w[0] * d[0] + w[1] * d[1] + w[2] * d[2];
+    for (int a = 0; a < 3; ++a) {
+        double Jw = G * mj * (phi * w[a] + psi * d[a] * wd);
+        gi[a] -= Jw;
+        gj[a] += Jw;
+    }
+    *gmj += G * phi * wd;
+}
+
+typedef struct {
+    const orc_tree *t;
+    double G, eps2, r_cut, gamma;
+    const double *w;   /* n x 3, original order */
+    double *gx, *gm;   /* per thread: n x 3, n, sorted order */
+    double *aM, *acom, *aQ; /* per thread cell adjoints: C, C x 3, C x 9 */
+} orc_vjp_args;
+
+static void orc_vjp_group(orc_vjp_args *a, int64_t g)
+{
+    const orc_tree *t = a->t;
+    for (int64_t i = t->g_first[g]; i < t->g_first[g] + t->g_count[g]; ++i) {
+        const double *xi = t->x + 3 * i;
+        const double *w = a->w + 3 * t->order[i];
+        double *gi = a->gx + 3 * i;
+        for (int64_t k = t->pc_off[g]; k < t->pc_off[g + 1]; ++k) {
+            int64_t c = t->pc[k];
+            const double *Q6 = t->Q + 6 * c;
+            double Q[3][3] = {{Q6[0], Q6[3], Q6[4]}, {Q6[3], Q6[1], Q6[5]},
+                              {Q6[4], Q6[5], Q6[2]}};
+            double d[3];
+            for (int q = 0; q < 3; ++q) d[q] = t->com[3 * c + q] - xi[q];
+            double s2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + a->eps2;
+            double s = sqrt(s2);
+            double s3 = s2 * s, s5 = s3 * s2, s7 = s5 * s2, s9 = s7 * s2;
+            double M = t->M[c];
+            double Qd[3], dQd = 0.0, wd = 0.0, wQd = 0.0;
+            for (int p = 0; p < 3; ++p) {
+                Qd[p] = Q[p][0] * d[0] + Q[p][1] * d[1] + Q[p][2] * d[2];
+            }
+            for (int p = 0; p < 3; ++p) {
+                dQd += d[p] * Qd[p];
+                wd += w[p] * d[p];
+                wQd += w[p] * Qd[p];
+            }
+            /* (J^T w)_b = sum_a w_a J_ab with J = df/dd */
+            double JTw[3];
+            for (int b = 0; b < 3; ++b) {
+                double wQ_b = w[0] * Q[0][b] + w[1] * Q[1][b] + w[2] * Q[2][b];
+                double v = M * (w[b] / s3 - 3.0 * wd * d[b] / s5)
+                           - (wQ_b / s5 - 5.0 * wQd * d[b] / s7)
+                           + 2.5 * (2.0 * wd * Qd[b] / s7 + dQd * w[b] / s7
+                                    - 7.0 * dQd * wd * d[b] / s9);
+                JTw[b] = a->G * v;
+            }
+            for (int b = 0; b < 3; ++b) {
+                gi[b] -= JTw[b];
+                a->acom[3 * c + b] += JTw[b];
+            }
+            a->aM[c] += a->G * wd / s3;
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q)
+                    a->aQ[9 * c + 3 * p + q] +=
+                        a->G * (-w[p] * d[q] / s5 + 2.5 * wd * d[p] * d[q] / s7);
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+            const int64_t *off = pass ? t->ppf_off : t->ppn_off;
+            const int64_t *lst = pass ? t->ppf : t->ppn;
+            for (int64_t k = off[g]; k < off[g + 1]; ++k) {
+                int64_t j = lst[k];
+                if (j == i) continue;
+                orc_pair_vjp(xi, t->x + 3 * j, t->m[j], w, a->G, a->eps2,
+                             a->r_cut, a->gamma, gi, a->gx + 3 * j, a->gm + j);
+            }
+        }
+    }
+}
+
+typedef struct {
+    orc_vjp_args *args;
+    int64_t ng;
+    int nthreads, id;
+} orc_vjp_job;
+
+static void *orc_vjp_main(void *p)
+{
+    orc_vjp_job *j = (orc_vjp_job *)p;
+    for (int64_t g = j->id; g < j->ng; g += j->nthreads)
+        orc_vjp_group(&j->args[j->id], g);
+    return NULL;
+}
+
+/* Gradient of sum_i w_i . a_i over the current lists (orc_tree_walk first).
+ * w, gx: n x 3 in ORIGINAL order; gm: n.  Returns 0 on success. */
+int orc_tree_vjp(const orc_tree *t, double G, double eps, double r_cut,
+                 double gamma, const double *w, double *gx, double *gm,
+                 int nthreads)
+{
+    if (!t->walked) return -1;
+    int64_t n = t->n, C = t->ncell;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 64) nthreads = 64;
+    orc_vjp_args *args = calloc(nthreads, sizeof(orc_vjp_args));
+    for (int k = 0; k < nthreads; ++k) {
+        args[k].t = t;
+        args[k].G = G;
+        args[k].eps2 = eps * eps;
+        args[k].r_cut = r_cut;
+        args[k].gamma = gamma;
+        args[k].w = w;
+        args[k].gx = calloc(3 * n + 1, sizeof(double));
+        args[k].gm = calloc(n + 1, sizeof(double));
+        args[k].aM = calloc(C + 1, sizeof(double));
+        args[k].acom = calloc(3 * C + 1, sizeof(double));
+        args[k].aQ = calloc(9 * C + 1, sizeof(double));
+    }
+    pthread_t th[64];
+    orc_vjp_job jobs[64];
+    for (int k = 0; k < nthreads; ++k) {
+        jobs[k].args = args;
+        jobs[k].ng = t->ngroup;
+        jobs[k].nthreads = nthreads;
+        jobs[k].id = k;
+        pthread_create(&th[k], NULL, orc_vjp_main, &jobs[k]);
+    }
+    for (int k = 0; k < nthreads; ++k) pthread_join(th[k], NULL);
+    /* reduce the per-thread buffers into thread 0's */
+    orc_vjp_args *r = &args[0];
+    for (int k = 1; k < nthreads; ++k) {
+        for (int64_t q = 0; q < 3 * n; ++q) r->gx[q] += args[k].gx[q];
+        for (int64_t q = 0; q < n; ++q) r->gm[q] += args[k].gm[q];
+        for (int64_t q = 0; q < C; ++q) r->aM[q] += args[k].aM[q];
+        for (int64_t q = 0; q < 3 * C; ++q) r->acom[q] += args[k].acom[q];
+        for (int64_t q = 0; q < 9 * C; ++q) r->aQ[q] += args[k].aQ[q];
+    }
+    /* push the cell adjoints to every member particle */
+    for (int64_t c = 0; c < C; ++c) {
+        double S[3][3], tr = 0.0;
+        for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q)
+                S[p][q] = 0.5 * (r->aQ[9 * c + 3 * p + q] + r->aQ[9 * c + 3 * q + p]);
+        tr = S[0][0] + S[1][1] + S[2][2];
+        double aM = r->aM[c];
+        const double *ac = r->acom + 3 * c;
+        if (aM == 0.0 && ac[0] == 0.0 && ac[1] == 0.0 && ac[2] == 0.0 &&
+            tr == 0.0 && S[0][1] == 0.0 && S[0][2] == 0.0 && S[1][2] == 0.0 &&
+            S[0][0] == 0.0 && S[1][1] == 0.0)
+            continue;
+        double M = t->M[c];
+        for (int64_t k = t->first[c]; k < t->first[c] + t->count[c]; ++k) {
+            double e[3];
+            for (int q = 0; q < 3; ++q) e[q] = t->x[3 * k + q] - t->com[3 * c + q];
+            double Se[3], eSe = 0.0, ee = 0.0, eac = 0.0;
+            for (int p = 0; p < 3; ++p) {
+                Se[p] = S[p][0] * e[0] + S[p][1] * e[1] + S[p][2] * e[2];
+            }
+            for (int p = 0; p < 3; ++p) {
+                eSe += e[p] * Se[p];
+                ee += e[p] * e[p];
+                eac += e[p] * ac[p];
+            }
+            double mk = t->m[k];
+            for (int q = 0; q < 3; ++q)
+                r->gx[3 * k + q] += (mk / M) * ac[q] + mk * (6.0 * Se[q] - 2.0 * tr * e[q]);
+            r->gm[k] += aM + eac / M + 3.0 * eSe - ee * tr;
+        }
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t o = t->order[k];
+        for (int q = 0; q < 3; ++q) gx[3 * o + q] = r->gx[3 * k + q];
+        gm[o] = r->gm[k];
+    }
+    for (int k = 0; k < nthreads; ++k) {
+        free(args[k].gx);
+        free(args[k].gm);
+        free(args[k].aM);
+        free(args[k].acom);
+        free(args[k].aQ);
+    }
+    free(args);
+    return 0;
+}
+
+/* Direct-summation gradient of sum_i w_i . a_soft,i (all pairs, Eq. 8). */
+void orc_direct_vjp(int64_t n, const double *pos, const double *m, double G,
+                    double eps, double r_cut, double gamma, const double *w,
+                    double *gx, double *gm, int nthreads)
+{
+    (void)nthreads;
+    memset(gx, 0, 3 * n * sizeof(double));
+    memset(gm, 0, n * sizeof(double));
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            orc_pair_vjp(pos + 3 * i, pos + 3 * j, m[j], w + 3 * i, G,
+                         eps * eps, r_cut, gamma, gx + 3 * i, gx + 3 * j,
+                         gm + j);
+        }
+}
+
+/* New positions / masses (original order) for the same tree: the sorted
+ * copies and all cell moments are recomputed; keys, topology, groups and
+ * interaction lists are kept (the frozen-structure function the gradients
+ * above differentiate). */
+void orc_tree_update(orc_tree *t, const double *pos, const double *m)
+{
+    for (int64_t k = 0; k < t->n; ++k) {
+        int64_t i = t->order[k];
+        for (int a = 0; a < 3; ++a) t->x[3 * k + a] = pos[3 * i + a];
+        t->m[k] = m[i];
+    }
+    for (int64_t c = 0; c < t->ncell; ++c) orc_cell_moments(t, c);
+}
