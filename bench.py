@@ -333,6 +333,35 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    # backward pass (gradient of sum_i w_i . a_i): fwd = build + force,
+    # bwd = p3t_long_force_vjp on the same tree
+    wgt = torch.randn((3, n), dtype=torch.float32, device=dev,
+                      generator=torch.Generator(device=dev).manual_seed(40))
+    gpos = torch.empty((3, n), dtype=torch.float64, device=dev)
+    gmass = torch.empty((n,), dtype=torch.float64, device=dev)
+    ctx.build_tree(pos, mass)
+    ctx.long_force(acc, check=False)
+    ctx.long_force_vjp(wgt, gpos, gmass)  # warm-up
+    fw, bw = [], []
+    for _ in range(3):
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a2 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        ctx.build_tree(pos, mass)
+        ctx.long_force(acc, check=False)
+        a1.record(stream)
+        ctx.long_force_vjp(wgt, gpos, gmass, check=False)
+        a2.record(stream)
+        torch.cuda.synchronize()
+        fw.append(a0.elapsed_time(a1))
+        bw.append(a1.elapsed_time(a2))
+    ctx.check()
+    t_f, t_b = float(np.median(fw)), float(np.median(bw))
+    line["fwd_bwd_ratio"] = (t_f + t_b) / t_f
+    line["fwd_bwd_ms"] = {"fwd_build_force": t_f, "bwd_vjp": t_b,
+                          "note": "median of 3, same tree; bwd recomputes the "
+                                  "interaction sets"}
     # end-to-end through the public API with host buffers
     if not args.no_e2e:
         pin = lambda a: torch.tensor(a).pin_memory()

@@ -113,6 +113,24 @@ int p3t_build_tree(p3t_ctx *ctx, int64_t n, const double *pos,
  * P3T_ERR_CUDA. */
 int p3t_long_force(p3t_ctx *ctx, float *acc, double *pot, void *stream);
 
+/* Backward pass of p3t_long_force: for weights w_i (the gradient of a loss
+ * with respect to the accelerations), computes dL/dx_i and dL/dm_i of
+ * L = sum_i w_i . a_i with the tree topology, the groups and the
+ * interaction sets of the current tree held fixed.  The paper has no
+ * backward pass; the derivative follows Eq. 8 (pair terms, including dK/ds
+ * from Eq. 12-15) and the softened quadrupole cell terms, with the cell
+ * moments' dependence on member positions and masses.  The interaction sets
+ * are recomputed by the same walk as the forward pass, not stored.
+ *   w         : device, float[3][n] (SoA, caller's order)
+ *   grad_pos  : device, double[3][n], overwritten
+ *   grad_mass : device, double[n], overwritten
+ * Uses context-owned scratch (10 doubles per cell).  No host
+ * synchronisation; walk-stack overflows latch P3T_ERR_CAPACITY (p3t_check).
+ * Errors: P3T_ERR_STATE (no tree), P3T_ERR_INVALID (NULL with n > 0),
+ * P3T_ERR_CUDA. */
+int p3t_long_force_vjp(p3t_ctx *ctx, const float *w, double *grad_pos,
+                       double *grad_mass, void *stream);
+
 /* Synchronises `stream` and returns (and clears) the first error latched by
  * a kernel of this context since the last check, or P3T_OK. */
 int p3t_check(p3t_ctx *ctx, void *stream);
@@ -202,7 +220,8 @@ int p3t_get_stats(p3t_ctx *ctx, p3t_stats *s);
  * device time of every phase since the last reset. */
 typedef struct p3t_profile {
     double build_ms;   /* p3t_build_tree, all kernels */
-    double walk_ms;    /* unused (the walk runs inside the force kernel) */
+    double walk_ms;    /* p3t_long_force_vjp (walk + Jacobian products +
+                          push of cell adjoints) */
     double force_ms;   /* p3t_long_force: the fused walk + force kernel */
     double ngb_ms;     /* p3t_neighbours: near walks, scan, row sort */
     int64_t builds, walks, forces, ngbs; /* number of timed calls */

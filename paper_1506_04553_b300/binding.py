@@ -92,6 +92,7 @@ _sigs = {
     "p3t_get_lists": [_vp] + [_vp] * 6,
     "p3t_profile_enable": [_vp, C.c_int],
     "p3t_check": [_vp, _vp],
+    "p3t_long_force_vjp": [_vp, _vp, _vp, _vp, _vp],
     "p3t_get_profile": [_vp, _vp, C.c_int],
 }
 for _name, _args in _sigs.items():
@@ -197,6 +198,7 @@ class Context:
         _check(_lib.p3t_build_tree(self._h, n, p, m, _stream(stream)),
                "p3t_build_tree")
         self.n = n
+        self.build_id = getattr(self, "build_id", 0) + 1
 
     def long_force(self, acc=None, pot=None, want_potential=False, stream=None,
                    check=True):
@@ -216,6 +218,26 @@ class Context:
         if check:
             self.check(stream)
         return (acc, pot) if pot is not None else acc
+
+    def long_force_vjp(self, w, grad_pos=None, grad_mass=None, stream=None,
+                       check=True):
+        """dL/dx (3, n) float64 and dL/dm (n,) float64 of L = sum_i w_i . a_i
+        for the current tree (structure and interaction sets held fixed);
+        w is (3, n) float32."""
+        import torch
+        n = self.n
+        if grad_pos is None:
+            grad_pos = torch.empty((3, n), dtype=torch.float64, device="cuda")
+        if grad_mass is None:
+            grad_mass = torch.empty((n,), dtype=torch.float64, device="cuda")
+        _check(_lib.p3t_long_force_vjp(
+            self._h, _dptr(w, torch.float32, (3, n), "w"),
+            _dptr(grad_pos, torch.float64, (3, n), "grad_pos"),
+            _dptr(grad_mass, torch.float64, (n,), "grad_mass"),
+            _stream(stream)), "p3t_long_force_vjp")
+        if check:
+            self.check(stream)
+        return grad_pos, grad_mass
 
     def check(self, stream=None):
         """Synchronise and raise the first error latched on the device."""

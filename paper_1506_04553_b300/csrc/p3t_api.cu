@@ -173,7 +173,7 @@ void free_all(p3t_ctx *c)
                     c->ccom, c->cQ, c->cbmin, c->cbmax, c->wmin, c->wmax,
                     c->cf0, c->cf1, c->cf2, c->grange, c->gmin, c->gmax,
                     c->gctr, c->lcnt, c->loff, c->list[0], c->list[1],
-                    c->list[2], c->scan_part, c->red_part};
+                    c->list[2], c->scan_part, c->red_part, c->cadj};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hst) cudaFreeHost(c->hst);
@@ -302,6 +302,26 @@ int p3t_long_force(p3t_ctx *c, float *acc, double *pot, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     int slot = p3t_prof_open(c, P3T_PH_FORCE, s);
     int rc = p3t_run_force(c, acc, pot, s);
+    p3t_prof_close(c, slot, s);
+    return rc;
+}
+
+int p3t_long_force_vjp(p3t_ctx *c, const float *w, double *grad_pos,
+                       double *grad_mass, void *stream)
+{
+    if (!c) return P3T_ERR_INVALID;
+    if (!c->built) return P3T_ERR_STATE;
+    if (c->n == 0) return P3T_OK;
+    if (!w || !grad_pos || !grad_mass) return P3T_ERR_INVALID;
+    const int64_t need = 10 * (int64_t)c->hst->ncell;
+    if (need > c->cap_cadj) {
+        int64_t d = 0;
+        P3T_TRY(grow(c->cadj, d, need + need / 4, sizeof(double)));
+        c->cap_cadj = need + need / 4;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int slot = p3t_prof_open(c, P3T_PH_WALK, s);
+    int rc = p3t_run_vjp(c, w, grad_pos, grad_mass, c->cadj, s);
     p3t_prof_close(c, slot, s);
     return rc;
 }

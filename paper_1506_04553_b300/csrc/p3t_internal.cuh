@@ -94,6 +94,9 @@ struct p3t_ctx {
     int *list[3];
     // generic scan scratch
     long long *scan_part;
+    // backward pass: 10 adjoints per cell
+    double *cadj;
+    int64_t cap_cadj;
     // energy scratch
     double *red_part;
     // profiling
@@ -188,6 +191,8 @@ int p3t_scan_lists(p3t_ctx *c, cudaStream_t s);                 // p3t_walk.cu
 int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s);   // p3t_force.cu
 int p3t_run_ngb(p3t_ctx *c, int fill, const long long *row_off, int *idx,
                 long long cap, cudaStream_t s);                  // p3t_ngb.cu
+int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,
+                double *cadj, cudaStream_t s);                   // p3t_vjp.cu
 int p3t_energy_launch(p3t_ctx *c, int n, const double *mass,
                       const double *vel, const double *pot, double *out,
                       cudaStream_t s);                           // p3t_misc.cu
