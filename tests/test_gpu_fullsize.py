@@ -1,0 +1,63 @@
+"""Full-size parity on sampled outputs, in the launch configuration bench.py
+times: Plummer N = 2^20 (theta 0.4, r_out 0.0025) and a King W0 = 9 model
+with Salpeter masses, N = 2^21 (theta 0.5, r_out 0.002).  Forces of randomly
+chosen groups against the same-tree FP64 oracle; neighbour rows of sampled
+particles (King: drawn from the 4 x 2048 densest) against brute force over
+all particles."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1506_04553_b300 import ics
+from parity_util import gpu_run, rel_err
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _check(pos, m, params, n_groups=256, n_rows=2048, dense_rows=False):
+    ctx, acc, _, ngb = gpu_run(pos, m, params)
+    n = pos.shape[0]
+    t = oracle.Tree(pos, m, n_leaf=params.n_leaf, n_group=params.n_group)
+    h = params.h if params.h > 0 else params.r_out
+    t.walk(params.theta, h, params.r_out)
+    st = ctx.stats()
+    L = t.lists()
+    assert st["list_pc"] == L["pc"].size and st["list_pp_near"] == L["ppn"].size
+    g = t.groups()
+    rng = np.random.default_rng(77)
+    sel = rng.choice(t.ngroup, n_groups, replace=False)
+    a_o = t.force(G=params.G, eps=params.eps, r_cut=params.r_out,
+                  gamma=params.gamma, groups=sel)
+    key, order = t.particles()
+    rows = np.concatenate([order[g["first"][q]:g["first"][q] + g["count"][q]] for q in sel])
+    e = rel_err(acc[rows], a_o[rows])
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4, (np.median(e), e.max())
+    off, idx = ngb
+    if dense_rows:
+        cnt = np.diff(off)
+        cand = np.argsort(-cnt)[: 4 * n_rows]
+        rsel = rng.choice(cand, n_rows, replace=False)
+    else:
+        rsel = rng.choice(n, n_rows, replace=False)
+    off_o, idx_o = oracle.neighbours(pos, h, rows=rsel)
+    for r, i in enumerate(rsel):
+        assert np.array_equal(idx[off[i]:off[i + 1]], idx_o[off_o[r]:off_o[r + 1]]), i
+    return np.diff(off)
+
+
+def test_plummer_2p20(cuda):
+    from paper_1506_04553_b300 import Params
+    n = 1 << 20
+    pos, _, m = ics.plummer(n, 2)
+    cnt = _check(pos.T.copy(), m, Params(theta=0.4, r_out=0.0025, eps=4.0 / n))
+    assert cnt.sum() > 0
+
+
+def test_king_w9_salpeter_2p21(cuda):
+    from paper_1506_04553_b300 import Params
+    n = 1 << 21
+    masses = ics.salpeter_masses(n, seed=3 + 7919)
+    pos, _, m = ics.king(n, 3, W0=9.0, masses=masses)
+    cnt = _check(pos.T.copy(), m, Params(theta=0.5, r_out=0.002, eps=4.0 / n),
+                 dense_rows=True)
+    assert cnt.max() >= 8  # dense core (measured maximum: 12 neighbours)
