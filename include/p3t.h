@@ -44,6 +44,14 @@ extern "C" {
 #define P3T_ERR_TIMEOUT 4  /* a bounded device-side wait expired */
 #define P3T_ERR_STATE 5    /* call out of order (e.g. force before build) */
 
+/* ---- flags ---- */
+/* p3t_build_tree neither allocates nor synchronises; capacities must have
+ * been sized by an earlier build without the flag (which keeps 50% headroom
+ * of cells), and a capacity overflow latches P3T_ERR_CAPACITY on the device
+ * (p3t_check).  With it every call of a step only enqueues work on the
+ * stream, so the step can be captured into a CUDA graph. */
+#define P3T_FLAG_NO_SYNC 1
+
 typedef struct p3t_ctx p3t_ctx;
 
 /* Parameters.  Names follow the paper: r_out is r_cut of Eq. 12-15 and
@@ -61,7 +69,7 @@ typedef struct p3t_params {
                         (1..64; default 16) */
     int32_t n_group; /* particles sharing one interaction list (1..64;
                         default 64) */
-    int32_t flags;   /* reserved, 0 */
+    int32_t flags;   /* P3T_FLAG_* */
     int32_t reserved;
 } p3t_params;
 
@@ -96,6 +104,18 @@ int p3t_set_params(p3t_ctx *ctx, const p3t_params *p);
  * coordinate, mass not finite and positive), P3T_ERR_CUDA. */
 int p3t_build_tree(p3t_ctx *ctx, int64_t n, const double *pos,
                    const double *mass, void *stream);
+
+/* Ensembles: the particle arrays hold n_clusters independent clusters,
+ * cluster k at [off[k], off[k+1]) (host int64, off[0] = 0, every cluster
+ * non-empty).  Each cluster gets its own root cube, octree and groups, and
+ * interacts only with itself (no forces or neighbours across clusters).
+ * r_out, eps, h: host double[n_clusters] per-cluster values, or NULL for the
+ * context's parameters.  Applies from the next p3t_build_tree, whose n must
+ * be off[n_clusters].  n_clusters = 0 returns to a single cluster.  The
+ * paper integrates one cluster; ensembles are a service of the library.
+ * Errors: P3T_ERR_INVALID. */
+int p3t_set_ensemble(p3t_ctx *ctx, int32_t n_clusters, const int64_t *off,
+                     const double *r_out, const double *eps, const double *h);
 
 /* Long-range acceleration a_soft (Eq. 8) of every particle by the tree.
  *   acc : device, float[3][n] (SoA), written in the caller's order

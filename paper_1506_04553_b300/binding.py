@@ -21,7 +21,9 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["Params", "Context", "P3TError", "kick", "drift", "library_path",
-           "launch_count"]
+           "launch_count", "FLAG_NO_SYNC"]
+
+FLAG_NO_SYNC = 1  # build without allocation or host synchronisation
 
 _STATUS = {0: "ok", 1: "invalid argument or input", 2: "capacity exceeded",
            3: "CUDA error", 4: "device wait timed out", 5: "call out of order"}
@@ -93,6 +95,7 @@ _sigs = {
     "p3t_profile_enable": [_vp, C.c_int],
     "p3t_check": [_vp, _vp],
     "p3t_long_force_vjp": [_vp, _vp, _vp, _vp, _vp],
+    "p3t_set_ensemble": [_vp, C.c_int32, _vp, _vp, _vp, _vp],
     "p3t_get_profile": [_vp, _vp, C.c_int],
 }
 for _name, _args in _sigs.items():
@@ -188,6 +191,19 @@ class Context:
         cp = params._c()
         _check(_lib.p3t_set_params(self._h, C.byref(cp)), "p3t_set_params")
         self.params = params
+
+    def set_ensemble(self, offsets, r_out=None, eps=None, h=None):
+        """Independent clusters: cluster k holds particles
+        [offsets[k], offsets[k+1]); optional per-cluster r_out, eps, h."""
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        nc = off.size - 1
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+                for a in (r_out, eps, h)]
+        _check(_lib.p3t_set_ensemble(
+            self._h, nc, _np_ptr(off) if nc > 0 else None,
+            *[None if a is None else _np_ptr(a) for a in arrs]),
+            "p3t_set_ensemble")
+        self._ens = (off, arrs)  # keep the host arrays alive
 
     # ---- hot path ----
     def build_tree(self, pos, mass, stream=None):

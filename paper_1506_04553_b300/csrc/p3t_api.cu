@@ -56,6 +56,31 @@ static int prof_resolve(p3t_ctx *c)
     return P3T_OK;
 }
 
+void p3t_cluster_consts(const p3t_params *p, double r_out, double eps,
+                        double h, ClusterConsts *k)
+{
+    double hh = h > 0.0 ? h : r_out;
+    k->eps2 = (float)(eps * eps);
+    k->kA = (float)(1.0 / ((1.0 - p->gamma) * r_out));
+    k->kB = (float)(-p->gamma / (1.0 - p->gamma));
+    float hg = (float)(hh > r_out ? hh : r_out);
+    float hs = hg * hg;
+    k->hg2 = hs * 1.0009765625f;
+    k->h = hh;
+    k->h2 = hh * hh;
+    k->r_out = r_out;
+    double g = p->gamma;
+    if (g > 0.0) {
+        double g2 = g * g, g3 = g2 * g, g4 = g3 * g, g5 = g4 * g, g6 = g5 * g;
+        double gm1 = g - 1.0;
+        double gm17 = gm1 * gm1 * gm1 * gm1 * gm1 * gm1 * gm1;
+        k->w_in = 7.0 * (g6 - 9.0 * g5 + 45.0 * g4 - 60.0 * g3 * log(g)
+                         - 45.0 * g2 + 9.0 * g - 1.0) / (3.0 * gm17);
+    } else {
+        k->w_in = 7.0 / 3.0;
+    }
+}
+
 namespace {
 
 template <class T>
@@ -89,6 +114,48 @@ int check_params(const p3t_params *p)
     return P3T_OK;
 }
 
+int ensure_clusters(p3t_ctx *c, int nc)
+{
+    if (nc <= c->cap_clus) return P3T_OK;
+    int cap = nc + 16;
+    if (c->clus_off_h) cudaFreeHost(c->clus_off_h);
+    if (c->cc_h) cudaFreeHost(c->cc_h);
+    c->clus_off_h = nullptr;
+    c->cc_h = nullptr;
+    P3T_CUDA_TRY(cudaMallocHost((void **)&c->clus_off_h, (cap + 1) * sizeof(int64_t)));
+    P3T_CUDA_TRY(cudaMallocHost((void **)&c->cc_h, cap * sizeof(ClusterConsts)));
+    free(c->clus_par);
+    c->clus_par = (double *)calloc(3 * (size_t)cap, sizeof(double));
+    if (!c->clus_par) return P3T_ERR_CUDA;
+    int64_t d = 0;
+    P3T_TRY(grow(c->clus_off, d, cap + 1, sizeof(int64_t)));
+    P3T_TRY(grow(c->cc, d, cap, sizeof(ClusterConsts)));
+    P3T_TRY(grow(c->clus_box, d, 4 * (int64_t)cap, sizeof(double)));
+    c->cap_clus = cap;
+    return P3T_OK;
+}
+
+// Writes the per-cluster constants of the current layout to pinned memory
+// and queues their upload.
+int upload_clusters(p3t_ctx *c, cudaStream_t s)
+{
+    for (int k = 0; k < c->nclus; ++k) {
+        double r = c->p.r_out, e = c->p.eps, h = c->p.h;
+        if (c->ensemble) {
+            if (c->clus_par[k] > 0.0) r = c->clus_par[k];
+            if (c->clus_par[c->cap_clus + k] >= 0.0) e = c->clus_par[c->cap_clus + k];
+            if (c->clus_par[2 * c->cap_clus + k] > 0.0) h = c->clus_par[2 * c->cap_clus + k];
+        }
+        p3t_cluster_consts(&c->p, r, e, h, &c->cc_h[k]);
+    }
+    P3T_CUDA_TRY(cudaMemcpyAsync(c->clus_off, c->clus_off_h,
+                                 (c->nclus + 1) * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s));
+    P3T_CUDA_TRY(cudaMemcpyAsync(c->cc, c->cc_h, c->nclus * sizeof(ClusterConsts),
+                                 cudaMemcpyHostToDevice, s));
+    return P3T_OK;
+}
+
 int ensure_particles(p3t_ctx *c, int64_t n)
 {
     if (n <= c->cap_n) return P3T_OK;
@@ -116,6 +183,8 @@ int ensure_particles(p3t_ctx *c, int64_t n)
     P3T_TRY(grow(c->gctr, d, cap, sizeof(float4)));
     P3T_TRY(grow(c->lcnt, d, 3 * cap, sizeof(long long)));
     P3T_TRY(grow(c->loff, d, 3 * (cap + 1), sizeof(long long)));
+    P3T_TRY(grow(c->pclus, d, cap, sizeof(int)));
+    P3T_TRY(grow(c->gclus, d, cap, sizeof(int)));
     c->cap_n = cap;
     return P3T_OK;
 }
@@ -138,6 +207,31 @@ int ensure_cells(p3t_ctx *c, int64_t want)
     P3T_TRY(grow(c->cf1, d, cap, sizeof(float4)));
     P3T_TRY(grow(c->cf2, d, cap, sizeof(float4)));
     c->cap_cells = cap;
+    return P3T_OK;
+}
+
+// Grows the cell arrays while keeping the current tree (copied over).
+int ensure_cells_keep(p3t_ctx *c, int64_t want)
+{
+    if (want <= c->cap_cells) return P3T_OK;
+    p3t_ctx old = *c;
+    c->node = nullptr; c->parent = nullptr; c->cM = nullptr; c->ccom = nullptr;
+    c->cQ = nullptr; c->cbmin = nullptr; c->cbmax = nullptr; c->wmin = nullptr;
+    c->wmax = nullptr; c->cf0 = nullptr; c->cf1 = nullptr; c->cf2 = nullptr;
+    c->cap_cells = 0;
+    P3T_TRY(ensure_cells(c, want));
+    const size_t C = (size_t)old.cap_cells;
+    struct { void *dst, *src; size_t bytes; } cp[] = {
+        {c->node, old.node, C * sizeof(int4)}, {c->parent, old.parent, C * 4},
+        {c->cM, old.cM, C * 8}, {c->ccom, old.ccom, 3 * C * 8},
+        {c->cQ, old.cQ, 6 * C * 8}, {c->cbmin, old.cbmin, 3 * C * 8},
+        {c->cbmax, old.cbmax, 3 * C * 8}, {c->wmin, old.wmin, C * 16},
+        {c->wmax, old.wmax, C * 16}, {c->cf0, old.cf0, C * 16},
+        {c->cf1, old.cf1, C * 16}, {c->cf2, old.cf2, C * 16}};
+    for (auto &e : cp) {
+        P3T_CUDA_TRY(cudaMemcpy(e.dst, e.src, e.bytes, cudaMemcpyDeviceToDevice));
+        cudaFree(e.src);
+    }
     return P3T_OK;
 }
 
@@ -173,10 +267,14 @@ void free_all(p3t_ctx *c)
                     c->ccom, c->cQ, c->cbmin, c->cbmax, c->wmin, c->wmax,
                     c->cf0, c->cf1, c->cf2, c->grange, c->gmin, c->gmax,
                     c->gctr, c->lcnt, c->loff, c->list[0], c->list[1],
-                    c->list[2], c->scan_part, c->red_part, c->cadj};
+                    c->list[2], c->scan_part, c->red_part, c->cadj,
+                    c->clus_off, c->cc, c->clus_box, c->pclus, c->gclus};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hst) cudaFreeHost(c->hst);
+    if (c->clus_off_h) cudaFreeHost(c->clus_off_h);
+    if (c->cc_h) cudaFreeHost(c->cc_h);
+    free(c->clus_par);
     for (int k = 0; k < 2 * c->prof.cap; ++k) cudaEventDestroy(c->prof.ev[k]);
     free(c->prof.ev);
     free(c->prof.phase);
@@ -228,6 +326,12 @@ int p3t_create(p3t_ctx **out, const p3t_params *p)
         delete c;
         return rc ? rc : P3T_ERR_CUDA;
     }
+    if (ensure_clusters(c, 1) != P3T_OK) {
+        free_all(c);
+        delete c;
+        return P3T_ERR_CUDA;
+    }
+    c->nclus = 1;
     if (cudaMemset(c->st, 0, sizeof(P3TDevState)) != cudaSuccess) {
         free_all(c);
         delete c;
@@ -262,6 +366,8 @@ int p3t_build_tree(p3t_ctx *c, int64_t n, const double *pos,
     if (!c || n < 0 || n > 0x7fffff00LL) return P3T_ERR_INVALID;
     if (n > 0 && (!pos || !mass)) return P3T_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
+    const bool no_sync = (c->p.flags & P3T_FLAG_NO_SYNC) != 0;
+    if (c->ensemble && n != c->clus_off_h[c->nclus]) return P3T_ERR_INVALID;
     c->built = 0;
     c->lists_valid = 0;
     c->n = n;
@@ -272,16 +378,35 @@ int p3t_build_tree(p3t_ctx *c, int64_t n, const double *pos,
         c->built = 1;
         return P3T_OK;
     }
-    P3T_TRY(ensure_particles(c, n));
-    if (c->cap_cells < n / 2 + 64) P3T_TRY(ensure_cells(c, n / 2 + 64));
+    if (!c->ensemble) {
+        c->nclus = 1;
+        c->clus_off_h[0] = 0;
+        c->clus_off_h[1] = n;
+    }
+    if (no_sync) {
+        // nothing may be allocated or waited for: capacities must suffice
+        if (n > c->cap_n || c->cap_cells < n / 2 + 64) return P3T_ERR_CAPACITY;
+    } else {
+        P3T_TRY(ensure_particles(c, n));
+        if (c->cap_cells < n / 2 + 64) P3T_TRY(ensure_cells(c, n / 2 + 64));
+    }
+    P3T_TRY(upload_clusters(c, s));
     for (int attempt = 0; attempt < 8; ++attempt) {
         P3T_TRY(clear_error(c, s));
         int slot = p3t_prof_open(c, P3T_PH_BUILD, s);
         int rc = p3t_build_levels(c, (int)n, s, pos, mass);
         p3t_prof_close(c, slot, s);
         P3T_TRY(rc);
+        if (no_sync) {
+            // errors (a cell capacity overflow included) latch on the device
+            c->built = 1;
+            return P3T_OK;
+        }
         P3T_TRY(sync_state(c, s));
         if (c->hst->error == 0) {
+            // leave room for later builds that may not allocate
+            int64_t want = c->hst->ncell + c->hst->ncell / 2 + 64;
+            if (want > c->cap_cells) P3T_TRY(ensure_cells_keep(c, want));
             c->built = 1;
             return P3T_OK;
         }
@@ -291,6 +416,36 @@ int p3t_build_tree(p3t_ctx *c, int64_t n, const double *pos,
         P3T_TRY(ensure_cells(c, want));
     }
     return P3T_ERR_CAPACITY;
+}
+
+int p3t_set_ensemble(p3t_ctx *c, int32_t n_clusters, const int64_t *off,
+                     const double *r_out, const double *eps, const double *h)
+{
+    if (!c || n_clusters < 0) return P3T_ERR_INVALID;
+    if (n_clusters == 0) {
+        c->ensemble = 0;
+        c->built = 0;
+        return P3T_OK;
+    }
+    if (!off || off[0] != 0) return P3T_ERR_INVALID;
+    for (int k = 0; k < n_clusters; ++k) {
+        if (off[k + 1] <= off[k]) return P3T_ERR_INVALID;
+        if (r_out && !(r_out[k] > 0.0 && isfinite(r_out[k]))) return P3T_ERR_INVALID;
+        if (eps && !(eps[k] >= 0.0 && isfinite(eps[k]))) return P3T_ERR_INVALID;
+        if (h && !(h[k] >= 0.0 && isfinite(h[k]))) return P3T_ERR_INVALID;
+    }
+    if (off[n_clusters] > 0x7fffff00LL) return P3T_ERR_INVALID;
+    P3T_TRY(ensure_clusters(c, n_clusters));
+    c->nclus = n_clusters;
+    for (int k = 0; k <= n_clusters; ++k) c->clus_off_h[k] = off[k];
+    for (int k = 0; k < n_clusters; ++k) {
+        c->clus_par[k] = r_out ? r_out[k] : 0.0;
+        c->clus_par[c->cap_clus + k] = eps ? eps[k] : -1.0;
+        c->clus_par[2 * c->cap_clus + k] = h ? h[k] : 0.0;
+    }
+    c->ensemble = 1;
+    c->built = 0;
+    return P3T_OK;
 }
 
 int p3t_long_force(p3t_ctx *c, float *acc, double *pot, void *stream)
@@ -313,8 +468,9 @@ int p3t_long_force_vjp(p3t_ctx *c, const float *w, double *grad_pos,
     if (!c->built) return P3T_ERR_STATE;
     if (c->n == 0) return P3T_OK;
     if (!w || !grad_pos || !grad_mass) return P3T_ERR_INVALID;
-    const int64_t need = 10 * (int64_t)c->hst->ncell;
+    const int64_t need = 10 * (int64_t)c->cap_cells;
     if (need > c->cap_cadj) {
+        if (c->p.flags & P3T_FLAG_NO_SYNC) return P3T_ERR_CAPACITY;
         int64_t d = 0;
         P3T_TRY(grow(c->cadj, d, need + need / 4, sizeof(double)));
         c->cap_cadj = need + need / 4;

@@ -348,11 +348,13 @@ __device__ __forceinline__ void particle_tile(
 
 template <bool POT>
 __global__ void __launch_bounds__(FW * 32)
-k_walk_force(int G, const int2 *__restrict__ grange,
+k_walk_force(const int *__restrict__ gclus,
+             const ClusterConsts *__restrict__ ccs,
+             const int2 *__restrict__ grange,
              const float4 *__restrict__ gmin, const float4 *__restrict__ gmax,
              const float4 *__restrict__ gctr, const float4 *__restrict__ wmin,
              const float4 *__restrict__ wmax, const int4 *__restrict__ node,
-             float theta2, float hg2, const float4 *__restrict__ phi,
+             float theta2, const float4 *__restrict__ phi,
              const float4 *__restrict__ plo, const float4 *__restrict__ cf0,
              const float4 *__restrict__ cf1, const float4 *__restrict__ cf2,
              const int *__restrict__ order, int n, ForceConsts k,
@@ -363,6 +365,7 @@ k_walk_force(int G, const int2 *__restrict__ grange,
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
     WarpSmem &S = smem[w];
+    const int G = st->ngroup;
     for (;;) {
         int g = 0;
         if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
@@ -371,6 +374,16 @@ k_walk_force(int G, const int2 *__restrict__ grange,
         const int2 gr = grange[g];
         const float4 ct = gctr[g];
         const float4 gmn = gmin[g], gmx = gmax[g];
+        const int cl = gclus[g];
+        const ClusterConsts cc = ccs[cl];
+        ForceConsts kg = k;
+        kg.eps2 = cc.eps2;
+        kg.kA = cc.kA;
+        kg.kB = cc.kB;
+        kg.h2 = cc.h2;
+        kg.r_out = cc.r_out;
+        kg.w_in = cc.w_in;
+        const float hg2 = cc.hg2;
         const int k0 = gr.x + lane, k1 = gr.x + 32 + lane;
         const bool v0 = lane < gr.y, v1 = lane + 32 < gr.y;
         const float4 p0 = v0 ? rel4(phi[k0], plo[k0], ct) : far_pad();
@@ -383,7 +396,7 @@ k_walk_force(int G, const int2 *__restrict__ grange,
         RangeRing rf = {0, 0, 0}, rn = {0, 0, 0};
         long long cnt_pc = 0, cnt_pn = 0, cnt_pf = 0;
 
-        if (lane == 0) S.stack[0] = 0;  // the root: child 0, one cell
+        if (lane == 0) S.stack[0] = cl * 8;  // the cluster's root, one cell
         int top = 1;
         int iter = 0;
         bool overflow = false;
@@ -464,13 +477,13 @@ k_walk_force(int G, const int2 *__restrict__ grange,
             // evaluate every full tile
             while (pc_n >= 32)
                 cell_tile<POT>(S, pc_head, pc_n, 32, cf0, cf1, cf2, ct, p0, p1,
-                               k.eps2, A, lane);
+                               kg.eps2, A, lane);
             while (rf.np >= 32)
                 particle_tile<false, POT>(S, S.pf, rf, 32, phi, plo, ct, p0, p1,
-                                          k0, k1, k, A, lane);
+                                          k0, k1, kg, A, lane);
             while (rn.np >= 32)
                 particle_tile<true, POT>(S, S.pn, rn, 32, phi, plo, ct, p0, p1,
-                                         k0, k1, k, A, lane);
+                                         k0, k1, kg, A, lane);
         }
         if (overflow) {
             if (lane == 0) p3t_raise(st, P3T_ERR_CAPACITY);
@@ -479,13 +492,13 @@ k_walk_force(int G, const int2 *__restrict__ grange,
         // the partial tiles left over
         if (pc_n > 0)
             cell_tile<POT>(S, pc_head, pc_n, pc_n, cf0, cf1, cf2, ct, p0, p1,
-                           k.eps2, A, lane);
+                           kg.eps2, A, lane);
         if (rf.np > 0)
             particle_tile<false, POT>(S, S.pf, rf, rf.np, phi, plo, ct, p0, p1,
-                                      k0, k1, k, A, lane);
+                                      k0, k1, kg, A, lane);
         if (rn.np > 0)
             particle_tile<true, POT>(S, S.pn, rn, rn.np, phi, plo, ct, p0, p1,
-                                     k0, k1, k, A, lane);
+                                     k0, k1, kg, A, lane);
         // ---- write back in the caller's order ----
         const float Gc = k.G;
         if (v0) {
@@ -557,26 +570,26 @@ ForceConsts make_consts(const p3t_params &p)
 
 int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s)
 {
-    const int G = c->hst->ngroup;
     const int n = (int)c->n;
     k_force_reset<<<1, 32, 0, s>>>(c->st);
     p3t_count_launches(1);
-    if (G == 0) return P3T_OK;
+    // the group count is read on the device; size the grid from the bound
+    const int64_t G = (n + 15) / 16 + c->nclus;
     ForceConsts k = make_consts(c->p);
     float theta2, hg2;
     p3t_mac_constants(&c->p, &theta2, &hg2);
-    int blocks = (G + FW - 1) / FW;
+    int blocks = (int)((G + FW - 1) / FW);
     if (blocks > c->sms * 16) blocks = c->sms * 16;
     if (pot)
         k_walk_force<true><<<blocks, FW * 32, 0, s>>>(
-            G, c->grange, c->gmin, c->gmax, c->gctr, c->wmin, c->wmax, c->node,
-            theta2, hg2, c->phi, c->plo, c->cf0, c->cf1, c->cf2, c->order, n, k,
-            acc, pot, c->st);
+            c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
+            c->wmax, c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
+            c->order, n, k, acc, pot, c->st);
     else
         k_walk_force<false><<<blocks, FW * 32, 0, s>>>(
-            G, c->grange, c->gmin, c->gmax, c->gctr, c->wmin, c->wmax, c->node,
-            theta2, hg2, c->phi, c->plo, c->cf0, c->cf1, c->cf2, c->order, n, k,
-            acc, pot, c->st);
+            c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
+            c->wmax, c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
+            c->order, n, k, acc, pot, c->st);
     p3t_count_launches(1);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;

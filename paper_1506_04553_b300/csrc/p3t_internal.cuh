@@ -56,6 +56,18 @@ struct P3TEvents {
     int used, cap;
 };
 
+// Per-cluster constants of the force, neighbour and backward kernels (an
+// ensemble holds independent clusters; a plain build is one cluster).
+struct ClusterConsts {
+    float eps2;    // softening squared
+    float kA, kB;  // x = s * kA + kB = (s / r_cut - gamma) / (1 - gamma)
+    float hg2;     // guard of the opening test, fl(max(h, r_cut))^2 (1 + 2^-10)
+    double h;      // neighbour radius
+    double h2;     // h * h (exact FP64 predicate)
+    double r_out;  // r_cut
+    double w_in;   // W = w_in * y below r_in (potential)
+};
+
 struct p3t_ctx {
     p3t_params p;
     int device;
@@ -99,6 +111,19 @@ struct p3t_ctx {
     int64_t cap_cadj;
     // energy scratch
     double *red_part;
+    // clusters (one for a plain build)
+    int nclus, cap_clus;
+    int ensemble;            // layout fixed by p3t_set_ensemble
+    int64_t *clus_off_h;     // pinned host [nclus + 1]
+    ClusterConsts *cc_h;     // pinned host [nclus]
+    double *clus_par;        // host [3][nclus]: r_out, eps, h (ensemble)
+    int64_t *clus_off;       // device [nclus + 1]
+    ClusterConsts *cc;       // device [nclus]
+    double *clus_box;        // device [nclus][4]: lo xyz, side
+    int *pclus;              // device [cap_n]: cluster of each original index
+    int *gclus;              // device [cap_groups]: cluster of each group
+    int cap_pclus;
+    int no_sync;             // P3T_FLAG_NO_SYNC: build without host sync
     // profiling
     int prof_on;
     P3TEvents prof;
@@ -186,6 +211,9 @@ int p3t_scan_ll(p3t_ctx *c, const int *in, long long *out, int n,
                 cudaStream_t s);                                 // p3t_misc.cu
 int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
                      const double *mass);                       // p3t_tree.cu
+int p3t_sort_cluster_passes(p3t_ctx *c, int n, cudaStream_t s); // p3t_sort.cu
+void p3t_cluster_consts(const p3t_params *p, double r_out, double eps,
+                        double h, ClusterConsts *out);          // p3t_api.cu
 int p3t_run_walk(p3t_ctx *c, int fill, cudaStream_t s);        // p3t_walk.cu
 int p3t_scan_lists(p3t_ctx *c, cudaStream_t s);                 // p3t_walk.cu
 int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s);   // p3t_force.cu

@@ -85,13 +85,15 @@ __device__ __forceinline__ void ngb_tile(NgbSmem &S, float4 p0, float4 p1,
 
 template <bool FILL>
 __global__ void __launch_bounds__(NW * 32)
-k_ngb_walk(int G, const int2 *__restrict__ grange,
+k_ngb_walk(const int *__restrict__ gclus,
+           const ClusterConsts *__restrict__ ccs,
+           const int2 *__restrict__ grange,
            const float4 *__restrict__ gmin, const float4 *__restrict__ gmax,
            const float4 *__restrict__ gctr, const float4 *__restrict__ wmin,
            const float4 *__restrict__ wmax, const int4 *__restrict__ node,
-           float hg2, const float4 *__restrict__ phi,
+           const float4 *__restrict__ phi,
            const float4 *__restrict__ plo, const int *__restrict__ order,
-           const double *__restrict__ xs, int n, double h2,
+           const double *__restrict__ xs, int n,
            int *__restrict__ cnt, const long long *__restrict__ row_off,
            int *__restrict__ idx, long long cap, P3TDevState *st)
 {
@@ -99,6 +101,7 @@ k_ngb_walk(int G, const int2 *__restrict__ grange,
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
     NgbSmem &S = smem[w];
+    const int G = st->ngroup;
     for (;;) {
         int g = 0;
         if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
@@ -108,6 +111,9 @@ k_ngb_walk(int G, const int2 *__restrict__ grange,
         const float4 ct = gctr[g];
         const float4 gmn = gmin[g], gmx = gmax[g];
         const float hs2 = gmn.w;
+        const int cl = gclus[g];
+        const float hg2 = ccs[cl].hg2;
+        const double h2 = ccs[cl].h2;
         const int k0 = gr.x + lane, k1 = gr.x + 32 + lane;
         const bool v0 = lane < gr.y, v1 = lane + 32 < gr.y;
         const float4 p0 = v0 ? rel4n(phi[k0], plo[k0], ct) : make_float4(1e15f, 1e15f, 1e15f, 0.f);
@@ -119,7 +125,7 @@ k_ngb_walk(int G, const int2 *__restrict__ grange,
             if (v1) w1 = row_off[order[k1]];
         }
         int head = 0, nr = 0, np = 0;  // ring of near leaf ranges
-        if (lane == 0) S.stack[0] = 0;
+        if (lane == 0) S.stack[0] = cl * 8;  // the cluster's root
         int top = 1, iter = 0;
         bool bad = false;
         __syncwarp();
@@ -259,24 +265,20 @@ __global__ void k_work_reset(P3TDevState *st)
 int p3t_run_ngb(p3t_ctx *c, int fill, const long long *row_off, int *idx,
                 long long cap, cudaStream_t s)
 {
-    const int G = c->hst->ngroup;
     const int n = (int)c->n;
-    if (G == 0) return P3T_OK;
-    float theta2, hg2;
-    p3t_mac_constants(&c->p, &theta2, &hg2);
-    double h = c->p.h > 0.0 ? c->p.h : c->p.r_out;
-    int blocks = (G + NW - 1) / NW;
+    const int64_t G = (n + 15) / 16 + c->nclus;  // bound; the count is on the device
+    int blocks = (int)((G + NW - 1) / NW);
     if (blocks > c->sms * 16) blocks = c->sms * 16;
     k_work_reset<<<1, 32, 0, s>>>(c->st);
     if (fill)
         k_ngb_walk<true><<<blocks, NW * 32, 0, s>>>(
-            G, c->grange, c->gmin, c->gmax, c->gctr, c->wmin, c->wmax, c->node,
-            hg2, c->phi, c->plo, c->order, c->xs, n, h * h, c->ngb_cnt,
+            c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
+            c->wmax, c->node, c->phi, c->plo, c->order, c->xs, n, c->ngb_cnt,
             row_off, idx, cap, c->st);
     else
         k_ngb_walk<false><<<blocks, NW * 32, 0, s>>>(
-            G, c->grange, c->gmin, c->gmax, c->gctr, c->wmin, c->wmax, c->node,
-            hg2, c->phi, c->plo, c->order, c->xs, n, h * h, c->ngb_cnt,
+            c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
+            c->wmax, c->node, c->phi, c->plo, c->order, c->xs, n, c->ngb_cnt,
             row_off, idx, cap, c->st);
     p3t_count_launches(2);
     if (fill) {

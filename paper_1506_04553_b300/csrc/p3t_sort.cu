@@ -23,8 +23,20 @@ constexpr int RS_ROUNDS = 8;                       // per warp segment
 constexpr int RS_SEG = 32 * RS_ROUNDS;             // 256 keys per warp
 constexpr int RS_TILE = RS_WARPS * RS_SEG;         // 2048 keys per block
 
+// Digit of element i: a byte of its key, or (CL) a byte of the cluster of
+// its original index.
+template <bool CL>
+__device__ __forceinline__ int rs_digit(u64 key, int val,
+                                        const int *__restrict__ pclus,
+                                        int shift)
+{
+    return CL ? ((pclus[val] >> shift) & 255) : (int)((key >> shift) & 255u);
+}
+
+template <bool CL>
 __global__ void __launch_bounds__(RS_THREADS)
-rs_hist(int n, const u64 *__restrict__ keys, int shift, int ntiles,
+rs_hist(int n, const u64 *__restrict__ keys, const int *__restrict__ vals,
+        const int *__restrict__ pclus, int shift, int ntiles,
         int *__restrict__ counts)
 {
     __shared__ int hist[256];
@@ -34,7 +46,9 @@ rs_hist(int n, const u64 *__restrict__ keys, int shift, int ntiles,
 #pragma unroll
     for (int k = 0; k < RS_TILE / RS_THREADS; ++k) {
         int i = base + k * RS_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&hist[(int)((keys[i] >> shift) & 255u)], 1);
+        if (i < n)
+            atomicAdd(&hist[rs_digit<CL>(CL ? 0ull : keys[i], CL ? vals[i] : 0,
+                                         pclus, shift)], 1);
     }
     __syncthreads();
     counts[threadIdx.x * ntiles + blockIdx.x] = hist[threadIdx.x];
@@ -78,11 +92,12 @@ rs_scan(int ntiles, int *__restrict__ counts, int *__restrict__ totals)
     if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
+template <bool CL>
 __global__ void __launch_bounds__(RS_THREADS)
 rs_scatter(int n, const u64 *__restrict__ kin, const int *__restrict__ vin,
-           u64 *__restrict__ kout, int *__restrict__ vout, int shift,
-           int ntiles, const int *__restrict__ counts,
-           const int *__restrict__ totals)
+           u64 *__restrict__ kout, int *__restrict__ vout,
+           const int *__restrict__ pclus, int shift, int ntiles,
+           const int *__restrict__ counts, const int *__restrict__ totals)
 {
     __shared__ int tile_off[256];
     __shared__ int whist[RS_WARPS][256];
@@ -105,7 +120,7 @@ rs_scatter(int n, const u64 *__restrict__ kin, const int *__restrict__ vin,
         bool ok = i < n;
         k[r] = ok ? kin[i] : 0ull;
         v[r] = ok ? vin[i] : 0;
-        int d = ok ? (int)((k[r] >> shift) & 255u) : 256;
+        int d = ok ? rs_digit<CL>(k[r], v[r], pclus, shift) : 256;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int leader = __ffs(peers) - 1;
         int prior = ok ? whist[w][d] : 0;
@@ -151,12 +166,12 @@ int p3t_sort_keys(p3t_ctx *c, int n, cudaStream_t s)
     int *va = c->idx_a, *vb = c->idx_b;
     for (int pass = 0; pass < 8; ++pass) {
         int shift = 8 * pass;
-        rs_hist<<<ntiles, RS_THREADS, 0, s>>>(n, ka, shift, ntiles,
-                                               c->rs_counts);
+        rs_hist<false><<<ntiles, RS_THREADS, 0, s>>>(n, ka, va, nullptr, shift,
+                                                      ntiles, c->rs_counts);
         rs_scan<<<256, RS_THREADS, 0, s>>>(ntiles, c->rs_counts, c->rs_totals);
-        rs_scatter<<<ntiles, RS_THREADS, 0, s>>>(n, ka, va, kb, vb, shift,
-                                                  ntiles, c->rs_counts,
-                                                  c->rs_totals);
+        rs_scatter<false><<<ntiles, RS_THREADS, 0, s>>>(
+            n, ka, va, kb, vb, nullptr, shift, ntiles, c->rs_counts,
+            c->rs_totals);
         u64 *tk = ka; ka = kb; kb = tk;
         int *tv = va; va = vb; vb = tv;
     }
@@ -167,3 +182,35 @@ int p3t_sort_keys(p3t_ctx *c, int n, cudaStream_t s)
 }
 
 int64_t p3t_sort_tiles(int64_t n) { return (n + RS_TILE - 1) / RS_TILE; }
+
+// Stable passes on the cluster id (most significant), after the key passes:
+// the result is ordered by (cluster, key, original index).
+int p3t_sort_cluster_passes(p3t_ctx *c, int n, cudaStream_t s)
+{
+    int ntiles = (n + RS_TILE - 1) / RS_TILE;
+    if (ntiles > c->cap_tiles) return P3T_ERR_STATE;
+    int passes = 0;
+    for (long long v = (long long)c->nclus - 1; v > 0; v >>= 8) ++passes;
+    u64 *ka = c->key_a, *kb = c->key_b;
+    int *va = c->idx_a, *vb = c->idx_b;
+    for (int pass = 0; pass < passes; ++pass) {
+        int shift = 8 * pass;
+        rs_hist<true><<<ntiles, RS_THREADS, 0, s>>>(n, ka, va, c->pclus, shift,
+                                                     ntiles, c->rs_counts);
+        rs_scan<<<256, RS_THREADS, 0, s>>>(ntiles, c->rs_counts, c->rs_totals);
+        rs_scatter<true><<<ntiles, RS_THREADS, 0, s>>>(
+            n, ka, va, kb, vb, c->pclus, shift, ntiles, c->rs_counts,
+            c->rs_totals);
+        u64 *tk = ka; ka = kb; kb = tk;
+        int *tv = va; va = vb; vb = tv;
+    }
+    p3t_count_launches(3 * passes);
+    if (ka != c->key_a) {
+        P3T_CUDA_TRY(cudaMemcpyAsync(c->key_a, ka, (size_t)n * sizeof(u64),
+                                     cudaMemcpyDeviceToDevice, s));
+        P3T_CUDA_TRY(cudaMemcpyAsync(c->idx_a, va, (size_t)n * sizeof(int),
+                                     cudaMemcpyDeviceToDevice, s));
+    }
+    P3T_CUDA_TRY(cudaGetLastError());
+    return P3T_OK;
+}

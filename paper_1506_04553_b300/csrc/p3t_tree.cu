@@ -76,7 +76,8 @@ k_bbox_partial(int n, const double *__restrict__ pos,
 }
 
 __global__ void __launch_bounds__(TB)
-k_bbox_final(int nblk, const double *__restrict__ part, P3TDevState *st)
+k_bbox_final(int nblk, const double *__restrict__ part, P3TDevState *st,
+             double *__restrict__ clus_box)
 {
     double mn[3] = {INFINITY, INFINITY, INFINITY};
     double mx[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -110,8 +111,81 @@ k_bbox_final(int nblk, const double *__restrict__ part, P3TDevState *st)
         double e = __dsub_rn(v, u);
         if (e > ext) ext = e;
         st->lo[a] = u;
+        clus_box[a] = u;
     }
     st->size = (ext == 0.0) ? 1.0 : __dmul_rn(ext, 1.0 + 0x1p-20);
+    clus_box[3] = st->size;
+}
+
+// One block per cluster of an ensemble: root cube of [off[k], off[k+1])
+// (same rule as for a single cluster) and input validation.
+__global__ void __launch_bounds__(TB)
+k_bbox_seg(const long long *__restrict__ off, int n,
+           const double *__restrict__ pos, const double *__restrict__ mass,
+           double *__restrict__ clus_box, P3TDevState *st)
+{
+    const int k = blockIdx.x;
+    const int b = (int)off[k], e = (int)off[k + 1];
+    double mn[3] = {INFINITY, INFINITY, INFINITY};
+    double mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    bool bad = false;
+    for (int i = b + threadIdx.x; i < e; i += TB) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double v = pos[(size_t)a * n + i];
+            bad |= !isfinite(v);
+            mn[a] = fmin(mn[a], v);
+            mx[a] = fmax(mx[a], v);
+        }
+        double m = mass[i];
+        bad |= !(m > 0.0) || !isfinite(m);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) p3t_raise(st, P3T_ERR_INVALID);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    __shared__ double smn[3][TB / 32], smx[3][TB / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) {
+            smn[a][w] = mn[a];
+            smx[a][w] = mx[a];
+        }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double ext = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double u = smn[a][0], v = smx[a][0];
+        for (int q = 1; q < TB / 32; ++q) {
+            u = fmin(u, smn[a][q]);
+            v = fmax(v, smx[a][q]);
+        }
+        double d = __dsub_rn(v, u);
+        if (d > ext) ext = d;
+        clus_box[4 * k + a] = u;
+    }
+    clus_box[4 * k + 3] = (ext == 0.0) ? 1.0 : __dmul_rn(ext, 1.0 + 0x1p-20);
+}
+
+// Cluster of every particle (original index) of an ensemble.
+__global__ void __launch_bounds__(TB)
+k_cluster_ids(int n, int nc, const long long *__restrict__ off,
+              int *__restrict__ pclus)
+{
+    int i = blockIdx.x * TB + threadIdx.x;
+    if (i >= n) return;
+    int lo = 0, hi = nc;  // off[lo] <= i < off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= i)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    pclus[i] = lo;
 }
 
 // ---------------------------------------------------------------- keys ----
@@ -139,15 +213,17 @@ __device__ __forceinline__ u64 spread3(u64 v)
 }
 
 __global__ void __launch_bounds__(TB)
-k_keys(int n, const double *__restrict__ pos, const P3TDevState *st,
+k_keys(int n, const double *__restrict__ pos, int nc,
+       const int *__restrict__ pclus, const double *__restrict__ clus_box,
        u64 *__restrict__ key, int *__restrict__ idx)
 {
     int i = blockIdx.x * TB + threadIdx.x;
     if (i >= n) return;
-    const double size = st->size;
-    u64 qx = quantise(pos[i], st->lo[0], size);
-    u64 qy = quantise(pos[(size_t)n + i], st->lo[1], size);
-    u64 qz = quantise(pos[2 * (size_t)n + i], st->lo[2], size);
+    const double *bx = clus_box + 4 * (nc > 1 ? pclus[i] : 0);
+    const double size = bx[3];
+    u64 qx = quantise(pos[i], bx[0], size);
+    u64 qy = quantise(pos[(size_t)n + i], bx[1], size);
+    u64 qz = quantise(pos[2 * (size_t)n + i], bx[2], size);
     key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     idx[i] = i;
 }
@@ -178,18 +254,24 @@ k_gather(int n, const int *__restrict__ sidx, const double *__restrict__ pos,
 }
 
 // --------------------------------------------------------------- split ----
-__global__ void k_tree_init(int n, int4 *node, int *parent, P3TDevState *st)
+// One root per cluster: cells 0 .. nc-1 are the roots, in cluster order
+// (the sort keeps clusters contiguous and in order).
+__global__ void k_tree_init(int nc, const long long *__restrict__ off,
+                            int4 *node, int *parent, P3TDevState *st)
 {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nc;
+         k += gridDim.x * blockDim.x) {
+        node[k] = make_int4((int)off[k], (int)(off[k + 1] - off[k]), -1, 0);
+        parent[k] = -1;
+    }
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    node[0] = make_int4(0, n, -1, 0);
-    parent[0] = -1;
-    st->ncell = 1;
+    st->ncell = nc;
     st->ngroup = 0;
     st->max_level = 0;
     st->need_cells = 0;
     st->blocks_done = 0;
     st->level_start[0] = 0;
-    for (int L = 1; L < P3T_MAX_LEVEL + 3; ++L) st->level_start[L] = 1;
+    for (int L = 1; L < P3T_MAX_LEVEL + 3; ++L) st->level_start[L] = nc;
 }
 
 __device__ __forceinline__ int digit_at(u64 key, int L)
@@ -409,7 +491,7 @@ k_groups(int ng, int gcap, const int4 *__restrict__ node,
         const int4 nd = node[c];
         const bool small = nd.y <= cap || (nd.w & 255) == 0;
         if (!small) continue;
-        if (c != 0 && node[parent[c]].y <= cap) continue;
+        if (parent[c] >= 0 && node[parent[c]].y <= cap) continue;
         const int k = chunks(nd.y, ng);
         int slot = atomicAdd(&st->ngroup, k);
         if (slot + k > gcap) {
@@ -426,7 +508,9 @@ k_groups(int ng, int gcap, const int4 *__restrict__ node,
 // |x_i - x_j| < h has an FP32 group-relative r^2 below hs2.
 __global__ void __launch_bounds__(TB)
 k_group_box(const int2 *__restrict__ grange, const double *__restrict__ xs,
-            int n, double h, float4 *__restrict__ gmin,
+            int n, int nc, const int *__restrict__ order,
+            const int *__restrict__ pclus, const ClusterConsts *__restrict__ cc,
+            int *__restrict__ gclus, float4 *__restrict__ gmin,
             float4 *__restrict__ gmax, float4 *__restrict__ gctr,
             const P3TDevState *st)
 {
@@ -434,6 +518,9 @@ k_group_box(const int2 *__restrict__ grange, const double *__restrict__ xs,
     const int G = st->ngroup;  // <= capacity (k_groups checks)
     for (int g = blockIdx.x * TB + threadIdx.x; g < G; g += gridDim.x * TB) {
         int2 r = grange[g];
+        const int cl = nc > 1 ? pclus[order[r.x]] : 0;
+        gclus[g] = cl;
+        const double h = cc[cl].h;
         double mn[3] = {INFINITY, INFINITY, INFINITY};
         double mx[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int k = r.x; k < r.x + r.y; ++k)
@@ -475,14 +562,27 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     int nb = (n + TB - 1) / TB;
     int nbb = nb < grid_small ? nb : grid_small;
     if (nbb < 1) nbb = 1;
-    k_bbox_partial<<<nbb, TB, 0, s>>>(n, pos, mass, c->bbox_part, c->st);
-    k_bbox_final<<<1, TB, 0, s>>>(nbb, c->bbox_part, c->st);
-    k_keys<<<nb, TB, 0, s>>>(n, pos, c->st, c->key_a, c->idx_a);
+    const int nc = c->nclus;
+    const long long *off = (const long long *)c->clus_off;
+    if (nc == 1) {
+        k_bbox_partial<<<nbb, TB, 0, s>>>(n, pos, mass, c->bbox_part, c->st);
+        k_bbox_final<<<1, TB, 0, s>>>(nbb, c->bbox_part, c->st, c->clus_box);
+    } else {
+        k_bbox_seg<<<nc, TB, 0, s>>>(off, n, pos, mass, c->clus_box, c->st);
+        k_cluster_ids<<<nb, TB, 0, s>>>(n, nc, off, c->pclus);
+    }
+    k_keys<<<nb, TB, 0, s>>>(n, pos, nc, c->pclus, c->clus_box, c->key_a,
+                             c->idx_a);
     int rc = p3t_sort_keys(c, n, s);
     if (rc) return rc;
+    if (nc > 1) {
+        rc = p3t_sort_cluster_passes(c, n, s);
+        if (rc) return rc;
+    }
     k_gather<<<nb, TB, 0, s>>>(n, c->idx_a, pos, mass, c->order, c->xs, c->ms,
                                c->phi, c->plo);
-    k_tree_init<<<1, 32, 0, s>>>(n, c->node, c->parent, c->st);
+    k_tree_init<<<(nc + 255) / 256, 256, 0, s>>>(nc, off, c->node, c->parent,
+                                                 c->st);
     const int cap = (int)c->cap_cells;
     for (int L = 0; L < P3T_MAX_LEVEL; ++L)
         k_tree_split<<<grid_small, TB, 0, s>>>(L, c->p.n_leaf, cap, c->key_a,
@@ -494,8 +594,8 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
                                              c->cf0, c->cf1, c->cf2, c->st);
     k_groups<<<grid_small, TB, 0, s>>>(c->p.n_group, (int)c->cap_groups,
                                         c->node, c->parent, c->grange, c->st);
-    double h = c->p.h > 0.0 ? c->p.h : c->p.r_out;
-    k_group_box<<<grid_small, TB, 0, s>>>(c->grange, c->xs, n, h, c->gmin,
+    k_group_box<<<grid_small, TB, 0, s>>>(c->grange, c->xs, n, nc, c->order,
+                                           c->pclus, c->cc, c->gclus, c->gmin,
                                            c->gmax, c->gctr, c->st);
     // bbox 2, keys, gather, init, 21 splits, 22 moment levels, groups, boxes
     p3t_count_launches(2 + 1 + 1 + 1 + P3T_MAX_LEVEL + (P3T_MAX_LEVEL + 1) + 2);

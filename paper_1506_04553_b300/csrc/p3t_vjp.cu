@@ -233,11 +233,13 @@ struct VjpEval {
 };
 
 __global__ void __launch_bounds__(VW * 32)
-k_walk_vjp(int G, const int2 *__restrict__ grange,
+k_walk_vjp(const int *__restrict__ gclus,
+           const ClusterConsts *__restrict__ ccs,
+           const int2 *__restrict__ grange,
            const float4 *__restrict__ gmin, const float4 *__restrict__ gmax,
            const float4 *__restrict__ gctr, const float4 *__restrict__ wmin,
            const float4 *__restrict__ wmax, const int4 *__restrict__ node,
-           float theta2, float hg2, const float4 *__restrict__ phi,
+           float theta2, const float4 *__restrict__ phi,
            const float4 *__restrict__ plo, const float4 *__restrict__ cf0,
            const float4 *__restrict__ cf1, const float4 *__restrict__ cf2,
            const int *__restrict__ order, int n, VjpConsts k,
@@ -248,12 +250,15 @@ k_walk_vjp(int G, const int2 *__restrict__ grange,
     __shared__ Smem smem[VW];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Smem &S = smem[wi];
+    const int G = st->ngroup;
     for (;;) {
         int g = 0;
         if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= G) break;
         const int2 gr = grange[g];
+        const int cl = gclus[g];
+        const ClusterConsts cc = ccs[cl];
         VjpEval ev;
         ev.ct = gctr[g];
         ev.k0 = gr.x + lane;
@@ -279,9 +284,12 @@ k_walk_vjp(int G, const int2 *__restrict__ grange,
         ev.n = n;
         ev.lane = lane;
         ev.k = k;
+        ev.k.eps2 = cc.eps2;
+        ev.k.kA = cc.kA;
+        ev.k.kB = cc.kB;
         long long cnt[3] = {0, 0, 0};
         if (!p3t_walk::walk_group(S, gmin[g], gmax[g], wmin, wmax, node,
-                                  theta2, hg2, lane, ev, cnt)) {
+                                  theta2, cc.hg2, cl, lane, ev, cnt)) {
             if (lane == 0) p3t_raise(st, P3T_ERR_CAPACITY);
             continue;
         }
@@ -298,7 +306,8 @@ k_walk_vjp(int G, const int2 *__restrict__ grange,
 // particles, FP64; one thread per particle (sorted id k) walks from the root
 // down to its leaf.
 __global__ void __launch_bounds__(256)
-k_vjp_push(int n, const int4 *__restrict__ node, const double *__restrict__ cM,
+k_vjp_push(int n, int nc, const long long *__restrict__ off,
+           const int4 *__restrict__ node, const double *__restrict__ cM,
            const double *__restrict__ ccom, const double *__restrict__ xs,
            const double *__restrict__ ms, const int *__restrict__ order,
            const double *__restrict__ cadj, double *__restrict__ gpos,
@@ -309,7 +318,18 @@ k_vjp_push(int n, const int4 *__restrict__ node, const double *__restrict__ cM,
     const double x[3] = {xs[kk], xs[(size_t)n + kk], xs[2 * (size_t)n + kk]};
     const double mk = ms[kk];
     double gx[3] = {0.0, 0.0, 0.0}, gm = 0.0;
-    int c = 0;
+    int c = 0;  // root of the particle's cluster (sorted order keeps clusters)
+    if (nc > 1) {
+        int lo = 0, hi = nc;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (off[mid] <= kk)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        c = lo;
+    }
     for (int depth = 0; depth <= P3T_MAX_LEVEL; ++depth) {
         const double *A = cadj + (size_t)c * 10;
         bool any = false;
@@ -360,12 +380,11 @@ int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,
                 double *cadj, cudaStream_t s)
 {
     const int n = (int)c->n;
-    const int G = c->hst->ngroup;
-    const int C = c->hst->ncell;
+    const int64_t G = (n + 15) / 16 + c->nclus;  // bound; the count is on the device
+    const int64_t C = c->cap_cells;
     P3T_CUDA_TRY(cudaMemsetAsync(gpos, 0, sizeof(double) * 3 * (size_t)n, s));
     P3T_CUDA_TRY(cudaMemsetAsync(gmass, 0, sizeof(double) * (size_t)n, s));
     P3T_CUDA_TRY(cudaMemsetAsync(cadj, 0, sizeof(double) * 10 * (size_t)C, s));
-    if (G == 0) return P3T_OK;
     float theta2, hg2;
     p3t_mac_constants(&c->p, &theta2, &hg2);
     VjpConsts k;
@@ -373,14 +392,17 @@ int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,
     k.kA = (float)(1.0 / ((1.0 - c->p.gamma) * c->p.r_out));
     k.kB = (float)(-c->p.gamma / (1.0 - c->p.gamma));
     k.G = c->p.G;
-    int blocks = (G + VW - 1) / VW;
+    int blocks = (int)((G + VW - 1) / VW);
     if (blocks > c->sms * 16) blocks = c->sms * 16;
     k_vjp_reset<<<1, 32, 0, s>>>(c->st);
     k_walk_vjp<<<blocks, VW * 32, 0, s>>>(
-        G, c->grange, c->gmin, c->gmax, c->gctr, c->wmin, c->wmax, c->node,
-        theta2, hg2, c->phi, c->plo, c->cf0, c->cf1, c->cf2, c->order, n, k, w,
+        c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
+        c->wmax, c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
+        c->order, n, k, w,
         gpos, gmass, cadj, c->st);
-    k_vjp_push<<<(n + 255) / 256, 256, 0, s>>>(n, c->node, c->cM, c->ccom,
+    k_vjp_push<<<(n + 255) / 256, 256, 0, s>>>(n, c->nclus,
+                                               (const long long *)c->clus_off,
+                                               c->node, c->cM, c->ccom,
                                                c->xs, c->ms, c->order, cadj,
                                                gpos, gmass);
     p3t_count_launches(3);

@@ -33,10 +33,11 @@ constexpr int WALK_STACK = 1024;
 
 template <bool FILL>
 __global__ void __launch_bounds__(WALK_WARPS * 32)
-k_walk(int ngroup, const int2 *__restrict__ grange,
+k_walk(int ngroup, const int *__restrict__ gclus,
+       const ClusterConsts *__restrict__ ccs, const int2 *__restrict__ grange,
        const float4 *__restrict__ gmin, const float4 *__restrict__ gmax,
        const float4 *__restrict__ wmin, const float4 *__restrict__ wmax,
-       const int4 *__restrict__ node, float theta2, float hg2,
+       const int4 *__restrict__ node, float theta2,
        long long *__restrict__ cnt, const long long *__restrict__ off,
        int *__restrict__ pc_list, int *__restrict__ ppn_list,
        int *__restrict__ ppf_list, P3TDevState *st)
@@ -50,6 +51,8 @@ k_walk(int ngroup, const int2 *__restrict__ grange,
     for (int g = blockIdx.x * WALK_WARPS + w; g < ngroup;
          g += gridDim.x * WALK_WARPS) {
         const float4 gmn = gmin[g], gmx = gmax[g];
+        const int cl = gclus[g];
+        const float hg2 = ccs[cl].hg2;
         long long npc = 0, nppn = 0, nppf = 0;
         long long o_pc = 0, o_ppn = 0, o_ppf = 0;
         if (FILL) {
@@ -57,7 +60,7 @@ k_walk(int ngroup, const int2 *__restrict__ grange,
             o_ppn = off[(ngroup + 1) + g];
             o_ppf = off[2 * (ngroup + 1) + g];
         }
-        if (lane == 0) stk[0] = make_int2(0, 1);  // the root
+        if (lane == 0) stk[0] = make_int2(cl, 1);  // the cluster's root
         int top = 1;
         bool overflow = false;
         int iter = 0;
@@ -236,12 +239,14 @@ int p3t_run_walk(p3t_ctx *c, int fill, cudaStream_t s)
     if (blocks > maxb) blocks = maxb;
     if (fill)
         k_walk<true><<<blocks, WALK_WARPS * 32, 0, s>>>(
-            G, c->grange, c->gmin, c->gmax, c->wmin, c->wmax, c->node, theta2,
-            hg2, c->lcnt, c->loff, c->list[0], c->list[1], c->list[2], c->st);
+            G, c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->wmin, c->wmax,
+            c->node, theta2, c->lcnt, c->loff, c->list[0], c->list[1],
+            c->list[2], c->st);
     else
         k_walk<false><<<blocks, WALK_WARPS * 32, 0, s>>>(
-            G, c->grange, c->gmin, c->gmax, c->wmin, c->wmax, c->node, theta2,
-            hg2, c->lcnt, c->loff, c->list[0], c->list[1], c->list[2], c->st);
+            G, c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->wmin, c->wmax,
+            c->node, theta2, c->lcnt, c->loff, c->list[0], c->list[1],
+            c->list[2], c->st);
     p3t_count_launches(1);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;

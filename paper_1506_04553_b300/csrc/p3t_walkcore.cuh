@@ -86,7 +86,8 @@ __device__ __forceinline__ void take_cells(Smem &S, CellRing &r, int take,
     r.n -= take;
 }
 
-// Walks the tree for one group.  The evaluator supplies
+// Walks the tree of cell `root` (the group's cluster) for one group.  The
+// evaluator supplies
 //   ev.cells(S, take)            tile of `take` cells, ids in S.tj
 //   ev.particles<NEAR>(S, take)  tile of `take` particles, ids in S.tj
 // Returns false when the stack overflowed (the group is left unfinished).
@@ -95,12 +96,12 @@ template <class Ev>
 __device__ __forceinline__ bool walk_group(
     Smem &S, float4 gmn, float4 gmx, const float4 *__restrict__ wmin,
     const float4 *__restrict__ wmax, const int4 *__restrict__ node,
-    float theta2, float hg2, int lane, Ev &ev, long long cnt[3])
+    float theta2, float hg2, int root, int lane, Ev &ev, long long cnt[3])
 {
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
     CellRing rc = {0, 0};
     RangeRing rf = {0, 0, 0}, rn = {0, 0, 0};
-    if (lane == 0) S.stack[0] = 0;  // the root: child 0, one cell
+    if (lane == 0) S.stack[0] = root * 8;  // the group's root, one cell
     int top = 1;
     int iter = 0;
     __syncwarp();
