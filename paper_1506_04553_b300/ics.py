@@ -147,3 +147,21 @@ def king(n: int, seed: int, W0: float = 9.0, masses=None):
     pos *= a
     vel /= math.sqrt(Mtot * a)
     return pos, vel, mass
+
+
+def plummer_ensemble(n_clusters: int, seed: int, n_min: int = 1024,
+                     n_max: int = 65536):
+    """Independent Plummer clusters (each in N-body units, total mass 1,
+    centred on the origin) of N_c = round(exp(U[ln n_min, ln n_max]))
+    particles, cluster c seeded with seed + c.  Returns (pos (3, N),
+    vel (3, N), mass (N,), offsets (n_clusters + 1,))."""
+    rng = np.random.default_rng(seed)
+    sizes = np.rint(np.exp(rng.uniform(math.log(n_min), math.log(n_max),
+                                       n_clusters))).astype(np.int64)
+    off = np.zeros(n_clusters + 1, np.int64)
+    np.cumsum(sizes, out=off[1:])
+    parts = [plummer(int(sz), seed + 1 + c) for c, sz in enumerate(sizes)]
+    pos = np.concatenate([p[0] for p in parts], axis=1)
+    vel = np.concatenate([p[1] for p in parts], axis=1)
+    mass = np.concatenate([p[2] for p in parts])
+    return pos, vel, mass, off
