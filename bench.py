@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     return ap.parse_args()
 
 
@@ -403,6 +404,8 @@ def run_ours(args, world, rank, local):
                        "h2d_bytes_per_step": 7 * 8 * n,
                        "d2h_bytes_per_step": 6 * 8 * n + 8 * (n + 1) + 4 * nnz_last[0],
                        "ms_per_step": te * 1e3}
+    if not args.no_ensemble:
+        line["ensemble"] = run_ensemble(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_step, desc = oracle_sample(pos_h, mass_h, frac=1 / 16)
         line["cpu_baseline"] = {"value": n / t_step, "unit": "particles/s",
@@ -412,6 +415,71 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_ensemble(args, dev):
+    """256 independent Plummer clusters, N_c log-uniform in [1024, 65536],
+    r_out = 0.01 (N_c / 8192)^(-1/3), eps = 4 / N_c, theta 0.4.  One step =
+    tree build + force + backward (gradient of sum w.a) for all clusters,
+    group/leaf sizes from the autotuner, the step captured once in a CUDA
+    graph and replayed."""
+    import torch
+    import paper_1506_04553_b300 as P
+    from paper_1506_04553_b300 import ics
+    pos_h, _, m_h, off = ics.plummer_ensemble(256, seed=5000)
+    n = int(off[-1])
+    sizes = np.diff(off)
+    r_out = 0.01 * (sizes / 8192.0) ** (-1.0 / 3.0)
+    eps = 4.0 / sizes
+    ctx = P.Context(P.Params(theta=THETA, gamma=GAMMA))
+    ctx.set_ensemble(off, r_out=r_out, eps=eps)
+    pos = torch.tensor(pos_h, device=dev)
+    mass = torch.tensor(m_h, device=dev)
+    ng, nl, tune_ms = ctx.autotune(pos, mass, reps=2)
+    acc = torch.empty((3, n), dtype=torch.float32, device=dev)
+    w = torch.randn((3, n), dtype=torch.float32, device=dev,
+                    generator=torch.Generator(device=dev).manual_seed(41))
+    gx = torch.empty((3, n), dtype=torch.float64, device=dev)
+    gm = torch.empty((n,), dtype=torch.float64, device=dev)
+    ctx.build_tree(pos, mass)
+    ctx.long_force(acc)
+    ctx.long_force_vjp(w, gx, gm)
+    p = ctx.params
+    ctx.set_params(P.Params(theta=THETA, gamma=GAMMA, n_group=p.n_group,
+                            n_leaf=p.n_leaf, flags=P.FLAG_NO_SYNC))
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        ctx.build_tree(pos, mass)
+        ctx.long_force(acc, check=False)
+        ctx.long_force_vjp(w, gx, gm, check=False)
+    torch.cuda.current_stream(dev).wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ctx.build_tree(pos, mass)
+        ctx.long_force(acc, check=False)
+        ctx.long_force_vjp(w, gx, gm, check=False)
+    for _ in range(max(args.warmup, 3)):
+        g.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    k = max(args.steps // 2, 4)
+    e0.record(stream)
+    for _ in range(k):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = e0.elapsed_time(e1) / k
+    return {"workload": "256 Plummer clusters, N_c log-uniform in [1024, 65536], "
+                        "theta 0.4, r_out 0.01 (N_c/8192)^(-1/3), eps 4/N_c",
+            "n": n, "clusters": 256, "step": "build + force + backward, "
+            "one CUDA graph, one walk+force launch for all clusters",
+            "value": n / (ms * 1e-3), "unit": "particles/s (fwd+bwd)",
+            "ms_per_step": ms, "autotuned": {"n_group": ng, "n_leaf": nl,
+                                             "build_force_ms": tune_ms}}
 
 
 def main():

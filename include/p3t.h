@@ -117,6 +117,18 @@ int p3t_build_tree(p3t_ctx *ctx, int64_t n, const double *pos,
 int p3t_set_ensemble(p3t_ctx *ctx, int32_t n_clusters, const int64_t *off,
                      const double *r_out, const double *eps, const double *h);
 
+/* Autotuner: times p3t_build_tree + p3t_long_force (best of `reps`) for
+ * n_group in {32, 48, 64} and n_leaf in {8, 16, 32} on the given particles
+ * and keeps the fastest pair in the context's parameters (the tree is left
+ * built with it).  The pair changes which cells are opened, not the
+ * accuracy target: every pair satisfies the same opening test.
+ *   acc : device float[3][n] scratch.
+ * Must not be called with P3T_FLAG_NO_SYNC set (it synchronises).
+ * Errors: P3T_ERR_INVALID, P3T_ERR_STATE, and those of the timed calls. */
+int p3t_autotune(p3t_ctx *ctx, int64_t n, const double *pos,
+                 const double *mass, float *acc, int reps, void *stream,
+                 int32_t *best_n_group, int32_t *best_n_leaf, double *best_ms);
+
 /* Long-range acceleration a_soft (Eq. 8) of every particle by the tree.
  *   acc : device, float[3][n] (SoA), written in the caller's order
  *   pot : device, double[n] or NULL; if given, the soft potential

@@ -96,6 +96,7 @@ _sigs = {
     "p3t_check": [_vp, _vp],
     "p3t_long_force_vjp": [_vp, _vp, _vp, _vp, _vp],
     "p3t_set_ensemble": [_vp, C.c_int32, _vp, _vp, _vp, _vp],
+    "p3t_autotune": [_vp, _i64, _vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp],
     "p3t_get_profile": [_vp, _vp, C.c_int],
 }
 for _name, _args in _sigs.items():
@@ -204,6 +205,23 @@ class Context:
             *[None if a is None else _np_ptr(a) for a in arrs]),
             "p3t_set_ensemble")
         self._ens = (off, arrs)  # keep the host arrays alive
+
+    def autotune(self, pos, mass, reps=2, stream=None):
+        """Time build + force for n_group in {32, 48, 64} x n_leaf in
+        {8, 16, 32}; keep the fastest (returns (n_group, n_leaf, ms))."""
+        import torch
+        n = int(mass.shape[0])
+        acc = torch.empty((3, n), dtype=torch.float32, device="cuda")
+        bg, bl, bm = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+        _check(_lib.p3t_autotune(
+            self._h, n, _dptr(pos, torch.float64, (3, n), "pos"),
+            _dptr(mass, torch.float64, (n,), "mass"), C.c_void_p(acc.data_ptr()),
+            reps, _stream(stream), C.byref(bg), C.byref(bl), C.byref(bm)),
+            "p3t_autotune")
+        self.params.n_group, self.params.n_leaf = int(bg.value), int(bl.value)
+        self.n = n
+        self.build_id = getattr(self, "build_id", 0) + 1
+        return int(bg.value), int(bl.value), float(bm.value)
 
     # ---- hot path ----
     def build_tree(self, pos, mass, stream=None):

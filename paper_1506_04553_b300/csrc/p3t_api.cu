@@ -758,3 +758,58 @@ const char *p3t_status_string(int s)
 }
 
 }  // extern "C"
+
+// ---- autotuning of the group and leaf sizes --------------------------------
+extern "C" int p3t_autotune(p3t_ctx *c, int64_t n, const double *pos,
+                            const double *mass, float *acc, int reps,
+                            void *stream, int32_t *best_n_group,
+                            int32_t *best_n_leaf, double *best_ms)
+{
+    if (!c || n <= 0 || !pos || !mass || !acc || reps < 1) return P3T_ERR_INVALID;
+    if (c->p.flags & P3T_FLAG_NO_SYNC) return P3T_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    static const int groups[] = {32, 48, 64};
+    static const int leaves[] = {8, 16, 32};
+    const p3t_params keep = c->p;
+    cudaEvent_t e0, e1;
+    P3T_CUDA_TRY(cudaEventCreate(&e0));
+    P3T_CUDA_TRY(cudaEventCreate(&e1));
+    double best = 1e300;
+    int bg = keep.n_group, bl = keep.n_leaf;
+    int rc = P3T_OK;
+    for (int gi = 0; gi < 3 && rc == P3T_OK; ++gi)
+        for (int li = 0; li < 3 && rc == P3T_OK; ++li) {
+            c->p.n_group = groups[gi];
+            c->p.n_leaf = leaves[li];
+            // one untimed evaluation sizes every buffer
+            rc = p3t_build_tree(c, n, pos, mass, stream);
+            if (rc == P3T_OK) rc = p3t_long_force(c, acc, nullptr, stream);
+            if (rc != P3T_OK) break;
+            double t = 1e300;
+            for (int r = 0; r < reps && rc == P3T_OK; ++r) {
+                cudaEventRecord(e0, s);
+                rc = p3t_build_tree(c, n, pos, mass, stream);
+                if (rc == P3T_OK) rc = p3t_long_force(c, acc, nullptr, stream);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = P3T_ERR_CUDA;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < t) t = ms;
+            }
+            if (rc == P3T_OK && t < best) {
+                best = t;
+                bg = groups[gi];
+                bl = leaves[li];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->p = keep;
+    c->p.n_group = bg;
+    c->p.n_leaf = bl;
+    if (rc == P3T_OK) rc = p3t_build_tree(c, n, pos, mass, stream);
+    if (best_n_group) *best_n_group = bg;
+    if (best_n_leaf) *best_n_leaf = bl;
+    if (best_ms) *best_ms = best;
+    return rc;
+}
