@@ -58,6 +58,55 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// Warp reduce-scatter of NS sources x NV values held by every lane: after
+// the call a[0][0..NV) of lane l holds the warp-wide totals of source
+// src_of<NS>(l); the 32/NS lanes sharing that source hold the same totals.
+// log2(NS) levels exchange half of the remaining sources with a partner,
+// the remaining levels are a butterfly over NV values.
+template <int NS>
+__device__ __forceinline__ int src_of(int lane)
+{
+    int s = 0;
+#pragma unroll
+    for (int b = 0; (1 << b) < NS; ++b) s = 2 * s + ((lane >> (4 - b)) & 1);
+    return s;
+}
+
+template <int NS, int NV>
+__device__ __forceinline__ void reduce_scatter(float (&a)[NS][NV], int lane)
+{
+#pragma unroll
+    for (int b = 0; (1 << b) < NS; ++b) {
+        const int mask = 16 >> b;
+        const int half = NS >> (b + 1);
+        const bool upper = (lane & mask) != 0;
+#pragma unroll
+        for (int q = 0; q < half; ++q)
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const float lo = a[q][v], hi = a[q + half][v];
+                const float send = upper ? lo : hi;
+                const float keep = upper ? hi : lo;
+                a[q][v] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+            }
+    }
+#pragma unroll
+    for (int mask = 16 / NS; mask > 0; mask >>= 1)
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            a[0][v] += __shfl_xor_sync(0xffffffffu, a[0][v], mask);
+}
+
+// Value v of a[0] without dynamic register indexing.
+template <int NV>
+__device__ __forceinline__ float pick(const float (&a)[NV], int v)
+{
+    float r = a[0];
+#pragma unroll
+    for (int q = 1; q < NV; ++q) r = (v == q) ? a[q] : r;
+    return r;
+}
+
 // Per-lane state of one group: two particles per lane.
 struct VjpEval {
     float4 p0, p1;        // group-relative positions
@@ -85,20 +134,26 @@ struct VjpEval {
         }
         __syncwarp();
         float s0[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f};
-        for (int j = 0; j < take; ++j) {
-            const float4 a = S.t0[j], B = S.t1[j], Cq = S.t2[j];
-            float acc[10];
+        constexpr int NS = 2, NV = 10, LPS = 32 / NS;
+        for (int j = 0; j < take; j += NS) {
+            float acc[NS][NV];
 #pragma unroll
-            for (int q = 0; q < 10; ++q) acc[q] = 0.f;
-            cell_one(a, B, Cq, p0, w0, s0, acc);
-            cell_one(a, B, Cq, p1, w1, s1, acc);
+            for (int u = 0; u < NS; ++u) {
 #pragma unroll
-            for (int q = 0; q < 10; ++q) acc[q] = warp_sum(acc[q]);
-            float v = acc[0];
-#pragma unroll
-            for (int q = 1; q < 10; ++q) v = (lane == q) ? acc[q] : v;
-            if (lane < 10)
-                atomicAdd(&cadj[(size_t)S.tj[j] * 10 + lane], k.G * (double)v);
+                for (int q = 0; q < NV; ++q) acc[u][q] = 0.f;
+                if (j + u < take) {
+                    const float4 a = S.t0[j + u], B = S.t1[j + u], Cq = S.t2[j + u];
+                    cell_one(a, B, Cq, p0, w0, s0, acc[u]);
+                    cell_one(a, B, Cq, p1, w1, s1, acc[u]);
+                }
+            }
+            reduce_scatter<NS, NV>(acc, lane);
+            const int src = j + src_of<NS>(lane);
+            if (src < take) {
+                const size_t base = (size_t)S.tj[src] * 10;
+                for (int v = lane & (LPS - 1); v < NV; v += LPS)
+                    atomicAdd(&cadj[base + v], k.G * (double)pick<NV>(acc[0], v));
+            }
         }
         for (int q = 0; q < 3; ++q) {
             g0[q] += (double)s0[q];
@@ -165,21 +220,27 @@ struct VjpEval {
         }
         __syncwarp();
         float s0[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f};
-        for (int j = 0; j < take; ++j) {
-            const float4 a = S.t0[j];
-            const int kj = S.tj[j];
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            pair_one<NEAR>(a, kj == k0, p0, w0, s0, acc);
-            pair_one<NEAR>(a, kj == k1, p1, w1, s1, acc);
+        constexpr int NS = 8, NV = 4;
+        for (int j = 0; j < take; j += NS) {
+            float acc[NS][NV];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = warp_sum(acc[q]);
-            float v = acc[0];
+            for (int u = 0; u < NS; ++u) {
 #pragma unroll
-            for (int q = 1; q < 4; ++q) v = (lane == q) ? acc[q] : v;
-            if (lane < 4) {
-                const int o = order[kj];
-                double *dst = lane < 3 ? gpos + (size_t)lane * n + o : gmass + o;
-                atomicAdd(dst, k.G * (double)v);
+                for (int q = 0; q < NV; ++q) acc[u][q] = 0.f;
+                if (j + u < take) {
+                    const float4 a = S.t0[j + u];
+                    const int kj = S.tj[j + u];
+                    pair_one<NEAR>(a, kj == k0, p0, w0, s0, acc[u]);
+                    pair_one<NEAR>(a, kj == k1, p1, w1, s1, acc[u]);
+                }
+            }
+            reduce_scatter<NS, NV>(acc, lane);
+            const int src = j + src_of<NS>(lane);
+            if (src < take) {
+                const int v = lane & 3;  // 32 / NS = 4 lanes per source
+                const int o = order[S.tj[src]];
+                double *dst = v < 3 ? gpos + (size_t)v * n + o : gmass + o;
+                atomicAdd(dst, k.G * (double)pick<NV>(acc[0], v));
             }
         }
         for (int q = 0; q < 3; ++q) {
