@@ -385,7 +385,7 @@ int p3t_build_tree(p3t_ctx *c, int64_t n, const double *pos,
     }
     if (no_sync) {
         // nothing may be allocated or waited for: capacities must suffice
-        if (n > c->cap_n || c->cap_cells < n / 2 + 64) return P3T_ERR_CAPACITY;
+        if (n > c->cap_n || c->cap_cells == 0) return P3T_ERR_CAPACITY;
     } else {
         P3T_TRY(ensure_particles(c, n));
         if (c->cap_cells < n / 2 + 64) P3T_TRY(ensure_cells(c, n / 2 + 64));
