@@ -30,6 +30,11 @@ namespace {
 
 constexpr int FW = 4;  // warps (groups in flight) per block
 
+#ifndef P3T_PC_UNROLL
+#define P3T_PC_UNROLL 8
+#endif
+constexpr int kPcUnroll = P3T_PC_UNROLL;  // unroll of the cell-tile loop
+
 struct ForceConsts {
     float eps2;    // eps^2
     float kA, kB;  // x = s * kA + kB = (s / r_cut - gamma) / (1 - gamma)
@@ -183,6 +188,11 @@ __device__ __forceinline__ float4 rel4(float4 hi, float4 lo, float4 c)
 }
 
 
+// Resident blocks per SM the force kernel's registers are sized for (0: let
+// the compiler choose).
+#ifndef P3T_FORCE_MIN_BLOCKS
+#define P3T_FORCE_MIN_BLOCKS 0
+#endif
 constexpr int FSTACK = 768;  // walk stack entries per warp (child ranges)
 constexpr int RING = 64;     // ring capacity (entries); never more than 63 used
 
@@ -273,7 +283,7 @@ __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
     __syncwarp();
     float tx0 = 0.f, ty0 = 0.f, tz0 = 0.f, tx1 = 0.f, ty1 = 0.f, tz1 = 0.f,
           tp0 = 0.f, tp1 = 0.f;
-#pragma unroll 8
+#pragma unroll kPcUnroll
     for (int j = 0; j < 32; ++j) {
         const float4 a = S.t0[j], bq = S.t1[j], cq = S.t2[j];
         pc_term(p0.x, p0.y, p0.z, a, bq, cq, eps2, tx0, ty0, tz0);
@@ -347,7 +357,7 @@ __device__ __forceinline__ void particle_tile(
 }
 
 template <bool POT>
-__global__ void __launch_bounds__(FW * 32)
+__global__ void __launch_bounds__(FW * 32, P3T_FORCE_MIN_BLOCKS)
 k_walk_force(const int *__restrict__ gclus,
              const ClusterConsts *__restrict__ ccs,
              const int2 *__restrict__ grange,

@@ -293,6 +293,59 @@ __device__ __forceinline__ int lower_digit(const u64 *__restrict__ key, int lo,
     return lo;
 }
 
+// Same as lower_digit, by a whole warp: 32 probes per step (the range
+// shrinks 32-fold per dependent load instead of 2-fold).
+__device__ __forceinline__ int warp_lower_digit(const u64 *__restrict__ key,
+                                                int lo, int hi, int L, int d,
+                                                int lane)
+{
+    while (hi - lo > 32) {
+        const int step = (hi - lo + 31) / 32;
+        const int p = lo + lane * step;
+        const bool ge = p < hi && digit_at(key[p], L) >= d;
+        const unsigned m = __ballot_sync(0xffffffffu, ge);
+        const int f = m ? __ffs(m) - 1 : 32;  // first probe with digit >= d
+        const int lastv = (hi - 1 - lo) / step;  // last probe inside [lo, hi)
+        const int nlo = f == 0 ? lo : lo + min(f - 1, lastv) * step + 1;
+        const int nhi = f == 32 ? hi : min(hi, lo + f * step);
+        lo = nlo;
+        hi = nhi;
+    }
+    const int p = lo + lane;
+    const bool ge = p < hi && digit_at(key[p], L) >= d;
+    const unsigned m = __ballot_sync(0xffffffffu, ge);
+    return m ? lo + __ffs(m) - 1 : hi;
+}
+
+// Children of one cell (boundaries b[0..8]) appended to the cell arrays.
+__device__ __forceinline__ void emit_children(int c, int L, int cap,
+                                              const int *b, int4 *node,
+                                              int *parent, P3TDevState *st)
+{
+    int k = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) k += b[d + 1] > b[d];
+    int base = atomicAdd(&st->ncell, k);
+    if (base + k > cap) {
+        p3t_raise(st, P3T_ERR_CAPACITY);
+        atomicMax(&st->need_cells, base + k);
+        return;
+    }
+    int j = 0;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+        if (b[d + 1] > b[d]) {
+            node[base + j] = make_int4(b[d], b[d + 1] - b[d], -1, (L + 1) << 8);
+            parent[base + j] = c;
+            ++j;
+        }
+    }
+    node[c].z = base;
+    node[c].w = (L << 8) | k;
+}
+
+constexpr int BIG_CELL = 2048;  // cells split by a whole warp
+
 __global__ void __launch_bounds__(TB)
 k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
              int4 *__restrict__ node, int *__restrict__ parent,
@@ -300,37 +353,33 @@ k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
 {
     const int beg = st->level_start[L], end = st->level_start[L + 1];
     const bool stop = st->error != 0;
+    // big cells: one warp each
+    {
+        const int lane = threadIdx.x & 31;
+        const int wg = (blockIdx.x * TB + threadIdx.x) >> 5;
+        const int nw = gridDim.x * (TB / 32);
+        for (int c = beg + wg; c < end && !stop; c += nw) {
+            const int4 nd = node[c];
+            if (nd.y <= BIG_CELL || L >= P3T_MAX_LEVEL) continue;
+            int b[9];
+            b[0] = nd.x;
+            b[8] = nd.x + nd.y;
+            for (int d = 1; d < 8; ++d)
+                b[d] = warp_lower_digit(key, b[d - 1], b[8], L + 1, d, lane);
+            if (lane == 0) emit_children(c, L, cap, b, node, parent, st);
+        }
+    }
     for (int c = beg + blockIdx.x * TB + threadIdx.x; c < end && !stop;
          c += gridDim.x * TB) {
         int4 nd = node[c];
-        if (nd.y <= n_leaf || L >= P3T_MAX_LEVEL) continue;
+        if (nd.y <= n_leaf || nd.y > BIG_CELL || L >= P3T_MAX_LEVEL) continue;
         int b[9];
         b[0] = nd.x;
         b[8] = nd.x + nd.y;
 #pragma unroll
         for (int d = 1; d < 8; ++d)
             b[d] = lower_digit(key, b[d - 1], b[8], L + 1, d);
-        int k = 0;
-#pragma unroll
-        for (int d = 0; d < 8; ++d) k += b[d + 1] > b[d];
-        int base = atomicAdd(&st->ncell, k);
-        if (base + k > cap) {
-            p3t_raise(st, P3T_ERR_CAPACITY);
-            atomicMax(&st->need_cells, base + k);
-            continue;
-        }
-        int j = 0;
-#pragma unroll
-        for (int d = 0; d < 8; ++d) {
-            if (b[d + 1] > b[d]) {
-                node[base + j] = make_int4(b[d], b[d + 1] - b[d], -1,
-                                           (L + 1) << 8);
-                parent[base + j] = c;
-                ++j;
-            }
-        }
-        node[c].z = base;
-        node[c].w = (L << 8) | k;
+        emit_children(c, L, cap, b, node, parent, st);
     }
     // the last block to finish closes the next level's range
     __syncthreads();
