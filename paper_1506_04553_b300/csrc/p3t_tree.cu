@@ -421,6 +421,9 @@ __device__ __forceinline__ void write_records(
                          __double2float_rn(Q[4]), __double2float_rn(Q[5]));
 }
 
+// LEAVES: every leaf of the tree in one launch (L unused); otherwise the
+// internal cells of level L, from their children.
+template <bool LEAVES>
 __global__ void __launch_bounds__(TB)
 k_moments(int L, const double *__restrict__ xs, const double *__restrict__ ms,
           int n, const int4 *__restrict__ node, double *__restrict__ cM,
@@ -431,10 +434,12 @@ k_moments(int L, const double *__restrict__ xs, const double *__restrict__ ms,
           float4 *__restrict__ cf2, const P3TDevState *st)
 {
     if (st->error) return;
-    const int beg = st->level_start[L], end = st->level_start[L + 1];
+    const int beg = LEAVES ? 0 : st->level_start[L];
+    const int end = LEAVES ? st->ncell : st->level_start[L + 1];
     for (int c = beg + blockIdx.x * TB + threadIdx.x; c < end;
          c += gridDim.x * TB) {
         int4 nd = node[c];
+        if (LEAVES != ((nd.w & 255) == 0)) continue;
         double M = 0.0, com[3] = {0, 0, 0}, Q[6] = {0, 0, 0, 0, 0, 0};
         double bmn[3] = {INFINITY, INFINITY, INFINITY};
         double bmx[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -636,11 +641,16 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     for (int L = 0; L < P3T_MAX_LEVEL; ++L)
         k_tree_split<<<grid_small, TB, 0, s>>>(L, c->p.n_leaf, cap, c->key_a,
                                                 c->node, c->parent, c->st);
-    for (int L = P3T_MAX_LEVEL; L >= 0; --L)
-        k_moments<<<grid_small, TB, 0, s>>>(L, c->xs, c->ms, n, c->node, c->cM,
-                                             c->ccom, c->cQ, c->cbmin,
-                                             c->cbmax, c->wmin, c->wmax,
-                                             c->cf0, c->cf1, c->cf2, c->st);
+    k_moments<true><<<c->sms * 8, TB, 0, s>>>(0, c->xs, c->ms, n, c->node,
+                                               c->cM, c->ccom, c->cQ, c->cbmin,
+                                               c->cbmax, c->wmin, c->wmax,
+                                               c->cf0, c->cf1, c->cf2, c->st);
+    for (int L = P3T_MAX_LEVEL - 1; L >= 0; --L)
+        k_moments<false><<<grid_small, TB, 0, s>>>(L, c->xs, c->ms, n, c->node,
+                                                    c->cM, c->ccom, c->cQ,
+                                                    c->cbmin, c->cbmax, c->wmin,
+                                                    c->wmax, c->cf0, c->cf1,
+                                                    c->cf2, c->st);
     k_groups<<<grid_small, TB, 0, s>>>(c->p.n_group, (int)c->cap_groups,
                                         c->node, c->parent, c->grange, c->st);
     k_group_box<<<grid_small, TB, 0, s>>>(c->grange, c->xs, n, nc, c->order,
