@@ -150,6 +150,24 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def reduce_max(value, device):
+    """Max of a float over all ranks (the timing rule: the slowest rank sets
+    the step time); identity without torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(n_per_rank, steps, ms_max, world):
+    """Particles per second of the whole job: all ranks' particles over the
+    slowest rank's time."""
+    return world * n_per_rank * steps / (ms_max * 1e-3)
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -320,13 +338,9 @@ def run_ours(args, world, rank, local):
     clocks = sampler.stop()
     # a replay relaunches the kernels captured from one step
     launches = (P.launch_count() - l0) + args.steps * launches_per_step
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(e0.elapsed_time(e1), dev)
     ms_step = ms / args.steps
-    value = world * n * args.steps / (ms * 1e-3)
+    value = whole_job_rate(n, args.steps, ms, world)
     ctx.set_params(params)
 
     # interactions and roofline of the force kernel
@@ -434,11 +448,7 @@ def run_ours(args, world, rank, local):
         for _ in range(ke):
             e2e_step()
         torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / ke
-        if world > 1:
-            t = torch.tensor([te], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
+        te = reduce_max((time.perf_counter() - t0) / ke, dev)
         line["e2e"] = {"value": world * n / te, "unit": "particles/s",
                        "h2d_bytes_per_step": 7 * 8 * n,
                        "d2h_bytes_per_step": 6 * 8 * n + 8 * (n + 1) + 4 * nnz_last[0],

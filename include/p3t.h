@@ -242,6 +242,10 @@ typedef struct p3t_stats {
                              group size x cell list length) */
     int64_t int_pp;       /* particle-particle interactions, self included */
     int64_t int_pp_near;  /* the part of int_pp from near lists */
+    int64_t max_walk_stack; /* deepest walk stack (child ranges) seen by the
+                               inspection walk of p3t_get_lists; the walks
+                               of the force, neighbour and backward kernels
+                               traverse identically and hold 768 */
     int64_t nnz;          /* neighbour pairs (after p3t_neighbours) */
 } p3t_stats;
 int p3t_get_stats(p3t_ctx *ctx, p3t_stats *s);

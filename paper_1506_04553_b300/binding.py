@@ -60,7 +60,8 @@ class _CParams(C.Structure):
 class _CStats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "n", "n_cells", "n_groups", "n_levels", "list_pc", "list_pp_near",
-        "list_pp_far", "int_pc", "int_pp", "int_pp_near", "nnz")]
+        "list_pp_far", "int_pc", "int_pp", "int_pp_near", "max_walk_stack",
+        "nnz")]
 
 
 class _CProfile(C.Structure):

@@ -567,6 +567,7 @@ int p3t_get_stats(p3t_ctx *c, p3t_stats *o)
     o->int_pc = c->hst->int_pc;
     o->int_pp = c->hst->int_pp;
     o->int_pp_near = c->hst->int_ppn;
+    o->max_walk_stack = c->hst->max_stack;
     o->nnz = nnz;
     return P3T_OK;
 }

@@ -270,6 +270,7 @@ __global__ void k_tree_init(int nc, const long long *__restrict__ off,
     st->max_level = 0;
     st->need_cells = 0;
     st->blocks_done = 0;
+    st->max_stack = 0;
     st->level_start[0] = 0;
     for (int L = 1; L < P3T_MAX_LEVEL + 3; ++L) st->level_start[L] = nc;
 }

@@ -140,7 +140,7 @@ k_walk(int ngroup, const int *__restrict__ gclus,
             }
             if (open) stk[top + __popc(mo & lt)] = make_int2(child, nchild);
             top += np;
-            if (lane == 0 && top > 64) atomicMax(&st->max_stack, top);
+            if (lane == 0) atomicMax(&st->max_stack, top);
             __syncwarp();
         }
         if (overflow) {

@@ -23,6 +23,10 @@ def _check(pos, m, params, n_groups=256, n_rows=2048, dense_rows=False):
     st = ctx.stats()
     L = t.lists()
     assert st["list_pc"] == L["pc"].size and st["list_pp_near"] == L["ppn"].size
+    ctx.lists()  # the inspection walk records the deepest stack
+    depth = ctx.stats()["max_walk_stack"]
+    print(f"deepest walk stack: {depth} of 768")
+    assert 0 < depth <= 768 // 4
     g = t.groups()
     rng = np.random.default_rng(77)
     sel = rng.choice(t.ngroup, n_groups, replace=False)
