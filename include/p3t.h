@@ -58,9 +58,14 @@ typedef struct p3t_ctx p3t_ctx;
  * Table 1, gamma = r_in / r_cut (Eq. 15; 0.1 in every run of the paper),
  * eps the Plummer softening of Eq. 2, theta the opening criterion of
  * Table 1, h the neighbour radius of Sect. 2.2 (h = r_cut + dr_buff). */
+/* Smallest accepted r_out.  Every source evaluated without the cut-off
+ * lies at least r_out away, so its squared distance is a normal FP32 number
+ * (the force kernel's reciprocal square root flushes subnormal inputs). */
+#define P3T_R_OUT_MIN 1e-15
+
 typedef struct p3t_params {
     double theta;    /* opening parameter, >= 0 (0 = direct summation) */
-    double r_out;    /* outer cut-off radius r_cut, > 0 */
+    double r_out;    /* outer cut-off radius r_cut, >= P3T_R_OUT_MIN */
     double gamma;    /* r_in / r_cut, in [0, 1) */
     double eps;      /* Plummer softening, >= 0 */
     double h;        /* neighbour radius, >= 0; 0 means h = r_out */

@@ -104,7 +104,7 @@ int check_params(const p3t_params *p)
 {
     if (!p) return P3T_ERR_INVALID;
     if (!(p->theta >= 0.0) || !isfinite(p->theta)) return P3T_ERR_INVALID;
-    if (!(p->r_out > 0.0) || !isfinite(p->r_out)) return P3T_ERR_INVALID;
+    if (!(p->r_out >= P3T_R_OUT_MIN) || !isfinite(p->r_out)) return P3T_ERR_INVALID;
     if (!(p->gamma >= 0.0 && p->gamma < 1.0)) return P3T_ERR_INVALID;
     if (!(p->eps >= 0.0) || !isfinite(p->eps)) return P3T_ERR_INVALID;
     if (!(p->h >= 0.0) || !isfinite(p->h)) return P3T_ERR_INVALID;
@@ -430,7 +430,7 @@ int p3t_set_ensemble(p3t_ctx *c, int32_t n_clusters, const int64_t *off,
     if (!off || off[0] != 0) return P3T_ERR_INVALID;
     for (int k = 0; k < n_clusters; ++k) {
         if (off[k + 1] <= off[k]) return P3T_ERR_INVALID;
-        if (r_out && !(r_out[k] > 0.0 && isfinite(r_out[k]))) return P3T_ERR_INVALID;
+        if (r_out && !(r_out[k] >= P3T_R_OUT_MIN && isfinite(r_out[k]))) return P3T_ERR_INVALID;
         if (eps && !(eps[k] >= 0.0 && isfinite(eps[k]))) return P3T_ERR_INVALID;
         if (h && !(h[k] >= 0.0 && isfinite(h[k]))) return P3T_ERR_INVALID;
     }

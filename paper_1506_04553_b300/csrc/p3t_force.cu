@@ -17,7 +17,7 @@
 // holds 32 sources they are staged in shared memory as group-relative FP32
 // vectors, (x_hi - c) + x_lo, so that no absolute coordinate enters the FP32
 // arithmetic, and every lane applies each staged source (a broadcast read) to
-// both of its particles.  Walking and evaluating in one kernel means the
+// both of its particles at once, as one packed FP32x2 pair.  Walking and evaluating in one kernel means the
 // interaction lists never go through HBM and the walk's memory latency hides
 // behind other warps' arithmetic.  Partial sums of a tile are added into
 // (hi, lo) pairs with an error-free two-sum, so the summation error is that
@@ -31,9 +31,9 @@ namespace {
 constexpr int FW = 4;  // warps (groups in flight) per block
 
 #ifndef P3T_PC_UNROLL
-#define P3T_PC_UNROLL 8
+#define P3T_PC_UNROLL 4
 #endif
-constexpr int kPcUnroll = P3T_PC_UNROLL;  // unroll of the cell-tile loop
+constexpr int kPcUnroll = P3T_PC_UNROLL;  // unroll of the cell-tile loop (pairs)
 
 struct ForceConsts {
     float eps2;    // eps^2
@@ -68,90 +68,118 @@ struct Acc3 {
     }
 };
 
-// cell term; A = (d_com.xyz, M), B = (Qxx, Qyy, Qzz, Qxy), C = (Qxz, Qyz, -, -)
-__device__ __forceinline__ void pc_term(float xi, float yi, float zi, float4 A,
-                                        float4 B, float4 C, float eps2,
-                                        float &ax, float &ay, float &az)
+// Every term is evaluated for one i-particle against two consecutive staged
+// sources at once, with the FP32x2 instructions of sm_100 and later (one issue
+// slot for two FMAs); each half rounds exactly like the scalar operation.
+// The sources are staged in shared memory as component arrays, so one 64-bit
+// load gives a component of both sources, and the particle's coordinates are
+// held as broadcast pairs.
+typedef float2 f2;
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 dup2(float a) { return make_float2(a, a); }
+// 1/sqrt(x) by the hardware approximation with subnormal inputs flushed
+// (rsqrt.approx.ftz.f32).  Used where x >= (near radius)^2 > 0 or x is the
+// padding's ~1e30, so no input is subnormal and the flush changes nothing;
+// it saves the subnormal guard that rsqrtf carries.
+__device__ __forceinline__ float rsqrt_ftz(float x)
 {
-    float dx = A.x - xi, dy = A.y - yi, dz = A.z - zi;
-    float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    float ri = rsqrtf(s2);
-    float ri2 = ri * ri;
-    float qx = fmaf(B.x, dx, fmaf(B.w, dy, C.x * dz));
-    float qy = fmaf(B.w, dx, fmaf(B.y, dy, C.y * dz));
-    float qz = fmaf(C.x, dx, fmaf(C.y, dy, B.z * dz));
-    float dqd = fmaf(dx, qx, fmaf(dy, qy, dz * qz));
-    float ri3 = ri * ri2;
-    float ri5 = ri3 * ri2;
-    float ri7 = ri5 * ri2;
-    float a = fmaf(2.5f * dqd, ri7, A.w * ri3);
-    ax = fmaf(a, dx, ax);
-    ay = fmaf(a, dy, ay);
-    az = fmaf(a, dz, az);
-    ax = fmaf(-ri5, qx, ax);
-    ay = fmaf(-ri5, qy, ay);
-    az = fmaf(-ri5, qz, az);
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ f2 rsqrt2(f2 a) { return make_float2(rsqrt_ftz(a.x), rsqrt_ftz(a.y)); }
+
+// Cell sources (components of two cells): position relative to the group
+// centre, mass and the negated traceless quadrupole Q' = -Q.  With Q',
+// q' = Q' d = -Q d and (d.Q'.d) = -(d.Q.d), so
+//   a = M d/s^3 - Q d/s^5 + (5/2)(d.Q.d) d/s^7
+//     = [(-5/2) (d.Q'.d) / s^7 + M / s^3] d + q' / s^5
+// needs no sign flips.  (nx, ny, nz) = minus the particle's coordinates.
+struct CellPair {
+    f2 X, Y, Z, M, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz;
+};
+
+template <bool POT>
+__device__ __forceinline__ void pc_term2(f2 nx, f2 ny, f2 nz,
+                                         const CellPair &c, f2 eps2, f2 &ax,
+                                         f2 &ay, f2 &az, f2 &pp)
+{
+    const f2 dx = add2(c.X, nx), dy = add2(c.Y, ny), dz = add2(c.Z, nz);
+    const f2 s2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
+    const f2 ri = rsqrt2(s2);
+    const f2 ri2 = mul2(ri, ri);
+    const f2 qx = fma2(c.Qxx, dx, fma2(c.Qxy, dy, mul2(c.Qxz, dz)));
+    const f2 qy = fma2(c.Qxy, dx, fma2(c.Qyy, dy, mul2(c.Qyz, dz)));
+    const f2 qz = fma2(c.Qxz, dx, fma2(c.Qyz, dy, mul2(c.Qzz, dz)));
+    const f2 dqd = fma2(dx, qx, fma2(dy, qy, mul2(dz, qz)));
+    const f2 ri3 = mul2(ri, ri2);
+    const f2 ri5 = mul2(ri3, ri2);
+    const f2 ri7 = mul2(ri5, ri2);
+    const f2 a = fma2(mul2(dup2(-2.5f), dqd), ri7, mul2(c.M, ri3));
+    ax = fma2(a, dx, ax);
+    ay = fma2(a, dy, ay);
+    az = fma2(a, dz, az);
+    ax = fma2(ri5, qx, ax);
+    ay = fma2(ri5, qy, ay);
+    az = fma2(ri5, qz, az);
+    if (POT)  // phi = -(M/s + (1/2)(d.Q.d)/s^5), summed with its sign flipped
+        pp = add2(pp, fma2(mul2(dup2(-0.5f), dqd), ri5, mul2(c.M, ri)));
 }
 
-__device__ __forceinline__ float pc_pot(float xi, float yi, float zi, float4 A,
-                                        float4 B, float4 C, float eps2)
+// Particle sources (two particles): position relative to the group centre
+// and mass.
+struct PartPair {
+    f2 X, Y, Z, M;
+};
+
+// far particle term (K = 1); pp accumulates m/s for the potential
+template <bool POT>
+__device__ __forceinline__ void pp_far2(f2 nx, f2 ny, f2 nz, const PartPair &p,
+                                        f2 eps2, f2 &ax, f2 &ay, f2 &az,
+                                        f2 &pp)
 {
-    float dx = A.x - xi, dy = A.y - yi, dz = A.z - zi;
-    float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    float ri = rsqrtf(s2);
-    float ri2 = ri * ri;
-    float qx = fmaf(B.x, dx, fmaf(B.w, dy, C.x * dz));
-    float qy = fmaf(B.w, dx, fmaf(B.y, dy, C.y * dz));
-    float qz = fmaf(C.x, dx, fmaf(C.y, dy, B.z * dz));
-    float dqd = fmaf(dx, qx, fmaf(dy, qy, dz * qz));
-    float ri5 = ri * ri2 * ri2;
-    return -(A.w * ri + 0.5f * dqd * ri5);
+    const f2 dx = add2(p.X, nx), dy = add2(p.Y, ny), dz = add2(p.Z, nz);
+    const f2 s2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
+    const f2 ri = rsqrt2(s2);
+    const f2 mr = mul2(p.M, ri);
+    const f2 ri2 = mul2(ri, ri);
+    const f2 f = mul2(mr, ri2);
+    ax = fma2(f, dx, ax);
+    ay = fma2(f, dy, ay);
+    az = fma2(f, dz, az);
+    if (POT) pp = add2(pp, mr);
 }
 
-// far particle term (K = 1)
-__device__ __forceinline__ void pp_far(float xi, float yi, float zi, float4 A,
-                                       float eps2, float &ax, float &ay,
-                                       float &az)
+// near particle term with the cut-off K; returns the softened distances
+__device__ __forceinline__ f2 pp_near2(f2 nx, f2 ny, f2 nz, const PartPair &p,
+                                       f2 eps2, f2 kA, f2 kB, f2 &ax, f2 &ay,
+                                       f2 &az)
 {
-    float dx = A.x - xi, dy = A.y - yi, dz = A.z - zi;
-    float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    float ri = rsqrtf(s2);
-    float mr = A.w * ri;
-    float ri2 = ri * ri;
-    float f = mr * ri2;
-    ax = fmaf(f, dx, ax);
-    ay = fmaf(f, dy, ay);
-    az = fmaf(f, dz, az);
-}
-
-// near particle term with the cut-off K; returns r^2 (unsoftened, FP32)
-__device__ __forceinline__ float pp_near(float xi, float yi, float zi,
-                                         float4 A, const ForceConsts &k,
-                                         float &ax, float &ay, float &az,
-                                         float &s_out)
-{
-    float dx = A.x - xi, dy = A.y - yi, dz = A.z - zi;
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float s2 = r2 + k.eps2;
-    float ri = s2 > 0.0f ? rsqrtf(s2) : 0.0f;
-    float s = s2 * ri;
-    float x = __saturatef(fmaf(s, k.kA, k.kB));
-    float x2 = x * x;
-    float x4 = x2 * x2;
-    float p = fmaf(-20.0f, x, 70.0f);
-    p = fmaf(p, x, -84.0f);
-    p = fmaf(p, x, 35.0f);
-    float K = p * x4;
+    const f2 dx = add2(p.X, nx), dy = add2(p.Y, ny), dz = add2(p.Z, nz);
+    const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    const f2 s2 = add2(r2, eps2);
+    const f2 ri = make_float2(s2.x > 0.0f ? rsqrtf(s2.x) : 0.0f,
+                              s2.y > 0.0f ? rsqrtf(s2.y) : 0.0f);
+    const f2 s = mul2(s2, ri);
+    f2 x = fma2(s, kA, kB);
+    x = make_float2(__saturatef(x.x), __saturatef(x.y));
+    const f2 x2 = mul2(x, x);
+    const f2 x4 = mul2(x2, x2);
+    f2 q = fma2(dup2(-20.0f), x, dup2(70.0f));
+    q = fma2(q, x, dup2(-84.0f));
+    q = fma2(q, x, dup2(35.0f));
+    const f2 K = mul2(q, x4);
     // ordered so that K = 0 with a huge 1/s never forms 0 * inf
-    float f = A.w * K;
-    f = f * ri;
-    f = f * ri;
-    f = f * ri;
-    ax = fmaf(f, dx, ax);
-    ay = fmaf(f, dy, ay);
-    az = fmaf(f, dz, az);
-    s_out = s;
-    return r2;
+    f2 f = mul2(p.M, K);
+    f = mul2(f, ri);
+    f = mul2(f, ri);
+    f = mul2(f, ri);
+    ax = fma2(f, dx, ax);
+    ay = fma2(f, dy, ay);
+    az = fma2(f, dz, az);
+    return s;
 }
 
 // W(s / r_cut) / s for the potential (Eq. 6, Eq. 16 with G's numerator sign
@@ -196,14 +224,19 @@ __device__ __forceinline__ float4 rel4(float4 hi, float4 lo, float4 c)
 constexpr int FSTACK = 768;  // walk stack entries per warp (child ranges)
 constexpr int RING = 64;     // ring capacity (entries); never more than 63 used
 
+// components of the staged sources (cells use all ten, particles the first
+// four): X Y Z M -Qxx -Qyy -Qzz -Qxy -Qxz -Qyz
+constexpr int NCOMP = 10;
+
 struct __align__(16) WarpSmem {
-    float4 t0[32], t1[32], t2[32];  // staged sources
+    float t[NCOMP][32];             // staged sources, one array per component
     int stack[FSTACK];              // packed child ranges: child * 8 + nchild-1
     int cb[32];                     // cells of the current walk batch
     int pc[RING];                   // accepted cells
     int2 pf[RING];                  // far leaf ranges (first, count)
     int2 pn[RING];                  // near leaf ranges
     int tj[32];                     // sorted ids of staged particles
+    float4 gmn, gmx, ct;            // the group's box and centre
 };
 
 struct RangeRing {
@@ -257,48 +290,85 @@ struct GroupAcc {
     float ph0, pl0, ph1, pl1;
 };
 
+// The lane's two particles, group-relative and negated, each coordinate as a
+// broadcast pair.
+struct IPair {
+    f2 x0, y0, z0, x1, y1, z1;
+};
+
+// Tile partial sums of one particle: the two halves of each pair hold the
+// sums over even and odd sources.
+struct Part3 {
+    f2 x, y, z, p;
+    __device__ __forceinline__ void zero() { x = y = z = p = dup2(0.f); }
+};
+
+template <bool POT>
+__device__ __forceinline__ void tile_end(GroupAcc<POT> &A, const Part3 &u,
+                                         const Part3 &v, float sgn)
+{
+    A.a0.add(u.x.x + u.x.y, u.y.x + u.y.y, u.z.x + u.z.y);
+    A.a1.add(v.x.x + v.x.y, v.y.x + v.y.y, v.z.x + v.z.y);
+    if (POT) {
+        two_sum_add(A.ph0, A.pl0, sgn * (u.p.x + u.p.y));
+        two_sum_add(A.ph1, A.pl1, sgn * (v.p.x + v.p.y));
+    }
+}
+
+__device__ __forceinline__ f2 ld2(const float *a, int j)
+{
+    return *reinterpret_cast<const float2 *>(a + j);
+}
+
 // One tile of up to 32 accepted cells.
 template <bool POT>
 __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
                                           int take, const float4 *cf0,
                                           const float4 *cf1, const float4 *cf2,
-                                          float4 ct, float4 p0, float4 p1,
+                                          const IPair &P,
                                           float eps2, GroupAcc<POT> &A, int lane)
 {
+    float v[NCOMP];
     if (lane < take) {
         int c = S.pc[(head + lane) & (RING - 1)];
         float4 a = cf0[c], bb = cf1[c], cc = cf2[c];
-        S.t0[lane] = make_float4(__fadd_rn(__fsub_rn(a.x, ct.x), bb.x),
-                                 __fadd_rn(__fsub_rn(a.y, ct.y), bb.y),
-                                 __fadd_rn(__fsub_rn(a.z, ct.z), bb.z), a.w);
-        S.t1[lane] = make_float4(bb.w, cc.x, -(bb.w + cc.x), cc.y);
-        S.t2[lane] = make_float4(cc.z, cc.w, 0.0f, 0.0f);
+        const float4 ct = S.ct;
+        v[0] = __fadd_rn(__fsub_rn(a.x, ct.x), bb.x);
+        v[1] = __fadd_rn(__fsub_rn(a.y, ct.y), bb.y);
+        v[2] = __fadd_rn(__fsub_rn(a.z, ct.z), bb.z);
+        v[3] = a.w;
+        v[4] = -bb.w;          // -Qxx
+        v[5] = -cc.x;          // -Qyy
+        v[6] = bb.w + cc.x;    // -Qzz = Qxx + Qyy (traceless)
+        v[7] = -cc.y;          // -Qxy
+        v[8] = -cc.z;          // -Qxz
+        v[9] = -cc.w;          // -Qyz
     } else {
-        S.t0[lane] = far_pad();
-        S.t1[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-        S.t2[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 fp = far_pad();
+        v[0] = fp.x; v[1] = fp.y; v[2] = fp.z;
+#pragma unroll
+        for (int q = 3; q < NCOMP; ++q) v[q] = 0.0f;
     }
+#pragma unroll
+    for (int q = 0; q < NCOMP; ++q) S.t[q][lane] = v[q];
     head = (head + take) & (RING - 1);
     n -= take;
     __syncwarp();
-    float tx0 = 0.f, ty0 = 0.f, tz0 = 0.f, tx1 = 0.f, ty1 = 0.f, tz1 = 0.f,
-          tp0 = 0.f, tp1 = 0.f;
+    Part3 u, w;
+    u.zero();
+    w.zero();
+    const f2 e2 = dup2(eps2);
 #pragma unroll kPcUnroll
-    for (int j = 0; j < 32; ++j) {
-        const float4 a = S.t0[j], bq = S.t1[j], cq = S.t2[j];
-        pc_term(p0.x, p0.y, p0.z, a, bq, cq, eps2, tx0, ty0, tz0);
-        pc_term(p1.x, p1.y, p1.z, a, bq, cq, eps2, tx1, ty1, tz1);
-        if (POT) {
-            tp0 += pc_pot(p0.x, p0.y, p0.z, a, bq, cq, eps2);
-            tp1 += pc_pot(p1.x, p1.y, p1.z, a, bq, cq, eps2);
-        }
+    for (int j = 0; j < 32; j += 2) {
+        CellPair c;
+        c.X = ld2(S.t[0], j);   c.Y = ld2(S.t[1], j);   c.Z = ld2(S.t[2], j);
+        c.M = ld2(S.t[3], j);   c.Qxx = ld2(S.t[4], j); c.Qyy = ld2(S.t[5], j);
+        c.Qzz = ld2(S.t[6], j); c.Qxy = ld2(S.t[7], j); c.Qxz = ld2(S.t[8], j);
+        c.Qyz = ld2(S.t[9], j);
+        pc_term2<POT>(P.x0, P.y0, P.z0, c, e2, u.x, u.y, u.z, u.p);
+        pc_term2<POT>(P.x1, P.y1, P.z1, c, e2, w.x, w.y, w.z, w.p);
     }
-    A.a0.add(tx0, ty0, tz0);
-    A.a1.add(tx1, ty1, tz1);
-    if (POT) {
-        two_sum_add(A.ph0, A.pl0, tp0);
-        two_sum_add(A.ph1, A.pl1, tp1);
-    }
+    tile_end<POT>(A, u, w, -1.0f);
     __syncwarp();
 }
 
@@ -306,52 +376,60 @@ __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
 template <bool NEAR, bool POT>
 __device__ __forceinline__ void particle_tile(
     WarpSmem &S, int2 *ring, RangeRing &r, int take, const float4 *phi,
-    const float4 *plo, float4 ct, float4 p0, float4 p1, int k0, int k1,
+    const float4 *plo, const IPair &P, int k0, int k1,
     const ForceConsts &k, GroupAcc<POT> &A, int lane)
 {
     ring_take(ring, r, take, S.tj, lane);
+    float4 v;
     if (lane < take) {
-        int j = S.tj[lane];
-        S.t0[lane] = rel4(phi[j], plo[j], ct);
+        const int j = S.tj[lane];
+        v = rel4(phi[j], plo[j], S.ct);
     } else {
-        S.t0[lane] = far_pad();
+        v = far_pad();
         S.tj[lane] = -1;
     }
+    S.t[0][lane] = v.x;
+    S.t[1][lane] = v.y;
+    S.t[2][lane] = v.z;
+    S.t[3][lane] = v.w;
     __syncwarp();
-    float tx0 = 0.f, ty0 = 0.f, tz0 = 0.f, tx1 = 0.f, ty1 = 0.f, tz1 = 0.f,
-          tp0 = 0.f, tp1 = 0.f;
+    Part3 u, w;
+    u.zero();
+    w.zero();
+    const f2 e2 = dup2(k.eps2);
     if (NEAR) {
-#pragma unroll 4
-        for (int j = 0; j < 32; ++j) {
-            const float4 a = S.t0[j];
-            float s0, s1;
-            pp_near(p0.x, p0.y, p0.z, a, k, tx0, ty0, tz0, s0);
-            pp_near(p1.x, p1.y, p1.z, a, k, tx1, ty1, tz1, s1);
+        const f2 kA = dup2(k.kA), kB = dup2(k.kB);
+        float tp0 = 0.f, tp1 = 0.f;
+#pragma unroll 2
+        for (int j = 0; j < 32; j += 2) {
+            PartPair p;
+            p.X = ld2(S.t[0], j); p.Y = ld2(S.t[1], j);
+            p.Z = ld2(S.t[2], j); p.M = ld2(S.t[3], j);
+            const f2 s0 = pp_near2(P.x0, P.y0, P.z0, p, e2, kA, kB, u.x, u.y, u.z);
+            const f2 s1 = pp_near2(P.x1, P.y1, P.z1, p, e2, kA, kB, w.x, w.y, w.z);
             if (POT) {
-                const int kj = S.tj[j];
-                if (kj >= 0 && kj != k0) tp0 -= a.w * (float)w_over_s((double)s0, k);
-                if (kj >= 0 && kj != k1) tp1 -= a.w * (float)w_over_s((double)s1, k);
+                const int ja = S.tj[j], jb = S.tj[j + 1];
+                if (ja >= 0 && ja != k0) tp0 -= p.M.x * (float)w_over_s((double)s0.x, k);
+                if (jb >= 0 && jb != k0) tp0 -= p.M.y * (float)w_over_s((double)s0.y, k);
+                if (ja >= 0 && ja != k1) tp1 -= p.M.x * (float)w_over_s((double)s1.x, k);
+                if (jb >= 0 && jb != k1) tp1 -= p.M.y * (float)w_over_s((double)s1.y, k);
             }
         }
+        if (POT) {
+            u.p = make_float2(tp0, 0.f);
+            w.p = make_float2(tp1, 0.f);
+        }
+        tile_end<POT>(A, u, w, 1.0f);
     } else {
-#pragma unroll 8
-        for (int j = 0; j < 32; ++j) {
-            const float4 a = S.t0[j];
-            pp_far(p0.x, p0.y, p0.z, a, k.eps2, tx0, ty0, tz0);
-            pp_far(p1.x, p1.y, p1.z, a, k.eps2, tx1, ty1, tz1);
-            if (POT) {
-                float dx = a.x - p0.x, dy = a.y - p0.y, dz = a.z - p0.z;
-                tp0 -= a.w * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, k.eps2))));
-                dx = a.x - p1.x; dy = a.y - p1.y; dz = a.z - p1.z;
-                tp1 -= a.w * rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, k.eps2))));
-            }
+#pragma unroll 4
+        for (int j = 0; j < 32; j += 2) {
+            PartPair p;
+            p.X = ld2(S.t[0], j); p.Y = ld2(S.t[1], j);
+            p.Z = ld2(S.t[2], j); p.M = ld2(S.t[3], j);
+            pp_far2<POT>(P.x0, P.y0, P.z0, p, e2, u.x, u.y, u.z, u.p);
+            pp_far2<POT>(P.x1, P.y1, P.z1, p, e2, w.x, w.y, w.z, w.p);
         }
-    }
-    A.a0.add(tx0, ty0, tz0);
-    A.a1.add(tx1, ty1, tz1);
-    if (POT) {
-        two_sum_add(A.ph0, A.pl0, tp0);
-        two_sum_add(A.ph1, A.pl1, tp1);
+        tile_end<POT>(A, u, w, -1.0f);
     }
     __syncwarp();
 }
@@ -383,7 +461,12 @@ k_walk_force(const int *__restrict__ gclus,
         if (g >= G) break;
         const int2 gr = grange[g];
         const float4 ct = gctr[g];
-        const float4 gmn = gmin[g], gmx = gmax[g];
+        __syncwarp();  // the previous group's reads of S are done
+        if (lane == 0) {
+            S.gmn = gmin[g];
+            S.gmx = gmax[g];
+            S.ct = ct;
+        }
         const int cl = gclus[g];
         const ClusterConsts cc = ccs[cl];
         ForceConsts kg = k;
@@ -398,13 +481,15 @@ k_walk_force(const int *__restrict__ gclus,
         const bool v0 = lane < gr.y, v1 = lane + 32 < gr.y;
         const float4 p0 = v0 ? rel4(phi[k0], plo[k0], ct) : far_pad();
         const float4 p1 = v1 ? rel4(phi[k1], plo[k1], ct) : far_pad();
+        const IPair P = {dup2(-p0.x), dup2(-p0.y), dup2(-p0.z),
+                         dup2(-p1.x), dup2(-p1.y), dup2(-p1.z)};
         GroupAcc<POT> A;
         A.a0.zero();
         A.a1.zero();
         A.ph0 = A.pl0 = A.ph1 = A.pl1 = 0.f;
         int pc_head = 0, pc_n = 0;
         RangeRing rf = {0, 0, 0}, rn = {0, 0, 0};
-        long long cnt_pc = 0, cnt_pn = 0, cnt_pf = 0;
+        int cnt_pc = 0, cnt_pn = 0, cnt_pf = 0;
 
         if (lane == 0) S.stack[0] = cl * 8;  // the cluster's root, one cell
         int top = 1;
@@ -438,7 +523,7 @@ k_walk_force(const int *__restrict__ gclus,
             int child = 0, nchild = 0, pfirst = 0, pcount = 0;
             if (c >= 0) {
                 const float4 cmn = wmin[c], cmx = wmax[c];
-                float d2 = box_d2(gmn, gmx, cmn, cmx);
+                float d2 = box_d2(S.gmn, S.gmx, cmn, cmx);
                 float l = box_side(cmn, cmx);
                 if (mac_accept(d2, l, theta2, hg2)) {
                     is_pc = true;
@@ -486,13 +571,13 @@ k_walk_force(const int *__restrict__ gclus,
             __syncwarp();
             // evaluate every full tile
             while (pc_n >= 32)
-                cell_tile<POT>(S, pc_head, pc_n, 32, cf0, cf1, cf2, ct, p0, p1,
+                cell_tile<POT>(S, pc_head, pc_n, 32, cf0, cf1, cf2, P,
                                kg.eps2, A, lane);
             while (rf.np >= 32)
-                particle_tile<false, POT>(S, S.pf, rf, 32, phi, plo, ct, p0, p1,
+                particle_tile<false, POT>(S, S.pf, rf, 32, phi, plo, P,
                                           k0, k1, kg, A, lane);
             while (rn.np >= 32)
-                particle_tile<true, POT>(S, S.pn, rn, 32, phi, plo, ct, p0, p1,
+                particle_tile<true, POT>(S, S.pn, rn, 32, phi, plo, P,
                                          k0, k1, kg, A, lane);
         }
         if (overflow) {
@@ -501,13 +586,13 @@ k_walk_force(const int *__restrict__ gclus,
         }
         // the partial tiles left over
         if (pc_n > 0)
-            cell_tile<POT>(S, pc_head, pc_n, pc_n, cf0, cf1, cf2, ct, p0, p1,
+            cell_tile<POT>(S, pc_head, pc_n, pc_n, cf0, cf1, cf2, P,
                            kg.eps2, A, lane);
         if (rf.np > 0)
-            particle_tile<false, POT>(S, S.pf, rf, rf.np, phi, plo, ct, p0, p1,
+            particle_tile<false, POT>(S, S.pf, rf, rf.np, phi, plo, P,
                                       k0, k1, kg, A, lane);
         if (rn.np > 0)
-            particle_tile<true, POT>(S, S.pn, rn, rn.np, phi, plo, ct, p0, p1,
+            particle_tile<true, POT>(S, S.pn, rn, rn.np, phi, plo, P,
                                      k0, k1, kg, A, lane);
         // ---- write back in the caller's order ----
         const float Gc = k.G;

@@ -27,6 +27,11 @@ namespace {
 
 constexpr int TB = 256;
 
+// containers hold at most this many times n_group particles
+#ifndef P3T_CONTAINER_FACTOR
+#define P3T_CONTAINER_FACTOR 16
+#endif
+
 // ---------------------------------------------------------------- bbox ----
 __global__ void __launch_bounds__(TB)
 k_bbox_partial(int n, const double *__restrict__ pos,
@@ -540,7 +545,7 @@ k_groups(int ng, int gcap, const int4 *__restrict__ node,
 {
     if (st->error) return;
     const int ncell = st->ncell;
-    const int cap = 16 * ng;
+    const int cap = P3T_CONTAINER_FACTOR * ng;
     for (int c = blockIdx.x * TB + threadIdx.x; c < ncell;
          c += gridDim.x * TB) {
         const int4 nd = node[c];

@@ -51,13 +51,6 @@ __device__ __forceinline__ float4 rel(float4 hi, float4 lo, float4 c)
                        __fadd_rn(__fsub_rn(hi.z, c.z), lo.z), hi.w);
 }
 
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // Warp reduce-scatter of NS sources x NV values held by every lane: after
 // the call a[0][0..NV) of lane l holds the warp-wide totals of source
 // src_of<NS>(l); the 32/NS lanes sharing that source hold the same totals.

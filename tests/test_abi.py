@@ -52,6 +52,11 @@ def test_host_only_paths(lib):
     assert lib.p3t_kick(5, None, None, 0.1, None) == 1
     lib.p3t_create.argtypes = [C.c_void_p, C.c_void_p]
     assert lib.p3t_create(None, None) == 1
+    # parameters are checked before any device call; r_out below
+    # P3T_R_OUT_MIN (1e-15) is refused
+    ctx = C.c_void_p()
+    buf[1] = 1e-16  # r_out
+    assert lib.p3t_create(C.byref(ctx), buf) == 1 and not ctx.value
 
 
 def test_binding_imports_without_gpu():
