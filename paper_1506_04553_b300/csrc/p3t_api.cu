@@ -185,6 +185,11 @@ int ensure_particles(p3t_ctx *c, int64_t n)
     P3T_TRY(grow(c->loff, d, 3 * (cap + 1), sizeof(long long)));
     P3T_TRY(grow(c->pclus, d, cap, sizeof(int)));
     P3T_TRY(grow(c->gclus, d, cap, sizeof(int)));
+    P3T_TRY(grow(c->gperm, d, cap, sizeof(int)));
+    P3T_TRY(grow(c->gcost, d, cap, sizeof(float)));
+    P3T_TRY(grow(c->pgroup, d, cap, sizeof(int)));
+    // the recorded group costs went with the old arrays
+    P3T_CUDA_TRY(cudaMemset(&c->st->cost_n, 0, sizeof(int)));
     c->cap_n = cap;
     return P3T_OK;
 }
@@ -268,7 +273,8 @@ void free_all(p3t_ctx *c)
                     c->cf0, c->cf1, c->cf2, c->grange, c->gmin, c->gmax,
                     c->gctr, c->lcnt, c->loff, c->list[0], c->list[1],
                     c->list[2], c->scan_part, c->red_part, c->cadj,
-                    c->clus_off, c->cc, c->clus_box, c->pclus, c->gclus};
+                    c->clus_off, c->cc, c->clus_box, c->pclus, c->gclus,
+                    c->gperm, c->gcost, c->pgroup};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hst) cudaFreeHost(c->hst);

@@ -446,19 +446,22 @@ k_walk_force(const int *__restrict__ gclus,
              const float4 *__restrict__ plo, const float4 *__restrict__ cf0,
              const float4 *__restrict__ cf1, const float4 *__restrict__ cf2,
              const int *__restrict__ order, int n, ForceConsts k,
-             float *__restrict__ acc, double *__restrict__ pot,
-             P3TDevState *st)
+             const int *__restrict__ gperm, float *__restrict__ gcost,
+             int *__restrict__ pgroup, float *__restrict__ acc,
+             double *__restrict__ pot, P3TDevState *st)
 {
     __shared__ WarpSmem smem[FW];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
     WarpSmem &S = smem[w];
+    if (st->error) return;  // no valid tree
     const int G = st->ngroup;
     for (;;) {
         int g = 0;
         if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
         g = __shfl_sync(full, g, 0);
         if (g >= G) break;
+        g = gperm[g];
         const int2 gr = grange[g];
         const float4 ct = gctr[g];
         __syncwarp();  // the previous group's reads of S are done
@@ -596,8 +599,13 @@ k_walk_force(const int *__restrict__ gclus,
                                      k0, k1, kg, A, lane);
         // ---- write back in the caller's order ----
         const float Gc = k.G;
+        // work of this group and group of its particles, for the evaluation
+        // order of the next build (same weights as the instruction counts
+        // per source of the cell, far and near tiles)
+        if (lane == 0) gcost[g] = 16.0f * cnt_pc + 6.0f * cnt_pf + 11.0f * cnt_pn;
         if (v0) {
             int o = order[k0];
+            pgroup[o] = g;
             acc[o] = Gc * (A.a0.hx + A.a0.lx);
             acc[(size_t)n + o] = Gc * (A.a0.hy + A.a0.ly);
             acc[2 * (size_t)n + o] = Gc * (A.a0.hz + A.a0.lz);
@@ -605,6 +613,7 @@ k_walk_force(const int *__restrict__ gclus,
         }
         if (v1) {
             int o = order[k1];
+            pgroup[o] = g;
             acc[o] = Gc * (A.a1.hx + A.a1.lx);
             acc[(size_t)n + o] = Gc * (A.a1.hy + A.a1.ly);
             acc[2 * (size_t)n + o] = Gc * (A.a1.hz + A.a1.lz);
@@ -627,11 +636,14 @@ k_walk_force(const int *__restrict__ gclus,
     }
 }
 
-// Resets the per-call counters of a force evaluation.
-__global__ void k_force_reset(P3TDevState *st)
+// Resets the per-call counters of a force evaluation and marks the group
+// costs it records as those of this n.
+__global__ void k_force_reset(P3TDevState *st, int n)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         st->work = 0;
+        st->cost_n = n;
+        st->cost_groups = st->ngroup;
         st->tot[0] = st->tot[1] = st->tot[2] = 0;
         st->int_pc = st->int_pp = st->int_ppn = 0;
     }
@@ -666,7 +678,7 @@ ForceConsts make_consts(const p3t_params &p)
 int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s)
 {
     const int n = (int)c->n;
-    k_force_reset<<<1, 32, 0, s>>>(c->st);
+    k_force_reset<<<1, 32, 0, s>>>(c->st, n);
     p3t_count_launches(1);
     // the group count is read on the device; size the grid from the bound
     const int64_t G = (n + 15) / 16 + c->nclus;
@@ -679,12 +691,12 @@ int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s)
         k_walk_force<true><<<blocks, FW * 32, 0, s>>>(
             c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
             c->wmax, c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
-            c->order, n, k, acc, pot, c->st);
+            c->order, n, k, c->gperm, c->gcost, c->pgroup, acc, pot, c->st);
     else
         k_walk_force<false><<<blocks, FW * 32, 0, s>>>(
             c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
             c->wmax, c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
-            c->order, n, k, acc, pot, c->st);
+            c->order, n, k, c->gperm, c->gcost, c->pgroup, acc, pot, c->st);
     p3t_count_launches(1);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;

@@ -11,7 +11,10 @@
 //                             .w = child / nchild bit patterns)
 //                             force record cf0/cf1/cf2 float4[C]
 //   groups                  : grange int2[G] = (first, count),
-//                             gmin/gmax/gctr float4[G]
+//                             gmin/gmax/gctr float4[G], gperm i32[G]
+//                             (evaluation order), gcost f32[G] and
+//                             pgroup i32[n] (work per group and group per
+//                             particle at the last force evaluation)
 //   lists (CSR per group)   : pc i32, ppn i32, ppf i32 with int64 offsets
 #pragma once
 #include <cuda_runtime.h>
@@ -45,6 +48,8 @@ struct P3TDevState {
     long long nnz;      // neighbour pairs
     long long cum_int[3];  // pc, pp, pp-near interactions since profile reset
     int max_stack;      // deepest walk stack seen (ranges)
+    int cost_n;         // n of the force evaluation that wrote gcost/pgroup
+    int cost_groups;    // number of groups of that evaluation
     int pad1;
 };
 
@@ -100,6 +105,9 @@ struct p3t_ctx {
     // groups
     int2 *grange;
     float4 *gmin, *gmax, *gctr;
+    int *gperm;        // [G] order in which the group kernels take the groups
+    float *gcost;      // [G] work of each group at the last force evaluation
+    int *pgroup;       // [n] group of each original index at that evaluation
     // lists
     long long *lcnt;   // [3][G] counts, then offsets [3][G+1]
     long long *loff;

@@ -95,18 +95,21 @@ k_ngb_walk(const int *__restrict__ gclus,
            const float4 *__restrict__ plo, const int *__restrict__ order,
            const double *__restrict__ xs, int n,
            int *__restrict__ cnt, const long long *__restrict__ row_off,
-           int *__restrict__ idx, long long cap, P3TDevState *st)
+           int *__restrict__ idx, long long cap, const int *__restrict__ gperm,
+           P3TDevState *st)
 {
     __shared__ NgbSmem smem[NW];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
     NgbSmem &S = smem[w];
+    if (st->error) return;  // no valid tree
     const int G = st->ngroup;
     for (;;) {
         int g = 0;
         if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
         g = __shfl_sync(full, g, 0);
         if (g >= G) break;
+        g = gperm[g];
         const int2 gr = grange[g];
         const float4 ct = gctr[g];
         const float4 gmn = gmin[g], gmx = gmax[g];
@@ -274,12 +277,12 @@ int p3t_run_ngb(p3t_ctx *c, int fill, const long long *row_off, int *idx,
         k_ngb_walk<true><<<blocks, NW * 32, 0, s>>>(
             c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
             c->wmax, c->node, c->phi, c->plo, c->order, c->xs, n, c->ngb_cnt,
-            row_off, idx, cap, c->st);
+            row_off, idx, cap, c->gperm, c->st);
     else
         k_ngb_walk<false><<<blocks, NW * 32, 0, s>>>(
             c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
             c->wmax, c->node, c->phi, c->plo, c->order, c->xs, n, c->ngb_cnt,
-            row_off, idx, cap, c->st);
+            row_off, idx, cap, c->gperm, c->st);
     p3t_count_launches(2);
     if (fill) {
         int nb = (n + 255) / 256;

@@ -612,6 +612,70 @@ k_group_box(const int2 *__restrict__ grange, const double *__restrict__ xs,
     }
 }
 
+// Evaluation order of the groups, most expensive first (longest processing
+// time first shortens the tail of the dynamically scheduled group kernels).
+// The work of a new group is estimated by the work of the group that held
+// its first particle at the last force evaluation of the same n; groups are
+// bucketed by log2 of that estimate (8 buckets per octave) and written out
+// bucket by bucket, the order inside a bucket being arbitrary.  Without a
+// recorded evaluation the order is the identity.  One block.
+constexpr int OB = 1024;
+constexpr int NBUCKET = 256;
+
+__device__ __forceinline__ int order_bucket(int g, const int2 *grange,
+                                            const int *order,
+                                            const int *pgroup,
+                                            const float *gcost, int cg)
+{
+    const int og = pgroup[order[grange[g].x]];
+    const float est = (og >= 0 && og < cg) ? gcost[og] : 0.0f;
+    int b = 0;
+    if (est >= 1.0f) b = min(NBUCKET - 1, (int)(8.0f * __log2f(est)));
+    return NBUCKET - 1 - b;  // descending work
+}
+
+__global__ void __launch_bounds__(OB)
+k_group_order(int n, const int2 *__restrict__ grange,
+              const int *__restrict__ order, const int *__restrict__ pgroup,
+              const float *__restrict__ gcost, int *__restrict__ gperm,
+              const P3TDevState *st)
+{
+    __shared__ int cnt[NBUCKET];
+    __shared__ int start[NBUCKET];
+    if (st->error) return;
+    const int G = st->ngroup;  // <= capacity (k_groups checks)
+    const int cg = st->cost_groups;
+    const int tid = threadIdx.x;
+    if (st->cost_n != n || cg <= 0) {
+        for (int g = tid; g < G; g += OB) gperm[g] = g;
+        return;
+    }
+    for (int b = tid; b < NBUCKET; b += OB) cnt[b] = 0;
+    __syncthreads();
+    for (int g = tid; g < G; g += OB)
+        atomicAdd(&cnt[order_bucket(g, grange, order, pgroup, gcost, cg)], 1);
+    __syncthreads();
+    if (tid < 32) {  // exclusive scan of the 256 counts, 8 per lane
+        int v[NBUCKET / 32], sum = 0;
+#pragma unroll
+        for (int q = 0; q < NBUCKET / 32; ++q) {
+            v[q] = cnt[tid * (NBUCKET / 32) + q];
+            sum += v[q];
+        }
+        int off = warp_incl_scan(sum) - sum;
+#pragma unroll
+        for (int q = 0; q < NBUCKET / 32; ++q) {
+            start[tid * (NBUCKET / 32) + q] = off;
+            off += v[q];
+        }
+    }
+    __syncthreads();
+    for (int g = tid; g < G; g += OB) {
+        const int b = order_bucket(g, grange, order, pgroup, gcost, cg);
+        gperm[atomicAdd(&start[b], 1)] = g;
+    }
+}
+
 }  // namespace
 
 // Bounding box, keys, sort, gather, level-wise split, moments, groups.
@@ -662,8 +726,11 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     k_group_box<<<grid_small, TB, 0, s>>>(c->grange, c->xs, n, nc, c->order,
                                            c->pclus, c->cc, c->gclus, c->gmin,
                                            c->gmax, c->gctr, c->st);
-    // bbox 2, keys, gather, init, 21 splits, 22 moment levels, groups, boxes
-    p3t_count_launches(2 + 1 + 1 + 1 + P3T_MAX_LEVEL + (P3T_MAX_LEVEL + 1) + 2);
+    k_group_order<<<1, OB, 0, s>>>(n, c->grange, c->order, c->pgroup, c->gcost,
+                                   c->gperm, c->st);
+    // bbox 2, keys, gather, init, 21 splits, 22 moment levels, groups, boxes,
+    // order
+    p3t_count_launches(2 + 1 + 1 + 1 + P3T_MAX_LEVEL + (P3T_MAX_LEVEL + 1) + 3);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
 }

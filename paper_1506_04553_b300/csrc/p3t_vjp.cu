@@ -299,17 +299,19 @@ k_walk_vjp(const int *__restrict__ gclus,
            const int *__restrict__ order, int n, VjpConsts k,
            const float *__restrict__ w, double *__restrict__ gpos,
            double *__restrict__ gmass, double *__restrict__ cadj,
-           P3TDevState *st)
+           const int *__restrict__ gperm, P3TDevState *st)
 {
     __shared__ Smem smem[VW];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Smem &S = smem[wi];
+    if (st->error) return;  // no valid tree
     const int G = st->ngroup;
     for (;;) {
         int g = 0;
         if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= G) break;
+        g = gperm[g];
         const int2 gr = grange[g];
         const int cl = gclus[g];
         const ClusterConsts cc = ccs[cl];
@@ -453,7 +455,7 @@ int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,
         c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
         c->wmax, c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
         c->order, n, k, w,
-        gpos, gmass, cadj, c->st);
+        gpos, gmass, cadj, c->gperm, c->st);
     k_vjp_push<<<(n + 255) / 256, 256, 0, s>>>(n, c->nclus,
                                                (const long long *)c->clus_off,
                                                c->node, c->cM, c->ccom,

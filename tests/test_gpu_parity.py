@@ -241,3 +241,35 @@ def test_errors(cuda):
     with pytest.raises(P3TError) as ei:
         ctx2.neighbours_into(off, idx)
     assert ei.value.code == 2
+
+
+def test_group_order_changes_nothing(cuda):
+    """The group kernels take the groups most expensive first, estimated from
+    the previous force evaluation; the first build of a context has no
+    estimate and takes them in index order.  Each group's sums do not depend
+    on that order, so forces, potentials, neighbour lists and interaction
+    counts are bit-identical across the two; the backward pass adds the
+    groups' contributions with FP64 atomics in whatever order they arrive, so
+    its gradients agree to FP64 rounding."""
+    import torch
+    from paper_1506_04553_b300 import Context
+    pos, _, m = _plummer(20000, 12)
+    ctx = Context(_params(theta=0.4, r_out=0.01, eps=1e-4))
+    pd = torch.tensor(np.ascontiguousarray(pos.T), device="cuda")
+    md = torch.tensor(m, device="cuda")
+    w = torch.randn((3, pos.shape[0]), generator=torch.Generator().manual_seed(5)).float().cuda()
+    runs = []
+    for _ in range(3):  # index order, then twice with recorded costs
+        ctx.build_tree(pd, md)
+        acc, pot = ctx.long_force(want_potential=True)
+        off, idx = ctx.neighbours()
+        gx, gm = ctx.long_force_vjp(w)
+        st = ctx.stats()
+        runs.append([t.cpu().numpy() for t in (acc, pot, off, idx, gx, gm)]
+                    + [st["int_pc"], st["int_pp"], st["int_pp_near"]])
+    for r in runs[1:]:
+        for a, b in zip(runs[0][:4], r[:4]):
+            assert np.array_equal(a, b)
+        for a, b in zip(runs[0][4:6], r[4:6]):
+            assert np.allclose(a, b, rtol=1e-12, atol=1e-12 * np.abs(a).max())
+        assert runs[0][6:] == r[6:]
