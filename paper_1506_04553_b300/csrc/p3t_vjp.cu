@@ -19,11 +19,16 @@
 //
 // k_walk_vjp walks each group exactly as the force kernel does (shared
 // walk in p3t_walkcore.cuh, so the interaction sets are recomputed, not
-// stored) and evaluates the Jacobian products in FP32 group-relative
-// coordinates; contributions to sources are summed over the warp and added
-// to FP64 accumulators with atomics.  k_vjp_push then sends every cell
-// adjoint to the member particles in FP64: one thread per particle descends
-// from the root to its leaf and applies the adjoint of each cell on the way.
+// stored).  For every tile of up to 32 sources each lane owns one source and
+// sweeps the group's particles (staged once per group in shared memory) two
+// at a time with FP32x2 instructions, in group-relative coordinates.  The
+// source's adjoints stay in the lane's registers and go to FP64 atomics once
+// per tile; the particle-side products (3 per particle) are summed over the
+// lanes by a warp reduce-scatter, four particle pairs at a time, and kept by
+// the particle's owner lane in two-sum (hi, lo) FP32 accumulators.
+// k_vjp_push then sends every cell adjoint to the member particles in FP64:
+// one thread per particle descends from the root to its leaf and applies the
+// adjoint of each cell on the way.
 #include <math.h>
 
 #include "p3t_walkcore.cuh"
@@ -32,23 +37,54 @@ namespace {
 
 using p3t_walk::Smem;
 
-constexpr int VW = 4;  // warps per block
+constexpr int VW = 4;    // warps per block
+#ifndef P3T_VJP_NSP
+#define P3T_VJP_NSP 4
+#endif
+#ifndef P3T_VJP_MIN_BLOCKS
+#define P3T_VJP_MIN_BLOCKS 0
+#endif
+constexpr int NSP = P3T_VJP_NSP;  // particle pairs per i-side reduce-scatter
+constexpr int GMAX = 64; // particle slots of a group
 
 struct VjpConsts {
     float eps2, kA, kB;
     double G;
 };
 
-__device__ __forceinline__ float4 vpad()
+typedef float2 f2;
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 dup2(float a) { return make_float2(a, a); }
+
+// 1/sqrt(x) with subnormal inputs flushed (rsqrt.approx.ftz.f32); used only
+// where x >= (near radius)^2 > 0 or x is a padding distance of ~1e31.
+__device__ __forceinline__ float rsqrt_ftz(float x)
 {
-    return make_float4(1e15f, 1e15f, 1e15f, 0.0f);
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
+
+// Padding: absent sources sit at -PAD, absent particles at +PAD, so that no
+// padded pair has a zero distance; masses and weights of padding are zero.
+constexpr float PAD = 1e15f;
 
 __device__ __forceinline__ float4 rel(float4 hi, float4 lo, float4 c)
 {
     return make_float4(__fadd_rn(__fsub_rn(hi.x, c.x), lo.x),
                        __fadd_rn(__fsub_rn(hi.y, c.y), lo.y),
                        __fadd_rn(__fsub_rn(hi.z, c.z), lo.z), hi.w);
+}
+
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v)
+{
+    float s = __fadd_rn(hi, v);
+    float bb = __fsub_rn(s, hi);
+    float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
 }
 
 // Warp reduce-scatter of NS sources x NV values held by every lane: after
@@ -100,193 +136,270 @@ __device__ __forceinline__ float pick(const float (&a)[NV], int v)
     return r;
 }
 
-// Per-lane state of one group: two particles per lane.
+// The group's particles, staged once per group: negated group-relative
+// positions and weights, slot = particle index in the group; and the
+// particle-side tile sums.
+struct __align__(16) VjpSmem {
+    float nx[GMAX], ny[GMAX], nz[GMAX], wx[GMAX], wy[GMAX], wz[GMAX];
+    float ts[3][GMAX];
+};
+
+__device__ __forceinline__ f2 ld2(const float *a, int j)
+{
+    return *reinterpret_cast<const float2 *>(a + j);
+}
+
+// One cell (broadcast pairs) against two particles (the pair's halves).
+struct CellSrc {
+    f2 X, Y, Z, M, M3, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz;  // M3 = -3 M
+};
+
+// J^T w for the pair (jx, jy, jz) and the cell adjoints
+// acc = (dL/dM, dL/dcom xyz, S xx yy zz xy xz yz), all without G.
+__device__ __forceinline__ void cell_pair(const CellSrc &c, f2 nx, f2 ny,
+                                          f2 nz, f2 wx, f2 wy, f2 wz, f2 eps2,
+                                          f2 (&acc)[10], f2 &jx, f2 &jy,
+                                          f2 &jz)
+{
+    const f2 dx = add2(c.X, nx), dy = add2(c.Y, ny), dz = add2(c.Z, nz);
+    const f2 s2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
+    const f2 ri = make_float2(rsqrt_ftz(s2.x), rsqrt_ftz(s2.y));
+    const f2 ri2 = mul2(ri, ri);
+    const f2 ri3 = mul2(ri, ri2), ri5 = mul2(ri3, ri2), ri7 = mul2(ri5, ri2),
+             ri9 = mul2(ri7, ri2);
+    // Q = [[Qxx, Qxy, Qxz], [Qxy, Qyy, Qyz], [Qxz, Qyz, Qzz]]
+    const f2 qx = fma2(c.Qxx, dx, fma2(c.Qxy, dy, mul2(c.Qxz, dz)));
+    const f2 qy = fma2(c.Qxy, dx, fma2(c.Qyy, dy, mul2(c.Qyz, dz)));
+    const f2 qz = fma2(c.Qxz, dx, fma2(c.Qyz, dy, mul2(c.Qzz, dz)));
+    const f2 wqx = fma2(c.Qxx, wx, fma2(c.Qxy, wy, mul2(c.Qxz, wz)));
+    const f2 wqy = fma2(c.Qxy, wx, fma2(c.Qyy, wy, mul2(c.Qyz, wz)));
+    const f2 wqz = fma2(c.Qxz, wx, fma2(c.Qyz, wy, mul2(c.Qzz, wz)));
+    const f2 dqd = fma2(dx, qx, fma2(dy, qy, mul2(dz, qz)));
+    const f2 wd = fma2(wx, dx, fma2(wy, dy, mul2(wz, dz)));
+    const f2 wqd = fma2(wx, qx, fma2(wy, qy, mul2(wz, qz)));
+    // J^T w = cw w + cd d + cq q - Qw / s^5 with
+    //   cw = M / s^3 + (5/2) dQd / s^7,   cq = 5 wd / s^7,
+    //   cd = -3 M wd / s^5 + 5 wQd / s^7 - (35/2) dQd wd / s^9
+    const f2 cw = fma2(mul2(dup2(2.5f), dqd), ri7, mul2(c.M, ri3));
+    f2 cd = mul2(mul2(c.M3, wd), ri5);
+    cd = fma2(mul2(dup2(5.0f), wqd), ri7, cd);
+    cd = fma2(mul2(dup2(-17.5f), mul2(dqd, wd)), ri9, cd);
+    const f2 t7 = mul2(dup2(2.5f), mul2(wd, ri7));  // (5/2) wd / s^7
+    const f2 cq = add2(t7, t7);
+    const f2 nri5 = mul2(dup2(-1.0f), ri5);
+    jx = fma2(cw, wx, fma2(cd, dx, fma2(cq, qx, mul2(nri5, wqx))));
+    jy = fma2(cw, wy, fma2(cd, dy, fma2(cq, qy, mul2(nri5, wqy))));
+    jz = fma2(cw, wz, fma2(cd, dz, fma2(cq, qz, mul2(nri5, wqz))));
+    acc[0] = fma2(wd, ri3, acc[0]);
+    acc[1] = add2(acc[1], jx);
+    acc[2] = add2(acc[2], jy);
+    acc[3] = add2(acc[3], jz);
+    // S = -(w d^T + d w^T) / (2 s^5) + (5/2) wd d d^T / s^7, with v = -w / (2 s^5)
+    const f2 h5 = mul2(dup2(-0.5f), ri5);
+    const f2 vx = mul2(h5, wx), vy = mul2(h5, wy), vz = mul2(h5, wz);
+    acc[4] = fma2(dx, fma2(t7, dx, add2(vx, vx)), acc[4]);
+    acc[5] = fma2(dy, fma2(t7, dy, add2(vy, vy)), acc[5]);
+    acc[6] = fma2(dz, fma2(t7, dz, add2(vz, vz)), acc[6]);
+    acc[7] = fma2(vx, dy, fma2(dx, fma2(t7, dy, vy), acc[7]));
+    acc[8] = fma2(vx, dz, fma2(dx, fma2(t7, dz, vz), acc[8]));
+    acc[9] = fma2(vy, dz, fma2(dy, fma2(t7, dz, vz), acc[9]));
+}
+
+// One source particle (broadcast pairs) against two particles.
+struct PartSrc {
+    f2 X, Y, Z, m;
+};
+
+// J w for the pair (jx, jy, jz) and the source adjoints
+// acc = (dL/dx_j xyz, dL/dm_j), all without G.  selfx / selfy: the half's
+// particle is the source itself (contributes 0).
+template <bool NEAR>
+__device__ __forceinline__ void pair_pair(const PartSrc &p, f2 nx, f2 ny,
+                                          f2 nz, f2 wx, f2 wy, f2 wz,
+                                          bool selfx, bool selfy, f2 eps2,
+                                          f2 kA, f2 kB, f2 (&acc)[4], f2 &jx,
+                                          f2 &jy, f2 &jz)
+{
+    const f2 dx = add2(p.X, nx), dy = add2(p.Y, ny), dz = add2(p.Z, nz);
+    const f2 s2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
+    f2 ri;
+    if (NEAR)
+        ri = make_float2((s2.x > 0.0f && !selfx) ? rsqrtf(s2.x) : 0.0f,
+                         (s2.y > 0.0f && !selfy) ? rsqrtf(s2.y) : 0.0f);
+    else  // far leaves: s^2 >= (near radius)^2, never the particle itself
+        ri = make_float2(rsqrt_ftz(s2.x), rsqrt_ftz(s2.y));
+    const f2 ri2 = mul2(ri, ri);
+    const f2 ri3 = mul2(ri2, ri);
+    f2 phi, psi;
+    if (NEAR) {
+        const f2 sv = mul2(s2, ri);
+        f2 x = fma2(sv, kA, kB);
+        x = make_float2(__saturatef(x.x), __saturatef(x.y));
+        const f2 x2 = mul2(x, x), x4 = mul2(x2, x2);
+        f2 pk = fma2(dup2(-20.0f), x, dup2(70.0f));
+        pk = fma2(pk, x, dup2(-84.0f));
+        pk = fma2(pk, x, dup2(35.0f));
+        const f2 K = mul2(pk, x4);
+        const f2 omx = fma2(x, dup2(-1.0f), dup2(1.0f));
+        const f2 Kp = mul2(mul2(mul2(dup2(140.0f), mul2(x2, x)),
+                                mul2(mul2(omx, omx), omx)), kA);
+        // products ordered so that K = 0 with a huge 1/s never forms 0*inf
+        phi = mul2(mul2(mul2(K, ri), ri), ri);
+        psi = fma2(dup2(-3.0f), mul2(mul2(phi, ri), ri),
+                   mul2(mul2(mul2(mul2(Kp, ri), ri), ri), ri));
+    } else {
+        phi = ri3;
+        psi = mul2(mul2(dup2(-3.0f), ri3), ri2);
+    }
+    const f2 wd = fma2(wx, dx, fma2(wy, dy, mul2(wz, dz)));
+    const f2 mphi = mul2(p.m, phi);
+    const f2 mpw = mul2(mul2(p.m, psi), wd);
+    jx = fma2(mphi, wx, mul2(mpw, dx));
+    jy = fma2(mphi, wy, mul2(mpw, dy));
+    jz = fma2(mphi, wz, mul2(mpw, dz));
+    acc[0] = add2(acc[0], jx);
+    acc[1] = add2(acc[1], jy);
+    acc[2] = add2(acc[2], jz);
+    acc[3] = fma2(phi, wd, acc[3]);
+}
+
+// Per-lane state of one group.  Lane l owns particle slots l and l + 32.
 struct VjpEval {
-    float4 p0, p1;        // group-relative positions
-    float3 w0, w1;        // weights (zero for empty slots)
-    int k0, k1;           // sorted ids
-    double g0[3], g1[3];  // dL/dx of the lane's particles (without G)
+    VjpSmem *V;
+    int lane, gfirst, npairs;  // npairs: particle pairs swept (multiple of NSP)
     float4 ct;
+    float ih[2][3], il[2][3];  // owner's dL/dx sums (without G, sign: + J w)
     const float4 *phi, *plo, *cf0, *cf1, *cf2;
     const int *order;
     double *gpos, *gmass, *cadj;
-    int n, lane;
+    int n;
     VjpConsts k;
 
-    // Cell tile: ids in S.tj[0..take).
+    // Particle-side products of NSP pairs starting at pair ch: summed over
+    // the lanes and stored in the tile sums.
+    __device__ __forceinline__ void flush(float (&r)[NSP][6], int ch)
+    {
+        reduce_scatter<NSP, 6>(r, lane);
+        const int v = lane & (32 / NSP - 1);
+        if (v < 6) {
+            const int slot = 2 * (ch + src_of<NSP>(lane)) + (v >= 3 ? 1 : 0);
+            V->ts[v % 3][slot] = pick<6>(r[0], v);
+        }
+    }
+
+    // The owners add the tile sums of their particles.
+    __device__ __forceinline__ void tile_end()
+    {
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            two_sum_add(ih[0][c], il[0][c], V->ts[c][lane]);
+            two_sum_add(ih[1][c], il[1][c], V->ts[c][lane + 32]);
+        }
+        __syncwarp();
+    }
+
+    // Cell tile: ids in S.tj[0..take); lane j owns cell j.
     __device__ __forceinline__ void cells(Smem &S, int take)
     {
+        CellSrc c;
+        int cid = -1;
         if (lane < take) {
-            const int c = S.tj[lane];
-            float4 a = cf0[c], bb = cf1[c], cc = cf2[c];
-            S.t0[lane] = make_float4(__fadd_rn(__fsub_rn(a.x, ct.x), bb.x),
-                                     __fadd_rn(__fsub_rn(a.y, ct.y), bb.y),
-                                     __fadd_rn(__fsub_rn(a.z, ct.z), bb.z), a.w);
-            S.t1[lane] = make_float4(bb.w, cc.x, -(bb.w + cc.x), cc.y);
-            S.t2[lane] = make_float4(cc.z, cc.w, 0.0f, 0.0f);
+            cid = S.tj[lane];
+            const float4 a = cf0[cid], bb = cf1[cid], cc = cf2[cid];
+            c.X = dup2(__fadd_rn(__fsub_rn(a.x, ct.x), bb.x));
+            c.Y = dup2(__fadd_rn(__fsub_rn(a.y, ct.y), bb.y));
+            c.Z = dup2(__fadd_rn(__fsub_rn(a.z, ct.z), bb.z));
+            c.M = dup2(a.w);
+            c.M3 = dup2(-3.0f * a.w);
+            c.Qxx = dup2(bb.w);
+            c.Qyy = dup2(cc.x);
+            c.Qzz = dup2(-(bb.w + cc.x));
+            c.Qxy = dup2(cc.y);
+            c.Qxz = dup2(cc.z);
+            c.Qyz = dup2(cc.w);
+        } else {
+            c.X = c.Y = c.Z = dup2(-PAD);
+            c.M = c.M3 = c.Qxx = c.Qyy = c.Qzz = c.Qxy = c.Qxz = c.Qyz = dup2(0.0f);
         }
-        __syncwarp();
-        float s0[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f};
-        constexpr int NS = 2, NV = 10, LPS = 32 / NS;
-        for (int j = 0; j < take; j += NS) {
-            float acc[NS][NV];
+        __syncwarp();  // S.tj is rewritten by the walk after the tile
+        f2 acc[10];
 #pragma unroll
-            for (int u = 0; u < NS; ++u) {
+        for (int v = 0; v < 10; ++v) acc[v] = dup2(0.0f);
+        const f2 e2 = dup2(k.eps2);
+        for (int ch = 0; ch < npairs; ch += NSP) {
+            float r[NSP][6];
 #pragma unroll
-                for (int q = 0; q < NV; ++q) acc[u][q] = 0.f;
-                if (j + u < take) {
-                    const float4 a = S.t0[j + u], B = S.t1[j + u], Cq = S.t2[j + u];
-                    cell_one(a, B, Cq, p0, w0, s0, acc[u]);
-                    cell_one(a, B, Cq, p1, w1, s1, acc[u]);
-                }
+            for (int u = 0; u < NSP; ++u) {
+                const int j = 2 * (ch + u);
+                f2 jx, jy, jz;
+                cell_pair(c, ld2(V->nx, j), ld2(V->ny, j), ld2(V->nz, j),
+                          ld2(V->wx, j), ld2(V->wy, j), ld2(V->wz, j), e2, acc,
+                          jx, jy, jz);
+                r[u][0] = jx.x; r[u][1] = jy.x; r[u][2] = jz.x;
+                r[u][3] = jx.y; r[u][4] = jy.y; r[u][5] = jz.y;
             }
-            reduce_scatter<NS, NV>(acc, lane);
-            const int src = j + src_of<NS>(lane);
-            if (src < take) {
-                const size_t base = (size_t)S.tj[src] * 10;
-                for (int v = lane & (LPS - 1); v < NV; v += LPS)
-                    atomicAdd(&cadj[base + v], k.G * (double)pick<NV>(acc[0], v));
-            }
+            flush(r, ch);
         }
-        for (int q = 0; q < 3; ++q) {
-            g0[q] += (double)s0[q];
-            g1[q] += (double)s1[q];
+        tile_end();
+        if (cid >= 0) {
+            double *dst = cadj + (size_t)cid * 10;
+#pragma unroll
+            for (int v = 0; v < 10; ++v)
+                atomicAdd(dst + v, k.G * (double)(acc[v].x + acc[v].y));
         }
-        __syncwarp();
     }
 
-    // One particle against one cell: i-side sum into s, cell adjoints
-    // (aM, acom[3], S xx yy zz xy xz yz) into acc.
-    __device__ __forceinline__ void cell_one(float4 a, float4 B, float4 Cq,
-                                             float4 p, float3 w, float *s,
-                                             float *acc)
-    {
-        const float dx = a.x - p.x, dy = a.y - p.y, dz = a.z - p.z;
-        const float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, k.eps2)));
-        const float ri = rsqrtf(s2);
-        const float ri2 = ri * ri;
-        const float ri3 = ri * ri2, ri5 = ri3 * ri2, ri7 = ri5 * ri2,
-                    ri9 = ri7 * ri2;
-        // Q = [[B.x, B.w, Cq.x], [B.w, B.y, Cq.y], [Cq.x, Cq.y, B.z]]
-        const float qx = fmaf(B.x, dx, fmaf(B.w, dy, Cq.x * dz));
-        const float qy = fmaf(B.w, dx, fmaf(B.y, dy, Cq.y * dz));
-        const float qz = fmaf(Cq.x, dx, fmaf(Cq.y, dy, B.z * dz));
-        const float wqx = fmaf(B.x, w.x, fmaf(B.w, w.y, Cq.x * w.z));
-        const float wqy = fmaf(B.w, w.x, fmaf(B.y, w.y, Cq.y * w.z));
-        const float wqz = fmaf(Cq.x, w.x, fmaf(Cq.y, w.y, B.z * w.z));
-        const float dqd = fmaf(dx, qx, fmaf(dy, qy, dz * qz));
-        const float wd = fmaf(w.x, dx, fmaf(w.y, dy, w.z * dz));
-        const float wqd = fmaf(w.x, qx, fmaf(w.y, qy, w.z * qz));
-        const float M = a.w;
-        // J^T w = M (w ri3 - 3 wd d ri5) - (Q w ri5 - 5 wQd d ri7)
-        //         + 2.5 (2 wd Qd ri7 + dQd w ri7 - 7 dQd wd d ri9)
-        const float cw = M * ri3 + 2.5f * dqd * ri7;
-        const float cd = -3.0f * M * wd * ri5 + 5.0f * wqd * ri7
-                         - 17.5f * dqd * wd * ri9;
-        const float cq = 5.0f * wd * ri7;
-        const float jx = cw * w.x + cd * dx + cq * qx - ri5 * wqx;
-        const float jy = cw * w.y + cd * dy + cq * qy - ri5 * wqy;
-        const float jz = cw * w.z + cd * dz + cq * qz - ri5 * wqz;
-        s[0] -= jx;
-        s[1] -= jy;
-        s[2] -= jz;
-        acc[0] += wd * ri3;
-        acc[1] += jx;
-        acc[2] += jy;
-        acc[3] += jz;
-        const float h5 = -0.5f * ri5, t7 = 2.5f * wd * ri7;
-        acc[4] += 2.0f * h5 * w.x * dx + t7 * dx * dx;
-        acc[5] += 2.0f * h5 * w.y * dy + t7 * dy * dy;
-        acc[6] += 2.0f * h5 * w.z * dz + t7 * dz * dz;
-        acc[7] += h5 * (w.x * dy + w.y * dx) + t7 * dx * dy;
-        acc[8] += h5 * (w.x * dz + w.z * dx) + t7 * dx * dz;
-        acc[9] += h5 * (w.y * dz + w.z * dy) + t7 * dy * dz;
-    }
-
-    // Particle tile: sorted ids in S.tj[0..take).
+    // Particle tile: sorted ids in S.tj[0..take); lane j owns source j.
     template <bool NEAR>
     __device__ __forceinline__ void particles(Smem &S, int take)
     {
+        PartSrc p;
+        int sj = -1;
         if (lane < take) {
-            const int j = S.tj[lane];
-            S.t0[lane] = rel(phi[j], plo[j], ct);
-        }
-        __syncwarp();
-        float s0[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f};
-        constexpr int NS = 8, NV = 4;
-        for (int j = 0; j < take; j += NS) {
-            float acc[NS][NV];
-#pragma unroll
-            for (int u = 0; u < NS; ++u) {
-#pragma unroll
-                for (int q = 0; q < NV; ++q) acc[u][q] = 0.f;
-                if (j + u < take) {
-                    const float4 a = S.t0[j + u];
-                    const int kj = S.tj[j + u];
-                    pair_one<NEAR>(a, kj == k0, p0, w0, s0, acc[u]);
-                    pair_one<NEAR>(a, kj == k1, p1, w1, s1, acc[u]);
-                }
-            }
-            reduce_scatter<NS, NV>(acc, lane);
-            const int src = j + src_of<NS>(lane);
-            if (src < take) {
-                const int v = lane & 3;  // 32 / NS = 4 lanes per source
-                const int o = order[S.tj[src]];
-                double *dst = v < 3 ? gpos + (size_t)v * n + o : gmass + o;
-                atomicAdd(dst, k.G * (double)pick<NV>(acc[0], v));
-            }
-        }
-        for (int q = 0; q < 3; ++q) {
-            g0[q] += (double)s0[q];
-            g1[q] += (double)s1[q];
-        }
-        __syncwarp();
-    }
-
-    // One particle against one source particle (self pairs contribute 0).
-    template <bool NEAR>
-    __device__ __forceinline__ void pair_one(float4 a, bool self, float4 p,
-                                             float3 w, float *s, float *acc)
-    {
-        const float dx = a.x - p.x, dy = a.y - p.y, dz = a.z - p.z;
-        const float s2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, k.eps2)));
-        const float ri = (s2 > 0.0f && !self) ? rsqrtf(s2) : 0.0f;
-        const float ri2 = ri * ri;
-        const float ri3 = ri2 * ri;
-        float phi_, psi;
-        if (NEAR) {
-            const float sv = s2 * ri;
-            const float x = __saturatef(fmaf(sv, k.kA, k.kB));
-            const float x2 = x * x, x4 = x2 * x2;
-            float pk = fmaf(-20.0f, x, 70.0f);
-            pk = fmaf(pk, x, -84.0f);
-            pk = fmaf(pk, x, 35.0f);
-            const float K = pk * x4;
-            const float omx = 1.0f - x;
-            const float Kp = 140.0f * (x2 * x) * (omx * omx * omx) * k.kA;
-            // products ordered so that K = 0 with a huge 1/s never forms 0*inf
-            phi_ = ((K * ri) * ri) * ri;
-            psi = ((((Kp * ri) * ri) * ri) * ri) - 3.0f * (((phi_ * ri) * ri));
+            sj = S.tj[lane];
+            const float4 a = rel(phi[sj], plo[sj], ct);
+            p.X = dup2(a.x);
+            p.Y = dup2(a.y);
+            p.Z = dup2(a.z);
+            p.m = dup2(a.w);
         } else {
-            phi_ = ri3;
-            psi = -3.0f * ri3 * ri2;
+            p.X = p.Y = p.Z = dup2(-PAD);
+            p.m = dup2(0.0f);
         }
-        const float wd = fmaf(w.x, dx, fmaf(w.y, dy, w.z * dz));
-        const float m = a.w;
-        const float jx = m * fmaf(phi_, w.x, psi * wd * dx);
-        const float jy = m * fmaf(phi_, w.y, psi * wd * dy);
-        const float jz = m * fmaf(phi_, w.z, psi * wd * dz);
-        s[0] -= jx;
-        s[1] -= jy;
-        s[2] -= jz;
-        acc[0] += jx;
-        acc[1] += jy;
-        acc[2] += jz;
-        acc[3] += phi_ * wd;
+        __syncwarp();
+        f2 acc[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] = dup2(0.0f);
+        const f2 e2 = dup2(k.eps2), kA = dup2(k.kA), kB = dup2(k.kB);
+        const int self = sj - gfirst;  // the source's slot if it is in the group
+        for (int ch = 0; ch < npairs; ch += NSP) {
+            float r[NSP][6];
+#pragma unroll
+            for (int u = 0; u < NSP; ++u) {
+                const int j = 2 * (ch + u);
+                f2 jx, jy, jz;
+                pair_pair<NEAR>(p, ld2(V->nx, j), ld2(V->ny, j), ld2(V->nz, j),
+                                ld2(V->wx, j), ld2(V->wy, j), ld2(V->wz, j),
+                                self == j, self == j + 1, e2, kA, kB, acc, jx,
+                                jy, jz);
+                r[u][0] = jx.x; r[u][1] = jy.x; r[u][2] = jz.x;
+                r[u][3] = jx.y; r[u][4] = jy.y; r[u][5] = jz.y;
+            }
+            flush(r, ch);
+        }
+        tile_end();
+        if (sj >= 0) {
+            const int o = order[sj];
+#pragma unroll
+            for (int v = 0; v < 3; ++v)
+                atomicAdd(gpos + (size_t)v * n + o, k.G * (double)(acc[v].x + acc[v].y));
+            atomicAdd(gmass + o, k.G * (double)(acc[3].x + acc[3].y));
+        }
     }
 };
 
-__global__ void __launch_bounds__(VW * 32)
+__global__ void __launch_bounds__(VW * 32, P3T_VJP_MIN_BLOCKS)
 k_walk_vjp(const int *__restrict__ gclus,
            const ClusterConsts *__restrict__ ccs,
            const int2 *__restrict__ grange,
@@ -302,6 +415,7 @@ k_walk_vjp(const int *__restrict__ gclus,
            const int *__restrict__ gperm, P3TDevState *st)
 {
     __shared__ Smem smem[VW];
+    __shared__ VjpSmem vsm[VW];
     const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Smem &S = smem[wi];
     if (st->error) return;  // no valid tree
@@ -316,18 +430,32 @@ k_walk_vjp(const int *__restrict__ gclus,
         const int cl = gclus[g];
         const ClusterConsts cc = ccs[cl];
         VjpEval ev;
+        ev.V = &vsm[wi];
+        ev.lane = lane;
+        ev.gfirst = gr.x;
+        ev.npairs = ((gr.y + 2 * NSP - 1) / (2 * NSP)) * NSP;
         ev.ct = gctr[g];
-        ev.k0 = gr.x + lane;
-        ev.k1 = gr.x + 32 + lane;
-        const bool v0 = lane < gr.y, v1 = lane + 32 < gr.y;
-        const int o0 = v0 ? order[ev.k0] : 0, o1 = v1 ? order[ev.k1] : 0;
-        ev.p0 = v0 ? rel(phi[ev.k0], plo[ev.k0], ev.ct) : vpad();
-        ev.p1 = v1 ? rel(phi[ev.k1], plo[ev.k1], ev.ct) : vpad();
-        ev.w0 = v0 ? make_float3(w[o0], w[(size_t)n + o0], w[2 * (size_t)n + o0])
-                   : make_float3(0.f, 0.f, 0.f);
-        ev.w1 = v1 ? make_float3(w[o1], w[(size_t)n + o1], w[2 * (size_t)n + o1])
-                   : make_float3(0.f, 0.f, 0.f);
-        for (int q = 0; q < 3; ++q) ev.g0[q] = ev.g1[q] = 0.0;
+        // stage the group's particles; slots past the group are padding
+        __syncwarp();  // the previous group's reads of vsm are done
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int slot = lane + 32 * h;
+            float4 p = make_float4(PAD, PAD, PAD, 0.0f);
+            float3 wv = make_float3(0.0f, 0.0f, 0.0f);
+            if (slot < gr.y) {
+                const int kk = gr.x + slot, o = order[kk];
+                p = rel(phi[kk], plo[kk], ev.ct);
+                wv = make_float3(w[o], w[(size_t)n + o], w[2 * (size_t)n + o]);
+            }
+            ev.V->nx[slot] = -p.x;
+            ev.V->ny[slot] = -p.y;
+            ev.V->nz[slot] = -p.z;
+            ev.V->wx[slot] = wv.x;
+            ev.V->wy[slot] = wv.y;
+            ev.V->wz[slot] = wv.z;
+            for (int c = 0; c < 3; ++c) ev.ih[h][c] = ev.il[h][c] = 0.0f;
+        }
+        __syncwarp();
         ev.phi = phi;
         ev.plo = plo;
         ev.cf0 = cf0;
@@ -338,7 +466,6 @@ k_walk_vjp(const int *__restrict__ gclus,
         ev.gmass = gmass;
         ev.cadj = cadj;
         ev.n = n;
-        ev.lane = lane;
         ev.k = k;
         ev.k.eps2 = cc.eps2;
         ev.k.kA = cc.kA;
@@ -349,12 +476,17 @@ k_walk_vjp(const int *__restrict__ gclus,
             if (lane == 0) p3t_raise(st, P3T_ERR_CAPACITY);
             continue;
         }
-        if (v0)
-            for (int q = 0; q < 3; ++q)
-                atomicAdd(&gpos[(size_t)q * n + o0], k.G * ev.g0[q]);
-        if (v1)
-            for (int q = 0; q < 3; ++q)
-                atomicAdd(&gpos[(size_t)q * n + o1], k.G * ev.g1[q]);
+        // dL/dx_i = -G sum J w over the particle's sources
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int slot = lane + 32 * h;
+            if (slot < gr.y) {
+                const int o = order[gr.x + slot];
+                for (int q = 0; q < 3; ++q)
+                    atomicAdd(&gpos[(size_t)q * n + o],
+                              -k.G * ((double)ev.ih[h][q] + (double)ev.il[h][q]));
+            }
+        }
     }
 }
 

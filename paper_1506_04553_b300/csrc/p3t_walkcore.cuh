@@ -19,7 +19,6 @@ constexpr int STACK = 768;  // child ranges per warp
 constexpr int RING = 64;    // ring capacity; at most 63 entries are held
 
 struct __align__(16) Smem {
-    float4 t0[32], t1[32], t2[32];  // staged sources (evaluator's use)
     int stack[STACK];               // packed child ranges: child*8 + nchild-1
     int cb[32];                     // cells of the current walk batch
     int pc[RING];                   // accepted cells
