@@ -285,22 +285,8 @@ __device__ __forceinline__ int digit_at(u64 key, int L)
     return (int)((key >> (3 * (P3T_MAX_LEVEL - L))) & 7u);
 }
 
-// first position p in [lo, hi) with digit_at(key[p], L) >= d
-__device__ __forceinline__ int lower_digit(const u64 *__restrict__ key, int lo,
-                                           int hi, int L, int d)
-{
-    while (lo < hi) {
-        int mid = lo + ((hi - lo) >> 1);
-        if (digit_at(key[mid], L) < d)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    return lo;
-}
-
-// Same as lower_digit, by a whole warp: 32 probes per step (the range
-// shrinks 32-fold per dependent load instead of 2-fold).
+// First position p in [lo, hi) with digit_at(key[p], L) >= d, by a whole
+// warp: 32 probes per step (the range shrinks 32-fold per dependent load).
 __device__ __forceinline__ int warp_lower_digit(const u64 *__restrict__ key,
                                                 int lo, int hi, int L, int d,
                                                 int lane)
@@ -321,6 +307,39 @@ __device__ __forceinline__ int warp_lower_digit(const u64 *__restrict__ key,
     const bool ge = p < hi && digit_at(key[p], L) >= d;
     const unsigned m = __ballot_sync(0xffffffffu, ge);
     return m ? lo + __ffs(m) - 1 : hi;
+}
+
+// Child boundaries of the cell [lo, hi) by one warp reading its keys in
+// coalesced chunks of 32: the digit at level L never decreases inside a cell,
+// so b[d] (first position with digit >= d) is the position where the digit
+// steps over d.  Each boundary is found by exactly one lane and written to
+// the warp's sb[0..8); b[d] = hi for digits above the last one present.
+__device__ __forceinline__ void warp_scan_digits(const u64 *__restrict__ key,
+                                                 int lo, int hi, int L,
+                                                 int *sb, int lane)
+{
+    constexpr int K = 8;  // chunks loaded before any is examined
+    if (lane < 9) sb[lane] = hi;
+    __syncwarp();
+    int prev_last = 0;  // digits below the first key's are empty
+    for (int base = lo; base < hi; base += 32 * K) {
+        int dg[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            const int p = base + 32 * u + lane;
+            dg[u] = p < hi ? digit_at(key[p], L) : 7;
+        }
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            const int p = base + 32 * u + lane;
+            int prev = __shfl_up_sync(0xffffffffu, dg[u], 1);
+            if (lane == 0) prev = prev_last;
+            if (p < hi)
+                for (int d = prev + 1; d <= dg[u]; ++d) sb[d] = p;
+            prev_last = __shfl_sync(0xffffffffu, dg[u], 31);
+        }
+    }
+    __syncwarp();
 }
 
 // Children of one cell (boundaries b[0..8]) appended to the cell arrays.
@@ -350,42 +369,37 @@ __device__ __forceinline__ void emit_children(int c, int L, int cap,
     node[c].w = (L << 8) | k;
 }
 
-constexpr int BIG_CELL = 2048;  // cells split by a whole warp
+constexpr int BIG_CELL = 2048;  // above: 32-ary searches; below: one scan
 
+// One warp per cell of level L that holds more than n_leaf particles.
 __global__ void __launch_bounds__(TB)
 k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
              int4 *__restrict__ node, int *__restrict__ parent,
              P3TDevState *st)
 {
+    __shared__ int sbuf[TB / 32][9];
     const int beg = st->level_start[L], end = st->level_start[L + 1];
-    const bool stop = st->error != 0;
-    // big cells: one warp each
-    {
-        const int lane = threadIdx.x & 31;
-        const int wg = (blockIdx.x * TB + threadIdx.x) >> 5;
-        const int nw = gridDim.x * (TB / 32);
-        for (int c = beg + wg; c < end && !stop; c += nw) {
-            const int4 nd = node[c];
-            if (nd.y <= BIG_CELL || L >= P3T_MAX_LEVEL) continue;
-            int b[9];
-            b[0] = nd.x;
-            b[8] = nd.x + nd.y;
-            for (int d = 1; d < 8; ++d)
-                b[d] = warp_lower_digit(key, b[d - 1], b[8], L + 1, d, lane);
-            if (lane == 0) emit_children(c, L, cap, b, node, parent, st);
-        }
-    }
-    for (int c = beg + blockIdx.x * TB + threadIdx.x; c < end && !stop;
-         c += gridDim.x * TB) {
-        int4 nd = node[c];
-        if (nd.y <= n_leaf || nd.y > BIG_CELL || L >= P3T_MAX_LEVEL) continue;
+    const bool stop = st->error != 0 || L >= P3T_MAX_LEVEL;
+    const int lane = threadIdx.x & 31;
+    const int wg = (blockIdx.x * TB + threadIdx.x) >> 5;
+    const int nw = gridDim.x * (TB / 32);
+    int *sb = sbuf[threadIdx.x >> 5];
+    for (int c = beg + wg; c < end && !stop; c += nw) {
+        const int4 nd = node[c];
+        if (nd.y <= n_leaf) continue;
         int b[9];
         b[0] = nd.x;
         b[8] = nd.x + nd.y;
+        if (nd.y > BIG_CELL) {
+            for (int d = 1; d < 8; ++d)
+                b[d] = warp_lower_digit(key, b[d - 1], b[8], L + 1, d, lane);
+        } else {
+            warp_scan_digits(key, b[0], b[8], L + 1, sb, lane);
 #pragma unroll
-        for (int d = 1; d < 8; ++d)
-            b[d] = lower_digit(key, b[d - 1], b[8], L + 1, d);
-        emit_children(c, L, cap, b, node, parent, st);
+            for (int d = 1; d < 8; ++d) b[d] = sb[d];
+            __syncwarp();  // sb is rewritten by the next cell
+        }
+        if (lane == 0) emit_children(c, L, cap, b, node, parent, st);
     }
     // the last block to finish closes the next level's range
     __syncthreads();
@@ -708,8 +722,9 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     k_tree_init<<<(nc + 255) / 256, 256, 0, s>>>(nc, off, c->node, c->parent,
                                                  c->st);
     const int cap = (int)c->cap_cells;
+    // one warp per cell: enough warps to fill every SM once
     for (int L = 0; L < P3T_MAX_LEVEL; ++L)
-        k_tree_split<<<grid_small, TB, 0, s>>>(L, c->p.n_leaf, cap, c->key_a,
+        k_tree_split<<<c->sms * 8, TB, 0, s>>>(L, c->p.n_leaf, cap, c->key_a,
                                                 c->node, c->parent, c->st);
     k_moments<true><<<c->sms * 8, TB, 0, s>>>(0, c->xs, c->ms, n, c->node,
                                                c->cM, c->ccom, c->cQ, c->cbmin,
