@@ -46,6 +46,15 @@ N_GROUP = 64
 SEED = 2
 
 # FP32 flops per interaction (FMA = 2), fixed from the force kernel source
+# Algorithmic bytes of the HBM-side steps.  Build: read x and m (32 B),
+# write key and index (12 B), 8 radix passes reading and writing both (192
+# B), FP64 and FP32 Morton-order copies (64 B) per particle; FP64 moments,
+# box and FP32 records per cell (228 B).  Kick: read and write v (48 B),
+# read a (12 B).  Drift: read and write x (48 B), read v (24 B).
+B_BUILD_PER_PARTICLE = 32 + 12 + 8 * 24 + 64
+B_BUILD_PER_CELL = 228
+B_KICK = 60
+B_DRIFT = 72
 FLOPS_PC = 49
 FLOPS_PP_FAR = 18
 FLOPS_PP_NEAR = 31
@@ -374,6 +383,29 @@ def run_ours(args, world, rank, local):
     value = whole_job_rate(n, args.steps, ms, world)
     ctx.set_params(params)
 
+    # HBM-side steps: kick and drift alone, `reps` launches captured in a
+    # CUDA graph so that host launch costs stay out (arrays exceed L2)
+    def timed(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(reps):
+                fn()
+        g.replay()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    kick_ms = timed(lambda: P.kick(vel, acc, 0.0))
+    drift_ms = timed(lambda: P.drift(pos, vel, 0.0))
+    st = ctx.stats()
+    cells_per_particle = st["n_cells"] / n
+    alu = P.alu_peaks()
+
     # interactions and roofline of the force kernel
     int_pc, int_pp, int_ppn = prof["int_pc"], prof["int_pp"], prof["int_pp_near"]
     nprof = max(prof["forces"], 1)
@@ -417,6 +449,33 @@ def run_ours(args, world, rank, local):
                                   f"{clk:.0f} MHz (max SM clock)"},
         "gpu_launches": launches,
         "clocks": clocks,
+    }
+    # measured ALU ceilings beside the nominal peak (p3t_alu_peaks)
+    fma_meas = max(alu["fma_flops"], alu["fma2_flops"]) / 1e12
+    line["roofline"]["peak_measured"] = {
+        "fp32_fma_tflops": alu["fma_flops"] / 1e12,
+        "fp32x2_fma_tflops": alu["fma2_flops"] / 1e12,
+        "rsqrt_tops": alu["rsqrt_ops"] / 1e12,
+        "note": "register-only FMA and rsqrt loops on every SM (p3t_alu_peaks)"}
+    line["roofline"]["frac_of_measured"] = achieved / fma_meas if achieved else None
+    # HBM-bound steps against the measured copy bandwidth
+    hbm = float(peaks.get("hbm_gbs", 6518.0))
+    b_build = (B_BUILD_PER_PARTICLE + B_BUILD_PER_CELL * cells_per_particle) * n
+    build_ms = prof["build_ms"] / nprof
+    line["hbm"] = {
+        "peak_gbs": hbm,
+        "build": {"bytes": b_build, "ms": build_ms,
+                  "gbs": b_build / (build_ms * 1e-3) / 1e9,
+                  "frac": b_build / (build_ms * 1e-3) / 1e9 / hbm,
+                  "note": f"{B_BUILD_PER_PARTICLE} B/particle + "
+                          f"{B_BUILD_PER_CELL} B/cell algorithmic; latency and "
+                          f"FP64 bound, not HBM"},
+        "kick": {"bytes_per_particle": B_KICK, "ms": kick_ms,
+                 "gbs": B_KICK * n / (kick_ms * 1e-3) / 1e9,
+                 "frac": B_KICK * n / (kick_ms * 1e-3) / 1e9 / hbm},
+        "drift": {"bytes_per_particle": B_DRIFT, "ms": drift_ms,
+                  "gbs": B_DRIFT * n / (drift_ms * 1e-3) / 1e9,
+                  "frac": B_DRIFT * n / (drift_ms * 1e-3) / 1e9 / hbm},
     }
     # backward pass (gradient of sum_i w_i . a_i): fwd = build + force,
     # bwd = p3t_long_force_vjp on the same tree

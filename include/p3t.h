@@ -277,6 +277,17 @@ int p3t_get_profile(p3t_ctx *ctx, p3t_profile *out, int reset);
  * contexts, all entry points). */
 int64_t p3t_launch_count(void);
 
+/* Measured arithmetic ceilings of the current device, for the roofline of
+ * the force kernel beside its nominal FP32 peak.  Runs register-only loops
+ * over every SM: independent FP32 FMA chains (scalar, and FP32x2 as the
+ * force kernel issues them) and chains of the hardware reciprocal square
+ * root.  Each loop is timed with CUDA events after one warm-up launch, for
+ * about 10 ms, on a private stream; the call synchronises the device work it
+ * launched and allocates (and frees) one small output buffer.
+ * fma_flops, fma2_flops: flop/s (an FMA counts 2); rsqrt_ops: 1/sqrt per
+ * second.  Any pointer may be NULL.  Errors: P3T_ERR_CUDA. */
+int p3t_alu_peaks(double *fma_flops, double *fma2_flops, double *rsqrt_ops);
+
 /* ---- inspection (tests and tools; each call synchronises and copies to
  * HOST buffers sized from p3t_get_stats) ---- */
 

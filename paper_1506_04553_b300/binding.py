@@ -99,6 +99,7 @@ _sigs = {
     "p3t_set_ensemble": [_vp, C.c_int32, _vp, _vp, _vp, _vp],
     "p3t_autotune": [_vp, _i64, _vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp],
     "p3t_get_profile": [_vp, _vp, C.c_int],
+    "p3t_alu_peaks": [_vp, _vp, _vp],
 }
 for _name, _args in _sigs.items():
     _f = getattr(_lib, _name)
@@ -113,6 +114,15 @@ _lib.p3t_launch_count.restype = C.c_int64
 def launch_count() -> int:
     """Kernels launched by libp3t since it was loaded."""
     return int(_lib.p3t_launch_count())
+
+
+def alu_peaks() -> dict:
+    """Measured FP32 FMA (scalar and FP32x2) flop/s and rsqrt/s of the
+    current device (p3t_alu_peaks)."""
+    v = [C.c_double(), C.c_double(), C.c_double()]
+    _check(_lib.p3t_alu_peaks(*[C.byref(x) for x in v]), "p3t_alu_peaks")
+    return {"fma_flops": v[0].value, "fma2_flops": v[1].value,
+            "rsqrt_ops": v[2].value}
 
 
 def _check(code: int, where: str):
