@@ -132,6 +132,12 @@ def _declare(lib):
     lib.orc_tree_vjp.argtypes = [_p, _d, _d, _d, _d, _p, _p, _p, C.c_int]
     lib.orc_tree_update.restype = None
     lib.orc_tree_update.argtypes = [_p, _p, _p]
+    lib.orc_hard_force.restype = None
+    lib.orc_hard_force.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _d, _d, _d,
+                                   _p, _p]
+    lib.orc_hermite.restype = C.c_int
+    lib.orc_hermite.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _d, _d, _d, _d,
+                                _d, _d, C.c_int, C.c_int, _p]
 
 
 def _ptr(a: np.ndarray):
@@ -248,6 +254,60 @@ def neighbours(pos, h, rows=None, threads=None):
     lib.orc_neighbours_fill(n, _ptr(pos), h, rp, nr, _ptr(off), _ptr(idx),
                             _ptr(cnt2), th)
     return off, idx[: int(off[-1])]
+
+
+# --------------------------------------------------------------------------
+# Hard part: F_hard over neighbour rows and the Hermite integrator
+# --------------------------------------------------------------------------
+
+def _csr(off, idx, n):
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    if off.shape != (n + 1,):
+        raise ValueError("offsets must have n + 1 entries")
+    if idx.size == 0:
+        idx = np.zeros(1, dtype=np.int32)
+    return off, idx
+
+
+def hard_force(pos, vel, mass, off, idx, *, G=1.0, eps=0.0, r_cut=1.0,
+               gamma=0.1):
+    """Hard acceleration and jerk of every particle from its neighbour row
+    (Eq. 7 with the pair weight 1 - K and its time derivative); returns
+    (a, jerk), each n x 3."""
+    lib = _load()
+    pos = _f64(pos, (-1, 3))
+    vel = _f64(vel, (-1, 3))
+    mass = _f64(mass)
+    n = pos.shape[0]
+    off, idx = _csr(off, idx, n)
+    a = np.zeros((n, 3))
+    jk = np.zeros((n, 3))
+    lib.orc_hard_force(n, _ptr(pos), _ptr(vel), _ptr(mass), _ptr(off),
+                       _ptr(idx), G, eps, r_cut, gamma, _ptr(a), _ptr(jk))
+    return a, jk
+
+
+def hermite(pos, vel, mass, off, idx, *, dt_soft, G=1.0, eps=0.0, r_cut=1.0,
+            gamma=0.1, eta=0.1, alpha=0.1, p=2, kmax=30):
+    """Fourth-order Hermite integration with block timesteps over dt_soft of
+    every particle with a non-empty neighbour row (dt_max = dt_soft 2^-p,
+    levels down to dt_max 2^-kmax); particles with an empty row drift.
+    Returns (pos, vel, stats) with stats = (block steps, particle steps,
+    pair evaluations, steps capped at kmax)."""
+    lib = _load()
+    pos = _f64(pos, (-1, 3)).copy()
+    vel = _f64(vel, (-1, 3)).copy()
+    mass = _f64(mass)
+    n = pos.shape[0]
+    off, idx = _csr(off, idx, n)
+    st = np.zeros(4, dtype=np.int64)
+    rc = lib.orc_hermite(n, _ptr(pos), _ptr(vel), _ptr(mass), _ptr(off),
+                         _ptr(idx), G, eps, r_cut, gamma, eta, alpha, dt_soft,
+                         p, kmax, _ptr(st))
+    if rc != 0:
+        raise ValueError("orc_hermite: bad arguments")
+    return pos, vel, tuple(int(v) for v in st)
 
 
 def is_neighbour(pi, pj, h) -> bool:

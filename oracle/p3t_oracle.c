@@ -1221,3 +1221,215 @@ void orc_tree_update(orc_tree *t, const double *pos, const double *m)
     }
     for (int64_t c = 0; c < t->ncell; ++c) orc_cell_moments(t, c);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Hard part (Sect. 2.1 and 2.2): F_hard over the neighbour lists and the   */
+/* fourth-order Hermite integrator with block timesteps                     */
+/* ------------------------------------------------------------------------ */
+/* Positions and velocities are n x 3 row-major; neighbour rows are CSR
+ * (off[n+1], idx) in ascending j, as the neighbour search returns them.
+ * Every expression is written in the order it is evaluated. */
+
+static double orc_dot3(const double *a, const double *b)
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+/* Hard acceleration and jerk of particle i from its neighbour row: the pair
+ * force of Eq. 7 (weight 1 - K(s), s of Eq. 2, q = x_i - x_j) and its time
+ * derivative along u = v_i - v_j, with ds/dt = (q.u)/s:
+ *   a_i  = -sum G m_j (1-K) q / s^3
+ *   da_i = -sum G m_j [ (1-K) (u - 3 (q.u) q / s^2) / s^3
+ *                       - (dK/ds) ((q.u) / s) q / s^3 ]. */
+static void orc_hard_one(int64_t i, const double *x, const double *v,
+                         const double *m, const int64_t *off,
+                         const int32_t *idx, double G, double eps2,
+                         double r_cut, double gamma, double *a, double *jk)
+{
+    double acc[3] = {0.0, 0.0, 0.0}, jrk[3] = {0.0, 0.0, 0.0};
+    for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+        int64_t j = idx[e];
+        double q[3], u[3];
+        for (int c = 0; c < 3; ++c) {
+            q[c] = x[3 * i + c] - x[3 * j + c];
+            u[c] = v[3 * i + c] - v[3 * j + c];
+        }
+        double s2 = orc_dot3(q, q) + eps2;
+        double s = sqrt(s2);
+        double xk = (s / r_cut - gamma) / (1.0 - gamma);
+        double w = 1.0 - orc_K(xk);
+        double dKds = orc_dKdx(xk) / ((1.0 - gamma) * r_cut);
+        double s3 = s2 * s;
+        double rv = orc_dot3(q, u);
+        double gm = G * m[j];
+        double fa = gm * w / s3;
+        double c1 = 3.0 * rv / s2;
+        double fb = gm * (dKds * rv / s) / s3;
+        for (int c = 0; c < 3; ++c) {
+            acc[c] = acc[c] - fa * q[c];
+            jrk[c] = jrk[c] - (fa * (u[c] - c1 * q[c]) - fb * q[c]);
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        a[c] = acc[c];
+        jk[c] = jrk[c];
+    }
+}
+
+/* Hard acceleration and jerk of every particle (a, jk: n x 3). */
+void orc_hard_force(int64_t n, const double *x, const double *v,
+                    const double *m, const int64_t *off, const int32_t *idx,
+                    double G, double eps, double r_cut, double gamma,
+                    double *a, double *jk)
+{
+    for (int64_t i = 0; i < n; ++i)
+        orc_hard_one(i, x, v, m, off, idx, G, eps * eps, r_cut, gamma,
+                     a + 3 * i, jk + 3 * i);
+}
+
+/* Block level for a step of at most dt_crit: the smallest k in [kmin, kmax]
+ * with dt_max 2^-k <= dt_crit (kmax when none is). */
+static int orc_level(double dt_crit, double dt_max, int kmin, int kmax)
+{
+    int k = kmin;
+    double dt = ldexp(dt_max, -k);
+    while (k < kmax && dt > dt_crit) {
+        ++k;
+        dt = dt * 0.5;
+    }
+    return k;
+}
+
+/* Fourth-order Hermite integration (Makino & Aarseth 1992) of every
+ * particle with a non-empty neighbour row over dt_soft under H_hard, with
+ * individual block timesteps (the third step of the P3T procedure of
+ * Sect. 2.1 / the sixth of Sect. 2.2); particles with an empty row are
+ * isolated and drift, x <- x + dt_soft v (the fifth step of Sect. 2.2).
+ *
+ * Time is counted in ticks of dt_max 2^-kmax, dt_max = dt_soft 2^-p.  A
+ * particle at level k steps dt_max 2^-k; its time is always a multiple of
+ * its step.  First step: Eq. timestep:2 with eta_s = eta / 10; later steps:
+ * Eq. timestep:0, a_0 = alpha G m_i / r_cut^2, with a^(2) and a^(3) from
+ * the Hermite interpolation of the last step; the level may rise by at most
+ * one per step (the step at most doubles) and is raised further until the
+ * current time is a multiple of the step.  Each block step: the next time
+ * t_n is the smallest t_i + dt_i; every particle is predicted to t_n
+ *   xp = x + v d + a (d^2 / 2) + j (d^3 / 6),  vp = v + a d + j (d^2 / 2),
+ * the particles with t_i + dt_i = t_n get a, j at t_n from the predicted
+ * values (own and neighbours') and are corrected, with h = their step:
+ *   a2 = (-6 (a0 - a1) - h (4 j0 + 2 j1)) / h^2
+ *   a3 = (12 (a0 - a1) + 6 h (j0 + j1)) / h^3
+ *   x = xp + a2 h^4 / 24 + a3 h^5 / 120,  v = vp + a2 h^3 / 6 + a3 h^4 / 24.
+ * stats (may be NULL): [0] block steps, [1] particle steps, [2] pair
+ * evaluations, [3] steps whose level was capped at kmax.
+ * Returns 0, or -1 on bad arguments or allocation failure. */
+int orc_hermite(int64_t n, double *x, double *v, const double *m,
+                const int64_t *off, const int32_t *idx, double G, double eps,
+                double r_cut, double gamma, double eta, double alpha,
+                double dt_soft, int p, int kmax, int64_t *stats)
+{
+    if (n < 0 || p < 0 || kmax < 0 || p + kmax > 60) return -1;
+    const double eps2 = eps * eps;
+    const double dt_max = ldexp(dt_soft, -p);
+    const double tick = ldexp(dt_max, -kmax);
+    const int64_t T = (int64_t)1 << (p + kmax);
+    const double eta_s = eta / 10.0;
+    int64_t st[4] = {0, 0, 0, 0};
+    double *a = malloc(3 * n * sizeof(double) + 1);
+    double *jk = malloc(3 * n * sizeof(double) + 1);
+    double *xp = malloc(3 * n * sizeof(double) + 1);
+    double *vp = malloc(3 * n * sizeof(double) + 1);
+    int64_t *t = malloc(n * sizeof(int64_t) + 1);
+    int *lev = malloc(n * sizeof(int) + 1);
+    if (!a || !jk || !xp || !vp || !t || !lev) {
+        free(a); free(jk); free(xp); free(vp); free(t); free(lev);
+        return -1;
+    }
+    /* start: forces at t = 0 and the first-step levels */
+    for (int64_t i = 0; i < n; ++i) {
+        t[i] = 0;
+        lev[i] = 0;
+        if (off[i + 1] == off[i]) continue;
+        orc_hard_one(i, x, v, m, off, idx, G, eps2, r_cut, gamma, a + 3 * i,
+                     jk + 3 * i);
+        st[2] += off[i + 1] - off[i];
+        double a0 = alpha * G * m[i] / (r_cut * r_cut);
+        double jj = orc_dot3(jk + 3 * i, jk + 3 * i);
+        double crit = INFINITY;
+        if (jj > 0.0)
+            crit = eta_s * sqrt((orc_dot3(a + 3 * i, a + 3 * i) + a0 * a0) / jj);
+        lev[i] = orc_level(crit, dt_max, 0, kmax);
+        if (lev[i] == kmax && ldexp(dt_max, -kmax) > crit) ++st[3];
+    }
+    for (;;) {
+        int64_t tn = T;
+        int any = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (off[i + 1] == off[i] || t[i] == T) continue;
+            int64_t e = t[i] + ((int64_t)1 << (kmax - lev[i]));
+            if (e < tn) tn = e;
+            any = 1;
+        }
+        if (!any) break;
+        ++st[0];
+        /* predict every non-isolated particle to tn */
+        for (int64_t i = 0; i < n; ++i) {
+            if (off[i + 1] == off[i]) continue;
+            double d = (double)(tn - t[i]) * tick;
+            double d2 = d * d * 0.5;
+            double d3 = d * d * d / 6.0;
+            for (int c = 0; c < 3; ++c) {
+                int64_t k = 3 * i + c;
+                xp[k] = x[k] + v[k] * d + a[k] * d2 + jk[k] * d3;
+                vp[k] = v[k] + a[k] * d + jk[k] * d2;
+            }
+        }
+        /* evaluate and correct the particles due at tn */
+        for (int64_t i = 0; i < n; ++i) {
+            if (off[i + 1] == off[i]) continue;
+            int64_t step = (int64_t)1 << (kmax - lev[i]);
+            if (t[i] + step != tn) continue;
+            double a1[3], j1[3];
+            orc_hard_one(i, xp, vp, m, off, idx, G, eps2, r_cut, gamma, a1, j1);
+            ++st[1];
+            st[2] += off[i + 1] - off[i];
+            double h = (double)step * tick;
+            double h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
+            double a2[3], a3[3], a2e[3];
+            for (int c = 0; c < 3; ++c) {
+                int64_t k = 3 * i + c;
+                double da = a[k] - a1[c];
+                a2[c] = (-6.0 * da - h * (4.0 * jk[k] + 2.0 * j1[c])) / h2;
+                a3[c] = (12.0 * da + 6.0 * h * (jk[k] + j1[c])) / h3;
+                x[k] = xp[k] + a2[c] * (h4 / 24.0) + a3[c] * (h5 / 120.0);
+                v[k] = vp[k] + a2[c] * (h3 / 6.0) + a3[c] * (h4 / 24.0);
+                a[k] = a1[c];
+                jk[k] = j1[c];
+                a2e[c] = a2[c] + a3[c] * h;
+            }
+            t[i] = tn;
+            if (tn == T) continue;
+            /* Eq. timestep:0 */
+            double a0 = alpha * G * m[i] / (r_cut * r_cut);
+            double aa = orc_dot3(a1, a1);
+            double a2sq = orc_dot3(a2e, a2e);
+            double num = sqrt(aa + a0 * a0) * sqrt(a2sq) + orc_dot3(j1, j1);
+            double den = sqrt(aa) * sqrt(orc_dot3(a3, a3)) + a2sq;
+            double crit = den > 0.0 ? eta * sqrt(num / den) : INFINITY;
+            int kmin = lev[i] > 0 ? lev[i] - 1 : 0;
+            int k = orc_level(crit, dt_max, kmin, kmax);
+            if (k == kmax && ldexp(dt_max, -kmax) > crit) ++st[3];
+            while (tn % ((int64_t)1 << (kmax - k)) != 0) ++k;
+            lev[i] = k;
+        }
+    }
+    /* isolated particles drift (Sect. 2.2, step 5) */
+    for (int64_t i = 0; i < n; ++i) {
+        if (off[i + 1] != off[i]) continue;
+        for (int c = 0; c < 3; ++c) x[3 * i + c] = x[3 * i + c] + dt_soft * v[3 * i + c];
+    }
+    if (stats)
+        for (int k = 0; k < 4; ++k) stats[k] = st[k];
+    free(a); free(jk); free(xp); free(vp); free(t); free(lev);
+    return 0;
+}
