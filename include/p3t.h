@@ -168,6 +168,67 @@ int p3t_long_force(p3t_ctx *ctx, float *acc, double *pot, void *stream);
 int p3t_long_force_vjp(p3t_ctx *ctx, const float *w, double *grad_pos,
                        double *grad_mass, void *stream);
 
+/* ---- the hard part (Sect. 2.1-2.2): F_hard over the neighbour lists ----
+ *
+ * Hard acceleration and jerk of every particle from its neighbour row (the
+ * CSR lists of p3t_neighbours: offsets int64[n+1], ascending original
+ * indices idx): with q = x_i - x_j, u = v_i - v_j, s^2 = |q|^2 + eps^2
+ * (Eq. 2) and the pair weight 1 - K(s) of Eq. 7 (K of Eq. 12-15, r_cut,
+ * gamma = r_in / r_cut),
+ *   a_i  = -sum_j G m_j (1-K) q / s^3,
+ *   da_i = -sum_j G m_j [(1-K)(u - 3 (q.u) q / s^2) / s^3
+ *                        - (dK/ds)((q.u)/s) q / s^3].
+ * pos, vel: device double[3][n] (SoA, original order); mass device
+ * double[n]; acc, jerk: device double[3][n] written.  FP64, one rounding
+ * per operation in a fixed order.  Stream-ordered, no synchronisation, no
+ * allocation.  Errors: P3T_ERR_INVALID (n < 0, NULL pointers with n > 0,
+ * r_cut < P3T_R_OUT_MIN, gamma outside [0, 1), eps < 0, G <= 0). */
+int p3t_hard_force(int64_t n, const double *pos, const double *vel,
+                   const double *mass, const int64_t *offsets,
+                   const int32_t *idx, double G, double eps, double r_cut,
+                   double gamma, double *acc, double *jerk, void *stream);
+
+/* Parameters of the Hermite integration of the hard part. */
+typedef struct p3t_hermite_params {
+    double eta;      /* accuracy parameter of Eq. timestep:0 (Table 1: 0.1);
+                        the first step uses eta / 10 (Eq. timestep:2) */
+    double alpha;    /* a_0 = alpha G m_i / r_cut^2 (Eq. timestep:1; 0.1) */
+    double dt_soft;  /* the soft step: the hard part runs over [0, dt_soft] */
+    int32_t log2_soft_over_max; /* p: dt_max = dt_soft 2^-p (Table 1: 2) */
+    int32_t kmax;    /* finest level: steps down to dt_max 2^-kmax (1..58-p) */
+} p3t_hermite_params;
+
+/* One hard step of the P3T procedure (Sect. 2.2, steps 5 and 6): particles
+ * with an empty neighbour row are isolated and drift, x <- x + dt_soft v;
+ * every other particle is integrated over dt_soft under H_hard (pair forces
+ * of p3t_hard_force over its row, using the context's G, eps, r_out and
+ * gamma) with the fourth-order Hermite scheme and individual block
+ * timesteps (Makino & Aarseth 1992):
+ *   - time in integer ticks of dt_max 2^-kmax; a particle at level k steps
+ *     dt_max 2^-k and its time is a multiple of its step;
+ *   - first levels from Eq. timestep:2 (eta / 10), later from
+ *     Eq. timestep:0 with a^(2), a^(3) from the Hermite interpolation; a
+ *     step may at most double and is halved until the current time is a
+ *     multiple of it;
+ *   - each block step predicts positions and velocities to the next time
+ *     (third order), evaluates the particles due then from the predicted
+ *     values and corrects them (fourth order).
+ * The rows must be symmetric (those of p3t_neighbours are) and must hold
+ * every particle that comes within r_cut during dt_soft (h = r_cut +
+ * buffer).  The connected components of the neighbour graph are integrated
+ * independently, one warp each.  pos and vel (device double[3][n]) are
+ * updated in place; mass device double[n].  Stream-ordered, no host
+ * synchronisation; scratch (about 140 B per particle) is allocated on the
+ * first call for a larger n.  Counters in p3t_stats (herm_*).
+ * Errors: P3T_ERR_INVALID (arguments, parameters, ensemble layout),
+ * P3T_ERR_CUDA; P3T_ERR_TIMEOUT (latched, see p3t_check) when a component
+ * needs more than 2^26 block steps or the component search does not
+ * settle. */
+int p3t_hard_step(p3t_ctx *ctx, int64_t n, double *pos, double *vel,
+                  const double *mass, const int64_t *offsets,
+                  const int32_t *idx, const p3t_hermite_params *hp,
+                  void *stream);
+
 /* Synchronises `stream` and returns (and clears) the first error latched by
  * a kernel of this context since the last check, or P3T_OK. */
 int p3t_check(p3t_ctx *ctx, void *stream);
@@ -252,6 +313,13 @@ typedef struct p3t_stats {
                                of the force, neighbour and backward kernels
                                traverse identically and hold 768 */
     int64_t nnz;          /* neighbour pairs (after p3t_neighbours) */
+    /* last p3t_hard_step */
+    int64_t herm_block_steps;    /* block steps, summed over components */
+    int64_t herm_particle_steps; /* particle steps (force evaluations) */
+    int64_t herm_pairs;          /* pair evaluations, first forces included */
+    int64_t herm_capped;         /* steps whose level hit kmax */
+    int64_t herm_components;     /* connected components integrated */
+    int64_t herm_max_component;  /* particles in the largest one */
 } p3t_stats;
 int p3t_get_stats(p3t_ctx *ctx, p3t_stats *s);
 

@@ -10,7 +10,8 @@ generators and needs no GPU.
 from __future__ import annotations
 
 _BINDING_NAMES = {"Params", "Context", "P3TError", "kick", "drift",
-                  "library_path", "launch_count", "alu_peaks", "FLAG_NO_SYNC"}
+                  "library_path", "launch_count", "alu_peaks", "FLAG_NO_SYNC",
+                  "HermiteParams", "hard_force"}
 
 __all__ = sorted(_BINDING_NAMES) + ["ics", "binding"]
 

@@ -61,7 +61,14 @@ class _CStats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "n", "n_cells", "n_groups", "n_levels", "list_pc", "list_pp_near",
         "list_pp_far", "int_pc", "int_pp", "int_pp_near", "max_walk_stack",
-        "nnz")]
+        "nnz", "herm_block_steps", "herm_particle_steps", "herm_pairs",
+        "herm_capped", "herm_components", "herm_max_component")]
+
+
+class _CHermite(C.Structure):
+    _fields_ = [("eta", C.c_double), ("alpha", C.c_double),
+                ("dt_soft", C.c_double), ("log2_soft_over_max", C.c_int32),
+                ("kmax", C.c_int32)]
 
 
 class _CProfile(C.Structure):
@@ -100,6 +107,9 @@ _sigs = {
     "p3t_autotune": [_vp, _i64, _vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp],
     "p3t_get_profile": [_vp, _vp, C.c_int],
     "p3t_alu_peaks": [_vp, _vp, _vp],
+    "p3t_hard_force": [_i64, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_double,
+                       C.c_double, C.c_double, _vp, _vp, _vp],
+    "p3t_hard_step": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
 }
 for _name, _args in _sigs.items():
     _f = getattr(_lib, _name)
@@ -284,6 +294,28 @@ class Context:
             self.check(stream)
         return grad_pos, grad_mass
 
+    def hard_step(self, pos, vel, mass, offsets, idx, hp: "HermiteParams",
+                  stream=None, check=True):
+        """One hard step (p3t_hard_step): isolated particles drift, the others
+        are Hermite-integrated over hp.dt_soft under H_hard; pos and vel
+        (3, n) float64 are updated in place."""
+        import torch
+        n = int(pos.shape[1])
+        ip, keep = _idx_ptr(idx)
+        c = hp._c()
+        _check(_lib.p3t_hard_step(
+            self._h, n, _dptr(pos, torch.float64, (3, n), "pos"),
+            _dptr(vel, torch.float64, (3, n), "vel"),
+            _dptr(mass, torch.float64, (n,), "mass"),
+            _dptr(offsets, torch.int64, (n + 1,), "offsets"), ip,
+            C.byref(c), _stream(stream)), "p3t_hard_step")
+        if check:
+            self.check(stream)
+        else:
+            # keep the dummy index buffer alive until the work has run
+            self._keep = keep
+        return pos, vel
+
     def check(self, stream=None):
         """Synchronise and raise the first error latched on the device."""
         _check(_lib.p3t_check(self._h, _stream(stream)), "p3t_check")
@@ -407,6 +439,59 @@ class Context:
         for k in ("pc", "ppn", "ppf"):
             out[k] = out[k][: int(offs[k + "_off"][-1])]
         return out
+
+
+@dataclass
+class HermiteParams:
+    """Hard-part integration (p3t_hermite_params): eta and alpha of
+    Eq. timestep:0-2, the soft step, dt_max = dt_soft 2^-log2_soft_over_max
+    and the finest level kmax."""
+    dt_soft: float
+    eta: float = 0.1
+    alpha: float = 0.1
+    log2_soft_over_max: int = 2
+    kmax: int = 30
+
+    def _c(self):
+        return _CHermite(self.eta, self.alpha, self.dt_soft,
+                         self.log2_soft_over_max, self.kmax)
+
+
+def _idx_ptr(idx):
+    """idx may be empty (no neighbour anywhere): pass a one-element dummy,
+    never read since every row is then empty."""
+    import torch
+    if not isinstance(idx, torch.Tensor) or not idx.is_cuda or idx.dtype != torch.int32:
+        raise TypeError("idx: expected a CUDA int32 tensor")
+    if idx.dim() != 1 or not idx.is_contiguous():
+        raise ValueError("idx: expected a contiguous 1-D tensor")
+    if idx.numel() == 0:
+        idx = torch.zeros((1,), dtype=torch.int32, device=idx.device)
+    return C.c_void_p(idx.data_ptr()), idx
+
+
+def hard_force(pos, vel, mass, offsets, idx, *, r_cut, G=1.0, eps=0.0,
+               gamma=0.1, acc=None, jerk=None, stream=None):
+    """Hard acceleration and jerk (3, n) float64 of every particle from its
+    neighbour row (p3t_hard_force)."""
+    import torch
+    n = int(pos.shape[1])
+    if acc is None:
+        acc = torch.empty((3, n), dtype=torch.float64, device="cuda")
+    if jerk is None:
+        jerk = torch.empty((3, n), dtype=torch.float64, device="cuda")
+    ip, keep = _idx_ptr(idx)
+    _check(_lib.p3t_hard_force(
+        n, _dptr(pos, torch.float64, (3, n), "pos"),
+        _dptr(vel, torch.float64, (3, n), "vel"),
+        _dptr(mass, torch.float64, (n,), "mass"),
+        _dptr(offsets, torch.int64, (n + 1,), "offsets"), ip, float(G),
+        float(eps), float(r_cut), float(gamma),
+        _dptr(acc, torch.float64, (3, n), "acc"),
+        _dptr(jerk, torch.float64, (3, n), "jerk"), _stream(stream)),
+        "p3t_hard_force")
+    del keep
+    return acc, jerk
 
 
 def kick(vel, acc, dt, stream=None):

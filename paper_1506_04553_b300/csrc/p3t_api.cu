@@ -274,7 +274,9 @@ void free_all(p3t_ctx *c)
                     c->gctr, c->lcnt, c->loff, c->list[0], c->list[1],
                     c->list[2], c->scan_part, c->red_part, c->cadj,
                     c->clus_off, c->cc, c->clus_box, c->pclus, c->gclus,
-                    c->gperm, c->gcost, c->pgroup};
+                    c->gperm, c->gcost, c->pgroup, c->hparent, c->hcsize,
+                    c->hcfill, c->hmember, c->hlev, c->hcstart, c->ht, c->ha,
+                    c->hj, c->hxp, c->hvp};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hst) cudaFreeHost(c->hst);
@@ -488,6 +490,56 @@ int p3t_long_force_vjp(p3t_ctx *c, const float *w, double *grad_pos,
     return rc;
 }
 
+int ensure_hermite(p3t_ctx *c, int64_t n)
+{
+    if (n > c->cap_herm) {
+        if (c->p.flags & P3T_FLAG_NO_SYNC) return P3T_ERR_CAPACITY;
+        const int64_t cap = n + n / 8 + 1024;
+        int64_t d = 0;
+        P3T_TRY(grow(c->hparent, d, cap, sizeof(int)));
+        P3T_TRY(grow(c->hcsize, d, cap, sizeof(int)));
+        P3T_TRY(grow(c->hcfill, d, cap, sizeof(int)));
+        P3T_TRY(grow(c->hmember, d, cap, sizeof(int)));
+        P3T_TRY(grow(c->hlev, d, cap, sizeof(int)));
+        P3T_TRY(grow(c->hcstart, d, cap + 1, sizeof(long long)));
+        P3T_TRY(grow(c->ht, d, cap, sizeof(long long)));
+        P3T_TRY(grow(c->ha, d, 3 * cap, sizeof(double)));
+        P3T_TRY(grow(c->hj, d, 3 * cap, sizeof(double)));
+        P3T_TRY(grow(c->hxp, d, 3 * cap, sizeof(double)));
+        P3T_TRY(grow(c->hvp, d, 3 * cap, sizeof(double)));
+        c->cap_herm = cap;
+    }
+    const int64_t nb = p3t_scan_blocks(n) + 2;
+    if (nb > c->cap_scan) {
+        if (c->p.flags & P3T_FLAG_NO_SYNC) return P3T_ERR_CAPACITY;
+        int64_t d = 0;
+        P3T_TRY(grow(c->scan_part, d, nb, sizeof(long long)));
+        c->cap_scan = nb;
+    }
+    return P3T_OK;
+}
+
+int p3t_hard_step(p3t_ctx *c, int64_t n, double *pos, double *vel,
+                  const double *mass, const int64_t *offsets,
+                  const int32_t *idx, const p3t_hermite_params *hp,
+                  void *stream)
+{
+    if (!c || !hp || n < 0 || n > INT32_MAX - 1) return P3T_ERR_INVALID;
+    if (c->ensemble) return P3T_ERR_INVALID;
+    if (n > 0 && (!pos || !vel || !mass || !offsets || !idx))
+        return P3T_ERR_INVALID;
+    if (!(hp->eta > 0.0) || !isfinite(hp->eta) || !(hp->alpha >= 0.0) ||
+        !isfinite(hp->alpha) || !(hp->dt_soft > 0.0) || !isfinite(hp->dt_soft) ||
+        hp->log2_soft_over_max < 0 || hp->log2_soft_over_max > 30 ||
+        hp->kmax < 1 || hp->log2_soft_over_max + hp->kmax > 58)
+        return P3T_ERR_INVALID;
+    if (n == 0) return P3T_OK;
+    P3T_TRY(ensure_hermite(c, n));
+    return p3t_run_hard_step(c, (int)n, pos, vel, mass,
+                             (const long long *)offsets, idx, hp,
+                             (cudaStream_t)stream);
+}
+
 int p3t_check(p3t_ctx *c, void *stream)
 {
     if (!c) return P3T_ERR_INVALID;
@@ -557,12 +609,17 @@ int p3t_get_stats(p3t_ctx *c, p3t_stats *o)
     if (!c || !o) return P3T_ERR_INVALID;
     if (cudaDeviceSynchronize() != cudaSuccess) return P3T_ERR_CUDA;
     long long nnz = c->hst->nnz;
-    if (c->n > 0)
-        P3T_CUDA_TRY(cudaMemcpy(c->hst, c->st, sizeof(P3TDevState),
-                                cudaMemcpyDeviceToHost));
+    P3T_CUDA_TRY(cudaMemcpy(c->hst, c->st, sizeof(P3TDevState),
+                            cudaMemcpyDeviceToHost));
     c->hst->nnz = nnz;
     memset(o, 0, sizeof(*o));
     o->n = c->n;
+    o->herm_block_steps = c->hst->herm[0];
+    o->herm_particle_steps = c->hst->herm[1];
+    o->herm_pairs = c->hst->herm[2];
+    o->herm_capped = c->hst->herm[3];
+    o->herm_components = c->hst->herm[4];
+    o->herm_max_component = c->hst->herm[5];
     if (c->n == 0) return P3T_OK;
     o->n_cells = c->hst->ncell;
     o->n_groups = c->hst->ngroup;

@@ -1,0 +1,528 @@
+// Hard part of the P3T step (Sect. 2.1 and 2.2): the hard force F_hard over
+// the neighbour lists with its jerk, and the fourth-order Hermite integrator
+// with block timesteps (Makino & Aarseth 1992) for the particles that have
+// neighbours; isolated particles drift.
+//
+// The hard force of particle i sums over its neighbour row (CSR, ascending
+// j): with q = x_i - x_j, u = v_i - v_j, s^2 = |q|^2 + eps^2 (Eq. 2) and the
+// pair weight 1 - K(s) (Eq. 7, K of Eq. 12-15),
+//   a_i  = -sum G m_j (1-K) q / s^3
+//   da_i = -sum G m_j [ (1-K) (u - 3 (q.u) q / s^2) / s^3
+//                       - (dK/ds) ((q.u) / s) q / s^3 ].
+// All of it is FP64 with one rounding per operation (explicit __d*_rn
+// intrinsics, no contraction), in a fixed order, so the results do not
+// depend on the compiler's choices.
+//
+// Integration.  Neighbour rows are symmetric (the neighbour predicate is),
+// and a particle never comes within r_cut of one outside its row during
+// dt_soft (h is chosen so), so the connected components of the neighbour
+// graph evolve independently for dt_soft.  Each component is integrated by
+// one warp with no synchronisation beyond the warp: components are labelled
+// by a lock-free union-find (label = smallest index of the component),
+// counted, scanned and filled into a member list.  The block-step schedule
+// restricted to one component is exactly the global one.
+//
+// Time is counted in integer ticks of dt_max 2^-kmax, dt_max = dt_soft 2^-p.
+// A particle at level k steps dt_max 2^-k and its time is a multiple of its
+// step.  First step: Eq. timestep:2 with eta_s = eta / 10; later steps:
+// Eq. timestep:0 with a_0 = alpha G m_i / r_cut^2 and a^(2), a^(3) from the
+// Hermite interpolation of the step just taken; the step may at most double
+// and is halved until the current time is a multiple of it.  Each block step
+// predicts every member to the next time t_n (the least t_i + dt_i),
+// evaluates a and da at t_n for the members due then from the predicted
+// values, and corrects them:
+//   a2 = (-6 (a0 - a1) - h (4 j0 + 2 j1)) / h^2
+//   a3 = (12 (a0 - a1) + 6 h (j0 + j1)) / h^3
+//   x = xp + a2 h^4 / 24 + a3 h^5 / 120,  v = vp + a2 h^3 / 6 + a3 h^4 / 24.
+#include <math.h>
+
+#include "p3t_internal.cuh"
+
+namespace {
+
+constexpr int HB = 256;
+constexpr long long MAX_BLOCK_STEPS = 1LL << 26;  // per component
+constexpr int MAX_UF_ROUNDS = 1 << 20;
+
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
+
+__device__ __forceinline__ double dot3(double ax, double ay, double az,
+                                       double bx, double by, double bz)
+{
+    return dadd(dadd(dmul(ax, bx), dmul(ay, by)), dmul(az, bz));
+}
+
+// Eq. 12
+__device__ __forceinline__ double K_of_x(double x)
+{
+    if (x < 0.0) return 0.0;
+    if (x >= 1.0) return 1.0;
+    const double x2 = dmul(x, x), x3 = dmul(x2, x), x4 = dmul(x2, x2);
+    const double x5 = dmul(x4, x), x6 = dmul(x3, x3), x7 = dmul(x6, x);
+    return dadd(dsub(dadd(dmul(-20.0, x7), dmul(70.0, x6)), dmul(84.0, x5)),
+                dmul(35.0, x4));
+}
+
+// dK/dx of Eq. 12
+__device__ __forceinline__ double dK_of_x(double x)
+{
+    if (x <= 0.0 || x >= 1.0) return 0.0;
+    const double x2 = dmul(x, x), x3 = dmul(x2, x), x4 = dmul(x2, x2);
+    const double x5 = dmul(x4, x), x6 = dmul(x3, x3);
+    return dadd(dsub(dadd(dmul(-140.0, x6), dmul(420.0, x5)), dmul(420.0, x4)),
+                dmul(140.0, x3));
+}
+
+struct HardPar {
+    double G, eps2, r_cut, gamma;
+};
+
+// Hard acceleration and jerk of particle i (SoA arrays of length 3n).
+// x and v may be the predicted arrays that other lanes of the warp wrote in
+// this launch: plain (coherent) loads, no read-only cache.
+__device__ void hard_one(int i, int n, const double *x, const double *v,
+                         const double *__restrict__ m,
+                         const long long *__restrict__ off,
+                         const int *__restrict__ idx, const HardPar &P,
+                         double *a, double *jk, long long *pairs)
+{
+    double acc[3] = {0.0, 0.0, 0.0}, jrk[3] = {0.0, 0.0, 0.0};
+    const double omg = dsub(1.0, P.gamma);
+    const double xi[3] = {x[i], x[(size_t)n + i], x[2 * (size_t)n + i]};
+    const double vi[3] = {v[i], v[(size_t)n + i], v[2 * (size_t)n + i]};
+    const long long e0 = off[i], e1 = off[i + 1];
+    for (long long e = e0; e < e1; ++e) {
+        const int j = idx[e];
+        double q[3], u[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            q[c] = dsub(xi[c], x[(size_t)c * n + j]);
+            u[c] = dsub(vi[c], v[(size_t)c * n + j]);
+        }
+        const double s2 = dadd(dot3(q[0], q[1], q[2], q[0], q[1], q[2]), P.eps2);
+        const double s = dsqrt(s2);
+        const double xk = ddiv(dsub(ddiv(s, P.r_cut), P.gamma), omg);
+        const double w = dsub(1.0, K_of_x(xk));
+        const double dKds = ddiv(dK_of_x(xk), dmul(omg, P.r_cut));
+        const double s3 = dmul(s2, s);
+        const double rv = dot3(q[0], q[1], q[2], u[0], u[1], u[2]);
+        const double gm = dmul(P.G, m[j]);
+        const double fa = ddiv(dmul(gm, w), s3);
+        const double c1 = ddiv(dmul(3.0, rv), s2);
+        const double fb = ddiv(dmul(gm, ddiv(dmul(dKds, rv), s)), s3);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            acc[c] = dsub(acc[c], dmul(fa, q[c]));
+            jrk[c] = dsub(jrk[c], dsub(dmul(fa, dsub(u[c], dmul(c1, q[c]))),
+                                       dmul(fb, q[c])));
+        }
+    }
+    *pairs += e1 - e0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        a[c] = acc[c];
+        jk[c] = jrk[c];
+    }
+}
+
+__global__ void __launch_bounds__(HB)
+k_hard_force(int n, const double *__restrict__ x, const double *__restrict__ v,
+             const double *__restrict__ m, const long long *__restrict__ off,
+             const int *__restrict__ idx, HardPar P, double *__restrict__ a,
+             double *__restrict__ jk)
+{
+    for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB) {
+        double ai[3], ji[3];
+        long long pairs = 0;
+        hard_one(i, n, x, v, m, off, idx, P, ai, ji, &pairs);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a[(size_t)c * n + i] = ai[c];
+            jk[(size_t)c * n + i] = ji[c];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- components
+
+__device__ __forceinline__ int uf_find(int *parent, int x, int *rounds)
+{
+    // path halving; the writes only shorten paths and are benign under races
+    for (;;) {
+        const int p = atomicAdd(parent + x, 0);
+        if (p == x) return x;
+        const int gp = atomicAdd(parent + p, 0);
+        if (gp != p) atomicCAS(parent + x, p, gp);
+        x = gp;
+        if (++*rounds > MAX_UF_ROUNDS) return -1;
+    }
+}
+
+__global__ void __launch_bounds__(HB) k_uf_init(int n, int *parent)
+{
+    for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB)
+        parent[i] = i;
+}
+
+// One thread per row: every edge (i, j > i) joins the two roots, the larger
+// hooked under the smaller, so each component's root ends as its smallest
+// index whatever the order of the hooks.
+__global__ void __launch_bounds__(HB)
+k_uf_union(int n, const long long *__restrict__ off, const int *__restrict__ idx,
+           int *parent, P3TDevState *st)
+{
+    for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB) {
+        for (long long e = off[i]; e < off[i + 1]; ++e) {
+            const int j = idx[e];
+            if (j <= i) continue;
+            int rounds = 0;
+            for (;;) {
+                int ri = uf_find(parent, i, &rounds);
+                int rj = uf_find(parent, j, &rounds);
+                if (ri < 0 || rj < 0) {
+                    p3t_raise(st, P3T_ERR_TIMEOUT);
+                    return;
+                }
+                if (ri == rj) break;
+                if (ri > rj) {
+                    const int t = ri;
+                    ri = rj;
+                    rj = t;
+                }
+                if (atomicCAS(parent + rj, rj, ri) == rj) break;
+                if (++rounds > MAX_UF_ROUNDS) {
+                    p3t_raise(st, P3T_ERR_TIMEOUT);
+                    return;
+                }
+            }
+        }
+    }
+}
+
+// label = root; component sizes counted at the root (non-isolated only).
+__global__ void __launch_bounds__(HB)
+k_uf_label(int n, const long long *__restrict__ off, int *parent,
+           int *__restrict__ csize, P3TDevState *st)
+{
+    for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB) {
+        int rounds = 0;
+        const int r = uf_find(parent, i, &rounds);
+        if (r < 0) {
+            p3t_raise(st, P3T_ERR_TIMEOUT);
+            continue;
+        }
+        if (off[i + 1] > off[i]) atomicAdd(csize + r, 1);
+    }
+}
+
+__global__ void __launch_bounds__(HB)
+k_comp_fill(int n, const long long *__restrict__ off, int *parent,
+            const long long *__restrict__ cstart, int *__restrict__ cfill,
+            int *__restrict__ member, P3TDevState *st)
+{
+    for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB) {
+        if (off[i + 1] == off[i]) continue;
+        int rounds = 0;
+        const int r = uf_find(parent, i, &rounds);
+        if (r < 0) {
+            p3t_raise(st, P3T_ERR_TIMEOUT);
+            continue;
+        }
+        member[cstart[r] + atomicAdd(cfill + r, 1)] = i;
+    }
+}
+
+// ------------------------------------------------------------------ Hermite
+
+struct HermPar {
+    HardPar f;
+    double eta, eta_s, alpha, dt_soft, dt_max, tick;
+    long long T;  // dt_soft in ticks
+    int kmax;
+};
+
+// smallest k in [kmin, kmax] with dt_max 2^-k <= crit (kmax when none is)
+__device__ __forceinline__ int level_for(double crit, double dt_max, int kmin,
+                                         int kmax)
+{
+    int k = kmin;
+    double dt = ldexp(dt_max, -k);
+    while (k < kmax && dt > crit) {
+        ++k;
+        dt = dmul(dt, 0.5);
+    }
+    return k;
+}
+
+// Forces at t = 0 and first-step levels (Eq. timestep:2) of every particle
+// with neighbours.
+__global__ void __launch_bounds__(HB)
+k_herm_init(int n, const double *__restrict__ x, const double *__restrict__ v,
+            const double *__restrict__ m, const long long *__restrict__ off,
+            const int *__restrict__ idx, HermPar H, double *__restrict__ a,
+            double *__restrict__ jk, long long *__restrict__ t,
+            int *__restrict__ lev, P3TDevState *st)
+{
+    long long pairs = 0, capped = 0;
+    for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB) {
+        t[i] = 0;
+        lev[i] = 0;
+        if (off[i + 1] == off[i]) continue;
+        double ai[3], ji[3];
+        hard_one(i, n, x, v, m, off, idx, H.f, ai, ji, &pairs);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a[(size_t)c * n + i] = ai[c];
+            jk[(size_t)c * n + i] = ji[c];
+        }
+        const double a0 = ddiv(dmul(dmul(H.alpha, H.f.G), m[i]),
+                               dmul(H.f.r_cut, H.f.r_cut));
+        const double jj = dot3(ji[0], ji[1], ji[2], ji[0], ji[1], ji[2]);
+        double crit = INFINITY;
+        if (jj > 0.0)
+            crit = dmul(H.eta_s,
+                        dsqrt(ddiv(dadd(dot3(ai[0], ai[1], ai[2], ai[0], ai[1], ai[2]),
+                                        dmul(a0, a0)),
+                                   jj)));
+        const int k = level_for(crit, H.dt_max, 0, H.kmax);
+        if (k == H.kmax && ldexp(H.dt_max, -H.kmax) > crit) ++capped;
+        lev[i] = k;
+    }
+    if (pairs) atomicAdd((unsigned long long *)&st->herm[2], (unsigned long long)pairs);
+    if (capped) atomicAdd((unsigned long long *)&st->herm[3], (unsigned long long)capped);
+}
+
+__device__ __forceinline__ long long warp_min_ll(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+// One warp per component (the warp that meets the component's root in a
+// warp-strided sweep over the particles).  The state arrays are shared by the
+// lanes of a warp (each lane writes its members, all read the neighbours'
+// predictions), so they are plain pointers; __syncwarp orders the phases.
+__global__ void __launch_bounds__(HB)
+k_herm_components(int n, double *x, double *v, const double *__restrict__ m,
+                  const long long *__restrict__ off, const int *__restrict__ idx,
+                  const int *__restrict__ parent, const int *__restrict__ csize,
+                  const long long *__restrict__ cstart,
+                  const int *__restrict__ member, HermPar H, double *a,
+                  double *jk, double *xp, double *vp, long long *t, int *lev,
+                  P3TDevState *st)
+{
+    if (st->error) return;
+    const int lane = threadIdx.x & 31;
+    const int wg = (blockIdx.x * HB + threadIdx.x) >> 5;
+    const int nw = gridDim.x * (HB / 32);
+    long long nblk = 0, nstep = 0, pairs = 0, capped = 0, ncomp = 0;
+    int maxsize = 0;
+    for (int r = wg; r < n; r += nw) {
+        if (parent[r] != r || csize[r] == 0) continue;  // not a root
+        const int size = csize[r];
+        const long long base = cstart[r];
+        ++ncomp;
+        maxsize = size > maxsize ? size : maxsize;
+        for (long long it = 0;; ++it) {
+            if (it >= MAX_BLOCK_STEPS) {
+                if (lane == 0) p3t_raise(st, P3T_ERR_TIMEOUT);
+                break;
+            }
+            // next block time
+            long long tmin = H.T;
+            bool live = false;
+            for (int q = lane; q < size; q += 32) {
+                const int i = member[base + q];
+                if (t[i] == H.T) continue;
+                const long long e = t[i] + (1LL << (H.kmax - lev[i]));
+                tmin = e < tmin ? e : tmin;
+                live = true;
+            }
+            if (!__any_sync(0xffffffffu, live)) break;
+            const long long tn = warp_min_ll(tmin);
+            ++nblk;
+            // predict every member to tn
+            for (int q = lane; q < size; q += 32) {
+                const int i = member[base + q];
+                const double d = dmul((double)(tn - t[i]), H.tick);
+                const double d2 = dmul(dmul(d, d), 0.5);
+                const double d3 = ddiv(dmul(dmul(d, d), d), 6.0);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const size_t k = (size_t)c * n + i;
+                    xp[k] = dadd(dadd(dadd(x[k], dmul(v[k], d)), dmul(a[k], d2)),
+                                 dmul(jk[k], d3));
+                    vp[k] = dadd(dadd(v[k], dmul(a[k], d)), dmul(jk[k], d2));
+                }
+            }
+            __syncwarp();
+            // evaluate and correct the members due at tn
+            for (int q = lane; q < size; q += 32) {
+                const int i = member[base + q];
+                const long long step = 1LL << (H.kmax - lev[i]);
+                if (t[i] + step != tn) continue;
+                double a1[3], j1[3];
+                hard_one(i, n, xp, vp, m, off, idx, H.f, a1, j1, &pairs);
+                ++nstep;
+                const double h = dmul((double)step, H.tick);
+                const double h2 = dmul(h, h), h3 = dmul(h2, h), h4 = dmul(h3, h),
+                             h5 = dmul(h4, h);
+                double a2[3], a3[3], a2e[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const size_t k = (size_t)c * n + i;
+                    const double j0 = jk[k];
+                    const double da = dsub(a[k], a1[c]);
+                    a2[c] = ddiv(dsub(dmul(-6.0, da),
+                                      dmul(h, dadd(dmul(4.0, j0), dmul(2.0, j1[c])))),
+                                 h2);
+                    a3[c] = ddiv(dadd(dmul(12.0, da), dmul(dmul(6.0, h), dadd(j0, j1[c]))),
+                                 h3);
+                    x[k] = dadd(dadd(xp[k], dmul(a2[c], ddiv(h4, 24.0))),
+                                dmul(a3[c], ddiv(h5, 120.0)));
+                    v[k] = dadd(dadd(vp[k], dmul(a2[c], ddiv(h3, 6.0))),
+                                dmul(a3[c], ddiv(h4, 24.0)));
+                    a[k] = a1[c];
+                    jk[k] = j1[c];
+                    a2e[c] = dadd(a2[c], dmul(a3[c], h));
+                }
+                t[i] = tn;
+                if (tn == H.T) continue;
+                // Eq. timestep:0
+                const double a0 = ddiv(dmul(dmul(H.alpha, H.f.G), m[i]),
+                                       dmul(H.f.r_cut, H.f.r_cut));
+                const double aa = dot3(a1[0], a1[1], a1[2], a1[0], a1[1], a1[2]);
+                const double a2sq = dot3(a2e[0], a2e[1], a2e[2], a2e[0], a2e[1], a2e[2]);
+                const double num = dadd(dmul(dsqrt(dadd(aa, dmul(a0, a0))), dsqrt(a2sq)),
+                                        dot3(j1[0], j1[1], j1[2], j1[0], j1[1], j1[2]));
+                const double den = dadd(dmul(dsqrt(aa),
+                                             dsqrt(dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]))),
+                                        a2sq);
+                const double crit = den > 0.0 ? dmul(H.eta, dsqrt(ddiv(num, den))) : INFINITY;
+                const int kmin = lev[i] > 0 ? lev[i] - 1 : 0;
+                int k = level_for(crit, H.dt_max, kmin, H.kmax);
+                if (k == H.kmax && ldexp(H.dt_max, -H.kmax) > crit) ++capped;
+                while (tn % (1LL << (H.kmax - k)) != 0) ++k;
+                lev[i] = k;
+            }
+            __syncwarp();
+        }
+    }
+    // totals: sums over lanes, then one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nstep += __shfl_xor_sync(0xffffffffu, nstep, o);
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        capped += __shfl_xor_sync(0xffffffffu, capped, o);
+    }
+    if (lane == 0) {
+        if (nblk) atomicAdd((unsigned long long *)&st->herm[0], (unsigned long long)nblk);
+        if (nstep) atomicAdd((unsigned long long *)&st->herm[1], (unsigned long long)nstep);
+        if (pairs) atomicAdd((unsigned long long *)&st->herm[2], (unsigned long long)pairs);
+        if (capped) atomicAdd((unsigned long long *)&st->herm[3], (unsigned long long)capped);
+        if (ncomp) atomicAdd((unsigned long long *)&st->herm[4], (unsigned long long)ncomp);
+        if (maxsize) atomicMax((unsigned long long *)&st->herm[5], (unsigned long long)maxsize);
+    }
+}
+
+// Isolated particles drift: x <- x + dt_soft v (Sect. 2.2, step 5).
+__global__ void __launch_bounds__(HB)
+k_drift_isolated(int n, double *__restrict__ x, const double *__restrict__ v,
+                 const long long *__restrict__ off, double dt)
+{
+    for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB) {
+        if (off[i + 1] != off[i]) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const size_t k = (size_t)c * n + i;
+            x[k] = dadd(x[k], dmul(dt, v[k]));
+        }
+    }
+}
+
+__global__ void k_herm_reset(P3TDevState *st)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        for (int k = 0; k < 6; ++k) st->herm[k] = 0;
+}
+
+int grid_for(long long n, int sms)
+{
+    long long b = (n + HB - 1) / HB;
+    if (b > (long long)sms * 8) b = (long long)sms * 8;
+    return b < 1 ? 1 : (int)b;
+}
+
+}  // namespace
+
+extern "C" int p3t_hard_force(int64_t n, const double *pos, const double *vel,
+                              const double *mass, const int64_t *offsets,
+                              const int32_t *idx, double G, double eps,
+                              double r_cut, double gamma, double *acc,
+                              double *jerk, void *stream)
+{
+    if (n < 0 || n > INT32_MAX - 1) return P3T_ERR_INVALID;
+    if (n > 0 && (!pos || !vel || !mass || !offsets || !acc || !jerk))
+        return P3T_ERR_INVALID;
+    if (!(r_cut >= P3T_R_OUT_MIN) || !(gamma >= 0.0 && gamma < 1.0) ||
+        !(eps >= 0.0) || !(G > 0.0))
+        return P3T_ERR_INVALID;
+    if (n == 0) return P3T_OK;
+    int dev = 0, sms = 0;
+    P3T_CUDA_TRY(cudaGetDevice(&dev));
+    P3T_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    HardPar P = {G, eps * eps, r_cut, gamma};
+    k_hard_force<<<grid_for(n, sms), HB, 0, (cudaStream_t)stream>>>(
+        (int)n, pos, vel, mass, (const long long *)offsets, idx, P, acc, jerk);
+    p3t_count_launches(1);
+    P3T_CUDA_TRY(cudaGetLastError());
+    return P3T_OK;
+}
+
+int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
+                      const double *mass, const long long *off, const int *idx,
+                      const p3t_hermite_params *hp, cudaStream_t s)
+{
+    HermPar H;
+    H.f.G = c->p.G;
+    H.f.eps2 = c->p.eps * c->p.eps;
+    H.f.r_cut = c->p.r_out;
+    H.f.gamma = c->p.gamma;
+    H.eta = hp->eta;
+    H.eta_s = hp->eta / 10.0;
+    H.alpha = hp->alpha;
+    H.dt_soft = hp->dt_soft;
+    H.dt_max = ldexp(hp->dt_soft, -hp->log2_soft_over_max);
+    H.tick = ldexp(H.dt_max, -hp->kmax);
+    H.T = 1LL << (hp->log2_soft_over_max + hp->kmax);
+    H.kmax = hp->kmax;
+    const int g = grid_for(n, c->sms);
+    k_herm_reset<<<1, 32, 0, s>>>(c->st);
+    k_uf_init<<<g, HB, 0, s>>>(n, c->hparent);
+    k_uf_union<<<g, HB, 0, s>>>(n, off, idx, c->hparent, c->st);
+    P3T_CUDA_TRY(cudaMemsetAsync(c->hcsize, 0, sizeof(int) * (size_t)n, s));
+    P3T_CUDA_TRY(cudaMemsetAsync(c->hcfill, 0, sizeof(int) * (size_t)n, s));
+    k_uf_label<<<g, HB, 0, s>>>(n, off, c->hparent, c->hcsize, c->st);
+    int rc = p3t_scan_ll(c, c->hcsize, c->hcstart, n, s);
+    if (rc != P3T_OK) return rc;
+    k_comp_fill<<<g, HB, 0, s>>>(n, off, c->hparent, c->hcstart, c->hcfill,
+                                 c->hmember, c->st);
+    k_herm_init<<<g, HB, 0, s>>>(n, pos, vel, mass, off, idx, H, c->ha, c->hj,
+                                 c->ht, c->hlev, c->st);
+    // one warp per component root, every SM busy
+    k_herm_components<<<c->sms * 4, HB, 0, s>>>(
+        n, pos, vel, mass, off, idx, c->hparent, c->hcsize, c->hcstart,
+        c->hmember, H, c->ha, c->hj, c->hxp, c->hvp, c->ht, c->hlev, c->st);
+    k_drift_isolated<<<g, HB, 0, s>>>(n, pos, vel, off, hp->dt_soft);
+    p3t_count_launches(8);
+    P3T_CUDA_TRY(cudaGetLastError());
+    return P3T_OK;
+}

@@ -51,6 +51,9 @@ struct P3TDevState {
     int cost_n;         // n of the force evaluation that wrote gcost/pgroup
     int cost_groups;    // number of groups of that evaluation
     int pad1;
+    long long herm[6];  // hard step: block steps (summed over components),
+                        // particle steps, pair evaluations, steps capped at
+                        // the finest level, components, largest component
 };
 
 // Phase timing with CUDA events (resolved lazily at p3t_get_profile).
@@ -119,6 +122,11 @@ struct p3t_ctx {
     int64_t cap_cadj;
     // energy scratch
     double *red_part;
+    // hard step (Hermite) scratch, per particle
+    int *hparent, *hcsize, *hcfill, *hmember, *hlev;
+    long long *hcstart, *ht;
+    double *ha, *hj, *hxp, *hvp;
+    int64_t cap_herm;
     // clusters (one for a plain build)
     int nclus, cap_clus;
     int ensemble;            // layout fixed by p3t_set_ensemble
@@ -229,6 +237,9 @@ int p3t_run_ngb(p3t_ctx *c, int fill, const long long *row_off, int *idx,
                 long long cap, cudaStream_t s);                  // p3t_ngb.cu
 int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,
                 double *cadj, cudaStream_t s);                   // p3t_vjp.cu
+int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
+                      const double *mass, const long long *off, const int *idx,
+                      const p3t_hermite_params *hp, cudaStream_t s); // p3t_hard.cu
 int p3t_energy_launch(p3t_ctx *c, int n, const double *mass,
                       const double *vel, const double *pot, double *out,
                       cudaStream_t s);                           // p3t_misc.cu
