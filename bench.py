@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-p3t", action="store_true")
     return ap.parse_args()
 
 
@@ -545,6 +546,8 @@ def run_ours(args, world, rank, local):
                        "ms_per_step": te * 1e3}
     if not args.no_ensemble:
         line["ensemble"] = run_ensemble(args, dev)
+    if not args.no_p3t:
+        line["p3t_step"] = run_p3t_step(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_step, desc = oracle_sample(pos_h, mass_h, frac=1 / 16)
         line["cpu_baseline"] = {"value": n / t_step, "unit": "particles/s",
@@ -554,6 +557,105 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_p3t_step(args, dev):
+    """Whole P3T steps (Sect. 2.2) at the paper's standard parameters
+    (Table 1) for N = 2^20: half-kick by F_soft, the hard step (isolated
+    drift + Hermite block steps of the non-isolated particles on the
+    neighbour lists), new tree, F_soft and neighbour lists within
+    h = r_cut + 3 sigma dt_soft, half-kick.  One step captured in a CUDA
+    graph and replayed; the hard step is also timed alone (same graph
+    replays, events around it in an uncaptured step)."""
+    import torch
+    import paper_1506_04553_b300 as P
+    from paper_1506_04553_b300 import ics
+    n = 1 << 20
+    dt = (1 / 256) * (n / 16384) ** (-1 / 3)
+    r_cut = 4 * dt
+    h = r_cut + 3 * dt / np.sqrt(2)
+    eps = 4.0 / n
+    pos_h, vel_h, mass_h = ics.plummer(n, SEED)
+    params = P.Params(theta=THETA, r_out=r_cut, gamma=GAMMA, eps=eps, h=h,
+                      G=1.0, n_leaf=N_LEAF, n_group=N_GROUP)
+    ctx = P.Context(params)
+    pos = torch.tensor(pos_h, device=dev)
+    vel = torch.tensor(vel_h, device=dev)
+    mass = torch.tensor(mass_h, device=dev)
+    acc = torch.empty((3, n), dtype=torch.float32, device=dev)
+    off = torch.empty((n + 1,), dtype=torch.int64, device=dev)
+    hp = P.HermiteParams(dt_soft=dt)
+    ctx.build_tree(pos, mass)
+    ctx.long_force(acc)
+    _, idx0 = ctx.neighbours()
+    idx = torch.empty((max(4 * int(idx0.numel()) + 1024, n),), dtype=torch.int32,
+                      device=dev)
+    ctx.neighbours_into(off, idx)
+    ctx.hard_step(pos.clone(), vel.clone(), mass, off, idx, hp)  # scratch
+
+    def step(time_hard=None):
+        P.kick(vel, acc, 0.5 * dt)
+        if time_hard:
+            time_hard[0].record(torch.cuda.current_stream(dev))
+        ctx.hard_step(pos, vel, mass, off, idx, hp, check=False)
+        if time_hard:
+            time_hard[1].record(torch.cuda.current_stream(dev))
+        ctx.build_tree(pos, mass)
+        ctx.long_force(acc, check=False)
+        ctx.neighbours_into(off, idx, sync=False)
+        P.kick(vel, acc, 0.5 * dt)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ctx.check()
+    # the hard step alone, in uncaptured steps
+    hard = []
+    for _ in range(3):
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        step(ev)
+        torch.cuda.synchronize()
+        hard.append(ev[0].elapsed_time(ev[1]))
+    st = ctx.stats()
+    nonis = int((off[1:] > off[:-1]).sum().item())
+    ctx.set_params(P.Params(theta=THETA, r_out=r_cut, gamma=GAMMA, eps=eps, h=h,
+                            G=1.0, n_leaf=N_LEAF, n_group=N_GROUP,
+                            flags=P.FLAG_NO_SYNC))
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        step()
+    torch.cuda.current_stream(dev).wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    k = max(args.steps // 4, 8)
+    e0.record(stream)
+    for _ in range(k):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = e0.elapsed_time(e1) / k
+    return {"workload": "Plummer N=2^20, P3T standard parameters (Table 1): "
+                        f"dt_soft {dt:.6g}, r_cut 4 dt_soft, h = r_cut + "
+                        "3 sigma dt_soft (sigma 1/sqrt 2), dt_max dt_soft/4, "
+                        "eps 4/N, eta 0.1, alpha 0.1, theta 0.4",
+            "step": "half-kick, hard step (isolated drift + Hermite), build, "
+                    "F_soft, neighbour lists, half-kick; one CUDA graph",
+            "n": n, "value": n / (ms * 1e-3), "unit": "particles/s",
+            "ms_per_step": ms, "hard_ms": float(np.median(hard)),
+            "non_isolated": nonis, "components": st["herm_components"],
+            "largest_component": st["herm_max_component"],
+            "hard_particle_steps": st["herm_particle_steps"],
+            "hard_pairs": st["herm_pairs"], "steps_at_kmax": st["herm_capped"],
+            "max_block_steps": st["herm_max_block_steps"]}
 
 
 def run_ensemble(args, dev):

@@ -320,6 +320,7 @@ typedef struct p3t_stats {
     int64_t herm_capped;         /* steps whose level hit kmax */
     int64_t herm_components;     /* connected components integrated */
     int64_t herm_max_component;  /* particles in the largest one */
+    int64_t herm_max_block_steps; /* most block steps of one component */
 } p3t_stats;
 int p3t_get_stats(p3t_ctx *ctx, p3t_stats *s);
 

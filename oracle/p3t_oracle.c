@@ -1235,16 +1235,45 @@ static double orc_dot3(const double *a, const double *b)
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
+/* Constants of the hard part, each computed once in this order. */
+typedef struct {
+    double G, eps2, r_cut, gamma;
+    double irc;    /* 1 / r_cut */
+    double iomg;   /* 1 / (1 - gamma) */
+    double iomgrc; /* 1 / ((1 - gamma) r_cut) */
+    double a0c;    /* alpha G / r_cut^2: a_0 = a0c m_i (Eq. timestep:1) */
+    double c6, c24, c120;  /* 1/6, 1/24, 1/120 */
+} orc_hard_par;
+
+static orc_hard_par orc_hard_par_make(double G, double eps, double r_cut,
+                                      double gamma, double alpha)
+{
+    orc_hard_par P;
+    P.G = G;
+    P.eps2 = eps * eps;
+    P.r_cut = r_cut;
+    P.gamma = gamma;
+    P.irc = 1.0 / r_cut;
+    P.iomg = 1.0 / (1.0 - gamma);
+    P.iomgrc = 1.0 / ((1.0 - gamma) * r_cut);
+    P.a0c = alpha * G / (r_cut * r_cut);
+    P.c6 = 1.0 / 6.0;
+    P.c24 = 1.0 / 24.0;
+    P.c120 = 1.0 / 120.0;
+    return P;
+}
+
 /* Hard acceleration and jerk of particle i from its neighbour row: the pair
  * force of Eq. 7 (weight 1 - K(s), s of Eq. 2, q = x_i - x_j) and its time
  * derivative along u = v_i - v_j, with ds/dt = (q.u)/s:
  *   a_i  = -sum G m_j (1-K) q / s^3
  *   da_i = -sum G m_j [ (1-K) (u - 3 (q.u) q / s^2) / s^3
- *                       - (dK/ds) ((q.u) / s) q / s^3 ]. */
+ *                       - (dK/ds) ((q.u) / s) q / s^3 ].
+ * One square root and one division per pair: 1/s, then its powers. */
 static void orc_hard_one(int64_t i, const double *x, const double *v,
                          const double *m, const int64_t *off,
-                         const int32_t *idx, double G, double eps2,
-                         double r_cut, double gamma, double *a, double *jk)
+                         const int32_t *idx, const orc_hard_par *P,
+                         double *a, double *jk)
 {
     double acc[3] = {0.0, 0.0, 0.0}, jrk[3] = {0.0, 0.0, 0.0};
     for (int64_t e = off[i]; e < off[i + 1]; ++e) {
@@ -1254,17 +1283,19 @@ static void orc_hard_one(int64_t i, const double *x, const double *v,
             q[c] = x[3 * i + c] - x[3 * j + c];
             u[c] = v[3 * i + c] - v[3 * j + c];
         }
-        double s2 = orc_dot3(q, q) + eps2;
+        double s2 = orc_dot3(q, q) + P->eps2;
         double s = sqrt(s2);
-        double xk = (s / r_cut - gamma) / (1.0 - gamma);
+        double ri = 1.0 / s;
+        double ri2 = ri * ri;
+        double ri3 = ri2 * ri;
+        double xk = (s * P->irc - P->gamma) * P->iomg;
         double w = 1.0 - orc_K(xk);
-        double dKds = orc_dKdx(xk) / ((1.0 - gamma) * r_cut);
-        double s3 = s2 * s;
+        double dKds = orc_dKdx(xk) * P->iomgrc;
         double rv = orc_dot3(q, u);
-        double gm = G * m[j];
-        double fa = gm * w / s3;
-        double c1 = 3.0 * rv / s2;
-        double fb = gm * (dKds * rv / s) / s3;
+        double gm = P->G * m[j];
+        double fa = gm * w * ri3;
+        double c1 = 3.0 * rv * ri2;
+        double fb = gm * (dKds * rv * ri) * ri3;
         for (int c = 0; c < 3; ++c) {
             acc[c] = acc[c] - fa * q[c];
             jrk[c] = jrk[c] - (fa * (u[c] - c1 * q[c]) - fb * q[c]);
@@ -1282,9 +1313,9 @@ void orc_hard_force(int64_t n, const double *x, const double *v,
                     double G, double eps, double r_cut, double gamma,
                     double *a, double *jk)
 {
+    orc_hard_par P = orc_hard_par_make(G, eps, r_cut, gamma, 0.0);
     for (int64_t i = 0; i < n; ++i)
-        orc_hard_one(i, x, v, m, off, idx, G, eps * eps, r_cut, gamma,
-                     a + 3 * i, jk + 3 * i);
+        orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
 }
 
 /* Block level for a step of at most dt_crit: the smallest k in [kmin, kmax]
@@ -1306,6 +1337,8 @@ static int orc_level(double dt_crit, double dt_max, int kmin, int kmax)
  * Sect. 2.1 / the sixth of Sect. 2.2); particles with an empty row are
  * isolated and drift, x <- x + dt_soft v (the fifth step of Sect. 2.2).
  *
+ * Divisions are few: 1/s per pair, 1/h per correction, and constants
+ * (1/r_cut, 1/(1 - gamma), alpha G / r_cut^2, 1/6, 1/24, 1/120) formed once.
  * Time is counted in ticks of dt_max 2^-kmax, dt_max = dt_soft 2^-p.  A
  * particle at level k steps dt_max 2^-k; its time is always a multiple of
  * its step.  First step: Eq. timestep:2 with eta_s = eta / 10; later steps:
@@ -1329,7 +1362,7 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
                 double dt_soft, int p, int kmax, int64_t *stats)
 {
     if (n < 0 || p < 0 || kmax < 0 || p + kmax > 60) return -1;
-    const double eps2 = eps * eps;
+    const orc_hard_par P = orc_hard_par_make(G, eps, r_cut, gamma, alpha);
     const double dt_max = ldexp(dt_soft, -p);
     const double tick = ldexp(dt_max, -kmax);
     const int64_t T = (int64_t)1 << (p + kmax);
@@ -1350,10 +1383,9 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
         t[i] = 0;
         lev[i] = 0;
         if (off[i + 1] == off[i]) continue;
-        orc_hard_one(i, x, v, m, off, idx, G, eps2, r_cut, gamma, a + 3 * i,
-                     jk + 3 * i);
+        orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
         st[2] += off[i + 1] - off[i];
-        double a0 = alpha * G * m[i] / (r_cut * r_cut);
+        double a0 = P.a0c * m[i];
         double jj = orc_dot3(jk + 3 * i, jk + 3 * i);
         double crit = INFINITY;
         if (jj > 0.0)
@@ -1377,7 +1409,7 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
             if (off[i + 1] == off[i]) continue;
             double d = (double)(tn - t[i]) * tick;
             double d2 = d * d * 0.5;
-            double d3 = d * d * d / 6.0;
+            double d3 = d * d * d * P.c6;
             for (int c = 0; c < 3; ++c) {
                 int64_t k = 3 * i + c;
                 xp[k] = x[k] + v[k] * d + a[k] * d2 + jk[k] * d3;
@@ -1390,31 +1422,33 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
             int64_t step = (int64_t)1 << (kmax - lev[i]);
             if (t[i] + step != tn) continue;
             double a1[3], j1[3];
-            orc_hard_one(i, xp, vp, m, off, idx, G, eps2, r_cut, gamma, a1, j1);
+            orc_hard_one(i, xp, vp, m, off, idx, &P, a1, j1);
             ++st[1];
             st[2] += off[i + 1] - off[i];
             double h = (double)step * tick;
+            double ih = 1.0 / h;
+            double ih2 = ih * ih, ih3 = ih2 * ih;
             double h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
             double a2[3], a3[3], a2e[3];
             for (int c = 0; c < 3; ++c) {
                 int64_t k = 3 * i + c;
                 double da = a[k] - a1[c];
-                a2[c] = (-6.0 * da - h * (4.0 * jk[k] + 2.0 * j1[c])) / h2;
-                a3[c] = (12.0 * da + 6.0 * h * (jk[k] + j1[c])) / h3;
-                x[k] = xp[k] + a2[c] * (h4 / 24.0) + a3[c] * (h5 / 120.0);
-                v[k] = vp[k] + a2[c] * (h3 / 6.0) + a3[c] * (h4 / 24.0);
+                a2[c] = (-6.0 * da - h * (4.0 * jk[k] + 2.0 * j1[c])) * ih2;
+                a3[c] = (12.0 * da + 6.0 * h * (jk[k] + j1[c])) * ih3;
+                x[k] = xp[k] + a2[c] * (h4 * P.c24) + a3[c] * (h5 * P.c120);
+                v[k] = vp[k] + a2[c] * (h3 * P.c6) + a3[c] * (h4 * P.c24);
                 a[k] = a1[c];
                 jk[k] = j1[c];
                 a2e[c] = a2[c] + a3[c] * h;
             }
             t[i] = tn;
             if (tn == T) continue;
-            /* Eq. timestep:0 */
-            double a0 = alpha * G * m[i] / (r_cut * r_cut);
+            /* Eq. timestep:0, with sqrt(A) sqrt(B) taken as sqrt(A B) */
+            double a0 = P.a0c * m[i];
             double aa = orc_dot3(a1, a1);
             double a2sq = orc_dot3(a2e, a2e);
-            double num = sqrt(aa + a0 * a0) * sqrt(a2sq) + orc_dot3(j1, j1);
-            double den = sqrt(aa) * sqrt(orc_dot3(a3, a3)) + a2sq;
+            double num = sqrt((aa + a0 * a0) * a2sq) + orc_dot3(j1, j1);
+            double den = sqrt(aa * orc_dot3(a3, a3)) + a2sq;
             double crit = den > 0.0 ? eta * sqrt(num / den) : INFINITY;
             int kmin = lev[i] > 0 ? lev[i] - 1 : 0;
             int k = orc_level(crit, dt_max, kmin, kmax);

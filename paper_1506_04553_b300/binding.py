@@ -62,7 +62,8 @@ class _CStats(C.Structure):
         "n", "n_cells", "n_groups", "n_levels", "list_pc", "list_pp_near",
         "list_pp_far", "int_pc", "int_pp", "int_pp_near", "max_walk_stack",
         "nnz", "herm_block_steps", "herm_particle_steps", "herm_pairs",
-        "herm_capped", "herm_components", "herm_max_component")]
+        "herm_capped", "herm_components", "herm_max_component",
+        "herm_max_block_steps")]
 
 
 class _CHermite(C.Structure):

@@ -276,7 +276,7 @@ void free_all(p3t_ctx *c)
                     c->clus_off, c->cc, c->clus_box, c->pclus, c->gclus,
                     c->gperm, c->gcost, c->pgroup, c->hparent, c->hcsize,
                     c->hcfill, c->hmember, c->hlev, c->hcstart, c->ht, c->ha,
-                    c->hj, c->hxp, c->hvp};
+                    c->hj, c->hxp, c->hvp, c->hroots, c->hroot_off};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hst) cudaFreeHost(c->hst);
@@ -502,6 +502,8 @@ int ensure_hermite(p3t_ctx *c, int64_t n)
         P3T_TRY(grow(c->hmember, d, cap, sizeof(int)));
         P3T_TRY(grow(c->hlev, d, cap, sizeof(int)));
         P3T_TRY(grow(c->hcstart, d, cap + 1, sizeof(long long)));
+        P3T_TRY(grow(c->hroots, d, cap, sizeof(int)));
+        P3T_TRY(grow(c->hroot_off, d, cap + 1, sizeof(long long)));
         P3T_TRY(grow(c->ht, d, cap, sizeof(long long)));
         P3T_TRY(grow(c->ha, d, 3 * cap, sizeof(double)));
         P3T_TRY(grow(c->hj, d, 3 * cap, sizeof(double)));
@@ -620,6 +622,7 @@ int p3t_get_stats(p3t_ctx *c, p3t_stats *o)
     o->herm_capped = c->hst->herm[3];
     o->herm_components = c->hst->herm[4];
     o->herm_max_component = c->hst->herm[5];
+    o->herm_max_block_steps = c->hst->herm[6];
     if (c->n == 0) return P3T_OK;
     o->n_cells = c->hst->ncell;
     o->n_groups = c->hst->ngroup;

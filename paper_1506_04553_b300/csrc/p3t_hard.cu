@@ -11,7 +11,9 @@
 //                       - (dK/ds) ((q.u) / s) q / s^3 ].
 // All of it is FP64 with one rounding per operation (explicit __d*_rn
 // intrinsics, no contraction), in a fixed order, so the results do not
-// depend on the compiler's choices.
+// depend on the compiler's choices.  Divisions and square roots are costly
+// in FP64 and few: 1/s per pair, 1/h per correction, and constants (1/r_cut,
+// 1/(1 - gamma), alpha G / r_cut^2, 1/6, 1/24, 1/120) formed once.
 //
 // Integration.  Neighbour rows are symmetric (the neighbour predicate is),
 // and a particle never comes within r_cut of one outside its row during
@@ -77,11 +79,29 @@ __device__ __forceinline__ double dK_of_x(double x)
                 dmul(140.0, x3));
 }
 
+// Constants of the hard part, formed once on the host in this order.
 struct HardPar {
     double G, eps2, r_cut, gamma;
+    double irc;     // 1 / r_cut
+    double iomg;    // 1 / (1 - gamma)
+    double iomgrc;  // 1 / ((1 - gamma) r_cut)
 };
 
-// Hard acceleration and jerk of particle i (SoA arrays of length 3n).
+HardPar hard_par(double G, double eps, double r_cut, double gamma)
+{
+    HardPar P;
+    P.G = G;
+    P.eps2 = eps * eps;
+    P.r_cut = r_cut;
+    P.gamma = gamma;
+    P.irc = 1.0 / r_cut;
+    P.iomg = 1.0 / (1.0 - gamma);
+    P.iomgrc = 1.0 / ((1.0 - gamma) * r_cut);
+    return P;
+}
+
+// Hard acceleration and jerk of particle i (SoA arrays of length 3n); one
+// square root and one division per pair (1/s, then its powers).
 // x and v may be the predicted arrays that other lanes of the warp wrote in
 // this launch: plain (coherent) loads, no read-only cache.
 __device__ void hard_one(int i, int n, const double *x, const double *v,
@@ -91,7 +111,6 @@ __device__ void hard_one(int i, int n, const double *x, const double *v,
                          double *a, double *jk, long long *pairs)
 {
     double acc[3] = {0.0, 0.0, 0.0}, jrk[3] = {0.0, 0.0, 0.0};
-    const double omg = dsub(1.0, P.gamma);
     const double xi[3] = {x[i], x[(size_t)n + i], x[2 * (size_t)n + i]};
     const double vi[3] = {v[i], v[(size_t)n + i], v[2 * (size_t)n + i]};
     const long long e0 = off[i], e1 = off[i + 1];
@@ -105,15 +124,17 @@ __device__ void hard_one(int i, int n, const double *x, const double *v,
         }
         const double s2 = dadd(dot3(q[0], q[1], q[2], q[0], q[1], q[2]), P.eps2);
         const double s = dsqrt(s2);
-        const double xk = ddiv(dsub(ddiv(s, P.r_cut), P.gamma), omg);
+        const double ri = ddiv(1.0, s);
+        const double ri2 = dmul(ri, ri);
+        const double ri3 = dmul(ri2, ri);
+        const double xk = dmul(dsub(dmul(s, P.irc), P.gamma), P.iomg);
         const double w = dsub(1.0, K_of_x(xk));
-        const double dKds = ddiv(dK_of_x(xk), dmul(omg, P.r_cut));
-        const double s3 = dmul(s2, s);
+        const double dKds = dmul(dK_of_x(xk), P.iomgrc);
         const double rv = dot3(q[0], q[1], q[2], u[0], u[1], u[2]);
         const double gm = dmul(P.G, m[j]);
-        const double fa = ddiv(dmul(gm, w), s3);
-        const double c1 = ddiv(dmul(3.0, rv), s2);
-        const double fb = ddiv(dmul(gm, ddiv(dmul(dKds, rv), s)), s3);
+        const double fa = dmul(dmul(gm, w), ri3);
+        const double c1 = dmul(dmul(3.0, rv), ri2);
+        const double fb = dmul(dmul(gm, dmul(dmul(dKds, rv), ri)), ri3);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             acc[c] = dsub(acc[c], dmul(fa, q[c]));
@@ -236,11 +257,95 @@ k_comp_fill(int n, const long long *__restrict__ off, int *parent,
     }
 }
 
+// The component roots in one dense list: the large components (more than
+// SMALL_COMP particles, integrated one warp each) first, then the small ones
+// (one thread each); deepest first within each class.  The depth of a
+// component is the deepest first-step level of its members (held at the
+// root in clev).  A counting sort over 2 x 64 buckets: histogram, one-warp
+// scan, scatter; the order inside a bucket is arbitrary and no result
+// depends on it.  Counts: nroot[0] all roots, nroot[1] large ones.
+constexpr int NLB = 64;   // level buckets per class
+constexpr int NB = 2 * NLB;
+
+#ifndef P3T_SMALL_COMP
+#define P3T_SMALL_COMP 4
+#endif
+// components up to this size: one thread each; larger ones: one warp each
+constexpr int SMALL_COMP = P3T_SMALL_COMP;
+
+__global__ void __launch_bounds__(HB)
+k_comp_level(int n, const long long *__restrict__ off, int *parent,
+             const int *__restrict__ lev, int *__restrict__ clev, P3TDevState *st)
+{
+    for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB) {
+        if (off[i + 1] == off[i]) continue;
+        int rounds = 0;
+        const int r = uf_find(parent, i, &rounds);
+        if (r < 0) {
+            p3t_raise(st, P3T_ERR_TIMEOUT);
+            continue;
+        }
+        atomicMax(clev + r, lev[i]);
+    }
+}
+
+__device__ __forceinline__ int root_bucket(int size, int lv)
+{
+    const int b = NLB - 1 - (lv < NLB - 1 ? lv : NLB - 1);  // deepest first
+    return size > SMALL_COMP ? b : NLB + b;                // large ones first
+}
+
+__global__ void __launch_bounds__(HB)
+k_root_hist(int n, const int *__restrict__ parent, const int *__restrict__ csize,
+            const int *__restrict__ clev, int *__restrict__ bcount)
+{
+    __shared__ int h[NB];
+    if (threadIdx.x < NB) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB)
+        if (parent[i] == i && csize[i] > 0)
+            atomicAdd(&h[root_bucket(csize[i], clev[i])], 1);
+    __syncthreads();
+    if (threadIdx.x < NB && h[threadIdx.x]) atomicAdd(bcount + threadIdx.x, h[threadIdx.x]);
+}
+
+// bcount[0..NB) -> exclusive starts in bcount[NB..2 NB); counts in nroot
+__global__ void k_root_scan(int *bcount, long long *nroot)
+{
+    const int lane = threadIdx.x;
+    int c[NB / 32], sum = 0;
+#pragma unroll
+    for (int q = 0; q < NB / 32; ++q) {
+        c[q] = bcount[lane * (NB / 32) + q];
+        sum += c[q];
+    }
+    int ex = warp_incl_scan(sum) - sum;
+#pragma unroll
+    for (int q = 0; q < NB / 32; ++q) {
+        const int b = lane * (NB / 32) + q;
+        bcount[NB + b] = ex;
+        if (b == NLB) nroot[1] = ex;  // roots before the first small bucket
+        ex += c[q];
+    }
+    if (lane == 31) nroot[0] = ex;
+}
+
+__global__ void __launch_bounds__(HB)
+k_root_scatter(int n, const int *__restrict__ parent, const int *__restrict__ csize,
+               const int *__restrict__ clev, int *bcount, int *__restrict__ roots)
+{
+    for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB)
+        if (parent[i] == i && csize[i] > 0)
+            roots[atomicAdd(bcount + NB + root_bucket(csize[i], clev[i]), 1)] = i;
+}
+
 // ------------------------------------------------------------------ Hermite
 
 struct HermPar {
     HardPar f;
-    double eta, eta_s, alpha, dt_soft, dt_max, tick;
+    double eta, eta_s, dt_soft, dt_max, tick;
+    double a0c;            // alpha G / r_cut^2: a_0 = a0c m_i
+    double c6, c24, c120;  // 1/6, 1/24, 1/120
     long long T;  // dt_soft in ticks
     int kmax;
 };
@@ -279,8 +384,7 @@ k_herm_init(int n, const double *__restrict__ x, const double *__restrict__ v,
             a[(size_t)c * n + i] = ai[c];
             jk[(size_t)c * n + i] = ji[c];
         }
-        const double a0 = ddiv(dmul(dmul(H.alpha, H.f.G), m[i]),
-                               dmul(H.f.r_cut, H.f.r_cut));
+        const double a0 = dmul(H.a0c, m[i]);
         const double jj = dot3(ji[0], ji[1], ji[2], ji[0], ji[1], ji[2]);
         double crit = INFINITY;
         if (jj > 0.0)
@@ -306,122 +410,230 @@ __device__ __forceinline__ long long warp_min_ll(long long v)
     return v;
 }
 
-// One warp per component (the warp that meets the component's root in a
-// warp-strided sweep over the particles).  The state arrays are shared by the
-// lanes of a warp (each lane writes its members, all read the neighbours'
-// predictions), so they are plain pointers; __syncwarp orders the phases.
+// Prediction of particle i to tick tn (third order).
+__device__ __forceinline__ void predict_one(int i, int n, long long tn,
+                                            const HermPar &H, const double *x,
+                                            const double *v, const double *a,
+                                            const double *jk, double *xp,
+                                            double *vp, const long long *t)
+{
+    const double d = dmul((double)(tn - t[i]), H.tick);
+    const double d2 = dmul(dmul(d, d), 0.5);
+    const double d3 = dmul(dmul(dmul(d, d), d), H.c6);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const size_t k = (size_t)c * n + i;
+        xp[k] = dadd(dadd(dadd(x[k], dmul(v[k], d)), dmul(a[k], d2)),
+                     dmul(jk[k], d3));
+        vp[k] = dadd(dadd(v[k], dmul(a[k], d)), dmul(jk[k], d2));
+    }
+}
+
+// Evaluation at tn from the predicted values and correction of particle i
+// (due at tn), then its next level (Eq. timestep:0).
+__device__ __forceinline__ void correct_one(
+    int i, int n, long long tn, const HermPar &H, double *x, double *v,
+    const double *__restrict__ m, const long long *__restrict__ off,
+    const int *__restrict__ idx, double *a, double *jk, const double *xp,
+    const double *vp, long long *t, int *lev, long long &pairs,
+    long long &capped)
+{
+    const long long step = 1LL << (H.kmax - lev[i]);
+    double a1[3], j1[3];
+    hard_one(i, n, xp, vp, m, off, idx, H.f, a1, j1, &pairs);
+    const double h = dmul((double)step, H.tick);
+    const double ih = ddiv(1.0, h);
+    const double ih2 = dmul(ih, ih), ih3 = dmul(ih2, ih);
+    const double h2 = dmul(h, h), h3 = dmul(h2, h), h4 = dmul(h3, h),
+                 h5 = dmul(h4, h);
+    (void)h2;
+    double a2[3], a3[3], a2e[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const size_t k = (size_t)c * n + i;
+        const double j0 = jk[k];
+        const double da = dsub(a[k], a1[c]);
+        a2[c] = dmul(dsub(dmul(-6.0, da),
+                          dmul(h, dadd(dmul(4.0, j0), dmul(2.0, j1[c])))),
+                     ih2);
+        a3[c] = dmul(dadd(dmul(12.0, da), dmul(dmul(6.0, h), dadd(j0, j1[c]))),
+                     ih3);
+        x[k] = dadd(dadd(xp[k], dmul(a2[c], dmul(h4, H.c24))),
+                    dmul(a3[c], dmul(h5, H.c120)));
+        v[k] = dadd(dadd(vp[k], dmul(a2[c], dmul(h3, H.c6))),
+                    dmul(a3[c], dmul(h4, H.c24)));
+        a[k] = a1[c];
+        jk[k] = j1[c];
+        a2e[c] = dadd(a2[c], dmul(a3[c], h));
+    }
+    t[i] = tn;
+    if (tn == H.T) return;
+    // Eq. timestep:0, with sqrt(A) sqrt(B) taken as sqrt(A B)
+    const double a0 = dmul(H.a0c, m[i]);
+    const double aa = dot3(a1[0], a1[1], a1[2], a1[0], a1[1], a1[2]);
+    const double a2sq = dot3(a2e[0], a2e[1], a2e[2], a2e[0], a2e[1], a2e[2]);
+    const double num = dadd(dsqrt(dmul(dadd(aa, dmul(a0, a0)), a2sq)),
+                            dot3(j1[0], j1[1], j1[2], j1[0], j1[1], j1[2]));
+    const double den = dadd(dsqrt(dmul(aa, dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]))),
+                            a2sq);
+    const double crit = den > 0.0 ? dmul(H.eta, dsqrt(ddiv(num, den))) : INFINITY;
+    const int kmin = lev[i] > 0 ? lev[i] - 1 : 0;
+    int k = level_for(crit, H.dt_max, kmin, H.kmax);
+    if (k == H.kmax && ldexp(H.dt_max, -H.kmax) > crit) ++capped;
+    while (tn % (1LL << (H.kmax - k)) != 0) ++k;
+    lev[i] = k;
+}
+
+
+
+// One hard step of one component by a whole warp: lanes over the members.
+// The state arrays are shared by the lanes (each lane writes its members,
+// all read the neighbours' predictions), so they are plain pointers;
+// __syncwarp orders the phases.
+__device__ void integrate_warp(int size, long long base, int lane, int n,
+                               double *x, double *v, const double *__restrict__ m,
+                               const long long *__restrict__ off,
+                               const int *__restrict__ idx,
+                               const int *__restrict__ member, const HermPar &H,
+                               double *a, double *jk, double *xp, double *vp,
+                               long long *t, int *lev, P3TDevState *st,
+                               long long &nblk, long long &nstep,
+                               long long &pairs, long long &capped,
+                               long long &maxblk)
+{
+    for (long long it = 0;; ++it) {
+        if (it >= MAX_BLOCK_STEPS) {
+            if (lane == 0) p3t_raise(st, P3T_ERR_TIMEOUT);
+            return;
+        }
+        long long tmin = H.T;
+        bool live = false;
+        for (int q = lane; q < size; q += 32) {
+            const int i = member[base + q];
+            if (t[i] == H.T) continue;
+            const long long e = t[i] + (1LL << (H.kmax - lev[i]));
+            tmin = e < tmin ? e : tmin;
+            live = true;
+        }
+        if (!__any_sync(0xffffffffu, live)) {
+            maxblk = it > maxblk ? it : maxblk;
+            return;
+        }
+        const long long tn = warp_min_ll(tmin);
+        if (lane == 0) ++nblk;
+        for (int q = lane; q < size; q += 32)
+            predict_one(member[base + q], n, tn, H, x, v, a, jk, xp, vp, t);
+        __syncwarp();
+        for (int q = lane; q < size; q += 32) {
+            const int i = member[base + q];
+            if (t[i] + (1LL << (H.kmax - lev[i])) != tn) continue;
+            correct_one(i, n, tn, H, x, v, m, off, idx, a, jk, xp, vp, t, lev,
+                        pairs, capped);
+            ++nstep;
+        }
+        __syncwarp();
+    }
+}
+
+// One hard step of one small component by a single thread.
+__device__ void integrate_thread(int size, long long base, int n, double *x,
+                                 double *v, const double *__restrict__ m,
+                                 const long long *__restrict__ off,
+                                 const int *__restrict__ idx,
+                                 const int *__restrict__ member,
+                                 const HermPar &H, double *a, double *jk,
+                                 double *xp, double *vp, long long *t, int *lev,
+                                 P3TDevState *st, long long &nblk,
+                                 long long &nstep, long long &pairs,
+                                 long long &capped, long long &maxblk)
+{
+    for (long long it = 0;; ++it) {
+        if (it >= MAX_BLOCK_STEPS) {
+            p3t_raise(st, P3T_ERR_TIMEOUT);
+            return;
+        }
+        long long tn = H.T;
+        bool live = false;
+        for (int q = 0; q < size; ++q) {
+            const int i = member[base + q];
+            if (t[i] == H.T) continue;
+            const long long e = t[i] + (1LL << (H.kmax - lev[i]));
+            tn = e < tn ? e : tn;
+            live = true;
+        }
+        if (!live) {
+            maxblk = it > maxblk ? it : maxblk;
+            return;
+        }
+        ++nblk;
+        for (int q = 0; q < size; ++q)
+            predict_one(member[base + q], n, tn, H, x, v, a, jk, xp, vp, t);
+        for (int q = 0; q < size; ++q) {
+            const int i = member[base + q];
+            if (t[i] + (1LL << (H.kmax - lev[i])) != tn) continue;
+            correct_one(i, n, tn, H, x, v, m, off, idx, a, jk, xp, vp, t, lev,
+                        pairs, capped);
+            ++nstep;
+        }
+    }
+}
+
+// All components of a hard step, fetched dynamically by warps from one work
+// list, longest first: item k < nlarge is the large component roots[k] (one
+// warp); later items are chunks of 32 consecutive small components (one
+// thread each).  *work counts the items handed out (zero at launch).
 __global__ void __launch_bounds__(HB)
-k_herm_components(int n, double *x, double *v, const double *__restrict__ m,
-                  const long long *__restrict__ off, const int *__restrict__ idx,
-                  const int *__restrict__ parent, const int *__restrict__ csize,
-                  const long long *__restrict__ cstart,
-                  const int *__restrict__ member, HermPar H, double *a,
-                  double *jk, double *xp, double *vp, long long *t, int *lev,
-                  P3TDevState *st)
+k_herm_all(int n, double *x, double *v, const double *__restrict__ m,
+           const long long *__restrict__ off, const int *__restrict__ idx,
+           const int *__restrict__ roots, const long long *__restrict__ nroot,
+           const int *__restrict__ csize, const long long *__restrict__ cstart,
+           const int *__restrict__ member, HermPar H, double *a, double *jk,
+           double *xp, double *vp, long long *t, int *lev,
+           unsigned long long *work, P3TDevState *st)
 {
     if (st->error) return;
     const int lane = threadIdx.x & 31;
-    const int wg = (blockIdx.x * HB + threadIdx.x) >> 5;
-    const int nw = gridDim.x * (HB / 32);
-    long long nblk = 0, nstep = 0, pairs = 0, capped = 0, ncomp = 0;
+    const long long nr = nroot[0], nlarge = nroot[1];
+    const long long nitems = nlarge + (nr - nlarge + 31) / 32;
+    long long nblk = 0, nstep = 0, pairs = 0, capped = 0, ncomp = 0, maxblk = 0;
     int maxsize = 0;
-    for (int r = wg; r < n; r += nw) {
-        if (parent[r] != r || csize[r] == 0) continue;  // not a root
-        const int size = csize[r];
-        const long long base = cstart[r];
-        ++ncomp;
-        maxsize = size > maxsize ? size : maxsize;
-        for (long long it = 0;; ++it) {
-            if (it >= MAX_BLOCK_STEPS) {
-                if (lane == 0) p3t_raise(st, P3T_ERR_TIMEOUT);
-                break;
+    for (;;) {
+        long long item = 0;
+        if (lane == 0) item = (long long)atomicAdd(work, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= nitems) break;
+        if (item < nlarge) {
+            const int r = roots[item];
+            const int size = csize[r];
+            if (lane == 0) {
+                ++ncomp;
+                maxsize = size > maxsize ? size : maxsize;
             }
-            // next block time
-            long long tmin = H.T;
-            bool live = false;
-            for (int q = lane; q < size; q += 32) {
-                const int i = member[base + q];
-                if (t[i] == H.T) continue;
-                const long long e = t[i] + (1LL << (H.kmax - lev[i]));
-                tmin = e < tmin ? e : tmin;
-                live = true;
+            integrate_warp(size, cstart[r], lane, n, x, v, m, off, idx, member,
+                           H, a, jk, xp, vp, t, lev, st, nblk, nstep, pairs,
+                           capped, maxblk);
+        } else {
+            const long long kr = nlarge + 32 * (item - nlarge) + lane;
+            if (kr < nr) {
+                const int r = roots[kr];
+                const int size = csize[r];
+                ++ncomp;
+                maxsize = size > maxsize ? size : maxsize;
+                integrate_thread(size, cstart[r], n, x, v, m, off, idx, member,
+                                 H, a, jk, xp, vp, t, lev, st, nblk, nstep,
+                                 pairs, capped, maxblk);
             }
-            if (!__any_sync(0xffffffffu, live)) break;
-            const long long tn = warp_min_ll(tmin);
-            ++nblk;
-            // predict every member to tn
-            for (int q = lane; q < size; q += 32) {
-                const int i = member[base + q];
-                const double d = dmul((double)(tn - t[i]), H.tick);
-                const double d2 = dmul(dmul(d, d), 0.5);
-                const double d3 = ddiv(dmul(dmul(d, d), d), 6.0);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const size_t k = (size_t)c * n + i;
-                    xp[k] = dadd(dadd(dadd(x[k], dmul(v[k], d)), dmul(a[k], d2)),
-                                 dmul(jk[k], d3));
-                    vp[k] = dadd(dadd(v[k], dmul(a[k], d)), dmul(jk[k], d2));
-                }
-            }
-            __syncwarp();
-            // evaluate and correct the members due at tn
-            for (int q = lane; q < size; q += 32) {
-                const int i = member[base + q];
-                const long long step = 1LL << (H.kmax - lev[i]);
-                if (t[i] + step != tn) continue;
-                double a1[3], j1[3];
-                hard_one(i, n, xp, vp, m, off, idx, H.f, a1, j1, &pairs);
-                ++nstep;
-                const double h = dmul((double)step, H.tick);
-                const double h2 = dmul(h, h), h3 = dmul(h2, h), h4 = dmul(h3, h),
-                             h5 = dmul(h4, h);
-                double a2[3], a3[3], a2e[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const size_t k = (size_t)c * n + i;
-                    const double j0 = jk[k];
-                    const double da = dsub(a[k], a1[c]);
-                    a2[c] = ddiv(dsub(dmul(-6.0, da),
-                                      dmul(h, dadd(dmul(4.0, j0), dmul(2.0, j1[c])))),
-                                 h2);
-                    a3[c] = ddiv(dadd(dmul(12.0, da), dmul(dmul(6.0, h), dadd(j0, j1[c]))),
-                                 h3);
-                    x[k] = dadd(dadd(xp[k], dmul(a2[c], ddiv(h4, 24.0))),
-                                dmul(a3[c], ddiv(h5, 120.0)));
-                    v[k] = dadd(dadd(vp[k], dmul(a2[c], ddiv(h3, 6.0))),
-                                dmul(a3[c], ddiv(h4, 24.0)));
-                    a[k] = a1[c];
-                    jk[k] = j1[c];
-                    a2e[c] = dadd(a2[c], dmul(a3[c], h));
-                }
-                t[i] = tn;
-                if (tn == H.T) continue;
-                // Eq. timestep:0
-                const double a0 = ddiv(dmul(dmul(H.alpha, H.f.G), m[i]),
-                                       dmul(H.f.r_cut, H.f.r_cut));
-                const double aa = dot3(a1[0], a1[1], a1[2], a1[0], a1[1], a1[2]);
-                const double a2sq = dot3(a2e[0], a2e[1], a2e[2], a2e[0], a2e[1], a2e[2]);
-                const double num = dadd(dmul(dsqrt(dadd(aa, dmul(a0, a0))), dsqrt(a2sq)),
-                                        dot3(j1[0], j1[1], j1[2], j1[0], j1[1], j1[2]));
-                const double den = dadd(dmul(dsqrt(aa),
-                                             dsqrt(dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]))),
-                                        a2sq);
-                const double crit = den > 0.0 ? dmul(H.eta, dsqrt(ddiv(num, den))) : INFINITY;
-                const int kmin = lev[i] > 0 ? lev[i] - 1 : 0;
-                int k = level_for(crit, H.dt_max, kmin, H.kmax);
-                if (k == H.kmax && ldexp(H.dt_max, -H.kmax) > crit) ++capped;
-                while (tn % (1LL << (H.kmax - k)) != 0) ++k;
-                lev[i] = k;
-            }
-            __syncwarp();
         }
     }
-    // totals: sums over lanes, then one atomic per warp
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
+        nblk += __shfl_xor_sync(0xffffffffu, nblk, o);
         nstep += __shfl_xor_sync(0xffffffffu, nstep, o);
         pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
         capped += __shfl_xor_sync(0xffffffffu, capped, o);
+        ncomp += __shfl_xor_sync(0xffffffffu, ncomp, o);
+        maxsize = max(maxsize, __shfl_xor_sync(0xffffffffu, maxsize, o));
+        maxblk = max(maxblk, __shfl_xor_sync(0xffffffffu, maxblk, o));
     }
     if (lane == 0) {
         if (nblk) atomicAdd((unsigned long long *)&st->herm[0], (unsigned long long)nblk);
@@ -430,6 +642,7 @@ k_herm_components(int n, double *x, double *v, const double *__restrict__ m,
         if (capped) atomicAdd((unsigned long long *)&st->herm[3], (unsigned long long)capped);
         if (ncomp) atomicAdd((unsigned long long *)&st->herm[4], (unsigned long long)ncomp);
         if (maxsize) atomicMax((unsigned long long *)&st->herm[5], (unsigned long long)maxsize);
+        if (maxblk) atomicMax((unsigned long long *)&st->herm[6], (unsigned long long)maxblk);
     }
 }
 
@@ -451,7 +664,7 @@ k_drift_isolated(int n, double *__restrict__ x, const double *__restrict__ v,
 __global__ void k_herm_reset(P3TDevState *st)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0)
-        for (int k = 0; k < 6; ++k) st->herm[k] = 0;
+        for (int k = 0; k < 7; ++k) st->herm[k] = 0;
 }
 
 int grid_for(long long n, int sms)
@@ -479,7 +692,7 @@ extern "C" int p3t_hard_force(int64_t n, const double *pos, const double *vel,
     int dev = 0, sms = 0;
     P3T_CUDA_TRY(cudaGetDevice(&dev));
     P3T_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    HardPar P = {G, eps * eps, r_cut, gamma};
+    const HardPar P = hard_par(G, eps, r_cut, gamma);
     k_hard_force<<<grid_for(n, sms), HB, 0, (cudaStream_t)stream>>>(
         (int)n, pos, vel, mass, (const long long *)offsets, idx, P, acc, jerk);
     p3t_count_launches(1);
@@ -492,13 +705,13 @@ int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
                       const p3t_hermite_params *hp, cudaStream_t s)
 {
     HermPar H;
-    H.f.G = c->p.G;
-    H.f.eps2 = c->p.eps * c->p.eps;
-    H.f.r_cut = c->p.r_out;
-    H.f.gamma = c->p.gamma;
+    H.f = hard_par(c->p.G, c->p.eps, c->p.r_out, c->p.gamma);
     H.eta = hp->eta;
     H.eta_s = hp->eta / 10.0;
-    H.alpha = hp->alpha;
+    H.a0c = hp->alpha * c->p.G / (c->p.r_out * c->p.r_out);
+    H.c6 = 1.0 / 6.0;
+    H.c24 = 1.0 / 24.0;
+    H.c120 = 1.0 / 120.0;
     H.dt_soft = hp->dt_soft;
     H.dt_max = ldexp(hp->dt_soft, -hp->log2_soft_over_max);
     H.tick = ldexp(H.dt_max, -hp->kmax);
@@ -517,12 +730,27 @@ int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
                                  c->hmember, c->st);
     k_herm_init<<<g, HB, 0, s>>>(n, pos, vel, mass, off, idx, H, c->ha, c->hj,
                                  c->ht, c->hlev, c->st);
-    // one warp per component root, every SM busy
-    k_herm_components<<<c->sms * 4, HB, 0, s>>>(
-        n, pos, vel, mass, off, idx, c->hparent, c->hcsize, c->hcstart,
-        c->hmember, H, c->ha, c->hj, c->hxp, c->hvp, c->ht, c->hlev, c->st);
+    // dense list of component roots, large then small, deepest first (the
+    // fill counters are free again and hold the component levels; the
+    // bucket counters sit at the start of hroot_off, then the two counts and
+    // the work counter)
+    P3T_CUDA_TRY(cudaMemsetAsync(c->hcfill, 0, sizeof(int) * (size_t)n, s));
+    int *bcount = (int *)c->hroot_off;
+    long long *nroot = c->hroot_off + NB;
+    unsigned long long *work = (unsigned long long *)(c->hroot_off + NB + 2);
+    P3T_CUDA_TRY(cudaMemsetAsync(c->hroot_off, 0, sizeof(long long) * (NB + 3), s));
+    k_comp_level<<<g, HB, 0, s>>>(n, off, c->hparent, c->hlev, c->hcfill, c->st);
+    k_root_hist<<<g, HB, 0, s>>>(n, c->hparent, c->hcsize, c->hcfill, bcount);
+    k_root_scan<<<1, 32, 0, s>>>(bcount, nroot);
+    k_root_scatter<<<g, HB, 0, s>>>(n, c->hparent, c->hcsize, c->hcfill, bcount,
+                                    c->hroots);
+    // every component, longest first, from one dynamically shared list
+    k_herm_all<<<c->sms * 4, HB, 0, s>>>(
+        n, pos, vel, mass, off, idx, c->hroots, nroot, c->hcsize, c->hcstart,
+        c->hmember, H, c->ha, c->hj, c->hxp, c->hvp, c->ht, c->hlev, work,
+        c->st);
     k_drift_isolated<<<g, HB, 0, s>>>(n, pos, vel, off, hp->dt_soft);
-    p3t_count_launches(8);
+    p3t_count_launches(12);  // the scan counts its own
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
 }

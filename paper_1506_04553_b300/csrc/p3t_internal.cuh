@@ -51,9 +51,10 @@ struct P3TDevState {
     int cost_n;         // n of the force evaluation that wrote gcost/pgroup
     int cost_groups;    // number of groups of that evaluation
     int pad1;
-    long long herm[6];  // hard step: block steps (summed over components),
+    long long herm[7];  // hard step: block steps (summed over components),
                         // particle steps, pair evaluations, steps capped at
-                        // the finest level, components, largest component
+                        // the finest level, components, largest component,
+                        // most block steps of one component
 };
 
 // Phase timing with CUDA events (resolved lazily at p3t_get_profile).
@@ -123,8 +124,8 @@ struct p3t_ctx {
     // energy scratch
     double *red_part;
     // hard step (Hermite) scratch, per particle
-    int *hparent, *hcsize, *hcfill, *hmember, *hlev;
-    long long *hcstart, *ht;
+    int *hparent, *hcsize, *hcfill, *hmember, *hlev, *hroots;
+    long long *hcstart, *ht, *hroot_off;
     double *ha, *hj, *hxp, *hvp;
     int64_t cap_herm;
     // clusters (one for a plain build)
