@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-p3t", action="store_true")
+    ap.add_argument("--no-king", action="store_true")
     return ap.parse_args()
 
 
@@ -548,6 +549,8 @@ def run_ours(args, world, rank, local):
         line["ensemble"] = run_ensemble(args, dev)
     if not args.no_p3t:
         line["p3t_step"] = run_p3t_step(args, dev)
+    if not args.no_king:
+        line["king"] = run_king(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_step, desc = oracle_sample(pos_h, mass_h, frac=1 / 16)
         line["cpu_baseline"] = {"value": n / t_step, "unit": "particles/s",
@@ -656,6 +659,90 @@ def run_p3t_step(args, dev):
             "hard_particle_steps": st["herm_particle_steps"],
             "hard_pairs": st["herm_pairs"], "steps_at_kmax": st["herm_capped"],
             "max_block_steps": st["herm_max_block_steps"]}
+
+
+def run_king(args, dev):
+    """KDK steps on the dense-core workload: King (1966) W0 = 9, N = 2^21,
+    Salpeter masses on [0.1, 10] normalised to M = 1, r_out = 0.002, theta
+    0.5, eps = 4/N, neighbour lists within h = r_out; dt = 1/256.  One step
+    captured in a CUDA graph and replayed; phases from uncaptured steps."""
+    import torch
+    import paper_1506_04553_b300 as P
+    from paper_1506_04553_b300 import ics
+    n = 1 << 21
+    masses = ics.salpeter_masses(n, seed=3 + 7919)
+    pos_h, vel_h, mass_h = ics.king(n, 3, W0=9.0, masses=masses)
+    r_out, theta = 0.002, 0.5
+    mk = lambda flags=0: P.Params(theta=theta, r_out=r_out, gamma=GAMMA,
+                                  eps=4.0 / n, h=r_out, G=1.0, n_leaf=N_LEAF,
+                                  n_group=N_GROUP, flags=flags)
+    ctx = P.Context(mk())
+    pos = torch.tensor(pos_h, device=dev)
+    vel = torch.tensor(vel_h, device=dev)
+    mass = torch.tensor(mass_h, device=dev)
+    acc = torch.empty((3, n), dtype=torch.float32, device=dev)
+    off = torch.empty((n + 1,), dtype=torch.int64, device=dev)
+    ctx.build_tree(pos, mass)
+    ctx.long_force(acc)
+    _, idx0 = ctx.neighbours()
+    idx = torch.empty((max(4 * int(idx0.numel()) + 1024, n),), dtype=torch.int32,
+                      device=dev)
+
+    def step():
+        P.kick(vel, acc, 0.5 * DT)
+        P.drift(pos, vel, DT)
+        ctx.build_tree(pos, mass)
+        ctx.long_force(acc, check=False)
+        ctx.neighbours_into(off, idx, sync=False)
+        P.kick(vel, acc, 0.5 * DT)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile(reset=True)
+    ctx.profile_enable(True)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile_enable(False)
+    prof = ctx.profile(reset=True)
+    nnz = int(off[-1].item())
+    ctx.set_params(mk(P.FLAG_NO_SYNC))
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        step()
+    torch.cuda.current_stream(dev).wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    k = max(args.steps // 4, 8)
+    e0.record(stream)
+    for _ in range(k):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms = e0.elapsed_time(e1) / k
+    nprof = max(prof["forces"], 1)
+    return {"workload": "King W0=9, N=2^21, Salpeter masses 0.1-10 (M=1), "
+                        "r_out 0.002, theta 0.5, eps 4/N, h = r_out, dt 1/256",
+            "step": "KDK (kick, drift, build, force, neighbour lists, kick); "
+                    "one CUDA graph",
+            "n": n, "value": n / (ms * 1e-3), "unit": "particles/s",
+            "ms_per_step": ms,
+            "phase_ms_per_step": {"build": prof["build_ms"] / nprof,
+                                  "walk_and_force": prof["force_ms"] / nprof,
+                                  "neighbours": prof["ngb_ms"] / nprof},
+            "interactions_per_particle": {"pc": prof["int_pc"] / (n * nprof),
+                                          "pp": prof["int_pp"] / (n * nprof)},
+            "neighbour_pairs": nnz}
 
 
 def run_ensemble(args, dev):
