@@ -107,3 +107,51 @@ def test_hard_step_all_isolated_is_a_drift(cuda):
     assert np.array_equal(pg.cpu().numpy().T, pos + 0.25 * vel)
     assert np.array_equal(vg.cpu().numpy().T, vel)
     assert ctx.stats()["herm_components"] == 0
+
+
+def test_hard_step_capped_levels_bitwise(cuda):
+    """A coarse finest level (kmax = 3) caps many steps; the capped schedule
+    and its counter agree with the oracle."""
+    import torch
+    from paper_1506_04553_b300 import Context, HermiteParams, Params
+    pos, vel, m = _gauss(800, 9, 0.02)
+    off, idx = oracle.neighbours(pos, 0.0125)
+    hp = HermiteParams(dt_soft=1 / 64, kmax=3)
+    xo, vo, st = oracle.hermite(pos, vel, m, off, idx, dt_soft=hp.dt_soft, eps=1e-4,
+                                r_cut=0.01, gamma=GAMMA, kmax=3)
+    assert st[3] > 0
+    ctx = Context(Params(r_out=0.01, eps=1e-4, gamma=GAMMA))
+    pg, vg = _dev(pos.T), _dev(vel.T)
+    ctx.hard_step(pg, vg, _dev(m), _dev(off), _dev(idx, torch.int32), hp)
+    assert np.array_equal(pg.cpu().numpy().T, xo)
+    assert np.array_equal(vg.cpu().numpy().T, vo)
+    assert ctx.stats()["herm_capped"] == st[3]
+
+
+def test_hard_part_argument_checks(cuda):
+    import torch
+    from paper_1506_04553_b300 import Context, HermiteParams, P3TError, Params, hard_force
+    pos, vel, m = _gauss(100, 10, 0.05)
+    off = np.zeros(101, dtype=np.int64)
+    idx = np.zeros(0, dtype=np.int32)
+    args = [_dev(pos.T), _dev(vel.T), _dev(m), _dev(off), _dev(idx, torch.int32)]
+    ctx = Context(Params(r_out=0.01))
+    for bad in (dict(eta=0.0), dict(eta=float("nan")), dict(alpha=-1.0),
+                dict(dt_soft=0.0), dict(kmax=0), dict(log2_soft_over_max=-1),
+                dict(log2_soft_over_max=30, kmax=40)):
+        with pytest.raises(P3TError):
+            ctx.hard_step(*args, HermiteParams(**{"dt_soft": 0.01, **bad}))
+    with pytest.raises(P3TError):
+        hard_force(*args, r_cut=1e-20)
+    a, j = hard_force(*args, r_cut=0.01)  # empty rows: no force
+    assert not a.any() and not j.any()
+    # the ensemble layout is refused
+    ctx.set_ensemble(np.array([0, 50, 100], dtype=np.int64))
+    with pytest.raises(P3TError):
+        ctx.hard_step(*args, HermiteParams(dt_soft=0.01))
+    # n = 0 is a no-op
+    e = [torch.zeros((3, 0), dtype=torch.float64, device="cuda"),
+         torch.zeros((3, 0), dtype=torch.float64, device="cuda"),
+         torch.zeros((0,), dtype=torch.float64, device="cuda"),
+         torch.zeros((1,), dtype=torch.int64, device="cuda"), _dev(idx, torch.int32)]
+    Context(Params(r_out=0.01)).hard_step(*e, HermiteParams(dt_soft=0.01))
