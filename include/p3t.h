@@ -213,12 +213,14 @@ typedef struct p3t_hermite_params {
  *   - each block step predicts positions and velocities to the next time
  *     (third order), evaluates the particles due then from the predicted
  *     values and corrects them (fourth order).
- * The rows must be symmetric (those of p3t_neighbours are) and must hold
- * every particle that comes within r_cut during dt_soft (h = r_cut +
- * buffer).  The connected components of the neighbour graph are integrated
- * independently, one warp each.  pos and vel (device double[3][n]) are
- * updated in place; mass device double[n].  Stream-ordered, no host
- * synchronisation; scratch (about 140 B per particle) is allocated on the
+ * The rows must be symmetric (those of p3t_neighbours are; other rows give
+ * undefined positions) and must hold every particle that comes within r_cut
+ * during dt_soft (h = r_cut + buffer).  The connected components of the
+ * neighbour graph are integrated independently: those of up to 32
+ * particles packed into warps, one particle per lane, larger ones one warp
+ * each.  pos and vel (device double[3][n]) are updated in place; mass
+ * device double[n].  Stream-ordered, no host synchronisation; scratch
+ * (about 145 B per particle) is allocated on the
  * first call for a larger n.  Counters in p3t_stats (herm_*).
  * Errors: P3T_ERR_INVALID (arguments, parameters, ensemble layout),
  * P3T_ERR_CUDA; P3T_ERR_TIMEOUT (latched, see p3t_check) when a component

@@ -276,7 +276,7 @@ void free_all(p3t_ctx *c)
                     c->clus_off, c->cc, c->clus_box, c->pclus, c->gclus,
                     c->gperm, c->gcost, c->pgroup, c->hparent, c->hcsize,
                     c->hcfill, c->hmember, c->hlev, c->hcstart, c->ht, c->ha,
-                    c->hj, c->hxp, c->hvp, c->hroots, c->hroot_off};
+                    c->hj, c->hxp, c->hvp, c->hroots, c->hloc, c->hbucket};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hst) cudaFreeHost(c->hst);
@@ -503,7 +503,8 @@ int ensure_hermite(p3t_ctx *c, int64_t n)
         P3T_TRY(grow(c->hlev, d, cap, sizeof(int)));
         P3T_TRY(grow(c->hcstart, d, cap + 1, sizeof(long long)));
         P3T_TRY(grow(c->hroots, d, cap, sizeof(int)));
-        P3T_TRY(grow(c->hroot_off, d, cap + 1, sizeof(long long)));
+        P3T_TRY(grow(c->hloc, d, cap, sizeof(int)));
+        P3T_TRY(grow(c->hbucket, d, P3T_HERM_BUCKET_LL, sizeof(long long)));
         P3T_TRY(grow(c->ht, d, cap, sizeof(long long)));
         P3T_TRY(grow(c->ha, d, 3 * cap, sizeof(double)));
         P3T_TRY(grow(c->hj, d, 3 * cap, sizeof(double)));

@@ -18,11 +18,15 @@
 // Integration.  Neighbour rows are symmetric (the neighbour predicate is),
 // and a particle never comes within r_cut of one outside its row during
 // dt_soft (h is chosen so), so the connected components of the neighbour
-// graph evolve independently for dt_soft.  Each component is integrated by
-// one warp with no synchronisation beyond the warp: components are labelled
-// by a lock-free union-find (label = smallest index of the component),
-// counted, scanned and filled into a member list.  The block-step schedule
-// restricted to one component is exactly the global one.
+// graph evolve independently for dt_soft.  The block-step schedule
+// restricted to one component is exactly the global one, so each component
+// runs its own: components are labelled by a lock-free union-find (label =
+// smallest index of the component), counted, scanned and filled into a
+// member list, then bucketed by depth and size.  Components of up to 32
+// particles are packed into warps, one particle per lane with its state in
+// registers (all slots of a warp step in lock-step, each at its own t_n);
+// larger ones take a warp each, lanes over the members.  No synchronisation
+// reaches beyond a warp.
 //
 // Time is counted in integer ticks of dt_max 2^-kmax, dt_max = dt_soft 2^-p.
 // A particle at level k steps dt_max 2^-k and its time is a multiple of its
@@ -100,8 +104,52 @@ HardPar hard_par(double G, double eps, double r_cut, double gamma)
     return P;
 }
 
-// Hard acceleration and jerk of particle i (SoA arrays of length 3n); one
-// square root and one division per pair (1/s, then its powers).
+// Hard acceleration and jerk of a particle at (xi, vi) from one neighbour at
+// (xj, vj) of mass mj, subtracted into acc and jrk: one square root and one
+// division (1/s, then its powers).
+__device__ __forceinline__ void pair_add(const double xi[3], const double vi[3],
+                                         double xj0, double xj1, double xj2,
+                                         double vj0, double vj1, double vj2,
+                                         double mj, const HardPar &P,
+                                         double acc[3], double jrk[3])
+{
+    const double q[3] = {dsub(xi[0], xj0), dsub(xi[1], xj1), dsub(xi[2], xj2)};
+    const double u[3] = {dsub(vi[0], vj0), dsub(vi[1], vj1), dsub(vi[2], vj2)};
+    const double s2 = dadd(dot3(q[0], q[1], q[2], q[0], q[1], q[2]), P.eps2);
+    const double s = dsqrt(s2);
+    const double ri = ddiv(1.0, s);
+    const double ri2 = dmul(ri, ri);
+    const double ri3 = dmul(ri2, ri);
+    const double xk = dmul(dsub(dmul(s, P.irc), P.gamma), P.iomg);
+    const double w = dsub(1.0, K_of_x(xk));
+    const double dKds = dmul(dK_of_x(xk), P.iomgrc);
+    const double rv = dot3(q[0], q[1], q[2], u[0], u[1], u[2]);
+    const double gm = dmul(P.G, mj);
+    const double fa = dmul(dmul(gm, w), ri3);
+    const double c1 = dmul(dmul(3.0, rv), ri2);
+    const double fb = dmul(dmul(gm, dmul(dmul(dKds, rv), ri)), ri3);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[c] = dsub(acc[c], dmul(fa, q[c]));
+        jrk[c] = dsub(jrk[c], dsub(dmul(fa, dsub(u[c], dmul(c1, q[c]))),
+                                   dmul(fb, q[c])));
+    }
+}
+
+__device__ __forceinline__ void load3(const double *p, int n, int i, double r[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r[c] = p[(size_t)c * n + i];
+}
+
+__device__ __forceinline__ void store3(double *p, int n, int i, const double r[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) p[(size_t)c * n + i] = r[c];
+}
+
+// Hard acceleration and jerk of particle i (SoA arrays of length 3n) over
+// its neighbour row, in row order.
 // x and v may be the predicted arrays that other lanes of the warp wrote in
 // this launch: plain (coherent) loads, no read-only cache.
 __device__ void hard_one(int i, int n, const double *x, const double *v,
@@ -111,36 +159,14 @@ __device__ void hard_one(int i, int n, const double *x, const double *v,
                          double *a, double *jk, long long *pairs)
 {
     double acc[3] = {0.0, 0.0, 0.0}, jrk[3] = {0.0, 0.0, 0.0};
-    const double xi[3] = {x[i], x[(size_t)n + i], x[2 * (size_t)n + i]};
-    const double vi[3] = {v[i], v[(size_t)n + i], v[2 * (size_t)n + i]};
+    double xi[3], vi[3];
+    load3(x, n, i, xi);
+    load3(v, n, i, vi);
     const long long e0 = off[i], e1 = off[i + 1];
     for (long long e = e0; e < e1; ++e) {
         const int j = idx[e];
-        double q[3], u[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            q[c] = dsub(xi[c], x[(size_t)c * n + j]);
-            u[c] = dsub(vi[c], v[(size_t)c * n + j]);
-        }
-        const double s2 = dadd(dot3(q[0], q[1], q[2], q[0], q[1], q[2]), P.eps2);
-        const double s = dsqrt(s2);
-        const double ri = ddiv(1.0, s);
-        const double ri2 = dmul(ri, ri);
-        const double ri3 = dmul(ri2, ri);
-        const double xk = dmul(dsub(dmul(s, P.irc), P.gamma), P.iomg);
-        const double w = dsub(1.0, K_of_x(xk));
-        const double dKds = dmul(dK_of_x(xk), P.iomgrc);
-        const double rv = dot3(q[0], q[1], q[2], u[0], u[1], u[2]);
-        const double gm = dmul(P.G, m[j]);
-        const double fa = dmul(dmul(gm, w), ri3);
-        const double c1 = dmul(dmul(3.0, rv), ri2);
-        const double fb = dmul(dmul(gm, dmul(dmul(dKds, rv), ri)), ri3);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            acc[c] = dsub(acc[c], dmul(fa, q[c]));
-            jrk[c] = dsub(jrk[c], dsub(dmul(fa, dsub(u[c], dmul(c1, q[c]))),
-                                       dmul(fb, q[c])));
-        }
+        pair_add(xi, vi, x[j], x[(size_t)n + j], x[2 * (size_t)n + j], v[j],
+                 v[(size_t)n + j], v[2 * (size_t)n + j], m[j], P, acc, jrk);
     }
     *pairs += e1 - e0;
 #pragma unroll
@@ -257,21 +283,44 @@ k_comp_fill(int n, const long long *__restrict__ off, int *parent,
     }
 }
 
-// The component roots in one dense list: the large components (more than
-// SMALL_COMP particles, integrated one warp each) first, then the small ones
-// (one thread each); deepest first within each class.  The depth of a
-// component is the deepest first-step level of its members (held at the
-// root in clev).  A counting sort over 2 x 64 buckets: histogram, one-warp
-// scan, scatter; the order inside a bucket is arbitrary and no result
-// depends on it.  Counts: nroot[0] all roots, nroot[1] large ones.
-constexpr int NLB = 64;   // level buckets per class
-constexpr int NB = 2 * NLB;
-
-#ifndef P3T_SMALL_COMP
-#define P3T_SMALL_COMP 4
+// The component roots in one dense list, in 33 size classes x 32 level
+// buckets: first the components of more than 32 particles, then sizes 32,
+// 31, ..., 1, and deepest first within a class (the depth of a component is
+// the deepest first-step level of its members, held at the root in clev;
+// levels from 31 on share the last bucket).  A counting sort: histogram,
+// one-warp scan, scatter; the order inside a bucket is arbitrary and no
+// result depends on it.
+//
+// Each class is a queue.  A component of more than 32 particles is one work
+// item (one warp, lanes over its members).  A class of s <= 32 particles is
+// served by ceil(count / (floor(32 / s) R)) work items: warps that pack
+// floor(32 / s) components side by side, one lane per particle, and take the
+// next component of the queue into a slot as soon as the slot's component
+// is done, so that each slot runs about R components back to back.
+#ifndef P3T_HERM_REFILL
+#define P3T_HERM_REFILL 1
 #endif
-// components up to this size: one thread each; larger ones: one warp each
-constexpr int SMALL_COMP = P3T_SMALL_COMP;
+constexpr int REFILL = P3T_HERM_REFILL;
+// k_herm_pack: warps per block and blocks per SM in the grid.  Small blocks
+// free a finished warp's registers at once instead of holding them until the
+// slowest warp of the block is done.
+#ifndef P3T_HERM_WARPS
+#define P3T_HERM_WARPS 8
+#endif
+constexpr int HW = P3T_HERM_WARPS;
+constexpr int NLB = 32;  // level buckets
+constexpr int NS = 33;   // size classes: more than 32, then s = 32 .. 1
+constexpr int NB = NLB * NS;
+static_assert(NB == P3T_HERM_BUCKETS, "bucket scratch");
+static_assert(NB % 32 == 0, "one-warp scan");
+// bucket scratch (ints): counts, root starts (NB + 1), fill counters, item
+// starts per class (NS + 1), queue heads per class, then a 64-bit counter
+constexpr int BK_COUNT = 0, BK_RSTART = NB, BK_RFILL = 2 * NB + 1,
+              BK_ISTART = 3 * NB + 1, BK_NEXT = 3 * NB + NS + 2,
+              BK_WORK = (3 * NB + 2 * NS + 2 + 1) & ~1;
+static_assert(BK_WORK + 2 <= 2 * P3T_HERM_BUCKET_LL, "bucket scratch size");
+
+__device__ __forceinline__ int class_size(int co) { return co == 0 ? 0 : NS - co; }
 
 __global__ void __launch_bounds__(HB)
 k_comp_level(int n, const long long *__restrict__ off, int *parent,
@@ -291,52 +340,69 @@ k_comp_level(int n, const long long *__restrict__ off, int *parent,
 
 __device__ __forceinline__ int root_bucket(int size, int lv)
 {
-    const int b = NLB - 1 - (lv < NLB - 1 ? lv : NLB - 1);  // deepest first
-    return size > SMALL_COMP ? b : NLB + b;                // large ones first
+    const int co = size > 32 ? 0 : NS - size;                 // class order
+    return co * NLB + NLB - 1 - (lv < NLB - 1 ? lv : NLB - 1);  // deepest first
 }
 
 __global__ void __launch_bounds__(HB)
 k_root_hist(int n, const int *__restrict__ parent, const int *__restrict__ csize,
-            const int *__restrict__ clev, int *__restrict__ bcount)
+            const int *__restrict__ clev, int *__restrict__ bk)
 {
     __shared__ int h[NB];
-    if (threadIdx.x < NB) h[threadIdx.x] = 0;
+    for (int b = threadIdx.x; b < NB; b += HB) h[b] = 0;
     __syncthreads();
     for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB)
         if (parent[i] == i && csize[i] > 0)
             atomicAdd(&h[root_bucket(csize[i], clev[i])], 1);
     __syncthreads();
-    if (threadIdx.x < NB && h[threadIdx.x]) atomicAdd(bcount + threadIdx.x, h[threadIdx.x]);
+    for (int b = threadIdx.x; b < NB; b += HB)
+        if (h[b]) atomicAdd(bk + BK_COUNT + b, h[b]);
 }
 
-// bcount[0..NB) -> exclusive starts in bcount[NB..2 NB); counts in nroot
-__global__ void k_root_scan(int *bcount, long long *nroot)
+// counts -> root starts and fill counters (exclusive); then the work items
+// of each class and their starts
+__global__ void k_root_scan(int *bk)
 {
+    constexpr int PER = NB / 32;
+    const int *bcount = bk + BK_COUNT;
+    int *rstart = bk + BK_RSTART, *rfill = bk + BK_RFILL, *istart = bk + BK_ISTART;
     const int lane = threadIdx.x;
-    int c[NB / 32], sum = 0;
-#pragma unroll
-    for (int q = 0; q < NB / 32; ++q) {
-        c[q] = bcount[lane * (NB / 32) + q];
-        sum += c[q];
+    int sr = 0;
+    for (int q = 0; q < PER; ++q) sr += bcount[lane * PER + q];
+    int er = warp_incl_scan(sr) - sr;
+    for (int q = 0; q < PER; ++q) {
+        const int b = lane * PER + q;
+        rstart[b] = er;
+        rfill[b] = er;
+        er += bcount[b];
     }
-    int ex = warp_incl_scan(sum) - sum;
-#pragma unroll
-    for (int q = 0; q < NB / 32; ++q) {
-        const int b = lane * (NB / 32) + q;
-        bcount[NB + b] = ex;
-        if (b == NLB) nroot[1] = ex;  // roots before the first small bucket
-        ex += c[q];
+    if (lane == 31) rstart[NB] = er;
+    __syncwarp();
+    if (lane == 0) {
+        int items = 0;
+        for (int co = 0; co < NS; ++co) {
+            istart[co] = items;
+            const int count = rstart[(co + 1) * NLB] - rstart[co * NLB];
+            const int s = class_size(co);
+            if (s == 0) {
+                items += count;
+            } else if (count > 0) {
+                const int per = (32 / s) * REFILL;
+                items += (count + per - 1) / per;
+            }
+        }
+        istart[NS] = items;
     }
-    if (lane == 31) nroot[0] = ex;
 }
 
 __global__ void __launch_bounds__(HB)
 k_root_scatter(int n, const int *__restrict__ parent, const int *__restrict__ csize,
-               const int *__restrict__ clev, int *bcount, int *__restrict__ roots)
+               const int *__restrict__ clev, int *bk, int *__restrict__ roots)
 {
+    int *rfill = bk + BK_RFILL;
     for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB)
         if (parent[i] == i && csize[i] > 0)
-            roots[atomicAdd(bcount + NB + root_bucket(csize[i], clev[i]), 1)] = i;
+            roots[atomicAdd(rfill + root_bucket(csize[i], clev[i]), 1)] = i;
 }
 
 // ------------------------------------------------------------------ Hermite
@@ -364,26 +430,25 @@ __device__ __forceinline__ int level_for(double crit, double dt_max, int kmin,
 }
 
 // Forces at t = 0 and first-step levels (Eq. timestep:2) of every particle
-// with neighbours.
+// with neighbours: one thread per entry of the member list (*total entries),
+// so that no lane idles on an isolated particle.
 __global__ void __launch_bounds__(HB)
 k_herm_init(int n, const double *__restrict__ x, const double *__restrict__ v,
             const double *__restrict__ m, const long long *__restrict__ off,
-            const int *__restrict__ idx, HermPar H, double *__restrict__ a,
-            double *__restrict__ jk, long long *__restrict__ t,
-            int *__restrict__ lev, P3TDevState *st)
+            const int *__restrict__ idx, const int *__restrict__ member,
+            const long long *__restrict__ total, HermPar H,
+            double *__restrict__ a, double *__restrict__ jk,
+            long long *__restrict__ t, int *__restrict__ lev, P3TDevState *st)
 {
     long long pairs = 0, capped = 0;
-    for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB) {
+    const long long nm = *total;
+    for (long long q = blockIdx.x * HB + threadIdx.x; q < nm; q += gridDim.x * HB) {
+        const int i = member[q];
         t[i] = 0;
-        lev[i] = 0;
-        if (off[i + 1] == off[i]) continue;
         double ai[3], ji[3];
         hard_one(i, n, x, v, m, off, idx, H.f, ai, ji, &pairs);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            a[(size_t)c * n + i] = ai[c];
-            jk[(size_t)c * n + i] = ji[c];
-        }
+        store3(a, n, i, ai);
+        store3(jk, n, i, ji);
         const double a0 = dmul(H.a0c, m[i]);
         const double jj = dot3(ji[0], ji[1], ji[2], ji[0], ji[1], ji[2]);
         double crit = INFINITY;
@@ -410,66 +475,61 @@ __device__ __forceinline__ long long warp_min_ll(long long v)
     return v;
 }
 
-// Prediction of particle i to tick tn (third order).
-__device__ __forceinline__ void predict_one(int i, int n, long long tn,
-                                            const HermPar &H, const double *x,
-                                            const double *v, const double *a,
-                                            const double *jk, double *xp,
-                                            double *vp, const long long *t)
+// Third-order prediction over d = (t_n - t) in time units.
+__device__ __forceinline__ void predict_reg(const double x[3], const double v[3],
+                                            const double a[3], const double jk[3],
+                                            double d, const HermPar &H,
+                                            double xp[3], double vp[3])
 {
-    const double d = dmul((double)(tn - t[i]), H.tick);
     const double d2 = dmul(dmul(d, d), 0.5);
     const double d3 = dmul(dmul(dmul(d, d), d), H.c6);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const size_t k = (size_t)c * n + i;
-        xp[k] = dadd(dadd(dadd(x[k], dmul(v[k], d)), dmul(a[k], d2)),
-                     dmul(jk[k], d3));
-        vp[k] = dadd(dadd(v[k], dmul(a[k], d)), dmul(jk[k], d2));
+        xp[c] = dadd(dadd(dadd(x[c], dmul(v[c], d)), dmul(a[c], d2)),
+                     dmul(jk[c], d3));
+        vp[c] = dadd(dadd(v[c], dmul(a[c], d)), dmul(jk[c], d2));
     }
 }
 
-// Evaluation at tn from the predicted values and correction of particle i
-// (due at tn), then its next level (Eq. timestep:0).
-__device__ __forceinline__ void correct_one(
-    int i, int n, long long tn, const HermPar &H, double *x, double *v,
-    const double *__restrict__ m, const long long *__restrict__ off,
-    const int *__restrict__ idx, double *a, double *jk, const double *xp,
-    const double *vp, long long *t, int *lev, long long &pairs,
-    long long &capped)
+// Correction at tn of a particle due then: from its prediction (xp, vp), the
+// force and jerk (a, jk) at the start of its step and (a1, j1) at tn, the new
+// x and v; a, jk become a1, j1; then its next level (Eq. timestep:0).
+__device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3],
+                                            double jk[3], const double xp[3],
+                                            const double vp[3], const double a1[3],
+                                            const double j1[3], double mi,
+                                            long long tn, const HermPar &H,
+                                            long long &t, int &lev,
+                                            long long &capped)
 {
-    const long long step = 1LL << (H.kmax - lev[i]);
-    double a1[3], j1[3];
-    hard_one(i, n, xp, vp, m, off, idx, H.f, a1, j1, &pairs);
+    const long long step = 1LL << (H.kmax - lev);
     const double h = dmul((double)step, H.tick);
     const double ih = ddiv(1.0, h);
     const double ih2 = dmul(ih, ih), ih3 = dmul(ih2, ih);
     const double h2 = dmul(h, h), h3 = dmul(h2, h), h4 = dmul(h3, h),
                  h5 = dmul(h4, h);
-    (void)h2;
     double a2[3], a3[3], a2e[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const size_t k = (size_t)c * n + i;
-        const double j0 = jk[k];
-        const double da = dsub(a[k], a1[c]);
+        const double j0 = jk[c];
+        const double da = dsub(a[c], a1[c]);
         a2[c] = dmul(dsub(dmul(-6.0, da),
                           dmul(h, dadd(dmul(4.0, j0), dmul(2.0, j1[c])))),
                      ih2);
         a3[c] = dmul(dadd(dmul(12.0, da), dmul(dmul(6.0, h), dadd(j0, j1[c]))),
                      ih3);
-        x[k] = dadd(dadd(xp[k], dmul(a2[c], dmul(h4, H.c24))),
+        x[c] = dadd(dadd(xp[c], dmul(a2[c], dmul(h4, H.c24))),
                     dmul(a3[c], dmul(h5, H.c120)));
-        v[k] = dadd(dadd(vp[k], dmul(a2[c], dmul(h3, H.c6))),
+        v[c] = dadd(dadd(vp[c], dmul(a2[c], dmul(h3, H.c6))),
                     dmul(a3[c], dmul(h4, H.c24)));
-        a[k] = a1[c];
-        jk[k] = j1[c];
+        a[c] = a1[c];
+        jk[c] = j1[c];
         a2e[c] = dadd(a2[c], dmul(a3[c], h));
     }
-    t[i] = tn;
+    t = tn;
     if (tn == H.T) return;
     // Eq. timestep:0, with sqrt(A) sqrt(B) taken as sqrt(A B)
-    const double a0 = dmul(H.a0c, m[i]);
+    const double a0 = dmul(H.a0c, mi);
     const double aa = dot3(a1[0], a1[1], a1[2], a1[0], a1[1], a1[2]);
     const double a2sq = dot3(a2e[0], a2e[1], a2e[2], a2e[0], a2e[1], a2e[2]);
     const double num = dadd(dsqrt(dmul(dadd(aa, dmul(a0, a0)), a2sq)),
@@ -477,19 +537,60 @@ __device__ __forceinline__ void correct_one(
     const double den = dadd(dsqrt(dmul(aa, dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]))),
                             a2sq);
     const double crit = den > 0.0 ? dmul(H.eta, dsqrt(ddiv(num, den))) : INFINITY;
-    const int kmin = lev[i] > 0 ? lev[i] - 1 : 0;
+    const int kmin = lev > 0 ? lev - 1 : 0;
     int k = level_for(crit, H.dt_max, kmin, H.kmax);
     if (k == H.kmax && ldexp(H.dt_max, -H.kmax) > crit) ++capped;
     while (tn % (1LL << (H.kmax - k)) != 0) ++k;
-    lev[i] = k;
+    lev = k;
 }
 
+// Prediction of particle i to tick tn, state in global memory.
+__device__ __forceinline__ void predict_one(int i, int n, long long tn,
+                                            const HermPar &H, const double *x,
+                                            const double *v, const double *a,
+                                            const double *jk, double *xp,
+                                            double *vp, const long long *t)
+{
+    double xi[3], vi[3], ai[3], ji[3], xq[3], vq[3];
+    load3(x, n, i, xi);
+    load3(v, n, i, vi);
+    load3(a, n, i, ai);
+    load3(jk, n, i, ji);
+    predict_reg(xi, vi, ai, ji, dmul((double)(tn - t[i]), H.tick), H, xq, vq);
+    store3(xp, n, i, xq);
+    store3(vp, n, i, vq);
+}
 
+// Evaluation at tn from the predicted arrays and correction of particle i
+// (due at tn), state in global memory.
+__device__ __forceinline__ void correct_one(
+    int i, int n, long long tn, const HermPar &H, double *x, double *v,
+    const double *__restrict__ m, const long long *__restrict__ off,
+    const int *__restrict__ idx, double *a, double *jk, const double *xp,
+    const double *vp, long long *t, int *lev, long long &pairs,
+    long long &capped)
+{
+    double a1[3], j1[3], ai[3], ji[3], xq[3], vq[3], xn[3], vn[3];
+    hard_one(i, n, xp, vp, m, off, idx, H.f, a1, j1, &pairs);
+    load3(a, n, i, ai);
+    load3(jk, n, i, ji);
+    load3(xp, n, i, xq);
+    load3(vp, n, i, vq);
+    long long ti = t[i];
+    int li = lev[i];
+    correct_reg(xn, vn, ai, ji, xq, vq, a1, j1, m[i], tn, H, ti, li, capped);
+    store3(x, n, i, xn);
+    store3(v, n, i, vn);
+    store3(a, n, i, ai);
+    store3(jk, n, i, ji);
+    t[i] = ti;
+    lev[i] = li;
+}
 
-// One hard step of one component by a whole warp: lanes over the members.
-// The state arrays are shared by the lanes (each lane writes its members,
-// all read the neighbours' predictions), so they are plain pointers;
-// __syncwarp orders the phases.
+// One hard step of one component of more than 32 particles by a whole warp:
+// lanes over the members.  The state arrays are shared by the lanes (each
+// lane writes its members, all read the neighbours' predictions), so they
+// are plain pointers; __syncwarp orders the phases.
 __device__ void integrate_warp(int size, long long base, int lane, int n,
                                double *x, double *v, const double *__restrict__ m,
                                const long long *__restrict__ off,
@@ -535,75 +636,168 @@ __device__ void integrate_warp(int size, long long base, int lane, int n,
     }
 }
 
-// One hard step of one small component by a single thread.
-__device__ void integrate_thread(int size, long long base, int n, double *x,
-                                 double *v, const double *__restrict__ m,
-                                 const long long *__restrict__ off,
-                                 const int *__restrict__ idx,
-                                 const int *__restrict__ member,
-                                 const HermPar &H, double *a, double *jk,
-                                 double *xp, double *vp, long long *t, int *lev,
-                                 P3TDevState *st, long long &nblk,
-                                 long long &nstep, long long &pairs,
-                                 long long &capped, long long &maxblk)
+// Predictions and masses of the particles of one packed warp, by lane.
+struct LaneSmem {
+    double xp[3][32], vp[3][32], m[32];
+};
+
+// neighbour rows up to this length are held as lane numbers, 5 bits each
+constexpr int ROW_PACK = 12;
+
+// The queue of one class of components of s <= 32 particles, served by one
+// warp with floor(32 / s) slots: slot q = lane / s holds a component, lane
+// q s + r its r-th member.  Each lane keeps its particle's state in
+// registers; the block steps of the slots run in lock-step, each slot with
+// its own t_n (the least t_i + dt_i over its lanes), and the predictions
+// pass through shared memory.  A slot whose component reaches dt_soft
+// writes it back and takes the next root of the queue (*next counts the
+// roots handed out); the warp leaves when the queue is empty and its slots
+// are done.  loc[i] receives the lane of particle i, so that the rows
+// (global indices) turn into lane numbers; with symmetric rows every
+// neighbour is a member of the same component, and the mask to 5 bits only
+// keeps the shared-memory reads in bounds for rows that are not.
+__device__ void integrate_class(int s, const int *__restrict__ croots, int count,
+                                unsigned *next, int lane, int n, double *x,
+                                double *v, const double *__restrict__ m,
+                                const long long *__restrict__ off,
+                                const int *__restrict__ idx,
+                                const long long *__restrict__ cstart,
+                                const int *__restrict__ member, const HermPar &H,
+                                const double *__restrict__ ga,
+                                const double *__restrict__ gj,
+                                const int *__restrict__ glev, int *loc,
+                                LaneSmem &S, P3TDevState *st, long long &nblk,
+                                long long &nstep, long long &pairs,
+                                long long &capped, long long &ncomp,
+                                int &maxsize, long long &maxblk)
 {
-    for (long long it = 0;; ++it) {
-        if (it >= MAX_BLOCK_STEPS) {
-            p3t_raise(st, P3T_ERR_TIMEOUT);
-            return;
+    const unsigned full = 0xffffffffu;
+    const int slot = lane / s, mi = lane - slot * s, head = slot * s;
+    bool retired = slot >= 32 / s;  // lanes past the last whole slot never work
+    bool have = false;              // the lane holds a particle in flight
+    int i = 0, lev = 0;
+    long long t = 0, e0 = 0, len = 0, blk = 0;
+    unsigned long long row = 0;
+    double xs[3] = {0.0, 0.0, 0.0}, vs[3] = {0.0, 0.0, 0.0};
+    double as[3] = {0.0, 0.0, 0.0}, js[3] = {0.0, 0.0, 0.0}, mass = 0.0;
+    for (;;) {
+        // empty slots take the next component of the queue
+        int r = -1;
+        if (!have && !retired && mi == 0) {
+            const unsigned k = atomicAdd(next, 1u);
+            if (k < (unsigned)count) r = croots[k];
         }
-        long long tn = H.T;
-        bool live = false;
-        for (int q = 0; q < size; ++q) {
-            const int i = member[base + q];
-            if (t[i] == H.T) continue;
-            const long long e = t[i] + (1LL << (H.kmax - lev[i]));
-            tn = e < tn ? e : tn;
-            live = true;
+        r = __shfl_sync(full, r, head);
+        const bool fresh = r >= 0;
+        if (!have && !fresh) retired = true;
+        if (fresh) {
+            i = member[cstart[r] + mi];
+            load3(x, n, i, xs);
+            load3(v, n, i, vs);
+            load3(ga, n, i, as);
+            load3(gj, n, i, js);
+            t = 0;
+            lev = glev[i];
+            mass = m[i];
+            e0 = off[i];
+            len = off[i + 1] - e0;
+            loc[i] = lane;
+            S.m[lane] = mass;
+            have = true;
+            blk = 0;
+            if (mi == 0) {
+                ++ncomp;
+                maxsize = s > maxsize ? s : maxsize;
+            }
         }
-        if (!live) {
-            maxblk = it > maxblk ? it : maxblk;
-            return;
+        if (!__any_sync(full, have)) break;
+        __syncwarp();
+        if (fresh && len <= ROW_PACK) {
+            row = 0;
+            for (int q = 0; q < (int)len; ++q)
+                row |= (unsigned long long)(loc[idx[e0 + q]] & 31) << (5 * q);
         }
-        ++nblk;
-        for (int q = 0; q < size; ++q)
-            predict_one(member[base + q], n, tn, H, x, v, a, jk, xp, vp, t);
-        for (int q = 0; q < size; ++q) {
-            const int i = member[base + q];
-            if (t[i] + (1LL << (H.kmax - lev[i])) != tn) continue;
-            correct_one(i, n, tn, H, x, v, m, off, idx, a, jk, xp, vp, t, lev,
-                        pairs, capped);
+        // one block step of every slot in flight
+        const long long e = have ? t + (1LL << (H.kmax - lev)) : LLONG_MAX;
+        long long tn = e;  // least over the slot: tree over lanes head..head+s-1
+        for (int o = 1; o < s; o <<= 1) {
+            const long long w = __shfl_down_sync(full, tn, o);
+            if (mi + o < s && w < tn) tn = w;
+        }
+        tn = __shfl_sync(full, tn, head);
+        if (have && mi == 0) ++blk;
+        double xp[3], vp[3];
+        if (have) {
+            predict_reg(xs, vs, as, js, dmul((double)(tn - t), H.tick), H, xp, vp);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                S.xp[c][lane] = xp[c];
+                S.vp[c][lane] = vp[c];
+            }
+        }
+        __syncwarp();
+        if (have && e == tn) {
+            double a1[3] = {0.0, 0.0, 0.0}, j1[3] = {0.0, 0.0, 0.0};
+            for (long long q = 0; q < len; ++q) {
+                const int jl = len <= ROW_PACK ? (int)((row >> (5 * q)) & 31)
+                                               : loc[idx[e0 + q]] & 31;
+                pair_add(xp, vp, S.xp[0][jl], S.xp[1][jl], S.xp[2][jl],
+                         S.vp[0][jl], S.vp[1][jl], S.vp[2][jl], S.m[jl], H.f, a1,
+                         j1);
+            }
+            pairs += len;
+            correct_reg(xs, vs, as, js, xp, vp, a1, j1, mass, tn, H, t, lev, capped);
             ++nstep;
         }
+        // every member is due at t_n = dt_soft: the component is done
+        if (have && tn == H.T) {
+            store3(x, n, i, xs);
+            store3(v, n, i, vs);
+            have = false;
+            if (mi == 0) {
+                nblk += blk;
+                maxblk = blk > maxblk ? blk : maxblk;
+            }
+        }
+        if (__any_sync(full, have && blk >= MAX_BLOCK_STEPS)) {
+            if (lane == 0) p3t_raise(st, P3T_ERR_TIMEOUT);
+            break;
+        }
+        __syncwarp();
     }
 }
 
-// All components of a hard step, fetched dynamically by warps from one work
-// list, longest first: item k < nlarge is the large component roots[k] (one
-// warp); later items are chunks of 32 consecutive small components (one
-// thread each).  *work counts the items handed out (zero at launch).
-__global__ void __launch_bounds__(HB)
-k_herm_all(int n, double *x, double *v, const double *__restrict__ m,
-           const long long *__restrict__ off, const int *__restrict__ idx,
-           const int *__restrict__ roots, const long long *__restrict__ nroot,
-           const int *__restrict__ csize, const long long *__restrict__ cstart,
-           const int *__restrict__ member, HermPar H, double *a, double *jk,
-           double *xp, double *vp, long long *t, int *lev,
-           unsigned long long *work, P3TDevState *st)
+// All components of a hard step: warps take work items in order (the big
+// components, deepest first, one warp each; then the queues of the packed
+// classes, largest size first).
+__global__ void __launch_bounds__(HW * 32)
+k_herm_pack(int n, double *x, double *v, const double *__restrict__ m,
+            const long long *__restrict__ off, const int *__restrict__ idx,
+            const int *__restrict__ roots, int *bk, const int *__restrict__ csize,
+            const long long *__restrict__ cstart, const int *__restrict__ member,
+            HermPar H, double *a, double *jk, double *xp, double *vp,
+            long long *t, int *lev, int *loc, P3TDevState *st)
 {
+    __shared__ LaneSmem smem[HW];
     if (st->error) return;
     const int lane = threadIdx.x & 31;
-    const long long nr = nroot[0], nlarge = nroot[1];
-    const long long nitems = nlarge + (nr - nlarge + 31) / 32;
+    LaneSmem &S = smem[threadIdx.x >> 5];
+    const int *rstart = bk + BK_RSTART, *istart = bk + BK_ISTART;
+    unsigned *next = (unsigned *)(bk + BK_NEXT);
+    unsigned long long *work = (unsigned long long *)(bk + BK_WORK);
+    const int nitems = istart[NS];
     long long nblk = 0, nstep = 0, pairs = 0, capped = 0, ncomp = 0, maxblk = 0;
     int maxsize = 0;
     for (;;) {
-        long long item = 0;
-        if (lane == 0) item = (long long)atomicAdd(work, 1ull);
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(work, 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nitems) break;
-        if (item < nlarge) {
-            const int r = roots[item];
+        int co = 0;  // the class: the last whose items start at or before
+        while (co + 1 < NS && istart[co + 1] <= item) ++co;
+        const int r0 = rstart[co * NLB], count = rstart[(co + 1) * NLB] - r0;
+        if (co == 0) {
+            const int r = roots[r0 + item - istart[0]];
             const int size = csize[r];
             if (lane == 0) {
                 ++ncomp;
@@ -613,16 +807,10 @@ k_herm_all(int n, double *x, double *v, const double *__restrict__ m,
                            H, a, jk, xp, vp, t, lev, st, nblk, nstep, pairs,
                            capped, maxblk);
         } else {
-            const long long kr = nlarge + 32 * (item - nlarge) + lane;
-            if (kr < nr) {
-                const int r = roots[kr];
-                const int size = csize[r];
-                ++ncomp;
-                maxsize = size > maxsize ? size : maxsize;
-                integrate_thread(size, cstart[r], n, x, v, m, off, idx, member,
-                                 H, a, jk, xp, vp, t, lev, st, nblk, nstep,
-                                 pairs, capped, maxblk);
-            }
+            integrate_class(class_size(co), roots + r0, count, next + co, lane, n,
+                            x, v, m, off, idx, cstart, member, H, a, jk, lev, loc,
+                            S, st, nblk, nstep, pairs, capped, ncomp, maxsize,
+                            maxblk);
         }
     }
 #pragma unroll
@@ -728,26 +916,23 @@ int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
     if (rc != P3T_OK) return rc;
     k_comp_fill<<<g, HB, 0, s>>>(n, off, c->hparent, c->hcstart, c->hcfill,
                                  c->hmember, c->st);
-    k_herm_init<<<g, HB, 0, s>>>(n, pos, vel, mass, off, idx, H, c->ha, c->hj,
-                                 c->ht, c->hlev, c->st);
-    // dense list of component roots, large then small, deepest first (the
-    // fill counters are free again and hold the component levels; the
-    // bucket counters sit at the start of hroot_off, then the two counts and
-    // the work counter)
+    k_herm_init<<<g, HB, 0, s>>>(n, pos, vel, mass, off, idx, c->hmember,
+                                 c->hcstart + n, H, c->ha, c->hj, c->ht,
+                                 c->hlev, c->st);
+    // component roots bucketed by depth and size, then packed into work
+    // items (the fill counters are free again and hold the component levels)
     P3T_CUDA_TRY(cudaMemsetAsync(c->hcfill, 0, sizeof(int) * (size_t)n, s));
-    int *bcount = (int *)c->hroot_off;
-    long long *nroot = c->hroot_off + NB;
-    unsigned long long *work = (unsigned long long *)(c->hroot_off + NB + 2);
-    P3T_CUDA_TRY(cudaMemsetAsync(c->hroot_off, 0, sizeof(long long) * (NB + 3), s));
+    int *bk = (int *)c->hbucket;
+    P3T_CUDA_TRY(cudaMemsetAsync(c->hbucket, 0, sizeof(long long) * P3T_HERM_BUCKET_LL, s));
     k_comp_level<<<g, HB, 0, s>>>(n, off, c->hparent, c->hlev, c->hcfill, c->st);
-    k_root_hist<<<g, HB, 0, s>>>(n, c->hparent, c->hcsize, c->hcfill, bcount);
-    k_root_scan<<<1, 32, 0, s>>>(bcount, nroot);
-    k_root_scatter<<<g, HB, 0, s>>>(n, c->hparent, c->hcsize, c->hcfill, bcount,
+    k_root_hist<<<g, HB, 0, s>>>(n, c->hparent, c->hcsize, c->hcfill, bk);
+    k_root_scan<<<1, 32, 0, s>>>(bk);
+    k_root_scatter<<<g, HB, 0, s>>>(n, c->hparent, c->hcsize, c->hcfill, bk,
                                     c->hroots);
-    // every component, longest first, from one dynamically shared list
-    k_herm_all<<<c->sms * 4, HB, 0, s>>>(
-        n, pos, vel, mass, off, idx, c->hroots, nroot, c->hcsize, c->hcstart,
-        c->hmember, H, c->ha, c->hj, c->hxp, c->hvp, c->ht, c->hlev, work,
+    // every component, deepest first, from one dynamically shared list
+    k_herm_pack<<<c->sms * (32 / HW) * 4, HW * 32, 0, s>>>(
+        n, pos, vel, mass, off, idx, c->hroots, bk, c->hcsize, c->hcstart,
+        c->hmember, H, c->ha, c->hj, c->hxp, c->hvp, c->ht, c->hlev, c->hloc,
         c->st);
     k_drift_isolated<<<g, HB, 0, s>>>(n, pos, vel, off, hp->dt_soft);
     p3t_count_launches(12);  // the scan counts its own

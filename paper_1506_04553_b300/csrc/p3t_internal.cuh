@@ -24,6 +24,10 @@
 
 #define P3T_MAX_LEVEL 21
 #define P3T_WARP 32
+// Hard step: components are ordered in 32 level buckets x 33 size classes;
+// the bucket scratch holds four int arrays of that length and a counter.
+#define P3T_HERM_BUCKETS (32 * 33)
+#define P3T_HERM_BUCKET_LL (2 * P3T_HERM_BUCKETS + 8)
 
 typedef unsigned long long u64;
 
@@ -123,9 +127,10 @@ struct p3t_ctx {
     int64_t cap_cadj;
     // energy scratch
     double *red_part;
-    // hard step (Hermite) scratch, per particle
-    int *hparent, *hcsize, *hcfill, *hmember, *hlev, *hroots;
-    long long *hcstart, *ht, *hroot_off;
+    // hard step (Hermite) scratch, per particle; hbucket is the fixed-size
+    // scratch of the component ordering (P3T_HERM_BUCKET_LL long longs)
+    int *hparent, *hcsize, *hcfill, *hmember, *hlev, *hroots, *hloc;
+    long long *hcstart, *ht, *hbucket;
     double *ha, *hj, *hxp, *hvp;
     int64_t cap_herm;
     // clusters (one for a plain build)

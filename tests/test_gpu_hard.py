@@ -51,6 +51,22 @@ def test_hard_force_bitwise(cuda):
     assert np.array_equal(j_g.cpu().numpy().T, j_o)
 
 
+def _clumps(seed):
+    """Separated clumps of 2..40 particles, some fully connected (rows up to
+    39 long), some split into smaller components: every packing size, rows
+    longer than the packed limit, and components of more than 32."""
+    rng = np.random.default_rng(seed)
+    sizes = np.concatenate([np.arange(2, 33), np.arange(2, 33), [33, 40]])
+    pos, vel = [], []
+    for c, s in enumerate(sizes):
+        scale = rng.uniform(0.003, 0.02)
+        pos.append(rng.normal(size=(s, 3)) * scale + [c * 1.0, 0.0, 0.0])
+        vel.append(rng.normal(size=(s, 3)) * 0.05)
+    pos, vel = np.concatenate(pos), np.concatenate(vel)
+    n = pos.shape[0]
+    return pos, vel, rng.uniform(0.5, 1.5, n) / n
+
+
 CASES = {
     # Plummer N = 8192 with a wide neighbour sphere: mostly small components
     "plummer8192": lambda: (*_plummer(8192, 3), dict(r_cut=0.02, h=0.025,
@@ -58,6 +74,8 @@ CASES = {
     # dense Gaussian clump: large components, deep block levels
     "gauss_dense": lambda: (*_gauss(2000, 4, 0.03), dict(r_cut=0.01, h=0.0125,
                                                           eps=1e-4, dt_soft=1 / 128)),
+    # clumps of every size up to 40: packed warps of each width, long rows
+    "clumps": lambda: (*_clumps(12), dict(r_cut=0.04, h=0.05, eps=1e-4, dt_soft=1 / 128)),
 }
 
 
