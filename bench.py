@@ -516,10 +516,12 @@ def run_ours(args, world, rank, local):
         hidx = torch.empty((cap,), dtype=torch.int32).pin_memory()
         nnz_last = [0]
 
-        # the step's compute replays two captured graphs: kick + drift, then
-        # build + force + neighbour lists + kick; the positions are final
-        # after the drift, so their download runs on a side stream while the
-        # tree is built and the force evaluated
+        # the step's compute replays three captured graphs: kick + drift;
+        # build + force + kick; neighbour lists.  The positions are final
+        # after the drift and the velocities after the second kick (the
+        # neighbour lists need only the tree), so their downloads run on a
+        # side stream while the tree is built and the force evaluated, and
+        # while the neighbour lists are made
         ctx.set_params(P.Params(theta=THETA, r_out=R_OUT, gamma=GAMMA,
                                 eps=4.0 / n, h=R_OUT, G=1.0, n_leaf=N_LEAF,
                                 n_group=N_GROUP, flags=P.FLAG_NO_SYNC))
@@ -533,20 +535,25 @@ def run_ours(args, world, rank, local):
         def part2():
             ctx.build_tree(pos, mass)
             ctx.long_force(acc, check=False)
-            ctx.neighbours_into(off, idx, sync=False)
             P.kick(vel, acc, 0.5 * DT)
+
+        def part3():
+            ctx.neighbours_into(off, idx, sync=False)
 
         side.wait_stream(stream)
         with torch.cuda.stream(side):
             part1()
             part2()
+            part3()
         stream.wait_stream(side)
-        g1, g2 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        g1, g2, g3 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
         with torch.cuda.graph(g1):
             part1()
         with torch.cuda.graph(g2):
             part2()
-        drifted = torch.cuda.Event()
+        with torch.cuda.graph(g3):
+            part3()
+        drifted, kicked = torch.cuda.Event(), torch.cuda.Event()
 
         def e2e_step():
             pos.copy_(hp, non_blocking=True)
@@ -558,9 +565,13 @@ def run_ours(args, world, rank, local):
             with torch.cuda.stream(copy_s):
                 hp.copy_(pos, non_blocking=True)
             g2.replay()
-            hv.copy_(vel, non_blocking=True)
+            kicked.record(stream)
+            copy_s.wait_event(kicked)
+            with torch.cuda.stream(copy_s):
+                hv.copy_(vel, non_blocking=True)
+            g3.replay()
             hoff.copy_(off, non_blocking=True)
-            stream.wait_stream(copy_s)  # the next upload reads hp
+            stream.wait_stream(copy_s)  # the next upload reads hp and hv
             stream.synchronize()
             nnz = int(hoff[n])
             hidx[:nnz].copy_(idx[:nnz], non_blocking=True)

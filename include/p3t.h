@@ -193,7 +193,9 @@ typedef struct p3t_hermite_params {
     double eta;      /* accuracy parameter of Eq. timestep:0 (Table 1: 0.1);
                         the first step uses eta / 10 (Eq. timestep:2) */
     double alpha;    /* a_0 = alpha G m_i / r_cut^2 (Eq. timestep:1; 0.1) */
-    double dt_soft;  /* the soft step: the hard part runs over [0, dt_soft] */
+    double dt_soft;  /* the soft step: the hard part runs over [0, dt_soft];
+                        at most 1e300, and dt_soft 2^-(p + kmax) must be a
+                        normal double */
     int32_t log2_soft_over_max; /* p: dt_max = dt_soft 2^-p (Table 1: 2) */
     int32_t kmax;    /* finest level: steps down to dt_max 2^-kmax (1..58-p) */
 } p3t_hermite_params;
@@ -207,7 +209,8 @@ typedef struct p3t_hermite_params {
  *   - time in integer ticks of dt_max 2^-kmax; a particle at level k steps
  *     dt_max 2^-k and its time is a multiple of its step;
  *   - first levels from Eq. timestep:2 (eta / 10), later from
- *     Eq. timestep:0 with a^(2), a^(3) from the Hermite interpolation; a
+ *     Eq. timestep:0 with a^(2), a^(3) from the Hermite interpolation, both
+ *     tested in squares (dt^2 den <= eta^2 num: no division); a
  *     step may at most double and is halved until the current time is a
  *     multiple of it;
  *   - each block step predicts positions and velocities to the next time

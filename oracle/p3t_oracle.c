@@ -1243,6 +1243,8 @@ typedef struct {
     double iomgrc; /* 1 / ((1 - gamma) r_cut) */
     double a0c;    /* alpha G / r_cut^2: a_0 = a0c m_i (Eq. timestep:1) */
     double c6, c24, c120;  /* 1/6, 1/24, 1/120 */
+    double eta2;   /* eta^2 (later steps) */
+    double eta_s2; /* eta_s^2 (first steps) */
 } orc_hard_par;
 
 static orc_hard_par orc_hard_par_make(double G, double eps, double r_cut,
@@ -1318,16 +1320,22 @@ void orc_hard_force(int64_t n, const double *x, const double *v,
         orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
 }
 
-/* Block level for a step of at most dt_crit: the smallest k in [kmin, kmax]
- * with dt_max 2^-k <= dt_crit (kmax when none is). */
-static int orc_level(double dt_crit, double dt_max, int kmin, int kmax)
+/* Block level for a step dt of at most eta sqrt(num / den) (Eq. timestep:0
+ * and :2), tested in squares so that it needs neither a division nor the
+ * outer square root: dt^2 den <= eta^2 num with e = eta^2 num and
+ * dm2 = dt_max^2.  The smallest k in [kmin, kmax] with
+ * (dt_max 2^-k)^2 den <= e (kmax when none is); *capped is set when even
+ * kmax fails. */
+static int orc_level(double den, double e, double dm2, int kmin, int kmax,
+                     int *capped)
 {
     int k = kmin;
-    double dt = ldexp(dt_max, -k);
-    while (k < kmax && dt > dt_crit) {
+    double q = ldexp(dm2, -2 * k);
+    while (k < kmax && q * den > e) {
         ++k;
-        dt = dt * 0.5;
+        q = q * 0.25;
     }
+    *capped = k == kmax && q * den > e;
     return k;
 }
 
@@ -1338,7 +1346,8 @@ static int orc_level(double dt_crit, double dt_max, int kmin, int kmax)
  * isolated and drift, x <- x + dt_soft v (the fifth step of Sect. 2.2).
  *
  * Divisions are few: 1/s per pair, 1/h per correction, and constants
- * (1/r_cut, 1/(1 - gamma), alpha G / r_cut^2, 1/6, 1/24, 1/120) formed once.
+ * (1/r_cut, 1/(1 - gamma), alpha G / r_cut^2, 1/6, 1/24, 1/120) formed once;
+ * the timestep criteria are tested in squares (orc_level).
  * Time is counted in ticks of dt_max 2^-kmax, dt_max = dt_soft 2^-p.  A
  * particle at level k steps dt_max 2^-k; its time is always a multiple of
  * its step.  First step: Eq. timestep:2 with eta_s = eta / 10; later steps:
@@ -1362,11 +1371,15 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
                 double dt_soft, int p, int kmax, int64_t *stats)
 {
     if (n < 0 || p < 0 || kmax < 0 || p + kmax > 60) return -1;
-    const orc_hard_par P = orc_hard_par_make(G, eps, r_cut, gamma, alpha);
+    orc_hard_par P = orc_hard_par_make(G, eps, r_cut, gamma, alpha);
     const double dt_max = ldexp(dt_soft, -p);
     const double tick = ldexp(dt_max, -kmax);
     const int64_t T = (int64_t)1 << (p + kmax);
     const double eta_s = eta / 10.0;
+    const double dm2 = dt_max * dt_max;
+    int capped = 0;
+    P.eta2 = eta * eta;
+    P.eta_s2 = eta_s * eta_s;
     int64_t st[4] = {0, 0, 0, 0};
     double *a = malloc(3 * n * sizeof(double) + 1);
     double *jk = malloc(3 * n * sizeof(double) + 1);
@@ -1385,13 +1398,12 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
         if (off[i + 1] == off[i]) continue;
         orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
         st[2] += off[i + 1] - off[i];
+        /* Eq. timestep:2: dt^2 |j|^2 <= eta_s^2 (|a|^2 + a0^2) */
         double a0 = P.a0c * m[i];
         double jj = orc_dot3(jk + 3 * i, jk + 3 * i);
-        double crit = INFINITY;
-        if (jj > 0.0)
-            crit = eta_s * sqrt((orc_dot3(a + 3 * i, a + 3 * i) + a0 * a0) / jj);
-        lev[i] = orc_level(crit, dt_max, 0, kmax);
-        if (lev[i] == kmax && ldexp(dt_max, -kmax) > crit) ++st[3];
+        double e = P.eta_s2 * (orc_dot3(a + 3 * i, a + 3 * i) + a0 * a0);
+        lev[i] = orc_level(jj, e, dm2, 0, kmax, &capped);
+        st[3] += capped;
     }
     for (;;) {
         int64_t tn = T;
@@ -1443,16 +1455,17 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
             }
             t[i] = tn;
             if (tn == T) continue;
-            /* Eq. timestep:0, with sqrt(A) sqrt(B) taken as sqrt(A B) */
+            /* Eq. timestep:0, with sqrt(A) sqrt(B) taken as sqrt(A B):
+             * dt^2 (sqrt(|a|^2 |a3|^2) + |a2|^2)
+             *     <= eta^2 (sqrt((|a|^2 + a0^2) |a2|^2) + |j|^2) */
             double a0 = P.a0c * m[i];
             double aa = orc_dot3(a1, a1);
             double a2sq = orc_dot3(a2e, a2e);
             double num = sqrt((aa + a0 * a0) * a2sq) + orc_dot3(j1, j1);
             double den = sqrt(aa * orc_dot3(a3, a3)) + a2sq;
-            double crit = den > 0.0 ? eta * sqrt(num / den) : INFINITY;
             int kmin = lev[i] > 0 ? lev[i] - 1 : 0;
-            int k = orc_level(crit, dt_max, kmin, kmax);
-            if (k == kmax && ldexp(dt_max, -kmax) > crit) ++st[3];
+            int k = orc_level(den, P.eta2 * num, dm2, kmin, kmax, &capped);
+            st[3] += capped;
             while (tn % ((int64_t)1 << (kmax - k)) != 0) ++k;
             lev[i] = k;
         }

@@ -1,5 +1,6 @@
 // C ABI of libp3t: context, memory management and the entry points declared
 // in include/p3t.h.
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -510,6 +511,7 @@ int ensure_hermite(p3t_ctx *c, int64_t n)
         P3T_TRY(grow(c->hj, d, 3 * cap, sizeof(double)));
         P3T_TRY(grow(c->hxp, d, 3 * cap, sizeof(double)));
         P3T_TRY(grow(c->hvp, d, 3 * cap, sizeof(double)));
+        P3T_TRY(p3t_hard_setup(c));
         c->cap_herm = cap;
     }
     const int64_t nb = p3t_scan_blocks(n) + 2;
@@ -535,6 +537,11 @@ int p3t_hard_step(p3t_ctx *c, int64_t n, double *pos, double *vel,
         !isfinite(hp->alpha) || !(hp->dt_soft > 0.0) || !isfinite(hp->dt_soft) ||
         hp->log2_soft_over_max < 0 || hp->log2_soft_over_max > 30 ||
         hp->kmax < 1 || hp->log2_soft_over_max + hp->kmax > 58)
+        return P3T_ERR_INVALID;
+    // the tick dt_soft 2^-(p + kmax) and 1 / dt_max stay normal, so that
+    // steps and their inverses are exact power-of-two scalings
+    if (!(ldexp(hp->dt_soft, -(hp->log2_soft_over_max + hp->kmax)) >= DBL_MIN) ||
+        !(hp->dt_soft <= 1e300))
         return P3T_ERR_INVALID;
     if (n == 0) return P3T_OK;
     P3T_TRY(ensure_hermite(c, n));

@@ -12,8 +12,11 @@
 // All of it is FP64 with one rounding per operation (explicit __d*_rn
 // intrinsics, no contraction), in a fixed order, so the results do not
 // depend on the compiler's choices.  Divisions and square roots are costly
-// in FP64 and few: 1/s per pair, 1/h per correction, and constants (1/r_cut,
-// 1/(1 - gamma), alpha G / r_cut^2, 1/6, 1/24, 1/120) formed once.
+// in FP64 (about 600 cycles of latency each on B300, ten times an add) and
+// few: 1/s per pair; 1/h is the exact scaling 2^k / dt_max; the timestep
+// criteria are tested in squares; constants
+// (1/r_cut, 1/(1 - gamma), alpha G / r_cut^2, 1/6, 1/24, 1/120, 1/dt_max)
+// are formed once.
 //
 // Integration.  Neighbour rows are symmetric (the neighbour predicate is),
 // and a particle never comes within r_cut of one outside its row during
@@ -55,6 +58,17 @@ __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a,
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
+
+// x 2^n: the exponent field moved when x and the result are normal (exact,
+// so equal to ldexp), ldexp otherwise.
+__device__ __forceinline__ double scale2(double x, int n)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e > 0 && e < 0x7ff && e + n > 0 && e + n < 0x7ff)
+        return __longlong_as_double(b + ((long long)n << 52));
+    return ldexp(x, n);
+}
 
 __device__ __forceinline__ double dot3(double ax, double ay, double az,
                                        double bx, double by, double bz)
@@ -292,32 +306,38 @@ k_comp_fill(int n, const long long *__restrict__ off, int *parent,
 // result depends on it.
 //
 // Each class is a queue.  A component of more than 32 particles is one work
-// item (one warp, lanes over its members).  A class of s <= 32 particles is
-// served by ceil(count / (floor(32 / s) R)) work items: warps that pack
-// floor(32 / s) components side by side, one lane per particle, and take the
-// next component of the queue into a slot as soon as the slot's component
-// is done, so that each slot runs about R components back to back.
-#ifndef P3T_HERM_REFILL
-#define P3T_HERM_REFILL 1
+// item (one warp, lanes over its members).  A class of s <= 32 particles
+// has one work item per floor(32 / s) components: a warp that packs that
+// many components side by side, one lane per particle, and takes the next
+// component of the queue into a slot as soon as the slot's component is
+// done (so a warp stays with a class while its queue lasts, and items that
+// find the queue empty end at once).  The first item of every class is
+// handed out before all others, so that each class's deepest components
+// start at once; the rest follow class by class.
+//
+// FP64 on B300: one warp per SM sub-partition already keeps its FP64 unit
+// busy (a dependent add takes ~63 cycles, about the unit's time for one
+// warp instruction), so more warps only share the unit and slow the
+// deepest components, whose block steps are a serial chain.  k_herm_pack
+// therefore runs HW = 4 warps per block and HBS blocks per SM, held there by
+// padding the block's shared memory.
+constexpr int HW = 4;
+#ifndef P3T_HERM_BLOCKS_PER_SM
+#define P3T_HERM_BLOCKS_PER_SM 1
 #endif
-constexpr int REFILL = P3T_HERM_REFILL;
-// k_herm_pack: warps per block and blocks per SM in the grid.  Small blocks
-// free a finished warp's registers at once instead of holding them until the
-// slowest warp of the block is done.
-#ifndef P3T_HERM_WARPS
-#define P3T_HERM_WARPS 8
-#endif
-constexpr int HW = P3T_HERM_WARPS;
+constexpr int HBS = P3T_HERM_BLOCKS_PER_SM;
 constexpr int NLB = 32;  // level buckets
 constexpr int NS = 33;   // size classes: more than 32, then s = 32 .. 1
 constexpr int NB = NLB * NS;
 static_assert(NB == P3T_HERM_BUCKETS, "bucket scratch");
 static_assert(NB % 32 == 0, "one-warp scan");
-// bucket scratch (ints): counts, root starts (NB + 1), fill counters, item
-// starts per class (NS + 1), queue heads per class, then a 64-bit counter
+// bucket scratch (ints): counts, root starts (NB + 1), fill counters, starts
+// of the later items per class (NS + 1), queue heads per class, the classes
+// with a first item and their number (NS + 1), then a 64-bit counter
 constexpr int BK_COUNT = 0, BK_RSTART = NB, BK_RFILL = 2 * NB + 1,
               BK_ISTART = 3 * NB + 1, BK_NEXT = 3 * NB + NS + 2,
-              BK_WORK = (3 * NB + 2 * NS + 2 + 1) & ~1;
+              BK_FIRST = 3 * NB + 2 * NS + 2,
+              BK_WORK = (3 * NB + 3 * NS + 3 + 1) & ~1;
 static_assert(BK_WORK + 2 <= 2 * P3T_HERM_BUCKET_LL, "bucket scratch size");
 
 __device__ __forceinline__ int class_size(int co) { return co == 0 ? 0 : NS - co; }
@@ -359,8 +379,8 @@ k_root_hist(int n, const int *__restrict__ parent, const int *__restrict__ csize
         if (h[b]) atomicAdd(bk + BK_COUNT + b, h[b]);
 }
 
-// counts -> root starts and fill counters (exclusive); then the work items
-// of each class and their starts
+// counts -> root starts and fill counters (exclusive); then the work items:
+// the first item of each nonempty class, then the later ones per class
 __global__ void k_root_scan(int *bk)
 {
     constexpr int PER = NB / 32;
@@ -379,19 +399,18 @@ __global__ void k_root_scan(int *bk)
     if (lane == 31) rstart[NB] = er;
     __syncwarp();
     if (lane == 0) {
-        int items = 0;
+        int *first = bk + BK_FIRST;
+        int later = 0, nfirst = 0;
         for (int co = 0; co < NS; ++co) {
-            istart[co] = items;
+            istart[co] = later;
             const int count = rstart[(co + 1) * NLB] - rstart[co * NLB];
             const int s = class_size(co);
-            if (s == 0) {
-                items += count;
-            } else if (count > 0) {
-                const int per = (32 / s) * REFILL;
-                items += (count + per - 1) / per;
-            }
+            if (count == 0) continue;
+            first[nfirst++] = co;
+            later += (s == 0 ? count : (count + 32 / s - 1) / (32 / s)) - 1;
         }
-        istart[NS] = items;
+        istart[NS] = later;
+        first[NS] = nfirst;
     }
 }
 
@@ -409,23 +428,30 @@ k_root_scatter(int n, const int *__restrict__ parent, const int *__restrict__ cs
 
 struct HermPar {
     HardPar f;
-    double eta, eta_s, dt_soft, dt_max, tick;
+    double eta2, eta_s2;   // eta^2 (Eq. timestep:0), eta_s^2 (Eq. timestep:2)
+    double dt_soft, dt_max, tick;
+    double dm2;            // dt_max^2
+    double idt_max;        // 1 / dt_max: 1 / h = 2^k / dt_max exactly
     double a0c;            // alpha G / r_cut^2: a_0 = a0c m_i
     double c6, c24, c120;  // 1/6, 1/24, 1/120
     long long T;  // dt_soft in ticks
     int kmax;
 };
 
-// smallest k in [kmin, kmax] with dt_max 2^-k <= crit (kmax when none is)
-__device__ __forceinline__ int level_for(double crit, double dt_max, int kmin,
-                                         int kmax)
+// Level of a step dt of at most eta sqrt(num / den), tested in squares (no
+// division, no outer square root): dt^2 den <= e with e = eta^2 num.  The
+// smallest k in [kmin, kmax] with (dt_max 2^-k)^2 den <= e (kmax when none
+// is); capped counts a step for which even kmax fails.
+__device__ __forceinline__ int level_sq(double den, double e, const HermPar &H,
+                                        int kmin, long long &capped)
 {
     int k = kmin;
-    double dt = ldexp(dt_max, -k);
-    while (k < kmax && dt > crit) {
+    double q = scale2(H.dm2, -2 * k);
+    while (k < H.kmax && dmul(q, den) > e) {
         ++k;
-        dt = dmul(dt, 0.5);
+        q = dmul(q, 0.25);
     }
+    if (k == H.kmax && dmul(q, den) > e) ++capped;
     return k;
 }
 
@@ -449,17 +475,12 @@ k_herm_init(int n, const double *__restrict__ x, const double *__restrict__ v,
         hard_one(i, n, x, v, m, off, idx, H.f, ai, ji, &pairs);
         store3(a, n, i, ai);
         store3(jk, n, i, ji);
+        // Eq. timestep:2: dt^2 |j|^2 <= eta_s^2 (|a|^2 + a0^2)
         const double a0 = dmul(H.a0c, m[i]);
         const double jj = dot3(ji[0], ji[1], ji[2], ji[0], ji[1], ji[2]);
-        double crit = INFINITY;
-        if (jj > 0.0)
-            crit = dmul(H.eta_s,
-                        dsqrt(ddiv(dadd(dot3(ai[0], ai[1], ai[2], ai[0], ai[1], ai[2]),
-                                        dmul(a0, a0)),
-                                   jj)));
-        const int k = level_for(crit, H.dt_max, 0, H.kmax);
-        if (k == H.kmax && ldexp(H.dt_max, -H.kmax) > crit) ++capped;
-        lev[i] = k;
+        const double e = dmul(H.eta_s2, dadd(dot3(ai[0], ai[1], ai[2], ai[0], ai[1], ai[2]),
+                                             dmul(a0, a0)));
+        lev[i] = level_sq(jj, e, H, 0, capped);
     }
     if (pairs) atomicAdd((unsigned long long *)&st->herm[2], (unsigned long long)pairs);
     if (capped) atomicAdd((unsigned long long *)&st->herm[3], (unsigned long long)capped);
@@ -502,9 +523,11 @@ __device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3
                                             long long &t, int &lev,
                                             long long &capped)
 {
-    const long long step = 1LL << (H.kmax - lev);
-    const double h = dmul((double)step, H.tick);
-    const double ih = ddiv(1.0, h);
+    // h = 2^(kmax - lev) ticks = dt_max 2^-lev and 1/h = 2^lev / dt_max,
+    // both exact scalings (the parameter checks keep them normal), so they
+    // equal the rounded product and quotient
+    const double h = scale2(H.dt_max, -lev);
+    const double ih = scale2(H.idt_max, lev);
     const double ih2 = dmul(ih, ih), ih3 = dmul(ih2, ih);
     const double h2 = dmul(h, h), h3 = dmul(h2, h), h4 = dmul(h3, h),
                  h5 = dmul(h4, h);
@@ -528,7 +551,8 @@ __device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3
     }
     t = tn;
     if (tn == H.T) return;
-    // Eq. timestep:0, with sqrt(A) sqrt(B) taken as sqrt(A B)
+    // Eq. timestep:0, with sqrt(A) sqrt(B) taken as sqrt(A B), in squares:
+    // dt^2 (sqrt(|a|^2 |a3|^2) + |a2|^2) <= eta^2 (sqrt((|a|^2 + a0^2) |a2|^2) + |j|^2)
     const double a0 = dmul(H.a0c, mi);
     const double aa = dot3(a1[0], a1[1], a1[2], a1[0], a1[1], a1[2]);
     const double a2sq = dot3(a2e[0], a2e[1], a2e[2], a2e[0], a2e[1], a2e[2]);
@@ -536,10 +560,8 @@ __device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3
                             dot3(j1[0], j1[1], j1[2], j1[0], j1[1], j1[2]));
     const double den = dadd(dsqrt(dmul(aa, dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]))),
                             a2sq);
-    const double crit = den > 0.0 ? dmul(H.eta, dsqrt(ddiv(num, den))) : INFINITY;
     const int kmin = lev > 0 ? lev - 1 : 0;
-    int k = level_for(crit, H.dt_max, kmin, H.kmax);
-    if (k == H.kmax && ldexp(H.dt_max, -H.kmax) > crit) ++capped;
+    int k = level_sq(den, dmul(H.eta2, num), H, kmin, capped);
     while (tn % (1LL << (H.kmax - k)) != 0) ++k;
     lev = k;
 }
@@ -782,10 +804,10 @@ k_herm_pack(int n, double *x, double *v, const double *__restrict__ m,
     if (st->error) return;
     const int lane = threadIdx.x & 31;
     LaneSmem &S = smem[threadIdx.x >> 5];
-    const int *rstart = bk + BK_RSTART, *istart = bk + BK_ISTART;
+    const int *rstart = bk + BK_RSTART, *istart = bk + BK_ISTART, *first = bk + BK_FIRST;
     unsigned *next = (unsigned *)(bk + BK_NEXT);
     unsigned long long *work = (unsigned long long *)(bk + BK_WORK);
-    const int nitems = istart[NS];
+    const int nfirst = first[NS], nitems = nfirst + istart[NS];
     long long nblk = 0, nstep = 0, pairs = 0, capped = 0, ncomp = 0, maxblk = 0;
     int maxsize = 0;
     for (;;) {
@@ -793,11 +815,17 @@ k_herm_pack(int n, double *x, double *v, const double *__restrict__ m,
         if (lane == 0) item = (int)atomicAdd(work, 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nitems) break;
-        int co = 0;  // the class: the last whose items start at or before
-        while (co + 1 < NS && istart[co + 1] <= item) ++co;
+        int co = 0, k = 0;  // the class and the item's rank in it
+        if (item < nfirst) {
+            co = first[item];
+        } else {
+            const int later = item - nfirst;  // the last class whose later items start at or before
+            while (co + 1 < NS && istart[co + 1] <= later) ++co;
+            k = 1 + later - istart[co];
+        }
         const int r0 = rstart[co * NLB], count = rstart[(co + 1) * NLB] - r0;
         if (co == 0) {
-            const int r = roots[r0 + item - istart[0]];
+            const int r = roots[r0 + k];
             const int size = csize[r];
             if (lane == 0) {
                 ++ncomp;
@@ -864,6 +892,33 @@ int grid_for(long long n, int sms)
 
 }  // namespace
 
+// Dynamic shared memory that holds k_herm_pack at HBS blocks per SM: the
+// SM's shared memory split HBS ways, less the per-block reserve and the
+// static part, lowered until the occupancy calculator agrees.  Host only;
+// called where the hard-step scratch is allocated (never under capture).
+int p3t_hard_setup(p3t_ctx *c)
+{
+    int dev = 0, per_sm = 0, reserved = 0, optin = 0;
+    P3T_CUDA_TRY(cudaGetDevice(&dev));
+    P3T_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    P3T_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    P3T_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int fixed = (int)sizeof(LaneSmem) * HW;
+    int pad = per_sm / HBS - reserved - fixed;
+    if (pad > optin - fixed) pad = optin - fixed;
+    if (pad < 0) pad = 0;
+    P3T_CUDA_TRY(cudaFuncSetAttribute(k_herm_pack,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, pad));
+    for (; pad > 0; pad -= 1024 < pad ? 1024 : pad) {
+        int nb = 0;
+        P3T_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_herm_pack,
+                                                                   HW * 32, pad));
+        if (nb >= HBS) break;
+    }
+    c->herm_pad = pad;
+    return P3T_OK;
+}
+
 extern "C" int p3t_hard_force(int64_t n, const double *pos, const double *vel,
                               const double *mass, const int64_t *offsets,
                               const int32_t *idx, double G, double eps,
@@ -894,8 +949,9 @@ int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
 {
     HermPar H;
     H.f = hard_par(c->p.G, c->p.eps, c->p.r_out, c->p.gamma);
-    H.eta = hp->eta;
-    H.eta_s = hp->eta / 10.0;
+    const double eta_s = hp->eta / 10.0;
+    H.eta2 = hp->eta * hp->eta;
+    H.eta_s2 = eta_s * eta_s;
     H.a0c = hp->alpha * c->p.G / (c->p.r_out * c->p.r_out);
     H.c6 = 1.0 / 6.0;
     H.c24 = 1.0 / 24.0;
@@ -903,6 +959,8 @@ int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
     H.dt_soft = hp->dt_soft;
     H.dt_max = ldexp(hp->dt_soft, -hp->log2_soft_over_max);
     H.tick = ldexp(H.dt_max, -hp->kmax);
+    H.dm2 = H.dt_max * H.dt_max;
+    H.idt_max = 1.0 / H.dt_max;
     H.T = 1LL << (hp->log2_soft_over_max + hp->kmax);
     H.kmax = hp->kmax;
     const int g = grid_for(n, c->sms);
@@ -930,7 +988,7 @@ int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
     k_root_scatter<<<g, HB, 0, s>>>(n, c->hparent, c->hcsize, c->hcfill, bk,
                                     c->hroots);
     // every component, deepest first, from one dynamically shared list
-    k_herm_pack<<<c->sms * (32 / HW) * 4, HW * 32, 0, s>>>(
+    k_herm_pack<<<c->sms * HBS, HW * 32, c->herm_pad, s>>>(
         n, pos, vel, mass, off, idx, c->hroots, bk, c->hcsize, c->hcstart,
         c->hmember, H, c->ha, c->hj, c->hxp, c->hvp, c->ht, c->hlev, c->hloc,
         c->st);

@@ -133,6 +133,7 @@ struct p3t_ctx {
     long long *hcstart, *ht, *hbucket;
     double *ha, *hj, *hxp, *hvp;
     int64_t cap_herm;
+    int herm_pad;            // dynamic shared memory of the Hermite kernel
     // clusters (one for a plain build)
     int nclus, cap_clus;
     int ensemble;            // layout fixed by p3t_set_ensemble
@@ -231,6 +232,7 @@ __device__ __forceinline__ bool mac_accept(float d2, float l, float theta2,
 int p3t_sort_keys(p3t_ctx *c, int n, cudaStream_t s);          // p3t_sort.cu
 int p3t_scan_ll(p3t_ctx *c, const int *in, long long *out, int n,
                 cudaStream_t s);                                 // p3t_misc.cu
+int p3t_hard_setup(p3t_ctx *c);                                 // p3t_hard.cu
 int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
                      const double *mass);                       // p3t_tree.cu
 int p3t_sort_cluster_passes(p3t_ctx *c, int n, cudaStream_t s); // p3t_sort.cu

@@ -156,7 +156,8 @@ def test_hard_part_argument_checks(cuda):
     ctx = Context(Params(r_out=0.01))
     for bad in (dict(eta=0.0), dict(eta=float("nan")), dict(alpha=-1.0),
                 dict(dt_soft=0.0), dict(kmax=0), dict(log2_soft_over_max=-1),
-                dict(log2_soft_over_max=30, kmax=40)):
+                dict(log2_soft_over_max=30, kmax=40), dict(dt_soft=1e-300),
+                dict(dt_soft=1e301)):
         with pytest.raises(P3TError):
             ctx.hard_step(*args, HermiteParams(**{"dt_soft": 0.01, **bad}))
     with pytest.raises(P3TError):
