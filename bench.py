@@ -705,7 +705,11 @@ def run_p3t_step(args, dev):
             "largest_component": st["herm_max_component"],
             "hard_particle_steps": st["herm_particle_steps"],
             "hard_pairs": st["herm_pairs"], "steps_at_kmax": st["herm_capped"],
-            "max_block_steps": st["herm_max_block_steps"]}
+            "max_block_steps": st["herm_max_block_steps"],
+            "fp64_measured": dict(P.fp64_peaks(),
+                                  note="p3t_fp64_peaks: FP64 FMA/s over all SMs; "
+                                       "latency (SM cycles) of one dependent add, "
+                                       "division, square root in one warp")}
 
 
 def run_king(args, dev):

@@ -362,6 +362,18 @@ int64_t p3t_launch_count(void);
  * second.  Any pointer may be NULL.  Errors: P3T_ERR_CUDA. */
 int p3t_alu_peaks(double *fma_flops, double *fma2_flops, double *rsqrt_ops);
 
+/* FP64 figures of the current device that set the design of the hard
+ * part's Hermite kernel (p3t_hard_step): dfma_ops, FP64 FMAs per second
+ * over every SM (independent register chains, CUDA-event timed after a
+ * warm-up launch, about 10 ms); add_cycles, div_cycles, sqrt_cycles, the
+ * latency in SM clock cycles of one dependent IEEE add, division and square
+ * root (correctly rounded, as the hard part uses them) in one warp, timed
+ * with the SM clock over 4096 operations.  Private stream, synchronised;
+ * allocates and frees two small buffers.  Any pointer may be NULL.
+ * Errors: P3T_ERR_CUDA. */
+int p3t_fp64_peaks(double *dfma_ops, double *add_cycles, double *div_cycles,
+                   double *sqrt_cycles);
+
 /* ---- inspection (tests and tools; each call synchronises and copies to
  * HOST buffers sized from p3t_get_stats) ---- */
 

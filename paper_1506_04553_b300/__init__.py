@@ -11,7 +11,7 @@ from __future__ import annotations
 
 _BINDING_NAMES = {"Params", "Context", "P3TError", "kick", "drift",
                   "library_path", "launch_count", "alu_peaks", "FLAG_NO_SYNC",
-                  "HermiteParams", "hard_force"}
+                  "HermiteParams", "hard_force", "fp64_peaks"}
 
 __all__ = sorted(_BINDING_NAMES) + ["ics", "binding"]
 

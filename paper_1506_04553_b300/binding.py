@@ -108,6 +108,7 @@ _sigs = {
     "p3t_autotune": [_vp, _i64, _vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp],
     "p3t_get_profile": [_vp, _vp, C.c_int],
     "p3t_alu_peaks": [_vp, _vp, _vp],
+    "p3t_fp64_peaks": [_vp, _vp, _vp, _vp],
     "p3t_hard_force": [_i64, _vp, _vp, _vp, _vp, _vp, C.c_double, C.c_double,
                        C.c_double, C.c_double, _vp, _vp, _vp],
     "p3t_hard_step": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -134,6 +135,15 @@ def alu_peaks() -> dict:
     _check(_lib.p3t_alu_peaks(*[C.byref(x) for x in v]), "p3t_alu_peaks")
     return {"fma_flops": v[0].value, "fma2_flops": v[1].value,
             "rsqrt_ops": v[2].value}
+
+
+def fp64_peaks() -> dict:
+    """Measured FP64 FMA/s and the latencies (SM cycles) of one dependent
+    add, division and square root on the current device (p3t_fp64_peaks)."""
+    v = [C.c_double() for _ in range(4)]
+    _check(_lib.p3t_fp64_peaks(*[C.byref(x) for x in v]), "p3t_fp64_peaks")
+    return {"dfma_ops": v[0].value, "add_cycles": v[1].value,
+            "div_cycles": v[2].value, "sqrt_cycles": v[3].value}
 
 
 def _check(code: int, where: str):

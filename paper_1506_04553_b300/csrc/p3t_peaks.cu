@@ -2,6 +2,8 @@
 // kernel's roofline next to the nominal FP32 peak (SMs x 128 lanes x 2 x
 // clock): register-only loops of independent FP32 FMA chains, scalar and
 // FP32x2, and of the MUFU reciprocal square root the force kernel uses.
+// Also the FP64 throughput and dependent-operation latencies that shape the
+// hard part's Hermite kernel.
 #include "p3t_internal.cuh"
 
 namespace {
@@ -64,7 +66,105 @@ int time_loop(float *out, int blocks, int iters, cudaStream_t s,
     return P3T_OK;
 }
 
+// FP64: MODE 0 independent DFMA chains on every SM (throughput); the
+// latency kernel runs one warp through dependent operations: 0 add, 1
+// division, 2 square root, timed with the SM clock.
+__global__ void __launch_bounds__(PB) k_dfma(double *out, int iters, double b, double c)
+{
+    double a[CH];
+#pragma unroll
+    for (int i = 0; i < CH; ++i) a[i] = 1.0 + 1e-3 * (threadIdx.x + i);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < CH; ++i) a[i] = __fma_rn(a[i], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < CH; ++i) s += a[i];
+    out[blockIdx.x * PB + threadIdx.x] = s;
+}
+
+template <int OP>
+__global__ void k_dlat(double *out, long long *cycles, int iters, double b)
+{
+    double x = 1.5 + 1e-9 * threadIdx.x;
+    const long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+        if (OP == 0) x = __dadd_rn(x, b);
+        if (OP == 1) x = __ddiv_rn(b, x);
+        if (OP == 2) x = __dsqrt_rn(x);
+    }
+    const long long t1 = clock64();
+    out[threadIdx.x] = x;
+    if (threadIdx.x == 0) *cycles = t1 - t0;
+}
+
+template <int OP>
+int time_latency(double *out, long long *cyc, double b, cudaStream_t s,
+                 double *per_op)
+{
+    constexpr int iters = 4096;
+    k_dlat<OP><<<1, 32, 0, s>>>(out, cyc, iters / 8, b);
+    k_dlat<OP><<<1, 32, 0, s>>>(out, cyc, iters, b);
+    long long h = 0;
+    P3T_CUDA_TRY(cudaMemcpyAsync(&h, cyc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    P3T_CUDA_TRY(cudaStreamSynchronize(s));
+    *per_op = (double)h / iters;
+    p3t_count_launches(2);
+    return P3T_OK;
+}
+
 }  // namespace
+
+// FP64 figures that set the hard part's design: DFMA/s over all SMs, and the
+// latency in SM cycles of one dependent add, division and square root.
+extern "C" int p3t_fp64_peaks(double *dfma_ops, double *add_cycles,
+                              double *div_cycles, double *sqrt_cycles)
+{
+    int dev = 0, sms = 0;
+    P3T_CUDA_TRY(cudaGetDevice(&dev));
+    P3T_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 4;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double *out = nullptr;
+    long long *cyc = nullptr;
+    int rc = P3T_OK;
+    double tp = 0.0, la = 0.0, ld = 0.0, ls = 0.0;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMalloc((void **)&out, sizeof(double) * (size_t)blocks * PB) != cudaSuccess ||
+        cudaMalloc((void **)&cyc, sizeof(long long)) != cudaSuccess)
+        rc = P3T_ERR_CUDA;
+    // about 10 ms at the B300's ~0.6 T DFMA/s
+    const int iters = 1024;
+    if (rc == P3T_OK) {
+        k_dfma<<<blocks, PB, 0, s>>>(out, iters / 8, 1.0000001, 1e-7);
+        if (cudaEventRecord(e0, s) != cudaSuccess) rc = P3T_ERR_CUDA;
+        k_dfma<<<blocks, PB, 0, s>>>(out, iters, 1.0000001, 1e-7);
+        p3t_count_launches(2);
+        float ms = 0.0f;
+        if (rc == P3T_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                             cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = P3T_ERR_CUDA;
+        if (rc == P3T_OK) tp = (double)blocks * PB * iters * CH / (ms * 1e-3);
+    }
+    if (rc == P3T_OK) rc = time_latency<0>(out, cyc, 1e-12, s, &la);
+    if (rc == P3T_OK) rc = time_latency<1>(out, cyc, 1.0, s, &ld);
+    if (rc == P3T_OK) rc = time_latency<2>(out, cyc, 0.0, s, &ls);
+    if (out) cudaFree(out);
+    if (cyc) cudaFree(cyc);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    if (rc != P3T_OK) return rc;
+    if (dfma_ops) *dfma_ops = tp;
+    if (add_cycles) *add_cycles = la;
+    if (div_cycles) *div_cycles = ld;
+    if (sqrt_cycles) *sqrt_cycles = ls;
+    return P3T_OK;
+}
 
 extern "C" int p3t_alu_peaks(double *fma_flops, double *fma2_flops,
                              double *rsqrt_ops)
