@@ -45,6 +45,9 @@ struct P3TDevState {
     unsigned int work;  // dynamic work counter
     int pad0;
     int level_start[P3T_MAX_LEVEL + 3];
+    int nleaf;          // leaves listed by the split (leaf_list)
+    int nint;           // split cells listed by the split (int_list)
+    int int_start[P3T_MAX_LEVEL + 2];  // int_list range of each level
     long long tot[3];   // list totals: pc, ppn, ppf
     long long int_pc;   // particle-cell interactions
     long long int_pp;   // particle-particle interactions
@@ -108,6 +111,7 @@ struct p3t_ctx {
     // cells
     int4 *node;
     int *parent;
+    int *leaf_list, *int_list;  // leaves; split cells grouped by level
     double *cM, *ccom, *cQ, *cbmin, *cbmax;
     float4 *wmin, *wmax, *cf0, *cf1, *cf2;
     // groups

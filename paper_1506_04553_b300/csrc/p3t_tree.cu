@@ -278,6 +278,9 @@ __global__ void k_tree_init(int nc, const long long *__restrict__ off,
     st->max_stack = 0;
     st->level_start[0] = 0;
     for (int L = 1; L < P3T_MAX_LEVEL + 3; ++L) st->level_start[L] = nc;
+    st->nleaf = 0;
+    st->nint = 0;
+    for (int L = 0; L < P3T_MAX_LEVEL + 2; ++L) st->int_start[L] = 0;
 }
 
 __device__ __forceinline__ int digit_at(u64 key, int L)
@@ -342,10 +345,12 @@ __device__ __forceinline__ void warp_scan_digits(const u64 *__restrict__ key,
     __syncwarp();
 }
 
-// Children of one cell (boundaries b[0..8]) appended to the cell arrays.
+// Children of one cell (boundaries b[0..8]) appended to the cell arrays;
+// children at the deepest level are never split and join the leaf list.
 __device__ __forceinline__ void emit_children(int c, int L, int cap,
                                               const int *b, int4 *node,
-                                              int *parent, P3TDevState *st)
+                                              int *parent, int *leaf_list,
+                                              P3TDevState *st)
 {
     int k = 0;
 #pragma unroll
@@ -362,6 +367,7 @@ __device__ __forceinline__ void emit_children(int c, int L, int cap,
         if (b[d + 1] > b[d]) {
             node[base + j] = make_int4(b[d], b[d + 1] - b[d], -1, (L + 1) << 8);
             parent[base + j] = c;
+            if (L + 1 >= P3T_MAX_LEVEL) leaf_list[atomicAdd(&st->nleaf, 1)] = base + j;
             ++j;
         }
     }
@@ -371,19 +377,39 @@ __device__ __forceinline__ void emit_children(int c, int L, int cap,
 
 constexpr int BIG_CELL = 2048;  // above: 32-ary searches; below: one scan
 
-// One warp per cell of level L that holds more than n_leaf particles.
+// Level L in two passes over its cells: one thread per cell files the
+// cells holding at most n_leaf particles in the leaf list and the others in
+// the list of split cells (one aggregated append per warp each); then one
+// warp per split cell finds the child boundaries.
 __global__ void __launch_bounds__(TB)
 k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
              int4 *__restrict__ node, int *__restrict__ parent,
+             int *__restrict__ leaf_list, int *__restrict__ int_list,
              P3TDevState *st)
 {
     __shared__ int sbuf[TB / 32][9];
     const int beg = st->level_start[L], end = st->level_start[L + 1];
     const bool stop = st->error != 0 || L >= P3T_MAX_LEVEL;
+    const unsigned full = 0xffffffffu, lt = lanemask_lt();
     const int lane = threadIdx.x & 31;
     const int wg = (blockIdx.x * TB + threadIdx.x) >> 5;
     const int nw = gridDim.x * (TB / 32);
     int *sb = sbuf[threadIdx.x >> 5];
+    for (int base = beg + 32 * wg; base < end && !stop; base += 32 * nw) {
+        const int cl = base + lane;
+        const int cnt = cl < end ? node[cl].y : -1;
+        const unsigned lm = __ballot_sync(full, cnt >= 0 && cnt <= n_leaf);
+        const unsigned sm = __ballot_sync(full, cnt > n_leaf);
+        int lb = 0, ib = 0;
+        if (lane == 0) {
+            if (lm) lb = atomicAdd(&st->nleaf, __popc(lm));
+            if (sm) ib = atomicAdd(&st->nint, __popc(sm));
+        }
+        lb = __shfl_sync(full, lb, 0);
+        ib = __shfl_sync(full, ib, 0);
+        if ((lm >> lane) & 1u) leaf_list[lb + __popc(lm & lt)] = cl;
+        if ((sm >> lane) & 1u) int_list[ib + __popc(sm & lt)] = cl;
+    }
     for (int c = beg + wg; c < end && !stop; c += nw) {
         const int4 nd = node[c];
         if (nd.y <= n_leaf) continue;
@@ -399,7 +425,7 @@ k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
             for (int d = 1; d < 8; ++d) b[d] = sb[d];
             __syncwarp();  // sb is rewritten by the next cell
         }
-        if (lane == 0) emit_children(c, L, cap, b, node, parent, st);
+        if (lane == 0) emit_children(c, L, cap, b, node, parent, leaf_list, st);
     }
     // the last block to finish closes the next level's range
     __syncthreads();
@@ -410,6 +436,7 @@ k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
             int nc = atomicAdd(&st->ncell, 0);
             if (nc > cap) nc = cap;
             st->level_start[L + 2] = nc;
+            st->int_start[L + 1] = atomicAdd(&st->nint, 0);
             if (nc > st->level_start[L + 1]) st->max_level = L + 1;
             st->blocks_done = 0;
             __threadfence();
@@ -442,11 +469,14 @@ __device__ __forceinline__ void write_records(
 }
 
 // LEAVES: every leaf of the tree in one launch (L unused); otherwise the
-// internal cells of level L, from their children.
+// internal cells of level L, from their children.  The cells come from the
+// lists the split made, so every thread has a cell of the right kind.
 template <bool LEAVES>
 __global__ void __launch_bounds__(TB)
 k_moments(int L, const double *__restrict__ xs, const double *__restrict__ ms,
-          int n, const int4 *__restrict__ node, double *__restrict__ cM,
+          int n, const int4 *__restrict__ node,
+          const int *__restrict__ leaf_list, const int *__restrict__ int_list,
+          double *__restrict__ cM,
           double *__restrict__ ccom, double *__restrict__ cQ,
           double *__restrict__ cbmin, double *__restrict__ cbmax,
           float4 *__restrict__ wmin, float4 *__restrict__ wmax,
@@ -454,66 +484,111 @@ k_moments(int L, const double *__restrict__ xs, const double *__restrict__ ms,
           float4 *__restrict__ cf2, const P3TDevState *st)
 {
     if (st->error) return;
-    const int beg = LEAVES ? 0 : st->level_start[L];
-    const int end = LEAVES ? st->ncell : st->level_start[L + 1];
-    for (int c = beg + blockIdx.x * TB + threadIdx.x; c < end;
-         c += gridDim.x * TB) {
+    const int beg = LEAVES ? 0 : st->int_start[L];
+    const int end = LEAVES ? st->nleaf : st->int_start[L + 1];
+    const int *list = LEAVES ? leaf_list : int_list;
+    for (int q = beg + blockIdx.x * TB + threadIdx.x; q < end;
+         q += gridDim.x * TB) {
+        const int c = list[q];
         int4 nd = node[c];
-        if (LEAVES != ((nd.w & 255) == 0)) continue;
         double M = 0.0, com[3] = {0, 0, 0}, Q[6] = {0, 0, 0, 0, 0, 0};
         double bmn[3] = {INFINITY, INFINITY, INFINITY};
         double bmx[3] = {-INFINITY, -INFINITY, -INFINITY};
         const int nch = nd.w & 255;
         if (nch == 0) {
-            // leaf: from its particles
-            for (int k = nd.x; k < nd.x + nd.y; ++k) {
-                double m = ms[k];
-                M += m;
+            // leaf: from its particles, in chunks of LCH whose loads are all
+            // issued before the sums that wait on them
+            constexpr int LCH = 8;
+            const int k0 = nd.x, k1 = nd.x + nd.y;
+            for (int kb = k0; kb < k1; kb += LCH) {
+                double pm[LCH], px[LCH], py[LCH], pz[LCH];
 #pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    double x = xs[(size_t)a * n + k];
-                    com[a] += m * x;
-                    bmn[a] = fmin(bmn[a], x);
-                    bmx[a] = fmax(bmx[a], x);
+                for (int u = 0; u < LCH; ++u) {
+                    const int k = kb + u < k1 ? kb + u : k0;
+                    pm[u] = ms[k];
+                    px[u] = xs[k];
+                    py[u] = xs[(size_t)n + k];
+                    pz[u] = xs[2 * (size_t)n + k];
+                }
+#pragma unroll
+                for (int u = 0; u < LCH; ++u) {
+                    if (kb + u >= k1) continue;
+                    M += pm[u];
+                    com[0] += pm[u] * px[u];
+                    com[1] += pm[u] * py[u];
+                    com[2] += pm[u] * pz[u];
+                    bmn[0] = fmin(bmn[0], px[u]);
+                    bmn[1] = fmin(bmn[1], py[u]);
+                    bmn[2] = fmin(bmn[2], pz[u]);
+                    bmx[0] = fmax(bmx[0], px[u]);
+                    bmx[1] = fmax(bmx[1], py[u]);
+                    bmx[2] = fmax(bmx[2], pz[u]);
                 }
             }
 #pragma unroll
             for (int a = 0; a < 3; ++a) com[a] /= M;
-            for (int k = nd.x; k < nd.x + nd.y; ++k) {
-                double m = ms[k];
-                double dx = xs[k] - com[0];
-                double dy = xs[(size_t)n + k] - com[1];
-                double dz = xs[2 * (size_t)n + k] - com[2];
-                double d2 = dx * dx + dy * dy + dz * dz;
-                Q[0] += m * (3.0 * dx * dx - d2);
-                Q[1] += m * (3.0 * dy * dy - d2);
-                Q[2] += m * (3.0 * dz * dz - d2);
-                Q[3] += m * (3.0 * dx * dy);
-                Q[4] += m * (3.0 * dx * dz);
-                Q[5] += m * (3.0 * dy * dz);
+            for (int kb = k0; kb < k1; kb += LCH) {
+                double pm[LCH], px[LCH], py[LCH], pz[LCH];
+#pragma unroll
+                for (int u = 0; u < LCH; ++u) {
+                    const int k = kb + u < k1 ? kb + u : k0;
+                    pm[u] = ms[k];
+                    px[u] = xs[k];
+                    py[u] = xs[(size_t)n + k];
+                    pz[u] = xs[2 * (size_t)n + k];
+                }
+#pragma unroll
+                for (int u = 0; u < LCH; ++u) {
+                    if (kb + u >= k1) continue;
+                    const double m = pm[u];
+                    const double dx = px[u] - com[0];
+                    const double dy = py[u] - com[1];
+                    const double dz = pz[u] - com[2];
+                    const double d2 = dx * dx + dy * dy + dz * dz;
+                    Q[0] += m * (3.0 * dx * dx - d2);
+                    Q[1] += m * (3.0 * dy * dy - d2);
+                    Q[2] += m * (3.0 * dz * dz - d2);
+                    Q[3] += m * (3.0 * dx * dy);
+                    Q[4] += m * (3.0 * dx * dz);
+                    Q[5] += m * (3.0 * dy * dz);
+                }
             }
         } else {
-            // internal: combine the children (parallel-axis shift)
-            for (int q = 0; q < nch; ++q) {
-                int ch = nd.z + q;
-                double m = cM[ch];
-                M += m;
+            // internal: combine the children (parallel-axis shift); the
+            // (at most 8) children's records are loaded before the sums
+            double cm[8], cx[8], cy[8], cz[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int ch = nd.z + (q < nch ? q : 0);
+                cm[q] = cM[ch];
+                cx[q] = ccom[3 * ch + 0];
+                cy[q] = ccom[3 * ch + 1];
+                cz[q] = ccom[3 * ch + 2];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    com[a] += m * ccom[3 * ch + a];
-                    bmn[a] = fmin(bmn[a], cbmin[3 * ch + a]);
+                    bmn[a] = fmin(bmn[a], cbmin[3 * ch + a]);  // repeats child 0: harmless
                     bmx[a] = fmax(bmx[a], cbmax[3 * ch + a]);
                 }
             }
 #pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q >= nch) continue;
+                M += cm[q];
+                com[0] += cm[q] * cx[q];
+                com[1] += cm[q] * cy[q];
+                com[2] += cm[q] * cz[q];
+            }
+#pragma unroll
             for (int a = 0; a < 3; ++a) com[a] /= M;
-            for (int q = 0; q < nch; ++q) {
-                int ch = nd.z + q;
-                double m = cM[ch];
-                double dx = ccom[3 * ch + 0] - com[0];
-                double dy = ccom[3 * ch + 1] - com[1];
-                double dz = ccom[3 * ch + 2] - com[2];
-                double d2 = dx * dx + dy * dy + dz * dz;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (q >= nch) continue;
+                const int ch = nd.z + q;
+                const double m = cm[q];
+                const double dx = cx[q] - com[0];
+                const double dy = cy[q] - com[1];
+                const double dz = cz[q] - com[2];
+                const double d2 = dx * dx + dy * dy + dz * dz;
                 const double *qc = cQ + 6 * ch;
                 Q[0] += qc[0] + m * (3.0 * dx * dx - d2);
                 Q[1] += qc[1] + m * (3.0 * dy * dy - d2);
@@ -725,13 +800,16 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     // one warp per cell: enough warps to fill every SM once
     for (int L = 0; L < P3T_MAX_LEVEL; ++L)
         k_tree_split<<<c->sms * 8, TB, 0, s>>>(L, c->p.n_leaf, cap, c->key_a,
-                                                c->node, c->parent, c->st);
+                                                c->node, c->parent, c->leaf_list,
+                                                c->int_list, c->st);
     k_moments<true><<<c->sms * 8, TB, 0, s>>>(0, c->xs, c->ms, n, c->node,
+                                               c->leaf_list, c->int_list,
                                                c->cM, c->ccom, c->cQ, c->cbmin,
                                                c->cbmax, c->wmin, c->wmax,
                                                c->cf0, c->cf1, c->cf2, c->st);
     for (int L = P3T_MAX_LEVEL - 1; L >= 0; --L)
         k_moments<false><<<grid_small, TB, 0, s>>>(L, c->xs, c->ms, n, c->node,
+                                                    c->leaf_list, c->int_list,
                                                     c->cM, c->ccom, c->cQ,
                                                     c->cbmin, c->cbmax, c->wmin,
                                                     c->wmax, c->cf0, c->cf1,
