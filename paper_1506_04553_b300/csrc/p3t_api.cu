@@ -172,6 +172,8 @@ int ensure_particles(p3t_ctx *c, int64_t n)
     P3T_TRY(grow(c->phi, d, cap, sizeof(float4)));
     P3T_TRY(grow(c->plo, d, cap, sizeof(float4)));
     P3T_TRY(grow(c->ngb_cnt, d, cap, sizeof(int)));
+    P3T_TRY(grow(c->ngb_slots, d, P3T_NGB_SLOTS * cap, sizeof(int)));
+    P3T_TRY(grow(c->ngb_ovf, d, cap, sizeof(int)));
     c->cap_tiles = p3t_sort_tiles(cap);
     P3T_TRY(grow(c->rs_counts, d, 256 * c->cap_tiles, sizeof(int)));
     c->cap_scan = p3t_scan_blocks(cap) + 2;
@@ -270,7 +272,7 @@ int clear_error(p3t_ctx *c, cudaStream_t s)
 void free_all(p3t_ctx *c)
 {
     void *ptrs[] = {c->st, c->key_a, c->key_b, c->idx_a, c->idx_b, c->order,
-                    c->xs, c->ms, c->phi, c->plo, c->ngb_cnt, c->rs_counts,
+                    c->xs, c->ms, c->phi, c->plo, c->ngb_cnt, c->ngb_slots, c->ngb_ovf, c->rs_counts,
                     c->rs_totals, c->bbox_part, c->node, c->parent, c->cM,
                     c->ccom, c->cQ, c->cbmin, c->cbmax, c->wmin, c->wmax,
                     c->cf0, c->cf1, c->cf2, c->grange, c->gmin, c->gmax,

@@ -24,6 +24,8 @@
 
 #define P3T_MAX_LEVEL 21
 #define P3T_WARP 32
+// neighbour rows up to this length are kept by the counting walk
+#define P3T_NGB_SLOTS 8
 // Hard step: components are ordered in 32 level buckets x 33 size classes;
 // the bucket scratch holds four int arrays of that length and a counter.
 #define P3T_HERM_BUCKETS (32 * 33)
@@ -45,6 +47,7 @@ struct P3TDevState {
     unsigned int work;  // dynamic work counter
     int pad0;
     int level_start[P3T_MAX_LEVEL + 3];
+    int novf;           // groups listed in ngb_ovf
     int nleaf;          // leaves listed by the split (leaf_list)
     int nint;           // split cells listed by the split (int_list)
     int int_start[P3T_MAX_LEVEL + 2];  // int_list range of each level
@@ -104,6 +107,8 @@ struct p3t_ctx {
     double *xs, *ms;
     float4 *phi, *plo;
     int *ngb_cnt;      // per original index
+    int *ngb_slots;    // first P3T_NGB_SLOTS neighbours of each particle
+    int *ngb_ovf;      // groups with a row longer than P3T_NGB_SLOTS
     // sort scratch
     int *rs_counts, *rs_totals;
     int64_t cap_tiles;

@@ -11,8 +11,12 @@
 // exceeds h^2 by more than the FP32 error of r^2, and the survivors are
 // decided by the FP64 predicate above: the result is exact.
 //
-// Two passes over the same walk: counts per particle (scanned into CSR
-// offsets), then the fill; rows are sorted by original index afterwards.
+// The counting walk also keeps the first P3T_NGB_SLOTS neighbours of every
+// particle and lists the groups with a longer row.  After the counts are
+// scanned into CSR offsets, the short rows are sorted and copied from the
+// kept neighbours; the walk runs a second time only over the listed groups,
+// to fill the long rows, which are sorted afterwards.  Rows are sorted by
+// original index.
 #include "p3t_internal.cuh"
 
 namespace {
@@ -47,14 +51,19 @@ struct __align__(16) NgbSmem {
     int2 ring[NRING];
 };
 
-// Screens the staged tile against the lane's two particles.
+constexpr int SL = P3T_NGB_SLOTS;
+
+// Screens the staged tile against the lane's two particles.  Counting:
+// neighbours beyond the count c go to the particle's slots while c < SL.
+// Filling (long rows only, b0 / b1): neighbours go to the CSR row at w.
 template <bool FILL>
 __device__ __forceinline__ void ngb_tile(NgbSmem &S, float4 p0, float4 p1,
                                          bool v0, bool v1, int k0, int k1,
                                          float hs2, const double *xs, int n,
                                          double h2, const int *order,
                                          int &c0, int &c1, long long &w0,
-                                         long long &w1, int *idx,
+                                         long long &w1, bool b0, bool b1,
+                                         int *s0, int *s1, int *idx,
                                          long long cap, P3TDevState *st)
 {
     for (int j = 0; j < 32; ++j) {
@@ -66,17 +75,25 @@ __device__ __forceinline__ void ngb_tile(NgbSmem &S, float4 p0, float4 p1,
         float r21 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (r20 < hs2 && v0 && kj >= 0 && kj != k0 && exact_ngb(xs, n, k0, kj, h2)) {
             if (FILL) {
-                if (w0 < cap) idx[w0] = order[kj];
-                else p3t_raise(st, P3T_ERR_CAPACITY);
-                ++w0;
+                if (b0) {
+                    if (w0 < cap) idx[w0] = order[kj];
+                    else p3t_raise(st, P3T_ERR_CAPACITY);
+                    ++w0;
+                }
+            } else if (c0 < SL) {
+                s0[c0] = order[kj];
             }
             ++c0;
         }
         if (r21 < hs2 && v1 && kj >= 0 && kj != k1 && exact_ngb(xs, n, k1, kj, h2)) {
             if (FILL) {
-                if (w1 < cap) idx[w1] = order[kj];
-                else p3t_raise(st, P3T_ERR_CAPACITY);
-                ++w1;
+                if (b1) {
+                    if (w1 < cap) idx[w1] = order[kj];
+                    else p3t_raise(st, P3T_ERR_CAPACITY);
+                    ++w1;
+                }
+            } else if (c1 < SL) {
+                s1[c1] = order[kj];
             }
             ++c1;
         }
@@ -96,20 +113,21 @@ k_ngb_walk(const int *__restrict__ gclus,
            const double *__restrict__ xs, int n,
            int *__restrict__ cnt, const long long *__restrict__ row_off,
            int *__restrict__ idx, long long cap, const int *__restrict__ gperm,
-           P3TDevState *st)
+           int *__restrict__ slots, int *__restrict__ ovf, P3TDevState *st)
 {
     __shared__ NgbSmem smem[NW];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
     NgbSmem &S = smem[w];
     if (st->error) return;  // no valid tree
-    const int G = st->ngroup;
+    // counting: every group, in the work order; filling: the listed groups
+    const int G = FILL ? st->novf : st->ngroup;
     for (;;) {
         int g = 0;
         if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
         g = __shfl_sync(full, g, 0);
         if (g >= G) break;
-        g = gperm[g];
+        g = FILL ? ovf[g] : gperm[g];
         const int2 gr = grange[g];
         const float4 ct = gctr[g];
         const float4 gmn = gmin[g], gmx = gmax[g];
@@ -122,11 +140,20 @@ k_ngb_walk(const int *__restrict__ gclus,
         const float4 p0 = v0 ? rel4n(phi[k0], plo[k0], ct) : make_float4(1e15f, 1e15f, 1e15f, 0.f);
         const float4 p1 = v1 ? rel4n(phi[k1], plo[k1], ct) : make_float4(1e15f, 1e15f, 1e15f, 0.f);
         int c0 = 0, c1 = 0;
+        const int o0 = v0 ? order[k0] : 0, o1 = v1 ? order[k1] : 0;
         long long w0 = 0, w1 = 0;
+        bool b0 = false, b1 = false;
         if (FILL) {
-            if (v0) w0 = row_off[order[k0]];
-            if (v1) w1 = row_off[order[k1]];
+            if (v0) {
+                w0 = row_off[o0];
+                b0 = row_off[o0 + 1] - w0 > SL;
+            }
+            if (v1) {
+                w1 = row_off[o1];
+                b1 = row_off[o1 + 1] - w1 > SL;
+            }
         }
+        int *s0 = slots + (size_t)o0 * SL, *s1 = slots + (size_t)o1 * SL;
         int head = 0, nr = 0, np = 0;  // ring of near leaf ranges
         if (lane == 0) S.stack[0] = cl * 8;  // the cluster's root
         int top = 1, iter = 0;
@@ -162,7 +189,7 @@ k_ngb_walk(const int *__restrict__ gclus,
                 }
                 __syncwarp();
                 ngb_tile<FILL>(S, p0, p1, v0, v1, k0, k1, hs2, xs, n, h2, order,
-                               c0, c1, w0, w1, idx, cap, st);
+                               c0, c1, w0, w1, b0, b1, s0, s1, idx, cap, st);
                 __syncwarp();
             }
             if (top == 0) break;
@@ -231,20 +258,57 @@ k_ngb_walk(const int *__restrict__ gclus,
             continue;
         }
         if (!FILL) {
-            if (v0) cnt[order[k0]] = c0;
-            if (v1) cnt[order[k1]] = c1;
+            if (v0) cnt[o0] = c0;
+            if (v1) cnt[o1] = c1;
+            if (__any_sync(full, c0 > SL || c1 > SL) && lane == 0)
+                ovf[atomicAdd(&st->novf, 1)] = g;
         }
     }
 }
 
-// Sorts each CSR row ascending (rows are short: insertion sort per thread).
+// Short rows (at most SL): the kept neighbours, sorted ascending in
+// registers, copied to the CSR row.
+__global__ void k_ngb_gather(int n, const long long *__restrict__ row_off,
+                             const int *__restrict__ slots,
+                             int *__restrict__ idx, long long cap,
+                             P3TDevState *st)
+{
+    if (st->error) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += gridDim.x * blockDim.x) {
+        const long long b = row_off[i];
+        const int len = (int)(row_off[i + 1] - b);
+        if (len == 0 || len > SL) continue;
+        if (b + len > cap) {
+            p3t_raise(st, P3T_ERR_CAPACITY);
+            continue;
+        }
+        int v[SL];
+#pragma unroll
+        for (int q = 0; q < SL; ++q) v[q] = q < len ? slots[(size_t)i * SL + q] : INT_MAX;
+#pragma unroll
+        for (int a = 1; a < SL; ++a)  // insertion sort, fixed shape
+#pragma unroll
+            for (int q = a; q > 0; --q)
+                if (v[q - 1] > v[q]) {
+                    const int t = v[q - 1];
+                    v[q - 1] = v[q];
+                    v[q] = t;
+                }
+#pragma unroll
+        for (int q = 0; q < SL; ++q)
+            if (q < len) idx[b + q] = v[q];
+    }
+}
+
+// Sorts each long CSR row ascending (insertion sort per thread).
 __global__ void k_ngb_sort(int n, const long long *__restrict__ row_off,
                            int *__restrict__ idx, long long cap)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += gridDim.x * blockDim.x) {
         long long b = row_off[i], e = row_off[i + 1];
-        if (e > cap) continue;
+        if (e > cap || e - b <= SL) continue;
         for (long long a = b + 1; a < e; ++a) {
             int v = idx[a];
             long long q = a - 1;
@@ -257,14 +321,19 @@ __global__ void k_ngb_sort(int n, const long long *__restrict__ row_off,
     }
 }
 
-__global__ void k_work_reset(P3TDevState *st)
+__global__ void k_work_reset(P3TDevState *st, int fill)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) st->work = 0;
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        st->work = 0;
+        if (!fill) st->novf = 0;
+    }
 }
 
 }  // namespace
 
-// fill == 0: per-particle counts into c->ngb_cnt; fill == 1: CSR rows.
+// fill == 0: per-particle counts into c->ngb_cnt (and the kept neighbours);
+// fill == 1: CSR rows (short rows from the kept neighbours, long rows by a
+// second walk over the listed groups).
 int p3t_run_ngb(p3t_ctx *c, int fill, const long long *row_off, int *idx,
                 long long cap, cudaStream_t s)
 {
@@ -272,24 +341,24 @@ int p3t_run_ngb(p3t_ctx *c, int fill, const long long *row_off, int *idx,
     const int64_t G = (n + 15) / 16 + c->nclus;  // bound; the count is on the device
     int blocks = (int)((G + NW - 1) / NW);
     if (blocks > c->sms * 16) blocks = c->sms * 16;
-    k_work_reset<<<1, 32, 0, s>>>(c->st);
-    if (fill)
+    int nb = (n + 255) / 256;
+    if (nb > c->sms * 8) nb = c->sms * 8;
+    if (nb < 1) nb = 1;
+    k_work_reset<<<1, 32, 0, s>>>(c->st, fill);
+    if (fill) {
+        k_ngb_gather<<<nb, 256, 0, s>>>(n, row_off, c->ngb_slots, idx, cap, c->st);
         k_ngb_walk<true><<<blocks, NW * 32, 0, s>>>(
             c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
             c->wmax, c->node, c->phi, c->plo, c->order, c->xs, n, c->ngb_cnt,
-            row_off, idx, cap, c->gperm, c->st);
-    else
+            row_off, idx, cap, c->gperm, c->ngb_slots, c->ngb_ovf, c->st);
+        k_ngb_sort<<<nb, 256, 0, s>>>(n, row_off, idx, cap);
+        p3t_count_launches(4);
+    } else {
         k_ngb_walk<false><<<blocks, NW * 32, 0, s>>>(
             c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
             c->wmax, c->node, c->phi, c->plo, c->order, c->xs, n, c->ngb_cnt,
-            row_off, idx, cap, c->gperm, c->st);
-    p3t_count_launches(2);
-    if (fill) {
-        int nb = (n + 255) / 256;
-        if (nb > c->sms * 8) nb = c->sms * 8;
-        if (nb < 1) nb = 1;
-        k_ngb_sort<<<nb, 256, 0, s>>>(n, row_off, idx, cap);
-        p3t_count_launches(1);
+            row_off, idx, cap, c->gperm, c->ngb_slots, c->ngb_ovf, c->st);
+        p3t_count_launches(2);
     }
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;

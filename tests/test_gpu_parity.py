@@ -87,6 +87,10 @@ def test_neighbours_bitexact(case):
     assert np.array_equal(idx.astype(np.int64), idx_o.astype(np.int64))
     if case["name"] == "gauss_dense":
         assert off[-1] > 5 * case["pos"].shape[0]  # several neighbours each
+        # rows kept by the counting walk (at most 8) and rows filled by the
+        # second walk over the listed groups both occur
+        rl = np.diff(off)
+        assert ((rl > 0) & (rl <= 8)).sum() > 100 and (rl > 8).sum() > 100
 
 
 def test_theta_zero_equals_direct_sum(cuda):
