@@ -71,8 +71,9 @@ struct Acc3 {
 // Every term is evaluated for one i-particle against two consecutive staged
 // sources at once, with the FP32x2 instructions of sm_100 and later (one issue
 // slot for two FMAs); each half rounds exactly like the scalar operation.
-// The sources are staged in shared memory as component arrays, so one 64-bit
-// load gives a component of both sources, and the particle's coordinates are
+// The sources are staged in shared memory pair-interleaved (two components
+// of both sources of a pair in 16 bytes), so one 128-bit load gives two
+// components of both sources, and the particle's coordinates are
 // held as broadcast pairs.
 typedef float2 f2;
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
@@ -229,7 +230,7 @@ constexpr int RING = 64;     // ring capacity (entries); never more than 63 used
 constexpr int NCOMP = 10;
 
 struct __align__(16) WarpSmem {
-    float t[NCOMP][32];             // staged sources, one array per component
+    float t[NCOMP][32];             // staged sources, pair-interleaved (see cell_tile)
     int stack[FSTACK];              // packed child ranges: child * 8 + nchild-1
     int cb[32];                     // cells of the current walk batch
     int pc[RING];                   // accepted cells
@@ -315,11 +316,6 @@ __device__ __forceinline__ void tile_end(GroupAcc<POT> &A, const Part3 &u,
     }
 }
 
-__device__ __forceinline__ f2 ld2(const float *a, int j)
-{
-    return *reinterpret_cast<const float2 *>(a + j);
-}
-
 // One tile of up to 32 accepted cells.
 template <bool POT>
 __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
@@ -349,8 +345,18 @@ __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
 #pragma unroll
         for (int q = 3; q < NCOMP; ++q) v[q] = 0.0f;
     }
+    // pair-interleaved: the cells 2p and 2p+1 fill 20 consecutive floats,
+    // components (2k, 2k+1) of both in float4 k, so one 128-bit load gives
+    // two components of the pair
+    {
+        float *t = &S.t[0][0];
+        const int pr = lane >> 1, hf = lane & 1;
 #pragma unroll
-    for (int q = 0; q < NCOMP; ++q) S.t[q][lane] = v[q];
+        for (int k = 0; k < NCOMP / 2; ++k) {
+            t[pr * 20 + 4 * k + hf] = v[2 * k];
+            t[pr * 20 + 4 * k + 2 + hf] = v[2 * k + 1];
+        }
+    }
     head = (head + take) & (RING - 1);
     n -= take;
     __syncwarp();
@@ -361,15 +367,31 @@ __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
 #pragma unroll kPcUnroll
     for (int j = 0; j < 32; j += 2) {
         CellPair c;
-        c.X = ld2(S.t[0], j);   c.Y = ld2(S.t[1], j);   c.Z = ld2(S.t[2], j);
-        c.M = ld2(S.t[3], j);   c.Qxx = ld2(S.t[4], j); c.Qyy = ld2(S.t[5], j);
-        c.Qzz = ld2(S.t[6], j); c.Qxy = ld2(S.t[7], j); c.Qxz = ld2(S.t[8], j);
-        c.Qyz = ld2(S.t[9], j);
+        const float4 *t4 = reinterpret_cast<const float4 *>(&S.t[0][0]) + (j >> 1) * 5;
+        const float4 A = t4[0], B = t4[1], C = t4[2], D = t4[3], E = t4[4];
+        c.X = make_float2(A.x, A.y);   c.Y = make_float2(A.z, A.w);
+        c.Z = make_float2(B.x, B.y);   c.M = make_float2(B.z, B.w);
+        c.Qxx = make_float2(C.x, C.y); c.Qyy = make_float2(C.z, C.w);
+        c.Qzz = make_float2(D.x, D.y); c.Qxy = make_float2(D.z, D.w);
+        c.Qxz = make_float2(E.x, E.y); c.Qyz = make_float2(E.z, E.w);
         pc_term2<POT>(P.x0, P.y0, P.z0, c, e2, u.x, u.y, u.z, u.p);
         pc_term2<POT>(P.x1, P.y1, P.z1, c, e2, w.x, w.y, w.z, w.p);
     }
     tile_end<POT>(A, u, w, -1.0f);
     __syncwarp();
+}
+
+// Staged particles j and j + 1 (j even).
+__device__ __forceinline__ PartPair part_pair(const WarpSmem &S, int j)
+{
+    PartPair p;
+    const float4 *t4 = reinterpret_cast<const float4 *>(&S.t[0][0]) + (j >> 1) * 2;
+    const float4 A = t4[0], B = t4[1];
+    p.X = make_float2(A.x, A.y);
+    p.Y = make_float2(A.z, A.w);
+    p.Z = make_float2(B.x, B.y);
+    p.M = make_float2(B.z, B.w);
+    return p;
 }
 
 // One tile of up to 32 particles from a ring of leaf ranges.
@@ -388,10 +410,14 @@ __device__ __forceinline__ void particle_tile(
         v = far_pad();
         S.tj[lane] = -1;
     }
-    S.t[0][lane] = v.x;
-    S.t[1][lane] = v.y;
-    S.t[2][lane] = v.z;
-    S.t[3][lane] = v.w;
+    {  // pair-interleaved, as for cells: (X, Y) and (Z, M) of a pair per float4
+        float *t = &S.t[0][0];
+        const int pr = lane >> 1, hf = lane & 1;
+        t[pr * 8 + hf] = v.x;
+        t[pr * 8 + 2 + hf] = v.y;
+        t[pr * 8 + 4 + hf] = v.z;
+        t[pr * 8 + 6 + hf] = v.w;
+    }
     __syncwarp();
     Part3 u, w;
     u.zero();
@@ -402,9 +428,7 @@ __device__ __forceinline__ void particle_tile(
         float tp0 = 0.f, tp1 = 0.f;
 #pragma unroll 2
         for (int j = 0; j < 32; j += 2) {
-            PartPair p;
-            p.X = ld2(S.t[0], j); p.Y = ld2(S.t[1], j);
-            p.Z = ld2(S.t[2], j); p.M = ld2(S.t[3], j);
+            const PartPair p = part_pair(S, j);
             const f2 s0 = pp_near2(P.x0, P.y0, P.z0, p, e2, kA, kB, u.x, u.y, u.z);
             const f2 s1 = pp_near2(P.x1, P.y1, P.z1, p, e2, kA, kB, w.x, w.y, w.z);
             if (POT) {
@@ -423,9 +447,7 @@ __device__ __forceinline__ void particle_tile(
     } else {
 #pragma unroll 4
         for (int j = 0; j < 32; j += 2) {
-            PartPair p;
-            p.X = ld2(S.t[0], j); p.Y = ld2(S.t[1], j);
-            p.Z = ld2(S.t[2], j); p.M = ld2(S.t[3], j);
+            const PartPair p = part_pair(S, j);
             pp_far2<POT>(P.x0, P.y0, P.z0, p, e2, u.x, u.y, u.z, u.p);
             pp_far2<POT>(P.x1, P.y1, P.z1, p, e2, w.x, w.y, w.z, w.p);
         }
