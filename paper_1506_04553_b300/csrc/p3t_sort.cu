@@ -6,8 +6,10 @@
 //   rs_scan    one block per digit: exclusive scan of counts[d][*] over the
 //              tiles, digit total
 //   rs_scatter per tile: stable rank of every key among the keys of the same
-//              digit (warp match + per-warp digit counters), written to
-//              base[d] + tile_offset[d][tile] + rank
+//              digit (warp match + per-warp digit counters); the tile is
+//              reordered by digit in shared memory and each digit's run is
+//              written to base[d] + tile_offset[d][tile] + rank with
+//              consecutive threads on consecutive positions
 // Stability: a tile is split into 8 warp segments of 256 keys; inside a
 // segment keys are handled in 8 rounds of 32 consecutive keys; the rank of a
 // key counts equal digits in earlier segments, earlier rounds and lower lanes,
@@ -100,7 +102,10 @@ rs_scatter(int n, const u64 *__restrict__ kin, const int *__restrict__ vin,
            const int *__restrict__ counts, const int *__restrict__ totals)
 {
     __shared__ int tile_off[256];
+    __shared__ int tile_start[256];  // first position of each digit in the tile
     __shared__ int whist[RS_WARPS][256];
+    __shared__ u64 sk[RS_TILE];
+    __shared__ int sv[RS_TILE];
     __shared__ int tot;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     // digit base = exclusive scan of the digit totals
@@ -131,25 +136,37 @@ rs_scatter(int n, const u64 *__restrict__ kin, const int *__restrict__ vin,
         dig[r] = d;
     }
     __syncthreads();
-    // exclusive prefix over warps for digit t
-    {
-        int run = 0;
+    // exclusive prefix over warps for digit t, then over digits
+    int run = 0;
 #pragma unroll
-        for (int q = 0; q < RS_WARPS; ++q) {
-            int c = whist[q][t];
-            whist[q][t] = run;
-            run += c;
-        }
+    for (int q = 0; q < RS_WARPS; ++q) {
+        int c = whist[q][t];
+        whist[q][t] = run;
+        run += c;
     }
+    const int start = block_excl_scan256(run, &tot);
+    tile_start[t] = start;
     __syncthreads();
+    // reorder the tile by digit (stable) in shared memory
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
         int d = dig[r];
         if (d < 256) {
-            int pos = tile_off[d] + whist[w][d] + rank[r];
-            kout[pos] = k[r];
-            vout[pos] = v[r];
+            int lp = tile_start[d] + whist[w][d] + rank[r];
+            sk[lp] = k[r];
+            sv[lp] = v[r];
         }
+    }
+    __syncthreads();
+    // runs of equal digits to consecutive global positions
+    const int cnt = min(RS_TILE, n - blockIdx.x * RS_TILE);
+    for (int j = t; j < cnt; j += RS_THREADS) {
+        const u64 kk = sk[j];
+        const int vv = sv[j];
+        const int d = rs_digit<CL>(kk, vv, pclus, shift);
+        const int pos = tile_off[d] + (j - tile_start[d]);
+        kout[pos] = kk;
+        vout[pos] = vv;
     }
 }
 
