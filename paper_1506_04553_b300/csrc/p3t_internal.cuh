@@ -182,6 +182,25 @@ __device__ __forceinline__ void p3t_raise(P3TDevState *st, int code)
 }
 
 // ---- warp helpers ----
+// Order-preserving map of a double to an int64 (its own inverse): for
+// values that are not NaN, a < b iff ord64(a) < ord64(b), with -0 below +0.
+// Minima and maxima of doubles then run on the integer pipe, bit for bit the
+// values fmin / fmax return (up to the sign of a zero), without occupying
+// the slow FP64 unit.
+__device__ __forceinline__ long long ord64(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double unord64(long long o)
+{
+    return __longlong_as_double(o ^ ((o >> 63) & 0x7fffffffffffffffLL));
+}
+__device__ __forceinline__ bool finite64(double x)
+{
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
 __device__ __forceinline__ int warp_incl_scan(int v)
 {
     const int lane = threadIdx.x & 31;

@@ -33,34 +33,23 @@ constexpr int TB = 256;
 #endif
 
 // ---------------------------------------------------------------- bbox ----
-__global__ void __launch_bounds__(TB)
-k_bbox_partial(int n, const double *__restrict__ pos,
-               const double *__restrict__ mass, double *__restrict__ part,
-               P3TDevState *st)
+// Minima and maxima run on order-preserving integer images of the
+// coordinates (ord64), so the reductions occupy the integer pipe, not the
+// FP64 unit; finiteness is read from the exponent field.
+// images of +inf and -inf: the neutral elements of min and max
+constexpr long long ORD_HI = 0x7ff0000000000000LL;
+constexpr long long ORD_LO = (long long)0x800fffffffffffffULL;
+
+// Block-wide min of mn[3] and max of mx[3]; the result in thread 0.
+__device__ __forceinline__ void block_minmax3(long long *mn, long long *mx)
 {
-    double mn[3] = {INFINITY, INFINITY, INFINITY};
-    double mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    bool bad = false;
-    for (int i = blockIdx.x * TB + threadIdx.x; i < n; i += gridDim.x * TB) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double v = pos[(size_t)a * n + i];
-            bad |= !isfinite(v);
-            mn[a] = fmin(mn[a], v);
-            mx[a] = fmax(mx[a], v);
-        }
-        double m = mass[i];
-        bad |= !(m > 0.0) || !isfinite(m);
-    }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) p3t_raise(st, P3T_ERR_INVALID);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < 3; ++a)
         for (int o = 16; o > 0; o >>= 1) {
-            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
-            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+            mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
         }
-    }
-    __shared__ double smn[3][TB / 32], smx[3][TB / 32];
+    __shared__ long long smn[3][TB / 32], smx[3][TB / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0)
         for (int a = 0; a < 3; ++a) {
@@ -68,58 +57,88 @@ k_bbox_partial(int n, const double *__restrict__ pos,
             smx[a][w] = mx[a];
         }
     __syncthreads();
-    if (threadIdx.x < 3) {
-        int a = threadIdx.x;
-        double u = smn[a][0], v = smx[a][0];
-        for (int q = 1; q < TB / 32; ++q) {
-            u = fmin(u, smn[a][q]);
-            v = fmax(v, smx[a][q]);
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 3; ++a)
+            for (int q = 1; q < TB / 32; ++q) {
+                mn[a] = min(mn[a], smn[a][q]);
+                mx[a] = max(mx[a], smx[a][q]);
+            }
+}
+
+// Particles [b, e) with stride: box images and validity (finite
+// coordinates, finite positive masses).
+__device__ __forceinline__ bool scan_box(int b, int e, int stride, int n,
+                                         const double *__restrict__ pos,
+                                         const double *__restrict__ mass,
+                                         long long *mn, long long *mx)
+{
+    bool bad = false;
+    for (int i = b; i < e; i += stride) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double v = pos[(size_t)a * n + i];
+            bad |= !finite64(v);
+            const long long o = ord64(v);
+            mn[a] = min(mn[a], o);
+            mx[a] = max(mx[a], o);
         }
-        part[blockIdx.x * 6 + a] = u;
-        part[blockIdx.x * 6 + 3 + a] = v;
+        const double m = mass[i];
+        bad |= !(m > 0.0) || !finite64(m);
     }
+    return bad;
+}
+
+__global__ void __launch_bounds__(TB)
+k_bbox_partial(int n, const double *__restrict__ pos,
+               const double *__restrict__ mass, double *__restrict__ part,
+               P3TDevState *st)
+{
+    long long mn[3] = {ORD_HI, ORD_HI, ORD_HI}, mx[3] = {ORD_LO, ORD_LO, ORD_LO};
+    const bool bad = scan_box(blockIdx.x * TB + threadIdx.x, n, gridDim.x * TB, n,
+                              pos, mass, mn, mx);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) p3t_raise(st, P3T_ERR_INVALID);
+    block_minmax3(mn, mx);
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 3; ++a) {
+            part[blockIdx.x * 6 + a] = unord64(mn[a]);
+            part[blockIdx.x * 6 + 3 + a] = unord64(mx[a]);
+        }
+}
+
+// Root cube from the box: side = largest extent (1 + 2^-20), 1 if zero.
+__device__ __forceinline__ void root_cube(const long long *mn, const long long *mx,
+                                          double *lo, double *size)
+{
+    double ext = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double u = unord64(mn[a]), v = unord64(mx[a]);
+        const double e = __dsub_rn(v, u);
+        if (e > ext) ext = e;
+        lo[a] = u;
+    }
+    *size = (ext == 0.0) ? 1.0 : __dmul_rn(ext, 1.0 + 0x1p-20);
 }
 
 __global__ void __launch_bounds__(TB)
 k_bbox_final(int nblk, const double *__restrict__ part, P3TDevState *st,
              double *__restrict__ clus_box)
 {
-    double mn[3] = {INFINITY, INFINITY, INFINITY};
-    double mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    long long mn[3] = {ORD_HI, ORD_HI, ORD_HI}, mx[3] = {ORD_LO, ORD_LO, ORD_LO};
     for (int b = threadIdx.x; b < nblk; b += TB)
         for (int a = 0; a < 3; ++a) {
-            mn[a] = fmin(mn[a], part[6 * b + a]);
-            mx[a] = fmax(mx[a], part[6 * b + 3 + a]);
+            mn[a] = min(mn[a], ord64(part[6 * b + a]));
+            mx[a] = max(mx[a], ord64(part[6 * b + 3 + a]));
         }
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
-            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
-        }
-    __shared__ double smn[3][TB / 32], smx[3][TB / 32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int a = 0; a < 3; ++a) {
-            smn[a][w] = mn[a];
-            smx[a][w] = mx[a];
-        }
-    __syncthreads();
+    block_minmax3(mn, mx);
     if (threadIdx.x != 0) return;
-    double ext = 0.0;
+    double lo[3], size;
+    root_cube(mn, mx, lo, &size);
     for (int a = 0; a < 3; ++a) {
-        double u = smn[a][0], v = smx[a][0];
-        for (int q = 1; q < TB / 32; ++q) {
-            u = fmin(u, smn[a][q]);
-            v = fmax(v, smx[a][q]);
-        }
-        double e = __dsub_rn(v, u);
-        if (e > ext) ext = e;
-        st->lo[a] = u;
-        clus_box[a] = u;
+        st->lo[a] = lo[a];
+        clus_box[a] = lo[a];
     }
-    st->size = (ext == 0.0) ? 1.0 : __dmul_rn(ext, 1.0 + 0x1p-20);
-    clus_box[3] = st->size;
+    st->size = size;
+    clus_box[3] = size;
 }
 
 // One block per cluster of an ensemble: root cube of [off[k], off[k+1])
@@ -131,48 +150,15 @@ k_bbox_seg(const long long *__restrict__ off, int n,
 {
     const int k = blockIdx.x;
     const int b = (int)off[k], e = (int)off[k + 1];
-    double mn[3] = {INFINITY, INFINITY, INFINITY};
-    double mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    bool bad = false;
-    for (int i = b + threadIdx.x; i < e; i += TB) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            double v = pos[(size_t)a * n + i];
-            bad |= !isfinite(v);
-            mn[a] = fmin(mn[a], v);
-            mx[a] = fmax(mx[a], v);
-        }
-        double m = mass[i];
-        bad |= !(m > 0.0) || !isfinite(m);
-    }
+    long long mn[3] = {ORD_HI, ORD_HI, ORD_HI}, mx[3] = {ORD_LO, ORD_LO, ORD_LO};
+    const bool bad = scan_box(b + threadIdx.x, e, TB, n, pos, mass, mn, mx);
     if (__syncthreads_or(bad) && threadIdx.x == 0) p3t_raise(st, P3T_ERR_INVALID);
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-        for (int o = 16; o > 0; o >>= 1) {
-            mn[a] = fmin(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
-            mx[a] = fmax(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
-        }
-    __shared__ double smn[3][TB / 32], smx[3][TB / 32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int a = 0; a < 3; ++a) {
-            smn[a][w] = mn[a];
-            smx[a][w] = mx[a];
-        }
-    __syncthreads();
+    block_minmax3(mn, mx);
     if (threadIdx.x != 0) return;
-    double ext = 0.0;
-    for (int a = 0; a < 3; ++a) {
-        double u = smn[a][0], v = smx[a][0];
-        for (int q = 1; q < TB / 32; ++q) {
-            u = fmin(u, smn[a][q]);
-            v = fmax(v, smx[a][q]);
-        }
-        double d = __dsub_rn(v, u);
-        if (d > ext) ext = d;
-        clus_box[4 * k + a] = u;
-    }
-    clus_box[4 * k + 3] = (ext == 0.0) ? 1.0 : __dmul_rn(ext, 1.0 + 0x1p-20);
+    double lo[3], size;
+    root_cube(mn, mx, lo, &size);
+    for (int a = 0; a < 3; ++a) clus_box[4 * k + a] = lo[a];
+    clus_box[4 * k + 3] = size;
 }
 
 // Cluster of every particle (original index) of an ensemble.
@@ -194,12 +180,20 @@ k_cluster_ids(int n, int nc, const long long *__restrict__ off,
 }
 
 // ---------------------------------------------------------------- keys ----
-__device__ __forceinline__ u64 quantise(double x, double lo, double size)
+// floor(((x - lo) / size) 2^21), each operation rounded once, clamped to
+// [0, 2^21 - 1].  The quotient is formed as t (1/size): it differs from the
+// rounded quotient by at most 4 ulp, i.e. by less than 2^-30 after the
+// scaling by 2^21, so the floor is the same unless the scaled value lies
+// within 2^-28 of an integer; there (rarely) the division itself decides.
+__device__ __forceinline__ u64 quantise(double x, double lo, double size,
+                                        double isize)
 {
-    double t = __dsub_rn(x, lo);
-    double u = __ddiv_rn(t, size);
-    double v = __dmul_rn(u, 2097152.0);
-    long long q = (long long)floor(v);
+    const double t = __dsub_rn(x, lo);
+    double v = __dmul_rn(__dmul_rn(t, isize), 2097152.0);
+    const double f = __dsub_rn(v, floor(v));
+    if (f < 0x1p-28 || f > 1.0 - 0x1p-28)
+        v = __dmul_rn(__ddiv_rn(t, size), 2097152.0);
+    long long q = __double2ll_rd(v);
     q = q < 0 ? 0 : q;
     q = q > 2097151 ? 2097151 : q;
     return (u64)q;
@@ -226,9 +220,10 @@ k_keys(int n, const double *__restrict__ pos, int nc,
     if (i >= n) return;
     const double *bx = clus_box + 4 * (nc > 1 ? pclus[i] : 0);
     const double size = bx[3];
-    u64 qx = quantise(pos[i], bx[0], size);
-    u64 qy = quantise(pos[(size_t)n + i], bx[1], size);
-    u64 qz = quantise(pos[2 * (size_t)n + i], bx[2], size);
+    const double isize = __drcp_rn(size);  // once per warp in a single cluster
+    u64 qx = quantise(pos[i], bx[0], size, isize);
+    u64 qy = quantise(pos[(size_t)n + i], bx[1], size, isize);
+    u64 qz = quantise(pos[2 * (size_t)n + i], bx[2], size, isize);
     key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     idx[i] = i;
 }
@@ -492,8 +487,8 @@ k_moments(int L, const double *__restrict__ xs, const double *__restrict__ ms,
         const int c = list[q];
         int4 nd = node[c];
         double M = 0.0, com[3] = {0, 0, 0}, Q[6] = {0, 0, 0, 0, 0, 0};
-        double bmn[3] = {INFINITY, INFINITY, INFINITY};
-        double bmx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        long long omn[3] = {ORD_HI, ORD_HI, ORD_HI};  // box images (ord64)
+        long long omx[3] = {ORD_LO, ORD_LO, ORD_LO};
         const int nch = nd.w & 255;
         if (nch == 0) {
             // leaf: from its particles, in chunks of LCH whose loads are all
@@ -517,12 +512,13 @@ k_moments(int L, const double *__restrict__ xs, const double *__restrict__ ms,
                     com[0] += pm[u] * px[u];
                     com[1] += pm[u] * py[u];
                     com[2] += pm[u] * pz[u];
-                    bmn[0] = fmin(bmn[0], px[u]);
-                    bmn[1] = fmin(bmn[1], py[u]);
-                    bmn[2] = fmin(bmn[2], pz[u]);
-                    bmx[0] = fmax(bmx[0], px[u]);
-                    bmx[1] = fmax(bmx[1], py[u]);
-                    bmx[2] = fmax(bmx[2], pz[u]);
+                    const long long ox = ord64(px[u]), oy = ord64(py[u]), oz = ord64(pz[u]);
+                    omn[0] = min(omn[0], ox);
+                    omn[1] = min(omn[1], oy);
+                    omn[2] = min(omn[2], oz);
+                    omx[0] = max(omx[0], ox);
+                    omx[1] = max(omx[1], oy);
+                    omx[2] = max(omx[2], oz);
                 }
             }
 #pragma unroll
@@ -566,8 +562,8 @@ k_moments(int L, const double *__restrict__ xs, const double *__restrict__ ms,
                 cz[q] = ccom[3 * ch + 2];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    bmn[a] = fmin(bmn[a], cbmin[3 * ch + a]);  // repeats child 0: harmless
-                    bmx[a] = fmax(bmx[a], cbmax[3 * ch + a]);
+                    omn[a] = min(omn[a], ord64(cbmin[3 * ch + a]));  // repeats child 0: harmless
+                    omx[a] = max(omx[a], ord64(cbmax[3 * ch + a]));
                 }
             }
 #pragma unroll
@@ -597,6 +593,12 @@ k_moments(int L, const double *__restrict__ xs, const double *__restrict__ ms,
                 Q[4] += qc[4] + m * (3.0 * dx * dz);
                 Q[5] += qc[5] + m * (3.0 * dy * dz);
             }
+        }
+        double bmn[3], bmx[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            bmn[a] = unord64(omn[a]);
+            bmx[a] = unord64(omx[a]);
         }
         cM[c] = M;
 #pragma unroll
@@ -665,20 +667,35 @@ k_group_box(const int2 *__restrict__ grange, const double *__restrict__ xs,
 {
     if (st->error) return;
     const int G = st->ngroup;  // <= capacity (k_groups checks)
-    for (int g = blockIdx.x * TB + threadIdx.x; g < G; g += gridDim.x * TB) {
-        int2 r = grange[g];
+    const int lane = threadIdx.x & 31;
+    const int wg = (blockIdx.x * TB + threadIdx.x) >> 5, nw = gridDim.x * (TB / 32);
+    // one warp per group: lanes over its particles, box on integer images
+    for (int g = wg; g < G; g += nw) {
+        const int2 r = grange[g];
+        long long omn[3] = {ORD_HI, ORD_HI, ORD_HI}, omx[3] = {ORD_LO, ORD_LO, ORD_LO};
+        for (int k = r.x + lane; k < r.x + r.y; k += 32)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const long long o = ord64(xs[(size_t)a * n + k]);
+                omn[a] = min(omn[a], o);
+                omx[a] = max(omx[a], o);
+            }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            for (int o = 16; o > 0; o >>= 1) {
+                omn[a] = min(omn[a], __shfl_xor_sync(0xffffffffu, omn[a], o));
+                omx[a] = max(omx[a], __shfl_xor_sync(0xffffffffu, omx[a], o));
+            }
+        if (lane != 0) continue;
         const int cl = nc > 1 ? pclus[order[r.x]] : 0;
         gclus[g] = cl;
         const double h = cc[cl].h;
-        double mn[3] = {INFINITY, INFINITY, INFINITY};
-        double mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int k = r.x; k < r.x + r.y; ++k)
+        double mn[3], mx[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                double x = xs[(size_t)a * n + k];
-                mn[a] = fmin(mn[a], x);
-                mx[a] = fmax(mx[a], x);
-            }
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = unord64(omn[a]);
+            mx[a] = unord64(omx[a]);
+        }
         float c[3];
         double R2 = 0.0, cabs = 0.0;
 #pragma unroll
@@ -816,7 +833,7 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
                                                     c->cf2, c->st);
     k_groups<<<grid_small, TB, 0, s>>>(c->p.n_group, (int)c->cap_groups,
                                         c->node, c->parent, c->grange, c->st);
-    k_group_box<<<grid_small, TB, 0, s>>>(c->grange, c->xs, n, nc, c->order,
+    k_group_box<<<c->sms * 16, TB, 0, s>>>(c->grange, c->xs, n, nc, c->order,
                                            c->pclus, c->cc, c->gclus, c->gmin,
                                            c->gmax, c->gctr, c->st);
     k_group_order<<<1, OB, 0, s>>>(n, c->grange, c->order, c->pgroup, c->gcost,
