@@ -131,7 +131,7 @@ int ensure_clusters(p3t_ctx *c, int nc)
     int64_t d = 0;
     P3T_TRY(grow(c->clus_off, d, cap + 1, sizeof(int64_t)));
     P3T_TRY(grow(c->cc, d, cap, sizeof(ClusterConsts)));
-    P3T_TRY(grow(c->clus_box, d, 4 * (int64_t)cap, sizeof(double)));
+    P3T_TRY(grow(c->clus_box, d, 8 * (int64_t)cap, sizeof(double)));
     c->cap_clus = cap;
     return P3T_OK;
 }

@@ -151,7 +151,7 @@ struct p3t_ctx {
     double *clus_par;        // host [3][nclus]: r_out, eps, h (ensemble)
     int64_t *clus_off;       // device [nclus + 1]
     ClusterConsts *cc;       // device [nclus]
-    double *clus_box;        // device [nclus][4]: lo xyz, side
+    double *clus_box;        // device [nclus][8]: lo xyz, side, RN(1/side) 2^21, pad
     int *pclus;              // device [cap_n]: cluster of each original index
     int *gclus;              // device [cap_groups]: cluster of each group
     int cap_pclus;

@@ -139,6 +139,7 @@ k_bbox_final(int nblk, const double *__restrict__ part, P3TDevState *st,
     }
     st->size = size;
     clus_box[3] = size;
+    clus_box[4] = __dmul_rn(__drcp_rn(size), 2097152.0);
 }
 
 // One block per cluster of an ensemble: root cube of [off[k], off[k+1])
@@ -157,8 +158,9 @@ k_bbox_seg(const long long *__restrict__ off, int n,
     if (threadIdx.x != 0) return;
     double lo[3], size;
     root_cube(mn, mx, lo, &size);
-    for (int a = 0; a < 3; ++a) clus_box[4 * k + a] = lo[a];
-    clus_box[4 * k + 3] = size;
+    for (int a = 0; a < 3; ++a) clus_box[8 * k + a] = lo[a];
+    clus_box[8 * k + 3] = size;
+    clus_box[8 * k + 4] = __dmul_rn(__drcp_rn(size), 2097152.0);
 }
 
 // Cluster of every particle (original index) of an ensemble.
@@ -181,19 +183,39 @@ k_cluster_ids(int n, int nc, const long long *__restrict__ off,
 
 // ---------------------------------------------------------------- keys ----
 // floor(((x - lo) / size) 2^21), each operation rounded once, clamped to
-// [0, 2^21 - 1].  The quotient is formed as t (1/size): it differs from the
-// rounded quotient by at most 4 ulp, i.e. by less than 2^-30 after the
-// scaling by 2^21, so the floor is the same unless the scaled value lies
-// within 2^-28 of an integer; there (rarely) the division itself decides.
+// [0, 2^21 - 1].  The quotient is formed as v = t s21 with s21 = (1/size)
+// 2^21 (an exact scaling of the rounded reciprocal): v differs from the
+// rounded, scaled quotient by less than 2^-30, so their floors agree unless
+// v lies within 2^-28 of an integer; there (rarely) the division itself
+// decides.  The floor and the distance to the nearest integer are read from
+// the bits of v with integer operations (0 <= v < 2^21 + 1), which keeps the
+// FP64 unit to one subtraction and one multiplication per coordinate.
 __device__ __forceinline__ u64 quantise(double x, double lo, double size,
-                                        double isize)
+                                        double s21)
 {
-    const double t = __dsub_rn(x, lo);
-    double v = __dmul_rn(__dmul_rn(t, isize), 2097152.0);
-    const double f = __dsub_rn(v, floor(v));
-    if (f < 0x1p-28 || f > 1.0 - 0x1p-28)
-        v = __dmul_rn(__ddiv_rn(t, size), 2097152.0);
-    long long q = __double2ll_rd(v);
+    const double t = __dsub_rn(x, lo);  // >= 0: lo is the minimum
+    const double v = __dmul_rn(t, s21);
+    const long long b = __double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    long long q;
+    bool near;
+    if (b <= 0) {  // +0 or -0
+        q = 0;
+        near = true;
+    } else if (e < 0) {  // (0, 1)
+        q = 0;
+        near = v < 0x1p-28 || v > 1.0 - 0x1p-28;
+    } else if (e >= 21) {  // the exact quotient is below 2^21 and v below 2^21 + 1
+        q = 2097151;
+        near = false;
+    } else {
+        const int sh = 52 - e;  // fraction bits: 32 .. 52
+        const long long m = (b & ((1LL << 52) - 1)) | (1LL << 52);
+        q = m >> sh;
+        const long long fb = m & ((1LL << sh) - 1), lim = 1LL << (sh - 28);
+        near = fb < lim || fb > (1LL << sh) - lim;
+    }
+    if (near) q = __double2ll_rd(__dmul_rn(__ddiv_rn(t, size), 2097152.0));
     q = q < 0 ? 0 : q;
     q = q > 2097151 ? 2097151 : q;
     return (u64)q;
@@ -218,12 +240,11 @@ k_keys(int n, const double *__restrict__ pos, int nc,
 {
     int i = blockIdx.x * TB + threadIdx.x;
     if (i >= n) return;
-    const double *bx = clus_box + 4 * (nc > 1 ? pclus[i] : 0);
-    const double size = bx[3];
-    const double isize = __drcp_rn(size);  // once per warp in a single cluster
-    u64 qx = quantise(pos[i], bx[0], size, isize);
-    u64 qy = quantise(pos[(size_t)n + i], bx[1], size, isize);
-    u64 qz = quantise(pos[2 * (size_t)n + i], bx[2], size, isize);
+    const double *bx = clus_box + 8 * (nc > 1 ? pclus[i] : 0);
+    const double size = bx[3], s21 = bx[4];
+    u64 qx = quantise(pos[i], bx[0], size, s21);
+    u64 qy = quantise(pos[(size_t)n + i], bx[1], size, s21);
+    u64 qz = quantise(pos[2 * (size_t)n + i], bx[2], size, s21);
     key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     idx[i] = i;
 }

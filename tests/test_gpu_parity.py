@@ -203,6 +203,43 @@ def test_exact_distance_ties(cuda):
     assert np.array_equal(ngb[0], off_o) and np.array_equal(ngb[1], idx_o)
 
 
+def test_keys_on_quantisation_boundaries(cuda):
+    """Coordinates on, and up to 3 ulp either side of, the boundaries of the
+    2^21 quantisation cells of a cube whose side makes the GPU's product
+    (x - lo) (2^21 / side) and the definition's quotient floor differently
+    for some of them: the division must decide there.  Keys are compared bit
+    for bit with the oracle."""
+    rng = np.random.default_rng(21)
+    n = 8000
+    ext = 1.4376431999070005
+    side = ext * (1.0 + 2.0 ** -20)
+    pos = rng.uniform(0.0, ext, size=(n, 3))
+    pos[0] = 0.0
+    pos[1] = ext  # extent ext on every axis, lo = 0
+    k = rng.integers(1, 2 ** 21 - 1, size=n - 2)
+    x = k * side / 2.0 ** 21
+    for _ in range(3):  # move each coordinate by -3 .. +3 ulp
+        step = rng.integers(-1, 2, size=n - 2)
+        x = np.where(step < 0, np.nextafter(x, -1.0),
+                     np.where(step > 0, np.nextafter(x, 2.0), x))
+    x = np.clip(x, 0.0, ext)
+    pos[2:, 0] = x
+    pos[2:, 1] = np.roll(x, 17)
+    m = np.full(n, 1.0 / n)
+    p = _params(theta=0.5, r_out=0.01, eps=1e-3)
+    ctx, _, _, _ = gpu_run(pos, m, p, neighbours=False)
+    t = oracle.Tree(pos, m, n_leaf=p.n_leaf, n_group=p.n_group)
+    _, size_g = ctx.root()
+    assert size_g == side
+    key_g, _ = ctx.order()
+    key_o, _ = t.particles()
+    assert np.array_equal(key_g, key_o)
+    # cases where the product and the quotient floor differently do occur
+    q_div = np.floor((x / side) * 2.0 ** 21)
+    q_mul = np.floor((x * (1.0 / side)) * 2.0 ** 21)
+    assert np.count_nonzero(q_div != q_mul) > 20
+
+
 def test_empty_input(cuda):
     import torch
     from paper_1506_04553_b300 import Context
