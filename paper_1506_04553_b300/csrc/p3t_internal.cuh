@@ -24,6 +24,8 @@
 
 #define P3T_MAX_LEVEL 21
 #define P3T_WARP 32
+// leaf sizes 0..64 and larger: bins of the size-ordered leaf list
+#define P3T_LEAF_BINS 66
 // neighbour rows up to this length are kept by the counting walk
 #define P3T_NGB_SLOTS 8
 // Hard step: components are ordered in 32 level buckets x 33 size classes;
@@ -48,6 +50,8 @@ struct P3TDevState {
     int pad0;
     int level_start[P3T_MAX_LEVEL + 3];
     int novf;           // groups listed in ngb_ovf
+    int leaf_bin[P3T_LEAF_BINS];   // leaves per size (sizes > 64 share the last)
+    int leaf_fill[P3T_LEAF_BINS];  // fill counters of the size-ordered leaf list
     int nleaf;          // leaves listed by the split (leaf_list)
     int nint;           // split cells listed by the split (int_list)
     int int_start[P3T_MAX_LEVEL + 2];  // int_list range of each level
@@ -117,6 +121,7 @@ struct p3t_ctx {
     int4 *node;
     int *parent;
     int *leaf_list, *int_list;  // leaves; split cells grouped by level
+    int *leaf_sorted;           // leaves, largest first
     double *cM, *ccom, *cQ, *cbmin, *cbmax;
     float4 *wmin, *wmax, *cf0, *cf1, *cf2;
     // groups

@@ -297,6 +297,7 @@ __global__ void k_tree_init(int nc, const long long *__restrict__ off,
     st->nleaf = 0;
     st->nint = 0;
     for (int L = 0; L < P3T_MAX_LEVEL + 2; ++L) st->int_start[L] = 0;
+    for (int b = 0; b < P3T_LEAF_BINS; ++b) st->leaf_bin[b] = st->leaf_fill[b] = 0;
 }
 
 __device__ __forceinline__ int digit_at(u64 key, int L)
@@ -457,6 +458,58 @@ k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
             st->blocks_done = 0;
             __threadfence();
         }
+    }
+}
+
+// ------------------------------------------------------- leaf ordering ----
+// The leaves, largest first (a counting sort by size): the leaf moments take
+// one thread per leaf, and a warp of equal sizes runs no idle iterations.
+__device__ __forceinline__ int leaf_bin(int count)
+{
+    return P3T_LEAF_BINS - 1 - (count < P3T_LEAF_BINS - 1 ? count : P3T_LEAF_BINS - 1);
+}
+
+__global__ void __launch_bounds__(TB)
+k_leaf_hist(const int *__restrict__ leaf_list, const int4 *__restrict__ node,
+            P3TDevState *st)
+{
+    __shared__ int h[P3T_LEAF_BINS];
+    for (int b = threadIdx.x; b < P3T_LEAF_BINS; b += TB) h[b] = 0;
+    __syncthreads();
+    const int nl = st->error ? 0 : st->nleaf;
+    for (int q = blockIdx.x * TB + threadIdx.x; q < nl; q += gridDim.x * TB)
+        atomicAdd(&h[leaf_bin(node[leaf_list[q]].y)], 1);
+    __syncthreads();
+    for (int b = threadIdx.x; b < P3T_LEAF_BINS; b += TB)
+        if (h[b]) atomicAdd(&st->leaf_bin[b], h[b]);
+}
+
+__global__ void __launch_bounds__(TB)
+k_leaf_scatter(const int *__restrict__ leaf_list, const int4 *__restrict__ node,
+               int *__restrict__ leaf_sorted, P3TDevState *st)
+{
+    __shared__ int start[P3T_LEAF_BINS], cnt[P3T_LEAF_BINS], base[P3T_LEAF_BINS];
+    const int nl = st->error ? 0 : st->nleaf;
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < P3T_LEAF_BINS; ++b) {
+            start[b] = run;
+            run += st->leaf_bin[b];
+        }
+    }
+    for (int q0 = blockIdx.x * TB; q0 < nl; q0 += gridDim.x * TB) {
+        for (int b = threadIdx.x; b < P3T_LEAF_BINS; b += TB) cnt[b] = 0;
+        __syncthreads();
+        const int q = q0 + threadIdx.x;
+        const int c = q < nl ? leaf_list[q] : -1;
+        const int b = c >= 0 ? leaf_bin(node[c].y) : 0;
+        const int rk = c >= 0 ? atomicAdd(&cnt[b], 1) : 0;
+        __syncthreads();
+        for (int k = threadIdx.x; k < P3T_LEAF_BINS; k += TB)
+            if (cnt[k]) base[k] = start[k] + atomicAdd(&st->leaf_fill[k], cnt[k]);
+        __syncthreads();
+        if (c >= 0) leaf_sorted[base[b] + rk] = c;
+        __syncthreads();
     }
 }
 
@@ -678,7 +731,9 @@ k_groups(int ng, int gcap, const int4 *__restrict__ node,
 // Group boxes (FP32 outward), relative origin and neighbour screening radius.
 // gmin.w = hs2: squared screening radius; any pair of the group with
 // |x_i - x_j| < h has an FP32 group-relative r^2 below hs2.
-__global__ void __launch_bounds__(TB)
+constexpr int GB = 1024;  // k_group_box: one warp per group, 32 groups per block
+
+__global__ void __launch_bounds__(GB)
 k_group_box(const int2 *__restrict__ grange, const double *__restrict__ xs,
             int n, int nc, const int *__restrict__ order,
             const int *__restrict__ pclus, const ClusterConsts *__restrict__ cc,
@@ -686,56 +741,76 @@ k_group_box(const int2 *__restrict__ grange, const double *__restrict__ xs,
             float4 *__restrict__ gmax, float4 *__restrict__ gctr,
             const P3TDevState *st)
 {
+    __shared__ long long sbox[GB / 32][6];
     if (st->error) return;
     const int G = st->ngroup;  // <= capacity (k_groups checks)
-    const int lane = threadIdx.x & 31;
-    const int wg = (blockIdx.x * TB + threadIdx.x) >> 5, nw = gridDim.x * (TB / 32);
-    // one warp per group: lanes over its particles, box on integer images
-    for (int g = wg; g < G; g += nw) {
-        const int2 r = grange[g];
-        long long omn[3] = {ORD_HI, ORD_HI, ORD_HI}, omx[3] = {ORD_LO, ORD_LO, ORD_LO};
-        for (int k = r.x + lane; k < r.x + r.y; k += 32)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // each warp the box of one group (lanes over its particles, integer
+    // images); then warp 0 finishes the block's 32 groups, one per lane, so
+    // that the FP64 tail is one set of instructions for 32 groups
+    for (int g0 = blockIdx.x * (GB / 32); g0 < G; g0 += gridDim.x * (GB / 32)) {
+        if (g0 + w < G) {
+            const int2 rw = grange[g0 + w];
+            long long omn[3] = {ORD_HI, ORD_HI, ORD_HI}, omx[3] = {ORD_LO, ORD_LO, ORD_LO};
+            for (int k = rw.x + lane; k < rw.x + rw.y; k += 32)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const long long o = ord64(xs[(size_t)a * n + k]);
+                    omn[a] = min(omn[a], o);
+                    omx[a] = max(omx[a], o);
+                }
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const long long o = ord64(xs[(size_t)a * n + k]);
-                omn[a] = min(omn[a], o);
-                omx[a] = max(omx[a], o);
+                for (int o = 16; o > 0; o >>= 1) {
+                    omn[a] = min(omn[a], __shfl_xor_sync(0xffffffffu, omn[a], o));
+                    omx[a] = max(omx[a], __shfl_xor_sync(0xffffffffu, omx[a], o));
+                }
+                if (lane == 0) {
+                    sbox[w][a] = omn[a];
+                    sbox[w][3 + a] = omx[a];
+                }
             }
+        }
+        __syncthreads();
+        if (w == 0 && g0 + lane < G) {
+            const int g = g0 + lane;
+            const int2 r = grange[g];
+            long long omn[3], omx[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-            for (int o = 16; o > 0; o >>= 1) {
-                omn[a] = min(omn[a], __shfl_xor_sync(0xffffffffu, omn[a], o));
-                omx[a] = max(omx[a], __shfl_xor_sync(0xffffffffu, omx[a], o));
+            for (int a = 0; a < 3; ++a) {
+                omn[a] = sbox[lane][a];
+                omx[a] = sbox[lane][3 + a];
             }
-        if (lane != 0) continue;
-        const int cl = nc > 1 ? pclus[order[r.x]] : 0;
-        gclus[g] = cl;
-        const double h = cc[cl].h;
-        double mn[3], mx[3];
+            const int cl = nc > 1 ? pclus[order[r.x]] : 0;
+            gclus[g] = cl;
+            const double h = cc[cl].h;
+            double mn[3], mx[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            mn[a] = unord64(omn[a]);
-            mx[a] = unord64(omx[a]);
-        }
-        float c[3];
-        double R2 = 0.0, cabs = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                mn[a] = unord64(omn[a]);
+                mx[a] = unord64(omx[a]);
+            }
+            float c[3];
+            double R2 = 0.0, cabs = 0.0;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            c[a] = __double2float_rn(0.5 * (mn[a] + mx[a]));
-            double e = fmax(fabs(mx[a] - (double)c[a]), fabs(mn[a] - (double)c[a]));
-            R2 += e * e;
-            cabs = fmax(cabs, fabs((double)c[a]));
+            for (int a = 0; a < 3; ++a) {
+                c[a] = __double2float_rn(0.5 * (mn[a] + mx[a]));
+                double e = fmax(fabs(mx[a] - (double)c[a]), fabs(mn[a] - (double)c[a]));
+                R2 += e * e;
+                cabs = fmax(cabs, fabs((double)c[a]));
+            }
+            double R = sqrt(R2);
+            // screening margin: 2^-14 h (R + h) + 2^-30 h |c| (>> the FP32
+            // rounding of group-relative coordinates and of r^2)
+            double hs2 = h * h + 0x1p-14 * h * (R + h) + 0x1p-30 * h * cabs;
+            gmin[g] = make_float4(__double2float_rd(mn[0]), __double2float_rd(mn[1]),
+                                  __double2float_rd(mn[2]),
+                                  __double2float_ru(hs2));
+            gmax[g] = make_float4(__double2float_ru(mx[0]), __double2float_ru(mx[1]),
+                                  __double2float_ru(mx[2]), 0.0f);
+            gctr[g] = make_float4(c[0], c[1], c[2], 0.0f);
         }
-        double R = sqrt(R2);
-        // screening margin: 2^-14 h (R + h) + 2^-30 h |c| (>> the FP32
-        // rounding of group-relative coordinates and of r^2)
-        double hs2 = h * h + 0x1p-14 * h * (R + h) + 0x1p-30 * h * cabs;
-        gmin[g] = make_float4(__double2float_rd(mn[0]), __double2float_rd(mn[1]),
-                              __double2float_rd(mn[2]),
-                              __double2float_ru(hs2));
-        gmax[g] = make_float4(__double2float_ru(mx[0]), __double2float_ru(mx[1]),
-                              __double2float_ru(mx[2]), 0.0f);
-        gctr[g] = make_float4(c[0], c[1], c[2], 0.0f);
+        __syncthreads();  // sbox is rewritten by the next round
     }
 }
 
@@ -840,8 +915,11 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
         k_tree_split<<<c->sms * 8, TB, 0, s>>>(L, c->p.n_leaf, cap, c->key_a,
                                                 c->node, c->parent, c->leaf_list,
                                                 c->int_list, c->st);
+    k_leaf_hist<<<c->sms * 4, TB, 0, s>>>(c->leaf_list, c->node, c->st);
+    k_leaf_scatter<<<c->sms * 4, TB, 0, s>>>(c->leaf_list, c->node,
+                                              c->leaf_sorted, c->st);
     k_moments<true><<<c->sms * 8, TB, 0, s>>>(0, c->xs, c->ms, n, c->node,
-                                               c->leaf_list, c->int_list,
+                                               c->leaf_sorted, c->int_list,
                                                c->cM, c->ccom, c->cQ, c->cbmin,
                                                c->cbmax, c->wmin, c->wmax,
                                                c->cf0, c->cf1, c->cf2, c->st);
@@ -854,14 +932,14 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
                                                     c->cf2, c->st);
     k_groups<<<grid_small, TB, 0, s>>>(c->p.n_group, (int)c->cap_groups,
                                         c->node, c->parent, c->grange, c->st);
-    k_group_box<<<c->sms * 16, TB, 0, s>>>(c->grange, c->xs, n, nc, c->order,
+    k_group_box<<<c->sms * 2, GB, 0, s>>>(c->grange, c->xs, n, nc, c->order,
                                            c->pclus, c->cc, c->gclus, c->gmin,
                                            c->gmax, c->gctr, c->st);
     k_group_order<<<1, OB, 0, s>>>(n, c->grange, c->order, c->pgroup, c->gcost,
                                    c->gperm, c->st);
-    // bbox 2, keys, gather, init, 21 splits, 22 moment levels, groups, boxes,
-    // order
-    p3t_count_launches(2 + 1 + 1 + 1 + P3T_MAX_LEVEL + (P3T_MAX_LEVEL + 1) + 3);
+    // bbox 2, keys, gather, init, 21 splits, leaf order 2, 22 moment levels,
+    // groups, boxes, order
+    p3t_count_launches(2 + 1 + 1 + 1 + P3T_MAX_LEVEL + 2 + (P3T_MAX_LEVEL + 1) + 3);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
 }
