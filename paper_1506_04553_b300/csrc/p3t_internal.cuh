@@ -50,6 +50,8 @@ struct P3TDevState {
     int pad0;
     int level_start[P3T_MAX_LEVEL + 3];
     int novf;           // groups listed in ngb_ovf
+    int gord_cnt[256];  // groups per work bucket (group order)
+    int gord_fill[256]; // fill counters of the group order
     int leaf_bin[P3T_LEAF_BINS];   // leaves per size (sizes > 64 share the last)
     int leaf_fill[P3T_LEAF_BINS];  // fill counters of the size-ordered leaf list
     int nleaf;          // leaves listed by the split (leaf_list)

@@ -298,6 +298,7 @@ __global__ void k_tree_init(int nc, const long long *__restrict__ off,
     st->nint = 0;
     for (int L = 0; L < P3T_MAX_LEVEL + 2; ++L) st->int_start[L] = 0;
     for (int b = 0; b < P3T_LEAF_BINS; ++b) st->leaf_bin[b] = st->leaf_fill[b] = 0;
+    for (int b = 0; b < 256; ++b) st->gord_cnt[b] = st->gord_fill[b] = 0;
 }
 
 __device__ __forceinline__ int digit_at(u64 key, int L)
@@ -820,8 +821,7 @@ k_group_box(const int2 *__restrict__ grange, const double *__restrict__ xs,
 // its first particle at the last force evaluation of the same n; groups are
 // bucketed by log2 of that estimate (8 buckets per octave) and written out
 // bucket by bucket, the order inside a bucket being arbitrary.  Without a
-// recorded evaluation the order is the identity.  One block.
-constexpr int OB = 1024;
+// recorded evaluation the order is the identity.
 constexpr int NBUCKET = 256;
 
 __device__ __forceinline__ int order_bucket(int g, const int2 *grange,
@@ -836,45 +836,69 @@ __device__ __forceinline__ int order_bucket(int g, const int2 *grange,
     return NBUCKET - 1 - b;  // descending work
 }
 
-__global__ void __launch_bounds__(OB)
+// Counting sort of the groups by bucket: histogram over many blocks, then
+// every block scatters its chunk of groups (positions reserved per bucket
+// with one global atomic per bucket and block).
+__global__ void __launch_bounds__(TB)
+k_group_hist(int n, const int2 *__restrict__ grange, const int *__restrict__ order,
+             const int *__restrict__ pgroup, const float *__restrict__ gcost,
+             P3TDevState *st)
+{
+    __shared__ int h[NBUCKET];
+    if (st->error) return;
+    const int G = st->ngroup, cg = st->cost_groups;
+    if (st->cost_n != n || cg <= 0) return;  // identity order
+    for (int b = threadIdx.x; b < NBUCKET; b += TB) h[b] = 0;
+    __syncthreads();
+    for (int g = blockIdx.x * TB + threadIdx.x; g < G; g += gridDim.x * TB)
+        atomicAdd(&h[order_bucket(g, grange, order, pgroup, gcost, cg)], 1);
+    __syncthreads();
+    for (int b = threadIdx.x; b < NBUCKET; b += TB)
+        if (h[b]) atomicAdd(&st->gord_cnt[b], h[b]);
+}
+
+__global__ void __launch_bounds__(TB)
 k_group_order(int n, const int2 *__restrict__ grange,
               const int *__restrict__ order, const int *__restrict__ pgroup,
               const float *__restrict__ gcost, int *__restrict__ gperm,
-              const P3TDevState *st)
+              P3TDevState *st)
 {
-    __shared__ int cnt[NBUCKET];
-    __shared__ int start[NBUCKET];
+    __shared__ int start[NBUCKET], cnt[NBUCKET], base[NBUCKET];
     if (st->error) return;
     const int G = st->ngroup;  // <= capacity (k_groups checks)
     const int cg = st->cost_groups;
-    const int tid = threadIdx.x;
     if (st->cost_n != n || cg <= 0) {
-        for (int g = tid; g < G; g += OB) gperm[g] = g;
+        for (int g = blockIdx.x * TB + threadIdx.x; g < G; g += gridDim.x * TB)
+            gperm[g] = g;
         return;
     }
-    for (int b = tid; b < NBUCKET; b += OB) cnt[b] = 0;
-    __syncthreads();
-    for (int g = tid; g < G; g += OB)
-        atomicAdd(&cnt[order_bucket(g, grange, order, pgroup, gcost, cg)], 1);
-    __syncthreads();
-    if (tid < 32) {  // exclusive scan of the 256 counts, 8 per lane
+    if (threadIdx.x < 32) {  // exclusive scan of the 256 counts, 8 per lane
+        const int lane = threadIdx.x;
         int v[NBUCKET / 32], sum = 0;
 #pragma unroll
         for (int q = 0; q < NBUCKET / 32; ++q) {
-            v[q] = cnt[tid * (NBUCKET / 32) + q];
+            v[q] = st->gord_cnt[lane * (NBUCKET / 32) + q];
             sum += v[q];
         }
         int off = warp_incl_scan(sum) - sum;
 #pragma unroll
         for (int q = 0; q < NBUCKET / 32; ++q) {
-            start[tid * (NBUCKET / 32) + q] = off;
+            start[lane * (NBUCKET / 32) + q] = off;
             off += v[q];
         }
     }
-    __syncthreads();
-    for (int g = tid; g < G; g += OB) {
-        const int b = order_bucket(g, grange, order, pgroup, gcost, cg);
-        gperm[atomicAdd(&start[b], 1)] = g;
+    for (int g0 = blockIdx.x * TB; g0 < G; g0 += gridDim.x * TB) {
+        for (int b = threadIdx.x; b < NBUCKET; b += TB) cnt[b] = 0;
+        __syncthreads();
+        const int g = g0 + threadIdx.x;
+        const int b = g < G ? order_bucket(g, grange, order, pgroup, gcost, cg) : 0;
+        const int rk = g < G ? atomicAdd(&cnt[b], 1) : 0;
+        __syncthreads();
+        for (int k = threadIdx.x; k < NBUCKET; k += TB)
+            if (cnt[k]) base[k] = start[k] + atomicAdd(&st->gord_fill[k], cnt[k]);
+        __syncthreads();
+        if (g < G) gperm[base[b] + rk] = g;
+        __syncthreads();
     }
 }
 
@@ -935,11 +959,13 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     k_group_box<<<c->sms * 2, GB, 0, s>>>(c->grange, c->xs, n, nc, c->order,
                                            c->pclus, c->cc, c->gclus, c->gmin,
                                            c->gmax, c->gctr, c->st);
-    k_group_order<<<1, OB, 0, s>>>(n, c->grange, c->order, c->pgroup, c->gcost,
-                                   c->gperm, c->st);
+    k_group_hist<<<grid_small, TB, 0, s>>>(n, c->grange, c->order, c->pgroup,
+                                            c->gcost, c->st);
+    k_group_order<<<grid_small, TB, 0, s>>>(n, c->grange, c->order, c->pgroup,
+                                             c->gcost, c->gperm, c->st);
     // bbox 2, keys, gather, init, 21 splits, leaf order 2, 22 moment levels,
-    // groups, boxes, order
-    p3t_count_launches(2 + 1 + 1 + 1 + P3T_MAX_LEVEL + 2 + (P3T_MAX_LEVEL + 1) + 3);
+    // groups, boxes, order 2
+    p3t_count_launches(2 + 1 + 1 + 1 + P3T_MAX_LEVEL + 2 + (P3T_MAX_LEVEL + 1) + 4);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
 }
