@@ -205,8 +205,8 @@ int ensure_cells(p3t_ctx *c, int64_t want)
     P3T_TRY(grow(c->node, d, cap, sizeof(int4)));
     P3T_TRY(grow(c->parent, d, cap, sizeof(int)));
     P3T_TRY(grow(c->leaf_list, d, cap, sizeof(int)));
-    P3T_TRY(grow(c->int_list, d, cap, sizeof(int)));
     P3T_TRY(grow(c->leaf_sorted, d, cap, sizeof(int)));
+    P3T_TRY(grow(c->cpend, d, cap, sizeof(int)));
     P3T_TRY(grow(c->cM, d, cap, sizeof(double)));
     P3T_TRY(grow(c->ccom, d, 3 * cap, sizeof(double)));
     P3T_TRY(grow(c->cQ, d, 6 * cap, sizeof(double)));
@@ -280,7 +280,7 @@ void free_all(p3t_ctx *c)
                     c->gctr, c->lcnt, c->loff, c->list[0], c->list[1],
                     c->list[2], c->scan_part, c->red_part, c->cadj,
                     c->clus_off, c->cc, c->clus_box, c->pclus, c->gclus,
-                    c->gperm, c->gcost, c->pgroup, c->leaf_list, c->int_list, c->leaf_sorted, c->hparent, c->hcsize,
+                    c->gperm, c->gcost, c->pgroup, c->leaf_list, c->leaf_sorted, c->cpend, c->hparent, c->hcsize,
                     c->hcfill, c->hmember, c->hlev, c->hcstart, c->ht, c->ha,
                     c->hj, c->hxp, c->hvp, c->hroots, c->hloc, c->hbucket};
     for (void *p : ptrs)

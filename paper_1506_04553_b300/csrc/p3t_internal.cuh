@@ -55,8 +55,6 @@ struct P3TDevState {
     int leaf_bin[P3T_LEAF_BINS];   // leaves per size (sizes > 64 share the last)
     int leaf_fill[P3T_LEAF_BINS];  // fill counters of the size-ordered leaf list
     int nleaf;          // leaves listed by the split (leaf_list)
-    int nint;           // split cells listed by the split (int_list)
-    int int_start[P3T_MAX_LEVEL + 2];  // int_list range of each level
     long long tot[3];   // list totals: pc, ppn, ppf
     long long int_pc;   // particle-cell interactions
     long long int_pp;   // particle-particle interactions
@@ -122,8 +120,9 @@ struct p3t_ctx {
     // cells
     int4 *node;
     int *parent;
-    int *leaf_list, *int_list;  // leaves; split cells grouped by level
+    int *leaf_list;             // leaves, as the split found them
     int *leaf_sorted;           // leaves, largest first
+    int *cpend;                 // children whose moments are done (bottom-up pass)
     double *cM, *ccom, *cQ, *cbmin, *cbmax;
     float4 *wmin, *wmax, *cf0, *cf1, *cf2;
     // groups

@@ -11,7 +11,8 @@
 //   split     level by level: a cell of level L < 21 holding more than n_leaf
 //             particles gets its non-empty octants (found by binary search
 //             on the sorted keys) as children, contiguous and in Morton order
-//   moments   level by level from the deepest: M, centre of mass, traceless
+//   moments   bottom-up in one launch (each internal cell by the last of
+//             its children to finish): M, centre of mass, traceless
 //             quadrupole Q_ab = sum m (3 d_a d_b - |d|^2 delta_ab) about the
 //             centre of mass, member box; leaves from their particles,
 //             internal cells from their children (parallel-axis shift) in
@@ -278,12 +279,13 @@ k_gather(int n, const int *__restrict__ sidx, const double *__restrict__ pos,
 // One root per cluster: cells 0 .. nc-1 are the roots, in cluster order
 // (the sort keeps clusters contiguous and in order).
 __global__ void k_tree_init(int nc, const long long *__restrict__ off,
-                            int4 *node, int *parent, P3TDevState *st)
+                            int4 *node, int *parent, int *cpend, P3TDevState *st)
 {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nc;
          k += gridDim.x * blockDim.x) {
         node[k] = make_int4((int)off[k], (int)(off[k + 1] - off[k]), -1, 0);
         parent[k] = -1;
+        cpend[k] = 0;
     }
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     st->ncell = nc;
@@ -295,8 +297,6 @@ __global__ void k_tree_init(int nc, const long long *__restrict__ off,
     st->level_start[0] = 0;
     for (int L = 1; L < P3T_MAX_LEVEL + 3; ++L) st->level_start[L] = nc;
     st->nleaf = 0;
-    st->nint = 0;
-    for (int L = 0; L < P3T_MAX_LEVEL + 2; ++L) st->int_start[L] = 0;
     for (int b = 0; b < P3T_LEAF_BINS; ++b) st->leaf_bin[b] = st->leaf_fill[b] = 0;
     for (int b = 0; b < 256; ++b) st->gord_cnt[b] = st->gord_fill[b] = 0;
 }
@@ -367,8 +367,8 @@ __device__ __forceinline__ void warp_scan_digits(const u64 *__restrict__ key,
 // children at the deepest level are never split and join the leaf list.
 __device__ __forceinline__ void emit_children(int c, int L, int cap,
                                               const int *b, int4 *node,
-                                              int *parent, int *leaf_list,
-                                              P3TDevState *st)
+                                              int *parent, int *cpend,
+                                              int *leaf_list, P3TDevState *st)
 {
     int k = 0;
 #pragma unroll
@@ -385,6 +385,7 @@ __device__ __forceinline__ void emit_children(int c, int L, int cap,
         if (b[d + 1] > b[d]) {
             node[base + j] = make_int4(b[d], b[d + 1] - b[d], -1, (L + 1) << 8);
             parent[base + j] = c;
+            cpend[base + j] = 0;
             if (L + 1 >= P3T_MAX_LEVEL) leaf_list[atomicAdd(&st->nleaf, 1)] = base + j;
             ++j;
         }
@@ -396,13 +397,13 @@ __device__ __forceinline__ void emit_children(int c, int L, int cap,
 constexpr int BIG_CELL = 2048;  // above: 32-ary searches; below: one scan
 
 // Level L in two passes over its cells: one thread per cell files the
-// cells holding at most n_leaf particles in the leaf list and the others in
-// the list of split cells (one aggregated append per warp each); then one
-// warp per split cell finds the child boundaries.
+// cells holding at most n_leaf particles in the leaf list (one aggregated
+// append per warp); then one warp per cell to split finds the child
+// boundaries.
 __global__ void __launch_bounds__(TB)
 k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
              int4 *__restrict__ node, int *__restrict__ parent,
-             int *__restrict__ leaf_list, int *__restrict__ int_list,
+             int *__restrict__ cpend, int *__restrict__ leaf_list,
              P3TDevState *st)
 {
     __shared__ int sbuf[TB / 32][9];
@@ -417,16 +418,10 @@ k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
         const int cl = base + lane;
         const int cnt = cl < end ? node[cl].y : -1;
         const unsigned lm = __ballot_sync(full, cnt >= 0 && cnt <= n_leaf);
-        const unsigned sm = __ballot_sync(full, cnt > n_leaf);
-        int lb = 0, ib = 0;
-        if (lane == 0) {
-            if (lm) lb = atomicAdd(&st->nleaf, __popc(lm));
-            if (sm) ib = atomicAdd(&st->nint, __popc(sm));
-        }
+        int lb = 0;
+        if (lane == 0 && lm) lb = atomicAdd(&st->nleaf, __popc(lm));
         lb = __shfl_sync(full, lb, 0);
-        ib = __shfl_sync(full, ib, 0);
         if ((lm >> lane) & 1u) leaf_list[lb + __popc(lm & lt)] = cl;
-        if ((sm >> lane) & 1u) int_list[ib + __popc(sm & lt)] = cl;
     }
     for (int c = beg + wg; c < end && !stop; c += nw) {
         const int4 nd = node[c];
@@ -443,7 +438,7 @@ k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
             for (int d = 1; d < 8; ++d) b[d] = sb[d];
             __syncwarp();  // sb is rewritten by the next cell
         }
-        if (lane == 0) emit_children(c, L, cap, b, node, parent, leaf_list, st);
+        if (lane == 0) emit_children(c, L, cap, b, node, parent, cpend, leaf_list, st);
     }
     // the last block to finish closes the next level's range
     __syncthreads();
@@ -454,7 +449,6 @@ k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
             int nc = atomicAdd(&st->ncell, 0);
             if (nc > cap) nc = cap;
             st->level_start[L + 2] = nc;
-            st->int_start[L + 1] = atomicAdd(&st->nint, 0);
             if (nc > st->level_start[L + 1]) st->max_level = L + 1;
             st->blocks_done = 0;
             __threadfence();
@@ -538,153 +532,178 @@ __device__ __forceinline__ void write_records(
                          __double2float_rn(Q[4]), __double2float_rn(Q[5]));
 }
 
-// LEAVES: every leaf of the tree in one launch (L unused); otherwise the
-// internal cells of level L, from their children.  The cells come from the
-// lists the split made, so every thread has a cell of the right kind.
-template <bool LEAVES>
+// Moments of cell c (node nd), written to the FP64 arrays and the FP32
+// records: a leaf from its particles, an internal cell from its children
+// (parallel-axis shift).  The children's records are read through L2
+// (__ldcg): another SM may have written them during this launch.
+__device__ __forceinline__ double ld(const double *p) { return __ldcg(p); }
+
+__device__ void cell_moments(int c, int4 nd, const double *__restrict__ xs,
+                             const double *__restrict__ ms, int n,
+                             double *cM, double *ccom, double *cQ,
+                             double *cbmin, double *cbmax,
+                             float4 *__restrict__ wmin, float4 *__restrict__ wmax,
+                             float4 *__restrict__ cf0, float4 *__restrict__ cf1,
+                             float4 *__restrict__ cf2)
+{
+    double M = 0.0, com[3] = {0, 0, 0}, Q[6] = {0, 0, 0, 0, 0, 0};
+    long long omn[3] = {ORD_HI, ORD_HI, ORD_HI};  // box images (ord64)
+    long long omx[3] = {ORD_LO, ORD_LO, ORD_LO};
+    const int nch = nd.w & 255;
+    if (nch == 0) {
+        // leaf: from its particles, in chunks of LCH whose loads are all
+        // issued before the sums that wait on them
+        constexpr int LCH = 8;
+        const int k0 = nd.x, k1 = nd.x + nd.y;
+        for (int kb = k0; kb < k1; kb += LCH) {
+            double pm[LCH], px[LCH], py[LCH], pz[LCH];
+#pragma unroll
+            for (int u = 0; u < LCH; ++u) {
+                const int k = kb + u < k1 ? kb + u : k0;
+                pm[u] = ms[k];
+                px[u] = xs[k];
+                py[u] = xs[(size_t)n + k];
+                pz[u] = xs[2 * (size_t)n + k];
+            }
+#pragma unroll
+            for (int u = 0; u < LCH; ++u) {
+                if (kb + u >= k1) continue;
+                M += pm[u];
+                com[0] += pm[u] * px[u];
+                com[1] += pm[u] * py[u];
+                com[2] += pm[u] * pz[u];
+                const long long ox = ord64(px[u]), oy = ord64(py[u]), oz = ord64(pz[u]);
+                omn[0] = min(omn[0], ox);
+                omn[1] = min(omn[1], oy);
+                omn[2] = min(omn[2], oz);
+                omx[0] = max(omx[0], ox);
+                omx[1] = max(omx[1], oy);
+                omx[2] = max(omx[2], oz);
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) com[a] /= M;
+        for (int kb = k0; kb < k1; kb += LCH) {
+            double pm[LCH], px[LCH], py[LCH], pz[LCH];
+#pragma unroll
+            for (int u = 0; u < LCH; ++u) {
+                const int k = kb + u < k1 ? kb + u : k0;
+                pm[u] = ms[k];
+                px[u] = xs[k];
+                py[u] = xs[(size_t)n + k];
+                pz[u] = xs[2 * (size_t)n + k];
+            }
+#pragma unroll
+            for (int u = 0; u < LCH; ++u) {
+                if (kb + u >= k1) continue;
+                const double m = pm[u];
+                const double dx = px[u] - com[0];
+                const double dy = py[u] - com[1];
+                const double dz = pz[u] - com[2];
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                Q[0] += m * (3.0 * dx * dx - d2);
+                Q[1] += m * (3.0 * dy * dy - d2);
+                Q[2] += m * (3.0 * dz * dz - d2);
+                Q[3] += m * (3.0 * dx * dy);
+                Q[4] += m * (3.0 * dx * dz);
+                Q[5] += m * (3.0 * dy * dz);
+            }
+        }
+    } else {
+        // internal: combine the children (parallel-axis shift); the
+        // (at most 8) children's records are loaded before the sums
+        double cm[8], cx[8], cy[8], cz[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int ch = nd.z + (q < nch ? q : 0);
+            cm[q] = ld(cM + ch);
+            cx[q] = ld(ccom + 3 * ch + 0);
+            cy[q] = ld(ccom + 3 * ch + 1);
+            cz[q] = ld(ccom + 3 * ch + 2);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                omn[a] = min(omn[a], ord64(ld(cbmin + 3 * ch + a)));  // repeats child 0: harmless
+                omx[a] = max(omx[a], ord64(ld(cbmax + 3 * ch + a)));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q >= nch) continue;
+            M += cm[q];
+            com[0] += cm[q] * cx[q];
+            com[1] += cm[q] * cy[q];
+            com[2] += cm[q] * cz[q];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) com[a] /= M;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q >= nch) continue;
+            const int ch = nd.z + q;
+            const double m = cm[q];
+            const double dx = cx[q] - com[0];
+            const double dy = cy[q] - com[1];
+            const double dz = cz[q] - com[2];
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            const double *qc = cQ + 6 * ch;
+            Q[0] += ld(qc + 0) + m * (3.0 * dx * dx - d2);
+            Q[1] += ld(qc + 1) + m * (3.0 * dy * dy - d2);
+            Q[2] += ld(qc + 2) + m * (3.0 * dz * dz - d2);
+            Q[3] += ld(qc + 3) + m * (3.0 * dx * dy);
+            Q[4] += ld(qc + 4) + m * (3.0 * dx * dz);
+            Q[5] += ld(qc + 5) + m * (3.0 * dy * dz);
+        }
+    }
+    double bmn[3], bmx[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        bmn[a] = unord64(omn[a]);
+        bmx[a] = unord64(omx[a]);
+    }
+    cM[c] = M;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ccom[3 * c + a] = com[a];
+        cbmin[3 * c + a] = bmn[a];
+        cbmax[3 * c + a] = bmx[a];
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) cQ[6 * c + q] = Q[q];
+    write_records(c, nd, M, com, Q, bmn, bmx, wmin, wmax, cf0, cf1, cf2);
+}
+
+// All moments in one launch, bottom-up: one thread per leaf (largest
+// first) computes the leaf, then climbs.  At each parent it counts itself
+// in (after a fence that publishes its cell); the last child to arrive
+// computes the parent from all its children, in child order, and climbs on;
+// the others stop.  Every cell is computed once, by whichever thread comes
+// last, with the same arithmetic: the result does not depend on the order.
 __global__ void __launch_bounds__(TB)
-k_moments(int L, const double *__restrict__ xs, const double *__restrict__ ms,
-          int n, const int4 *__restrict__ node,
-          const int *__restrict__ leaf_list, const int *__restrict__ int_list,
-          double *__restrict__ cM,
-          double *__restrict__ ccom, double *__restrict__ cQ,
-          double *__restrict__ cbmin, double *__restrict__ cbmax,
-          float4 *__restrict__ wmin, float4 *__restrict__ wmax,
-          float4 *__restrict__ cf0, float4 *__restrict__ cf1,
-          float4 *__restrict__ cf2, const P3TDevState *st)
+k_moments_up(const double *__restrict__ xs, const double *__restrict__ ms,
+             int n, const int4 *__restrict__ node, const int *__restrict__ parent,
+             const int *__restrict__ leaf_sorted, int *cpend, double *cM,
+             double *ccom, double *cQ, double *cbmin, double *cbmax,
+             float4 *__restrict__ wmin, float4 *__restrict__ wmax,
+             float4 *__restrict__ cf0, float4 *__restrict__ cf1,
+             float4 *__restrict__ cf2, const P3TDevState *st)
 {
     if (st->error) return;
-    const int beg = LEAVES ? 0 : st->int_start[L];
-    const int end = LEAVES ? st->nleaf : st->int_start[L + 1];
-    const int *list = LEAVES ? leaf_list : int_list;
-    for (int q = beg + blockIdx.x * TB + threadIdx.x; q < end;
-         q += gridDim.x * TB) {
-        const int c = list[q];
-        int4 nd = node[c];
-        double M = 0.0, com[3] = {0, 0, 0}, Q[6] = {0, 0, 0, 0, 0, 0};
-        long long omn[3] = {ORD_HI, ORD_HI, ORD_HI};  // box images (ord64)
-        long long omx[3] = {ORD_LO, ORD_LO, ORD_LO};
-        const int nch = nd.w & 255;
-        if (nch == 0) {
-            // leaf: from its particles, in chunks of LCH whose loads are all
-            // issued before the sums that wait on them
-            constexpr int LCH = 8;
-            const int k0 = nd.x, k1 = nd.x + nd.y;
-            for (int kb = k0; kb < k1; kb += LCH) {
-                double pm[LCH], px[LCH], py[LCH], pz[LCH];
-#pragma unroll
-                for (int u = 0; u < LCH; ++u) {
-                    const int k = kb + u < k1 ? kb + u : k0;
-                    pm[u] = ms[k];
-                    px[u] = xs[k];
-                    py[u] = xs[(size_t)n + k];
-                    pz[u] = xs[2 * (size_t)n + k];
-                }
-#pragma unroll
-                for (int u = 0; u < LCH; ++u) {
-                    if (kb + u >= k1) continue;
-                    M += pm[u];
-                    com[0] += pm[u] * px[u];
-                    com[1] += pm[u] * py[u];
-                    com[2] += pm[u] * pz[u];
-                    const long long ox = ord64(px[u]), oy = ord64(py[u]), oz = ord64(pz[u]);
-                    omn[0] = min(omn[0], ox);
-                    omn[1] = min(omn[1], oy);
-                    omn[2] = min(omn[2], oz);
-                    omx[0] = max(omx[0], ox);
-                    omx[1] = max(omx[1], oy);
-                    omx[2] = max(omx[2], oz);
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) com[a] /= M;
-            for (int kb = k0; kb < k1; kb += LCH) {
-                double pm[LCH], px[LCH], py[LCH], pz[LCH];
-#pragma unroll
-                for (int u = 0; u < LCH; ++u) {
-                    const int k = kb + u < k1 ? kb + u : k0;
-                    pm[u] = ms[k];
-                    px[u] = xs[k];
-                    py[u] = xs[(size_t)n + k];
-                    pz[u] = xs[2 * (size_t)n + k];
-                }
-#pragma unroll
-                for (int u = 0; u < LCH; ++u) {
-                    if (kb + u >= k1) continue;
-                    const double m = pm[u];
-                    const double dx = px[u] - com[0];
-                    const double dy = py[u] - com[1];
-                    const double dz = pz[u] - com[2];
-                    const double d2 = dx * dx + dy * dy + dz * dz;
-                    Q[0] += m * (3.0 * dx * dx - d2);
-                    Q[1] += m * (3.0 * dy * dy - d2);
-                    Q[2] += m * (3.0 * dz * dz - d2);
-                    Q[3] += m * (3.0 * dx * dy);
-                    Q[4] += m * (3.0 * dx * dz);
-                    Q[5] += m * (3.0 * dy * dz);
-                }
-            }
-        } else {
-            // internal: combine the children (parallel-axis shift); the
-            // (at most 8) children's records are loaded before the sums
-            double cm[8], cx[8], cy[8], cz[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int ch = nd.z + (q < nch ? q : 0);
-                cm[q] = cM[ch];
-                cx[q] = ccom[3 * ch + 0];
-                cy[q] = ccom[3 * ch + 1];
-                cz[q] = ccom[3 * ch + 2];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    omn[a] = min(omn[a], ord64(cbmin[3 * ch + a]));  // repeats child 0: harmless
-                    omx[a] = max(omx[a], ord64(cbmax[3 * ch + a]));
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (q >= nch) continue;
-                M += cm[q];
-                com[0] += cm[q] * cx[q];
-                com[1] += cm[q] * cy[q];
-                com[2] += cm[q] * cz[q];
-            }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) com[a] /= M;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                if (q >= nch) continue;
-                const int ch = nd.z + q;
-                const double m = cm[q];
-                const double dx = cx[q] - com[0];
-                const double dy = cy[q] - com[1];
-                const double dz = cz[q] - com[2];
-                const double d2 = dx * dx + dy * dy + dz * dz;
-                const double *qc = cQ + 6 * ch;
-                Q[0] += qc[0] + m * (3.0 * dx * dx - d2);
-                Q[1] += qc[1] + m * (3.0 * dy * dy - d2);
-                Q[2] += qc[2] + m * (3.0 * dz * dz - d2);
-                Q[3] += qc[3] + m * (3.0 * dx * dy);
-                Q[4] += qc[4] + m * (3.0 * dx * dz);
-                Q[5] += qc[5] + m * (3.0 * dy * dz);
-            }
+    const int nl = st->nleaf;
+    for (int q = blockIdx.x * TB + threadIdx.x; q < nl; q += gridDim.x * TB) {
+        int c = leaf_sorted[q];
+        cell_moments(c, node[c], xs, ms, n, cM, ccom, cQ, cbmin, cbmax, wmin,
+                     wmax, cf0, cf1, cf2);
+        for (int up = 0; up <= P3T_MAX_LEVEL; ++up) {  // at most one per level
+            const int p = parent[c];
+            if (p < 0) break;
+            const int4 np = node[p];
+            __threadfence();  // this cell's records before the count
+            if (atomicAdd(cpend + p, 1) != (np.w & 255) - 1) break;
+            __threadfence();  // the siblings' records after it
+            cell_moments(p, np, xs, ms, n, cM, ccom, cQ, cbmin, cbmax, wmin,
+                         wmax, cf0, cf1, cf2);
+            c = p;
         }
-        double bmn[3], bmx[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            bmn[a] = unord64(omn[a]);
-            bmx[a] = unord64(omx[a]);
-        }
-        cM[c] = M;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            ccom[3 * c + a] = com[a];
-            cbmin[3 * c + a] = bmn[a];
-            cbmax[3 * c + a] = bmx[a];
-        }
-#pragma unroll
-        for (int q = 0; q < 6; ++q) cQ[6 * c + q] = Q[q];
-        write_records(c, nd, M, com, Q, bmn, bmx, wmin, wmax, cf0, cf1, cf2);
     }
 }
 
@@ -932,28 +951,21 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     k_gather<<<nb, TB, 0, s>>>(n, c->idx_a, pos, mass, c->order, c->xs, c->ms,
                                c->phi, c->plo);
     k_tree_init<<<(nc + 255) / 256, 256, 0, s>>>(nc, off, c->node, c->parent,
-                                                 c->st);
+                                                 c->cpend, c->st);
     const int cap = (int)c->cap_cells;
     // one warp per cell: enough warps to fill every SM once
     for (int L = 0; L < P3T_MAX_LEVEL; ++L)
         k_tree_split<<<c->sms * 8, TB, 0, s>>>(L, c->p.n_leaf, cap, c->key_a,
-                                                c->node, c->parent, c->leaf_list,
-                                                c->int_list, c->st);
+                                                c->node, c->parent, c->cpend,
+                                                c->leaf_list, c->st);
     k_leaf_hist<<<c->sms * 4, TB, 0, s>>>(c->leaf_list, c->node, c->st);
     k_leaf_scatter<<<c->sms * 4, TB, 0, s>>>(c->leaf_list, c->node,
                                               c->leaf_sorted, c->st);
-    k_moments<true><<<c->sms * 8, TB, 0, s>>>(0, c->xs, c->ms, n, c->node,
-                                               c->leaf_sorted, c->int_list,
-                                               c->cM, c->ccom, c->cQ, c->cbmin,
-                                               c->cbmax, c->wmin, c->wmax,
-                                               c->cf0, c->cf1, c->cf2, c->st);
-    for (int L = P3T_MAX_LEVEL - 1; L >= 0; --L)
-        k_moments<false><<<grid_small, TB, 0, s>>>(L, c->xs, c->ms, n, c->node,
-                                                    c->leaf_list, c->int_list,
-                                                    c->cM, c->ccom, c->cQ,
-                                                    c->cbmin, c->cbmax, c->wmin,
-                                                    c->wmax, c->cf0, c->cf1,
-                                                    c->cf2, c->st);
+    k_moments_up<<<c->sms * 8, TB, 0, s>>>(c->xs, c->ms, n, c->node, c->parent,
+                                            c->leaf_sorted, c->cpend, c->cM,
+                                            c->ccom, c->cQ, c->cbmin, c->cbmax,
+                                            c->wmin, c->wmax, c->cf0, c->cf1,
+                                            c->cf2, c->st);
     k_groups<<<grid_small, TB, 0, s>>>(c->p.n_group, (int)c->cap_groups,
                                         c->node, c->parent, c->grange, c->st);
     k_group_box<<<c->sms * 2, GB, 0, s>>>(c->grange, c->xs, n, nc, c->order,
@@ -963,9 +975,9 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
                                             c->gcost, c->st);
     k_group_order<<<grid_small, TB, 0, s>>>(n, c->grange, c->order, c->pgroup,
                                              c->gcost, c->gperm, c->st);
-    // bbox 2, keys, gather, init, 21 splits, leaf order 2, 22 moment levels,
-    // groups, boxes, order 2
-    p3t_count_launches(2 + 1 + 1 + 1 + P3T_MAX_LEVEL + 2 + (P3T_MAX_LEVEL + 1) + 4);
+    // bbox 2, keys, gather, init, 21 splits, leaf order 2, moments, groups,
+    // boxes, order 2
+    p3t_count_launches(2 + 1 + 1 + 1 + P3T_MAX_LEVEL + 2 + 1 + 4);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
 }
