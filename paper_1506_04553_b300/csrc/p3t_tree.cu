@@ -306,28 +306,58 @@ __device__ __forceinline__ int digit_at(u64 key, int L)
     return (int)((key >> (3 * (P3T_MAX_LEVEL - L))) & 7u);
 }
 
-// First position p in [lo, hi) with digit_at(key[p], L) >= d, by a whole
-// warp: 32 probes per step (the range shrinks 32-fold per dependent load).
-__device__ __forceinline__ int warp_lower_digit(const u64 *__restrict__ key,
-                                                int lo, int hi, int L, int d,
-                                                int lane)
+// All seven child boundaries of the cell [lo, hi) at once: b[d] (d = 1..7)
+// is the first position with digit_at >= d.  The seven 32-ary searches run
+// side by side, each round issuing the probes of all of them before any is
+// examined, so a round costs one memory latency (4 rounds for 2^20 keys).
+__device__ __forceinline__ void warp_lower_digits7(const u64 *__restrict__ key,
+                                                   int lo0, int hi0, int L,
+                                                   int lane, int *b)
 {
-    while (hi - lo > 32) {
-        const int step = (hi - lo + 31) / 32;
-        const int p = lo + lane * step;
-        const bool ge = p < hi && digit_at(key[p], L) >= d;
-        const unsigned m = __ballot_sync(0xffffffffu, ge);
-        const int f = m ? __ffs(m) - 1 : 32;  // first probe with digit >= d
-        const int lastv = (hi - 1 - lo) / step;  // last probe inside [lo, hi)
-        const int nlo = f == 0 ? lo : lo + min(f - 1, lastv) * step + 1;
-        const int nhi = f == 32 ? hi : min(hi, lo + f * step);
-        lo = nlo;
-        hi = nhi;
+    int lo[8], hi[8];
+#pragma unroll
+    for (int d = 1; d < 8; ++d) {
+        lo[d] = lo0;
+        hi[d] = hi0;
     }
-    const int p = lo + lane;
-    const bool ge = p < hi && digit_at(key[p], L) >= d;
-    const unsigned m = __ballot_sync(0xffffffffu, ge);
-    return m ? lo + __ffs(m) - 1 : hi;
+    for (int round = 0; round < 8; ++round) {  // 32^8 > 2^31: always enough
+        bool more = false;
+#pragma unroll
+        for (int d = 1; d < 8; ++d) more |= hi[d] - lo[d] > 32;
+        if (!more) break;
+        int dg[8];
+#pragma unroll
+        for (int d = 1; d < 8; ++d) {
+            const int step = (hi[d] - lo[d] + 31) / 32;
+            const int p = lo[d] + lane * step;
+            dg[d] = (hi[d] - lo[d] > 32 && p < hi[d]) ? digit_at(key[p], L) : 8;
+        }
+#pragma unroll
+        for (int d = 1; d < 8; ++d) {
+            if (hi[d] - lo[d] <= 32) continue;  // warp-uniform
+            const int step = (hi[d] - lo[d] + 31) / 32;
+            const int p = lo[d] + lane * step;
+            const unsigned m = __ballot_sync(0xffffffffu, p < hi[d] && dg[d] >= d);
+            const int f = m ? __ffs(m) - 1 : 32;
+            const int lastv = (hi[d] - 1 - lo[d]) / step;
+            const int nlo = f == 0 ? lo[d] : lo[d] + min(f - 1, lastv) * step + 1;
+            const int nhi = f == 32 ? hi[d] : min(hi[d], lo[d] + f * step);
+            lo[d] = nlo;
+            hi[d] = nhi;
+        }
+    }
+    int dg[8];
+#pragma unroll
+    for (int d = 1; d < 8; ++d) {
+        const int p = lo[d] + lane;
+        dg[d] = p < hi[d] ? digit_at(key[p], L) : 8;
+    }
+#pragma unroll
+    for (int d = 1; d < 8; ++d) {
+        const int p = lo[d] + lane;
+        const unsigned m = __ballot_sync(0xffffffffu, p < hi[d] && dg[d] >= d);
+        b[d] = m ? lo[d] + __ffs(m) - 1 : hi[d];
+    }
 }
 
 // Child boundaries of the cell [lo, hi) by one warp reading its keys in
@@ -430,8 +460,7 @@ k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
         b[0] = nd.x;
         b[8] = nd.x + nd.y;
         if (nd.y > BIG_CELL) {
-            for (int d = 1; d < 8; ++d)
-                b[d] = warp_lower_digit(key, b[d - 1], b[8], L + 1, d, lane);
+            warp_lower_digits7(key, b[0], b[8], L + 1, lane, b);
         } else {
             warp_scan_digits(key, b[0], b[8], L + 1, sb, lane);
 #pragma unroll
