@@ -191,6 +191,27 @@ def test_coincident_particles(cuda):
     assert np.array_equal(off, off_o) and np.array_equal(idx, idx_o)
 
 
+def test_deep_chain_inside_a_cluster(cuda):
+    """A Plummer sphere with 80 coincident particles inside: a chain of
+    single-child cells down to level 21 ending in a leaf of 80 particles (more
+    than any leaf size bin below it) among ordinary leaves.  The bottom-up
+    moments climb the chain; cells, boxes and moments match the oracle."""
+    pos, _, m = ics.plummer(4000, 31)
+    pos = pos.T.copy()
+    pos[:80] = 0.0123
+    m = np.full(4000, 1.0 / 4000)
+    p = _params(theta=0.5, r_out=0.01, eps=1e-3)
+    ctx, acc, _, _ = gpu_run(pos, m, p, neighbours=False)
+    t = oracle.Tree(pos, m, n_leaf=p.n_leaf, n_group=p.n_group)
+    t.walk(p.theta, p.r_out, p.r_out)
+    og, gid = compare_structure(ctx, t)
+    compare_lists(ctx, t, og, gid)
+    assert ctx.stats()["n_levels"] == 22
+    a_o = t.force(G=p.G, eps=p.eps, r_cut=p.r_out, gamma=p.gamma)
+    e = rel_err(acc, a_o)
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4, (np.median(e), e.max())
+
+
 def test_exact_distance_ties(cuda):
     # pairs at exactly r = h (excluded) and just inside (included)
     h = 0.5
