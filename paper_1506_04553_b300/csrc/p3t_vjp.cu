@@ -165,8 +165,7 @@ __device__ __forceinline__ void cell_pair(const CellSrc &c, f2 nx, f2 ny,
     const f2 s2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, eps2)));
     const f2 ri = make_float2(rsqrt_ftz(s2.x), rsqrt_ftz(s2.y));
     const f2 ri2 = mul2(ri, ri);
-    const f2 ri3 = mul2(ri, ri2), ri5 = mul2(ri3, ri2), ri7 = mul2(ri5, ri2),
-             ri9 = mul2(ri7, ri2);
+    const f2 ri3 = mul2(ri, ri2), ri5 = mul2(ri3, ri2), ri7 = mul2(ri5, ri2);
     // Q = [[Qxx, Qxy, Qxz], [Qxy, Qyy, Qyz], [Qxz, Qyz, Qzz]]
     const f2 qx = fma2(c.Qxx, dx, fma2(c.Qxy, dy, mul2(c.Qxz, dz)));
     const f2 qy = fma2(c.Qxy, dx, fma2(c.Qyy, dy, mul2(c.Qyz, dz)));
@@ -180,10 +179,10 @@ __device__ __forceinline__ void cell_pair(const CellSrc &c, f2 nx, f2 ny,
     // J^T w = cw w + cd d + cq q - Qw / s^5 with
     //   cw = M / s^3 + (5/2) dQd / s^7,   cq = 5 wd / s^7,
     //   cd = -3 M wd / s^5 + 5 wQd / s^7 - (35/2) dQd wd / s^9
+    //      = [-3 M wd + (5 wQd - (35/2) dQd wd / s^2) / s^2] / s^5
     const f2 cw = fma2(mul2(dup2(2.5f), dqd), ri7, mul2(c.M, ri3));
-    f2 cd = mul2(mul2(c.M3, wd), ri5);
-    cd = fma2(mul2(dup2(5.0f), wqd), ri7, cd);
-    cd = fma2(mul2(dup2(-17.5f), mul2(dqd, wd)), ri9, cd);
+    const f2 cdi = fma2(mul2(mul2(dqd, wd), ri2), dup2(-17.5f), mul2(dup2(5.0f), wqd));
+    const f2 cd = mul2(fma2(cdi, ri2, mul2(c.M3, wd)), ri5);
     const f2 t7 = mul2(dup2(2.5f), mul2(wd, ri7));  // (5/2) wd / s^7
     const f2 cq = add2(t7, t7);
     const f2 nri5 = mul2(dup2(-1.0f), ri5);
@@ -195,14 +194,16 @@ __device__ __forceinline__ void cell_pair(const CellSrc &c, f2 nx, f2 ny,
     acc[2] = add2(acc[2], jy);
     acc[3] = add2(acc[3], jz);
     // S = -(w d^T + d w^T) / (2 s^5) + (5/2) wd d d^T / s^7, with v = -w / (2 s^5)
+    // and u = t7 d + v: S_ab = d_a u_b + v_a d_b, S_aa = d_a (u_a + v_a)
     const f2 h5 = mul2(dup2(-0.5f), ri5);
     const f2 vx = mul2(h5, wx), vy = mul2(h5, wy), vz = mul2(h5, wz);
-    acc[4] = fma2(dx, fma2(t7, dx, add2(vx, vx)), acc[4]);
-    acc[5] = fma2(dy, fma2(t7, dy, add2(vy, vy)), acc[5]);
-    acc[6] = fma2(dz, fma2(t7, dz, add2(vz, vz)), acc[6]);
-    acc[7] = fma2(vx, dy, fma2(dx, fma2(t7, dy, vy), acc[7]));
-    acc[8] = fma2(vx, dz, fma2(dx, fma2(t7, dz, vz), acc[8]));
-    acc[9] = fma2(vy, dz, fma2(dy, fma2(t7, dz, vz), acc[9]));
+    const f2 ux = fma2(t7, dx, vx), uy = fma2(t7, dy, vy), uz = fma2(t7, dz, vz);
+    acc[4] = fma2(dx, add2(ux, vx), acc[4]);
+    acc[5] = fma2(dy, add2(uy, vy), acc[5]);
+    acc[6] = fma2(dz, add2(uz, vz), acc[6]);
+    acc[7] = fma2(dx, uy, fma2(vx, dy, acc[7]));
+    acc[8] = fma2(dx, uz, fma2(vx, dz, acc[8]));
+    acc[9] = fma2(dy, uz, fma2(vy, dz, acc[9]));
 }
 
 // One source particle (broadcast pairs) against two particles.
