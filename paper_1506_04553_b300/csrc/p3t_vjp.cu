@@ -137,16 +137,45 @@ __device__ __forceinline__ float pick(const float (&a)[NV], int v)
 }
 
 // The group's particles, staged once per group: negated group-relative
-// positions and weights, slot = particle index in the group; and the
-// particle-side tile sums.
+// positions and weights, slot = particle index in the group, stored
+// pair-interleaved (slots 2p and 2p+1 fill 12 consecutive floats: nx, ny,
+// nz, wx, wy, wz of both), so that three 128-bit loads give a particle
+// pair; and the particle-side tile sums.
 struct __align__(16) VjpSmem {
-    float nx[GMAX], ny[GMAX], nz[GMAX], wx[GMAX], wy[GMAX], wz[GMAX];
+    float pp[GMAX * 6];
     float ts[3][GMAX];
 };
 
-__device__ __forceinline__ f2 ld2(const float *a, int j)
+__device__ __forceinline__ void stage_slot(VjpSmem *V, int slot, float nx,
+                                           float ny, float nz, float wx,
+                                           float wy, float wz)
 {
-    return *reinterpret_cast<const float2 *>(a + j);
+    float *q = V->pp + (slot >> 1) * 12 + (slot & 1);
+    q[0] = nx;
+    q[2] = ny;
+    q[4] = nz;
+    q[6] = wx;
+    q[8] = wy;
+    q[10] = wz;
+}
+
+// Particle pair j, j + 1 (j even) as broadcast-free pairs.
+struct PPair {
+    f2 nx, ny, nz, wx, wy, wz;
+};
+
+__device__ __forceinline__ PPair load_pair(const VjpSmem *V, int j)
+{
+    const float4 *t4 = reinterpret_cast<const float4 *>(V->pp) + (j >> 1) * 3;
+    const float4 A = t4[0], B = t4[1], C = t4[2];
+    PPair r;
+    r.nx = make_float2(A.x, A.y);
+    r.ny = make_float2(A.z, A.w);
+    r.nz = make_float2(B.x, B.y);
+    r.wx = make_float2(B.z, B.w);
+    r.wy = make_float2(C.x, C.y);
+    r.wz = make_float2(C.z, C.w);
+    return r;
 }
 
 // One cell (broadcast pairs) against two particles (the pair's halves).
@@ -334,9 +363,9 @@ struct VjpEval {
             for (int u = 0; u < NSP; ++u) {
                 const int j = 2 * (ch + u);
                 f2 jx, jy, jz;
-                cell_pair(c, ld2(V->nx, j), ld2(V->ny, j), ld2(V->nz, j),
-                          ld2(V->wx, j), ld2(V->wy, j), ld2(V->wz, j), e2, acc,
-                          jx, jy, jz);
+                const PPair q = load_pair(V, j);
+                cell_pair(c, q.nx, q.ny, q.nz, q.wx, q.wy, q.wz, e2, acc, jx, jy,
+                          jz);
                 r[u][0] = jx.x; r[u][1] = jy.x; r[u][2] = jz.x;
                 r[u][3] = jx.y; r[u][4] = jy.y; r[u][5] = jz.y;
             }
@@ -380,8 +409,8 @@ struct VjpEval {
             for (int u = 0; u < NSP; ++u) {
                 const int j = 2 * (ch + u);
                 f2 jx, jy, jz;
-                pair_pair<NEAR>(p, ld2(V->nx, j), ld2(V->ny, j), ld2(V->nz, j),
-                                ld2(V->wx, j), ld2(V->wy, j), ld2(V->wz, j),
+                const PPair q = load_pair(V, j);
+                pair_pair<NEAR>(p, q.nx, q.ny, q.nz, q.wx, q.wy, q.wz,
                                 self == j, self == j + 1, e2, kA, kB, acc, jx,
                                 jy, jz);
                 r[u][0] = jx.x; r[u][1] = jy.x; r[u][2] = jz.x;
@@ -448,12 +477,7 @@ k_walk_vjp(const int *__restrict__ gclus,
                 p = rel(phi[kk], plo[kk], ev.ct);
                 wv = make_float3(w[o], w[(size_t)n + o], w[2 * (size_t)n + o]);
             }
-            ev.V->nx[slot] = -p.x;
-            ev.V->ny[slot] = -p.y;
-            ev.V->nz[slot] = -p.z;
-            ev.V->wx[slot] = wv.x;
-            ev.V->wy[slot] = wv.y;
-            ev.V->wz[slot] = wv.z;
+            stage_slot(ev.V, slot, -p.x, -p.y, -p.z, wv.x, wv.y, wv.z);
             for (int c = 0; c < 3; ++c) ev.ih[h][c] = ev.il[h][c] = 0.0f;
         }
         __syncwarp();
