@@ -439,6 +439,10 @@ k_tree_split(int L, int n_leaf, int cap, const u64 *__restrict__ key,
     __shared__ int sbuf[TB / 32][9];
     const int beg = st->level_start[L], end = st->level_start[L + 1];
     const bool stop = st->error != 0 || L >= P3T_MAX_LEVEL;
+    if (beg == end && !stop) {  // empty level: the next one is empty too
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->level_start[L + 2] = end;
+        return;
+    }
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
     const int lane = threadIdx.x & 31;
     const int wg = (blockIdx.x * TB + threadIdx.x) >> 5;
