@@ -643,29 +643,35 @@ def run_p3t_step(args, dev):
     ctx.neighbours_into(off, idx)
     ctx.hard_step(pos.clone(), vel.clone(), mass, off, idx, hp)  # scratch
 
-    def step(time_hard=None):
+    def step(ev=None):
+        rec = (lambda k: ev[k].record(torch.cuda.current_stream(dev))) if ev else (lambda k: None)
+        rec(0)
         P.kick(vel, acc, 0.5 * dt)
-        if time_hard:
-            time_hard[0].record(torch.cuda.current_stream(dev))
+        rec(1)
         ctx.hard_step(pos, vel, mass, off, idx, hp, check=False)
-        if time_hard:
-            time_hard[1].record(torch.cuda.current_stream(dev))
+        rec(2)
         ctx.build_tree(pos, mass)
+        rec(3)
         ctx.long_force(acc, check=False)
+        rec(4)
         ctx.neighbours_into(off, idx, sync=False)
+        rec(5)
         P.kick(vel, acc, 0.5 * dt)
+        rec(6)
 
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
     ctx.check()
-    # the hard step alone, in uncaptured steps
-    hard = []
+    # phases, in uncaptured steps
+    phases = []
     for _ in range(3):
-        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
         step(ev)
         torch.cuda.synchronize()
-        hard.append(ev[0].elapsed_time(ev[1]))
+        phases.append([ev[k].elapsed_time(ev[k + 1]) for k in range(6)])
+    ph = np.median(np.array(phases), axis=0)
+    hard = [ph[1]]
     st = ctx.stats()
     nonis = int((off[1:] > off[:-1]).sum().item())
     ctx.set_params(P.Params(theta=THETA, r_out=r_cut, gamma=GAMMA, eps=eps, h=h,
@@ -701,6 +707,10 @@ def run_p3t_step(args, dev):
                     "F_soft, neighbour lists, half-kick; one CUDA graph",
             "n": n, "value": n / (ms * 1e-3), "unit": "particles/s",
             "ms_per_step": ms, "hard_ms": float(np.median(hard)),
+            "phase_ms_per_step": {"kicks": float(ph[0] + ph[5]), "hard": float(ph[1]),
+                                  "build": float(ph[2]), "force": float(ph[3]),
+                                  "neighbours": float(ph[4]),
+                                  "note": "CUDA events, steps without the graph"},
             "non_isolated": nonis, "components": st["herm_components"],
             "largest_component": st["herm_max_component"],
             "hard_particle_steps": st["herm_particle_steps"],
