@@ -43,7 +43,9 @@ DEFAULT_THREADS = os.cpu_count() or 1
 
 
 def build(force: bool = False) -> str:
-    """Compile p3t_oracle.c into a shared library (gcc, FP64, no FMA)."""
+    """Compile p3t_oracle.c into a shared library (gcc, FP64, no implicit
+    FMA contraction; where the hard part fuses a multiply-add it calls fma()
+    explicitly)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):

@@ -1230,9 +1230,31 @@ void orc_tree_update(orc_tree *t, const double *pos, const double *m)
  * (off[n+1], idx) in ascending j, as the neighbour search returns them.
  * Every expression is written in the order it is evaluated. */
 
-static double orc_dot3(const double *a, const double *b)
+/* The hard part evaluates its formulas with fused multiply-adds: fma(a, b, c)
+ * is a b + c with one rounding (IEEE 754 fusedMultiplyAdd), written out at
+ * every use so that the order of operations is explicit.  The same holds
+ * for the GPU path, so the two agree bit for bit. */
+static double orc_fdot3(const double *a, const double *b)
 {
-    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+    return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
+}
+
+/* K and dK/dx of Eq. 12 in Horner form for the hard part:
+ *   K = x^4 (35 + x (-84 + x (70 - 20 x))),
+ *   dK/dx = 140 x^3 (1 - x)^3 = x^3 (140 + x (-420 + x (420 - 140 x))). */
+static double orc_hK(double x)
+{
+    if (x < 0.0) return 0.0;
+    if (x >= 1.0) return 1.0;
+    double x2 = x * x, x4 = x2 * x2;
+    return x4 * fma(fma(fma(-20.0, x, 70.0), x, -84.0), x, 35.0);
+}
+
+static double orc_hdK(double x)
+{
+    if (x <= 0.0 || x >= 1.0) return 0.0;
+    double x3 = x * x * x;
+    return x3 * fma(fma(fma(-140.0, x, 420.0), x, -420.0), x, 140.0);
 }
 
 /* Constants of the hard part, each computed once in this order. */
@@ -1285,22 +1307,22 @@ static void orc_hard_one(int64_t i, const double *x, const double *v,
             q[c] = x[3 * i + c] - x[3 * j + c];
             u[c] = v[3 * i + c] - v[3 * j + c];
         }
-        double s2 = orc_dot3(q, q) + P->eps2;
+        double s2 = fma(q[0], q[0], fma(q[1], q[1], fma(q[2], q[2], P->eps2)));
         double s = sqrt(s2);
         double ri = 1.0 / s;
         double ri2 = ri * ri;
         double ri3 = ri2 * ri;
-        double xk = (s * P->irc - P->gamma) * P->iomg;
-        double w = 1.0 - orc_K(xk);
-        double dKds = orc_dKdx(xk) * P->iomgrc;
-        double rv = orc_dot3(q, u);
+        double xk = fma(s, P->irc, -P->gamma) * P->iomg;
+        double w = 1.0 - orc_hK(xk);
+        double dKds = orc_hdK(xk) * P->iomgrc;
+        double rv = orc_fdot3(q, u);
         double gm = P->G * m[j];
         double fa = gm * w * ri3;
         double c1 = 3.0 * rv * ri2;
         double fb = gm * (dKds * rv * ri) * ri3;
         for (int c = 0; c < 3; ++c) {
-            acc[c] = acc[c] - fa * q[c];
-            jrk[c] = jrk[c] - (fa * (u[c] - c1 * q[c]) - fb * q[c]);
+            acc[c] = fma(-fa, q[c], acc[c]);
+            jrk[c] = fma(-fa, fma(-c1, q[c], u[c]), fma(fb, q[c], jrk[c]));
         }
     }
     for (int c = 0; c < 3; ++c) {
@@ -1345,6 +1367,7 @@ static int orc_level(double den, double e, double dm2, int kmin, int kmax,
  * Sect. 2.1 / the sixth of Sect. 2.2); particles with an empty row are
  * isolated and drift, x <- x + dt_soft v (the fifth step of Sect. 2.2).
  *
+ * Products that feed a sum are fused (fma, one rounding each).
  * Divisions are few: 1/s per pair, 1/h per correction, and constants
  * (1/r_cut, 1/(1 - gamma), alpha G / r_cut^2, 1/6, 1/24, 1/120) formed once;
  * the timestep criteria are tested in squares (orc_level).
@@ -1400,8 +1423,8 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
         st[2] += off[i + 1] - off[i];
         /* Eq. timestep:2: dt^2 |j|^2 <= eta_s^2 (|a|^2 + a0^2) */
         double a0 = P.a0c * m[i];
-        double jj = orc_dot3(jk + 3 * i, jk + 3 * i);
-        double e = P.eta_s2 * (orc_dot3(a + 3 * i, a + 3 * i) + a0 * a0);
+        double jj = orc_fdot3(jk + 3 * i, jk + 3 * i);
+        double e = P.eta_s2 * fma(a0, a0, orc_fdot3(a + 3 * i, a + 3 * i));
         lev[i] = orc_level(jj, e, dm2, 0, kmax, &capped);
         st[3] += capped;
     }
@@ -1424,8 +1447,8 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
             double d3 = d * d * d * P.c6;
             for (int c = 0; c < 3; ++c) {
                 int64_t k = 3 * i + c;
-                xp[k] = x[k] + v[k] * d + a[k] * d2 + jk[k] * d3;
-                vp[k] = v[k] + a[k] * d + jk[k] * d2;
+                xp[k] = fma(jk[k], d3, fma(a[k], d2, fma(v[k], d, x[k])));
+                vp[k] = fma(jk[k], d2, fma(a[k], d, v[k]));
             }
         }
         /* evaluate and correct the particles due at tn */
@@ -1441,17 +1464,18 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
             double ih = 1.0 / h;
             double ih2 = ih * ih, ih3 = ih2 * ih;
             double h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
+            double h3c6 = h3 * P.c6, h4c24 = h4 * P.c24, h5c120 = h5 * P.c120;
             double a2[3], a3[3], a2e[3];
             for (int c = 0; c < 3; ++c) {
                 int64_t k = 3 * i + c;
                 double da = a[k] - a1[c];
-                a2[c] = (-6.0 * da - h * (4.0 * jk[k] + 2.0 * j1[c])) * ih2;
-                a3[c] = (12.0 * da + 6.0 * h * (jk[k] + j1[c])) * ih3;
-                x[k] = xp[k] + a2[c] * (h4 * P.c24) + a3[c] * (h5 * P.c120);
-                v[k] = vp[k] + a2[c] * (h3 * P.c6) + a3[c] * (h4 * P.c24);
+                a2[c] = fma(-h, fma(4.0, jk[k], 2.0 * j1[c]), -6.0 * da) * ih2;
+                a3[c] = fma(6.0 * h, jk[k] + j1[c], 12.0 * da) * ih3;
+                x[k] = fma(a3[c], h5c120, fma(a2[c], h4c24, xp[k]));
+                v[k] = fma(a3[c], h4c24, fma(a2[c], h3c6, vp[k]));
                 a[k] = a1[c];
                 jk[k] = j1[c];
-                a2e[c] = a2[c] + a3[c] * h;
+                a2e[c] = fma(a3[c], h, a2[c]);
             }
             t[i] = tn;
             if (tn == T) continue;
@@ -1459,10 +1483,10 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
              * dt^2 (sqrt(|a|^2 |a3|^2) + |a2|^2)
              *     <= eta^2 (sqrt((|a|^2 + a0^2) |a2|^2) + |j|^2) */
             double a0 = P.a0c * m[i];
-            double aa = orc_dot3(a1, a1);
-            double a2sq = orc_dot3(a2e, a2e);
-            double num = sqrt((aa + a0 * a0) * a2sq) + orc_dot3(j1, j1);
-            double den = sqrt(aa * orc_dot3(a3, a3)) + a2sq;
+            double aa = orc_fdot3(a1, a1);
+            double a2sq = orc_fdot3(a2e, a2e);
+            double num = sqrt(fma(a0, a0, aa) * a2sq) + orc_fdot3(j1, j1);
+            double den = sqrt(aa * orc_fdot3(a3, a3)) + a2sq;
             int kmin = lev[i] > 0 ? lev[i] - 1 : 0;
             int k = orc_level(den, P.eta2 * num, dm2, kmin, kmax, &capped);
             st[3] += capped;

@@ -9,8 +9,9 @@
 //   a_i  = -sum G m_j (1-K) q / s^3
 //   da_i = -sum G m_j [ (1-K) (u - 3 (q.u) q / s^2) / s^3
 //                       - (dK/ds) ((q.u) / s) q / s^3 ].
-// All of it is FP64 with one rounding per operation (explicit __d*_rn
-// intrinsics, no contraction), in a fixed order, so the results do not
+// All of it is FP64 with one rounding per operation (explicit __d*_rn and
+// __fma_rn intrinsics: products that feed a sum are fused, as written, and
+// nothing else is contracted), in a fixed order, so the results do not
 // depend on the compiler's choices.  Divisions and square roots are costly
 // in FP64 (about 600 cycles of latency each on B300, ten times an add) and
 // few: 1/s per pair; 1/h is the exact scaling 2^k / dt_max; the timestep
@@ -70,31 +71,31 @@ __device__ __forceinline__ double scale2(double x, int n)
     return ldexp(x, n);
 }
 
+// a b + c with one rounding; products that feed a sum are fused, in the
+// order written, here and in the reference alike
+__device__ __forceinline__ double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 __device__ __forceinline__ double dot3(double ax, double ay, double az,
                                        double bx, double by, double bz)
 {
-    return dadd(dadd(dmul(ax, bx), dmul(ay, by)), dmul(az, bz));
+    return dfma(ax, bx, dfma(ay, by, dmul(az, bz)));
 }
 
-// Eq. 12
+// Eq. 12 in Horner form: K = x^4 (35 + x (-84 + x (70 - 20 x)))
 __device__ __forceinline__ double K_of_x(double x)
 {
     if (x < 0.0) return 0.0;
     if (x >= 1.0) return 1.0;
-    const double x2 = dmul(x, x), x3 = dmul(x2, x), x4 = dmul(x2, x2);
-    const double x5 = dmul(x4, x), x6 = dmul(x3, x3), x7 = dmul(x6, x);
-    return dadd(dsub(dadd(dmul(-20.0, x7), dmul(70.0, x6)), dmul(84.0, x5)),
-                dmul(35.0, x4));
+    const double x2 = dmul(x, x), x4 = dmul(x2, x2);
+    return dmul(x4, dfma(dfma(dfma(-20.0, x, 70.0), x, -84.0), x, 35.0));
 }
 
-// dK/dx of Eq. 12
+// dK/dx of Eq. 12: 140 x^3 (1 - x)^3 = x^3 (140 + x (-420 + x (420 - 140 x)))
 __device__ __forceinline__ double dK_of_x(double x)
 {
     if (x <= 0.0 || x >= 1.0) return 0.0;
-    const double x2 = dmul(x, x), x3 = dmul(x2, x), x4 = dmul(x2, x2);
-    const double x5 = dmul(x4, x), x6 = dmul(x3, x3);
-    return dadd(dsub(dadd(dmul(-140.0, x6), dmul(420.0, x5)), dmul(420.0, x4)),
-                dmul(140.0, x3));
+    const double x3 = dmul(dmul(x, x), x);
+    return dmul(x3, dfma(dfma(dfma(-140.0, x, 420.0), x, -420.0), x, 140.0));
 }
 
 // Constants of the hard part, formed once on the host in this order.
@@ -129,12 +130,12 @@ __device__ __forceinline__ void pair_add(const double xi[3], const double vi[3],
 {
     const double q[3] = {dsub(xi[0], xj0), dsub(xi[1], xj1), dsub(xi[2], xj2)};
     const double u[3] = {dsub(vi[0], vj0), dsub(vi[1], vj1), dsub(vi[2], vj2)};
-    const double s2 = dadd(dot3(q[0], q[1], q[2], q[0], q[1], q[2]), P.eps2);
+    const double s2 = dfma(q[0], q[0], dfma(q[1], q[1], dfma(q[2], q[2], P.eps2)));
     const double s = dsqrt(s2);
     const double ri = ddiv(1.0, s);
     const double ri2 = dmul(ri, ri);
     const double ri3 = dmul(ri2, ri);
-    const double xk = dmul(dsub(dmul(s, P.irc), P.gamma), P.iomg);
+    const double xk = dmul(dfma(s, P.irc, -P.gamma), P.iomg);
     const double w = dsub(1.0, K_of_x(xk));
     const double dKds = dmul(dK_of_x(xk), P.iomgrc);
     const double rv = dot3(q[0], q[1], q[2], u[0], u[1], u[2]);
@@ -144,9 +145,8 @@ __device__ __forceinline__ void pair_add(const double xi[3], const double vi[3],
     const double fb = dmul(dmul(gm, dmul(dmul(dKds, rv), ri)), ri3);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        acc[c] = dsub(acc[c], dmul(fa, q[c]));
-        jrk[c] = dsub(jrk[c], dsub(dmul(fa, dsub(u[c], dmul(c1, q[c]))),
-                                   dmul(fb, q[c])));
+        acc[c] = dfma(-fa, q[c], acc[c]);
+        jrk[c] = dfma(-fa, dfma(-c1, q[c], u[c]), dfma(fb, q[c], jrk[c]));
     }
 }
 
@@ -478,8 +478,7 @@ k_herm_init(int n, const double *__restrict__ x, const double *__restrict__ v,
         // Eq. timestep:2: dt^2 |j|^2 <= eta_s^2 (|a|^2 + a0^2)
         const double a0 = dmul(H.a0c, m[i]);
         const double jj = dot3(ji[0], ji[1], ji[2], ji[0], ji[1], ji[2]);
-        const double e = dmul(H.eta_s2, dadd(dot3(ai[0], ai[1], ai[2], ai[0], ai[1], ai[2]),
-                                             dmul(a0, a0)));
+        const double e = dmul(H.eta_s2, dfma(a0, a0, dot3(ai[0], ai[1], ai[2], ai[0], ai[1], ai[2])));
         lev[i] = level_sq(jj, e, H, 0, capped);
     }
     if (pairs) atomicAdd((unsigned long long *)&st->herm[2], (unsigned long long)pairs);
@@ -506,9 +505,8 @@ __device__ __forceinline__ void predict_reg(const double x[3], const double v[3]
     const double d3 = dmul(dmul(dmul(d, d), d), H.c6);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        xp[c] = dadd(dadd(dadd(x[c], dmul(v[c], d)), dmul(a[c], d2)),
-                     dmul(jk[c], d3));
-        vp[c] = dadd(dadd(v[c], dmul(a[c], d)), dmul(jk[c], d2));
+        xp[c] = dfma(jk[c], d3, dfma(a[c], d2, dfma(v[c], d, x[c])));
+        vp[c] = dfma(jk[c], d2, dfma(a[c], d, v[c]));
     }
 }
 
@@ -531,23 +529,20 @@ __device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3
     const double ih2 = dmul(ih, ih), ih3 = dmul(ih2, ih);
     const double h2 = dmul(h, h), h3 = dmul(h2, h), h4 = dmul(h3, h),
                  h5 = dmul(h4, h);
+    const double h3c6 = dmul(h3, H.c6), h4c24 = dmul(h4, H.c24),
+                 h5c120 = dmul(h5, H.c120);
     double a2[3], a3[3], a2e[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const double j0 = jk[c];
         const double da = dsub(a[c], a1[c]);
-        a2[c] = dmul(dsub(dmul(-6.0, da),
-                          dmul(h, dadd(dmul(4.0, j0), dmul(2.0, j1[c])))),
-                     ih2);
-        a3[c] = dmul(dadd(dmul(12.0, da), dmul(dmul(6.0, h), dadd(j0, j1[c]))),
-                     ih3);
-        x[c] = dadd(dadd(xp[c], dmul(a2[c], dmul(h4, H.c24))),
-                    dmul(a3[c], dmul(h5, H.c120)));
-        v[c] = dadd(dadd(vp[c], dmul(a2[c], dmul(h3, H.c6))),
-                    dmul(a3[c], dmul(h4, H.c24)));
+        a2[c] = dmul(dfma(-h, dfma(4.0, j0, dmul(2.0, j1[c])), dmul(-6.0, da)), ih2);
+        a3[c] = dmul(dfma(dmul(6.0, h), dadd(j0, j1[c]), dmul(12.0, da)), ih3);
+        x[c] = dfma(a3[c], h5c120, dfma(a2[c], h4c24, xp[c]));
+        v[c] = dfma(a3[c], h4c24, dfma(a2[c], h3c6, vp[c]));
         a[c] = a1[c];
         jk[c] = j1[c];
-        a2e[c] = dadd(a2[c], dmul(a3[c], h));
+        a2e[c] = dfma(a3[c], h, a2[c]);
     }
     t = tn;
     if (tn == H.T) return;
@@ -556,7 +551,7 @@ __device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3
     const double a0 = dmul(H.a0c, mi);
     const double aa = dot3(a1[0], a1[1], a1[2], a1[0], a1[1], a1[2]);
     const double a2sq = dot3(a2e[0], a2e[1], a2e[2], a2e[0], a2e[1], a2e[2]);
-    const double num = dadd(dsqrt(dmul(dadd(aa, dmul(a0, a0)), a2sq)),
+    const double num = dadd(dsqrt(dmul(dfma(a0, a0, aa), a2sq)),
                             dot3(j1[0], j1[1], j1[2], j1[0], j1[1], j1[2]));
     const double den = dadd(dsqrt(dmul(aa, dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]))),
                             a2sq);
