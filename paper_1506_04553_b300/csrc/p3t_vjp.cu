@@ -549,7 +549,7 @@ k_vjp_push(int n, int nc, const long long *__restrict__ off,
 #pragma unroll
         for (int q = 0; q < 10; ++q) any |= A[q] != 0.0;
         if (any) {
-            const double M = cM[c];
+            // A[1..3] holds dL/dcom / M (k_vjp_prep)
             const double e[3] = {x[0] - ccom[3 * c], x[1] - ccom[3 * c + 1],
                                  x[2] - ccom[3 * c + 2]};
             const double Sxx = A[4], Syy = A[5], Szz = A[6], Sxy = A[7],
@@ -562,8 +562,8 @@ k_vjp_push(int n, int nc, const long long *__restrict__ off,
             const double ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
             const double eac = e[0] * A[1] + e[1] * A[2] + e[2] * A[3];
             for (int q = 0; q < 3; ++q)
-                gx[q] += (mk / M) * A[1 + q] + mk * (6.0 * Se[q] - 2.0 * tr * e[q]);
-            gm += A[0] + eac / M + 3.0 * eSe - ee * tr;
+                gx[q] += mk * (A[1 + q] + (6.0 * Se[q] - 2.0 * tr * e[q]));
+            gm += A[0] + eac + 3.0 * eSe - ee * tr;
         }
         const int4 nd = node[c];
         const int nch = nd.w & 255;
@@ -578,6 +578,26 @@ k_vjp_push(int n, int nc, const long long *__restrict__ off,
     const int o = order[kk];
     for (int q = 0; q < 3; ++q) gpos[(size_t)q * n + o] += gx[q];
     gmass[o] += gm;
+}
+
+// Cell adjoints prepared for the push: dL/dcom divided by M once per cell,
+// so that the push, which visits every cell on every particle's path, does
+// no division.
+__global__ void k_vjp_prep(const P3TDevState *__restrict__ st,
+                           const double *__restrict__ cM, double *__restrict__ cadj)
+{
+    const int nc = st->ncell;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc;
+         c += gridDim.x * blockDim.x) {
+        double *A = cadj + (size_t)c * 10;
+        const double a1 = A[1], a2 = A[2], a3 = A[3];
+        if (a1 != 0.0 || a2 != 0.0 || a3 != 0.0) {
+            const double iM = 1.0 / cM[c];
+            A[1] = a1 * iM;
+            A[2] = a2 * iM;
+            A[3] = a3 * iM;
+        }
+    }
 }
 
 __global__ void k_vjp_reset(P3TDevState *st)
@@ -613,12 +633,13 @@ int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,
         c->wmax, c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
         c->order, n, k, w,
         gpos, gmass, cadj, c->gperm, c->st);
+    k_vjp_prep<<<c->sms * 8, 256, 0, s>>>(c->st, c->cM, cadj);
     k_vjp_push<<<(n + 255) / 256, 256, 0, s>>>(n, c->nclus,
                                                (const long long *)c->clus_off,
                                                c->node, c->cM, c->ccom,
                                                c->xs, c->ms, c->order, cadj,
                                                gpos, gmass);
-    p3t_count_launches(3);
+    p3t_count_launches(4);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
 }
