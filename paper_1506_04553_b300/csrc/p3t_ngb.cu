@@ -57,7 +57,7 @@ constexpr int SL = P3T_NGB_SLOTS;
 // neighbours beyond the count c go to the particle's slots while c < SL.
 // Filling (long rows only, b0 / b1): neighbours go to the CSR row at w.
 template <bool FILL>
-__device__ __forceinline__ void ngb_tile(NgbSmem &S, float4 p0, float4 p1,
+__device__ __forceinline__ void ngb_tile(NgbSmem &S, int nk, float4 p0, float4 p1,
                                          bool v0, bool v1, int k0, int k1,
                                          float hs2, const double *xs, int n,
                                          double h2, const int *order,
@@ -66,7 +66,7 @@ __device__ __forceinline__ void ngb_tile(NgbSmem &S, float4 p0, float4 p1,
                                          int *s0, int *s1, int *idx,
                                          long long cap, P3TDevState *st)
 {
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < nk; ++j) {
         const float4 a = S.t0[j];
         const int kj = S.tj[j];
         float dx = a.x - p0.x, dy = a.y - p0.y, dz = a.z - p0.z;
@@ -133,6 +133,12 @@ k_ngb_walk(const int *__restrict__ gclus,
         const float4 gmn = gmin[g], gmx = gmax[g];
         const float hs2 = gmn.w;
         const int cl = gclus[g];
+        // a neighbour of a group particle lies within R + h of the group's
+        // centre (R: gmx.w, a sphere about the centre holding the group);
+        // candidates outside, with a 1% margin in the square, are dropped
+        // when staged
+        const float rfl = gmx.w + sqrtf((float)ccs[cl].h2);
+        const float rf2 = 1.01f * rfl * rfl;
         const float hg2 = ccs[cl].hg2;
         const double h2 = ccs[cl].h2;
         const int k0 = gr.x + lane, k1 = gr.x + 32 + lane;
@@ -180,15 +186,23 @@ k_ngb_walk(const int *__restrict__ gclus,
                 head = (head + nfull) & (NRING - 1);
                 nr -= nfull;
                 np -= take;
+                float4 pv = make_float4(1e15f, 1e15f, 1e15f, 0.f);
+                int jv = -1;
                 if (lane < take) {
-                    int j = S.tj[lane];
-                    S.t0[lane] = rel4n(phi[j], plo[j], ct);
-                } else {
-                    S.t0[lane] = make_float4(1e15f, 1e15f, 1e15f, 0.f);
-                    S.tj[lane] = -1;
+                    jv = S.tj[lane];
+                    pv = rel4n(phi[jv], plo[jv], ct);
+                }
+                const bool keep = lane < take &&
+                                  fmaf(pv.x, pv.x, fmaf(pv.y, pv.y, pv.z * pv.z)) < rf2;
+                const unsigned km = __ballot_sync(full, keep);
+                __syncwarp();  // every lane has read its S.tj entry
+                if (keep) {
+                    const int q = __popc(km & lt);
+                    S.t0[q] = pv;
+                    S.tj[q] = jv;
                 }
                 __syncwarp();
-                ngb_tile<FILL>(S, p0, p1, v0, v1, k0, k1, hs2, xs, n, h2, order,
+                ngb_tile<FILL>(S, __popc(km), p0, p1, v0, v1, k0, k1, hs2, xs, n, h2, order,
                                c0, c1, w0, w1, b0, b1, s0, s1, idx, cap, st);
                 __syncwarp();
             }

@@ -859,8 +859,9 @@ k_group_box(const int2 *__restrict__ grange, const double *__restrict__ xs,
             gmin[g] = make_float4(__double2float_rd(mn[0]), __double2float_rd(mn[1]),
                                   __double2float_rd(mn[2]),
                                   __double2float_ru(hs2));
+            // w: radius about the centre of a sphere holding the group
             gmax[g] = make_float4(__double2float_ru(mx[0]), __double2float_ru(mx[1]),
-                                  __double2float_ru(mx[2]), 0.0f);
+                                  __double2float_ru(mx[2]), __double2float_ru(R));
             gctr[g] = make_float4(c[0], c[1], c[2], 0.0f);
         }
         __syncthreads();  // sbox is rewritten by the next round
