@@ -98,6 +98,19 @@ def measured_peaks():
         return {}
 
 
+def force_and_neighbours(ctx, acc, off, idx, side):
+    """The force on the current stream and the neighbour lists on `side`,
+    concurrently: both read the same tree (separate work counters), and the
+    neighbour walk fills the SMs that the force kernel's tail leaves idle."""
+    import torch
+    cur = torch.cuda.current_stream()
+    side.wait_stream(cur)
+    ctx.long_force(acc, check=False)
+    with torch.cuda.stream(side):
+        ctx.neighbours_into(off, idx, sync=False)
+    cur.wait_stream(side)
+
+
 def profile_traffic():
     """Per-launch DRAM bytes of the force kernel from the committed ncu
     summary (a line 'dram_bytes_per_launch: <float>'), else None."""
@@ -315,13 +328,17 @@ def run_ours(args, world, rank, local):
     _, idx0 = ctx.neighbours()
     cap = max(4 * int(idx0.numel()) + 1024, n)
     idx = torch.empty((cap,), dtype=torch.int32, device=dev)
+    ngb_stream = torch.cuda.Stream(dev)
 
-    def step():
+    def step(sequential=False):
         P.kick(vel, acc, 0.5 * DT)
         P.drift(pos, vel, DT)
         ctx.build_tree(pos, mass)
-        ctx.long_force(acc, check=False)
-        ctx.neighbours_into(off, idx, sync=False)
+        if sequential:  # phase times: one stream
+            ctx.long_force(acc, check=False)
+            ctx.neighbours_into(off, idx, sync=False)
+        else:
+            force_and_neighbours(ctx, acc, off, idx, ngb_stream)
         P.kick(vel, acc, 0.5 * DT)
 
     for _ in range(args.warmup):
@@ -340,7 +357,7 @@ def run_ours(args, world, rank, local):
     p1 = torch.cuda.Event(enable_timing=True)
     p0.record(stream)
     for _ in range(kp):
-        step()
+        step(sequential=True)
     p1.record(stream)
     torch.cuda.synchronize()
     ctx.profile_enable(False)
@@ -437,10 +454,12 @@ def run_ours(args, world, rank, local):
                               "walk_and_force": prof["force_ms"] / nprof,
                               "neighbours": prof["ngb_ms"] / nprof,
                               "note": "CUDA events per phase, steps without "
-                                      "the graph"},
+                                      "the graph, on one stream"},
         "no_graph": {"ms_per_step": ms_nograph,
-                     "value": world * n / (ms_nograph * 1e-3)},
-        "timing": "K replays of one KDK step captured in a CUDA graph",
+                     "value": world * n / (ms_nograph * 1e-3),
+                     "note": "the same steps, one stream"},
+        "timing": "K replays of one KDK step captured in a CUDA graph; the "
+                  "neighbour lists run on a second stream beside the force",
         "force_particles_per_s": world * n * nprof / force_s if force_s else None,
         "fwd_bwd_ratio": None,
         "roofline": {"kernel": "k_walk_force", "bound": "alu",
@@ -643,7 +662,11 @@ def run_p3t_step(args, dev):
     ctx.neighbours_into(off, idx)
     ctx.hard_step(pos.clone(), vel.clone(), mass, off, idx, hp)  # scratch
 
+    ngb_stream = torch.cuda.Stream(dev)
+
     def step(ev=None):
+        # with events (phase times): one stream; without: the neighbour
+        # lists beside the force
         rec = (lambda k: ev[k].record(torch.cuda.current_stream(dev))) if ev else (lambda k: None)
         rec(0)
         P.kick(vel, acc, 0.5 * dt)
@@ -652,10 +675,13 @@ def run_p3t_step(args, dev):
         rec(2)
         ctx.build_tree(pos, mass)
         rec(3)
-        ctx.long_force(acc, check=False)
-        rec(4)
-        ctx.neighbours_into(off, idx, sync=False)
-        rec(5)
+        if ev:
+            ctx.long_force(acc, check=False)
+            rec(4)
+            ctx.neighbours_into(off, idx, sync=False)
+            rec(5)
+        else:
+            force_and_neighbours(ctx, acc, off, idx, ngb_stream)
         P.kick(vel, acc, 0.5 * dt)
         rec(6)
 
@@ -749,12 +775,17 @@ def run_king(args, dev):
     idx = torch.empty((max(4 * int(idx0.numel()) + 1024, n),), dtype=torch.int32,
                       device=dev)
 
-    def step():
+    ngb_stream = torch.cuda.Stream(dev)
+
+    def step(sequential=False):
         P.kick(vel, acc, 0.5 * DT)
         P.drift(pos, vel, DT)
         ctx.build_tree(pos, mass)
-        ctx.long_force(acc, check=False)
-        ctx.neighbours_into(off, idx, sync=False)
+        if sequential:  # phase times: one stream
+            ctx.long_force(acc, check=False)
+            ctx.neighbours_into(off, idx, sync=False)
+        else:
+            force_and_neighbours(ctx, acc, off, idx, ngb_stream)
         P.kick(vel, acc, 0.5 * DT)
 
     for _ in range(max(args.warmup, 3)):
@@ -763,7 +794,7 @@ def run_king(args, dev):
     ctx.profile(reset=True)
     ctx.profile_enable(True)
     for _ in range(3):
-        step()
+        step(sequential=True)
     torch.cuda.synchronize()
     ctx.profile_enable(False)
     prof = ctx.profile(reset=True)

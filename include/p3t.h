@@ -250,6 +250,10 @@ int p3t_check(p3t_ctx *ctx, void *stream);
  *             which case no host synchronisation happens and a too-small
  *             cap is latched (nothing is written past cap) and reported by
  *             the next p3t_check.
+ * May run concurrently with p3t_long_force on another stream, after the
+ * same p3t_build_tree (both only read the tree; each walk has its own
+ * device work counter): the neighbour walk then fills the SMs that the
+ * force kernel's tail leaves idle.
  * Errors: P3T_ERR_CAPACITY (nnz > cap; offsets valid, idx undefined),
  * P3T_ERR_STATE (no tree), P3T_ERR_CUDA. */
 int p3t_neighbours(p3t_ctx *ctx, int64_t *offsets, int32_t *idx, int64_t cap,

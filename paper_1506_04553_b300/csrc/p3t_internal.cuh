@@ -46,7 +46,9 @@ struct P3TDevState {
     int max_level;    // deepest level holding a cell
     int need_cells;   // cells requested when the cell capacity overflowed
     unsigned int blocks_done;
-    unsigned int work;  // dynamic work counter
+    unsigned int work;  // dynamic work counter of the force walk
+    unsigned int work_ngb;  // ... of the neighbour walk
+    unsigned int work_vjp;  // ... of the backward walk
     int pad0;
     int level_start[P3T_MAX_LEVEL + 3];
     int novf;           // groups listed in ngb_ovf

@@ -124,7 +124,7 @@ k_ngb_walk(const int *__restrict__ gclus,
     const int G = FILL ? st->novf : st->ngroup;
     for (;;) {
         int g = 0;
-        if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
+        if (lane == 0) g = (int)atomicAdd(&st->work_ngb, 1u);
         g = __shfl_sync(full, g, 0);
         if (g >= G) break;
         g = FILL ? ovf[g] : gperm[g];
@@ -338,7 +338,7 @@ __global__ void k_ngb_sort(int n, const long long *__restrict__ row_off,
 __global__ void k_work_reset(P3TDevState *st, int fill)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        st->work = 0;
+        st->work_ngb = 0;
         if (!fill) st->novf = 0;
     }
 }

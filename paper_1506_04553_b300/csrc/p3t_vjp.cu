@@ -452,7 +452,7 @@ k_walk_vjp(const int *__restrict__ gclus,
     const int G = st->ngroup;
     for (;;) {
         int g = 0;
-        if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
+        if (lane == 0) g = (int)atomicAdd(&st->work_vjp, 1u);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= G) break;
         g = gperm[g];
@@ -602,7 +602,7 @@ __global__ void k_vjp_prep(const P3TDevState *__restrict__ st,
 
 __global__ void k_vjp_reset(P3TDevState *st)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) st->work = 0;
+    if (threadIdx.x == 0 && blockIdx.x == 0) st->work_vjp = 0;
 }
 
 }  // namespace
