@@ -212,6 +212,41 @@ def test_deep_chain_inside_a_cluster(cuda):
     assert np.median(e) <= 1e-5 and e.max() <= 1e-4, (np.median(e), e.max())
 
 
+def test_force_and_neighbours_concurrently(cuda):
+    """p3t_long_force and p3t_neighbours on two streams after one build (each
+    walk has its own work counter) give bit for bit the sequential results,
+    also on a dense case with long neighbour rows."""
+    import torch
+    from paper_1506_04553_b300 import Context
+    pos = np.random.default_rng(3).normal(size=(20000, 3)) * 0.05
+    m = np.full(20000, 1.0 / 20000)
+    ctx = Context(_params(theta=0.5, r_out=0.006, eps=1e-4, h=0.008))
+    pd = torch.tensor(pos.T.copy(), device="cuda")
+    md = torch.tensor(m, device="cuda")
+    ctx.build_tree(pd, md)
+    n = pos.shape[0]
+    acc_s = torch.empty((3, n), dtype=torch.float32, device="cuda")
+    ctx.long_force(acc_s)
+    off_s, idx_s = ctx.neighbours()
+    nnz = int(off_s[-1])
+    assert int((torch.diff(off_s) > 8).sum()) > 1000  # long rows: the second walk runs
+    acc_c = torch.empty_like(acc_s)
+    off_c = torch.empty_like(off_s)
+    idx_c = torch.empty((nnz + 1024,), dtype=torch.int32, device="cuda")
+    side = torch.cuda.Stream()
+    for _ in range(3):
+        side.wait_stream(torch.cuda.current_stream())
+        ctx.long_force(acc_c, check=False)
+        with torch.cuda.stream(side):
+            ctx.neighbours_into(off_c, idx_c, sync=False)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        ctx.check()
+        assert torch.equal(acc_c, acc_s)
+        assert torch.equal(off_c, off_s)
+        assert torch.equal(idx_c[:nnz], idx_s)
+
+
 def test_exact_distance_ties(cuda):
     # pairs at exactly r = h (excluded) and just inside (included)
     h = 0.5
