@@ -26,9 +26,15 @@
 // per tile; the particle-side products (3 per particle) are summed over the
 // lanes by a warp reduce-scatter, four particle pairs at a time, and kept by
 // the particle's owner lane in two-sum (hi, lo) FP32 accumulators.
-// k_vjp_push then sends every cell adjoint to the member particles in FP64:
-// one thread per particle descends from the root to its leaf and applies the
-// adjoint of each cell on the way.
+// The cell adjoints then reach the member particles in FP64: with
+// T = 3 S - tr(S) I and e = x_k - com (so 6 S e - 2 tr(S) e = 2 T e and
+// 3 e.S.e - |e|^2 tr(S) = e.T.e), the sums over a particle's ancestors are
+// a quadratic form in x_k.  One thread per leaf adds its ancestors' terms
+// about the leaf's centre of mass r (delta = com - r, x' = x_k - r):
+//   P = sum dL/dcom / M,  Ts = sum T,  Tc = sum T delta,
+//   a = sum (dL/dM - delta . dL/dcom / M + delta.T.delta)
+// and every member gets dL/dx_k += m_k (P + 2 (Ts x' - Tc)) and
+// dL/dm_k += a + x'.P + x'.Ts.x' - 2 x'.Tc.
 #include <math.h>
 
 #include "p3t_walkcore.cuh"
@@ -515,69 +521,72 @@ k_walk_vjp(const int *__restrict__ gclus,
     }
 }
 
-// Cell adjoints (aM, acom[3], S xx yy zz xy xz yz) pushed to the member
-// particles, FP64; one thread per particle (sorted id k) walks from the root
-// down to its leaf.
+// Cell adjoints (aM, acom[3] / M, S xx yy zz xy xz yz) pushed to the member
+// particles, FP64; one thread per leaf climbs to the root summing the
+// coefficients of the quadratic form about the leaf's centre of mass, then
+// evaluates it for each member (every particle lies in exactly one leaf).
 __global__ void __launch_bounds__(256)
-k_vjp_push(int n, int nc, const long long *__restrict__ off,
-           const int4 *__restrict__ node, const double *__restrict__ cM,
-           const double *__restrict__ ccom, const double *__restrict__ xs,
-           const double *__restrict__ ms, const int *__restrict__ order,
-           const double *__restrict__ cadj, double *__restrict__ gpos,
-           double *__restrict__ gmass)
+k_vjp_leaves(const P3TDevState *__restrict__ st, int n,
+             const int *__restrict__ leaf_sorted, const int4 *__restrict__ node,
+             const int *__restrict__ parent, const double *__restrict__ ccom,
+             const double *__restrict__ xs, const double *__restrict__ ms,
+             const int *__restrict__ order, const double *__restrict__ cadj,
+             double *__restrict__ gpos, double *__restrict__ gmass)
 {
-    const int kk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (kk >= n) return;
-    const double x[3] = {xs[kk], xs[(size_t)n + kk], xs[2 * (size_t)n + kk]};
-    const double mk = ms[kk];
-    double gx[3] = {0.0, 0.0, 0.0}, gm = 0.0;
-    int c = 0;  // root of the particle's cluster (sorted order keeps clusters)
-    if (nc > 1) {
-        int lo = 0, hi = nc;
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (off[mid] <= kk)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        c = lo;
-    }
-    for (int depth = 0; depth <= P3T_MAX_LEVEL; ++depth) {
-        const double *A = cadj + (size_t)c * 10;
-        bool any = false;
+    if (st->error) return;
+    const int nl = st->nleaf;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nl;
+         q += gridDim.x * blockDim.x) {
+        const int leaf = leaf_sorted[q];
+        const double r[3] = {ccom[3 * leaf], ccom[3 * leaf + 1], ccom[3 * leaf + 2]};
+        double P[3] = {0.0, 0.0, 0.0}, Tc[3] = {0.0, 0.0, 0.0};
+        double Ts[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // xx yy zz xy xz yz
+        double a = 0.0;
+        int c = leaf;
+        for (int up = 0; up <= P3T_MAX_LEVEL && c >= 0; ++up) {
+            const double *A = cadj + (size_t)c * 10;
+            bool any = false;
 #pragma unroll
-        for (int q = 0; q < 10; ++q) any |= A[q] != 0.0;
-        if (any) {
-            // A[1..3] holds dL/dcom / M (k_vjp_prep)
-            const double e[3] = {x[0] - ccom[3 * c], x[1] - ccom[3 * c + 1],
-                                 x[2] - ccom[3 * c + 2]};
-            const double Sxx = A[4], Syy = A[5], Szz = A[6], Sxy = A[7],
-                         Sxz = A[8], Syz = A[9];
-            const double tr = Sxx + Syy + Szz;
-            const double Se[3] = {Sxx * e[0] + Sxy * e[1] + Sxz * e[2],
-                                  Sxy * e[0] + Syy * e[1] + Syz * e[2],
-                                  Sxz * e[0] + Syz * e[1] + Szz * e[2]};
-            const double eSe = e[0] * Se[0] + e[1] * Se[1] + e[2] * Se[2];
-            const double ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
-            const double eac = e[0] * A[1] + e[1] * A[2] + e[2] * A[3];
-            for (int q = 0; q < 3; ++q)
-                gx[q] += mk * (A[1 + q] + (6.0 * Se[q] - 2.0 * tr * e[q]));
-            gm += A[0] + eac + 3.0 * eSe - ee * tr;
+            for (int v = 0; v < 10; ++v) any |= A[v] != 0.0;
+            if (any) {
+                const double d[3] = {ccom[3 * c] - r[0], ccom[3 * c + 1] - r[1],
+                                     ccom[3 * c + 2] - r[2]};
+                const double tr = A[4] + A[5] + A[6];
+                // T = 3 S - tr(S) I
+                const double T[6] = {3.0 * A[4] - tr, 3.0 * A[5] - tr, 3.0 * A[6] - tr,
+                                     3.0 * A[7], 3.0 * A[8], 3.0 * A[9]};
+                const double Td[3] = {T[0] * d[0] + T[3] * d[1] + T[4] * d[2],
+                                      T[3] * d[0] + T[1] * d[1] + T[5] * d[2],
+                                      T[4] * d[0] + T[5] * d[1] + T[2] * d[2]};
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    P[v] += A[1 + v];
+                    Tc[v] += Td[v];
+                }
+#pragma unroll
+                for (int v = 0; v < 6; ++v) Ts[v] += T[v];
+                a += A[0] - (d[0] * A[1] + d[1] * A[2] + d[2] * A[3]) +
+                     (d[0] * Td[0] + d[1] * Td[1] + d[2] * Td[2]);
+            }
+            c = parent[c];
         }
-        const int4 nd = node[c];
-        const int nch = nd.w & 255;
-        if (nch == 0) break;
-        int next = nd.z;
-        for (int q = 0; q < nch; ++q) {
-            const int4 ch = node[nd.z + q];
-            if (kk >= ch.x && kk < ch.x + ch.y) next = nd.z + q;
+        const int4 nd = node[leaf];
+        for (int k = nd.x; k < nd.x + nd.y; ++k) {
+            const double x[3] = {xs[k] - r[0], xs[(size_t)n + k] - r[1],
+                                 xs[2 * (size_t)n + k] - r[2]};
+            const double Tx[3] = {Ts[0] * x[0] + Ts[3] * x[1] + Ts[4] * x[2],
+                                  Ts[3] * x[0] + Ts[1] * x[1] + Ts[5] * x[2],
+                                  Ts[4] * x[0] + Ts[5] * x[1] + Ts[2] * x[2]};
+            const double mk = ms[k];
+            const int o = order[k];
+#pragma unroll
+            for (int v = 0; v < 3; ++v)
+                gpos[(size_t)v * n + o] += mk * (P[v] + 2.0 * (Tx[v] - Tc[v]));
+            gmass[o] += a + (x[0] * P[0] + x[1] * P[1] + x[2] * P[2]) +
+                        (x[0] * Tx[0] + x[1] * Tx[1] + x[2] * Tx[2]) -
+                        2.0 * (x[0] * Tc[0] + x[1] * Tc[1] + x[2] * Tc[2]);
         }
-        c = next;
     }
-    const int o = order[kk];
-    for (int q = 0; q < 3; ++q) gpos[(size_t)q * n + o] += gx[q];
-    gmass[o] += gm;
 }
 
 // Cell adjoints prepared for the push: dL/dcom divided by M once per cell,
@@ -634,11 +643,9 @@ int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,
         c->order, n, k, w,
         gpos, gmass, cadj, c->gperm, c->st);
     k_vjp_prep<<<c->sms * 8, 256, 0, s>>>(c->st, c->cM, cadj);
-    k_vjp_push<<<(n + 255) / 256, 256, 0, s>>>(n, c->nclus,
-                                               (const long long *)c->clus_off,
-                                               c->node, c->cM, c->ccom,
-                                               c->xs, c->ms, c->order, cadj,
-                                               gpos, gmass);
+    k_vjp_leaves<<<c->sms * 8, 256, 0, s>>>(c->st, n, c->leaf_sorted, c->node,
+                                            c->parent, c->ccom, c->xs, c->ms,
+                                            c->order, cadj, gpos, gmass);
     p3t_count_launches(4);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
