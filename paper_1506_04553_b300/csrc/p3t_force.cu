@@ -10,7 +10,8 @@
 // d = 0 and contribute exactly zero.
 //
 // Layout of the work: one warp per group (groups fetched dynamically), two
-// i-particles per lane (group size <= 64).  The warp walks the tree for its
+// i-particles per lane (group size <= 64; groups of at most 32 evaluate only
+// the first).  The warp walks the tree for its
 // group (the same traversal and opening test as the list walk in
 // p3t_walk.cu) and feeds what it finds into three small rings in shared
 // memory: accepted cells, far leaf ranges, near leaf ranges.  Whenever a ring
@@ -316,8 +317,9 @@ __device__ __forceinline__ void tile_end(GroupAcc<POT> &A, const Part3 &u,
     }
 }
 
-// One tile of up to 32 accepted cells.
-template <bool POT>
+// One tile of up to 32 accepted cells.  TWO: the lane's second particle
+// (slot lane + 32) exists; groups of at most 32 particles skip it.
+template <bool POT, bool TWO>
 __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
                                           int take, const float4 *cf0,
                                           const float4 *cf1, const float4 *cf2,
@@ -375,7 +377,7 @@ __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
         c.Qzz = make_float2(D.x, D.y); c.Qxy = make_float2(D.z, D.w);
         c.Qxz = make_float2(E.x, E.y); c.Qyz = make_float2(E.z, E.w);
         pc_term2<POT>(P.x0, P.y0, P.z0, c, e2, u.x, u.y, u.z, u.p);
-        pc_term2<POT>(P.x1, P.y1, P.z1, c, e2, w.x, w.y, w.z, w.p);
+        if (TWO) pc_term2<POT>(P.x1, P.y1, P.z1, c, e2, w.x, w.y, w.z, w.p);
     }
     tile_end<POT>(A, u, w, -1.0f);
     __syncwarp();
@@ -394,8 +396,9 @@ __device__ __forceinline__ PartPair part_pair(const WarpSmem &S, int j)
     return p;
 }
 
-// One tile of up to 32 particles from a ring of leaf ranges.
-template <bool NEAR, bool POT>
+// One tile of up to 32 particles from a ring of leaf ranges (TWO as for
+// cell_tile).
+template <bool NEAR, bool POT, bool TWO>
 __device__ __forceinline__ void particle_tile(
     WarpSmem &S, int2 *ring, RangeRing &r, int take, const float4 *phi,
     const float4 *plo, const IPair &P, int k0, int k1,
@@ -430,13 +433,16 @@ __device__ __forceinline__ void particle_tile(
         for (int j = 0; j < 32; j += 2) {
             const PartPair p = part_pair(S, j);
             const f2 s0 = pp_near2(P.x0, P.y0, P.z0, p, e2, kA, kB, u.x, u.y, u.z);
-            const f2 s1 = pp_near2(P.x1, P.y1, P.z1, p, e2, kA, kB, w.x, w.y, w.z);
+            const f2 s1 = TWO ? pp_near2(P.x1, P.y1, P.z1, p, e2, kA, kB, w.x, w.y, w.z)
+                              : dup2(0.f);
             if (POT) {
                 const int ja = S.tj[j], jb = S.tj[j + 1];
                 if (ja >= 0 && ja != k0) tp0 -= p.M.x * (float)w_over_s((double)s0.x, k);
                 if (jb >= 0 && jb != k0) tp0 -= p.M.y * (float)w_over_s((double)s0.y, k);
-                if (ja >= 0 && ja != k1) tp1 -= p.M.x * (float)w_over_s((double)s1.x, k);
-                if (jb >= 0 && jb != k1) tp1 -= p.M.y * (float)w_over_s((double)s1.y, k);
+                if (TWO && ja >= 0 && ja != k1)
+                    tp1 -= p.M.x * (float)w_over_s((double)s1.x, k);
+                if (TWO && jb >= 0 && jb != k1)
+                    tp1 -= p.M.y * (float)w_over_s((double)s1.y, k);
             }
         }
         if (POT) {
@@ -449,11 +455,33 @@ __device__ __forceinline__ void particle_tile(
         for (int j = 0; j < 32; j += 2) {
             const PartPair p = part_pair(S, j);
             pp_far2<POT>(P.x0, P.y0, P.z0, p, e2, u.x, u.y, u.z, u.p);
-            pp_far2<POT>(P.x1, P.y1, P.z1, p, e2, w.x, w.y, w.z, w.p);
+            if (TWO) pp_far2<POT>(P.x1, P.y1, P.z1, p, e2, w.x, w.y, w.z, w.p);
         }
         tile_end<POT>(A, u, w, -1.0f);
     }
     __syncwarp();
+}
+
+// Evaluates tiles while a ring holds at least `lim` sources: lim = 32 during
+// the walk (full tiles), lim = 1 at its end (the partial tiles left over).
+template <bool POT, bool TWO>
+__device__ __forceinline__ void drain(WarpSmem &S, int lim, int &pc_head,
+                                      int &pc_n, RangeRing &rf, RangeRing &rn,
+                                      const float4 *cf0, const float4 *cf1,
+                                      const float4 *cf2, const float4 *phi,
+                                      const float4 *plo, const IPair &P,
+                                      int k0, int k1, const ForceConsts &kg,
+                                      GroupAcc<POT> &A, int lane)
+{
+    while (pc_n >= lim)
+        cell_tile<POT, TWO>(S, pc_head, pc_n, min(pc_n, 32), cf0, cf1, cf2, P,
+                            kg.eps2, A, lane);
+    while (rf.np >= lim)
+        particle_tile<false, POT, TWO>(S, S.pf, rf, min(rf.np, 32), phi, plo,
+                                       P, k0, k1, kg, A, lane);
+    while (rn.np >= lim)
+        particle_tile<true, POT, TWO>(S, S.pn, rn, min(rn.np, 32), phi, plo,
+                                      P, k0, k1, kg, A, lane);
 }
 
 template <bool POT>
@@ -504,6 +532,7 @@ k_walk_force(const int *__restrict__ gclus,
         const float hg2 = cc.hg2;
         const int k0 = gr.x + lane, k1 = gr.x + 32 + lane;
         const bool v0 = lane < gr.y, v1 = lane + 32 < gr.y;
+        const bool two = gr.y > 32;  // warp-uniform
         const float4 p0 = v0 ? rel4(phi[k0], plo[k0], ct) : far_pad();
         const float4 p1 = v1 ? rel4(phi[k1], plo[k1], ct) : far_pad();
         const IPair P = {dup2(-p0.x), dup2(-p0.y), dup2(-p0.z),
@@ -595,36 +624,32 @@ k_walk_force(const int *__restrict__ gclus,
             }
             __syncwarp();
             // evaluate every full tile
-            while (pc_n >= 32)
-                cell_tile<POT>(S, pc_head, pc_n, 32, cf0, cf1, cf2, P,
-                               kg.eps2, A, lane);
-            while (rf.np >= 32)
-                particle_tile<false, POT>(S, S.pf, rf, 32, phi, plo, P,
-                                          k0, k1, kg, A, lane);
-            while (rn.np >= 32)
-                particle_tile<true, POT>(S, S.pn, rn, 32, phi, plo, P,
-                                         k0, k1, kg, A, lane);
+            if (two)
+                drain<POT, true>(S, 32, pc_head, pc_n, rf, rn, cf0, cf1, cf2,
+                                 phi, plo, P, k0, k1, kg, A, lane);
+            else
+                drain<POT, false>(S, 32, pc_head, pc_n, rf, rn, cf0, cf1, cf2,
+                                  phi, plo, P, k0, k1, kg, A, lane);
         }
         if (overflow) {
             if (lane == 0) p3t_raise(st, P3T_ERR_CAPACITY);
             continue;
         }
         // the partial tiles left over
-        if (pc_n > 0)
-            cell_tile<POT>(S, pc_head, pc_n, pc_n, cf0, cf1, cf2, P,
-                           kg.eps2, A, lane);
-        if (rf.np > 0)
-            particle_tile<false, POT>(S, S.pf, rf, rf.np, phi, plo, P,
-                                      k0, k1, kg, A, lane);
-        if (rn.np > 0)
-            particle_tile<true, POT>(S, S.pn, rn, rn.np, phi, plo, P,
-                                     k0, k1, kg, A, lane);
+        if (two)
+            drain<POT, true>(S, 1, pc_head, pc_n, rf, rn, cf0, cf1, cf2, phi,
+                             plo, P, k0, k1, kg, A, lane);
+        else
+            drain<POT, false>(S, 1, pc_head, pc_n, rf, rn, cf0, cf1, cf2, phi,
+                              plo, P, k0, k1, kg, A, lane);
         // ---- write back in the caller's order ----
         const float Gc = k.G;
         // work of this group and group of its particles, for the evaluation
         // order of the next build (same weights as the instruction counts
         // per source of the cell, far and near tiles)
-        if (lane == 0) gcost[g] = 16.0f * cnt_pc + 6.0f * cnt_pf + 11.0f * cnt_pn;
+        if (lane == 0)
+            gcost[g] = (two ? 16.0f : 8.0f) * cnt_pc + (two ? 6.0f : 3.0f) * cnt_pf +
+                       (two ? 11.0f : 5.5f) * cnt_pn;
         if (v0) {
             int o = order[k0];
             pgroup[o] = g;
