@@ -579,7 +579,10 @@ __device__ void cell_moments(int c, int4 nd, const double *__restrict__ xs,
                              float4 *__restrict__ cf0, float4 *__restrict__ cf1,
                              float4 *__restrict__ cf2)
 {
+    // Q = 3 S - tr(S) I with S = sum m d d^T about the centre of mass (plus,
+    // for an internal cell, the children's own Q)
     double M = 0.0, com[3] = {0, 0, 0}, Q[6] = {0, 0, 0, 0, 0, 0};
+    double S[6] = {0, 0, 0, 0, 0, 0};
     long long omn[3] = {ORD_HI, ORD_HI, ORD_HI};  // box images (ord64)
     long long omx[3] = {ORD_LO, ORD_LO, ORD_LO};
     const int nch = nd.w & 255;
@@ -614,8 +617,9 @@ __device__ void cell_moments(int c, int4 nd, const double *__restrict__ xs,
                 omx[2] = max(omx[2], oz);
             }
         }
+        const double iM = 1.0 / M;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) com[a] /= M;
+        for (int a = 0; a < 3; ++a) com[a] *= iM;
         for (int kb = k0; kb < k1; kb += LCH) {
             double pm[LCH], px[LCH], py[LCH], pz[LCH];
 #pragma unroll
@@ -633,13 +637,13 @@ __device__ void cell_moments(int c, int4 nd, const double *__restrict__ xs,
                 const double dx = px[u] - com[0];
                 const double dy = py[u] - com[1];
                 const double dz = pz[u] - com[2];
-                const double d2 = dx * dx + dy * dy + dz * dz;
-                Q[0] += m * (3.0 * dx * dx - d2);
-                Q[1] += m * (3.0 * dy * dy - d2);
-                Q[2] += m * (3.0 * dz * dz - d2);
-                Q[3] += m * (3.0 * dx * dy);
-                Q[4] += m * (3.0 * dx * dz);
-                Q[5] += m * (3.0 * dy * dz);
+                const double mx = m * dx, my = m * dy, mz = m * dz;
+                S[0] = fma(mx, dx, S[0]);
+                S[1] = fma(my, dy, S[1]);
+                S[2] = fma(mz, dz, S[2]);
+                S[3] = fma(mx, dy, S[3]);
+                S[4] = fma(mx, dz, S[4]);
+                S[5] = fma(my, dz, S[5]);
             }
         }
     } else {
@@ -667,8 +671,9 @@ __device__ void cell_moments(int c, int4 nd, const double *__restrict__ xs,
             com[1] += cm[q] * cy[q];
             com[2] += cm[q] * cz[q];
         }
+        const double iM = 1.0 / M;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) com[a] /= M;
+        for (int a = 0; a < 3; ++a) com[a] *= iM;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             if (q >= nch) continue;
@@ -677,14 +682,24 @@ __device__ void cell_moments(int c, int4 nd, const double *__restrict__ xs,
             const double dx = cx[q] - com[0];
             const double dy = cy[q] - com[1];
             const double dz = cz[q] - com[2];
-            const double d2 = dx * dx + dy * dy + dz * dz;
+            const double mx = m * dx, my = m * dy, mz = m * dz;
+            S[0] = fma(mx, dx, S[0]);
+            S[1] = fma(my, dy, S[1]);
+            S[2] = fma(mz, dz, S[2]);
+            S[3] = fma(mx, dy, S[3]);
+            S[4] = fma(mx, dz, S[4]);
+            S[5] = fma(my, dz, S[5]);
             const double *qc = cQ + 6 * ch;
-            Q[0] += ld(qc + 0) + m * (3.0 * dx * dx - d2);
-            Q[1] += ld(qc + 1) + m * (3.0 * dy * dy - d2);
-            Q[2] += ld(qc + 2) + m * (3.0 * dz * dz - d2);
-            Q[3] += ld(qc + 3) + m * (3.0 * dx * dy);
-            Q[4] += ld(qc + 4) + m * (3.0 * dx * dz);
-            Q[5] += ld(qc + 5) + m * (3.0 * dy * dz);
+#pragma unroll
+            for (int v = 0; v < 6; ++v) Q[v] += ld(qc + v);
+        }
+    }
+    {
+        const double tr = S[0] + S[1] + S[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Q[a] += fma(3.0, S[a], -tr);
+            Q[3 + a] += 3.0 * S[3 + a];
         }
     }
     double bmn[3], bmx[3];
