@@ -190,7 +190,7 @@ struct CellSrc {
 };
 
 // J^T w for the pair (jx, jy, jz) and the cell adjoints
-// acc = (dL/dM, dL/dcom xyz, S xx yy zz xy xz yz), all without G.
+// acc = (dL/dM, dL/dcom xyz, 2S xx yy zz xy xz yz), all without G.
 __device__ __forceinline__ void cell_pair(const CellSrc &c, f2 nx, f2 ny,
                                           f2 nz, f2 wx, f2 wy, f2 wz, f2 eps2,
                                           f2 (&acc)[10], f2 &jx, f2 &jy,
@@ -218,8 +218,7 @@ __device__ __forceinline__ void cell_pair(const CellSrc &c, f2 nx, f2 ny,
     const f2 cw = fma2(mul2(dup2(2.5f), dqd), ri7, mul2(c.M, ri3));
     const f2 cdi = fma2(mul2(mul2(dqd, wd), ri2), dup2(-17.5f), mul2(dup2(5.0f), wqd));
     const f2 cd = mul2(fma2(cdi, ri2, mul2(c.M3, wd)), ri5);
-    const f2 t7 = mul2(dup2(2.5f), mul2(wd, ri7));  // (5/2) wd / s^7
-    const f2 cq = add2(t7, t7);
+    const f2 cq = mul2(dup2(5.0f), mul2(wd, ri7));  // 5 wd / s^7
     const f2 nri5 = mul2(dup2(-1.0f), ri5);
     jx = fma2(cw, wx, fma2(cd, dx, fma2(cq, qx, mul2(nri5, wqx))));
     jy = fma2(cw, wy, fma2(cd, dy, fma2(cq, qy, mul2(nri5, wqy))));
@@ -228,11 +227,11 @@ __device__ __forceinline__ void cell_pair(const CellSrc &c, f2 nx, f2 ny,
     acc[1] = add2(acc[1], jx);
     acc[2] = add2(acc[2], jy);
     acc[3] = add2(acc[3], jz);
-    // S = -(w d^T + d w^T) / (2 s^5) + (5/2) wd d d^T / s^7, with v = -w / (2 s^5)
-    // and u = t7 d + v: S_ab = d_a u_b + v_a d_b, S_aa = d_a (u_a + v_a)
-    const f2 h5 = mul2(dup2(-0.5f), ri5);
-    const f2 vx = mul2(h5, wx), vy = mul2(h5, wy), vz = mul2(h5, wz);
-    const f2 ux = fma2(t7, dx, vx), uy = fma2(t7, dy, vy), uz = fma2(t7, dz, vz);
+    // 2S = -(w d^T + d w^T) / s^5 + 5 wd d d^T / s^7 (twice the adjoint: its
+    // factors are those of J^T w), with v = -w / s^5 and u = cq d + v:
+    // 2S_ab = d_a u_b + v_a d_b, 2S_aa = d_a (u_a + v_a)
+    const f2 vx = mul2(nri5, wx), vy = mul2(nri5, wy), vz = mul2(nri5, wz);
+    const f2 ux = fma2(cq, dx, vx), uy = fma2(cq, dy, vy), uz = fma2(cq, dz, vz);
     acc[4] = fma2(dx, add2(ux, vx), acc[4]);
     acc[5] = fma2(dy, add2(uy, vy), acc[5]);
     acc[6] = fma2(dz, add2(uz, vz), acc[6]);
@@ -521,7 +520,7 @@ k_walk_vjp(const int *__restrict__ gclus,
     }
 }
 
-// Cell adjoints (aM, acom[3] / M, S xx yy zz xy xz yz) pushed to the member
+// Cell adjoints (aM, acom[3] / M, 2S xx yy zz xy xz yz) pushed to the member
 // particles, FP64; one thread per leaf climbs to the root summing the
 // coefficients of the quadratic form about the leaf's centre of mass, then
 // evaluates it for each member (every particle lies in exactly one leaf).
@@ -551,10 +550,10 @@ k_vjp_leaves(const P3TDevState *__restrict__ st, int n,
             if (any) {
                 const double d[3] = {ccom[3 * c] - r[0], ccom[3 * c + 1] - r[1],
                                      ccom[3 * c + 2] - r[2]};
-                const double tr = A[4] + A[5] + A[6];
-                // T = 3 S - tr(S) I
-                const double T[6] = {3.0 * A[4] - tr, 3.0 * A[5] - tr, 3.0 * A[6] - tr,
-                                     3.0 * A[7], 3.0 * A[8], 3.0 * A[9]};
+                // T = 3 S - tr(S) I, A[4..9] holding 2S
+                const double tr = 0.5 * (A[4] + A[5] + A[6]);
+                const double T[6] = {1.5 * A[4] - tr, 1.5 * A[5] - tr, 1.5 * A[6] - tr,
+                                     1.5 * A[7], 1.5 * A[8], 1.5 * A[9]};
                 const double Td[3] = {T[0] * d[0] + T[3] * d[1] + T[4] * d[2],
                                       T[3] * d[0] + T[1] * d[1] + T[5] * d[2],
                                       T[4] * d[0] + T[5] * d[1] + T[2] * d[2]};
