@@ -190,9 +190,9 @@ int p3t_hard_force(int64_t n, const double *pos, const double *vel,
 
 /* Parameters of the Hermite integration of the hard part. */
 typedef struct p3t_hermite_params {
-    double eta;      /* accuracy parameter of Eq. timestep:0 (Table 1: 0.1);
-                        the first step uses eta / 10 (Eq. timestep:2) */
-    double alpha;    /* a_0 = alpha G m_i / r_cut^2 (Eq. timestep:1; 0.1) */
+    double eta;      /* accuracy parameter of Eq. 18 (Table 1: 0.1);
+                        the first step uses eta / 10 (Eq. 20) */
+    double alpha;    /* a_0 = alpha G m_i / r_cut^2 (Eq. 19; 0.1) */
     double dt_soft;  /* the soft step: the hard part runs over [0, dt_soft];
                         at most 1e300, and dt_soft 2^-(p + kmax) must be a
                         normal double */
@@ -208,8 +208,8 @@ typedef struct p3t_hermite_params {
  * timesteps (Makino & Aarseth 1992):
  *   - time in integer ticks of dt_max 2^-kmax; a particle at level k steps
  *     dt_max 2^-k and its time is a multiple of its step;
- *   - first levels from Eq. timestep:2 (eta / 10), later from
- *     Eq. timestep:0 with a^(2), a^(3) from the Hermite interpolation, both
+ *   - first levels from Eq. 20 (eta / 10), later from
+ *     Eq. 18 with a^(2), a^(3) from the Hermite interpolation, both
  *     tested in squares (dt^2 den <= eta^2 num: no division); a
  *     step may at most double and is halved until the current time is a
  *     multiple of it;

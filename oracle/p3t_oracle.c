@@ -1263,7 +1263,7 @@ typedef struct {
     double irc;    /* 1 / r_cut */
     double iomg;   /* 1 / (1 - gamma) */
     double iomgrc; /* 1 / ((1 - gamma) r_cut) */
-    double a0c;    /* alpha G / r_cut^2: a_0 = a0c m_i (Eq. timestep:1) */
+    double a0c;    /* alpha G / r_cut^2: a_0 = a0c m_i (Eq. 19) */
     double c6, c24, c120;  /* 1/6, 1/24, 1/120 */
     double eta2;   /* eta^2 (later steps) */
     double eta_s2; /* eta_s^2 (first steps) */
@@ -1342,7 +1342,7 @@ void orc_hard_force(int64_t n, const double *x, const double *v,
         orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
 }
 
-/* Block level for a step dt of at most eta sqrt(num / den) (Eq. timestep:0
+/* Block level for a step dt of at most eta sqrt(num / den) (Eq. 18
  * and :2), tested in squares so that it needs neither a division nor the
  * outer square root: dt^2 den <= eta^2 num with e = eta^2 num and
  * dm2 = dt_max^2.  The smallest k in [kmin, kmax] with
@@ -1373,8 +1373,8 @@ static int orc_level(double den, double e, double dm2, int kmin, int kmax,
  * the timestep criteria are tested in squares (orc_level).
  * Time is counted in ticks of dt_max 2^-kmax, dt_max = dt_soft 2^-p.  A
  * particle at level k steps dt_max 2^-k; its time is always a multiple of
- * its step.  First step: Eq. timestep:2 with eta_s = eta / 10; later steps:
- * Eq. timestep:0, a_0 = alpha G m_i / r_cut^2, with a^(2) and a^(3) from
+ * its step.  First step: Eq. 20 with eta_s = eta / 10; later steps:
+ * Eq. 18, a_0 = alpha G m_i / r_cut^2, with a^(2) and a^(3) from
  * the Hermite interpolation of the last step; the level may rise by at most
  * one per step (the step at most doubles) and is raised further until the
  * current time is a multiple of the step.  Each block step: the next time
@@ -1421,7 +1421,7 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
         if (off[i + 1] == off[i]) continue;
         orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
         st[2] += off[i + 1] - off[i];
-        /* Eq. timestep:2: dt^2 |j|^2 <= eta_s^2 (|a|^2 + a0^2) */
+        /* Eq. 20: dt^2 |j|^2 <= eta_s^2 (|a|^2 + a0^2) */
         double a0 = P.a0c * m[i];
         double jj = orc_fdot3(jk + 3 * i, jk + 3 * i);
         double e = P.eta_s2 * fma(a0, a0, orc_fdot3(a + 3 * i, a + 3 * i));
@@ -1479,7 +1479,7 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
             }
             t[i] = tn;
             if (tn == T) continue;
-            /* Eq. timestep:0, with sqrt(A) sqrt(B) taken as sqrt(A B):
+            /* Eq. 18, with sqrt(A) sqrt(B) taken as sqrt(A B):
              * dt^2 (sqrt(|a|^2 |a3|^2) + |a2|^2)
              *     <= eta^2 (sqrt((|a|^2 + a0^2) |a2|^2) + |j|^2) */
             double a0 = P.a0c * m[i];

@@ -455,7 +455,7 @@ class Context:
 @dataclass
 class HermiteParams:
     """Hard-part integration (p3t_hermite_params): eta and alpha of
-    Eq. timestep:0-2, the soft step, dt_max = dt_soft 2^-log2_soft_over_max
+    Eq. 18-20, the soft step, dt_max = dt_soft 2^-log2_soft_over_max
     and the finest level kmax."""
     dt_soft: float
     eta: float = 0.1

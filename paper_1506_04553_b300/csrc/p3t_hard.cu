@@ -34,8 +34,8 @@
 //
 // Time is counted in integer ticks of dt_max 2^-kmax, dt_max = dt_soft 2^-p.
 // A particle at level k steps dt_max 2^-k and its time is a multiple of its
-// step.  First step: Eq. timestep:2 with eta_s = eta / 10; later steps:
-// Eq. timestep:0 with a_0 = alpha G m_i / r_cut^2 and a^(2), a^(3) from the
+// step.  First step: Eq. 20 with eta_s = eta / 10; later steps:
+// Eq. 18 with a_0 = alpha G m_i / r_cut^2 and a^(2), a^(3) from the
 // Hermite interpolation of the step just taken; the step may at most double
 // and is halved until the current time is a multiple of it.  Each block step
 // predicts every member to the next time t_n (the least t_i + dt_i),
@@ -428,7 +428,7 @@ k_root_scatter(int n, const int *__restrict__ parent, const int *__restrict__ cs
 
 struct HermPar {
     HardPar f;
-    double eta2, eta_s2;   // eta^2 (Eq. timestep:0), eta_s^2 (Eq. timestep:2)
+    double eta2, eta_s2;   // eta^2 (Eq. 18), eta_s^2 (Eq. 20)
     double dt_soft, dt_max, tick;
     double dm2;            // dt_max^2
     double idt_max;        // 1 / dt_max: 1 / h = 2^k / dt_max exactly
@@ -455,7 +455,7 @@ __device__ __forceinline__ int level_sq(double den, double e, const HermPar &H,
     return k;
 }
 
-// Forces at t = 0 and first-step levels (Eq. timestep:2) of every particle
+// Forces at t = 0 and first-step levels (Eq. 20) of every particle
 // with neighbours: one thread per entry of the member list (*total entries),
 // so that no lane idles on an isolated particle.
 __global__ void __launch_bounds__(HB)
@@ -475,7 +475,7 @@ k_herm_init(int n, const double *__restrict__ x, const double *__restrict__ v,
         hard_one(i, n, x, v, m, off, idx, H.f, ai, ji, &pairs);
         store3(a, n, i, ai);
         store3(jk, n, i, ji);
-        // Eq. timestep:2: dt^2 |j|^2 <= eta_s^2 (|a|^2 + a0^2)
+        // Eq. 20: dt^2 |j|^2 <= eta_s^2 (|a|^2 + a0^2)
         const double a0 = dmul(H.a0c, m[i]);
         const double jj = dot3(ji[0], ji[1], ji[2], ji[0], ji[1], ji[2]);
         const double e = dmul(H.eta_s2, dfma(a0, a0, dot3(ai[0], ai[1], ai[2], ai[0], ai[1], ai[2])));
@@ -512,7 +512,7 @@ __device__ __forceinline__ void predict_reg(const double x[3], const double v[3]
 
 // Correction at tn of a particle due then: from its prediction (xp, vp), the
 // force and jerk (a, jk) at the start of its step and (a1, j1) at tn, the new
-// x and v; a, jk become a1, j1; then its next level (Eq. timestep:0).
+// x and v; a, jk become a1, j1; then its next level (Eq. 18).
 __device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3],
                                             double jk[3], const double xp[3],
                                             const double vp[3], const double a1[3],
@@ -546,7 +546,7 @@ __device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3
     }
     t = tn;
     if (tn == H.T) return;
-    // Eq. timestep:0, with sqrt(A) sqrt(B) taken as sqrt(A B), in squares:
+    // Eq. 18, with sqrt(A) sqrt(B) taken as sqrt(A B), in squares:
     // dt^2 (sqrt(|a|^2 |a3|^2) + |a2|^2) <= eta^2 (sqrt((|a|^2 + a0^2) |a2|^2) + |j|^2)
     const double a0 = dmul(H.a0c, mi);
     const double aa = dot3(a1[0], a1[1], a1[2], a1[0], a1[1], a1[2]);
