@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-p3t", action="store_true")
     ap.add_argument("--no-king", action="store_true")
+    ap.add_argument("--no-cost-model", action="store_true")
     return ap.parse_args()
 
 
@@ -617,6 +618,8 @@ def run_ours(args, world, rank, local):
         line["p3t_step"] = run_p3t_step(args, dev)
     if not args.no_king:
         line["king"] = run_king(args, dev)
+    if not args.no_cost_model:
+        line["cost_model"] = run_cost_model(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_step, desc = oracle_sample(pos_h, mass_h, frac=1 / 16)
         line["cpu_baseline"] = {"value": n / t_step, "unit": "particles/s",
@@ -835,6 +838,64 @@ def run_king(args, dev):
             "interactions_per_particle": {"pc": prof["int_pc"] / (n * nprof),
                                           "pp": prof["int_pp"] / (n * nprof)},
             "neighbour_pairs": nnz}
+
+
+def run_cost_model(args, dev):
+    """Soft-interaction counts against theta and N, for the cost model of
+    Sect. 3.1.2 (the tree part costs O(theta^-3 N log N) per soft step):
+    Plummer spheres of 2^16, 2^18 and 2^20 particles, theta in {0.3, 0.4,
+    0.5, 0.6, 0.8}, r_out = 0.01 (N/8192)^(-1/3), eps = 4/N, h = r_out.  Per
+    point one build and force evaluation; the force kernel counts its
+    interactions itself.  Reported per point: interactions per particle
+    (cells, particles) and the force time; per N the least-squares exponent
+    of N_int in theta; and N_int / (theta^-3 N ln N) over the grid."""
+    import torch
+    import paper_1506_04553_b300 as P
+    from paper_1506_04553_b300 import ics
+    thetas = (0.3, 0.4, 0.5, 0.6, 0.8)
+    points, fits = [], {}
+    for lg in (16, 18, 20):
+        n = 1 << lg
+        pos_h, _, mass_h = ics.plummer(n, 4000 + lg)
+        r_out = 0.01 * (n / 8192) ** (-1.0 / 3.0)
+        pos = torch.tensor(pos_h, device=dev)
+        mass = torch.tensor(mass_h, device=dev)
+        acc = torch.empty((3, n), dtype=torch.float32, device=dev)
+        tot = []
+        for th in thetas:
+            ctx = P.Context(P.Params(theta=th, r_out=r_out, gamma=GAMMA,
+                                     eps=4.0 / n, h=r_out, G=1.0,
+                                     n_leaf=N_LEAF, n_group=N_GROUP))
+            ctx.build_tree(pos, mass)
+            ctx.long_force(acc)
+            ts = []
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ctx.long_force(acc, check=False)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ctx.check()
+            st = ctx.stats()
+            pc, pp = st["int_pc"] / n, st["int_pp"] / n
+            tot.append(pc + pp)
+            points.append({"n": n, "theta": th, "pc_per_particle": pc,
+                           "pp_per_particle": pp,
+                           "force_ms": float(np.median(ts)),
+                           "ns_per_interaction": float(np.median(ts)) * 1e6
+                           / ((pc + pp) * n),
+                           "n_int_over_model": (pc + pp) * n
+                           / (th ** -3 * n * np.log(n))})
+            del ctx
+        fits[n] = float(np.polyfit(np.log(thetas), np.log(tot), 1)[0])
+    return {"workload": "Plummer N = 2^16, 2^18, 2^20; theta 0.3-0.8; r_out "
+                        "0.01 (N/8192)^(-1/3); eps 4/N; h = r_out; one force "
+                        "evaluation per point",
+            "model": "N_int,soft ~ theta^-3 N ln N per soft step (Sect. 3.1.2)",
+            "theta_exponent": {str(k): v for k, v in fits.items()},
+            "points": points}
 
 
 def run_ensemble(args, dev):
