@@ -140,6 +140,19 @@ def _declare(lib):
     lib.orc_hermite.restype = C.c_int
     lib.orc_hermite.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _d, _d, _d, _d,
                                 _d, _d, C.c_int, C.c_int, _p]
+    lib.orc_direct_species.restype = None
+    lib.orc_direct_species.argtypes = [_i64, _i64, _p, _p, _d, _p, _p, _d,
+                                       C.c_int, _p, _i64, _p, _p, C.c_int]
+    lib.orc_neighbours_species.restype = None
+    lib.orc_neighbours_species.argtypes = [_i64, _i64, _p, _p, _p, _p, _p,
+                                           C.c_int]
+    lib.orc_hard_force_species.restype = None
+    lib.orc_hard_force_species.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _d,
+                                           _p, _p, _d, _p, _p]
+    lib.orc_hermite_species.restype = C.c_int
+    lib.orc_hermite_species.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _d,
+                                        _p, _p, _d, _p, _d, _d, C.c_int,
+                                        C.c_int, _p]
 
 
 def _ptr(a: np.ndarray):
@@ -498,3 +511,99 @@ class Tree:
                                     threads or DEFAULT_THREADS)
         assert rc == 0
         return gx, gm
+
+
+# --------------------------------------------------------------------------
+# Two species (Sect. 3.2.2): stars and black holes
+# --------------------------------------------------------------------------
+# The last n_bh particles are black holes.  A pair of type t (0 star-star,
+# 1 black hole-star, 2 black hole-black hole) takes eps[t], r_cut[t] and the
+# neighbour radius h[t]; r_cut = h = inf for the black hole pair, whose force
+# is not split (F_soft = 0, all of it hard, always a neighbour pair).
+
+def _three(v):
+    a = np.ascontiguousarray(v, dtype=np.float64)
+    if a.shape != (3,):
+        raise ValueError("one value per pair type (3)")
+    return a
+
+
+def direct_species(pos, mass, n_bh, *, eps, r_cut, G=1.0, gamma=0.1,
+                   kind="soft", rows=None, potential=False, threads=None):
+    """direct() with per-pair-type eps and r_cut."""
+    lib = _load()
+    pos = _f64(pos, (-1, 3))
+    mass = _f64(mass)
+    n = pos.shape[0]
+    e3, r3 = _three(eps), _three(r_cut)
+    rws = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nr = n if rws is None else rws.shape[0]
+    acc = np.zeros((nr, 3))
+    pot = np.zeros(nr) if potential else None
+    lib.orc_direct_species(n, int(n_bh), _ptr(pos), _ptr(mass), G, _ptr(e3),
+                           _ptr(r3), gamma, KINDS[kind],
+                           None if rws is None else _ptr(rws), nr, _ptr(acc),
+                           None if pot is None else _ptr(pot),
+                           threads or DEFAULT_THREADS)
+    return (acc, pot) if potential else acc
+
+
+def neighbours_species(pos, n_bh, h, threads=None):
+    """neighbours() with a radius per pair type; returns (offsets, idx)."""
+    lib = _load()
+    pos = _f64(pos, (-1, 3))
+    n = pos.shape[0]
+    h3 = _three(h)
+    th = threads or DEFAULT_THREADS
+    cnt = np.zeros(n, dtype=np.int64)
+    lib.orc_neighbours_species(n, int(n_bh), _ptr(pos), _ptr(h3), None, None,
+                               _ptr(cnt), th)
+    off = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(cnt, out=off[1:])
+    idx = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
+    lib.orc_neighbours_species(n, int(n_bh), _ptr(pos), _ptr(h3), _ptr(off),
+                               _ptr(idx), _ptr(cnt), th)
+    return off, idx[: int(off[-1])]
+
+
+def hard_force_species(pos, vel, mass, off, idx, n_bh, *, eps, r_cut, G=1.0,
+                       gamma=0.1):
+    """hard_force() with per-pair-type eps and r_cut."""
+    lib = _load()
+    pos = _f64(pos, (-1, 3))
+    vel = _f64(vel, (-1, 3))
+    mass = _f64(mass)
+    n = pos.shape[0]
+    off, idx = _csr(off, idx, n)
+    e3, r3 = _three(eps), _three(r_cut)
+    a = np.zeros((n, 3))
+    jk = np.zeros((n, 3))
+    lib.orc_hard_force_species(n, int(n_bh), _ptr(pos), _ptr(vel), _ptr(mass),
+                               _ptr(off), _ptr(idx), G, _ptr(e3), _ptr(r3),
+                               gamma, _ptr(a), _ptr(jk))
+    return a, jk
+
+
+def hermite_species(pos, vel, mass, off, idx, n_bh, *, dt_soft, eps, r_cut,
+                    eta, G=1.0, gamma=0.1, alpha=0.1, p=2, kmax=30):
+    """hermite() with per-pair-type eps and r_cut and eta per species
+    (eta[0] stars, eta[1] black holes); a_0 of a black hole takes the
+    black hole-star cut-off.  Returns (pos, vel, stats)."""
+    lib = _load()
+    pos = _f64(pos, (-1, 3)).copy()
+    vel = _f64(vel, (-1, 3)).copy()
+    mass = _f64(mass)
+    n = pos.shape[0]
+    off, idx = _csr(off, idx, n)
+    e3, r3 = _three(eps), _three(r_cut)
+    et = np.ascontiguousarray(eta, dtype=np.float64)
+    if et.shape != (2,):
+        raise ValueError("one eta per species (2)")
+    st = np.zeros(4, dtype=np.int64)
+    rc = lib.orc_hermite_species(n, int(n_bh), _ptr(pos), _ptr(vel),
+                                 _ptr(mass), _ptr(off), _ptr(idx), G, _ptr(e3),
+                                 _ptr(r3), gamma, _ptr(et), alpha, dt_soft, p,
+                                 kmax, _ptr(st))
+    if rc != 0:
+        raise ValueError("orc_hermite_species: bad arguments")
+    return pos, vel, tuple(int(v) for v in st)

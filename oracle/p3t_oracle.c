@@ -186,7 +186,9 @@ typedef struct {
     int64_t n;
     const double *pos; /* n x 3, row-major */
     const double *m;
-    double G, eps, r_cut, gamma;
+    double G, gamma;
+    double eps[3], r_cut[3]; /* per pair type (see orc_direct_species) */
+    int64_t n_fs;
     int kind;
     double *acc; /* n x 3 */
     double *pot; /* n or NULL */
@@ -212,19 +214,20 @@ static double orc_pot_weight(int kind, double s, double r_cut, double g)
 static void orc_direct_range(void *p, int64_t lo, int64_t hi)
 {
     orc_direct_args *a = (orc_direct_args *)p;
-    double eps2 = a->eps * a->eps;
     for (int64_t r = lo; r < hi; ++r) {
         int64_t i = a->rows ? a->rows[r] : r;
         double ax = 0.0, ay = 0.0, az = 0.0, ph = 0.0;
         for (int64_t j = 0; j < a->n; ++j) {
             if (j == i) continue;
+            const int t = (i >= a->n_fs) + (j >= a->n_fs);
+            const double eps2 = a->eps[t] * a->eps[t], r_cut = a->r_cut[t];
             /* q_ij = q_i - q_j (Eq. 3), s_ij = sqrt(|q_ij|^2 + eps^2) (Eq. 2) */
             double qx = a->pos[3 * i + 0] - a->pos[3 * j + 0];
             double qy = a->pos[3 * i + 1] - a->pos[3 * j + 1];
             double qz = a->pos[3 * i + 2] - a->pos[3 * j + 2];
             double s2 = qx * qx + qy * qy + qz * qz + eps2;
             double s = sqrt(s2);
-            double w = orc_force_weight(a->kind, s, a->r_cut, a->gamma);
+            double w = orc_force_weight(a->kind, s, r_cut, a->gamma);
             if (w != 0.0) {
                 /* acceleration of i: F_i / m_i = -G m_j w q_ij / s^3 */
                 double f = -a->G * a->m[j] * w / (s2 * s);
@@ -233,7 +236,7 @@ static void orc_direct_range(void *p, int64_t lo, int64_t hi)
                 az += f * qz;
             }
             if (a->pot) ph -= a->G * a->m[j]
-                              * orc_pot_weight(a->kind, s, a->r_cut, a->gamma);
+                              * orc_pot_weight(a->kind, s, r_cut, a->gamma);
         }
         a->acc[3 * r + 0] = ax;
         a->acc[3 * r + 1] = ay;
@@ -250,8 +253,25 @@ void orc_direct(int64_t n, const double *pos, const double *m, double G,
                 const int64_t *rows, int64_t nr, double *acc, double *pot,
                 int nthreads)
 {
-    orc_direct_args a = {n, pos, m, G, eps, r_cut, gamma, kind, acc, pot,
+    orc_direct_args a = {n, pos, m, G, gamma, {eps, eps, eps},
+                         {r_cut, r_cut, r_cut}, INT64_MAX, kind, acc, pot,
                          rows};
+    orc_parallel_for(rows ? nr : n, nthreads, orc_direct_range, &a);
+}
+
+/* The same with two species (Sect. 3.2.2): the last n_bh particles are black
+ * holes, and a pair of type t (0 star-star, 1 black hole-star, 2 black
+ * hole-black hole) takes eps[t] and r_cut[t].  r_cut = infinity means the
+ * force is not split: K = 0, all of it hard (the black hole pair). */
+void orc_direct_species(int64_t n, int64_t n_bh, const double *pos,
+                        const double *m, double G, const double *eps,
+                        const double *r_cut, double gamma, int kind,
+                        const int64_t *rows, int64_t nr, double *acc,
+                        double *pot, int nthreads)
+{
+    orc_direct_args a = {n, pos, m, G, gamma, {eps[0], eps[1], eps[2]},
+                         {r_cut[0], r_cut[1], r_cut[2]}, n - n_bh, kind, acc,
+                         pot, rows};
     orc_parallel_for(rows ? nr : n, nthreads, orc_direct_range, &a);
 }
 
@@ -273,7 +293,8 @@ int orc_is_neighbour(const double *pi, const double *pj, double h)
 typedef struct {
     int64_t n;
     const double *pos;
-    double h;
+    double h[3];  /* per pair type */
+    int64_t n_fs;
     const int64_t *rows;
     int64_t *count; /* per row */
     const int64_t *offsets; /* NULL in the counting pass */
@@ -288,7 +309,8 @@ static void orc_ngb_range(void *p, int64_t lo, int64_t hi)
         int64_t c = 0;
         for (int64_t j = 0; j < a->n; ++j) {
             if (j == i) continue;
-            if (orc_is_neighbour(a->pos + 3 * i, a->pos + 3 * j, a->h)) {
+            const int t = (i >= a->n_fs) + (j >= a->n_fs);
+            if (orc_is_neighbour(a->pos + 3 * i, a->pos + 3 * j, a->h[t])) {
                 if (a->offsets) a->idx[a->offsets[r] + c] = (int32_t)j;
                 ++c;
             }
@@ -302,7 +324,7 @@ void orc_neighbours_count(int64_t n, const double *pos, double h,
                           const int64_t *rows, int64_t nr, int64_t *count,
                           int nthreads)
 {
-    orc_ngb_args a = {n, pos, h, rows, count, NULL, NULL};
+    orc_ngb_args a = {n, pos, {h, h, h}, INT64_MAX, rows, count, NULL, NULL};
     orc_parallel_for(rows ? nr : n, nthreads, orc_ngb_range, &a);
 }
 
@@ -312,8 +334,22 @@ void orc_neighbours_fill(int64_t n, const double *pos, double h,
                          const int64_t *offsets, int32_t *idx, int64_t *count,
                          int nthreads)
 {
-    orc_ngb_args a = {n, pos, h, rows, count, offsets, idx};
+    orc_ngb_args a = {n, pos, {h, h, h}, INT64_MAX, rows, count, offsets, idx};
     orc_parallel_for(rows ? nr : n, nthreads, orc_ngb_range, &a);
+}
+
+/* Both passes with two species (Sect. 3.2.2): the last n_bh particles are
+ * black holes and a pair of type t (0 star-star, 1 black hole-star, 2 black
+ * hole-black hole) is a neighbour pair within h[t]; h = infinity makes every
+ * such pair one (the black holes, whose force is not split).  offsets ==
+ * NULL counts, else fills. */
+void orc_neighbours_species(int64_t n, int64_t n_bh, const double *pos,
+                            const double *h, const int64_t *offsets,
+                            int32_t *idx, int64_t *count, int nthreads)
+{
+    orc_ngb_args a = {n, pos, {h[0], h[1], h[2]}, n - n_bh, NULL, count,
+                      offsets, idx};
+    orc_parallel_for(n, nthreads, orc_ngb_range, &a);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1257,30 +1293,52 @@ static double orc_hdK(double x)
     return x3 * fma(fma(fma(-140.0, x, 420.0), x, -420.0), x, 140.0);
 }
 
+/* Per pair type: softening and cut-off.  Types (Sect. 3.2.2): 0 star-star,
+ * 1 black hole-star, 2 black hole-black hole.  The black holes are the last
+ * n_bh particles; the type of (i, j) is [i >= n_fs] + [j >= n_fs].  Between
+ * black holes the force is not split (F_soft = 0): 1 / r_cut = 0, so that
+ * x = -gamma / (1 - gamma) < 0 and K = 0. */
+typedef struct {
+    double eps2;
+    double irc;    /* 1 / r_cut (0: not split) */
+    double iomgrc; /* 1 / ((1 - gamma) r_cut) */
+} orc_pair_par;
+
 /* Constants of the hard part, each computed once in this order. */
 typedef struct {
-    double G, eps2, r_cut, gamma;
-    double irc;    /* 1 / r_cut */
+    double G, gamma;
     double iomg;   /* 1 / (1 - gamma) */
-    double iomgrc; /* 1 / ((1 - gamma) r_cut) */
-    double a0c;    /* alpha G / r_cut^2: a_0 = a0c m_i (Eq. 19) */
+    orc_pair_par pt[3];
+    int64_t n_fs;  /* particles [n_fs, n) are black holes */
+    double a0c[2]; /* per species: alpha G / r_cut^2, a_0 = a0c m_i (Eq. 19) */
     double c6, c24, c120;  /* 1/6, 1/24, 1/120 */
-    double eta2;   /* eta^2 (later steps) */
-    double eta_s2; /* eta_s^2 (first steps) */
+    double eta2[2];   /* per species: eta^2 (later steps) */
+    double eta_s2[2]; /* per species: eta_s^2 (first steps) */
 } orc_hard_par;
 
+static orc_pair_par orc_pair_par_make(double eps, double r_cut, double gamma)
+{
+    orc_pair_par q;
+    q.eps2 = eps * eps;
+    q.irc = isinf(r_cut) ? 0.0 : 1.0 / r_cut;
+    q.iomgrc = isinf(r_cut) ? 0.0 : 1.0 / ((1.0 - gamma) * r_cut);
+    return q;
+}
+
+/* One species (every particle a star): the parameters of the plain path. */
 static orc_hard_par orc_hard_par_make(double G, double eps, double r_cut,
                                       double gamma, double alpha)
 {
     orc_hard_par P;
     P.G = G;
-    P.eps2 = eps * eps;
-    P.r_cut = r_cut;
     P.gamma = gamma;
-    P.irc = 1.0 / r_cut;
     P.iomg = 1.0 / (1.0 - gamma);
-    P.iomgrc = 1.0 / ((1.0 - gamma) * r_cut);
-    P.a0c = alpha * G / (r_cut * r_cut);
+    P.pt[0] = orc_pair_par_make(eps, r_cut, gamma);
+    P.pt[1] = P.pt[0];
+    P.pt[2] = P.pt[0];
+    P.n_fs = INT64_MAX;
+    P.a0c[0] = alpha * G / (r_cut * r_cut);
+    P.a0c[1] = P.a0c[0];
     P.c6 = 1.0 / 6.0;
     P.c24 = 1.0 / 24.0;
     P.c120 = 1.0 / 120.0;
@@ -1302,19 +1360,20 @@ static void orc_hard_one(int64_t i, const double *x, const double *v,
     double acc[3] = {0.0, 0.0, 0.0}, jrk[3] = {0.0, 0.0, 0.0};
     for (int64_t e = off[i]; e < off[i + 1]; ++e) {
         int64_t j = idx[e];
+        const orc_pair_par *pp = &P->pt[(i >= P->n_fs) + (j >= P->n_fs)];
         double q[3], u[3];
         for (int c = 0; c < 3; ++c) {
             q[c] = x[3 * i + c] - x[3 * j + c];
             u[c] = v[3 * i + c] - v[3 * j + c];
         }
-        double s2 = fma(q[0], q[0], fma(q[1], q[1], fma(q[2], q[2], P->eps2)));
+        double s2 = fma(q[0], q[0], fma(q[1], q[1], fma(q[2], q[2], pp->eps2)));
         double s = sqrt(s2);
         double ri = 1.0 / s;
         double ri2 = ri * ri;
         double ri3 = ri2 * ri;
-        double xk = fma(s, P->irc, -P->gamma) * P->iomg;
+        double xk = fma(s, pp->irc, -P->gamma) * P->iomg;
         double w = 1.0 - orc_hK(xk);
-        double dKds = orc_hdK(xk) * P->iomgrc;
+        double dKds = orc_hdK(xk) * pp->iomgrc;
         double rv = orc_fdot3(q, u);
         double gm = P->G * m[j];
         double fa = gm * w * ri3;
@@ -1342,8 +1401,23 @@ void orc_hard_force(int64_t n, const double *x, const double *v,
         orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
 }
 
+/* The same with two species: the last n_bh particles are black holes and a
+ * pair of type t takes eps[t] and r_cut[t] (as orc_hermite_species). */
+void orc_hard_force_species(int64_t n, int64_t n_bh, const double *x,
+                            const double *v, const double *m,
+                            const int64_t *off, const int32_t *idx, double G,
+                            const double *eps, const double *r_cut,
+                            double gamma, double *a, double *jk)
+{
+    orc_hard_par P = orc_hard_par_make(G, eps[0], r_cut[0], gamma, 0.0);
+    for (int t = 1; t < 3; ++t) P.pt[t] = orc_pair_par_make(eps[t], r_cut[t], gamma);
+    P.n_fs = n - n_bh;
+    for (int64_t i = 0; i < n; ++i)
+        orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
+}
+
 /* Block level for a step dt of at most eta sqrt(num / den) (Eq. 18
- * and :2), tested in squares so that it needs neither a division nor the
+ * and Eq. 20), tested in squares so that it needs neither a division nor the
  * outer square root: dt^2 den <= eta^2 num with e = eta^2 num and
  * dm2 = dt_max^2.  The smallest k in [kmin, kmax] with
  * (dt_max 2^-k)^2 den <= e (kmax when none is); *capped is set when even
@@ -1388,21 +1462,60 @@ static int orc_level(double den, double e, double dm2, int kmin, int kmax,
  * stats (may be NULL): [0] block steps, [1] particle steps, [2] pair
  * evaluations, [3] steps whose level was capped at kmax.
  * Returns 0, or -1 on bad arguments or allocation failure. */
+static int orc_hermite_run(int64_t n, double *x, double *v, const double *m,
+                           const int64_t *off, const int32_t *idx,
+                           orc_hard_par P, double dt_soft, int p, int kmax,
+                           int64_t *stats);
+
 int orc_hermite(int64_t n, double *x, double *v, const double *m,
                 const int64_t *off, const int32_t *idx, double G, double eps,
                 double r_cut, double gamma, double eta, double alpha,
                 double dt_soft, int p, int kmax, int64_t *stats)
 {
-    if (n < 0 || p < 0 || kmax < 0 || p + kmax > 60) return -1;
     orc_hard_par P = orc_hard_par_make(G, eps, r_cut, gamma, alpha);
+    const double eta_s = eta / 10.0;
+    P.eta2[0] = P.eta2[1] = eta * eta;
+    P.eta_s2[0] = P.eta_s2[1] = eta_s * eta_s;
+    return orc_hermite_run(n, x, v, m, off, idx, P, dt_soft, p, kmax, stats);
+}
+
+/* The same with two species (Sect. 3.2.2): the last n_bh particles are black
+ * holes.  Pair types 0 star-star, 1 black hole-star, 2 black hole-black
+ * hole take eps[t] and r_cut[t] (r_cut[2] = infinity: not split, K = 0);
+ * species s takes eta[s] (eta_s = eta / 10 on the first step) and
+ * a_0 = alpha G m_i / r_cut^2 with the cut-off of its own pairs with stars,
+ * r_cut[s]. */
+int orc_hermite_species(int64_t n, int64_t n_bh, double *x, double *v,
+                        const double *m, const int64_t *off,
+                        const int32_t *idx, double G, const double *eps,
+                        const double *r_cut, double gamma, const double *eta,
+                        double alpha, double dt_soft, int p, int kmax,
+                        int64_t *stats)
+{
+    if (n_bh < 0 || n_bh > n) return -1;
+    orc_hard_par P = orc_hard_par_make(G, eps[0], r_cut[0], gamma, alpha);
+    for (int t = 1; t < 3; ++t) P.pt[t] = orc_pair_par_make(eps[t], r_cut[t], gamma);
+    P.n_fs = n - n_bh;
+    P.a0c[1] = alpha * G / (r_cut[1] * r_cut[1]);
+    for (int sp = 0; sp < 2; ++sp) {
+        const double eta_s = eta[sp] / 10.0;
+        P.eta2[sp] = eta[sp] * eta[sp];
+        P.eta_s2[sp] = eta_s * eta_s;
+    }
+    return orc_hermite_run(n, x, v, m, off, idx, P, dt_soft, p, kmax, stats);
+}
+
+static int orc_hermite_run(int64_t n, double *x, double *v, const double *m,
+                           const int64_t *off, const int32_t *idx,
+                           orc_hard_par P, double dt_soft, int p, int kmax,
+                           int64_t *stats)
+{
+    if (n < 0 || p < 0 || kmax < 0 || p + kmax > 60) return -1;
     const double dt_max = ldexp(dt_soft, -p);
     const double tick = ldexp(dt_max, -kmax);
     const int64_t T = (int64_t)1 << (p + kmax);
-    const double eta_s = eta / 10.0;
     const double dm2 = dt_max * dt_max;
     int capped = 0;
-    P.eta2 = eta * eta;
-    P.eta_s2 = eta_s * eta_s;
     int64_t st[4] = {0, 0, 0, 0};
     double *a = malloc(3 * n * sizeof(double) + 1);
     double *jk = malloc(3 * n * sizeof(double) + 1);
@@ -1422,9 +1535,10 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
         orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
         st[2] += off[i + 1] - off[i];
         /* Eq. 20: dt^2 |j|^2 <= eta_s^2 (|a|^2 + a0^2) */
-        double a0 = P.a0c * m[i];
+        const int sp = i >= P.n_fs;
+        double a0 = P.a0c[sp] * m[i];
         double jj = orc_fdot3(jk + 3 * i, jk + 3 * i);
-        double e = P.eta_s2 * fma(a0, a0, orc_fdot3(a + 3 * i, a + 3 * i));
+        double e = P.eta_s2[sp] * fma(a0, a0, orc_fdot3(a + 3 * i, a + 3 * i));
         lev[i] = orc_level(jj, e, dm2, 0, kmax, &capped);
         st[3] += capped;
     }
@@ -1482,13 +1596,14 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
             /* Eq. 18, with sqrt(A) sqrt(B) taken as sqrt(A B):
              * dt^2 (sqrt(|a|^2 |a3|^2) + |a2|^2)
              *     <= eta^2 (sqrt((|a|^2 + a0^2) |a2|^2) + |j|^2) */
-            double a0 = P.a0c * m[i];
+            const int sp = i >= P.n_fs;
+            double a0 = P.a0c[sp] * m[i];
             double aa = orc_fdot3(a1, a1);
             double a2sq = orc_fdot3(a2e, a2e);
             double num = sqrt(fma(a0, a0, aa) * a2sq) + orc_fdot3(j1, j1);
             double den = sqrt(aa * orc_fdot3(a3, a3)) + a2sq;
             int kmin = lev[i] > 0 ? lev[i] - 1 : 0;
-            int k = orc_level(den, P.eta2 * num, dm2, kmin, kmax, &capped);
+            int k = orc_level(den, P.eta2[sp] * num, dm2, kmin, kmax, &capped);
             st[3] += capped;
             while (tn % ((int64_t)1 << (kmax - k)) != 0) ++k;
             lev[i] = k;
