@@ -122,6 +122,39 @@ int p3t_build_tree(p3t_ctx *ctx, int64_t n, const double *pos,
 int p3t_set_ensemble(p3t_ctx *ctx, int32_t n_clusters, const int64_t *off,
                      const double *r_out, const double *eps, const double *h);
 
+/* Two species (Sect. 3.2.2): stars and black holes, with a cut-off per kind
+ * of pair. */
+typedef struct p3t_species {
+    double r_cut_bh; /* cut-off of a black hole-star pair (paper: 1/32) */
+    double eps_bh;   /* softening of a black hole-star pair (paper: 1e-4) */
+    double h_bh;     /* neighbour radius of a black hole-star pair
+                        (r_cut_bh + dr_buff), >= 0 */
+    double eta_bh;   /* Hermite accuracy parameter of the black holes
+                        (paper: 0.03); the stars use p3t_hermite_params.eta */
+} p3t_species;
+
+/* The last n_bh of the n particles are black holes (1 <= n_bh < n; n_bh = 0
+ * switches species off).  Pairs of stars keep the context's r_out, eps and
+ * h.  A black hole and a star: r_cut_bh, eps_bh, h_bh.  Two black holes: the
+ * force is not split (F_soft = 0, all of it hard), not softened, and they
+ * are always neighbours.  Applies from the next p3t_build_tree, whose n must
+ * be this n:
+ *  - p3t_build_tree: one tree over the stars, one over the black holes;
+ *  - p3t_long_force: star pairs by the tree; black hole-star pairs by direct
+ *    FP64 summation, added to the result; nothing between black holes (the
+ *    potential between black holes is W(s / 1e10) / s, below 3e-10 G m);
+ *  - p3t_neighbours: a star's row is its stars by the tree, then the black
+ *    holes within h_bh (their indices are the largest, so rows stay
+ *    ascending); a black hole's row is the stars within h_bh, then every
+ *    other black hole;
+ *  - p3t_hard_step: pair constants by pair type; eta and a_0 per species, a
+ *    black hole's a_0 = alpha G m / r_cut_bh^2.
+ * Replaces any ensemble layout (p3t_set_ensemble replaces it in turn).
+ * p3t_long_force_vjp returns P3T_ERR_STATE while species are set.
+ * Errors: P3T_ERR_INVALID. */
+int p3t_set_species(p3t_ctx *ctx, int64_t n, int64_t n_bh,
+                    const p3t_species *sp);
+
 /* Autotuner: times p3t_build_tree + p3t_long_force (best of `reps`) for
  * n_group in {32, 48, 64} and n_leaf in {8, 16, 32} on the given particles
  * and keeps the fastest pair in the context's parameters (the tree is left

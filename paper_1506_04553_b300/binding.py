@@ -105,6 +105,7 @@ _sigs = {
     "p3t_check": [_vp, _vp],
     "p3t_long_force_vjp": [_vp, _vp, _vp, _vp, _vp],
     "p3t_set_ensemble": [_vp, C.c_int32, _vp, _vp, _vp, _vp],
+    "p3t_set_species": [_vp, C.c_int64, C.c_int64, _vp],
     "p3t_autotune": [_vp, _i64, _vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp],
     "p3t_get_profile": [_vp, _vp, C.c_int],
     "p3t_alu_peaks": [_vp, _vp, _vp],
@@ -237,6 +238,17 @@ class Context:
             *[None if a is None else _np_ptr(a) for a in arrs]),
             "p3t_set_ensemble")
         self._ens = (off, arrs)  # keep the host arrays alive
+
+    def set_species(self, n, n_bh, r_cut_bh=0.0, eps_bh=0.0, h_bh=0.0,
+                    eta_bh=0.03):
+        """Two species (p3t_set_species, Sect. 3.2.2): the last n_bh of the
+        n particles are black holes with their own cut-off, softening and
+        neighbour radius against stars and their own eta; n_bh = 0 turns
+        species off."""
+        sp = _Species(r_cut_bh, eps_bh, h_bh, eta_bh)
+        _check(_lib.p3t_set_species(self._h, int(n), int(n_bh),
+                                    C.byref(sp) if n_bh else None),
+               "p3t_set_species")
 
     def autotune(self, pos, mass, reps=2, stream=None):
         """Time build + force for n_group in {32, 48, 64} x n_leaf in
@@ -450,6 +462,11 @@ class Context:
         for k in ("pc", "ppn", "ppf"):
             out[k] = out[k][: int(offs[k + "_off"][-1])]
         return out
+
+
+class _Species(C.Structure):
+    _fields_ = [("r_cut_bh", C.c_double), ("eps_bh", C.c_double),
+                ("h_bh", C.c_double), ("eta_bh", C.c_double)]
 
 
 @dataclass

@@ -282,7 +282,8 @@ void free_all(p3t_ctx *c)
                     c->clus_off, c->cc, c->clus_box, c->pclus, c->gclus,
                     c->gperm, c->gcost, c->pgroup, c->leaf_list, c->leaf_sorted, c->cpend, c->hparent, c->hcsize,
                     c->hcfill, c->hmember, c->hlev, c->hcstart, c->ht, c->ha,
-                    c->hj, c->hxp, c->hvp, c->hroots, c->hloc, c->hbucket};
+                    c->hj, c->hxp, c->hvp, c->hroots, c->hloc, c->hbucket,
+                    c->sp_off, c->sp_idx, c->sp_inv, c->sp_bh, c->sp_part};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->hst) cudaFreeHost(c->hst);
@@ -436,6 +437,7 @@ int p3t_set_ensemble(p3t_ctx *c, int32_t n_clusters, const int64_t *off,
                      const double *r_out, const double *eps, const double *h)
 {
     if (!c || n_clusters < 0) return P3T_ERR_INVALID;
+    c->n_bh = 0;
     if (n_clusters == 0) {
         c->ensemble = 0;
         c->built = 0;
@@ -462,6 +464,44 @@ int p3t_set_ensemble(p3t_ctx *c, int32_t n_clusters, const int64_t *off,
     return P3T_OK;
 }
 
+int p3t_set_species(p3t_ctx *c, int64_t n, int64_t n_bh, const p3t_species *sp)
+{
+    if (!c || n_bh < 0) return P3T_ERR_INVALID;
+    if (n_bh == 0) return p3t_set_ensemble(c, 0, nullptr, nullptr, nullptr, nullptr);
+    if (!sp || n_bh > 32 || n_bh >= n || n > 0x7fffff00LL) return P3T_ERR_INVALID;
+    if (!(sp->r_cut_bh >= P3T_R_OUT_MIN) || !isfinite(sp->r_cut_bh) ||
+        !(sp->eps_bh >= 0.0) || !isfinite(sp->eps_bh) || !(sp->h_bh >= 0.0) ||
+        !isfinite(sp->h_bh) || !(sp->eta_bh > 0.0) || !isfinite(sp->eta_bh))
+        return P3T_ERR_INVALID;
+    // two clusters: the stars with the context's r_out, eps and h (the
+    // per-cluster values 0, -1, 0 select them), the black holes with K = 0
+    // (r_out 1e10) and a neighbour radius that admits no pair (its square
+    // underflows to 0): the black hole-star pairs and the black hole pairs
+    // are added by the species kernels
+    P3T_TRY(ensure_clusters(c, 2));
+    c->nclus = 2;
+    c->clus_off_h[0] = 0;
+    c->clus_off_h[1] = n - n_bh;
+    c->clus_off_h[2] = n;
+    c->clus_par[0] = 0.0;
+    c->clus_par[1] = 1e10;
+    c->clus_par[c->cap_clus + 0] = -1.0;
+    c->clus_par[c->cap_clus + 1] = 0.0;
+    c->clus_par[2 * c->cap_clus + 0] = 0.0;
+    c->clus_par[2 * c->cap_clus + 1] = 1e-300;
+    const int64_t nblk = (n - n_bh + 255) / 256;
+    int64_t d = 0;
+    P3T_TRY(grow(c->sp_off, d, n + 1, sizeof(long long)));
+    P3T_TRY(grow(c->sp_inv, d, n, sizeof(int)));
+    P3T_TRY(grow(c->sp_bh, d, 32 + nblk * n_bh, sizeof(int)));
+    P3T_TRY(grow(c->sp_part, d, 4 * nblk * n_bh, sizeof(double)));
+    c->ensemble = 1;
+    c->built = 0;
+    c->n_bh = n_bh;
+    c->sp = *sp;
+    return P3T_OK;
+}
+
 int p3t_long_force(p3t_ctx *c, float *acc, double *pot, void *stream)
 {
     if (!c) return P3T_ERR_INVALID;
@@ -482,6 +522,7 @@ int p3t_long_force_vjp(p3t_ctx *c, const float *w, double *grad_pos,
     if (!c->built) return P3T_ERR_STATE;
     if (c->n == 0) return P3T_OK;
     if (!w || !grad_pos || !grad_mass) return P3T_ERR_INVALID;
+    if (c->n_bh > 0) return P3T_ERR_STATE;  // no gradient of the species terms
     const int64_t need = 10 * (int64_t)c->cap_cells;
     if (need > c->cap_cadj) {
         if (c->p.flags & P3T_FLAG_NO_SYNC) return P3T_ERR_CAPACITY;
@@ -535,7 +576,9 @@ int p3t_hard_step(p3t_ctx *c, int64_t n, double *pos, double *vel,
                   void *stream)
 {
     if (!c || !hp || n < 0 || n > INT32_MAX - 1) return P3T_ERR_INVALID;
-    if (c->ensemble) return P3T_ERR_INVALID;
+    // an ensemble layout only as the two species, with their n
+    if (c->ensemble && (c->n_bh == 0 || n != c->clus_off_h[c->nclus]))
+        return P3T_ERR_INVALID;
     if (n > 0 && (!pos || !vel || !mass || !offsets || !idx))
         return P3T_ERR_INVALID;
     if (!(hp->eta > 0.0) || !isfinite(hp->eta) || !(hp->alpha >= 0.0) ||
@@ -578,6 +621,23 @@ int p3t_neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, int64_t cap,
         return P3T_OK;
     }
     int slot = p3t_prof_open(c, P3T_PH_NGB, s);
+    if (c->n_bh > 0) {
+        long long nnz = 0;
+        int rc = p3t_run_ngb_species(c, (long long *)offsets, idx, cap,
+                                     needed ? &nnz : nullptr, s);
+        p3t_prof_close(c, slot, s);
+        if (needed) {
+            *needed = nnz;
+            if (rc == P3T_OK) {
+                rc = sync_state(c, s);
+                if (rc == P3T_OK && c->hst->error) {
+                    rc = c->hst->error;
+                    clear_error(c, s);
+                }
+            }
+        }
+        return rc;
+    }
     int rc = p3t_run_ngb(c, 0, nullptr, nullptr, 0, s);
     if (rc == P3T_OK)
         rc = p3t_scan_ll(c, c->ngb_cnt, (long long *)offsets, n, s);

@@ -720,6 +720,107 @@ ForceConsts make_consts(const p3t_params &p)
     return k;
 }
 
+// ---- two species (Sect. 3.2.2): black hole-star soft forces ----
+// The tree evaluates star-star pairs (and zero between black holes, whose
+// cluster has K = 0).  Each black hole-star pair is evaluated once, in FP64,
+// by the star's thread (sorted order: stars first, then the black holes):
+// with d = x_b - x_i, s^2 = |d|^2 + eps_bh^2 and y = s / r_cut_bh,
+//   a_i += G m_b K(y) d / s^3,   a_b -= G m_i K(y) d / s^3,
+//   phi_i -= G m_b W(y) / s,     phi_b -= G m_i W(y) / s.
+// The black holes' terms are summed per block, then per black hole over the
+// blocks in block order (deterministic).
+constexpr int SFB = 256;
+
+__device__ __forceinline__ double k_of_x64(double x)
+{
+    if (x <= 0.0) return 0.0;
+    if (x >= 1.0) return 1.0;
+    const double x2 = x * x;
+    return x2 * x2 * fma(fma(fma(-20.0, x, 70.0), x, -84.0), x, 35.0);
+}
+
+__global__ void __launch_bounds__(SFB)
+k_sp_soft(int n, int nfs, int nbh, const double *__restrict__ xs,
+          const double *__restrict__ ms, const int *__restrict__ order,
+          ForceConsts kb, double G, double eps2, float *__restrict__ acc,
+          double *__restrict__ pot, double *__restrict__ part)
+{
+    __shared__ double red[SFB / 32][4];
+    const int k = blockIdx.x * SFB + threadIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool star = k < nfs;
+    const double xi = star ? xs[k] : 0.0, yi = star ? xs[(size_t)n + k] : 0.0,
+                 zi = star ? xs[2 * (size_t)n + k] : 0.0;
+    const double mi = star ? ms[k] : 0.0;
+    const double irc = 1.0 / kb.r_out, iomg = 1.0 / (1.0 - kb.gamma);
+    double ax = 0.0, ay = 0.0, az = 0.0, ph = 0.0;
+    for (int b = 0; b < nbh; ++b) {
+        const int kk = nfs + b;
+        const double dx = xs[kk] - xi, dy = xs[(size_t)n + kk] - yi,
+                     dz = xs[2 * (size_t)n + kk] - zi;
+        const double s2 = dx * dx + dy * dy + dz * dz + eps2;
+        const double sq = sqrt(s2);
+        double f = 0.0, wos = 0.0;
+        if (star) {
+            f = G * k_of_x64((sq * irc - kb.gamma) * iomg) / (s2 * sq);
+            if (pot) wos = G * w_over_s(sq, kb);
+        }
+        const double mb = ms[kk];
+        ax += mb * f * dx;
+        ay += mb * f * dy;
+        az += mb * f * dz;
+        ph -= mb * wos;
+        double r[4] = {-mi * f * dx, -mi * f * dy, -mi * f * dz, -mi * wos};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                r[c] += __shfl_xor_sync(0xffffffffu, r[c], o);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) red[w][c] = r[c];
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            double t = 0.0;
+            for (int q = 0; q < SFB / 32; ++q) t += red[q][threadIdx.x];
+            part[((size_t)blockIdx.x * nbh + b) * 4 + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+    if (star) {
+        const int o = order[k];
+        acc[o] = (float)((double)acc[o] + ax);
+        acc[(size_t)n + o] = (float)((double)acc[(size_t)n + o] + ay);
+        acc[2 * (size_t)n + o] = (float)((double)acc[2 * (size_t)n + o] + az);
+        if (pot) pot[o] += ph;
+    }
+}
+
+// One warp per black hole: its terms summed over the blocks of k_sp_soft.
+__global__ void k_sp_soft_bh(int n, int nfs, int nbh, int nblk,
+                             const int *__restrict__ order,
+                             const double *__restrict__ part,
+                             float *__restrict__ acc, double *__restrict__ pot)
+{
+    const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (b >= nbh) return;
+    double r[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = lane; q < nblk; q += 32)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) r[c] += part[((size_t)q * nbh + b) * 4 + c];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r[c] += __shfl_xor_sync(0xffffffffu, r[c], o);
+    if (lane == 0) {
+        const int o = order[nfs + b];
+        acc[o] = (float)((double)acc[o] + r[0]);
+        acc[(size_t)n + o] = (float)((double)acc[(size_t)n + o] + r[1]);
+        acc[2 * (size_t)n + o] = (float)((double)acc[2 * (size_t)n + o] + r[2]);
+        if (pot) pot[o] += r[3];
+    }
+}
+
 }  // namespace
 
 int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s)
@@ -745,6 +846,19 @@ int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s)
             c->wmax, c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
             c->order, n, k, c->gperm, c->gcost, c->pgroup, acc, pot, c->st);
     p3t_count_launches(1);
+    if (c->n_bh > 0) {
+        const int nbh = (int)c->n_bh, nfs = n - nbh;
+        const int nblk = (nfs + SFB - 1) / SFB;
+        p3t_params q = c->p;
+        q.r_out = c->sp.r_cut_bh;
+        const ForceConsts kb = make_consts(q);
+        k_sp_soft<<<nblk, SFB, 0, s>>>(n, nfs, nbh, c->xs, c->ms, c->order, kb,
+                                       c->p.G, c->sp.eps_bh * c->sp.eps_bh, acc,
+                                       pot, c->sp_part);
+        k_sp_soft_bh<<<1, 32 * 32, 0, s>>>(n, nfs, nbh, nblk, c->order,
+                                           c->sp_part, acc, pot);
+        p3t_count_launches(2);
+    }
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
 }

@@ -98,25 +98,56 @@ __device__ __forceinline__ double dK_of_x(double x)
     return dmul(x3, dfma(dfma(dfma(-140.0, x, 420.0), x, -420.0), x, 140.0));
 }
 
-// Constants of the hard part, formed once on the host in this order.
-struct HardPar {
-    double G, eps2, r_cut, gamma;
+// Softening and cut-off of one pair type.  Types (Sect. 3.2.2): 0 star-
+// star, 1 black hole-star, 2 black hole-black hole; the black holes are the
+// particles from nfs on, so the type of (i, j) is [i >= nfs] + [j >= nfs].
+// r_cut = infinity (the black hole pair, not split): 1 / r_cut = 0, hence
+// x = -gamma / (1 - gamma) < 0 and K = 0.
+struct PairPar {
+    double eps2;
     double irc;     // 1 / r_cut
-    double iomg;    // 1 / (1 - gamma)
     double iomgrc;  // 1 / ((1 - gamma) r_cut)
 };
+
+// Constants of the hard part, formed once on the host in this order.
+struct HardPar {
+    double G, gamma;
+    double iomg;    // 1 / (1 - gamma)
+    PairPar pt[3];
+    int nfs;        // particles [nfs, n) are black holes (INT_MAX: none)
+};
+
+PairPar pair_par(double eps, double r_cut, double gamma)
+{
+    PairPar q;
+    q.eps2 = eps * eps;
+    q.irc = isinf(r_cut) ? 0.0 : 1.0 / r_cut;
+    q.iomgrc = isinf(r_cut) ? 0.0 : 1.0 / ((1.0 - gamma) * r_cut);
+    return q;
+}
 
 HardPar hard_par(double G, double eps, double r_cut, double gamma)
 {
     HardPar P;
     P.G = G;
-    P.eps2 = eps * eps;
-    P.r_cut = r_cut;
     P.gamma = gamma;
-    P.irc = 1.0 / r_cut;
     P.iomg = 1.0 / (1.0 - gamma);
-    P.iomgrc = 1.0 / ((1.0 - gamma) * r_cut);
+    P.pt[0] = pair_par(eps, r_cut, gamma);
+    P.pt[1] = P.pt[0];
+    P.pt[2] = P.pt[0];
+    P.nfs = INT_MAX;
     return P;
+}
+
+// The constants of pair type t, by selects (no indexed access to the
+// parameter block).
+__device__ __forceinline__ PairPar pair_of(const HardPar &P, int t)
+{
+    PairPar q;
+    q.eps2 = t == 0 ? P.pt[0].eps2 : (t == 1 ? P.pt[1].eps2 : P.pt[2].eps2);
+    q.irc = t == 0 ? P.pt[0].irc : (t == 1 ? P.pt[1].irc : P.pt[2].irc);
+    q.iomgrc = t == 0 ? P.pt[0].iomgrc : (t == 1 ? P.pt[1].iomgrc : P.pt[2].iomgrc);
+    return q;
 }
 
 // Hard acceleration and jerk of a particle at (xi, vi) from one neighbour at
@@ -125,19 +156,20 @@ HardPar hard_par(double G, double eps, double r_cut, double gamma)
 __device__ __forceinline__ void pair_add(const double xi[3], const double vi[3],
                                          double xj0, double xj1, double xj2,
                                          double vj0, double vj1, double vj2,
-                                         double mj, const HardPar &P,
+                                         double mj, const HardPar &P, int t,
                                          double acc[3], double jrk[3])
 {
+    const PairPar pp = pair_of(P, t);
     const double q[3] = {dsub(xi[0], xj0), dsub(xi[1], xj1), dsub(xi[2], xj2)};
     const double u[3] = {dsub(vi[0], vj0), dsub(vi[1], vj1), dsub(vi[2], vj2)};
-    const double s2 = dfma(q[0], q[0], dfma(q[1], q[1], dfma(q[2], q[2], P.eps2)));
+    const double s2 = dfma(q[0], q[0], dfma(q[1], q[1], dfma(q[2], q[2], pp.eps2)));
     const double s = dsqrt(s2);
     const double ri = ddiv(1.0, s);
     const double ri2 = dmul(ri, ri);
     const double ri3 = dmul(ri2, ri);
-    const double xk = dmul(dfma(s, P.irc, -P.gamma), P.iomg);
+    const double xk = dmul(dfma(s, pp.irc, -P.gamma), P.iomg);
     const double w = dsub(1.0, K_of_x(xk));
-    const double dKds = dmul(dK_of_x(xk), P.iomgrc);
+    const double dKds = dmul(dK_of_x(xk), pp.iomgrc);
     const double rv = dot3(q[0], q[1], q[2], u[0], u[1], u[2]);
     const double gm = dmul(P.G, mj);
     const double fa = dmul(dmul(gm, w), ri3);
@@ -177,10 +209,12 @@ __device__ void hard_one(int i, int n, const double *x, const double *v,
     load3(x, n, i, xi);
     load3(v, n, i, vi);
     const long long e0 = off[i], e1 = off[i + 1];
+    const int ti = i >= P.nfs;
     for (long long e = e0; e < e1; ++e) {
         const int j = idx[e];
         pair_add(xi, vi, x[j], x[(size_t)n + j], x[2 * (size_t)n + j], v[j],
-                 v[(size_t)n + j], v[2 * (size_t)n + j], m[j], P, acc, jrk);
+                 v[(size_t)n + j], v[2 * (size_t)n + j], m[j], P,
+                 ti + (j >= P.nfs), acc, jrk);
     }
     *pairs += e1 - e0;
 #pragma unroll
@@ -428,11 +462,11 @@ k_root_scatter(int n, const int *__restrict__ parent, const int *__restrict__ cs
 
 struct HermPar {
     HardPar f;
-    double eta2, eta_s2;   // eta^2 (Eq. 18), eta_s^2 (Eq. 20)
+    double eta2[2], eta_s2[2];  // per species: eta^2 (Eq. 18), eta_s^2 (Eq. 20)
     double dt_soft, dt_max, tick;
     double dm2;            // dt_max^2
     double idt_max;        // 1 / dt_max: 1 / h = 2^k / dt_max exactly
-    double a0c;            // alpha G / r_cut^2: a_0 = a0c m_i
+    double a0c[2];         // per species: alpha G / r_cut^2, a_0 = a0c m_i
     double c6, c24, c120;  // 1/6, 1/24, 1/120
     long long T;  // dt_soft in ticks
     int kmax;
@@ -476,9 +510,10 @@ k_herm_init(int n, const double *__restrict__ x, const double *__restrict__ v,
         store3(a, n, i, ai);
         store3(jk, n, i, ji);
         // Eq. 20: dt^2 |j|^2 <= eta_s^2 (|a|^2 + a0^2)
-        const double a0 = dmul(H.a0c, m[i]);
+        const int sp = i >= H.f.nfs;
+        const double a0 = dmul(H.a0c[sp], m[i]);
         const double jj = dot3(ji[0], ji[1], ji[2], ji[0], ji[1], ji[2]);
-        const double e = dmul(H.eta_s2, dfma(a0, a0, dot3(ai[0], ai[1], ai[2], ai[0], ai[1], ai[2])));
+        const double e = dmul(H.eta_s2[sp], dfma(a0, a0, dot3(ai[0], ai[1], ai[2], ai[0], ai[1], ai[2])));
         lev[i] = level_sq(jj, e, H, 0, capped);
     }
     if (pairs) atomicAdd((unsigned long long *)&st->herm[2], (unsigned long long)pairs);
@@ -517,9 +552,9 @@ __device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3
                                             double jk[3], const double xp[3],
                                             const double vp[3], const double a1[3],
                                             const double j1[3], double mi,
-                                            long long tn, const HermPar &H,
-                                            long long &t, int &lev,
-                                            long long &capped)
+                                            int sp, long long tn,
+                                            const HermPar &H, long long &t,
+                                            int &lev, long long &capped)
 {
     // h = 2^(kmax - lev) ticks = dt_max 2^-lev and 1/h = 2^lev / dt_max,
     // both exact scalings (the parameter checks keep them normal), so they
@@ -548,7 +583,7 @@ __device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3
     if (tn == H.T) return;
     // Eq. 18, with sqrt(A) sqrt(B) taken as sqrt(A B), in squares:
     // dt^2 (sqrt(|a|^2 |a3|^2) + |a2|^2) <= eta^2 (sqrt((|a|^2 + a0^2) |a2|^2) + |j|^2)
-    const double a0 = dmul(H.a0c, mi);
+    const double a0 = dmul(H.a0c[sp], mi);
     const double aa = dot3(a1[0], a1[1], a1[2], a1[0], a1[1], a1[2]);
     const double a2sq = dot3(a2e[0], a2e[1], a2e[2], a2e[0], a2e[1], a2e[2]);
     const double num = dadd(dsqrt(dmul(dfma(a0, a0, aa), a2sq)),
@@ -556,7 +591,7 @@ __device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3
     const double den = dadd(dsqrt(dmul(aa, dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]))),
                             a2sq);
     const int kmin = lev > 0 ? lev - 1 : 0;
-    int k = level_sq(den, dmul(H.eta2, num), H, kmin, capped);
+    int k = level_sq(den, dmul(H.eta2[sp], num), H, kmin, capped);
     while (tn % (1LL << (H.kmax - k)) != 0) ++k;
     lev = k;
 }
@@ -595,7 +630,8 @@ __device__ __forceinline__ void correct_one(
     load3(vp, n, i, vq);
     long long ti = t[i];
     int li = lev[i];
-    correct_reg(xn, vn, ai, ji, xq, vq, a1, j1, m[i], tn, H, ti, li, capped);
+    correct_reg(xn, vn, ai, ji, xq, vq, a1, j1, m[i], i >= H.f.nfs, tn, H, ti,
+                li, capped);
     store3(x, n, i, xn);
     store3(v, n, i, vn);
     store3(a, n, i, ai);
@@ -728,6 +764,8 @@ __device__ void integrate_class(int s, const int *__restrict__ croots, int count
             }
         }
         if (!__any_sync(full, have)) break;
+        // black holes among the lanes (pair types, Sect. 3.2.2)
+        const unsigned bhm = __ballot_sync(full, have && i >= H.f.nfs);
         __syncwarp();
         if (fresh && len <= ROW_PACK) {
             row = 0;
@@ -759,11 +797,12 @@ __device__ void integrate_class(int s, const int *__restrict__ croots, int count
                 const int jl = len <= ROW_PACK ? (int)((row >> (5 * q)) & 31)
                                                : loc[idx[e0 + q]] & 31;
                 pair_add(xp, vp, S.xp[0][jl], S.xp[1][jl], S.xp[2][jl],
-                         S.vp[0][jl], S.vp[1][jl], S.vp[2][jl], S.m[jl], H.f, a1,
-                         j1);
+                         S.vp[0][jl], S.vp[1][jl], S.vp[2][jl], S.m[jl], H.f,
+                         (i >= H.f.nfs) + (int)((bhm >> jl) & 1u), a1, j1);
             }
             pairs += len;
-            correct_reg(xs, vs, as, js, xp, vp, a1, j1, mass, tn, H, t, lev, capped);
+            correct_reg(xs, vs, as, js, xp, vp, a1, j1, mass, i >= H.f.nfs, tn, H,
+                        t, lev, capped);
             ++nstep;
         }
         // every member is due at t_n = dt_soft: the component is done
@@ -945,9 +984,20 @@ int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
     HermPar H;
     H.f = hard_par(c->p.G, c->p.eps, c->p.r_out, c->p.gamma);
     const double eta_s = hp->eta / 10.0;
-    H.eta2 = hp->eta * hp->eta;
-    H.eta_s2 = eta_s * eta_s;
-    H.a0c = hp->alpha * c->p.G / (c->p.r_out * c->p.r_out);
+    H.eta2[0] = H.eta2[1] = hp->eta * hp->eta;
+    H.eta_s2[0] = H.eta_s2[1] = eta_s * eta_s;
+    H.a0c[0] = H.a0c[1] = hp->alpha * c->p.G / (c->p.r_out * c->p.r_out);
+    if (c->n_bh > 0) {
+        // two species (Sect. 3.2.2): black holes from n - n_bh on; a black
+        // hole's a_0 takes its cut-off with the stars
+        H.f.pt[1] = pair_par(c->sp.eps_bh, c->sp.r_cut_bh, c->p.gamma);
+        H.f.pt[2] = pair_par(0.0, INFINITY, c->p.gamma);
+        H.f.nfs = n - (int)c->n_bh;
+        H.a0c[1] = hp->alpha * c->p.G / (c->sp.r_cut_bh * c->sp.r_cut_bh);
+        const double eta_sb = c->sp.eta_bh / 10.0;
+        H.eta2[1] = c->sp.eta_bh * c->sp.eta_bh;
+        H.eta_s2[1] = eta_sb * eta_sb;
+    }
     H.c6 = 1.0 / 6.0;
     H.c24 = 1.0 / 24.0;
     H.c120 = 1.0 / 120.0;

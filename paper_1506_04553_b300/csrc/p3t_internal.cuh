@@ -153,7 +153,17 @@ struct p3t_ctx {
     int herm_pad;            // dynamic shared memory of the Hermite kernel
     // clusters (one for a plain build)
     int nclus, cap_clus;
-    int ensemble;            // layout fixed by p3t_set_ensemble
+    int ensemble;            // layout fixed by p3t_set_ensemble or p3t_set_species
+    // two species (p3t_set_species): the last n_bh particles are black holes
+    int64_t n_bh;
+    p3t_species sp;
+    long long *sp_off;       // device [cap_n + 1]: star rows by the tree
+    int *sp_idx;             // device [cap_sp_idx]
+    int64_t cap_sp_idx;
+    int *sp_inv;             // device [cap_n]: sorted position of each index
+    int *sp_bh;              // device [32 + star blocks * n_bh]: black hole
+                             // positions, per-block neighbour counts
+    double *sp_part;         // device [star blocks * n_bh * 4]: force partials
     int64_t *clus_off_h;     // pinned host [nclus + 1]
     ClusterConsts *cc_h;     // pinned host [nclus]
     double *clus_par;        // host [3][nclus]: r_out, eps, h (ensemble)
@@ -277,6 +287,8 @@ void p3t_cluster_consts(const p3t_params *p, double r_out, double eps,
 int p3t_run_walk(p3t_ctx *c, int fill, cudaStream_t s);        // p3t_walk.cu
 int p3t_scan_lists(p3t_ctx *c, cudaStream_t s);                 // p3t_walk.cu
 int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s);   // p3t_force.cu
+int p3t_run_ngb_species(p3t_ctx *c, long long *offsets, int *idx, long long cap,
+                        long long *needed, cudaStream_t s);
 int p3t_run_ngb(p3t_ctx *c, int fill, const long long *row_off, int *idx,
                 long long cap, cudaStream_t s);                  // p3t_ngb.cu
 int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,

@@ -343,6 +343,135 @@ __global__ void k_work_reset(P3TDevState *st, int fill)
     }
 }
 
+// ---- two species (Sect. 3.2.2): rows with the black holes ----
+// The tree gives the star-star rows (the black holes form a cluster of their
+// own whose neighbour radius admits no pair).  The black hole-star pairs
+// within h_bh and the black hole pairs (always neighbours) are added here,
+// in ascending index order: a star's row is its tree row, then the black
+// holes (indices n_fs .. n-1, the largest); a black hole's row is its stars
+// (one thread per star, in index order, ranked by warp ballots and per-block
+// offsets), then the other black holes.  At most 32 black holes.
+constexpr int SPB = 256;  // threads per block of the star passes
+
+// sorted position of every index (inv) and of every black hole (bhpos)
+__global__ void k_sp_inv(int n, int nfs, const int *__restrict__ order,
+                         int *__restrict__ inv, int *__restrict__ bhpos)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += gridDim.x * blockDim.x) {
+        const int o = order[k];
+        inv[o] = k;
+        if (o >= nfs) bhpos[o - nfs] = k;
+    }
+}
+
+// Per star (thread o of block o / SPB): its row length (tree row plus black
+// holes within h_bh) and, per black hole, the block's count of such stars.
+__global__ void __launch_bounds__(SPB)
+k_sp_count(int n, int nfs, int nbh, const double *__restrict__ xs,
+           const int *__restrict__ inv, const int *__restrict__ bhpos,
+           const long long *__restrict__ toff, double h2, int *__restrict__ cnt,
+           int *__restrict__ blockcnt)
+{
+    __shared__ int wc[SPB / 32][32];
+    const int o = blockIdx.x * SPB + threadIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool star = o < nfs;
+    const int k = star ? inv[o] : 0;
+    int mine = 0;
+    for (int b = 0; b < nbh; ++b) {
+        const bool f = star && exact_ngb(xs, n, k, bhpos[b], h2);
+        mine += f;
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wc[w][b] = __popc(m);
+    }
+    if (star) cnt[o] = (int)(toff[o + 1] - toff[o]) + mine;
+    __syncthreads();
+    if (threadIdx.x < nbh) {
+        int t = 0;
+        for (int q = 0; q < SPB / 32; ++q) t += wc[q][threadIdx.x];
+        blockcnt[(size_t)blockIdx.x * nbh + threadIdx.x] = t;
+    }
+}
+
+// One warp per black hole: exclusive scan of its per-block counts, and the
+// length of its row (the stars, then the other black holes).
+__global__ void k_sp_scan_bh(int nblk, int nfs, int nbh, int *__restrict__ blockcnt,
+                             int *__restrict__ cnt)
+{
+    const int b = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (b >= nbh) return;
+    int run = 0;
+    for (int q0 = 0; q0 < nblk; q0 += 32) {
+        const int q = q0 + lane;
+        const int v = q < nblk ? blockcnt[(size_t)q * nbh + b] : 0;
+        const int inc = warp_incl_scan(v);
+        if (q < nblk) blockcnt[(size_t)q * nbh + b] = run + inc - v;
+        run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) cnt[nfs + b] = run + (nbh - 1);
+}
+
+// Rows: every star copies its tree row and appends its black holes; every
+// star within h_bh of black hole b writes its index at its rank in b's row;
+// thread b < nbh of block 0 appends the other black holes to row n_fs + b.
+__global__ void __launch_bounds__(SPB)
+k_sp_fill(int n, int nfs, int nbh, const double *__restrict__ xs,
+          const int *__restrict__ inv, const int *__restrict__ bhpos,
+          const long long *__restrict__ toff, const int *__restrict__ tidx,
+          long long tcap, double h2, const int *__restrict__ blockcnt,
+          const long long *__restrict__ off, int *__restrict__ idx,
+          long long cap, P3TDevState *st)
+{
+    __shared__ int wc[SPB / 32][32];
+    const int o = blockIdx.x * SPB + threadIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool star = o < nfs;
+    const int k = star ? inv[o] : 0;
+    unsigned mine = 0;
+    for (int b = 0; b < nbh; ++b) {
+        const bool f = star && exact_ngb(xs, n, k, bhpos[b], h2);
+        mine |= (unsigned)f << b;
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wc[w][b] = __popc(m);
+    }
+    __syncthreads();
+    if (star) {
+        if (off[o + 1] > cap || toff[o + 1] > tcap) {
+            p3t_raise(st, P3T_ERR_CAPACITY);
+        } else {
+            long long p = off[o];
+            for (long long e = toff[o]; e < toff[o + 1]; ++e) idx[p++] = tidx[e];
+            for (int b = 0; b < nbh; ++b)
+                if ((mine >> b) & 1u) idx[p++] = nfs + b;
+        }
+    }
+    for (int b = 0; b < nbh; ++b) {
+        const bool f = (mine >> b) & 1u;
+        const unsigned m = __ballot_sync(0xffffffffu, f);  // same as above
+        if (!f) continue;
+        int before = 0;
+        for (int q = 0; q < w; ++q) before += wc[q][b];
+        const long long pos = off[nfs + b] + blockcnt[(size_t)blockIdx.x * nbh + b] +
+                              before + __popc(m & lanemask_lt());
+        if (pos < cap)
+            idx[pos] = o;
+        else
+            p3t_raise(st, P3T_ERR_CAPACITY);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < nbh) {
+        const int b = threadIdx.x;
+        const long long e = off[nfs + b + 1];
+        if (e > cap) {
+            p3t_raise(st, P3T_ERR_CAPACITY);
+        } else {
+            long long p = e - (nbh - 1);
+            for (int b2 = 0; b2 < nbh; ++b2)
+                if (b2 != b) idx[p++] = nfs + b2;
+        }
+    }
+}
+
 }  // namespace
 
 // fill == 0: per-particle counts into c->ngb_cnt (and the kept neighbours);
@@ -374,6 +503,61 @@ int p3t_run_ngb(p3t_ctx *c, int fill, const long long *row_off, int *idx,
             row_off, idx, cap, c->gperm, c->ngb_slots, c->ngb_ovf, c->st);
         p3t_count_launches(2);
     }
+    P3T_CUDA_TRY(cudaGetLastError());
+    return P3T_OK;
+}
+
+// Neighbour lists with two species: the tree rows into the context's scratch
+// (sp_off, sp_idx), then the merged rows into the caller's arrays.  needed !=
+// NULL: synchronous, with capacity checks on both (the scratch grows unless
+// P3T_FLAG_NO_SYNC is set).
+int p3t_run_ngb_species(p3t_ctx *c, long long *offsets, int *idx, long long cap,
+                        long long *needed, cudaStream_t s)
+{
+    const int n = (int)c->n, nbh = (int)c->n_bh, nfs = n - nbh;
+    int rc = p3t_run_ngb(c, 0, nullptr, nullptr, 0, s);
+    if (rc == P3T_OK) rc = p3t_scan_ll(c, c->ngb_cnt, c->sp_off, n, s);
+    if (rc != P3T_OK) return rc;
+    if (needed) {
+        long long tnnz = 0;
+        P3T_CUDA_TRY(cudaMemcpyAsync(&tnnz, c->sp_off + n, sizeof(long long),
+                                     cudaMemcpyDeviceToHost, s));
+        P3T_CUDA_TRY(cudaStreamSynchronize(s));
+        if (tnnz > c->cap_sp_idx) {
+            if (c->p.flags & P3T_FLAG_NO_SYNC) return P3T_ERR_CAPACITY;
+            const int64_t want = tnnz + tnnz / 4 + 1024;
+            if (c->sp_idx) cudaFree(c->sp_idx);
+            c->sp_idx = nullptr;
+            c->cap_sp_idx = 0;
+            P3T_CUDA_TRY(cudaMalloc((void **)&c->sp_idx, (size_t)want * sizeof(int)));
+            c->cap_sp_idx = want;
+        }
+    }
+    rc = p3t_run_ngb(c, 1, c->sp_off, c->sp_idx, c->cap_sp_idx, s);
+    if (rc != P3T_OK) return rc;
+    const int g = (n + SPB - 1) / SPB;
+    const int nblk = (nfs + SPB - 1) / SPB;
+    const double h2 = c->sp.h_bh * c->sp.h_bh;
+    int *bhpos = c->sp_bh, *blockcnt = c->sp_bh + 32;
+    k_sp_inv<<<g, SPB, 0, s>>>(n, nfs, c->order, c->sp_inv, bhpos);
+    k_sp_count<<<nblk, SPB, 0, s>>>(n, nfs, nbh, c->xs, c->sp_inv, bhpos,
+                                    c->sp_off, h2, c->ngb_cnt, blockcnt);
+    k_sp_scan_bh<<<1, 32 * 32, 0, s>>>(nblk, nfs, nbh, blockcnt, c->ngb_cnt);
+    p3t_count_launches(3);
+    rc = p3t_scan_ll(c, c->ngb_cnt, offsets, n, s);
+    if (rc != P3T_OK) return rc;
+    if (needed) {
+        long long nnz = 0;
+        P3T_CUDA_TRY(cudaMemcpyAsync(&nnz, offsets + n, sizeof(long long),
+                                     cudaMemcpyDeviceToHost, s));
+        P3T_CUDA_TRY(cudaStreamSynchronize(s));
+        *needed = nnz;
+        if (nnz > cap) return P3T_ERR_CAPACITY;
+    }
+    k_sp_fill<<<nblk, SPB, 0, s>>>(n, nfs, nbh, c->xs, c->sp_inv, bhpos,
+                                   c->sp_off, c->sp_idx, c->cap_sp_idx, h2,
+                                   blockcnt, offsets, idx, cap, c->st);
+    p3t_count_launches(1);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
 }

@@ -1,0 +1,155 @@
+"""Two species on the GPU (p3t_set_species, Sect. 3.2.2: a star cluster
+with black holes, a cut-off per kind of pair) against the oracle: neighbour
+rows bit for bit (star pairs within h, black hole-star pairs within h_bh,
+black hole pairs always); soft forces of the stars against the oracle's
+tree over the stars plus the black holes' direct terms, and of the black
+holes against direct sums; whole hard steps bit for bit with pair
+constants per type and eta per species."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1506_04553_b300 import ics
+from parity_util import rel_err
+
+pytestmark = pytest.mark.gpu
+
+INF = math.inf
+GAMMA = 0.1
+
+
+def _system(n_star, seed, n_bh=2):
+    """Plummer stars (N-body units) and n_bh black holes of 1% of the
+    cluster's mass each, on a ring of radius 0.5 with speed 0.5 (the
+    binary of Sect. 3.2.2 for n_bh = 2)."""
+    pos, vel, m = ics.plummer(n_star, seed)
+    pos, vel = pos.T.copy(), vel.T.copy()
+    ang = 2 * np.pi * np.arange(n_bh) / n_bh
+    bp = np.stack([0.5 * np.cos(ang), 0.5 * np.sin(ang), np.zeros(n_bh)], 1)
+    bv = np.stack([-0.5 * np.sin(ang), 0.5 * np.cos(ang), np.zeros(n_bh)], 1)
+    return (np.concatenate([pos, bp]), np.concatenate([vel, bv]),
+            np.concatenate([m, np.full(n_bh, 0.01)]))
+
+
+P = dict(theta=0.4, r_out=0.01, h=0.0125, eps=1e-4)
+SP = dict(r_cut_bh=1 / 32, eps_bh=1e-4, h_bh=1 / 32 + 0.01, eta_bh=0.03)
+
+
+def _ctx(n, n_bh, **kw):
+    from paper_1506_04553_b300 import Context, Params
+    ctx = Context(Params(gamma=GAMMA, **{**P, **kw}))
+    ctx.set_species(n, n_bh, **SP)
+    return ctx
+
+
+def _dev(a, dtype=None):
+    import torch
+    t = torch.tensor(np.ascontiguousarray(a))
+    return (t.to(dtype) if dtype is not None else t).cuda()
+
+
+@pytest.mark.parametrize("n_bh", [1, 2, 5])
+def test_species_neighbours_bitexact(cuda, n_bh):
+    pos, _, m = _system(20000, 21, n_bh)
+    # put one black hole in the core so that its row is long
+    pos[-1] = [0.01, -0.02, 0.0]
+    n = pos.shape[0]
+    ctx = _ctx(n, n_bh)
+    ctx.build_tree(_dev(pos.T), _dev(m))
+    ctx.long_force()
+    off, idx = ctx.neighbours()
+    off, idx = off.cpu().numpy(), idx.cpu().numpy()
+    off_o, idx_o = oracle.neighbours_species(pos, n_bh, h=[P["h"], SP["h_bh"], INF])
+    assert np.array_equal(off, off_o)
+    assert np.array_equal(idx, idx_o)
+    assert off_o[-1] - off_o[-2] > 5  # the core black hole's row
+
+
+def test_species_soft_force(cuda):
+    pos, _, m = _system(30000, 22)
+    pos[-1] = [0.02, 0.01, -0.01]
+    n, n_bh = pos.shape[0], 2
+    nfs = n - n_bh
+    ctx = _ctx(n, n_bh)
+    ctx.build_tree(_dev(pos.T), _dev(m))
+    acc = ctx.long_force().cpu().numpy().astype(np.float64).T
+    # stars: the tree over the stars (same lists) plus the black holes
+    t = oracle.Tree(pos[:nfs], m[:nfs], n_leaf=16, n_group=64)
+    t.walk(P["theta"], P["h"], P["r_out"])
+    a_tree = t.force(eps=P["eps"], r_cut=P["r_out"], gamma=GAMMA)
+    kw = dict(eps=[P["eps"], SP["eps_bh"], 0.0], r_cut=[P["r_out"], SP["r_cut_bh"], INF],
+              gamma=GAMMA, kind="soft")
+    m_bh_only = m.copy()
+    m_bh_only[:nfs] = 0.0
+    a_cross = oracle.direct_species(pos, m_bh_only, n_bh, rows=np.arange(nfs), **kw)
+    e = rel_err(acc[:nfs], a_tree + a_cross)
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4, (np.median(e), e.max())
+    # black holes: stars only (no soft force between black holes)
+    a_bh = oracle.direct_species(pos, m, n_bh, rows=np.arange(nfs, n), **kw)
+    assert np.allclose(acc[nfs:], a_bh, rtol=1e-6, atol=0)
+    # the core black hole's stars within r_cut_bh are weighted by K < 1
+    assert np.linalg.norm(a_cross, axis=1).max() > 0.1
+
+
+@pytest.mark.parametrize("where", ["core", "far"])
+def test_species_hard_step_bitwise(cuda, where):
+    """A tight black hole binary in the core (one component of the binary
+    and many stars: the per-component warp path) or far out (the binary
+    alone: a packed warp)."""
+    import torch
+    from paper_1506_04553_b300 import HermiteParams
+    pos, vel, m = _system(6000, 23)
+    c = 0.0 if where == "core" else 3.0
+    pos[-1] = [c + 0.005, 0.0, 0.0]
+    pos[-2] = [c - 0.005, 0.0, 0.0]
+    vel[-1] = [0.0, 0.9, 0.0]
+    vel[-2] = [0.0, -0.9, 0.0]
+    n, n_bh = pos.shape[0], 2
+    h = [0.02, 0.15 if where == "core" else 0.05, INF]
+    off, idx = oracle.neighbours_species(pos, n_bh, h=h)
+    eps = [1e-4, 1e-4, 0.0]
+    r_cut = [0.016, 1 / 32, INF]
+    hp = HermiteParams(dt_soft=1 / 256, eta=0.1, alpha=0.1)
+    xo, vo, st = oracle.hermite_species(pos, vel, m, off, idx, n_bh, dt_soft=hp.dt_soft,
+                                        eps=eps, r_cut=r_cut, eta=[0.1, 0.03],
+                                        gamma=GAMMA, alpha=0.1,
+                                        p=hp.log2_soft_over_max, kmax=hp.kmax)
+    from paper_1506_04553_b300 import Context, Params
+    ctx = Context(Params(r_out=r_cut[0], eps=eps[0], gamma=GAMMA))
+    ctx.set_species(n, n_bh, r_cut_bh=r_cut[1], eps_bh=eps[1], h_bh=h[1], eta_bh=0.03)
+    pg, vg = _dev(pos.T), _dev(vel.T)
+    ctx.hard_step(pg, vg, _dev(m), _dev(off), _dev(idx, torch.int32), hp)
+    s = ctx.stats()
+    assert np.array_equal(pg.cpu().numpy().T, xo)
+    assert np.array_equal(vg.cpu().numpy().T, vo)
+    assert (s["herm_particle_steps"], s["herm_pairs"], s["herm_capped"]) == st[1:]
+    comp = s["herm_max_component"]
+    assert (comp > 32) if where == "core" else (comp <= 32)
+
+
+def test_species_argument_checks(cuda):
+    import torch
+    from paper_1506_04553_b300 import Context, P3TError, Params
+    ctx = Context(Params(r_out=0.01))
+    for bad in (dict(n=10, n_bh=10), dict(n=10, n_bh=-1), dict(n=100, n_bh=33),
+                dict(n=10, n_bh=2, r_cut_bh=0.0), dict(n=10, n_bh=2, eta_bh=0.0),
+                dict(n=10, n_bh=2, h_bh=float("nan"))):
+        kw = {"r_cut_bh": 0.03, "eps_bh": 0.0, "h_bh": 0.04, "eta_bh": 0.03, **bad}
+        with pytest.raises(P3TError):
+            ctx.set_species(**kw)
+    pos, _, m = _system(500, 24)
+    ctx.set_species(pos.shape[0], 2, **SP)
+    ctx.build_tree(_dev(pos.T), _dev(m))
+    with pytest.raises(P3TError):  # n must be the species layout's
+        ctx.build_tree(_dev(pos[:400].T), _dev(m[:400]))
+    ctx.build_tree(_dev(pos.T), _dev(m))
+    ctx.long_force()
+    w = torch.zeros((3, pos.shape[0]), dtype=torch.float32, device="cuda")
+    with pytest.raises(P3TError) as ei:
+        ctx.long_force_vjp(w)
+    assert ei.value.code == 5
+    ctx.set_species(0, 0)  # off again: a plain build of any n
+    ctx.build_tree(_dev(pos[:400].T), _dev(m[:400]))
+    ctx.long_force_vjp(torch.zeros((3, 400), dtype=torch.float32, device="cuda"))
