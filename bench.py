@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--no-p3t", action="store_true")
     ap.add_argument("--no-king", action="store_true")
     ap.add_argument("--no-cost-model", action="store_true")
+    ap.add_argument("--no-smbh", action="store_true")
     return ap.parse_args()
 
 
@@ -620,6 +621,8 @@ def run_ours(args, world, rank, local):
         line["king"] = run_king(args, dev)
     if not args.no_cost_model:
         line["cost_model"] = run_cost_model(args, dev)
+    if not args.no_smbh:
+        line["smbh"] = run_smbh(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_step, desc = oracle_sample(pos_h, mass_h, frac=1 / 16)
         line["cpu_baseline"] = {"value": n / t_step, "unit": "particles/s",
@@ -749,6 +752,103 @@ def run_p3t_step(args, dev):
                                   note="p3t_fp64_peaks: FP64 FMA/s over all SMs; "
                                        "latency (SM cycles) of one dependent add, "
                                        "division, square root in one warp")}
+
+
+def run_smbh(args, dev):
+    """Whole P3T steps of the black hole binary run of Sect. 3.2.2: a
+    Plummer model of 2^17 stars (N-body units) with two black holes of 1% of
+    its mass at (+-0.5, 0, 0) moving at (0, +-0.5, 0); cut-offs 1/256
+    between stars and 1/32 between a black hole and a star, none between the
+    black holes (not split, unsoftened); eps 1e-4; eta 0.1 for stars, 0.03
+    for black holes; dr_buff = 3 sigma dt_soft (sigma 1/sqrt 2), dt_max =
+    dt_soft / 4, theta 0.4, dt_soft 1/1024.  Each step: half-kick, hard step,
+    build, F_soft, neighbour lists, half-kick; one step captured in a CUDA
+    graph and replayed."""
+    import torch
+    import paper_1506_04553_b300 as P
+    from paper_1506_04553_b300 import ics
+    nfs, n_bh = 1 << 17, 2
+    n = nfs + n_bh
+    dt = 1.0 / 1024
+    buf = 3 * dt / np.sqrt(2)
+    r_fs, r_bh = 1 / 256, 1 / 32
+    ps, vs, ms = ics.plummer(nfs, 7000)
+    pos_h = np.concatenate([ps, [[0.5, -0.5], [0.0, 0.0], [0.0, 0.0]]], axis=1)
+    vel_h = np.concatenate([vs, [[0.0, 0.0], [0.5, -0.5], [0.0, 0.0]]], axis=1)
+    mass_h = np.concatenate([ms, [0.01, 0.01]])
+
+    def mk(flags=0):
+        return P.Params(theta=THETA, r_out=r_fs, gamma=GAMMA, eps=1e-4,
+                        h=r_fs + buf, G=1.0, n_leaf=N_LEAF, n_group=N_GROUP,
+                        flags=flags)
+    ctx = P.Context(mk())
+    ctx.set_species(n, n_bh, r_cut_bh=r_bh, eps_bh=1e-4, h_bh=r_bh + buf,
+                    eta_bh=0.03)
+    pos = torch.tensor(np.ascontiguousarray(pos_h), device=dev)
+    vel = torch.tensor(np.ascontiguousarray(vel_h), device=dev)
+    mass = torch.tensor(mass_h, device=dev)
+    acc = torch.empty((3, n), dtype=torch.float32, device=dev)
+    off = torch.empty((n + 1,), dtype=torch.int64, device=dev)
+    hp = P.HermiteParams(dt_soft=dt, eta=0.1, alpha=0.1)
+    ctx.build_tree(pos, mass)
+    ctx.long_force(acc)
+    _, idx0 = ctx.neighbours()
+    idx = torch.empty((max(4 * int(idx0.numel()) + 1024, n),), dtype=torch.int32,
+                      device=dev)
+    ctx.neighbours_into(off, idx)
+    ngb_stream = torch.cuda.Stream(dev)
+
+    def step():
+        P.kick(vel, acc, 0.5 * dt)
+        ctx.hard_step(pos, vel, mass, off, idx, hp, check=False)
+        ctx.build_tree(pos, mass)
+        force_and_neighbours(ctx, acc, off, idx, ngb_stream)
+        P.kick(vel, acc, 0.5 * dt)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ctx.check()
+    st = ctx.stats()
+    ctx.set_params(mk(P.FLAG_NO_SYNC))
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        step()
+    torch.cuda.current_stream(dev).wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    k = max(args.steps // 4, 8)
+    e0.record(stream)
+    for _ in range(k):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    ms_step = e0.elapsed_time(e1) / k
+    bh = pos[:, nfs:].cpu().numpy()
+    return {"workload": "black hole binary in a Plummer model (Sect. 3.2.2): "
+                        "2^17 stars + 2 black holes of 0.01 at (+-0.5, 0, 0), "
+                        "(0, +-0.5, 0); r_cut 1/256 star-star, 1/32 black "
+                        "hole-star, none black hole-black hole; eps 1e-4 "
+                        "(0 between black holes); eta 0.1 / 0.03; dt_soft "
+                        "1/1024; theta 0.4",
+            "step": "half-kick, hard step, build, F_soft, neighbour lists, "
+                    "half-kick; one CUDA graph",
+            "n": n, "value": n / (ms_step * 1e-3), "unit": "particles/s",
+            "ms_per_step": ms_step,
+            "black_hole_rows": int((off[nfs + 1:] - off[nfs:-1]).sum().item()),
+            "hard_particle_steps": st["herm_particle_steps"],
+            "largest_component": st["herm_max_component"],
+            "binary_separation": float(np.linalg.norm(bh[:, 0] - bh[:, 1])),
+            "steps_done": max(args.warmup, 3) + 4 + k}
 
 
 def run_king(args, dev):
