@@ -762,7 +762,10 @@ k_sp_soft(int n, int nfs, int nbh, const double *__restrict__ xs,
         const double sq = sqrt(s2);
         double f = 0.0, wos = 0.0;
         if (star) {
-            f = G * k_of_x64((sq * irc - kb.gamma) * iomg) / (s2 * sq);
+            // K = 0 inside r_in: a coincident pair (s = 0 with eps_bh = 0)
+            // contributes no force, and its potential has a finite limit
+            const double K = k_of_x64((sq * irc - kb.gamma) * iomg);
+            f = K > 0.0 ? G * K / (s2 * sq) : 0.0;
             if (pot) wos = G * w_over_s(sq, kb);
         }
         const double mb = ms[kk];

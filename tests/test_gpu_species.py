@@ -153,3 +153,27 @@ def test_species_argument_checks(cuda):
     ctx.set_species(0, 0)  # off again: a plain build of any n
     ctx.build_tree(_dev(pos[:400].T), _dev(m[:400]))
     ctx.long_force_vjp(torch.zeros((3, 400), dtype=torch.float32, device="cuda"))
+
+
+def test_species_coincident_black_hole_and_star(cuda):
+    """A black hole exactly on a star with eps_bh = 0: K(0) = 0, so the pair
+    adds no force (as for coincident stars); the pair is a neighbour pair
+    (distance 0 < h_bh); everything else matches the oracle."""
+    from paper_1506_04553_b300 import Context, Params
+    pos, _, m = _system(3000, 25, n_bh=1)
+    pos[-1] = pos[17]
+    n, nfs = pos.shape[0], pos.shape[0] - 1
+    ctx = Context(Params(gamma=GAMMA, **P))
+    ctx.set_species(n, 1, r_cut_bh=1 / 32, eps_bh=0.0, h_bh=0.04, eta_bh=0.03)
+    ctx.build_tree(_dev(pos.T), _dev(m))
+    acc = ctx.long_force().cpu().numpy().astype(np.float64).T
+    assert np.all(np.isfinite(acc))
+    kw = dict(eps=[P["eps"], 0.0, 0.0], r_cut=[P["r_out"], 1 / 32, INF], gamma=GAMMA,
+              kind="soft")
+    a_bh = oracle.direct_species(pos, m, 1, rows=np.array([n - 1]), **kw)
+    assert np.allclose(acc[-1], a_bh[0], rtol=1e-6, atol=0)
+    off, idx = ctx.neighbours()
+    off_o, idx_o = oracle.neighbours_species(pos, 1, h=[P["h"], 0.04, INF])
+    assert np.array_equal(off.cpu().numpy(), off_o)
+    assert np.array_equal(idx.cpu().numpy(), idx_o)
+    assert 17 in idx_o[off_o[-2]:off_o[-1]]
