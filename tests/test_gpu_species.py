@@ -177,3 +177,78 @@ def test_species_coincident_black_hole_and_star(cuda):
     assert np.array_equal(off.cpu().numpy(), off_o)
     assert np.array_equal(idx.cpu().numpy(), idx_o)
     assert 17 in idx_o[off_o[-2]:off_o[-1]]
+
+
+def test_species_p3t_step_in_a_graph(cuda):
+    """A whole P3T step with black holes (half-kick, hard step, build,
+    F_soft with the black hole terms, merged neighbour rows, half-kick),
+    captured in a CUDA graph with P3T_FLAG_NO_SYNC, replays bit for bit what
+    the same step gives uncaptured."""
+    import torch
+    from paper_1506_04553_b300 import (FLAG_NO_SYNC, Context, HermiteParams,
+                                       Params, drift, kick)
+    pos_h, vel_h, m_h = _system(8000, 26)
+    pos_h[-1] = [0.01, 0.0, 0.0]
+    n, n_bh = pos_h.shape[0], 2
+    dt = 1 / 512
+    mk = lambda flags=0: Params(theta=0.4, r_out=0.01, gamma=GAMMA, eps=1e-4,
+                                h=0.0125, flags=flags)
+    hp = HermiteParams(dt_soft=dt, eta=0.1, alpha=0.1)
+
+    def state():
+        return [_dev(pos_h.T), _dev(vel_h.T), _dev(m_h)]
+
+    def setup(ctx, pos, vel, mass):
+        ctx.set_species(n, n_bh, **SP)
+        ctx.build_tree(pos, mass)
+        acc = ctx.long_force()
+        off, idx0 = ctx.neighbours()
+        idx = torch.empty(4 * idx0.numel() + 1024, dtype=torch.int32, device="cuda")
+        ctx.neighbours_into(off, idx)
+        ctx.hard_step(pos.clone(), vel.clone(), mass, off, idx, hp)  # scratch
+        return acc, off, idx
+
+    def step(ctx, pos, vel, mass, acc, off, idx):
+        kick(vel, acc, 0.5 * dt)
+        ctx.hard_step(pos, vel, mass, off, idx, hp, check=False)
+        ctx.build_tree(pos, mass)
+        ctx.long_force(acc, check=False)
+        ctx.neighbours_into(off, idx, sync=False)
+        kick(vel, acc, 0.5 * dt)
+
+    # uncaptured
+    ca = Context(mk())
+    pa, va, ma = state()
+    acc_a, off_a, idx_a = setup(ca, pa, va, ma)
+    ca.set_params(mk(FLAG_NO_SYNC))
+    ca.set_species(n, n_bh, **SP)
+    step(ca, pa, va, ma, acc_a, off_a, idx_a)
+    torch.cuda.synchronize()
+    ca.check()
+    # captured
+    cb = Context(mk())
+    pb, vb, mb = state()
+    acc_b, off_b, idx_b = setup(cb, pb, vb, mb)
+    cb.set_params(mk(FLAG_NO_SYNC))
+    cb.set_species(n, n_bh, **SP)
+    p0, v0, a0 = pb.clone(), vb.clone(), acc_b.clone()
+    o0, i0 = off_b.clone(), idx_b.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        step(cb, pb, vb, mb, acc_b, off_b, idx_b)  # warm the stream
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step(cb, pb, vb, mb, acc_b, off_b, idx_b)
+    for t, t0 in ((pb, p0), (vb, v0), (acc_b, a0), (off_b, o0), (idx_b, i0)):
+        t.copy_(t0)
+    g.replay()
+    torch.cuda.synchronize()
+    cb.check()
+    nnz = int(off_a[-1])
+    assert torch.equal(pa, pb) and torch.equal(va, vb)
+    assert torch.equal(acc_a, acc_b)
+    assert torch.equal(off_a, off_b)
+    assert torch.equal(idx_a[:nnz], idx_b[:nnz])
+    assert off_a[-1] - off_a[-2] > 0  # the core black hole has a row
