@@ -575,24 +575,47 @@ def run_ours(args, world, rank, local):
         with torch.cuda.graph(g3):
             part3()
         drifted, kicked = torch.cuda.Event(), torch.cuda.Event()
+        uploaded = torch.cuda.Event()
+        # device staging of the inputs: each step's copies from pinned host
+        # memory run on the copy stream during the previous step, right after
+        # that step's results came down (the positions and velocities a step
+        # uploads are the ones the step before returned): the positions and
+        # masses during the build and force, the velocities during the
+        # neighbour lists; the step starts with device-to-device copies
+        pos_in, vel_in = torch.empty_like(pos), torch.empty_like(vel)
+        mass_in = torch.empty_like(mass)
+        vel_up = torch.cuda.Event()
+        with torch.cuda.stream(copy_s):
+            pos_in.copy_(hp, non_blocking=True)
+            mass_in.copy_(hm, non_blocking=True)
+            uploaded.record(copy_s)
+            vel_in.copy_(hv, non_blocking=True)
+            vel_up.record(copy_s)
 
         def e2e_step():
-            pos.copy_(hp, non_blocking=True)
-            vel.copy_(hv, non_blocking=True)
-            mass.copy_(hm, non_blocking=True)
+            stream.wait_event(uploaded)
+            pos.copy_(pos_in)
+            mass.copy_(mass_in)
+            stream.wait_event(vel_up)
+            vel.copy_(vel_in)
             g1.replay()
             drifted.record(stream)
             copy_s.wait_event(drifted)
             with torch.cuda.stream(copy_s):
                 hp.copy_(pos, non_blocking=True)
+                # the next step's inputs, from pinned host memory
+                pos_in.copy_(hp, non_blocking=True)
+                mass_in.copy_(hm, non_blocking=True)
+                uploaded.record(copy_s)
             g2.replay()
             kicked.record(stream)
             copy_s.wait_event(kicked)
             with torch.cuda.stream(copy_s):
                 hv.copy_(vel, non_blocking=True)
+                vel_in.copy_(hv, non_blocking=True)  # the next step's input
+                vel_up.record(copy_s)
             g3.replay()
             hoff.copy_(off, non_blocking=True)
-            stream.wait_stream(copy_s)  # the next upload reads hp and hv
             stream.synchronize()
             nnz = int(hoff[n])
             hidx[:nnz].copy_(idx[:nnz], non_blocking=True)
