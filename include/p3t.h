@@ -237,7 +237,8 @@ typedef struct p3t_hermite_params {
  * with an empty neighbour row are isolated and drift, x <- x + dt_soft v;
  * every other particle is integrated over dt_soft under H_hard (pair forces
  * of p3t_hard_force over its row, using the context's G, eps, r_out and
- * gamma) with the fourth-order Hermite scheme and individual block
+ * gamma; with species set, eps and r_out per pair type and eta per species,
+ * see p3t_set_species) with the fourth-order Hermite scheme and individual block
  * timesteps (Makino & Aarseth 1992):
  *   - time in integer ticks of dt_max 2^-kmax; a particle at level k steps
  *     dt_max 2^-k and its time is a multiple of its step;
@@ -287,6 +288,10 @@ int p3t_check(p3t_ctx *ctx, void *stream);
  * same p3t_build_tree (both only read the tree; each walk has its own
  * device work counter): the neighbour walk then fills the SMs that the
  * force kernel's tail leaves idle.
+ * With species set (p3t_set_species) the radius depends on the pair type
+ * and the rows are built through context scratch for the star rows, which
+ * grows only when `needed` is given: call once with `needed` before
+ * capturing calls without it in a CUDA graph.
  * Errors: P3T_ERR_CAPACITY (nnz > cap; offsets valid, idx undefined),
  * P3T_ERR_STATE (no tree), P3T_ERR_CUDA. */
 int p3t_neighbours(p3t_ctx *ctx, int64_t *offsets, int32_t *idx, int64_t cap,
