@@ -144,8 +144,8 @@ def _declare(lib):
     lib.orc_direct_species.argtypes = [_i64, _i64, _p, _p, _d, _p, _p, _d,
                                        C.c_int, _p, _i64, _p, _p, C.c_int]
     lib.orc_neighbours_species.restype = None
-    lib.orc_neighbours_species.argtypes = [_i64, _i64, _p, _p, _p, _p, _p,
-                                           C.c_int]
+    lib.orc_neighbours_species.argtypes = [_i64, _i64, _p, _p, _p, _i64, _p,
+                                           _p, _p, C.c_int]
     lib.orc_hard_force_species.restype = None
     lib.orc_hard_force_species.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _d,
                                            _p, _p, _d, _p, _p]
@@ -548,21 +548,25 @@ def direct_species(pos, mass, n_bh, *, eps, r_cut, G=1.0, gamma=0.1,
     return (acc, pot) if potential else acc
 
 
-def neighbours_species(pos, n_bh, h, threads=None):
-    """neighbours() with a radius per pair type; returns (offsets, idx)."""
+def neighbours_species(pos, n_bh, h, rows=None, threads=None):
+    """neighbours() with a radius per pair type; ``rows`` restricts the
+    rows; returns (offsets, idx)."""
     lib = _load()
     pos = _f64(pos, (-1, 3))
     n = pos.shape[0]
     h3 = _three(h)
     th = threads or DEFAULT_THREADS
-    cnt = np.zeros(n, dtype=np.int64)
-    lib.orc_neighbours_species(n, int(n_bh), _ptr(pos), _ptr(h3), None, None,
-                               _ptr(cnt), th)
-    off = np.zeros(n + 1, dtype=np.int64)
+    rws = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nr = n if rws is None else rws.shape[0]
+    rp = None if rws is None else _ptr(rws)
+    cnt = np.zeros(nr, dtype=np.int64)
+    lib.orc_neighbours_species(n, int(n_bh), _ptr(pos), _ptr(h3), rp, nr, None,
+                               None, _ptr(cnt), th)
+    off = np.zeros(nr + 1, dtype=np.int64)
     np.cumsum(cnt, out=off[1:])
     idx = np.zeros(max(int(off[-1]), 1), dtype=np.int32)
-    lib.orc_neighbours_species(n, int(n_bh), _ptr(pos), _ptr(h3), _ptr(off),
-                               _ptr(idx), _ptr(cnt), th)
+    lib.orc_neighbours_species(n, int(n_bh), _ptr(pos), _ptr(h3), rp, nr,
+                               _ptr(off), _ptr(idx), _ptr(cnt), th)
     return off, idx[: int(off[-1])]
 
 

@@ -341,15 +341,17 @@ void orc_neighbours_fill(int64_t n, const double *pos, double h,
 /* Both passes with two species (Sect. 3.2.2): the last n_bh particles are
  * black holes and a pair of type t (0 star-star, 1 black hole-star, 2 black
  * hole-black hole) is a neighbour pair within h[t]; h = infinity makes every
- * such pair one (the black holes, whose force is not split).  offsets ==
- * NULL counts, else fills. */
+ * such pair one (the black holes, whose force is not split).  rows == NULL
+ * takes every particle, else rows[0..nr) (outputs by position in rows).
+ * offsets == NULL counts, else fills. */
 void orc_neighbours_species(int64_t n, int64_t n_bh, const double *pos,
-                            const double *h, const int64_t *offsets,
-                            int32_t *idx, int64_t *count, int nthreads)
+                            const double *h, const int64_t *rows, int64_t nr,
+                            const int64_t *offsets, int32_t *idx,
+                            int64_t *count, int nthreads)
 {
-    orc_ngb_args a = {n, pos, {h[0], h[1], h[2]}, n - n_bh, NULL, count,
+    orc_ngb_args a = {n, pos, {h[0], h[1], h[2]}, n - n_bh, rows, count,
                       offsets, idx};
-    orc_parallel_for(n, nthreads, orc_ngb_range, &a);
+    orc_parallel_for(rows ? nr : n, nthreads, orc_ngb_range, &a);
 }
 
 /* ------------------------------------------------------------------------ */

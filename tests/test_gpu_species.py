@@ -252,3 +252,45 @@ def test_species_p3t_step_in_a_graph(cuda):
     assert torch.equal(off_a, off_b)
     assert torch.equal(idx_a[:nnz], idx_b[:nnz])
     assert off_a[-1] - off_a[-2] > 0  # the core black hole has a row
+
+
+def test_species_black_hole_binary_full_size(cuda):
+    """The bench's black hole binary setup (2^17 stars, two black holes of
+    0.01 at (+-0.5, 0, 0); r_cut 1/256 and 1/32, h = r_cut + 3 sigma
+    dt_soft, dt_soft 1/1024) in the bench's launch configuration: the black
+    hole rows and 2000 sampled star rows of the neighbour lists bit for bit,
+    and the soft forces of the same rows, against the oracle."""
+    from paper_1506_04553_b300 import Context, Params
+    nfs, n_bh = 1 << 17, 2
+    n = nfs + n_bh
+    dt = 1.0 / 1024
+    buf = 3 * dt / np.sqrt(2)
+    r_fs, r_bh = 1 / 256, 1 / 32
+    ps, _, ms = ics.plummer(nfs, 7000)
+    pos = np.concatenate([ps.T, [[0.5, 0.0, 0.0], [-0.5, 0.0, 0.0]]])
+    m = np.concatenate([ms, [0.01, 0.01]])
+    ctx = Context(Params(theta=0.4, r_out=r_fs, gamma=GAMMA, eps=1e-4, h=r_fs + buf))
+    ctx.set_species(n, n_bh, r_cut_bh=r_bh, eps_bh=1e-4, h_bh=r_bh + buf, eta_bh=0.03)
+    ctx.build_tree(_dev(pos.T), _dev(m))
+    acc = ctx.long_force().cpu().numpy().astype(np.float64).T
+    off, idx = ctx.neighbours()
+    off, idx = off.cpu().numpy(), idx.cpu().numpy()
+    rows = np.sort(np.concatenate([np.random.default_rng(5).choice(nfs, 2000, replace=False),
+                                   [nfs, nfs + 1]]))
+    off_o, idx_o = oracle.neighbours_species(pos, n_bh, h=[r_fs + buf, r_bh + buf, INF],
+                                             rows=rows)
+    for q, r in enumerate(rows):
+        assert np.array_equal(idx[off[r]:off[r + 1]], idx_o[off_o[q]:off_o[q + 1]]), r
+    assert off[n] - off[nfs] > 2  # black hole rows hold stars
+    kw = dict(eps=[1e-4, 1e-4, 0.0], r_cut=[r_fs, r_bh, INF], gamma=GAMMA, kind="soft")
+    a_bh = oracle.direct_species(pos, m, n_bh, rows=np.arange(nfs, n), **kw)
+    assert np.allclose(acc[nfs:], a_bh, rtol=1e-6, atol=0)
+    t = oracle.Tree(pos[:nfs], m[:nfs], n_leaf=16, n_group=64)
+    t.walk(0.4, r_fs + buf, r_fs)
+    a_tree = t.force(eps=1e-4, r_cut=r_fs, gamma=GAMMA)
+    srows = rows[rows < nfs]
+    m_bh_only = m.copy()
+    m_bh_only[:nfs] = 0.0
+    a_cross = oracle.direct_species(pos, m_bh_only, n_bh, rows=srows, **kw)
+    e = rel_err(acc[srows], a_tree[srows] + a_cross)
+    assert np.median(e) <= 1e-5 and e.max() <= 1e-4, (np.median(e), e.max())
