@@ -133,8 +133,8 @@ typedef struct p3t_species {
                         (paper: 0.03); the stars use p3t_hermite_params.eta */
 } p3t_species;
 
-/* The last n_bh of the n particles are black holes (1 <= n_bh < n; n_bh = 0
- * switches species off).  Pairs of stars keep the context's r_out, eps and
+/* The last n_bh of the n particles are black holes (1 <= n_bh <= 32 and
+ * n_bh < n; n_bh = 0 switches species off).  Pairs of stars keep the context's r_out, eps and
  * h.  A black hole and a star: r_cut_bh, eps_bh, h_bh.  Two black holes: the
  * force is not split (F_soft = 0, all of it hard), not softened, and they
  * are always neighbours.  Applies from the next p3t_build_tree, whose n must
