@@ -243,7 +243,9 @@ typedef struct p3t_hermite_params {
  *   - time in integer ticks of dt_max 2^-kmax; a particle at level k steps
  *     dt_max 2^-k and its time is a multiple of its step;
  *   - first levels from Eq. 20 (eta / 10), later from
- *     Eq. 18 with a^(2), a^(3) from the Hermite interpolation, both
+ *     Eq. 18 with a^(2), a^(3) from the Hermite interpolation and
+ *     |a^(1)| |a^(3)| + |a^(2)|^2 as its denominator (the printed
+ *     |a^(0)| |a^(3)| is not a time^-2 term beside |a^(2)|^2), both
  *     tested in squares (dt^2 den <= eta^2 num: no division); a
  *     step may at most double and is halved until the current time is a
  *     multiple of it;

@@ -134,25 +134,33 @@ def _declare(lib):
     lib.orc_tree_vjp.argtypes = [_p, _d, _d, _d, _d, _p, _p, _p, C.c_int]
     lib.orc_tree_update.restype = None
     lib.orc_tree_update.argtypes = [_p, _p, _p]
-    lib.orc_hard_force.restype = None
-    lib.orc_hard_force.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _d, _d, _d,
-                                   _p, _p]
+    for pre in ("orc_", "orc_mirror_"):
+        f = getattr(lib, pre + "hard_force")
+        f.restype = None
+        f.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _d, _d, _d, _p, _p]
+        f = getattr(lib, pre + "hard_force_species")
+        f.restype = None
+        f.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _d, _p, _p, _d, _p, _p]
     lib.orc_hermite.restype = C.c_int
     lib.orc_hermite.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _d, _d, _d, _d,
-                                _d, _d, C.c_int, C.c_int, _p]
+                                _d, _d, C.c_int, C.c_int, _p, _p, _p, _p]
+    lib.orc_mirror_hermite.restype = C.c_int
+    lib.orc_mirror_hermite.argtypes = [_i64, _p, _p, _p, _p, _p, _d, _d, _d,
+                                       _d, _d, _d, _d, C.c_int, C.c_int, _p]
     lib.orc_direct_species.restype = None
     lib.orc_direct_species.argtypes = [_i64, _i64, _p, _p, _d, _p, _p, _d,
                                        C.c_int, _p, _i64, _p, _p, C.c_int]
     lib.orc_neighbours_species.restype = None
     lib.orc_neighbours_species.argtypes = [_i64, _i64, _p, _p, _p, _i64, _p,
                                            _p, _p, C.c_int]
-    lib.orc_hard_force_species.restype = None
-    lib.orc_hard_force_species.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _d,
-                                           _p, _p, _d, _p, _p]
     lib.orc_hermite_species.restype = C.c_int
     lib.orc_hermite_species.argtypes = [_i64, _i64, _p, _p, _p, _p, _p, _d,
                                         _p, _p, _d, _p, _d, _d, C.c_int,
-                                        C.c_int, _p]
+                                        C.c_int, _p, _p, _p, _p]
+    lib.orc_mirror_hermite_species.restype = C.c_int
+    lib.orc_mirror_hermite_species.argtypes = [_i64, _i64, _p, _p, _p, _p, _p,
+                                               _d, _p, _p, _d, _p, _d, _d,
+                                               C.c_int, C.c_int, _p]
 
 
 def _ptr(a: np.ndarray):
@@ -286,10 +294,12 @@ def _csr(off, idx, n):
 
 
 def hard_force(pos, vel, mass, off, idx, *, G=1.0, eps=0.0, r_cut=1.0,
-               gamma=0.1):
+               gamma=0.1, mirror=False):
     """Hard acceleration and jerk of every particle from its neighbour row
     (Eq. 7 with the pair weight 1 - K and its time derivative); returns
-    (a, jerk), each n x 3."""
+    (a, jerk), each n x 3.  mirror=True evaluates the fused-order mirror of
+    the GPU kernels instead of the plain formulas (a separate check, not
+    the oracle)."""
     lib = _load()
     pos = _f64(pos, (-1, 3))
     vel = _f64(vel, (-1, 3))
@@ -298,18 +308,27 @@ def hard_force(pos, vel, mass, off, idx, *, G=1.0, eps=0.0, r_cut=1.0,
     off, idx = _csr(off, idx, n)
     a = np.zeros((n, 3))
     jk = np.zeros((n, 3))
-    lib.orc_hard_force(n, _ptr(pos), _ptr(vel), _ptr(mass), _ptr(off),
-                       _ptr(idx), G, eps, r_cut, gamma, _ptr(a), _ptr(jk))
+    f = lib.orc_mirror_hard_force if mirror else lib.orc_hard_force
+    f(n, _ptr(pos), _ptr(vel), _ptr(mass), _ptr(off), _ptr(idx), G, eps,
+      r_cut, gamma, _ptr(a), _ptr(jk))
     return a, jk
 
 
+def hard_force_mirror(pos, vel, mass, off, idx, **kw):
+    """hard_force() in the GPU kernels' fused order (bit-exact check)."""
+    return hard_force(pos, vel, mass, off, idx, mirror=True, **kw)
+
+
 def hermite(pos, vel, mass, off, idx, *, dt_soft, G=1.0, eps=0.0, r_cut=1.0,
-            gamma=0.1, eta=0.1, alpha=0.1, p=2, kmax=30):
+            gamma=0.1, eta=0.1, alpha=0.1, p=2, kmax=30, detail=False):
     """Fourth-order Hermite integration with block timesteps over dt_soft of
     every particle with a non-empty neighbour row (dt_max = dt_soft 2^-p,
-    levels down to dt_max 2^-kmax); particles with an empty row drift.
+    levels down to dt_max 2^-kmax); particles with an empty row drift.  The
+    formulas and the timestep criteria of Eq. 18-20 as printed.
     Returns (pos, vel, stats) with stats = (block steps, particle steps,
-    pair evaluations, steps capped at kmax)."""
+    pair evaluations, steps capped at kmax); with detail=True also a dict of
+    per-particle arrays: nstep (steps taken), lev0 (first level) and margin
+    (least relative distance of a level decision from a tie)."""
     lib = _load()
     pos = _f64(pos, (-1, 3)).copy()
     vel = _f64(vel, (-1, 3)).copy()
@@ -317,11 +336,37 @@ def hermite(pos, vel, mass, off, idx, *, dt_soft, G=1.0, eps=0.0, r_cut=1.0,
     n = pos.shape[0]
     off, idx = _csr(off, idx, n)
     st = np.zeros(4, dtype=np.int64)
+    ns = np.zeros(max(n, 1), dtype=np.int64)
+    l0 = np.zeros(max(n, 1), dtype=np.int32)
+    mg = np.zeros(max(n, 1))
     rc = lib.orc_hermite(n, _ptr(pos), _ptr(vel), _ptr(mass), _ptr(off),
                          _ptr(idx), G, eps, r_cut, gamma, eta, alpha, dt_soft,
-                         p, kmax, _ptr(st))
+                         p, kmax, _ptr(st), _ptr(ns), _ptr(l0), _ptr(mg))
     if rc != 0:
         raise ValueError("orc_hermite: bad arguments")
+    out = (pos, vel, tuple(int(v) for v in st))
+    if detail:
+        out += (dict(nstep=ns[:n], lev0=l0[:n], margin=mg[:n]),)
+    return out
+
+
+def hermite_mirror(pos, vel, mass, off, idx, *, dt_soft, G=1.0, eps=0.0,
+                   r_cut=1.0, gamma=0.1, eta=0.1, alpha=0.1, p=2, kmax=30):
+    """hermite() in the GPU kernels' fused order, criteria tested in squares:
+    a separate bit-exact check of the GPU, not the oracle.  Returns (pos,
+    vel, stats)."""
+    lib = _load()
+    pos = _f64(pos, (-1, 3)).copy()
+    vel = _f64(vel, (-1, 3)).copy()
+    mass = _f64(mass)
+    n = pos.shape[0]
+    off, idx = _csr(off, idx, n)
+    st = np.zeros(4, dtype=np.int64)
+    rc = lib.orc_mirror_hermite(n, _ptr(pos), _ptr(vel), _ptr(mass),
+                                _ptr(off), _ptr(idx), G, eps, r_cut, gamma,
+                                eta, alpha, dt_soft, p, kmax, _ptr(st))
+    if rc != 0:
+        raise ValueError("orc_mirror_hermite: bad arguments")
     return pos, vel, tuple(int(v) for v in st)
 
 
@@ -571,7 +616,7 @@ def neighbours_species(pos, n_bh, h, rows=None, threads=None):
 
 
 def hard_force_species(pos, vel, mass, off, idx, n_bh, *, eps, r_cut, G=1.0,
-                       gamma=0.1):
+                       gamma=0.1, mirror=False):
     """hard_force() with per-pair-type eps and r_cut."""
     lib = _load()
     pos = _f64(pos, (-1, 3))
@@ -582,17 +627,21 @@ def hard_force_species(pos, vel, mass, off, idx, n_bh, *, eps, r_cut, G=1.0,
     e3, r3 = _three(eps), _three(r_cut)
     a = np.zeros((n, 3))
     jk = np.zeros((n, 3))
-    lib.orc_hard_force_species(n, int(n_bh), _ptr(pos), _ptr(vel), _ptr(mass),
-                               _ptr(off), _ptr(idx), G, _ptr(e3), _ptr(r3),
-                               gamma, _ptr(a), _ptr(jk))
+    f = (lib.orc_mirror_hard_force_species if mirror
+         else lib.orc_hard_force_species)
+    f(n, int(n_bh), _ptr(pos), _ptr(vel), _ptr(mass), _ptr(off), _ptr(idx),
+      G, _ptr(e3), _ptr(r3), gamma, _ptr(a), _ptr(jk))
     return a, jk
 
 
 def hermite_species(pos, vel, mass, off, idx, n_bh, *, dt_soft, eps, r_cut,
-                    eta, G=1.0, gamma=0.1, alpha=0.1, p=2, kmax=30):
+                    eta, G=1.0, gamma=0.1, alpha=0.1, p=2, kmax=30,
+                    detail=False, mirror=False):
     """hermite() with per-pair-type eps and r_cut and eta per species
     (eta[0] stars, eta[1] black holes); a_0 of a black hole takes the
-    black hole-star cut-off.  Returns (pos, vel, stats)."""
+    black hole-star cut-off.  Returns (pos, vel, stats) (+ the detail dict
+    of hermite() with detail=True).  mirror=True runs the GPU kernels'
+    fused-order mirror instead (no detail)."""
     lib = _load()
     pos = _f64(pos, (-1, 3)).copy()
     vel = _f64(vel, (-1, 3)).copy()
@@ -604,10 +653,19 @@ def hermite_species(pos, vel, mass, off, idx, n_bh, *, dt_soft, eps, r_cut,
     if et.shape != (2,):
         raise ValueError("one eta per species (2)")
     st = np.zeros(4, dtype=np.int64)
-    rc = lib.orc_hermite_species(n, int(n_bh), _ptr(pos), _ptr(vel),
-                                 _ptr(mass), _ptr(off), _ptr(idx), G, _ptr(e3),
-                                 _ptr(r3), gamma, _ptr(et), alpha, dt_soft, p,
-                                 kmax, _ptr(st))
+    args = (n, int(n_bh), _ptr(pos), _ptr(vel), _ptr(mass), _ptr(off),
+            _ptr(idx), G, _ptr(e3), _ptr(r3), gamma, _ptr(et), alpha, dt_soft,
+            p, kmax, _ptr(st))
+    if mirror:
+        rc = lib.orc_mirror_hermite_species(*args)
+    else:
+        ns = np.zeros(max(n, 1), dtype=np.int64)
+        l0 = np.zeros(max(n, 1), dtype=np.int32)
+        mg = np.zeros(max(n, 1))
+        rc = lib.orc_hermite_species(*args, _ptr(ns), _ptr(l0), _ptr(mg))
     if rc != 0:
         raise ValueError("orc_hermite_species: bad arguments")
-    return pos, vel, tuple(int(v) for v in st)
+    out = (pos, vel, tuple(int(v) for v in st))
+    if detail and not mirror:
+        out += (dict(nstep=ns[:n], lev0=l0[:n], margin=mg[:n]),)
+    return out

@@ -1268,11 +1268,369 @@ void orc_tree_update(orc_tree *t, const double *pos, const double *m)
  * (off[n+1], idx) in ascending j, as the neighbour search returns them.
  * Every expression is written in the order it is evaluated. */
 
+/* ---- The oracle proper: the hard part as the paper writes it ----
+ *
+ * Plain FP64 with one rounding per written operation (the file is compiled
+ * with -ffp-contract=off): the pair force of Eq. 7 and its time derivative
+ * with K of Eq. 12 in its monomial form (orc_K, orc_dKdx), the timestep
+ * criteria of Eq. 18-20 in their printed form, dt <= eta sqrt(num / den)
+ * (Eq. 18 read with |a^(1)| |a^(3)| in the denominator, see below), and the
+ * Hermite predictor and corrector of Makino & Aarseth (1992) as written
+ * below.  The mirror further down evaluates the same formulas in the GPU
+ * path's fused order; only that mirror, not this code, is bit-identical to
+ * the GPU. */
+
+/* Per pair type (Sect. 3.2.2; 0 star-star, 1 black hole-star, 2 black
+ * hole-black hole): softening and cut-off.  r_cut = infinity means the pair
+ * is not split: y = s / r_cut = 0, x < 0 and K = 0, so all of it is hard. */
+typedef struct {
+    double eps, r_cut;
+} orc_plain_pair;
+
+typedef struct {
+    double G, gamma, alpha;
+    orc_plain_pair pt[3];
+    int64_t n_fs;       /* particles [n_fs, n) are black holes */
+    double a0_rcut[2];  /* per species: the r_cut of a_0 (Eq. 19) */
+    double eta[2];      /* per species: eta of Eq. 18 */
+} orc_plain_par;
+
+static orc_plain_par orc_plain_par_make(double G, double eps, double r_cut,
+                                        double gamma, double alpha, double eta)
+{
+    orc_plain_par P;
+    P.G = G;
+    P.gamma = gamma;
+    P.alpha = alpha;
+    for (int t = 0; t < 3; ++t) {
+        P.pt[t].eps = eps;
+        P.pt[t].r_cut = r_cut;
+    }
+    P.n_fs = INT64_MAX;
+    P.a0_rcut[0] = P.a0_rcut[1] = r_cut;
+    P.eta[0] = P.eta[1] = eta;
+    return P;
+}
+
+static double orc_norm3(const double *a)
+{
+    return sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+}
+
+/* Hard acceleration and jerk of particle i from its neighbour row, Eq. 7 as
+ * written: with q = x_i - x_j, u = v_i - v_j, s = sqrt(|q|^2 + eps^2)
+ * (Eq. 2), y = s / r_cut, x = (y - gamma) / (1 - gamma) (Eq. 13-15),
+ *   a_i  = -sum_j G m_j (1 - K(x)) q / s^3,
+ *   da_i = -sum_j G m_j [ (1 - K) (u / s^3 - 3 (q.u) q / s^5)
+ *                         - (dK/ds) ((q.u) / s) q / s^3 ],
+ * dK/ds = (dK/dx) / ((1 - gamma) r_cut), ds/dt = (q.u) / s. */
+static void orc_hard_one(int64_t i, const double *x, const double *v,
+                         const double *m, const int64_t *off,
+                         const int32_t *idx, const orc_plain_par *P,
+                         double *a, double *jk)
+{
+    double acc[3] = {0.0, 0.0, 0.0}, jrk[3] = {0.0, 0.0, 0.0};
+    for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+        int64_t j = idx[e];
+        const orc_plain_pair *pp = &P->pt[(i >= P->n_fs) + (j >= P->n_fs)];
+        double q[3], u[3];
+        for (int c = 0; c < 3; ++c) {
+            q[c] = x[3 * i + c] - x[3 * j + c];
+            u[c] = v[3 * i + c] - v[3 * j + c];
+        }
+        double s = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + pp->eps * pp->eps);
+        double y = s / pp->r_cut;
+        double xk = (y - P->gamma) / (1.0 - P->gamma);
+        double K = orc_K(xk);
+        double dKds = orc_dKdx(xk) / ((1.0 - P->gamma) * pp->r_cut);
+        double qu = q[0] * u[0] + q[1] * u[1] + q[2] * u[2];
+        double s3 = s * s * s;
+        double s5 = s3 * s * s;
+        double Gm = P->G * m[j];
+        for (int c = 0; c < 3; ++c) {
+            acc[c] -= Gm * (1.0 - K) * q[c] / s3;
+            jrk[c] -= Gm * ((1.0 - K) * (u[c] / s3 - 3.0 * qu * q[c] / s5)
+                            - dKds * (qu / s) * q[c] / s3);
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        a[c] = acc[c];
+        jk[c] = jrk[c];
+    }
+}
+
+/* Hard acceleration and jerk of every particle (a, jk: n x 3). */
+void orc_hard_force(int64_t n, const double *x, const double *v,
+                    const double *m, const int64_t *off, const int32_t *idx,
+                    double G, double eps, double r_cut, double gamma,
+                    double *a, double *jk)
+{
+    orc_plain_par P = orc_plain_par_make(G, eps, r_cut, gamma, 0.0, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+        orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
+}
+
+/* The same with two species: the last n_bh particles are black holes and a
+ * pair of type t takes eps[t] and r_cut[t]. */
+void orc_hard_force_species(int64_t n, int64_t n_bh, const double *x,
+                            const double *v, const double *m,
+                            const int64_t *off, const int32_t *idx, double G,
+                            const double *eps, const double *r_cut,
+                            double gamma, double *a, double *jk)
+{
+    orc_plain_par P = orc_plain_par_make(G, eps[0], r_cut[0], gamma, 0.0, 0.0);
+    for (int t = 1; t < 3; ++t) {
+        P.pt[t].eps = eps[t];
+        P.pt[t].r_cut = r_cut[t];
+    }
+    P.n_fs = n - n_bh;
+    for (int64_t i = 0; i < n; ++i)
+        orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
+}
+
+/* Block level from a criterion dt_crit (Eq. 18 or Eq. 20, before the min
+ * with dt_max): the smallest k in [kmin, kmax] whose step dt_max 2^-k is at
+ * most dt_crit (kmax, and *capped set, when none is).  *margin receives the
+ * least relative distance |dt_k - dt_crit| / dt_crit over the steps
+ * compared, the size of the rounding change that could flip the decision. */
+static int orc_plain_level(double dt_crit, double dt_max, int kmin, int kmax,
+                           int *capped, double *margin)
+{
+    int k = kmin;
+    for (;;) {
+        double dt_k = ldexp(dt_max, -k);
+        double d = fabs(dt_k - dt_crit) / dt_crit;
+        if (d < *margin) *margin = d;
+        if (dt_k <= dt_crit) {
+            *capped = 0;
+            return k;
+        }
+        if (k == kmax) {
+            *capped = 1;
+            return k;
+        }
+        ++k;
+    }
+}
+
+/* Eq. 18-20 in the printed form.  A criterion whose denominator vanishes
+ * (no hard force) puts no limit on the step. */
+static double orc_plain_crit(double eta, double num, double den)
+{
+    if (den == 0.0) return INFINITY;
+    return eta * sqrt(num / den);
+}
+
+/* Fourth-order Hermite integration (Makino & Aarseth 1992) of every
+ * particle with a non-empty neighbour row over dt_soft under H_hard, with
+ * individual block timesteps (the sixth step of Sect. 2.2); particles with
+ * an empty row are isolated and drift, x <- x + dt_soft v (the fifth).
+ *
+ * Time is counted in ticks of dt_max 2^-kmax, dt_max = dt_soft 2^-p.  A
+ * particle at level k steps h = dt_max 2^-k and its time is a multiple of h.
+ *   - First level: Eq. 20, dt = eta_s sqrt((|a|^2 + a0^2) / |j|^2),
+ *     eta_s = eta / 10, a0 = alpha G m_i / r_cut^2 (Eq. 19).
+ *   - Later levels: Eq. 18,
+ *       dt = eta sqrt((sqrt(|a|^2 + a0^2) |a2| + |j|^2) / (|j| |a3| + |a2|^2))
+ *     with a, j at the end of the step and a2, a3 the Hermite
+ *     interpolation's, a2 advanced to the end of the step (a2 + h a3).  The
+ *     step may at most double, and is halved until the current time is a
+ *     multiple of it.
+ *   - Block step: t_n is the least t_i + h_i; every particle is predicted
+ *       xp = x + v d + a d^2 / 2 + j d^3 / 6,  vp = v + a d + j d^2 / 2
+ *     (d = t_n - t_i); the particles due at t_n get a1, j1 from the
+ *     predicted values of their rows and are corrected:
+ *       a2 = (-6 (a0 - a1) - h (4 j0 + 2 j1)) / h^2
+ *       a3 = (12 (a0 - a1) + 6 h (j0 + j1)) / h^3
+ *       x = xp + a2 h^4 / 24 + a3 h^5 / 120,  v = vp + a2 h^3 / 6 + a3 h^4 / 24.
+ * stats (may be NULL): [0] block steps, [1] particle steps, [2] pair
+ * evaluations, [3] steps whose level was capped at kmax.  Per particle (each
+ * may be NULL): nstep, its number of steps; lev0, its first level; margin,
+ * the least relative distance of any of its level decisions from a tie
+ * (orc_plain_level; +infinity for an isolated particle).
+ * Returns 0, or -1 on bad arguments or allocation failure. */
+static int orc_hermite_run(int64_t n, double *x, double *v, const double *m,
+                           const int64_t *off, const int32_t *idx,
+                           const orc_plain_par *P, double dt_soft, int p,
+                           int kmax, int64_t *stats, int64_t *nstep,
+                           int32_t *lev0, double *margin)
+{
+    if (n < 0 || p < 0 || kmax < 0 || p + kmax > 60) return -1;
+    const double dt_max = ldexp(dt_soft, -p);
+    const double tick = ldexp(dt_max, -kmax);
+    const int64_t T = (int64_t)1 << (p + kmax);
+    int capped = 0;
+    int64_t st[4] = {0, 0, 0, 0};
+    double *a = malloc(3 * n * sizeof(double) + 1);
+    double *jk = malloc(3 * n * sizeof(double) + 1);
+    double *xp = malloc(3 * n * sizeof(double) + 1);
+    double *vp = malloc(3 * n * sizeof(double) + 1);
+    int64_t *t = malloc(n * sizeof(int64_t) + 1);
+    int *lev = malloc(n * sizeof(int) + 1);
+    int64_t *ns = malloc(n * sizeof(int64_t) + 1);
+    double *mg = malloc(n * sizeof(double) + 1);
+    if (!a || !jk || !xp || !vp || !t || !lev || !ns || !mg) {
+        free(a); free(jk); free(xp); free(vp); free(t); free(lev); free(ns);
+        free(mg);
+        return -1;
+    }
+    /* start: forces at t = 0 and the first levels (Eq. 20) */
+    for (int64_t i = 0; i < n; ++i) {
+        t[i] = 0;
+        lev[i] = 0;
+        ns[i] = 0;
+        mg[i] = INFINITY;
+        if (off[i + 1] == off[i]) continue;
+        orc_hard_one(i, x, v, m, off, idx, P, a + 3 * i, jk + 3 * i);
+        st[2] += off[i + 1] - off[i];
+        const int sp = i >= P->n_fs;
+        double rc = P->a0_rcut[sp];
+        double a0 = P->alpha * P->G * m[i] / (rc * rc);
+        double an = orc_norm3(a + 3 * i), jn = orc_norm3(jk + 3 * i);
+        double eta_s = P->eta[sp] / 10.0;
+        double crit = orc_plain_crit(eta_s, an * an + a0 * a0, jn * jn);
+        lev[i] = orc_plain_level(crit, dt_max, 0, kmax, &capped, &mg[i]);
+        st[3] += capped;
+    }
+    if (lev0)
+        for (int64_t i = 0; i < n; ++i) lev0[i] = lev[i];
+    for (;;) {
+        int64_t tn = T;
+        int any = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (off[i + 1] == off[i] || t[i] == T) continue;
+            int64_t e = t[i] + ((int64_t)1 << (kmax - lev[i]));
+            if (e < tn) tn = e;
+            any = 1;
+        }
+        if (!any) break;
+        ++st[0];
+        /* predict every non-isolated particle to tn */
+        for (int64_t i = 0; i < n; ++i) {
+            if (off[i + 1] == off[i]) continue;
+            double d = (double)(tn - t[i]) * tick;
+            for (int c = 0; c < 3; ++c) {
+                int64_t k = 3 * i + c;
+                xp[k] = x[k] + v[k] * d + a[k] * (d * d / 2.0)
+                        + jk[k] * (d * d * d / 6.0);
+                vp[k] = v[k] + a[k] * d + jk[k] * (d * d / 2.0);
+            }
+        }
+        /* evaluate and correct the particles due at tn */
+        for (int64_t i = 0; i < n; ++i) {
+            if (off[i + 1] == off[i]) continue;
+            int64_t step = (int64_t)1 << (kmax - lev[i]);
+            if (t[i] + step != tn) continue;
+            double a1[3], j1[3];
+            orc_hard_one(i, xp, vp, m, off, idx, P, a1, j1);
+            ++st[1];
+            ++ns[i];
+            st[2] += off[i + 1] - off[i];
+            double h = (double)step * tick;
+            double h2 = h * h, h3 = h2 * h, h4 = h3 * h, h5 = h4 * h;
+            double a2[3], a3[3], a2e[3];
+            for (int c = 0; c < 3; ++c) {
+                int64_t k = 3 * i + c;
+                double a0c = a[k], j0c = jk[k];
+                a2[c] = (-6.0 * (a0c - a1[c]) - h * (4.0 * j0c + 2.0 * j1[c])) / h2;
+                a3[c] = (12.0 * (a0c - a1[c]) + 6.0 * h * (j0c + j1[c])) / h3;
+                x[k] = xp[k] + a2[c] * h4 / 24.0 + a3[c] * h5 / 120.0;
+                v[k] = vp[k] + a2[c] * h3 / 6.0 + a3[c] * h4 / 24.0;
+                a[k] = a1[c];
+                jk[k] = j1[c];
+                a2e[c] = a2[c] + h * a3[c];
+            }
+            t[i] = tn;
+            if (tn == T) continue;
+            /* Eq. 18, with |a^(1)| |a^(3)| as the first term of the
+             * denominator: as printed, |a^(0)| |a^(3)| has the dimension
+             * L^2 T^-7 beside |a^(2)|^2 of L^2 T^-8, so the printed step
+             * would change with the unit of time; with |a^(1)| the ratio is
+             * a time squared, as in the Aarseth criterion that Eq. 18
+             * extends by a_0. */
+            const int sp = i >= P->n_fs;
+            double rc = P->a0_rcut[sp];
+            double a0 = P->alpha * P->G * m[i] / (rc * rc);
+            double an = orc_norm3(a1), jn = orc_norm3(j1);
+            double a2n = orc_norm3(a2e), a3n = orc_norm3(a3);
+            double num = sqrt(an * an + a0 * a0) * a2n + jn * jn;
+            double den = jn * a3n + a2n * a2n;
+            double crit = orc_plain_crit(P->eta[sp], num, den);
+            int kmin = lev[i] > 0 ? lev[i] - 1 : 0;
+            int k = orc_plain_level(crit, dt_max, kmin, kmax, &capped, &mg[i]);
+            st[3] += capped;
+            while (tn % ((int64_t)1 << (kmax - k)) != 0) ++k;
+            lev[i] = k;
+        }
+    }
+    /* isolated particles drift (Sect. 2.2, step 5) */
+    for (int64_t i = 0; i < n; ++i) {
+        if (off[i + 1] != off[i]) continue;
+        for (int c = 0; c < 3; ++c) x[3 * i + c] = x[3 * i + c] + dt_soft * v[3 * i + c];
+    }
+    if (stats)
+        for (int k = 0; k < 4; ++k) stats[k] = st[k];
+    if (nstep)
+        for (int64_t i = 0; i < n; ++i) nstep[i] = ns[i];
+    if (margin)
+        for (int64_t i = 0; i < n; ++i) margin[i] = mg[i];
+    free(a); free(jk); free(xp); free(vp); free(t); free(lev); free(ns);
+    free(mg);
+    return 0;
+}
+
+int orc_hermite(int64_t n, double *x, double *v, const double *m,
+                const int64_t *off, const int32_t *idx, double G, double eps,
+                double r_cut, double gamma, double eta, double alpha,
+                double dt_soft, int p, int kmax, int64_t *stats,
+                int64_t *nstep, int32_t *lev0, double *margin)
+{
+    orc_plain_par P = orc_plain_par_make(G, eps, r_cut, gamma, alpha, eta);
+    return orc_hermite_run(n, x, v, m, off, idx, &P, dt_soft, p, kmax, stats,
+                           nstep, lev0, margin);
+}
+
+/* The same with two species (Sect. 3.2.2): the last n_bh particles are black
+ * holes.  Pair type t takes eps[t] and r_cut[t] (r_cut[2] = infinity: not
+ * split, K = 0); species s takes eta[s] (eta / 10 on the first step) and
+ * a_0 = alpha G m_i / r_cut[s]^2, the cut-off of its own pairs with stars. */
+int orc_hermite_species(int64_t n, int64_t n_bh, double *x, double *v,
+                        const double *m, const int64_t *off,
+                        const int32_t *idx, double G, const double *eps,
+                        const double *r_cut, double gamma, const double *eta,
+                        double alpha, double dt_soft, int p, int kmax,
+                        int64_t *stats, int64_t *nstep, int32_t *lev0,
+                        double *margin)
+{
+    if (n_bh < 0 || n_bh > n) return -1;
+    orc_plain_par P = orc_plain_par_make(G, eps[0], r_cut[0], gamma, alpha,
+                                         eta[0]);
+    for (int t = 1; t < 3; ++t) {
+        P.pt[t].eps = eps[t];
+        P.pt[t].r_cut = r_cut[t];
+    }
+    P.n_fs = n - n_bh;
+    P.a0_rcut[1] = r_cut[1];
+    P.eta[1] = eta[1];
+    return orc_hermite_run(n, x, v, m, off, idx, &P, dt_soft, p, kmax, stats,
+                           nstep, lev0, margin);
+}
+
+/* ---- The fused-order mirror of the GPU's hard part ----
+ *
+ * NOT the oracle: a second, separately named check.  It evaluates the same
+ * formulas as the code above in the order the GPU kernels do: every product
+ * that feeds a sum as one fused multiply-add, K and dK/dx in Horner form,
+ * reciprocal powers of s, and the timestep criteria compared in squares
+ * (dt^2 den <= eta^2 num, with sqrt(A) sqrt(B) taken as sqrt(A B)).  It
+ * agrees with the GPU bit for bit, which checks the GPU's block schedule
+ * and component bookkeeping exactly; the oracle above checks the GPU's
+ * arithmetic against the printed formulas within a rounding tolerance. */
 /* The hard part evaluates its formulas with fused multiply-adds: fma(a, b, c)
  * is a b + c with one rounding (IEEE 754 fusedMultiplyAdd), written out at
  * every use so that the order of operations is explicit.  The same holds
  * for the GPU path, so the two agree bit for bit. */
-static double orc_fdot3(const double *a, const double *b)
+static double orc_mirror_dot3(const double *a, const double *b)
 {
     return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
 }
@@ -1280,7 +1638,7 @@ static double orc_fdot3(const double *a, const double *b)
 /* K and dK/dx of Eq. 12 in Horner form for the hard part:
  *   K = x^4 (35 + x (-84 + x (70 - 20 x))),
  *   dK/dx = 140 x^3 (1 - x)^3 = x^3 (140 + x (-420 + x (420 - 140 x))). */
-static double orc_hK(double x)
+static double orc_mirror_K(double x)
 {
     if (x < 0.0) return 0.0;
     if (x >= 1.0) return 1.0;
@@ -1288,7 +1646,7 @@ static double orc_hK(double x)
     return x4 * fma(fma(fma(-20.0, x, 70.0), x, -84.0), x, 35.0);
 }
 
-static double orc_hdK(double x)
+static double orc_mirror_dK(double x)
 {
     if (x <= 0.0 || x >= 1.0) return 0.0;
     double x3 = x * x * x;
@@ -1304,23 +1662,23 @@ typedef struct {
     double eps2;
     double irc;    /* 1 / r_cut (0: not split) */
     double iomgrc; /* 1 / ((1 - gamma) r_cut) */
-} orc_pair_par;
+} orc_mirror_pair;
 
 /* Constants of the hard part, each computed once in this order. */
 typedef struct {
     double G, gamma;
     double iomg;   /* 1 / (1 - gamma) */
-    orc_pair_par pt[3];
+    orc_mirror_pair pt[3];
     int64_t n_fs;  /* particles [n_fs, n) are black holes */
     double a0c[2]; /* per species: alpha G / r_cut^2, a_0 = a0c m_i (Eq. 19) */
     double c6, c24, c120;  /* 1/6, 1/24, 1/120 */
     double eta2[2];   /* per species: eta^2 (later steps) */
     double eta_s2[2]; /* per species: eta_s^2 (first steps) */
-} orc_hard_par;
+} orc_mirror_par;
 
-static orc_pair_par orc_pair_par_make(double eps, double r_cut, double gamma)
+static orc_mirror_pair orc_mirror_pair_make(double eps, double r_cut, double gamma)
 {
-    orc_pair_par q;
+    orc_mirror_pair q;
     q.eps2 = eps * eps;
     q.irc = isinf(r_cut) ? 0.0 : 1.0 / r_cut;
     q.iomgrc = isinf(r_cut) ? 0.0 : 1.0 / ((1.0 - gamma) * r_cut);
@@ -1328,14 +1686,14 @@ static orc_pair_par orc_pair_par_make(double eps, double r_cut, double gamma)
 }
 
 /* One species (every particle a star): the parameters of the plain path. */
-static orc_hard_par orc_hard_par_make(double G, double eps, double r_cut,
+static orc_mirror_par orc_mirror_par_make(double G, double eps, double r_cut,
                                       double gamma, double alpha)
 {
-    orc_hard_par P;
+    orc_mirror_par P;
     P.G = G;
     P.gamma = gamma;
     P.iomg = 1.0 / (1.0 - gamma);
-    P.pt[0] = orc_pair_par_make(eps, r_cut, gamma);
+    P.pt[0] = orc_mirror_pair_make(eps, r_cut, gamma);
     P.pt[1] = P.pt[0];
     P.pt[2] = P.pt[0];
     P.n_fs = INT64_MAX;
@@ -1354,15 +1712,15 @@ static orc_hard_par orc_hard_par_make(double G, double eps, double r_cut,
  *   da_i = -sum G m_j [ (1-K) (u - 3 (q.u) q / s^2) / s^3
  *                       - (dK/ds) ((q.u) / s) q / s^3 ].
  * One square root and one division per pair: 1/s, then its powers. */
-static void orc_hard_one(int64_t i, const double *x, const double *v,
+static void orc_mirror_hard_one(int64_t i, const double *x, const double *v,
                          const double *m, const int64_t *off,
-                         const int32_t *idx, const orc_hard_par *P,
+                         const int32_t *idx, const orc_mirror_par *P,
                          double *a, double *jk)
 {
     double acc[3] = {0.0, 0.0, 0.0}, jrk[3] = {0.0, 0.0, 0.0};
     for (int64_t e = off[i]; e < off[i + 1]; ++e) {
         int64_t j = idx[e];
-        const orc_pair_par *pp = &P->pt[(i >= P->n_fs) + (j >= P->n_fs)];
+        const orc_mirror_pair *pp = &P->pt[(i >= P->n_fs) + (j >= P->n_fs)];
         double q[3], u[3];
         for (int c = 0; c < 3; ++c) {
             q[c] = x[3 * i + c] - x[3 * j + c];
@@ -1374,9 +1732,9 @@ static void orc_hard_one(int64_t i, const double *x, const double *v,
         double ri2 = ri * ri;
         double ri3 = ri2 * ri;
         double xk = fma(s, pp->irc, -P->gamma) * P->iomg;
-        double w = 1.0 - orc_hK(xk);
-        double dKds = orc_hdK(xk) * pp->iomgrc;
-        double rv = orc_fdot3(q, u);
+        double w = 1.0 - orc_mirror_K(xk);
+        double dKds = orc_mirror_dK(xk) * pp->iomgrc;
+        double rv = orc_mirror_dot3(q, u);
         double gm = P->G * m[j];
         double fa = gm * w * ri3;
         double c1 = 3.0 * rv * ri2;
@@ -1393,29 +1751,29 @@ static void orc_hard_one(int64_t i, const double *x, const double *v,
 }
 
 /* Hard acceleration and jerk of every particle (a, jk: n x 3). */
-void orc_hard_force(int64_t n, const double *x, const double *v,
+void orc_mirror_hard_force(int64_t n, const double *x, const double *v,
                     const double *m, const int64_t *off, const int32_t *idx,
                     double G, double eps, double r_cut, double gamma,
                     double *a, double *jk)
 {
-    orc_hard_par P = orc_hard_par_make(G, eps, r_cut, gamma, 0.0);
+    orc_mirror_par P = orc_mirror_par_make(G, eps, r_cut, gamma, 0.0);
     for (int64_t i = 0; i < n; ++i)
-        orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
+        orc_mirror_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
 }
 
 /* The same with two species: the last n_bh particles are black holes and a
- * pair of type t takes eps[t] and r_cut[t] (as orc_hermite_species). */
-void orc_hard_force_species(int64_t n, int64_t n_bh, const double *x,
+ * pair of type t takes eps[t] and r_cut[t] (as orc_mirror_hermite_species). */
+void orc_mirror_hard_force_species(int64_t n, int64_t n_bh, const double *x,
                             const double *v, const double *m,
                             const int64_t *off, const int32_t *idx, double G,
                             const double *eps, const double *r_cut,
                             double gamma, double *a, double *jk)
 {
-    orc_hard_par P = orc_hard_par_make(G, eps[0], r_cut[0], gamma, 0.0);
-    for (int t = 1; t < 3; ++t) P.pt[t] = orc_pair_par_make(eps[t], r_cut[t], gamma);
+    orc_mirror_par P = orc_mirror_par_make(G, eps[0], r_cut[0], gamma, 0.0);
+    for (int t = 1; t < 3; ++t) P.pt[t] = orc_mirror_pair_make(eps[t], r_cut[t], gamma);
     P.n_fs = n - n_bh;
     for (int64_t i = 0; i < n; ++i)
-        orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
+        orc_mirror_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
 }
 
 /* Block level for a step dt of at most eta sqrt(num / den) (Eq. 18
@@ -1424,7 +1782,7 @@ void orc_hard_force_species(int64_t n, int64_t n_bh, const double *x,
  * dm2 = dt_max^2.  The smallest k in [kmin, kmax] with
  * (dt_max 2^-k)^2 den <= e (kmax when none is); *capped is set when even
  * kmax fails. */
-static int orc_level(double den, double e, double dm2, int kmin, int kmax,
+static int orc_mirror_level(double den, double e, double dm2, int kmin, int kmax,
                      int *capped)
 {
     int k = kmin;
@@ -1446,7 +1804,7 @@ static int orc_level(double den, double e, double dm2, int kmin, int kmax,
  * Products that feed a sum are fused (fma, one rounding each).
  * Divisions are few: 1/s per pair, 1/h per correction, and constants
  * (1/r_cut, 1/(1 - gamma), alpha G / r_cut^2, 1/6, 1/24, 1/120) formed once;
- * the timestep criteria are tested in squares (orc_level).
+ * the timestep criteria are tested in squares (orc_mirror_level).
  * Time is counted in ticks of dt_max 2^-kmax, dt_max = dt_soft 2^-p.  A
  * particle at level k steps dt_max 2^-k; its time is always a multiple of
  * its step.  First step: Eq. 20 with eta_s = eta / 10; later steps:
@@ -1464,21 +1822,21 @@ static int orc_level(double den, double e, double dm2, int kmin, int kmax,
  * stats (may be NULL): [0] block steps, [1] particle steps, [2] pair
  * evaluations, [3] steps whose level was capped at kmax.
  * Returns 0, or -1 on bad arguments or allocation failure. */
-static int orc_hermite_run(int64_t n, double *x, double *v, const double *m,
+static int orc_mirror_hermite_run(int64_t n, double *x, double *v, const double *m,
                            const int64_t *off, const int32_t *idx,
-                           orc_hard_par P, double dt_soft, int p, int kmax,
+                           orc_mirror_par P, double dt_soft, int p, int kmax,
                            int64_t *stats);
 
-int orc_hermite(int64_t n, double *x, double *v, const double *m,
+int orc_mirror_hermite(int64_t n, double *x, double *v, const double *m,
                 const int64_t *off, const int32_t *idx, double G, double eps,
                 double r_cut, double gamma, double eta, double alpha,
                 double dt_soft, int p, int kmax, int64_t *stats)
 {
-    orc_hard_par P = orc_hard_par_make(G, eps, r_cut, gamma, alpha);
+    orc_mirror_par P = orc_mirror_par_make(G, eps, r_cut, gamma, alpha);
     const double eta_s = eta / 10.0;
     P.eta2[0] = P.eta2[1] = eta * eta;
     P.eta_s2[0] = P.eta_s2[1] = eta_s * eta_s;
-    return orc_hermite_run(n, x, v, m, off, idx, P, dt_soft, p, kmax, stats);
+    return orc_mirror_hermite_run(n, x, v, m, off, idx, P, dt_soft, p, kmax, stats);
 }
 
 /* The same with two species (Sect. 3.2.2): the last n_bh particles are black
@@ -1487,7 +1845,7 @@ int orc_hermite(int64_t n, double *x, double *v, const double *m,
  * species s takes eta[s] (eta_s = eta / 10 on the first step) and
  * a_0 = alpha G m_i / r_cut^2 with the cut-off of its own pairs with stars,
  * r_cut[s]. */
-int orc_hermite_species(int64_t n, int64_t n_bh, double *x, double *v,
+int orc_mirror_hermite_species(int64_t n, int64_t n_bh, double *x, double *v,
                         const double *m, const int64_t *off,
                         const int32_t *idx, double G, const double *eps,
                         const double *r_cut, double gamma, const double *eta,
@@ -1495,8 +1853,8 @@ int orc_hermite_species(int64_t n, int64_t n_bh, double *x, double *v,
                         int64_t *stats)
 {
     if (n_bh < 0 || n_bh > n) return -1;
-    orc_hard_par P = orc_hard_par_make(G, eps[0], r_cut[0], gamma, alpha);
-    for (int t = 1; t < 3; ++t) P.pt[t] = orc_pair_par_make(eps[t], r_cut[t], gamma);
+    orc_mirror_par P = orc_mirror_par_make(G, eps[0], r_cut[0], gamma, alpha);
+    for (int t = 1; t < 3; ++t) P.pt[t] = orc_mirror_pair_make(eps[t], r_cut[t], gamma);
     P.n_fs = n - n_bh;
     P.a0c[1] = alpha * G / (r_cut[1] * r_cut[1]);
     for (int sp = 0; sp < 2; ++sp) {
@@ -1504,12 +1862,12 @@ int orc_hermite_species(int64_t n, int64_t n_bh, double *x, double *v,
         P.eta2[sp] = eta[sp] * eta[sp];
         P.eta_s2[sp] = eta_s * eta_s;
     }
-    return orc_hermite_run(n, x, v, m, off, idx, P, dt_soft, p, kmax, stats);
+    return orc_mirror_hermite_run(n, x, v, m, off, idx, P, dt_soft, p, kmax, stats);
 }
 
-static int orc_hermite_run(int64_t n, double *x, double *v, const double *m,
+static int orc_mirror_hermite_run(int64_t n, double *x, double *v, const double *m,
                            const int64_t *off, const int32_t *idx,
-                           orc_hard_par P, double dt_soft, int p, int kmax,
+                           orc_mirror_par P, double dt_soft, int p, int kmax,
                            int64_t *stats)
 {
     if (n < 0 || p < 0 || kmax < 0 || p + kmax > 60) return -1;
@@ -1534,14 +1892,14 @@ static int orc_hermite_run(int64_t n, double *x, double *v, const double *m,
         t[i] = 0;
         lev[i] = 0;
         if (off[i + 1] == off[i]) continue;
-        orc_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
+        orc_mirror_hard_one(i, x, v, m, off, idx, &P, a + 3 * i, jk + 3 * i);
         st[2] += off[i + 1] - off[i];
         /* Eq. 20: dt^2 |j|^2 <= eta_s^2 (|a|^2 + a0^2) */
         const int sp = i >= P.n_fs;
         double a0 = P.a0c[sp] * m[i];
-        double jj = orc_fdot3(jk + 3 * i, jk + 3 * i);
-        double e = P.eta_s2[sp] * fma(a0, a0, orc_fdot3(a + 3 * i, a + 3 * i));
-        lev[i] = orc_level(jj, e, dm2, 0, kmax, &capped);
+        double jj = orc_mirror_dot3(jk + 3 * i, jk + 3 * i);
+        double e = P.eta_s2[sp] * fma(a0, a0, orc_mirror_dot3(a + 3 * i, a + 3 * i));
+        lev[i] = orc_mirror_level(jj, e, dm2, 0, kmax, &capped);
         st[3] += capped;
     }
     for (;;) {
@@ -1573,7 +1931,7 @@ static int orc_hermite_run(int64_t n, double *x, double *v, const double *m,
             int64_t step = (int64_t)1 << (kmax - lev[i]);
             if (t[i] + step != tn) continue;
             double a1[3], j1[3];
-            orc_hard_one(i, xp, vp, m, off, idx, &P, a1, j1);
+            orc_mirror_hard_one(i, xp, vp, m, off, idx, &P, a1, j1);
             ++st[1];
             st[2] += off[i + 1] - off[i];
             double h = (double)step * tick;
@@ -1595,17 +1953,19 @@ static int orc_hermite_run(int64_t n, double *x, double *v, const double *m,
             }
             t[i] = tn;
             if (tn == T) continue;
-            /* Eq. 18, with sqrt(A) sqrt(B) taken as sqrt(A B):
-             * dt^2 (sqrt(|a|^2 |a3|^2) + |a2|^2)
+            /* Eq. 18, with sqrt(A) sqrt(B) taken as sqrt(A B) and |j| |a3|
+             * in the denominator (as the oracle above):
+             * dt^2 (sqrt(|j|^2 |a3|^2) + |a2|^2)
              *     <= eta^2 (sqrt((|a|^2 + a0^2) |a2|^2) + |j|^2) */
             const int sp = i >= P.n_fs;
             double a0 = P.a0c[sp] * m[i];
-            double aa = orc_fdot3(a1, a1);
-            double a2sq = orc_fdot3(a2e, a2e);
-            double num = sqrt(fma(a0, a0, aa) * a2sq) + orc_fdot3(j1, j1);
-            double den = sqrt(aa * orc_fdot3(a3, a3)) + a2sq;
+            double aa = orc_mirror_dot3(a1, a1);
+            double jj = orc_mirror_dot3(j1, j1);
+            double a2sq = orc_mirror_dot3(a2e, a2e);
+            double num = sqrt(fma(a0, a0, aa) * a2sq) + jj;
+            double den = sqrt(jj * orc_mirror_dot3(a3, a3)) + a2sq;
             int kmin = lev[i] > 0 ? lev[i] - 1 : 0;
-            int k = orc_level(den, P.eta2[sp] * num, dm2, kmin, kmax, &capped);
+            int k = orc_mirror_level(den, P.eta2[sp] * num, dm2, kmin, kmax, &capped);
             st[3] += capped;
             while (tn % ((int64_t)1 << (kmax - k)) != 0) ++k;
             lev[i] = k;

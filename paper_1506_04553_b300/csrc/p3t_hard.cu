@@ -35,8 +35,9 @@
 // Time is counted in integer ticks of dt_max 2^-kmax, dt_max = dt_soft 2^-p.
 // A particle at level k steps dt_max 2^-k and its time is a multiple of its
 // step.  First step: Eq. 20 with eta_s = eta / 10; later steps:
-// Eq. 18 with a_0 = alpha G m_i / r_cut^2 and a^(2), a^(3) from the
-// Hermite interpolation of the step just taken; the step may at most double
+// Eq. 18 with a_0 = alpha G m_i / r_cut^2, a^(2), a^(3) from the
+// Hermite interpolation of the step just taken and |a^(1)| |a^(3)| as the
+// first term of the denominator (the dimensionally consistent reading); the step may at most double
 // and is halved until the current time is a multiple of it.  Each block step
 // predicts every member to the next time t_n (the least t_i + dt_i),
 // evaluates a and da at t_n for the members due then from the predicted
@@ -581,14 +582,16 @@ __device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3
     }
     t = tn;
     if (tn == H.T) return;
-    // Eq. 18, with sqrt(A) sqrt(B) taken as sqrt(A B), in squares:
-    // dt^2 (sqrt(|a|^2 |a3|^2) + |a2|^2) <= eta^2 (sqrt((|a|^2 + a0^2) |a2|^2) + |j|^2)
+    // Eq. 18, with sqrt(A) sqrt(B) taken as sqrt(A B), in squares, and the
+    // denominator's first term |a^(1)| |a^(3)| (the printed |a^(0)| |a^(3)|
+    // is not of the dimension of |a^(2)|^2):
+    // dt^2 (sqrt(|j|^2 |a3|^2) + |a2|^2) <= eta^2 (sqrt((|a|^2 + a0^2) |a2|^2) + |j|^2)
     const double a0 = dmul(H.a0c[sp], mi);
     const double aa = dot3(a1[0], a1[1], a1[2], a1[0], a1[1], a1[2]);
+    const double jj = dot3(j1[0], j1[1], j1[2], j1[0], j1[1], j1[2]);
     const double a2sq = dot3(a2e[0], a2e[1], a2e[2], a2e[0], a2e[1], a2e[2]);
-    const double num = dadd(dsqrt(dmul(dfma(a0, a0, aa), a2sq)),
-                            dot3(j1[0], j1[1], j1[2], j1[0], j1[1], j1[2]));
-    const double den = dadd(dsqrt(dmul(aa, dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]))),
+    const double num = dadd(dsqrt(dmul(dfma(a0, a0, aa), a2sq)), jj);
+    const double den = dadd(dsqrt(dmul(jj, dot3(a3[0], a3[1], a3[2], a3[0], a3[1], a3[2]))),
                             a2sq);
     const int kmin = lev > 0 ? lev - 1 : 0;
     int k = level_sq(den, dmul(H.eta2[sp], num), H, kmin, capped);

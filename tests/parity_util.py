@@ -94,3 +94,60 @@ def compare_lists(ctx, tree, og, gid, groups=None):
             lo_ = Lo[name][Lo[name + "_off"][g]:Lo[name + "_off"][g + 1]]
             lg_ = Lg[name][Lg[name + "_off"][q]:Lg[name + "_off"][q + 1]]
             assert sorted(lo_.tolist()) == sorted(lg_.tolist()), f"{name} list of group {g}"
+
+
+# --------------------------------------------------------------------------
+# Tolerances of the hard part (GPU against the plain FP64 oracle)
+# --------------------------------------------------------------------------
+
+U64 = 2.0 ** -53  # unit roundoff of FP64
+
+
+def hard_force_scales(pos, vel, m, off, idx, eps, r_cut, G=1.0):
+    """Per-particle bounds of the terms of the hard sums (Eq. 7): sum_j G m_j
+    / s^2 for the acceleration and sum_j G m_j |u| (4 / s^3 + 2.5 / (r_cut
+    s^2)) for the jerk (1 - K <= 1, |dK/dx| <= 35/16).  Rounding in the sums
+    is of order U64 times these, however much the terms cancel."""
+    n = len(m)
+    rows = np.repeat(np.arange(n), np.diff(off))
+    q = pos[rows] - pos[idx]
+    u = vel[rows] - vel[idx]
+    s2 = (q * q).sum(1) + eps * eps
+    un = np.sqrt((u * u).sum(1))
+    sa = np.bincount(rows, G * m[idx] / s2, minlength=n)
+    sj = np.bincount(rows, G * m[idx] * un * (4 / s2 ** 1.5 + 2.5 / (r_cut * s2)),
+                     minlength=n)
+    return sa, sj
+
+
+def hermite_sensitivity(run, pos, vel, reps=4, seed=0):
+    """How far rounding alone can move the result of a hard step: the
+    per-particle largest change of the plain oracle's final positions and
+    velocities when its input positions and velocities are perturbed by one
+    unit in the last place (random signs), over `reps` perturbations.
+    run(pos, vel) -> (x, v).  Returns (x0, v0, dx, dv)."""
+    x0, v0 = run(pos, vel)
+    rng = np.random.default_rng(seed)
+    dx = np.zeros(len(pos))
+    dv = np.zeros(len(pos))
+    for _ in range(reps):
+        pp = pos * (1 + rng.choice([-1.0, 1.0], pos.shape) * 2.0 * U64)
+        vp = vel * (1 + rng.choice([-1.0, 1.0], vel.shape) * 2.0 * U64)
+        x1, v1 = run(pp, vp)
+        dx = np.maximum(dx, np.abs(x1 - x0).max(axis=1))
+        dv = np.maximum(dv, np.abs(v1 - v0).max(axis=1))
+    return x0, v0, dx, dv
+
+
+def assert_hard_step_close(xg, vg, x0, v0, sx, sv, factor=16.0):
+    """GPU hard step against the plain oracle: every particle within
+    `factor` times the oracle's own response to one-ulp input perturbations
+    (hermite_sensitivity), and never tighter than 4 ulp of its coordinates.
+    Returns the largest ratios (x, v) for reporting."""
+    fx = 4 * 2 * U64 * np.abs(x0).max(axis=1)
+    fv = 4 * 2 * U64 * np.maximum(np.abs(v0).max(axis=1), np.abs(v0).max() * 1e-3)
+    rx = np.abs(xg - x0).max(axis=1) / np.maximum(sx, fx)
+    rv = np.abs(vg - v0).max(axis=1) / np.maximum(sv, fv)
+    assert rx.max() <= factor, (rx.max(), int(rx.argmax()))
+    assert rv.max() <= factor, (rv.max(), int(rv.argmax()))
+    return float(rx.max()), float(rv.max())

@@ -12,7 +12,7 @@ import pytest
 
 import oracle
 from paper_1506_04553_b300 import ics
-from parity_util import rel_err
+from parity_util import assert_hard_step_close, hermite_sensitivity, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -94,10 +94,12 @@ def test_species_soft_force(cuda):
 
 
 @pytest.mark.parametrize("where", ["core", "far"])
-def test_species_hard_step_bitwise(cuda, where):
+def test_species_hard_step(cuda, where):
     """A tight black hole binary in the core (one component of the binary
     and many stars: the per-component warp path) or far out (the binary
-    alone: a packed warp)."""
+    alone: a packed warp).  Against the plain oracle within 16 times its
+    response to one-ulp input perturbations; against the fused-order mirror
+    bit for bit."""
     import torch
     from paper_1506_04553_b300 import HermiteParams
     pos, vel, m = _system(6000, 23)
@@ -112,19 +114,26 @@ def test_species_hard_step_bitwise(cuda, where):
     eps = [1e-4, 1e-4, 0.0]
     r_cut = [0.016, 1 / 32, INF]
     hp = HermiteParams(dt_soft=1 / 256, eta=0.1, alpha=0.1)
-    xo, vo, st = oracle.hermite_species(pos, vel, m, off, idx, n_bh, dt_soft=hp.dt_soft,
-                                        eps=eps, r_cut=r_cut, eta=[0.1, 0.03],
-                                        gamma=GAMMA, alpha=0.1,
-                                        p=hp.log2_soft_over_max, kmax=hp.kmax)
+    okw = dict(dt_soft=hp.dt_soft, eps=eps, r_cut=r_cut, eta=[0.1, 0.03],
+               gamma=GAMMA, alpha=0.1, p=hp.log2_soft_over_max, kmax=hp.kmax)
+    xm, vm, sm = oracle.hermite_species(pos, vel, m, off, idx, n_bh, mirror=True, **okw)
+    _, _, st, det = oracle.hermite_species(pos, vel, m, off, idx, n_bh, detail=True, **okw)
+    x0, v0, sx, sv = hermite_sensitivity(
+        lambda p, v: oracle.hermite_species(p, v, m, off, idx, n_bh, **okw)[:2],
+        pos, vel)
     from paper_1506_04553_b300 import Context, Params
     ctx = Context(Params(r_out=r_cut[0], eps=eps[0], gamma=GAMMA))
     ctx.set_species(n, n_bh, r_cut_bh=r_cut[1], eps_bh=eps[1], h_bh=h[1], eta_bh=0.03)
     pg, vg = _dev(pos.T), _dev(vel.T)
     ctx.hard_step(pg, vg, _dev(m), _dev(off), _dev(idx, torch.int32), hp)
     s = ctx.stats()
-    assert np.array_equal(pg.cpu().numpy().T, xo)
-    assert np.array_equal(vg.cpu().numpy().T, vo)
+    xg, vg = pg.cpu().numpy().T, vg.cpu().numpy().T
+    assert det["margin"].min() > 1e-10  # no level decision near a tie
+    assert_hard_step_close(xg, vg, x0, v0, sx, sv)
     assert (s["herm_particle_steps"], s["herm_pairs"], s["herm_capped"]) == st[1:]
+    assert np.array_equal(xg, xm)
+    assert np.array_equal(vg, vm)
+    assert (s["herm_particle_steps"], s["herm_pairs"], s["herm_capped"]) == sm[1:]
     comp = s["herm_max_component"]
     assert (comp > 32) if where == "core" else (comp <= 32)
 

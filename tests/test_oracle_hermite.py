@@ -12,6 +12,15 @@ and its jerk, and the fourth-order Hermite integrator with block timesteps.
 * Energy of a compact softened cluster (all pairs hard) is conserved.
 * Particles with empty rows drift, x + dt v, and particles whose neighbours
   all lie beyond r_cut move in straight lines.
+* The block schedule does not depend on the unit of time: with time scaled
+  by 2 (velocities halved, G quartered, dt_soft doubled; all exact in
+  binary) the step gives the same positions and half the velocities, bit
+  for bit.  This pins the dimension of every term of Eq. 18-20 (Eq. 18's
+  denominator as printed, |a^(0)| |a^(3)|, fails it).
+* The first level of a binary at pericentre is the one Eq. 20 gives with
+  the closed-form acceleration and jerk of a Kepler orbit.
+* The fused-order mirror of the GPU kernels stays within the oracle's own
+  response to one-ulp input perturbations.
 """
 import numpy as np
 import pytest
@@ -112,8 +121,8 @@ def test_energy_of_compact_cluster_is_conserved():
         assert st[1] > st[0] > 4  # individual steps: more particle steps than blocks
         return abs(sum(energies(p, v)) - e0) / abs(e0)
 
-    e1, e2 = error(0.1), error(0.05)
-    assert e1 < 1e-5 and e2 < e1 / 8, (e1, e2)
+    e1, e2 = error(0.05), error(0.025)
+    assert e1 < 1e-7 and e2 < e1 / 8, (e1, e2)  # fourth order: ~1/16
 
 
 def test_isolated_and_out_of_range_particles_move_straight():
@@ -130,3 +139,59 @@ def test_isolated_and_out_of_range_particles_move_straight():
     assert np.array_equal(p[2:], pos[2:] + 0.5 * vel[2:])  # isolated drift
     assert np.array_equal(v, vel)
     assert np.abs(p[:2] - (pos[:2] + 0.5 * vel[:2])).max() <= 1e-15 * np.abs(pos).max() * 8
+
+
+def _scaled_run(lam):
+    pos, vel, m = _cluster(200, 11, 0.02)
+    off, idx = oracle.neighbours(pos, 0.03)
+    x, v, st, det = oracle.hermite(pos, vel / lam, m, off, idx, dt_soft=lam / 128,
+                                   G=1.0 / lam ** 2, eps=1e-4, r_cut=0.02,
+                                   gamma=GAMMA, detail=True)
+    return x, v * lam, st, det
+
+
+def test_schedule_does_not_depend_on_the_time_unit():
+    x1, v1, st1, d1 = _scaled_run(1.0)
+    for lam in (2.0, 0.25):
+        x2, v2, st2, d2 = _scaled_run(lam)
+        assert st1 == st2
+        assert np.array_equal(d1["nstep"], d2["nstep"])
+        assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
+    assert st1[1] > 2 * np.count_nonzero(d1["nstep"])  # several steps each
+
+
+def test_first_level_follows_eq20_for_a_kepler_binary():
+    # a binary at pericentre, separation r, relative speed w, far inside r_in
+    # (K = 0): |a_i| = G m_j / r^2 and, with q . u = 0, |da_i| = G m_j w / r^3
+    eta, alpha, r_cut, dt_soft = 0.1, 0.1, 1.0, 1.0
+    for e in (0.0, 0.3, 0.6, 0.9):
+        pos, vel, m, _ = _binary(e)
+        r = pos[1, 0] - pos[0, 0]
+        w = vel[1, 1] - vel[0, 1]
+        off, idx = np.array([0, 1, 2]), np.array([1, 0], dtype=np.int32)
+        _, _, _, det = oracle.hermite(pos, vel, m, off, idx, dt_soft=dt_soft,
+                                      r_cut=r_cut, gamma=GAMMA, eta=eta,
+                                      alpha=alpha, detail=True)
+        a = m[1] / r ** 2
+        j = m[1] * w / r ** 3
+        a0 = alpha * m[0] / r_cut ** 2
+        dt = (eta / 10) * np.sqrt((a * a + a0 * a0) / (j * j))
+        k = int(np.ceil(np.log2(dt_soft / 4 / dt)))  # dt_max = dt_soft / 4
+        assert det["lev0"][0] == det["lev0"][1] == k, (e, det["lev0"], k)
+
+
+def test_mirror_is_within_rounding_of_the_oracle():
+    from parity_util import assert_hard_step_close, hermite_sensitivity
+    pos, vel, m = _cluster(1500, 4, 0.03)
+    off, idx = oracle.neighbours(pos, 0.0125)
+    kw = dict(dt_soft=1 / 128, eps=1e-4, r_cut=0.01, gamma=GAMMA)
+    x0, v0, sx, sv = hermite_sensitivity(
+        lambda p, v: oracle.hermite(p, v, m, off, idx, **kw)[:2], pos, vel)
+    xm, vm, stm = oracle.hermite_mirror(pos, vel, m, off, idx, **kw)
+    assert_hard_step_close(xm, vm, x0, v0, sx, sv)
+    assert stm == oracle.hermite(pos, vel, m, off, idx, **kw)[2]
+    a, j = oracle.hard_force(pos, vel, m, off, idx, eps=1e-4, r_cut=0.01, gamma=GAMMA)
+    am, jm = oracle.hard_force_mirror(pos, vel, m, off, idx, eps=1e-4, r_cut=0.01,
+                                      gamma=GAMMA)
+    assert not np.array_equal(a, am)  # the two really round differently
+    assert np.abs(am - a).max() <= 1e-12 * np.abs(a).max()
