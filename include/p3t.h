@@ -327,8 +327,10 @@ int p3t_energy(p3t_ctx *ctx, int64_t n, const double *mass, const double *vel,
  * keeps until exit; no cudaMalloc, cudaFree or allocating library routine is
  * called.  The launch uses min(ceil(n / 256), 4 x SM count) blocks, so any n
  * fits as long as the device has at most 256 SMs.
- *   n    : 0 <= n <= P3T_ENERGY_NOALLOC_MAX_N (INT32_MAX, the kernel's
- *          index type); larger n is rejected with P3T_ERR_CAPACITY
+ *   n    : 0 <= n <= P3T_ENERGY_NOALLOC_MAX_N (INT32_MAX, the most
+ *          particles the library indexes: neighbour indices are int32);
+ *          larger n is rejected with P3T_ERR_CAPACITY.  The kernel indexes
+ *          in 64 bits, so no accepted n overflows it.
  *   mass, vel, pot, out : as p3t_energy (device pointers; pot may be NULL)
  * The first call on a device looks up the scratch address for that device
  * (cudaGetSymbolAddress); make that first call before any stream capture.

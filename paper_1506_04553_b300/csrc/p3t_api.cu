@@ -676,7 +676,7 @@ int p3t_energy(p3t_ctx *c, int64_t n, const double *mass, const double *vel,
         P3T_CUDA_TRY(cudaMemsetAsync(out, 0, 2 * sizeof(double), s));
         return P3T_OK;
     }
-    return p3t_energy_launch(c, (int)n, mass, vel, pot, out, s);
+    return p3t_energy_launch(c, (long long)n, mass, vel, pot, out, s);
 }
 
 int p3t_get_stats(p3t_ctx *c, p3t_stats *o)

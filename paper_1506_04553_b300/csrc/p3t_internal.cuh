@@ -296,7 +296,7 @@ int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,
 int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
                       const double *mass, const long long *off, const int *idx,
                       const p3t_hermite_params *hp, cudaStream_t s); // p3t_hard.cu
-int p3t_energy_launch(p3t_ctx *c, int n, const double *mass,
+int p3t_energy_launch(p3t_ctx *c, long long n, const double *mass,
                       const double *vel, const double *pot, double *out,
                       cudaStream_t s);                           // p3t_misc.cu
 int64_t p3t_sort_tiles(int64_t n);                               // p3t_sort.cu

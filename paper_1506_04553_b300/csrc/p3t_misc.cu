@@ -2,6 +2,8 @@
 // turns per-particle neighbour counts into CSR offsets.
 #include <mutex>
 
+#include <climits>
+
 #include "p3t_internal.cuh"
 
 namespace {
@@ -42,14 +44,17 @@ __device__ __forceinline__ double block_sum(double v)
     return s;
 }
 
-// Per-block partial sums of 1/2 m |v|^2 and 1/2 m phi.
+// Per-block partial sums of 1/2 m |v|^2 and 1/2 m phi.  The index is 64-bit:
+// a thread's last increment may pass n by up to one grid stride.
 __global__ void __launch_bounds__(TB)
-k_energy_part(int n, const double *__restrict__ m, const double *__restrict__ v,
-              const double *__restrict__ phi, double *__restrict__ part)
+k_energy_part(long long n, const double *__restrict__ m,
+              const double *__restrict__ v, const double *__restrict__ phi,
+              double *__restrict__ part)
 {
     double ek = 0.0, ep = 0.0;
-    for (int i = blockIdx.x * TB + threadIdx.x; i < n; i += gridDim.x * TB) {
-        double vx = v[i], vy = v[(size_t)n + i], vz = v[2 * (size_t)n + i];
+    const long long stride = (long long)gridDim.x * TB;
+    for (long long i = (long long)blockIdx.x * TB + threadIdx.x; i < n; i += stride) {
+        double vx = v[i], vy = v[n + i], vz = v[2 * n + i];
         ek += 0.5 * m[i] * (vx * vx + vy * vy + vz * vz);
         if (phi) ep += 0.5 * m[i] * phi[i];
     }
@@ -209,14 +214,15 @@ extern "C" int p3t_drift(int64_t n, double *pos, const double *vel, double dt,
     return P3T_OK;
 }
 
-int p3t_energy_launch(p3t_ctx *c, int n, const double *mass, const double *vel,
-                      const double *pot, double *out, cudaStream_t s)
+int p3t_energy_launch(p3t_ctx *c, long long n, const double *mass,
+                      const double *vel, const double *pot, double *out,
+                      cudaStream_t s)
 {
-    int nb = (n + TB - 1) / TB;
-    if (nb > c->sms * 4) nb = c->sms * 4;
+    long long nb = (n + TB - 1) / TB;
+    if (nb > c->sms * 4LL) nb = c->sms * 4LL;
     if (nb < 1) nb = 1;
-    k_energy_part<<<nb, TB, 0, s>>>(n, mass, vel, pot, c->red_part);
-    k_energy_final<<<1, 32, 0, s>>>(nb, c->red_part, out);
+    k_energy_part<<<(int)nb, TB, 0, s>>>(n, mass, vel, pot, c->red_part);
+    k_energy_final<<<1, 32, 0, s>>>((int)nb, c->red_part, out);
     p3t_count_launches(2);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
@@ -230,6 +236,12 @@ int p3t_energy_launch(p3t_ctx *c, int n, const double *mass, const double *vel,
 // current, and that address is what the kernels receive.
 static __device__ __align__(256) double
     g_energy_scratch[2 * P3T_ENERGY_NOALLOC_MAX_PARTIALS];
+
+// The largest index k_energy_part forms is below n + (blocks x TB), with at
+// most P3T_ENERGY_NOALLOC_MAX_PARTIALS blocks; it must fit its index type.
+static_assert(P3T_ENERGY_NOALLOC_MAX_N
+                  <= LLONG_MAX - (long long)P3T_ENERGY_NOALLOC_MAX_PARTIALS * TB,
+              "k_energy_part's index can overflow");
 
 namespace {
 constexpr int kMaxDevices = 64;
@@ -269,7 +281,7 @@ extern "C" int p3t_energy_noalloc(int64_t n, const double *mass,
     if (nb > 4LL * sms) nb = 4LL * sms;
     if (nb < 1) nb = 1;
     if (nb > P3T_ENERGY_NOALLOC_MAX_PARTIALS) return P3T_ERR_CAPACITY;
-    k_energy_part<<<(int)nb, TB, 0, s>>>((int)n, mass, vel, pot, scratch);
+    k_energy_part<<<(int)nb, TB, 0, s>>>((long long)n, mass, vel, pot, scratch);
     k_energy_final<<<1, 32, 0, s>>>((int)nb, scratch, out);
     p3t_count_launches(2);
     P3T_CUDA_TRY(cudaGetLastError());

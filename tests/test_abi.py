@@ -63,3 +63,19 @@ def test_binding_imports_without_gpu():
     import paper_1506_04553_b300 as P
     assert P.Params().n_group == 64
     assert os.path.exists(P.library_path())
+
+
+def test_noalloc_energy_limits_fit_the_kernel_index():
+    """The largest index the energy kernel forms is below n + blocks x 256
+    with at most P3T_ENERGY_NOALLOC_MAX_PARTIALS blocks; at the largest
+    accepted n it must fit the kernel's 64-bit index (and the entry point
+    must reject 2^31, the first n the library cannot index)."""
+    src = open(HEADER).read()
+    max_n = int(re.search(r"#define P3T_ENERGY_NOALLOC_MAX_N (\d+)LL", src).group(1))
+    parts = int(re.search(r"#define P3T_ENERGY_NOALLOC_MAX_PARTIALS (\d+)", src).group(1))
+    assert max_n + parts * 256 < 2 ** 63
+    assert max_n == 2 ** 31 - 1
+    misc = open(os.path.join(ROOT, "paper_1506_04553_b300", "csrc", "p3t_misc.cu")).read()
+    body = misc[misc.index("k_energy_part(long long n"):]
+    body = body[:body.index("block_sum")]
+    assert "for (long long i" in body
