@@ -208,33 +208,197 @@ def dist_setup(args):
 # CPU reference arm / baseline: the FP64 oracle on the host cores
 # --------------------------------------------------------------------------
 
-def oracle_sample(pos, mass, frac=1 / 16, seed=0):
-    """Times one step of the oracle on a bounded sample: tree build and walk
-    over all particles, forces of a random subset of groups holding about
-    `frac` of the particles; returns (seconds per full step, description)."""
-    import oracle
-    n = pos.shape[1]
-    p = np.ascontiguousarray(pos.T)
+SUBSAMPLE = 4096  # fixed subsample of the 16-step workload: the first 4096
+                  # of a seeded permutation
+
+
+def err_stats(a, ref):
+    """Median, 99th percentile and maximum of the per-particle relative error
+    |a - ref| / max(|ref|, 1e-3 rms|ref|) (vectors: rows; scalars: entries)."""
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if ref.ndim == 1:
+        a, ref = a[:, None], ref[:, None]
+    nr = np.linalg.norm(ref, axis=1)
+    floor = 1e-3 * np.sqrt(np.mean(nr ** 2))
+    e = np.linalg.norm(a - ref, axis=1) / np.maximum(nr, floor)
+    return {"median": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
+            "max": float(e.max()), "n": int(e.size)}
+
+
+def _timed(fn):
     t0 = time.perf_counter()
-    tree = oracle.Tree(p, mass, n_leaf=N_LEAF, n_group=N_GROUP)
-    t1 = time.perf_counter()
-    tree.walk(THETA, R_OUT, R_OUT)
-    t2 = time.perf_counter()
+    out = fn()
+    return out, time.perf_counter() - t0
+
+
+def cpu_baseline_and_accuracy(gs):
+    """The FP64 oracle on the host cores, on bounded samples of the GPU arm's
+    workloads, and, from the same oracle results, the error of the GPU's
+    outputs on those samples.  gs holds the GPU's inputs and outputs (host
+    arrays, particles as rows):
+
+    * kdk: the 16-step workload's state after the timed steps (positions,
+      forces).  Timed: oracle tree build + walk over all particles, forces of
+      random groups holding 1/16 of the particles, scaled (the baseline
+      value, all cores); direct summation on the fixed subsample.  Accuracy:
+      the subsample against the same-tree oracle and against direct sums.
+    * cfg1: Plummer N = 8192, r_out 0.01, in full.  Timed: tree and direct,
+      all cores and one core (the paper's one-core setup, Sect. 3.1.2).
+      Accuracy: every particle; neighbour rows compared bit for bit.
+    * vjp: Plummer N = 65536, r_out 0.005, loss sum w.a (seeded Gaussian
+      w).  Timed: oracle forward + gradient.  Accuracy: dL/dx, dL/dm.
+    * ensemble: eight clusters of the ensemble spanning its sizes (the
+      largest included), forces and gradients.
+    * king: the dense-core workload after its timed steps; oracle build +
+      walk and forces of groups holding 1/64 of the particles (timed, scaled);
+      accuracy of those particles.
+    Returns (cpu_baseline, accuracy)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    base, acc_out, legs = {}, {}, {}
+
+    # --- the 16-step workload (the bench's step) ---
+    k = gs["kdk"]
+    n = k["pos"].shape[0]
+    tree, t_build = _timed(lambda: oracle.Tree(k["pos"], k["m"], n_leaf=N_LEAF,
+                                               n_group=N_GROUP))
+    _, t_walk = _timed(lambda: tree.walk(THETA, R_OUT, R_OUT))
     g = tree.groups()
-    rng = np.random.default_rng(seed)
-    sel = rng.permutation(tree.ngroup)
+    sel = np.random.default_rng(0).permutation(tree.ngroup)
     cum = np.cumsum(g["count"][sel])
-    k = int(np.searchsorted(cum, frac * n)) + 1
-    sel = sel[:k]
-    t3 = time.perf_counter()
-    tree.force(eps=4.0 / n, r_cut=R_OUT, gamma=GAMMA, groups=sel)
-    t4 = time.perf_counter()
+    sel = sel[:int(np.searchsorted(cum, n / 16)) + 1]
     covered = int(g["count"][sel].sum())
-    t_step = (t1 - t0) + (t2 - t1) + (t4 - t3) * n / covered
-    desc = (f"oracle tree build + walk over all {n} particles, forces of "
-            f"{k} random groups ({covered} particles) scaled by {n / covered:.2f}; "
-            f"neighbour lists and kick/drift not included")
-    return t_step, desc
+    _, t_force = _timed(lambda: tree.force(eps=4.0 / n, r_cut=R_OUT, gamma=GAMMA,
+                                           groups=sel))
+    t_step = t_build + t_walk + t_force * n / covered
+    base = {"value": n / t_step, "unit": "particles/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"oracle tree build + walk over all {n} particles, forces "
+                      f"of {len(sel)} random groups ({covered} particles) scaled "
+                      f"by {n / covered:.2f}; neighbour lists and kick/drift not "
+                      f"included"}
+    sub = k["sub"]
+    a_tree = tree.force_particles(sub, eps=4.0 / n, r_cut=R_OUT, gamma=GAMMA)
+    a_dir, t_dir = _timed(lambda: oracle.direct(k["pos"], k["m"], eps=4.0 / n,
+                                                r_cut=R_OUT, gamma=GAMMA,
+                                                rows=sub))
+    legs["direct_subsample"] = {
+        "value": len(sub) / t_dir, "unit": "particles/s", "cores": cores,
+        "sample": f"O-direct of {len(sub)} particles against all {n}"}
+    acc_out["force_16step_subsample"] = dict(
+        err_stats(k["acc"][sub], a_tree), after_steps=k["steps"],
+        vs_direct=err_stats(k["acc"][sub], a_dir),
+        oracle_tree_vs_direct=err_stats(a_tree, a_dir))
+
+    # --- config 1 in full, all cores and one core ---
+    c = gs["cfg1"]
+    n1 = c["pos"].shape[0]
+    for th, name in ((None, "all_cores"), (1, "one_core")):
+        def tree_full():
+            t = oracle.Tree(c["pos"], c["m"], n_leaf=N_LEAF, n_group=N_GROUP)
+            t.walk(THETA, 0.01, 0.01, threads=th)
+            return t.force(eps=4.0 / n1, r_cut=0.01, gamma=GAMMA, threads=th)
+        a1, tt = _timed(tree_full)
+        d1, td = _timed(lambda: oracle.direct(c["pos"], c["m"], eps=4.0 / n1,
+                                              r_cut=0.01, gamma=GAMMA,
+                                              threads=th))
+        legs[f"cfg1_{name}"] = {"tree": n1 / tt, "direct": n1 / td,
+                                "unit": "particles/s",
+                                "cores": cores if th is None else 1}
+    off_o, idx_o = oracle.neighbours(c["pos"], 0.01)
+    rows_eq = int(sum(np.array_equal(c["idx"][c["off"][i]:c["off"][i + 1]],
+                                     idx_o[off_o[i]:off_o[i + 1]])
+                      for i in range(n1)))
+    acc_out["force_cfg1_full"] = dict(
+        err_stats(c["acc"], a1), vs_direct=err_stats(c["acc"], d1),
+        neighbour_rows_identical=f"{rows_eq}/{n1}",
+        offsets_identical=bool(np.array_equal(c["off"], off_o)))
+
+    # --- gradient workload ---
+    v = gs["vjp"]
+    n4 = v["pos"].shape[0]
+    r4 = 0.01 * (n4 / 8192) ** (-1.0 / 3.0)
+
+    def fwd_bwd():
+        t = oracle.Tree(v["pos"], v["m"], n_leaf=N_LEAF, n_group=N_GROUP)
+        t.walk(THETA, r4, r4)
+        a = t.force(eps=4.0 / n4, r_cut=r4, gamma=GAMMA)
+        return (a,) + t.vjp(v["w"], eps=4.0 / n4, r_cut=r4, gamma=GAMMA)
+    (a4, ox, om), t4 = _timed(fwd_bwd)
+    legs["vjp_fwd_bwd"] = {"value": n4 / t4, "unit": "particles/s (fwd+bwd)",
+                           "cores": cores}
+    acc_out["vjp_65536"] = {"force": err_stats(v["acc"], a4),
+                            "dL_dx": err_stats(v["gx"], ox),
+                            "dL_dm": err_stats(v["gm"], om)}
+
+    # --- ensemble: sampled clusters ---
+    e = gs.get("ensemble")
+    if e:
+        fa, fo, xa, xo, ma, mo = [], [], [], [], [], []
+        te = 0.0
+        for cl in e["clusters"]:
+            def one():
+                t = oracle.Tree(cl["pos"], cl["m"], n_leaf=e["n_leaf"],
+                                n_group=e["n_group"])
+                t.walk(THETA, cl["r_out"], cl["r_out"])
+                a = t.force(eps=cl["eps"], r_cut=cl["r_out"], gamma=GAMMA)
+                return (a,) + t.vjp(cl["w"], eps=cl["eps"], r_cut=cl["r_out"],
+                                    gamma=GAMMA)
+            (a, gx, gm), dt = _timed(one)
+            te += dt
+            fa.append(cl["acc"]), fo.append(a)
+            xa.append(cl["gx"]), xo.append(gx)
+            ma.append(cl["gm"]), mo.append(gm)
+        ne = sum(len(x) for x in fo)
+        legs["ensemble_sample"] = {"value": ne / te,
+                                   "unit": "particles/s (fwd+bwd)",
+                                   "cores": cores,
+                                   "sample": f"{len(fo)} clusters, {ne} particles"}
+        # errors per cluster (each cluster's own rms floor), pooled
+        def pooled(xs, rs):
+            errs = []
+            for a, r in zip(xs, rs):
+                a = a if a.ndim == 2 else a[:, None]
+                r = r if r.ndim == 2 else r[:, None]
+                nr = np.linalg.norm(r, axis=1)
+                fl = 1e-3 * np.sqrt(np.mean(nr ** 2))
+                errs.append(np.linalg.norm(a - r, axis=1) / np.maximum(nr, fl))
+            q = np.concatenate(errs)
+            return {"median": float(np.median(q)), "p99": float(np.quantile(q, 0.99)),
+                    "max": float(q.max()), "n": int(q.size)}
+        acc_out["ensemble_sampled"] = {
+            "cluster_sizes": [len(x) for x in fo],
+            "force": pooled(fa, fo), "dL_dx": pooled(xa, xo),
+            "dL_dm": pooled(ma, mo)}
+
+    # --- King W0 = 9 ---
+    kg = gs.get("king")
+    if kg:
+        nk = kg["pos"].shape[0]
+        tk, tb = _timed(lambda: oracle.Tree(kg["pos"], kg["m"], n_leaf=N_LEAF,
+                                            n_group=N_GROUP))
+        _, tw = _timed(lambda: tk.walk(kg["theta"], kg["r_out"], kg["r_out"]))
+        g = tk.groups()
+        sel = np.random.default_rng(1).permutation(tk.ngroup)
+        sel = sel[:int(np.searchsorted(np.cumsum(g["count"][sel]), nk / 64)) + 1]
+        cov = int(g["count"][sel].sum())
+        ak, tf = _timed(lambda: tk.force(eps=4.0 / nk, r_cut=kg["r_out"],
+                                         gamma=GAMMA, groups=sel))
+        _, order = tk.particles()
+        rows = np.concatenate([order[g["first"][q]:g["first"][q] + g["count"][q]]
+                               for q in sel])
+        legs["king"] = {"value": nk / (tb + tw + tf * nk / cov),
+                        "unit": "particles/s", "cores": cores,
+                        "sample": f"tree build + walk over all {nk}, forces of "
+                                  f"{len(sel)} groups ({cov} particles) scaled"}
+        acc_out["force_king_sampled"] = err_stats(kg["acc"][rows], ak[rows])
+    base["legs"] = legs
+    acc_out["measure"] = ("per-particle |x - x_ref| / max(|x_ref|, 1e-3 rms "
+                          "|x_ref|) against the same-tree FP64 oracle (R12); "
+                          "vs_direct: against FP64 direct summation")
+    acc_out["targets"] = "forces: median <= 1e-5, max <= 1e-4"
+    return base, acc_out
 
 
 def run_reference(args, world, rank):
@@ -270,9 +434,10 @@ def run_reference(args, world, rank):
 
     for w in range(args.warmup):
         forces(10_000 + w)
-    ts = []
+    ts, tfs = [], []
     for st in range(args.steps):
         tf, covered, k = forces(st)
+        tfs.append(tf)
         ts.append(t_build_walk + tf * n / covered)
     t_step = float(np.mean(ts))
     value = n / t_step
@@ -283,7 +448,14 @@ def run_reference(args, world, rank):
             f"kick/drift not included")
     line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "particles/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(tfs)),
+            "value_is_estimate": "yes: value = N / (build + walk + the sampled "
+                                 "forces x N / sampled particles); ms_per_step "
+                                 "is the measured time of one sampled step (the "
+                                 "1/256 force sample), estimated_full_step_ms "
+                                 "the extrapolated whole step",
+            "estimated_full_step_ms": 1e3 * t_step,
+            "build_walk_ms_once": 1e3 * t_build_walk,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": config(n, world),
             "cpu_baseline": {"value": value, "unit": "particles/s",
@@ -397,6 +569,14 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     ctx.check()  # any error latched on the device during the timed steps
     clocks = sampler.stop()
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    gs = {}  # the GPU's inputs and outputs for the oracle leg (host arrays)
+    if want_cpu:
+        # the forces of the last step were evaluated at these positions
+        gs["kdk"] = {"pos": pos.cpu().numpy().T.copy(), "m": mass_h,
+                     "acc": acc.cpu().numpy().T.astype(np.float64),
+                     "sub": np.random.default_rng(SEED).permutation(n)[:SUBSAMPLE],
+                     "steps": 2 * args.warmup + 1 + kp + args.steps + 1}
     # a replay relaunches the kernels captured from one step
     launches = (P.launch_count() - l0) + args.steps * launches_per_step
     ms = reduce_max(e0.elapsed_time(e1), dev)
@@ -637,20 +817,19 @@ def run_ours(args, world, rank, local):
                        "d2h_bytes_per_step": 6 * 8 * n + 8 * (n + 1) + 4 * nnz_last[0],
                        "ms_per_step": te * 1e3}
     if not args.no_ensemble:
-        line["ensemble"] = run_ensemble(args, dev)
+        line["ensemble"], gs["ensemble"] = run_ensemble(args, dev, want_cpu)
     if not args.no_p3t:
         line["p3t_step"] = run_p3t_step(args, dev)
     if not args.no_king:
-        line["king"] = run_king(args, dev)
+        line["king"], gs["king"] = run_king(args, dev, want_cpu)
     if not args.no_cost_model:
         line["cost_model"] = run_cost_model(args, dev)
     if not args.no_smbh:
         line["smbh"] = run_smbh(args, dev)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t_step, desc = oracle_sample(pos_h, mass_h, frac=1 / 16)
-        line["cpu_baseline"] = {"value": n / t_step, "unit": "particles/s",
-                                "cores": os.cpu_count() or 1, "kind": "oracle",
-                                "sample": desc}
+    line["vjp_65536"], gs["vjp"] = run_vjp_small(args, dev)
+    if want_cpu:
+        gs["cfg1"] = run_cfg1(dev)
+        line["cpu_baseline"], line["accuracy"] = cpu_baseline_and_accuracy(gs)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -874,7 +1053,7 @@ def run_smbh(args, dev):
             "steps_done": max(args.warmup, 3) + 4 + k}
 
 
-def run_king(args, dev):
+def run_king(args, dev, sample=False):
     """KDK steps on the dense-core workload: King (1966) W0 = 9, N = 2^21,
     Salpeter masses on [0.1, 10] normalised to M = 1, r_out = 0.002, theta
     0.5, eps = 4/N, neighbour lists within h = r_out; dt = 1/256.  One step
@@ -949,6 +1128,11 @@ def run_king(args, dev):
     ctx.check()
     ms = e0.elapsed_time(e1) / k
     nprof = max(prof["forces"], 1)
+    state = None
+    if sample:  # the forces of the last step were evaluated at these positions
+        state = {"pos": pos.cpu().numpy().T.copy(), "m": mass_h,
+                 "acc": acc.cpu().numpy().T.astype(np.float64),
+                 "theta": theta, "r_out": r_out}
     return {"workload": "King W0=9, N=2^21, Salpeter masses 0.1-10 (M=1), "
                         "r_out 0.002, theta 0.5, eps 4/N, h = r_out, dt 1/256",
             "step": "KDK (kick, drift, build, force, neighbour lists, kick); "
@@ -960,7 +1144,71 @@ def run_king(args, dev):
                                   "neighbours": prof["ngb_ms"] / nprof},
             "interactions_per_particle": {"pc": prof["int_pc"] / (n * nprof),
                                           "pp": prof["int_pp"] / (n * nprof)},
-            "neighbour_pairs": nnz}
+            "neighbour_pairs": nnz}, state
+
+
+def run_cfg1(dev):
+    """Plummer N = 8192 (seed 1), r_out 0.01, theta 0.4, eps 4/N, h = r_out:
+    one tree build, force and neighbour lists, for the accuracy record."""
+    import torch
+    import paper_1506_04553_b300 as P
+    from paper_1506_04553_b300 import ics
+    n = 8192
+    pos_h, _, m_h = ics.plummer(n, 1)
+    ctx = P.Context(P.Params(theta=THETA, r_out=0.01, gamma=GAMMA, eps=4.0 / n,
+                             h=0.01, n_leaf=N_LEAF, n_group=N_GROUP))
+    ctx.build_tree(torch.tensor(pos_h, device=dev), torch.tensor(m_h, device=dev))
+    acc = ctx.long_force()
+    off, idx = ctx.neighbours()
+    return {"pos": pos_h.T.copy(), "m": m_h,
+            "acc": acc.cpu().numpy().T.astype(np.float64),
+            "off": off.cpu().numpy(), "idx": idx.cpu().numpy()}
+
+
+def run_vjp_small(args, dev):
+    """The gradient workload: Plummer N = 65536 (seed 4), theta 0.4, r_out =
+    0.01 (N/8192)^(-1/3) = 0.005, eps 4/N, loss L = sum_i w_i . a_i with
+    w_i ~ N(0, I) (seed 40).  Times the forward (build + force) and the
+    backward (p3t_long_force_vjp) with CUDA events, median of 5; returns
+    (result, host arrays for the accuracy record)."""
+    import torch
+    import paper_1506_04553_b300 as P
+    from paper_1506_04553_b300 import ics
+    n = 65536
+    r_out = 0.01 * (n / 8192) ** (-1.0 / 3.0)
+    pos_h, _, m_h = ics.plummer(n, 4)
+    w_h = np.random.default_rng(40).normal(size=(n, 3))
+    ctx = P.Context(P.Params(theta=THETA, r_out=r_out, gamma=GAMMA, eps=4.0 / n,
+                             h=r_out, n_leaf=N_LEAF, n_group=N_GROUP))
+    pos = torch.tensor(pos_h, device=dev)
+    mass = torch.tensor(m_h, device=dev)
+    w = torch.tensor(w_h.T.copy(), dtype=torch.float32, device=dev)
+    acc = torch.empty((3, n), dtype=torch.float32, device=dev)
+    gx = torch.empty((3, n), dtype=torch.float64, device=dev)
+    gm = torch.empty((n,), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    fw, bw = [], []
+    for it in range(6):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        ctx.build_tree(pos, mass)
+        ctx.long_force(acc, check=False)
+        ev[1].record(stream)
+        ctx.long_force_vjp(w, gx, gm, check=False)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        if it:
+            fw.append(ev[0].elapsed_time(ev[1]))
+            bw.append(ev[1].elapsed_time(ev[2]))
+    ctx.check()
+    t_f, t_b = float(np.median(fw)), float(np.median(bw))
+    res = {"workload": "Plummer N=65536, theta 0.4, r_out 0.005, eps 4/N, "
+                       "L = sum w.a, w ~ N(0, I) seed 40",
+           "fwd_ms": t_f, "bwd_ms": t_b, "fwd_bwd_ratio": (t_f + t_b) / t_f,
+           "value": n / ((t_f + t_b) * 1e-3), "unit": "particles/s (fwd+bwd)"}
+    return res, {"pos": pos_h.T.copy(), "m": m_h, "w": w.cpu().numpy().T.astype(np.float64),
+                 "acc": acc.cpu().numpy().T.astype(np.float64),
+                 "gx": gx.cpu().numpy().T.copy(), "gm": gm.cpu().numpy()}
 
 
 def run_cost_model(args, dev):
@@ -1021,7 +1269,7 @@ def run_cost_model(args, dev):
             "points": points}
 
 
-def run_ensemble(args, dev):
+def run_ensemble(args, dev, sample=False):
     """256 independent Plummer clusters, N_c log-uniform in [1024, 65536],
     r_out = 0.01 (N_c / 8192)^(-1/3), eps = 4 / N_c, theta 0.4.  One step =
     tree build + force + backward (gradient of sum w.a) for all clusters,
@@ -1077,13 +1325,29 @@ def run_ensemble(args, dev):
     torch.cuda.synchronize()
     ctx.check()
     ms = e0.elapsed_time(e1) / k
-    return {"workload": "256 Plummer clusters, N_c log-uniform in [1024, 65536], "
-                        "theta 0.4, r_out 0.01 (N_c/8192)^(-1/3), eps 4/N_c",
-            "n": n, "clusters": 256, "step": "build + force + backward, "
-            "one CUDA graph, one walk+force launch for all clusters",
-            "value": n / (ms * 1e-3), "unit": "particles/s (fwd+bwd)",
-            "ms_per_step": ms, "autotuned": {"n_group": ng, "n_leaf": nl,
-                                             "build_force_ms": tune_ms}}
+    res = {"workload": "256 Plummer clusters, N_c log-uniform in [1024, 65536], "
+                       "theta 0.4, r_out 0.01 (N_c/8192)^(-1/3), eps 4/N_c",
+           "n": n, "clusters": 256, "step": "build + force + backward, "
+           "one CUDA graph, one walk+force launch for all clusters",
+           "value": n / (ms * 1e-3), "unit": "particles/s (fwd+bwd)",
+           "ms_per_step": ms, "autotuned": {"n_group": ng, "n_leaf": nl,
+                                            "build_force_ms": tune_ms}}
+    if not sample:
+        return res, None
+    # eight clusters spanning the sizes (smallest and largest included)
+    order = np.argsort(sizes, kind="stable")
+    pick = order[np.round(np.linspace(0, len(sizes) - 1, 8)).astype(int)]
+    a_h = acc.cpu().numpy().T.astype(np.float64)
+    w_h = w.cpu().numpy().T.astype(np.float64)
+    gx_h, gm_h = gx.cpu().numpy().T, gm.cpu().numpy()
+    cl = []
+    for c in pick:
+        lo, hi = int(off[c]), int(off[c + 1])
+        cl.append({"pos": pos_h[:, lo:hi].T.copy(), "m": m_h[lo:hi],
+                   "acc": a_h[lo:hi], "w": w_h[lo:hi], "gx": gx_h[lo:hi],
+                   "gm": gm_h[lo:hi], "r_out": float(r_out[c]),
+                   "eps": float(eps[c])})
+    return res, {"clusters": cl, "n_group": ng, "n_leaf": nl}
 
 
 def main():

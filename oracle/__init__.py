@@ -134,6 +134,9 @@ def _declare(lib):
     lib.orc_tree_vjp.argtypes = [_p, _d, _d, _d, _d, _p, _p, _p, C.c_int]
     lib.orc_tree_update.restype = None
     lib.orc_tree_update.argtypes = [_p, _p, _p]
+    lib.orc_tree_force_particles.restype = C.c_int
+    lib.orc_tree_force_particles.argtypes = [_p, _d, _d, _d, _d, _p, _p, _i64,
+                                             _p, _p, C.c_int]
     for pre in ("orc_", "orc_mirror_"):
         f = getattr(lib, pre + "hard_force")
         f.restype = None
@@ -535,6 +538,32 @@ class Tree:
             threads or DEFAULT_THREADS)
         assert rc == 0
         return (acc, pot) if potential else acc
+
+    def force_particles(self, particles, *, G=1.0, eps=0.0, r_cut, gamma=0.1,
+                        potential=False, threads=None):
+        """force() for the listed particles only (ORIGINAL indices); returns
+        acc (len x 3) (and pot) in the order listed."""
+        assert self._walk is not None, "walk() first"
+        particles = np.asarray(particles, dtype=np.int64)
+        _, order = self.particles()
+        inv = np.empty(self.n, np.int64)
+        inv[order] = np.arange(self.n)
+        g = self.groups()
+        # group of every sorted particle (groups are disjoint ranges)
+        cnt = g["count"]
+        start = np.cumsum(cnt) - cnt
+        gof = np.empty(self.n, np.int64)
+        gof[np.repeat(g["first"] - start, cnt) + np.arange(cnt.sum())] = \
+            np.repeat(np.arange(self.ngroup), cnt)
+        ids = np.ascontiguousarray(inv[particles])
+        grp = np.ascontiguousarray(gof[ids])
+        acc = np.zeros((self.n, 3))
+        pot = np.zeros(self.n)
+        rc = self._lib.orc_tree_force_particles(
+            self._h, G, eps, r_cut, gamma, _ptr(ids), _ptr(grp), ids.shape[0],
+            _ptr(acc), _ptr(pot), threads or DEFAULT_THREADS)
+        assert rc == 0
+        return (acc[particles], pot[particles]) if potential else acc[particles]
 
     # ---- gradients (structure frozen) ----
     def update(self, pos, mass):

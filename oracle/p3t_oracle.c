@@ -957,8 +957,32 @@ typedef struct {
     const orc_tree *t;
     double G, eps2, r_cut, gamma;
     const int64_t *groups; /* groups to evaluate, NULL = all */
+    const int64_t *ids;    /* or: sorted particles to evaluate (with groups[r]
+                              their groups) */
     double *acc, *pot;     /* indexed by ORIGINAL particle index */
 } orc_force_args;
+
+/* Acceleration and soft potential of sorted particle i of group g over the
+ * group's lists. */
+static void orc_force_one(const orc_force_args *a, int64_t g, int64_t i)
+{
+    const orc_tree *t = a->t;
+    const double *xi = t->x + 3 * i;
+    double acc[3] = {0, 0, 0}, pot = 0.0;
+    for (int64_t k = t->pc_off[g]; k < t->pc_off[g + 1]; ++k)
+        orc_cell_accel(t, t->pc[k], xi, a->G, a->eps2, acc, &pot);
+    for (int64_t k = t->ppf_off[g]; k < t->ppf_off[g + 1]; ++k)
+        orc_pair_soft(t, t->ppf[k], xi, a->G, a->eps2, a->r_cut, a->gamma,
+                      acc, &pot);
+    for (int64_t k = t->ppn_off[g]; k < t->ppn_off[g + 1]; ++k) {
+        if (t->ppn[k] == i) continue;
+        orc_pair_soft(t, t->ppn[k], xi, a->G, a->eps2, a->r_cut, a->gamma,
+                      acc, &pot);
+    }
+    int64_t o = t->order[i];
+    for (int c = 0; c < 3; ++c) a->acc[3 * o + c] = acc[c];
+    if (a->pot) a->pot[o] = pot;
+}
 
 static void orc_force_range(void *p, int64_t lo, int64_t hi)
 {
@@ -966,23 +990,12 @@ static void orc_force_range(void *p, int64_t lo, int64_t hi)
     const orc_tree *t = a->t;
     for (int64_t r = lo; r < hi; ++r) {
         int64_t g = a->groups ? a->groups[r] : r;
-        for (int64_t i = t->g_first[g]; i < t->g_first[g] + t->g_count[g]; ++i) {
-            const double *xi = t->x + 3 * i;
-            double acc[3] = {0, 0, 0}, pot = 0.0;
-            for (int64_t k = t->pc_off[g]; k < t->pc_off[g + 1]; ++k)
-                orc_cell_accel(t, t->pc[k], xi, a->G, a->eps2, acc, &pot);
-            for (int64_t k = t->ppf_off[g]; k < t->ppf_off[g + 1]; ++k)
-                orc_pair_soft(t, t->ppf[k], xi, a->G, a->eps2, a->r_cut,
-                              a->gamma, acc, &pot);
-            for (int64_t k = t->ppn_off[g]; k < t->ppn_off[g + 1]; ++k) {
-                if (t->ppn[k] == i) continue;
-                orc_pair_soft(t, t->ppn[k], xi, a->G, a->eps2, a->r_cut,
-                              a->gamma, acc, &pot);
-            }
-            int64_t o = t->order[i];
-            for (int c = 0; c < 3; ++c) a->acc[3 * o + c] = acc[c];
-            if (a->pot) a->pot[o] = pot;
+        if (a->ids) {
+            orc_force_one(a, g, a->ids[r]);
+            continue;
         }
+        for (int64_t i = t->g_first[g]; i < t->g_first[g] + t->g_count[g]; ++i)
+            orc_force_one(a, g, i);
     }
 }
 
@@ -994,8 +1007,27 @@ int orc_tree_force(const orc_tree *t, double G, double eps, double r_cut,
                    double *acc, double *pot, int nthreads)
 {
     if (!t->walked) return -1;
-    orc_force_args a = {t, G, eps * eps, r_cut, gamma, groups, acc, pot};
+    orc_force_args a = {t, G, eps * eps, r_cut, gamma, groups, NULL, acc, pot};
     orc_parallel_for(groups ? ng : t->ngroup, nthreads, orc_force_range, &a);
+    return 0;
+}
+
+/* The same for cnt single particles: sorted particle ids[r], a member of
+ * group groups[r]. */
+int orc_tree_force_particles(const orc_tree *t, double G, double eps,
+                             double r_cut, double gamma, const int64_t *ids,
+                             const int64_t *groups, int64_t cnt, double *acc,
+                             double *pot, int nthreads)
+{
+    if (!t->walked) return -1;
+    for (int64_t r = 0; r < cnt; ++r) {
+        int64_t g = groups[r];
+        if (g < 0 || g >= t->ngroup || ids[r] < t->g_first[g]
+            || ids[r] >= t->g_first[g] + t->g_count[g])
+            return -1;
+    }
+    orc_force_args a = {t, G, eps * eps, r_cut, gamma, groups, ids, acc, pot};
+    orc_parallel_for(cnt, nthreads, orc_force_range, &a);
     return 0;
 }
 

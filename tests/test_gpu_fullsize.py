@@ -65,3 +65,45 @@ def test_king_w9_salpeter_2p21(cuda):
     cnt = _check(pos.T.copy(), m, Params(theta=0.5, r_out=0.002, eps=4.0 / n),
                  dense_rows=True)
     assert cnt.max() >= 8  # dense core (measured maximum: 12 neighbours)
+
+
+def test_plummer_2p20_sixteen_kdk_steps(cuda):
+    """The 16-step workload: Plummer N = 2^20 (seed 2), theta 0.4, r_out
+    0.0025, eps 4/N, 16 leapfrog steps of the soft part at dt = 1/256 (kick
+    dt/2, drift dt, build, force, neighbour lists, kick dt/2: the Sect. 2.2
+    step with the Hermite step replaced by a drift of every particle).  After
+    every step the GPU's force on a fixed subsample (the first 4096 of a
+    seeded permutation) is compared with the same-tree FP64 oracle built from
+    the GPU's own positions of that step: trajectories of an N-body system
+    diverge, so the error is measured per step on the GPU's state."""
+    import torch
+    from paper_1506_04553_b300 import Context, Params, drift, kick
+    n, dt = 1 << 20, 1.0 / 256
+    pos, vel, m = ics.plummer(n, 2)
+    params = Params(theta=0.4, r_out=0.0025, eps=4.0 / n)
+    ctx = Context(params)
+    pd = torch.tensor(pos, device="cuda")
+    vd = torch.tensor(vel, device="cuda")
+    md = torch.tensor(m, device="cuda")
+    ctx.build_tree(pd, md)
+    acc = ctx.long_force()
+    sub = np.random.default_rng(2).permutation(n)[:4096]
+    worst = []
+    for step in range(16):
+        kick(vd, acc, dt / 2)
+        drift(pd, vd, dt)
+        ctx.build_tree(pd, md)
+        ctx.long_force(acc)
+        ctx.neighbours()
+        kick(vd, acc, dt / 2)
+        p_h = pd.cpu().numpy().T.copy()
+        a_g = acc.cpu().numpy().T.astype(np.float64)[sub]
+        t = oracle.Tree(p_h, m, n_leaf=params.n_leaf, n_group=params.n_group)
+        t.walk(params.theta, params.r_out, params.r_out)
+        a_o = t.force_particles(sub, G=params.G, eps=params.eps,
+                                r_cut=params.r_out, gamma=params.gamma)
+        e = rel_err(a_g, a_o)
+        worst.append((step + 1, float(np.median(e)), float(e.max())))
+        assert np.median(e) <= 1e-5 and e.max() <= 1e-4, worst[-1]
+    print("per-step error on the subsample (step, median, max):",
+          ", ".join(f"({s}, {a:.2e}, {b:.2e})" for s, a, b in worst))

@@ -4,8 +4,10 @@ oracle's gradient of L = sum_i w_i . a_i with the tree structure frozen.
 Tolerance: the CUDA path evaluates every Jacobian product in FP32
 (group-relative coordinates, ~1e-7 relative per term) and sums them into FP64;
 per-particle relative error (floor 1e-3 rms): median <= 1e-5 for dL/dx and
-dL/dm, max <= 1e-3 for dL/dx and <= 1e-2 for dL/dm (mass gradients cancel
-more; measured: medians ~3e-7, maxima 3e-5 and 1.3e-3)."""
+dL/dm, max <= 1e-4 for dL/dx and <= 4e-3 for dL/dm, about three times the
+largest values measured over these cases (medians ~3e-7; maxima 3.3e-5 for
+dL/dx and 1.2e-3 for dL/dm, whose terms cancel more: a particle's mass
+gradient sums signed potentials of opposite sign)."""
 import numpy as np
 import pytest
 
@@ -16,7 +18,7 @@ from parity_util import rel_err
 pytestmark = pytest.mark.gpu
 
 GAMMA = 0.1
-MED, MAX_X, MAX_M = 1e-5, 1e-3, 1e-2
+MED, MAX_X, MAX_M = 1e-5, 1e-4, 4e-3
 
 
 def _gpu_vjp(pos, m, w, params):
