@@ -20,9 +20,11 @@
 // arithmetic, and every lane applies each staged source (a broadcast read) to
 // both of its particles at once, as one packed FP32x2 pair.  Walking and evaluating in one kernel means the
 // interaction lists never go through HBM and the walk's memory latency hides
-// behind other warps' arithmetic.  Partial sums of a tile are added into
-// (hi, lo) pairs with an error-free two-sum, so the summation error is that
-// of 32-term FP32 sums.
+// behind other warps' arithmetic; the walk is software-pipelined by one
+// batch, so that a batch's box records are in flight while the previous
+// batch's tiles are evaluated.  Partial sums of a tile are added into (hi,
+// lo) pairs by compensated (Kahan) addition, so the summation error is
+// essentially that of 32-term FP32 sums.
 #include <math.h>
 
 #include "p3t_internal.cuh"
@@ -49,11 +51,15 @@ __device__ __forceinline__ float4 far_pad()
     return make_float4(1e15f, 1e15f, 1e15f, 0.0f);
 }
 
+// Compensated addition of v to the sum (hi, lo), Kahan's form: the rounding
+// error of hi + v, recovered as v - ((hi + v) - hi), goes into lo.  It is
+// exact whenever |hi| >= |v|, which holds after a group's first tiles (a
+// tile's partial sum is one of many); the terms themselves carry FP32
+// rounding, so no more exactness is needed.
 __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v)
 {
     float s = __fadd_rn(hi, v);
-    float bb = __fsub_rn(s, hi);
-    float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    float err = __fsub_rn(v, __fsub_rn(s, hi));
     hi = s;
     lo = __fadd_rn(lo, err);
 }
@@ -253,29 +259,43 @@ __device__ __forceinline__ void ring_push_ranges(int2 *ring, RangeRing &r,
     const unsigned m = __ballot_sync(0xffffffffu, flag);
     if (flag) ring[(r.head + r.nr + __popc(m & lanemask_lt())) & (RING - 1)] =
         make_int2(first, count);
-    int c = flag ? count : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    const int c = __reduce_add_sync(0xffffffffu, flag ? count : 0);
     r.nr += __popc(m);
     r.np += c;
 }
 
 // Takes the next `take` (<= 32, <= r.np) particle ids off the front of a
-// ring of ranges into tj[0..take).
-__device__ __forceinline__ void ring_take(int2 *ring, RangeRing &r, int take,
+// ring of ranges; returns this lane's id (lane < take) and writes it to
+// tj[lane].  Lane p finds the range holding tile position p by a binary
+// search over the ranges' inclusive prefix counts (held one per lane), so no
+// lane loops over a range.
+__device__ __forceinline__ int ring_take(int2 *ring, RangeRing &r, int take,
                                          int *tj, int lane)
 {
     const bool have = lane < r.nr;
     int2 g = have ? ring[(r.head + lane) & (RING - 1)] : make_int2(0, 0);
     int inc = warp_incl_scan(g.y);
-    int exc = inc - g.y;
-    if (have && exc < take) {
-        int stop = min(inc, take);
-        for (int p = exc; p < stop; ++p) tj[p] = g.x + (p - exc);
+    // the first range whose inclusive count exceeds p = lane: inc rises
+    // strictly over the ranges (none is empty) and stays at their total on
+    // the lanes past them, which is at least take > p
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int mid = (lo + hi) >> 1;
+        const bool right = __shfl_sync(0xffffffffu, inc, mid) <= lane;
+        lo = right ? mid + 1 : lo;
+        hi = right ? hi : mid;
     }
+    const int own = min(lo, 31);
+    const int ox = __shfl_sync(0xffffffffu, g.x, own);
+    const int oy = __shfl_sync(0xffffffffu, g.y, own);
+    const int oinc = __shfl_sync(0xffffffffu, inc, own);
+    const int id = ox + (lane - (oinc - oy));
+    if (lane < take) tj[lane] = id;
     const unsigned full = __ballot_sync(0xffffffffu, have && inc <= take);
     const int nfull = __popc(full);
     // the range straddling the tile boundary keeps its remainder
+    const int exc = inc - g.y;
     if (lane == nfull && have && exc < take) {
         int used = take - exc;
         ring[(r.head + lane) & (RING - 1)] = make_int2(g.x + used, g.y - used);
@@ -284,6 +304,7 @@ __device__ __forceinline__ void ring_take(int2 *ring, RangeRing &r, int take,
     r.head = (r.head + nfull) & (RING - 1);
     r.nr -= nfull;
     r.np -= take;
+    return id;
 }
 
 template <bool POT>
@@ -317,8 +338,22 @@ __device__ __forceinline__ void tile_end(GroupAcc<POT> &A, const Part3 &u,
     }
 }
 
-// One tile of up to 32 accepted cells.  TWO: the lane's second particle
-// (slot lane + 32) exists; groups of at most 32 particles skip it.
+// Cells 2p and 2p + 1 of the staged tile (j = 2p).
+__device__ __forceinline__ CellPair cell_pair(const WarpSmem &S, int j)
+{
+    CellPair c;
+    const float4 *t4 = reinterpret_cast<const float4 *>(&S.t[0][0]) + (j >> 1) * 5;
+    const float4 A = t4[0], B = t4[1], C = t4[2], D = t4[3], E = t4[4];
+    c.X = make_float2(A.x, A.y);   c.Y = make_float2(A.z, A.w);
+    c.Z = make_float2(B.x, B.y);   c.M = make_float2(B.z, B.w);
+    c.Qxx = make_float2(C.x, C.y); c.Qyy = make_float2(C.z, C.w);
+    c.Qzz = make_float2(D.x, D.y); c.Qxy = make_float2(D.z, D.w);
+    c.Qxz = make_float2(E.x, E.y); c.Qyz = make_float2(E.z, E.w);
+    return c;
+}
+
+// One tile of up to 32 accepted cells.  TWO: the lane holds a second
+// particle (slot 32 + lane); groups of at most 32 particles skip it.
 template <bool POT, bool TWO>
 __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
                                           int take, const float4 *cf0,
@@ -368,14 +403,7 @@ __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
     const f2 e2 = dup2(eps2);
 #pragma unroll kPcUnroll
     for (int j = 0; j < 32; j += 2) {
-        CellPair c;
-        const float4 *t4 = reinterpret_cast<const float4 *>(&S.t[0][0]) + (j >> 1) * 5;
-        const float4 A = t4[0], B = t4[1], C = t4[2], D = t4[3], E = t4[4];
-        c.X = make_float2(A.x, A.y);   c.Y = make_float2(A.z, A.w);
-        c.Z = make_float2(B.x, B.y);   c.M = make_float2(B.z, B.w);
-        c.Qxx = make_float2(C.x, C.y); c.Qyy = make_float2(C.z, C.w);
-        c.Qzz = make_float2(D.x, D.y); c.Qxy = make_float2(D.z, D.w);
-        c.Qxz = make_float2(E.x, E.y); c.Qyz = make_float2(E.z, E.w);
+        const CellPair c = cell_pair(S, j);
         pc_term2<POT>(P.x0, P.y0, P.z0, c, e2, u.x, u.y, u.z, u.p);
         if (TWO) pc_term2<POT>(P.x1, P.y1, P.z1, c, e2, w.x, w.y, w.z, w.p);
     }
@@ -404,10 +432,9 @@ __device__ __forceinline__ void particle_tile(
     const float4 *plo, const IPair &P, int k0, int k1,
     const ForceConsts &k, GroupAcc<POT> &A, int lane)
 {
-    ring_take(ring, r, take, S.tj, lane);
+    const int j = ring_take(ring, r, take, S.tj, lane);
     float4 v;
     if (lane < take) {
-        const int j = S.tj[lane];
         v = rel4(phi[j], plo[j], S.ct);
     } else {
         v = far_pad();
@@ -484,6 +511,36 @@ __device__ __forceinline__ void drain(WarpSmem &S, int lim, int &pc_head,
                                       P, k0, k1, kg, A, lane);
 }
 
+// Pops child ranges from the top of the walk stack until they hold at most
+// 32 cells and returns this lane's cell of the batch (-1 past its end);
+// total receives the batch size (warp-uniform, 0 when the stack is empty).
+__device__ __forceinline__ int pop_batch(WarpSmem &S, int &top, int &total,
+                                         int lane)
+{
+    const unsigned full = 0xffffffffu;
+    if (top == 0) {
+        total = 0;
+        return -1;
+    }
+    int rx = 0, ry = 0;
+    if (lane < top) {
+        int e = S.stack[top - 1 - lane];
+        rx = e >> 3;
+        ry = (e & 7) + 1;
+    }
+    int inc = warp_incl_scan(ry);
+    bool take = lane < top && inc <= 32;
+    int ntake = __popc(__ballot_sync(full, take));
+    total = __shfl_sync(full, inc, ntake - 1);
+    if (take)
+        for (int t = 0; t < ry; ++t) S.cb[inc - ry + t] = rx + t;
+    top -= ntake;
+    __syncwarp();
+    const int c = lane < total ? S.cb[lane] : -1;
+    __syncwarp();
+    return c;
+}
+
 template <bool POT>
 __global__ void __launch_bounds__(FW * 32, P3T_FORCE_MIN_BLOCKS)
 k_walk_force(const int *__restrict__ gclus,
@@ -550,33 +607,26 @@ k_walk_force(const int *__restrict__ gclus,
         int iter = 0;
         bool overflow = false;
         __syncwarp();
-        while (top > 0) {
+        // The walk is software-pipelined by one batch: the next batch is
+        // popped and its box records requested before the full tiles are
+        // evaluated, so the records' latency hides behind the warp's own
+        // arithmetic.  The batches, and so the tiles, are those of the plain
+        // loop (pop, test, push, evaluate), in the same order.
+        int total = 0;
+        int c = pop_batch(S, top, total, lane);
+        float4 cmn = make_float4(0.f, 0.f, 0.f, 0.f), cmx = cmn;
+        if (c >= 0) {
+            cmn = wmin[c];
+            cmx = wmax[c];
+        }
+        while (total > 0) {
             if (++iter > (1 << 24)) {  // a finite tree never gets here
                 overflow = true;
                 break;
             }
-            // pop child ranges from the top holding at most 32 cells
-            int rx = 0, ry = 0;
-            if (lane < top) {
-                int e = S.stack[top - 1 - lane];
-                rx = e >> 3;
-                ry = (e & 7) + 1;
-            }
-            int inc = warp_incl_scan(ry);
-            bool take = lane < top && inc <= 32;
-            int ntake = __popc(__ballot_sync(full, take));
-            int total = __shfl_sync(full, inc, ntake - 1);
-            if (take)
-                for (int t = 0; t < ry; ++t) S.cb[inc - ry + t] = rx + t;
-            top -= ntake;
-            __syncwarp();
-            const int c = lane < total ? S.cb[lane] : -1;
-            __syncwarp();
-
             bool is_pc = false, near = false, farl = false, open = false;
             int child = 0, nchild = 0, pfirst = 0, pcount = 0;
             if (c >= 0) {
-                const float4 cmn = wmin[c], cmx = wmax[c];
                 float d2 = box_d2(S.gmn, S.gmx, cmn, cmx);
                 float l = box_side(cmn, cmx);
                 if (mac_accept(d2, l, theta2, hg2)) {
@@ -584,10 +634,9 @@ k_walk_force(const int *__restrict__ gclus,
                 } else {
                     child = __float_as_int(cmn.w);
                     nchild = __float_as_int(cmx.w);
-                    if (nchild == 0) {
-                        int4 nd = node[c];
-                        pfirst = nd.x;
-                        pcount = nd.y;
+                    if (nchild <= 0) {  // a leaf: first particle, -count
+                        pfirst = child;
+                        pcount = -nchild;
                         near = d2 <= hg2;
                         farl = !near;
                     } else {
@@ -623,6 +672,12 @@ k_walk_force(const int *__restrict__ gclus,
                 top += np;
             }
             __syncwarp();
+            // the next batch, requested now
+            c = pop_batch(S, top, total, lane);
+            if (c >= 0) {
+                cmn = wmin[c];
+                cmx = wmax[c];
+            }
             // evaluate every full tile
             if (two)
                 drain<POT, true>(S, 32, pc_head, pc_n, rf, rn, cf0, cf1, cf2,

@@ -234,10 +234,9 @@ k_ngb_walk(const int *__restrict__ gclus,
                 if (box_d2(gmn, gmx, cmn, cmx) <= hg2) {
                     child = __float_as_int(cmn.w);
                     nchild = __float_as_int(cmx.w);
-                    if (nchild == 0) {
-                        int4 nd = node[c];
-                        pfirst = nd.x;
-                        pcount = nd.y;
+                    if (nchild <= 0) {  // a leaf: first particle, -count
+                        pfirst = child;
+                        pcount = -nchild;
                         near = true;
                     } else {
                         open = true;

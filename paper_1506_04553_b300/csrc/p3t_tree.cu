@@ -548,11 +548,16 @@ __device__ __forceinline__ void write_records(
     const double *bmn, const double *bmx, float4 *wmin, float4 *wmax,
     float4 *cf0, float4 *cf1, float4 *cf2)
 {
+    // .w: an internal cell's first child and number of children; a leaf's
+    // first particle and minus its particle count, so that a walk finds a
+    // leaf's range without a second, dependent load
+    const bool leaf = (nd.w & 255) == 0;
     wmin[c] = make_float4(__double2float_rd(bmn[0]), __double2float_rd(bmn[1]),
-                          __double2float_rd(bmn[2]), __int_as_float(nd.z));
+                          __double2float_rd(bmn[2]),
+                          __int_as_float(leaf ? nd.x : nd.z));
     wmax[c] = make_float4(__double2float_ru(bmx[0]), __double2float_ru(bmx[1]),
                           __double2float_ru(bmx[2]),
-                          __int_as_float(nd.w & 255));
+                          __int_as_float(leaf ? -nd.y : (nd.w & 255)));
     float ch[3], cl[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {

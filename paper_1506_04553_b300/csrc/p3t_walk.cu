@@ -95,10 +95,9 @@ k_walk(int ngroup, const int *__restrict__ gclus,
                 } else {
                     child = __float_as_int(cmn.w);
                     nchild = __float_as_int(cmx.w);
-                    if (nchild == 0) {
-                        int4 nd = node[c];
-                        pfirst = nd.x;
-                        pcount = nd.y;
+                    if (nchild <= 0) {  // a leaf: first particle, -count
+                        pfirst = child;
+                        pcount = -nchild;
                         near = d2 <= hg2;
                         far = !near;
                     } else {

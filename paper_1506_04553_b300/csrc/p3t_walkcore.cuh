@@ -43,9 +43,7 @@ __device__ __forceinline__ void push_ranges(int2 *ring, RangeRing &r,
     if (flag)
         ring[(r.head + r.nr + __popc(m & lanemask_lt())) & (RING - 1)] =
             make_int2(first, count);
-    int c = flag ? count : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    const int c = __reduce_add_sync(0xffffffffu, flag ? count : 0);
     r.nr += __popc(m);
     r.np += c;
 }
@@ -134,10 +132,9 @@ __device__ __forceinline__ bool walk_group(
             } else {
                 child = __float_as_int(cmn.w);
                 nchild = __float_as_int(cmx.w);
-                if (nchild == 0) {
-                    int4 nd = node[c];
-                    pfirst = nd.x;
-                    pcount = nd.y;
+                if (nchild <= 0) {  // a leaf: first particle, -count
+                    pfirst = child;
+                    pcount = -nchild;
                     near = d2 <= hg2;
                     farl = !near;
                 } else {
