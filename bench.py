@@ -58,6 +58,13 @@ B_DRIFT = 72
 FLOPS_PC = 49
 FLOPS_PP_FAR = 18
 FLOPS_PP_NEAR = 31
+# FP32 flops per interaction of the backward kernel (FMA = 2), fixed from its
+# source: the cell term's J^T w, dL/dM and twice the quadrupole adjoint (121)
+# and the three adds that sum J^T w over the sources; far and near particle
+# terms likewise (35 + 3, 64 + 3).
+FLOPS_BWD_PC = 124
+FLOPS_BWD_PP_FAR = 38
+FLOPS_BWD_PP_NEAR = 67
 FP32_LANES_PER_SM = 128
 
 
@@ -648,6 +655,11 @@ def run_ours(args, world, rank, local):
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if achieved else None,
                      "traffic": traffic,
+                     "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum "
+                                       "of one ncu capture of this kernel on this "
+                                       "workload, read from the committed summary "
+                                       "profiles/k_walk_force_plummer_1M.txt (not "
+                                       "measured in this run)",
                      "peak_note": f"FP32 FMA: {sms} SMs x 128 lanes x 2 x "
                                   f"{clk:.0f} MHz (max SM clock)"},
         "gpu_launches": launches,
@@ -690,6 +702,8 @@ def run_ours(args, world, rank, local):
     ctx.long_force(acc, check=False)
     ctx.long_force_vjp(wgt, gpos, gmass)  # warm-up
     fw, bw = [], []
+    ctx.profile(reset=True)
+    ctx.profile_enable(True)
     for _ in range(3):
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
@@ -704,8 +718,26 @@ def run_ours(args, world, rank, local):
         fw.append(a0.elapsed_time(a1))
         bw.append(a1.elapsed_time(a2))
     ctx.check()
+    ctx.profile_enable(False)
+    pb = ctx.profile(reset=True)
+    sb = ctx.stats()  # the interaction sets of this tree, walked by both
     t_f, t_b = float(np.median(fw)), float(np.median(bw))
     line["fwd_bwd_ratio"] = (t_f + t_b) / t_f
+    # roofline of the backward's walk + Jacobian kernel (k_walk_vjp)
+    vjp_ms = pb["vjp_walk_ms"] / max(pb["vjp_walks"], 1)
+    flops_b = (FLOPS_BWD_PC * sb["int_pc"]
+               + FLOPS_BWD_PP_FAR * (sb["int_pp"] - sb["int_pp_near"])
+               + FLOPS_BWD_PP_NEAR * sb["int_pp_near"])
+    ach_b = flops_b / (vjp_ms * 1e-3) / 1e12
+    line["roofline_bwd"] = {
+        "kernel": "k_walk_vjp", "bound": "alu", "achieved": ach_b,
+        "peak": peak, "unit": "TFLOP/s", "frac": ach_b / peak,
+        "frac_of_measured": ach_b / fma_meas, "kernel_ms": vjp_ms,
+        "flops": flops_b, "traffic": None,
+        "note": f"{FLOPS_BWD_PC} / {FLOPS_BWD_PP_FAR} / {FLOPS_BWD_PP_NEAR} "
+                "flops per cell / far / near interaction (FMA = 2) x the "
+                "interaction counts of the same tree, over the kernel's CUDA-"
+                "event time (mean of 3 calls); peak as for the forward"}
     line["fwd_bwd_ms"] = {"fwd_build_force": t_f, "bwd_vjp": t_b,
                           "note": "median of 3, same tree; bwd recomputes the "
                                   "interaction sets"}

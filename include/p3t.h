@@ -389,6 +389,9 @@ typedef struct p3t_profile {
     int64_t int_pc, int_pp, int_pp_near; /* interactions evaluated by
                                             p3t_long_force since the last
                                             reset */
+    double vjp_walk_ms;  /* the backward's walk + Jacobian kernel alone (part
+                            of walk_ms) */
+    int64_t vjp_walks;
 } p3t_profile;
 int p3t_profile_enable(p3t_ctx *ctx, int on);
 int p3t_get_profile(p3t_ctx *ctx, p3t_profile *out, int reset);

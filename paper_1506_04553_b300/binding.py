@@ -78,7 +78,8 @@ class _CProfile(C.Structure):
                 ("builds", C.c_int64), ("walks", C.c_int64),
                 ("forces", C.c_int64), ("ngbs", C.c_int64),
                 ("int_pc", C.c_int64), ("int_pp", C.c_int64),
-                ("int_pp_near", C.c_int64)]
+                ("int_pp_near", C.c_int64), ("vjp_walk_ms", C.c_double),
+                ("vjp_walks", C.c_int64)]
 
 
 _lib = _load_lib()

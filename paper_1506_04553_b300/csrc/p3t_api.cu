@@ -861,6 +861,8 @@ int p3t_get_profile(p3t_ctx *c, p3t_profile *o, int reset)
     o->walks = c->prof_calls[P3T_PH_WALK];
     o->forces = c->prof_calls[P3T_PH_FORCE];
     o->ngbs = c->prof_calls[P3T_PH_NGB];
+    o->vjp_walk_ms = c->prof_ms[P3T_PH_VJPWALK];
+    o->vjp_walks = c->prof_calls[P3T_PH_VJPWALK];
     if (c->built && c->n > 0) {
         long long cum[3];
         P3T_CUDA_TRY(cudaMemcpy(cum, c->st->cum_int, sizeof(cum),

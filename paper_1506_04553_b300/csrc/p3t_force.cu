@@ -478,7 +478,7 @@ __device__ __forceinline__ void particle_tile(
         }
         tile_end<POT>(A, u, w, 1.0f);
     } else {
-#pragma unroll 4
+#pragma unroll 8
         for (int j = 0; j < 32; j += 2) {
             const PartPair p = part_pair(S, j);
             pp_far2<POT>(P.x0, P.y0, P.z0, p, e2, u.x, u.y, u.z, u.p);
@@ -509,6 +509,16 @@ __device__ __forceinline__ void drain(WarpSmem &S, int lim, int &pc_head,
     while (rn.np >= lim)
         particle_tile<true, POT, TWO>(S, S.pn, rn, min(rn.np, 32), phi, plo,
                                       P, k0, k1, kg, A, lane);
+}
+
+// Prefetches [ptr, ptr + bytes) into L2, one 128-byte line per request,
+// lines t, t + nt, ... of the range.
+__device__ __forceinline__ void prefetch_l2(const void *ptr, size_t bytes,
+                                            size_t t, size_t nt)
+{
+    const char *p = (const char *)ptr;
+    for (size_t off = t * 128; off < bytes; off += nt * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
 }
 
 // Pops child ranges from the top of the walk stack until they hold at most
@@ -563,6 +573,23 @@ k_walk_force(const int *__restrict__ gclus,
     WarpSmem &S = smem[w];
     if (st->error) return;  // no valid tree
     const int G = st->ngroup;
+    {
+        // Warm L2 with the records every walk reads (the cells' box and
+        // force records, the particles' FP32 copies, ~80 B per cell and 32 B
+        // per particle), spread over all threads before the first group:
+        // after a build has streamed other data through L2, the walks' first
+        // touches of a record then hit L2 instead of waiting for HBM.
+        const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const size_t nt = (size_t)gridDim.x * blockDim.x;
+        const size_t nc = (size_t)st->ncell;
+        prefetch_l2(wmin, nc * sizeof(float4), t, nt);
+        prefetch_l2(wmax, nc * sizeof(float4), t, nt);
+        prefetch_l2(cf0, nc * sizeof(float4), t, nt);
+        prefetch_l2(cf1, nc * sizeof(float4), t, nt);
+        prefetch_l2(cf2, nc * sizeof(float4), t, nt);
+        prefetch_l2(phi, (size_t)n * sizeof(float4), t, nt);
+        prefetch_l2(plo, (size_t)n * sizeof(float4), t, nt);
+    }
     for (;;) {
         int g = 0;
         if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
@@ -699,12 +726,14 @@ k_walk_force(const int *__restrict__ gclus,
                               plo, P, k0, k1, kg, A, lane);
         // ---- write back in the caller's order ----
         const float Gc = k.G;
-        // work of this group and group of its particles, for the evaluation
-        // order of the next build (same weights as the instruction counts
-        // per source of the cell, far and near tiles)
+        // work of this group per particle slot of a lane, and the group of
+        // its particles, for the evaluation order of the next build (weights:
+        // the instruction counts per source of the cell, far and near tiles;
+        // the next build multiplies by the slots of the new group, so that a
+        // group estimated from a group of the other size class is not off by
+        // a factor of two)
         if (lane == 0)
-            gcost[g] = (two ? 16.0f : 8.0f) * cnt_pc + (two ? 6.0f : 3.0f) * cnt_pf +
-                       (two ? 11.0f : 5.5f) * cnt_pn;
+            gcost[g] = 8.0f * cnt_pc + 3.0f * cnt_pf + 5.5f * cnt_pn;
         if (v0) {
             int o = order[k0];
             pgroup[o] = g;

@@ -890,11 +890,13 @@ k_group_box(const int2 *__restrict__ grange, const double *__restrict__ xs,
 
 // Evaluation order of the groups, most expensive first (longest processing
 // time first shortens the tail of the dynamically scheduled group kernels).
-// The work of a new group is estimated by the work of the group that held
-// its first particle at the last force evaluation of the same n; groups are
-// bucketed by log2 of that estimate (8 buckets per octave) and written out
-// bucket by bucket, the order inside a bucket being arbitrary.  Without a
-// recorded evaluation the order is the identity.
+// The work of a new group is estimated from the work per particle slot of
+// the group that held its first particle at the last force evaluation of the
+// same n (its lists depend on where it is), times the slots of the new group
+// (two particles per lane above 32 particles); groups are bucketed by log2 of
+// that estimate (8 buckets per octave) and written out bucket by bucket, the
+// order inside a bucket being arbitrary.  Without a recorded evaluation the
+// order is the identity.
 constexpr int NBUCKET = 256;
 
 __device__ __forceinline__ int order_bucket(int g, const int2 *grange,
@@ -902,8 +904,14 @@ __device__ __forceinline__ int order_bucket(int g, const int2 *grange,
                                             const int *pgroup,
                                             const float *gcost, int cg)
 {
-    const int og = pgroup[order[grange[g].x]];
-    const float est = (og >= 0 && og < cg) ? gcost[og] : 0.0f;
+    const int2 gr = grange[g];
+    float sum = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {  // first, middle and last particle
+        const int og = pgroup[order[gr.x + (q * (gr.y - 1)) / 2]];
+        sum += (og >= 0 && og < cg) ? gcost[og] : 0.0f;
+    }
+    const float est = sum * (1.0f / 3.0f) * (gr.y > 32 ? 2.0f : 1.0f);
     int b = 0;
     if (est >= 1.0f) b = min(NBUCKET - 1, (int)(8.0f * __log2f(est)));
     return NBUCKET - 1 - b;  // descending work

@@ -205,33 +205,32 @@ __device__ __forceinline__ void cell_pair(const CellSrc &c, f2 nx, f2 ny,
     const f2 qx = fma2(c.Qxx, dx, fma2(c.Qxy, dy, mul2(c.Qxz, dz)));
     const f2 qy = fma2(c.Qxy, dx, fma2(c.Qyy, dy, mul2(c.Qyz, dz)));
     const f2 qz = fma2(c.Qxz, dx, fma2(c.Qyz, dy, mul2(c.Qzz, dz)));
-    const f2 wqx = fma2(c.Qxx, wx, fma2(c.Qxy, wy, mul2(c.Qxz, wz)));
-    const f2 wqy = fma2(c.Qxy, wx, fma2(c.Qyy, wy, mul2(c.Qyz, wz)));
-    const f2 wqz = fma2(c.Qxz, wx, fma2(c.Qyz, wy, mul2(c.Qzz, wz)));
     const f2 dqd = fma2(dx, qx, fma2(dy, qy, mul2(dz, qz)));
     const f2 wd = fma2(wx, dx, fma2(wy, dy, mul2(wz, dz)));
     const f2 wqd = fma2(wx, qx, fma2(wy, qy, mul2(wz, qz)));
     // J^T w = cw w + cd d + cq q - Qw / s^5 with
     //   cw = M / s^3 + (5/2) dQd / s^7,   cq = 5 wd / s^7,
     //   cd = -3 M wd / s^5 + 5 wQd / s^7 - (35/2) dQd wd / s^9
-    //      = [-3 M wd + (5 wQd - (35/2) dQd wd / s^2) / s^2] / s^5
+    //      = [-3 M wd + (5 wQd - (35/2) dQd wd / s^2) / s^2] / s^5;
+    // with v = -w / s^5 and u = cq d + v, cq q - Qw / s^5 = Q u, so
+    //   J^T w = cw w + cd d + Q u
     const f2 cw = fma2(mul2(dup2(2.5f), dqd), ri7, mul2(c.M, ri3));
     const f2 cdi = fma2(mul2(mul2(dqd, wd), ri2), dup2(-17.5f), mul2(dup2(5.0f), wqd));
     const f2 cd = mul2(fma2(cdi, ri2, mul2(c.M3, wd)), ri5);
     const f2 cq = mul2(dup2(5.0f), mul2(wd, ri7));  // 5 wd / s^7
     const f2 nri5 = mul2(dup2(-1.0f), ri5);
-    jx = fma2(cw, wx, fma2(cd, dx, fma2(cq, qx, mul2(nri5, wqx))));
-    jy = fma2(cw, wy, fma2(cd, dy, fma2(cq, qy, mul2(nri5, wqy))));
-    jz = fma2(cw, wz, fma2(cd, dz, fma2(cq, qz, mul2(nri5, wqz))));
+    const f2 vx = mul2(nri5, wx), vy = mul2(nri5, wy), vz = mul2(nri5, wz);
+    const f2 ux = fma2(cq, dx, vx), uy = fma2(cq, dy, vy), uz = fma2(cq, dz, vz);
+    jx = fma2(cw, wx, fma2(cd, dx, fma2(c.Qxx, ux, fma2(c.Qxy, uy, mul2(c.Qxz, uz)))));
+    jy = fma2(cw, wy, fma2(cd, dy, fma2(c.Qxy, ux, fma2(c.Qyy, uy, mul2(c.Qyz, uz)))));
+    jz = fma2(cw, wz, fma2(cd, dz, fma2(c.Qxz, ux, fma2(c.Qyz, uy, mul2(c.Qzz, uz)))));
     acc[0] = fma2(wd, ri3, acc[0]);
     acc[1] = add2(acc[1], jx);
     acc[2] = add2(acc[2], jy);
     acc[3] = add2(acc[3], jz);
     // 2S = -(w d^T + d w^T) / s^5 + 5 wd d d^T / s^7 (twice the adjoint: its
-    // factors are those of J^T w), with v = -w / s^5 and u = cq d + v:
-    // 2S_ab = d_a u_b + v_a d_b, 2S_aa = d_a (u_a + v_a)
-    const f2 vx = mul2(nri5, wx), vy = mul2(nri5, wy), vz = mul2(nri5, wz);
-    const f2 ux = fma2(cq, dx, vx), uy = fma2(cq, dy, vy), uz = fma2(cq, dz, vz);
+    // factors are those of J^T w): 2S_ab = d_a u_b + v_a d_b,
+    // 2S_aa = d_a (u_a + v_a)
     acc[4] = fma2(dx, add2(ux, vx), acc[4]);
     acc[5] = fma2(dy, add2(uy, vy), acc[5]);
     acc[6] = fma2(dz, add2(uz, vz), acc[6]);
@@ -440,7 +439,7 @@ k_walk_vjp(const int *__restrict__ gclus,
            const int2 *__restrict__ grange,
            const float4 *__restrict__ gmin, const float4 *__restrict__ gmax,
            const float4 *__restrict__ gctr, const float4 *__restrict__ wmin,
-           const float4 *__restrict__ wmax, const int4 *__restrict__ node,
+           const float4 *__restrict__ wmax,
            float theta2, const float4 *__restrict__ phi,
            const float4 *__restrict__ plo, const float4 *__restrict__ cf0,
            const float4 *__restrict__ cf1, const float4 *__restrict__ cf2,
@@ -501,8 +500,8 @@ k_walk_vjp(const int *__restrict__ gclus,
         ev.k.kA = cc.kA;
         ev.k.kB = cc.kB;
         long long cnt[3] = {0, 0, 0};
-        if (!p3t_walk::walk_group(S, gmin[g], gmax[g], wmin, wmax, node,
-                                  theta2, cc.hg2, cl, lane, ev, cnt)) {
+        if (!p3t_walk::walk_group(S, gmin[g], gmax[g], wmin, wmax, theta2,
+                                  cc.hg2, cl, lane, ev, cnt)) {
             if (lane == 0) p3t_raise(st, P3T_ERR_CAPACITY);
             continue;
         }
@@ -636,11 +635,13 @@ int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,
     int blocks = (int)((G + VW - 1) / VW);
     if (blocks > c->sms * 16) blocks = c->sms * 16;
     k_vjp_reset<<<1, 32, 0, s>>>(c->st);
+    const int slot = p3t_prof_open(c, P3T_PH_VJPWALK, s);
     k_walk_vjp<<<blocks, VW * 32, 0, s>>>(
         c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
-        c->wmax, c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
+        c->wmax, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
         c->order, n, k, w,
         gpos, gmass, cadj, c->gperm, c->st);
+    p3t_prof_close(c, slot, s);
     k_vjp_prep<<<c->sms * 8, 256, 0, s>>>(c->st, c->cM, cadj);
     k_vjp_leaves<<<c->sms * 8, 256, 0, s>>>(c->st, n, c->leaf_sorted, c->node,
                                             c->parent, c->ccom, c->xs, c->ms,

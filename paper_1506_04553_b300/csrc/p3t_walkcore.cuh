@@ -49,20 +49,32 @@ __device__ __forceinline__ void push_ranges(int2 *ring, RangeRing &r,
 }
 
 // Moves the next `take` (<= 32, <= r.np) particle ids off the front of a ring
-// of ranges into tj[0..take).
+// of ranges into tj[0..take).  Lane p finds the range holding position p by a
+// binary search over the ranges' inclusive prefix counts (one per lane):
+// they rise strictly over the ranges (none is empty) and stay at their total,
+// at least take > p, on the lanes past them.
 __device__ __forceinline__ void take_particles(int2 *ring, RangeRing &r,
                                                int take, int *tj, int lane)
 {
     const bool have = lane < r.nr;
     int2 g = have ? ring[(r.head + lane) & (RING - 1)] : make_int2(0, 0);
     int inc = warp_incl_scan(g.y);
-    int exc = inc - g.y;
-    if (have && exc < take) {
-        int stop = min(inc, take);
-        for (int p = exc; p < stop; ++p) tj[p] = g.x + (p - exc);
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        const int mid = (lo + hi) >> 1;
+        const bool right = __shfl_sync(0xffffffffu, inc, mid) <= lane;
+        lo = right ? mid + 1 : lo;
+        hi = right ? hi : mid;
     }
+    const int own = min(lo, 31);
+    const int ox = __shfl_sync(0xffffffffu, g.x, own);
+    const int oy = __shfl_sync(0xffffffffu, g.y, own);
+    const int oinc = __shfl_sync(0xffffffffu, inc, own);
+    if (lane < take) tj[lane] = ox + (lane - (oinc - oy));
     const unsigned full = __ballot_sync(0xffffffffu, have && inc <= take);
     const int nfull = __popc(full);
+    const int exc = inc - g.y;
     if (lane == nfull && have && exc < take) {
         int used = take - exc;
         ring[(r.head + lane) & (RING - 1)] = make_int2(g.x + used, g.y - used);
@@ -83,17 +95,52 @@ __device__ __forceinline__ void take_cells(Smem &S, CellRing &r, int take,
     r.n -= take;
 }
 
+// Pops child ranges from the top of the stack until they hold at most 32
+// cells; returns this lane's cell of the batch (-1 past its end) and the
+// batch size in total (warp-uniform, 0 when the stack is empty).
+__device__ __forceinline__ int pop_batch(Smem &S, int &top, int &total,
+                                         int lane)
+{
+    const unsigned full = 0xffffffffu;
+    if (top == 0) {
+        total = 0;
+        return -1;
+    }
+    int rx = 0, ry = 0;
+    if (lane < top) {
+        int e = S.stack[top - 1 - lane];
+        rx = e >> 3;
+        ry = (e & 7) + 1;
+    }
+    int inc = warp_incl_scan(ry);
+    bool take = lane < top && inc <= 32;
+    int ntake = __popc(__ballot_sync(full, take));
+    total = __shfl_sync(full, inc, ntake - 1);
+    if (take)
+        for (int t = 0; t < ry; ++t) S.cb[inc - ry + t] = rx + t;
+    top -= ntake;
+    __syncwarp();
+    const int c = lane < total ? S.cb[lane] : -1;
+    __syncwarp();
+    return c;
+}
+
 // Walks the tree of cell `root` (the group's cluster) for one group.  The
 // evaluator supplies
 //   ev.cells(S, take)            tile of `take` cells, ids in S.tj
 //   ev.particles<NEAR>(S, take)  tile of `take` particles, ids in S.tj
 // Returns false when the stack overflowed (the group is left unfinished).
-// cnt[0..2] receive the numbers of cells, near and far particles met.
+// cnt[0..2] receive the numbers of cells, near and far particles met.  The
+// walk is software-pipelined by one batch: the next batch is popped and its
+// box records requested before the full tiles are evaluated (the batches and
+// tiles are those of the plain pop-test-push-evaluate loop, in its order).
+// A leaf's box records carry its particle range (first particle in
+// wmin.w, minus the count in wmax.w), so no second load is needed.
 template <class Ev>
 __device__ __forceinline__ bool walk_group(
     Smem &S, float4 gmn, float4 gmx, const float4 *__restrict__ wmin,
-    const float4 *__restrict__ wmax, const int4 *__restrict__ node,
-    float theta2, float hg2, int root, int lane, Ev &ev, long long cnt[3])
+    const float4 *__restrict__ wmax, float theta2, float hg2, int root,
+    int lane, Ev &ev, long long cnt[3])
 {
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
     CellRing rc = {0, 0};
@@ -102,29 +149,18 @@ __device__ __forceinline__ bool walk_group(
     int top = 1;
     int iter = 0;
     __syncwarp();
-    while (top > 0) {
+    int total = 0;
+    int c = pop_batch(S, top, total, lane);
+    float4 cmn = make_float4(0.f, 0.f, 0.f, 0.f), cmx = cmn;
+    if (c >= 0) {
+        cmn = wmin[c];
+        cmx = wmax[c];
+    }
+    while (total > 0) {
         if (++iter > (1 << 24)) return false;  // a finite tree never gets here
-        int rx = 0, ry = 0;
-        if (lane < top) {
-            int e = S.stack[top - 1 - lane];
-            rx = e >> 3;
-            ry = (e & 7) + 1;
-        }
-        int inc = warp_incl_scan(ry);
-        bool take = lane < top && inc <= 32;
-        int ntake = __popc(__ballot_sync(full, take));
-        int total = __shfl_sync(full, inc, ntake - 1);
-        if (take)
-            for (int t = 0; t < ry; ++t) S.cb[inc - ry + t] = rx + t;
-        top -= ntake;
-        __syncwarp();
-        const int c = lane < total ? S.cb[lane] : -1;
-        __syncwarp();
-
         bool is_pc = false, near = false, farl = false, open = false;
         int child = 0, nchild = 0, pfirst = 0, pcount = 0;
         if (c >= 0) {
-            const float4 cmn = wmin[c], cmx = wmax[c];
             float d2 = box_d2(gmn, gmx, cmn, cmx);
             float l = box_side(cmn, cmx);
             if (mac_accept(d2, l, theta2, hg2)) {
@@ -164,6 +200,11 @@ __device__ __forceinline__ bool walk_group(
             top += np;
         }
         __syncwarp();
+        c = pop_batch(S, top, total, lane);
+        if (c >= 0) {
+            cmn = wmin[c];
+            cmx = wmax[c];
+        }
         while (rc.n >= 32) {
             take_cells(S, rc, 32, lane);
             ev.cells(S, 32);
