@@ -372,6 +372,9 @@ typedef struct p3t_stats {
     int64_t herm_components;     /* connected components integrated */
     int64_t herm_max_component;  /* particles in the largest one */
     int64_t herm_max_block_steps; /* most block steps of one component */
+    int64_t need_cells;  /* cells the last p3t_build_tree needed (its count
+                            when it succeeded; at least what the failing level
+                            asked for when a p3t_limits cell bound stopped it) */
 } p3t_stats;
 int p3t_get_stats(p3t_ctx *ctx, p3t_stats *s);
 
@@ -456,6 +459,51 @@ int p3t_get_groups(p3t_ctx *ctx, int32_t *first, int32_t *count, float *fmin,
 int p3t_get_lists(p3t_ctx *ctx, int64_t *pc_off, int32_t *pc,
                   int64_t *ppn_off, int32_t *ppn, int64_t *ppf_off,
                   int32_t *ppf);
+
+/* Bounds of the kernels' loops and bounded waits, and of the cells a build may
+ * allocate: a service for tests and for callers that want a failure rather
+ * than a long wait.  The paper has no counterpart.  A value <= 0 selects the
+ * default.
+ *   walk_iters  : iterations of one group's tree walk in the force,
+ *                 neighbour, backward and inspection walks (default 2^24;
+ *                 a walk of a finite tree needs a few hundred to a few
+ *                 thousand); past it the group is abandoned and
+ *                 P3T_ERR_TIMEOUT latched
+ *   uf_rounds   : rounds of the lock-free union-find of p3t_hard_step per
+ *                 edge and lookup (default 2^20): P3T_ERR_TIMEOUT
+ *   block_steps : block steps of one component in p3t_hard_step (default
+ *                 2^26): P3T_ERR_TIMEOUT
+ *   max_cells   : cells p3t_build_tree may allocate (default: no bound); a
+ *                 tree that needs more returns P3T_ERR_CAPACITY, and
+ *                 p3t_stats.need_cells says how many the failing level asked
+ *                 for
+ * A kernel that reaches a bound stops that work item and returns normally;
+ * the latched error is returned by p3t_check (or the next synchronising
+ * call), after which the context is usable again. */
+typedef struct p3t_limits {
+    int64_t walk_iters;
+    int64_t uf_rounds;
+    int64_t block_steps;
+    int64_t max_cells;
+} p3t_limits;
+
+/* Sets the bounds (NULL: all defaults).  Errors: P3T_ERR_INVALID (ctx NULL). */
+int p3t_set_limits(p3t_ctx *ctx, const p3t_limits *lim);
+
+/* The sources the fused walk + force kernel itself evaluates, per group: runs
+ * p3t_long_force (acc as there, device float[3][n], written) with a recording
+ * instantiation of the kernel that appends, for every staged tile, one record
+ * per source to rec (device int64[cap]): the group (numbering of
+ * p3t_get_groups) in bits 33-62, the kind (0 accepted cell, 1 near-leaf
+ * particle, 2 far-leaf particle) in bits 31-32, and the cell id (numbering
+ * of p3t_get_cells) or sorted particle id in bits 0-30.  Records are in no
+ * particular order; *count (host) receives their number.  The timed path
+ * uses the instantiation without recording.  Synchronises.
+ * Errors: P3T_ERR_CAPACITY (*count > cap; the first cap records written),
+ * P3T_ERR_INVALID (cap < 1, NULL pointers), P3T_ERR_STATE (no tree), and
+ * those of p3t_long_force. */
+int p3t_force_lists(p3t_ctx *ctx, float *acc, int64_t *rec, int64_t cap,
+                    int64_t *count, void *stream);
 
 /* Human-readable name of a status code. */
 const char *p3t_status_string(int status);

@@ -63,7 +63,7 @@ class _CStats(C.Structure):
         "list_pp_far", "int_pc", "int_pp", "int_pp_near", "max_walk_stack",
         "nnz", "herm_block_steps", "herm_particle_steps", "herm_pairs",
         "herm_capped", "herm_components", "herm_max_component",
-        "herm_max_block_steps")]
+        "herm_max_block_steps", "need_cells")]
 
 
 class _CHermite(C.Structure):
@@ -102,6 +102,8 @@ _sigs = {
     "p3t_get_cells": [_vp] + [_vp] * 10,
     "p3t_get_groups": [_vp, _vp, _vp, _vp, _vp],
     "p3t_get_lists": [_vp] + [_vp] * 6,
+    "p3t_force_lists": [_vp, _vp, _vp, _i64, _vp, _vp],
+    "p3t_set_limits": [_vp, _vp],
     "p3t_profile_enable": [_vp, C.c_int],
     "p3t_check": [_vp, _vp],
     "p3t_long_force_vjp": [_vp, _vp, _vp, _vp, _vp],
@@ -462,6 +464,46 @@ class Context:
             "pc_off", "pc", "ppn_off", "ppn", "ppf_off", "ppf")]), "p3t_get_lists")
         for k in ("pc", "ppn", "ppf"):
             out[k] = out[k][: int(offs[k + "_off"][-1])]
+        return out
+
+
+    def set_limits(self, walk_iters=0, uf_rounds=0, block_steps=0, max_cells=0):
+        """Bounds of the kernels' loops and waits and of the cells a build may
+        allocate (p3t_set_limits; 0 = the default)."""
+        lim = (C.c_int64 * 4)(walk_iters, uf_rounds, block_steps, max_cells)
+        _check(_lib.p3t_set_limits(self._h, lim), "p3t_set_limits")
+
+    def force_lists(self, stream=None) -> dict:
+        """The sources the fused walk + force kernel evaluated, per group, as
+        recorded by the kernel itself (p3t_force_lists): sorted arrays of
+        cell ids ("pc"), near-leaf and far-leaf sorted particle ids ("ppn",
+        "ppf") in CSR per group (numbering of groups() and cells())."""
+        import torch
+        n = self.stats()["n"]
+        acc = torch.empty((3, max(n, 1)), dtype=torch.float32, device="cuda")
+        cnt = C.c_int64(0)
+        cap = 1 << 16
+        for _ in range(2):
+            rec = torch.empty((cap,), dtype=torch.int64, device="cuda")
+            code = _lib.p3t_force_lists(self._h, _vp(acc.data_ptr()),
+                                        _vp(rec.data_ptr()), cap,
+                                        C.byref(cnt), _stream(stream))
+            if code != 2:
+                break
+            cap = cnt.value
+        _check(code, "p3t_force_lists")
+        r = rec[: cnt.value].cpu().numpy()
+        g = (r >> 33).astype(np.int64)
+        kind = (r >> 31) & 3
+        ident = (r & ((1 << 31) - 1)).astype(np.int64)
+        ng = self.stats()["n_groups"]
+        out = {}
+        for k, name in enumerate(("pc", "ppn", "ppf")):
+            sel = kind == k
+            o = np.lexsort((ident[sel], g[sel]))
+            gs, ids = g[sel][o], ident[sel][o]
+            out[name + "_off"] = np.searchsorted(gs, np.arange(ng + 1))
+            out[name] = ids
         return out
 
 

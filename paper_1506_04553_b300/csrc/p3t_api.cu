@@ -330,6 +330,9 @@ int p3t_create(p3t_ctx **out, const p3t_params *p)
     }
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     if (c->sms <= 0) c->sms = 148;
+    c->lim_walk = P3T_LIM_WALK;
+    c->lim_uf = P3T_LIM_UF;
+    c->lim_block = P3T_LIM_BLOCK;
     int64_t d = 0;
     int rc = P3T_OK;
     if ((rc = grow(c->st, d, 1, sizeof(P3TDevState))) != P3T_OK ||
@@ -403,7 +406,9 @@ int p3t_build_tree(p3t_ctx *c, int64_t n, const double *pos,
         if (n > c->cap_n || c->cap_cells == 0) return P3T_ERR_CAPACITY;
     } else {
         P3T_TRY(ensure_particles(c, n));
-        if (c->cap_cells < n / 2 + 64) P3T_TRY(ensure_cells(c, n / 2 + 64));
+        int64_t first = n / 2 + 64;
+        if (c->lim_cells > 0 && first > c->lim_cells) first = c->lim_cells;
+        if (c->cap_cells < first) P3T_TRY(ensure_cells(c, first));
     }
     P3T_TRY(upload_clusters(c, s));
     for (int attempt = 0; attempt < 8; ++attempt) {
@@ -420,14 +425,28 @@ int p3t_build_tree(p3t_ctx *c, int64_t n, const double *pos,
         P3T_TRY(sync_state(c, s));
         if (c->hst->error == 0) {
             // leave room for later builds that may not allocate
+            c->need_cells = c->hst->ncell;
             int64_t want = c->hst->ncell + c->hst->ncell / 2 + 64;
+            if (c->lim_cells > 0 && want > c->lim_cells) want = c->lim_cells;
             if (want > c->cap_cells) P3T_TRY(ensure_cells_keep(c, want));
             c->built = 1;
             return P3T_OK;
         }
-        if (c->hst->error != P3T_ERR_CAPACITY) return c->hst->error;
+        if (c->hst->error != P3T_ERR_CAPACITY) {  // returned once, then cleared
+            const int e = c->hst->error;
+            P3T_TRY(clear_error(c, s));
+            return e;
+        }
+        c->need_cells = c->hst->need_cells;
         int64_t want = 2 * c->cap_cells;
         if (c->hst->need_cells > want) want = c->hst->need_cells;
+        if (c->lim_cells > 0 && want > c->lim_cells) {
+            if (c->cap_cells >= c->lim_cells) {
+                P3T_TRY(clear_error(c, s));
+                return P3T_ERR_CAPACITY;
+            }
+            want = c->lim_cells;
+        }
         P3T_TRY(ensure_cells(c, want));
     }
     return P3T_ERR_CAPACITY;
@@ -513,6 +532,36 @@ int p3t_long_force(p3t_ctx *c, float *acc, double *pot, void *stream)
     int rc = p3t_run_force(c, acc, pot, s);
     p3t_prof_close(c, slot, s);
     return rc;
+}
+
+int p3t_set_limits(p3t_ctx *c, const p3t_limits *l)
+{
+    if (!c) return P3T_ERR_INVALID;
+    c->lim_walk = (l && l->walk_iters > 0) ? l->walk_iters : P3T_LIM_WALK;
+    c->lim_uf = (l && l->uf_rounds > 0) ? l->uf_rounds : P3T_LIM_UF;
+    c->lim_block = (l && l->block_steps > 0) ? l->block_steps : P3T_LIM_BLOCK;
+    c->lim_cells = (l && l->max_cells > 0) ? l->max_cells : 0;
+    return P3T_OK;
+}
+
+int p3t_force_lists(p3t_ctx *c, float *acc, int64_t *rec, int64_t cap,
+                    int64_t *count, void *stream)
+{
+    if (!c || !count || cap < 1 || !rec) return P3T_ERR_INVALID;
+    if (!c->built) return P3T_ERR_STATE;
+    *count = 0;
+    if (c->n == 0) return P3T_OK;
+    if (!acc) return P3T_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    P3T_TRY(p3t_run_force(c, acc, nullptr, s, (long long *)rec, cap));
+    P3T_TRY(sync_state(c, s));
+    if (c->hst->error) {
+        const int e = c->hst->error;
+        P3T_TRY(clear_error(c, s));
+        return e;
+    }
+    *count = c->hst->rec_n;
+    return *count > cap ? P3T_ERR_CAPACITY : P3T_OK;
 }
 
 int p3t_long_force_vjp(p3t_ctx *c, const float *w, double *grad_pos,
@@ -697,6 +746,7 @@ int p3t_get_stats(p3t_ctx *c, p3t_stats *o)
     o->herm_max_component = c->hst->herm[5];
     o->herm_max_block_steps = c->hst->herm[6];
     if (c->n == 0) return P3T_OK;
+    o->need_cells = c->need_cells;
     o->n_cells = c->hst->ncell;
     o->n_groups = c->hst->ngroup;
     o->n_levels = c->hst->max_level + 1;
@@ -817,7 +867,11 @@ int p3t_get_lists(p3t_ctx *c, int64_t *pc_off, int32_t *pc, int64_t *ppn_off,
         P3T_TRY(p3t_run_walk(c, 0, s));
         P3T_TRY(p3t_scan_lists(c, s));
         P3T_TRY(sync_state(c, s));
-        if (c->hst->error) return c->hst->error;
+        if (c->hst->error) {  // returned once, then cleared
+            const int e = c->hst->error;
+            P3T_TRY(clear_error(c, s));
+            return e;
+        }
         for (int L = 0; L < 3; ++L) {
             P3T_TRY(ensure_list(c, L, c->hst->tot[L]));
             c->list_tot[L] = c->hst->tot[L];

@@ -307,6 +307,29 @@ __device__ __forceinline__ int ring_take(int2 *ring, RangeRing &r, int take,
     return id;
 }
 
+// Recording of the sources a group evaluates (the inspection entry point
+// p3t_force_lists; the timed kernels are the instantiations without it).
+// Every staged tile appends one record per real source: the group in bits
+// 33-62, the kind (0 cell, 1 near particle, 2 far particle) in bits 31-32 and
+// the cell id or sorted particle id in bits 0-30; records past cap are
+// counted, not written.
+struct Rec {
+    long long *buf;
+    long long cap;
+    unsigned long long *cnt;
+    int g;
+};
+
+__device__ __forceinline__ void rec_tile(const Rec &R, int take, int lane,
+                                         int kind, int id)
+{
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(R.cnt, (unsigned long long)take);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (lane < take && base + lane < (unsigned long long)R.cap)
+        R.buf[base + lane] = ((long long)R.g << 33) | ((long long)kind << 31) | id;
+}
+
 template <bool POT>
 struct GroupAcc {
     Acc3 a0, a1;
@@ -354,14 +377,16 @@ __device__ __forceinline__ CellPair cell_pair(const WarpSmem &S, int j)
 
 // One tile of up to 32 accepted cells.  TWO: the lane holds a second
 // particle (slot 32 + lane); groups of at most 32 particles skip it.
-template <bool POT, bool TWO>
+template <bool POT, bool TWO, bool REC>
 __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
                                           int take, const float4 *cf0,
                                           const float4 *cf1, const float4 *cf2,
                                           const IPair &P,
-                                          float eps2, GroupAcc<POT> &A, int lane)
+                                          float eps2, GroupAcc<POT> &A, int lane,
+                                          const Rec &R)
 {
     float v[NCOMP];
+    if (REC) rec_tile(R, take, lane, 0, lane < take ? S.pc[(head + lane) & (RING - 1)] : 0);
     if (lane < take) {
         int c = S.pc[(head + lane) & (RING - 1)];
         float4 a = cf0[c], bb = cf1[c], cc = cf2[c];
@@ -426,13 +451,14 @@ __device__ __forceinline__ PartPair part_pair(const WarpSmem &S, int j)
 
 // One tile of up to 32 particles from a ring of leaf ranges (TWO as for
 // cell_tile).
-template <bool NEAR, bool POT, bool TWO>
+template <bool NEAR, bool POT, bool TWO, bool REC>
 __device__ __forceinline__ void particle_tile(
     WarpSmem &S, int2 *ring, RangeRing &r, int take, const float4 *phi,
     const float4 *plo, const IPair &P, int k0, int k1,
-    const ForceConsts &k, GroupAcc<POT> &A, int lane)
+    const ForceConsts &k, GroupAcc<POT> &A, int lane, const Rec &R)
 {
     const int j = ring_take(ring, r, take, S.tj, lane);
+    if (REC) rec_tile(R, take, lane, NEAR ? 1 : 2, j);
     float4 v;
     if (lane < take) {
         v = rel4(phi[j], plo[j], S.ct);
@@ -491,24 +517,24 @@ __device__ __forceinline__ void particle_tile(
 
 // Evaluates tiles while a ring holds at least `lim` sources: lim = 32 during
 // the walk (full tiles), lim = 1 at its end (the partial tiles left over).
-template <bool POT, bool TWO>
+template <bool POT, bool TWO, bool REC>
 __device__ __forceinline__ void drain(WarpSmem &S, int lim, int &pc_head,
                                       int &pc_n, RangeRing &rf, RangeRing &rn,
                                       const float4 *cf0, const float4 *cf1,
                                       const float4 *cf2, const float4 *phi,
                                       const float4 *plo, const IPair &P,
                                       int k0, int k1, const ForceConsts &kg,
-                                      GroupAcc<POT> &A, int lane)
+                                      GroupAcc<POT> &A, int lane, const Rec &R)
 {
     while (pc_n >= lim)
-        cell_tile<POT, TWO>(S, pc_head, pc_n, min(pc_n, 32), cf0, cf1, cf2, P,
-                            kg.eps2, A, lane);
+        cell_tile<POT, TWO, REC>(S, pc_head, pc_n, min(pc_n, 32), cf0, cf1, cf2,
+                                 P, kg.eps2, A, lane, R);
     while (rf.np >= lim)
-        particle_tile<false, POT, TWO>(S, S.pf, rf, min(rf.np, 32), phi, plo,
-                                       P, k0, k1, kg, A, lane);
+        particle_tile<false, POT, TWO, REC>(S, S.pf, rf, min(rf.np, 32), phi,
+                                            plo, P, k0, k1, kg, A, lane, R);
     while (rn.np >= lim)
-        particle_tile<true, POT, TWO>(S, S.pn, rn, min(rn.np, 32), phi, plo,
-                                      P, k0, k1, kg, A, lane);
+        particle_tile<true, POT, TWO, REC>(S, S.pn, rn, min(rn.np, 32), phi,
+                                           plo, P, k0, k1, kg, A, lane, R);
 }
 
 // Prefetches [ptr, ptr + bytes) into L2, one 128-byte line per request,
@@ -551,7 +577,7 @@ __device__ __forceinline__ int pop_batch(WarpSmem &S, int &top, int &total,
     return c;
 }
 
-template <bool POT>
+template <bool POT, bool REC>
 __global__ void __launch_bounds__(FW * 32, P3T_FORCE_MIN_BLOCKS)
 k_walk_force(const int *__restrict__ gclus,
              const ClusterConsts *__restrict__ ccs,
@@ -565,7 +591,8 @@ k_walk_force(const int *__restrict__ gclus,
              const int *__restrict__ order, int n, ForceConsts k,
              const int *__restrict__ gperm, float *__restrict__ gcost,
              int *__restrict__ pgroup, float *__restrict__ acc,
-             double *__restrict__ pot, P3TDevState *st)
+             double *__restrict__ pot, P3TDevState *st,
+             long long *__restrict__ rec, long long rec_cap, long long lim_walk)
 {
     __shared__ WarpSmem smem[FW];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -596,6 +623,7 @@ k_walk_force(const int *__restrict__ gclus,
         g = __shfl_sync(full, g, 0);
         if (g >= G) break;
         g = gperm[g];
+        const Rec R = {rec, rec_cap, (unsigned long long *)&st->rec_n, g};
         const int2 gr = grange[g];
         const float4 ct = gctr[g];
         __syncwarp();  // the previous group's reads of S are done
@@ -631,8 +659,8 @@ k_walk_force(const int *__restrict__ gclus,
 
         if (lane == 0) S.stack[0] = cl * 8;  // the cluster's root, one cell
         int top = 1;
-        int iter = 0;
-        bool overflow = false;
+        long long iter = 0;
+        bool overflow = false, timeout = false;
         __syncwarp();
         // The walk is software-pipelined by one batch: the next batch is
         // popped and its box records requested before the full tiles are
@@ -647,8 +675,8 @@ k_walk_force(const int *__restrict__ gclus,
             cmx = wmax[c];
         }
         while (total > 0) {
-            if (++iter > (1 << 24)) {  // a finite tree never gets here
-                overflow = true;
+            if (++iter > lim_walk) {  // a finite tree stays far below the default
+                timeout = true;
                 break;
             }
             bool is_pc = false, near = false, farl = false, open = false;
@@ -707,23 +735,23 @@ k_walk_force(const int *__restrict__ gclus,
             }
             // evaluate every full tile
             if (two)
-                drain<POT, true>(S, 32, pc_head, pc_n, rf, rn, cf0, cf1, cf2,
-                                 phi, plo, P, k0, k1, kg, A, lane);
+                drain<POT, true, REC>(S, 32, pc_head, pc_n, rf, rn, cf0, cf1,
+                                      cf2, phi, plo, P, k0, k1, kg, A, lane, R);
             else
-                drain<POT, false>(S, 32, pc_head, pc_n, rf, rn, cf0, cf1, cf2,
-                                  phi, plo, P, k0, k1, kg, A, lane);
+                drain<POT, false, REC>(S, 32, pc_head, pc_n, rf, rn, cf0, cf1,
+                                       cf2, phi, plo, P, k0, k1, kg, A, lane, R);
         }
-        if (overflow) {
-            if (lane == 0) p3t_raise(st, P3T_ERR_CAPACITY);
+        if (overflow || timeout) {
+            if (lane == 0) p3t_raise(st, timeout ? P3T_ERR_TIMEOUT : P3T_ERR_CAPACITY);
             continue;
         }
         // the partial tiles left over
         if (two)
-            drain<POT, true>(S, 1, pc_head, pc_n, rf, rn, cf0, cf1, cf2, phi,
-                             plo, P, k0, k1, kg, A, lane);
+            drain<POT, true, REC>(S, 1, pc_head, pc_n, rf, rn, cf0, cf1, cf2,
+                                  phi, plo, P, k0, k1, kg, A, lane, R);
         else
-            drain<POT, false>(S, 1, pc_head, pc_n, rf, rn, cf0, cf1, cf2, phi,
-                              plo, P, k0, k1, kg, A, lane);
+            drain<POT, false, REC>(S, 1, pc_head, pc_n, rf, rn, cf0, cf1, cf2,
+                                   phi, plo, P, k0, k1, kg, A, lane, R);
         // ---- write back in the caller's order ----
         const float Gc = k.G;
         // work of this group per particle slot of a lane, and the group of
@@ -777,6 +805,7 @@ __global__ void k_force_reset(P3TDevState *st, int n)
         st->cost_groups = st->ngroup;
         st->tot[0] = st->tot[1] = st->tot[2] = 0;
         st->int_pc = st->int_pp = st->int_ppn = 0;
+        st->rec_n = 0;
     }
 }
 
@@ -910,7 +939,8 @@ __global__ void k_sp_soft_bh(int n, int nfs, int nbh, int nblk,
 
 }  // namespace
 
-int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s)
+int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s,
+                  long long *rec, long long rec_cap)
 {
     const int n = (int)c->n;
     k_force_reset<<<1, 32, 0, s>>>(c->st, n);
@@ -922,16 +952,18 @@ int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s)
     p3t_mac_constants(&c->p, &theta2, &hg2);
     int blocks = (int)((G + FW - 1) / FW);
     if (blocks > c->sms * 16) blocks = c->sms * 16;
-    if (pot)
-        k_walk_force<true><<<blocks, FW * 32, 0, s>>>(
-            c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
-            c->wmax, c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
-            c->order, n, k, c->gperm, c->gcost, c->pgroup, acc, pot, c->st);
+#define P3T_FORCE_ARGS                                                         \
+    c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin, c->wmax,   \
+        c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2, c->order, n,  \
+        k, c->gperm, c->gcost, c->pgroup, acc, pot, c->st, rec, rec_cap,   \
+        c->lim_walk
+    if (rec)
+        k_walk_force<false, true><<<blocks, FW * 32, 0, s>>>(P3T_FORCE_ARGS);
+    else if (pot)
+        k_walk_force<true, false><<<blocks, FW * 32, 0, s>>>(P3T_FORCE_ARGS);
     else
-        k_walk_force<false><<<blocks, FW * 32, 0, s>>>(
-            c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
-            c->wmax, c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
-            c->order, n, k, c->gperm, c->gcost, c->pgroup, acc, pot, c->st);
+        k_walk_force<false, false><<<blocks, FW * 32, 0, s>>>(P3T_FORCE_ARGS);
+#undef P3T_FORCE_ARGS
     p3t_count_launches(1);
     if (c->n_bh > 0) {
         const int nbh = (int)c->n_bh, nfs = n - nbh;

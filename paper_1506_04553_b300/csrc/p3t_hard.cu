@@ -52,8 +52,6 @@
 namespace {
 
 constexpr int HB = 256;
-constexpr long long MAX_BLOCK_STEPS = 1LL << 26;  // per component
-constexpr int MAX_UF_ROUNDS = 1 << 20;
 
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
@@ -245,7 +243,8 @@ k_hard_force(int n, const double *__restrict__ x, const double *__restrict__ v,
 
 // ---------------------------------------------------------------- components
 
-__device__ __forceinline__ int uf_find(int *parent, int x, int *rounds)
+__device__ __forceinline__ int uf_find(int *parent, int x, long long *rounds,
+                                       long long lim)
 {
     // path halving; the writes only shorten paths and are benign under races
     for (;;) {
@@ -254,7 +253,7 @@ __device__ __forceinline__ int uf_find(int *parent, int x, int *rounds)
         const int gp = atomicAdd(parent + p, 0);
         if (gp != p) atomicCAS(parent + x, p, gp);
         x = gp;
-        if (++*rounds > MAX_UF_ROUNDS) return -1;
+        if (++*rounds > lim) return -1;
     }
 }
 
@@ -269,16 +268,16 @@ __global__ void __launch_bounds__(HB) k_uf_init(int n, int *parent)
 // index whatever the order of the hooks.
 __global__ void __launch_bounds__(HB)
 k_uf_union(int n, const long long *__restrict__ off, const int *__restrict__ idx,
-           int *parent, P3TDevState *st)
+           int *parent, P3TDevState *st, long long lim)
 {
     for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB) {
         for (long long e = off[i]; e < off[i + 1]; ++e) {
             const int j = idx[e];
             if (j <= i) continue;
-            int rounds = 0;
+            long long rounds = 0;
             for (;;) {
-                int ri = uf_find(parent, i, &rounds);
-                int rj = uf_find(parent, j, &rounds);
+                int ri = uf_find(parent, i, &rounds, lim);
+                int rj = uf_find(parent, j, &rounds, lim);
                 if (ri < 0 || rj < 0) {
                     p3t_raise(st, P3T_ERR_TIMEOUT);
                     return;
@@ -290,7 +289,7 @@ k_uf_union(int n, const long long *__restrict__ off, const int *__restrict__ idx
                     rj = t;
                 }
                 if (atomicCAS(parent + rj, rj, ri) == rj) break;
-                if (++rounds > MAX_UF_ROUNDS) {
+                if (++rounds > lim) {
                     p3t_raise(st, P3T_ERR_TIMEOUT);
                     return;
                 }
@@ -302,11 +301,11 @@ k_uf_union(int n, const long long *__restrict__ off, const int *__restrict__ idx
 // label = root; component sizes counted at the root (non-isolated only).
 __global__ void __launch_bounds__(HB)
 k_uf_label(int n, const long long *__restrict__ off, int *parent,
-           int *__restrict__ csize, P3TDevState *st)
+           int *__restrict__ csize, P3TDevState *st, long long lim)
 {
     for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB) {
-        int rounds = 0;
-        const int r = uf_find(parent, i, &rounds);
+        long long rounds = 0;
+        const int r = uf_find(parent, i, &rounds, lim);
         if (r < 0) {
             p3t_raise(st, P3T_ERR_TIMEOUT);
             continue;
@@ -318,12 +317,12 @@ k_uf_label(int n, const long long *__restrict__ off, int *parent,
 __global__ void __launch_bounds__(HB)
 k_comp_fill(int n, const long long *__restrict__ off, int *parent,
             const long long *__restrict__ cstart, int *__restrict__ cfill,
-            int *__restrict__ member, P3TDevState *st)
+            int *__restrict__ member, P3TDevState *st, long long lim)
 {
     for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB) {
         if (off[i + 1] == off[i]) continue;
-        int rounds = 0;
-        const int r = uf_find(parent, i, &rounds);
+        long long rounds = 0;
+        const int r = uf_find(parent, i, &rounds, lim);
         if (r < 0) {
             p3t_raise(st, P3T_ERR_TIMEOUT);
             continue;
@@ -379,12 +378,13 @@ __device__ __forceinline__ int class_size(int co) { return co == 0 ? 0 : NS - co
 
 __global__ void __launch_bounds__(HB)
 k_comp_level(int n, const long long *__restrict__ off, int *parent,
-             const int *__restrict__ lev, int *__restrict__ clev, P3TDevState *st)
+             const int *__restrict__ lev, int *__restrict__ clev, P3TDevState *st,
+             long long lim)
 {
     for (int i = blockIdx.x * HB + threadIdx.x; i < n; i += gridDim.x * HB) {
         if (off[i + 1] == off[i]) continue;
-        int rounds = 0;
-        const int r = uf_find(parent, i, &rounds);
+        long long rounds = 0;
+        const int r = uf_find(parent, i, &rounds, lim);
         if (r < 0) {
             p3t_raise(st, P3T_ERR_TIMEOUT);
             continue;
@@ -470,6 +470,7 @@ struct HermPar {
     double a0c[2];         // per species: alpha G / r_cut^2, a_0 = a0c m_i
     double c6, c24, c120;  // 1/6, 1/24, 1/120
     long long T;  // dt_soft in ticks
+    long long max_block;  // block steps allowed per component
     int kmax;
 };
 
@@ -659,7 +660,7 @@ __device__ void integrate_warp(int size, long long base, int lane, int n,
                                long long &maxblk)
 {
     for (long long it = 0;; ++it) {
-        if (it >= MAX_BLOCK_STEPS) {
+        if (it >= H.max_block) {
             if (lane == 0) p3t_raise(st, P3T_ERR_TIMEOUT);
             return;
         }
@@ -818,7 +819,7 @@ __device__ void integrate_class(int s, const int *__restrict__ croots, int count
                 maxblk = blk > maxblk ? blk : maxblk;
             }
         }
-        if (__any_sync(full, have && blk >= MAX_BLOCK_STEPS)) {
+        if (__any_sync(full, have && blk >= H.max_block)) {
             if (lane == 0) p3t_raise(st, P3T_ERR_TIMEOUT);
             break;
         }
@@ -1011,17 +1012,18 @@ int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
     H.idt_max = 1.0 / H.dt_max;
     H.T = 1LL << (hp->log2_soft_over_max + hp->kmax);
     H.kmax = hp->kmax;
+    H.max_block = c->lim_block;
     const int g = grid_for(n, c->sms);
     k_herm_reset<<<1, 32, 0, s>>>(c->st);
     k_uf_init<<<g, HB, 0, s>>>(n, c->hparent);
-    k_uf_union<<<g, HB, 0, s>>>(n, off, idx, c->hparent, c->st);
+    k_uf_union<<<g, HB, 0, s>>>(n, off, idx, c->hparent, c->st, c->lim_uf);
     P3T_CUDA_TRY(cudaMemsetAsync(c->hcsize, 0, sizeof(int) * (size_t)n, s));
     P3T_CUDA_TRY(cudaMemsetAsync(c->hcfill, 0, sizeof(int) * (size_t)n, s));
-    k_uf_label<<<g, HB, 0, s>>>(n, off, c->hparent, c->hcsize, c->st);
+    k_uf_label<<<g, HB, 0, s>>>(n, off, c->hparent, c->hcsize, c->st, c->lim_uf);
     int rc = p3t_scan_ll(c, c->hcsize, c->hcstart, n, s);
     if (rc != P3T_OK) return rc;
     k_comp_fill<<<g, HB, 0, s>>>(n, off, c->hparent, c->hcstart, c->hcfill,
-                                 c->hmember, c->st);
+                                 c->hmember, c->st, c->lim_uf);
     k_herm_init<<<g, HB, 0, s>>>(n, pos, vel, mass, off, idx, c->hmember,
                                  c->hcstart + n, H, c->ha, c->hj, c->ht,
                                  c->hlev, c->st);
@@ -1030,7 +1032,8 @@ int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
     P3T_CUDA_TRY(cudaMemsetAsync(c->hcfill, 0, sizeof(int) * (size_t)n, s));
     int *bk = (int *)c->hbucket;
     P3T_CUDA_TRY(cudaMemsetAsync(c->hbucket, 0, sizeof(long long) * P3T_HERM_BUCKET_LL, s));
-    k_comp_level<<<g, HB, 0, s>>>(n, off, c->hparent, c->hlev, c->hcfill, c->st);
+    k_comp_level<<<g, HB, 0, s>>>(n, off, c->hparent, c->hlev, c->hcfill, c->st,
+                                  c->lim_uf);
     k_root_hist<<<g, HB, 0, s>>>(n, c->hparent, c->hcsize, c->hcfill, bk);
     k_root_scan<<<1, 32, 0, s>>>(bk);
     k_root_scatter<<<g, HB, 0, s>>>(n, c->hparent, c->hcsize, c->hcfill, bk,

@@ -67,6 +67,7 @@ struct P3TDevState {
     int cost_n;         // n of the force evaluation that wrote gcost/pgroup
     int cost_groups;    // number of groups of that evaluation
     int pad1;
+    long long rec_n;    // source records written by a recording force walk
     long long herm[7];  // hard step: block steps (summed over components),
                         // particle steps, pair evaluations, steps capped at
                         // the finest level, components, largest component,
@@ -152,6 +153,12 @@ struct p3t_ctx {
     double *ha, *hj, *hxp, *hvp;
     int64_t cap_herm;
     int herm_pad;            // dynamic shared memory of the Hermite kernel
+    // bounds of the kernels' loops and waits (p3t_set_limits)
+    long long lim_walk;      // walk iterations per group
+    long long lim_uf;        // union-find rounds per edge
+    long long lim_block;     // block steps per component
+    int64_t lim_cells;       // cells a build may allocate (0: no bound)
+    int64_t need_cells;      // cells the last build found it needed
     // clusters (one for a plain build)
     int nclus, cap_clus;
     int ensemble;            // layout fixed by p3t_set_ensemble or p3t_set_species
@@ -287,7 +294,11 @@ void p3t_cluster_consts(const p3t_params *p, double r_out, double eps,
                         double h, ClusterConsts *out);          // p3t_api.cu
 int p3t_run_walk(p3t_ctx *c, int fill, cudaStream_t s);        // p3t_walk.cu
 int p3t_scan_lists(p3t_ctx *c, cudaStream_t s);                 // p3t_walk.cu
-int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s);   // p3t_force.cu
+constexpr long long P3T_LIM_WALK = 1LL << 24;   // default p3t_limits
+constexpr long long P3T_LIM_UF = 1LL << 20;
+constexpr long long P3T_LIM_BLOCK = 1LL << 26;
+int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s,
+                  long long *rec = nullptr, long long rec_cap = 0);   // p3t_force.cu
 int p3t_run_ngb_species(p3t_ctx *c, long long *offsets, int *idx, long long cap,
                         long long *needed, cudaStream_t s);
 int p3t_run_ngb(p3t_ctx *c, int fill, const long long *row_off, int *idx,

@@ -113,7 +113,8 @@ k_ngb_walk(const int *__restrict__ gclus,
            const double *__restrict__ xs, int n,
            int *__restrict__ cnt, const long long *__restrict__ row_off,
            int *__restrict__ idx, long long cap, const int *__restrict__ gperm,
-           int *__restrict__ slots, int *__restrict__ ovf, P3TDevState *st)
+           int *__restrict__ slots, int *__restrict__ ovf, P3TDevState *st,
+           long long lim_walk)
 {
     __shared__ NgbSmem smem[NW];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -162,8 +163,9 @@ k_ngb_walk(const int *__restrict__ gclus,
         int *s0 = slots + (size_t)o0 * SL, *s1 = slots + (size_t)o1 * SL;
         int head = 0, nr = 0, np = 0;  // ring of near leaf ranges
         if (lane == 0) S.stack[0] = cl * 8;  // the cluster's root
-        int top = 1, iter = 0;
-        bool bad = false;
+        int top = 1;
+        long long iter = 0;
+        bool bad = false, timeout = false;
         __syncwarp();
         for (;;) {
             // drain full tiles (and everything once the walk is done)
@@ -207,8 +209,8 @@ k_ngb_walk(const int *__restrict__ gclus,
                 __syncwarp();
             }
             if (top == 0) break;
-            if (++iter > (1 << 24)) {
-                bad = true;
+            if (++iter > lim_walk) {  // a finite tree stays far below the default
+                timeout = true;
                 break;
             }
             int rx = 0, ry = 0;
@@ -266,8 +268,8 @@ k_ngb_walk(const int *__restrict__ gclus,
             }
             __syncwarp();
         }
-        if (bad) {
-            if (lane == 0) p3t_raise(st, P3T_ERR_CAPACITY);
+        if (bad || timeout) {
+            if (lane == 0) p3t_raise(st, timeout ? P3T_ERR_TIMEOUT : P3T_ERR_CAPACITY);
             continue;
         }
         if (!FILL) {
@@ -492,14 +494,16 @@ int p3t_run_ngb(p3t_ctx *c, int fill, const long long *row_off, int *idx,
         k_ngb_walk<true><<<blocks, NW * 32, 0, s>>>(
             c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
             c->wmax, c->node, c->phi, c->plo, c->order, c->xs, n, c->ngb_cnt,
-            row_off, idx, cap, c->gperm, c->ngb_slots, c->ngb_ovf, c->st);
+            row_off, idx, cap, c->gperm, c->ngb_slots, c->ngb_ovf, c->st,
+            c->lim_walk);
         k_ngb_sort<<<nb, 256, 0, s>>>(n, row_off, idx, cap);
         p3t_count_launches(4);
     } else {
         k_ngb_walk<false><<<blocks, NW * 32, 0, s>>>(
             c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
             c->wmax, c->node, c->phi, c->plo, c->order, c->xs, n, c->ngb_cnt,
-            row_off, idx, cap, c->gperm, c->ngb_slots, c->ngb_ovf, c->st);
+            row_off, idx, cap, c->gperm, c->ngb_slots, c->ngb_ovf, c->st,
+            c->lim_walk);
         p3t_count_launches(2);
     }
     P3T_CUDA_TRY(cudaGetLastError());

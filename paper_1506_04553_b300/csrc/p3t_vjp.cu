@@ -446,7 +446,7 @@ k_walk_vjp(const int *__restrict__ gclus,
            const int *__restrict__ order, int n, VjpConsts k,
            const float *__restrict__ w, double *__restrict__ gpos,
            double *__restrict__ gmass, double *__restrict__ cadj,
-           const int *__restrict__ gperm, P3TDevState *st)
+           const int *__restrict__ gperm, P3TDevState *st, long long lim_walk)
 {
     __shared__ Smem smem[VW];
     __shared__ VjpSmem vsm[VW];
@@ -500,9 +500,11 @@ k_walk_vjp(const int *__restrict__ gclus,
         ev.k.kA = cc.kA;
         ev.k.kB = cc.kB;
         long long cnt[3] = {0, 0, 0};
-        if (!p3t_walk::walk_group(S, gmin[g], gmax[g], wmin, wmax, theta2,
-                                  cc.hg2, cl, lane, ev, cnt)) {
-            if (lane == 0) p3t_raise(st, P3T_ERR_CAPACITY);
+        const int wst = p3t_walk::walk_group(S, gmin[g], gmax[g], wmin, wmax,
+                                             theta2, cc.hg2, cl, lane, ev, cnt,
+                                             lim_walk);
+        if (wst != P3T_OK) {
+            if (lane == 0) p3t_raise(st, wst);
             continue;
         }
         // dL/dx_i = -G sum J w over the particle's sources
@@ -640,7 +642,7 @@ int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,
         c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
         c->wmax, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
         c->order, n, k, w,
-        gpos, gmass, cadj, c->gperm, c->st);
+        gpos, gmass, cadj, c->gperm, c->st, c->lim_walk);
     p3t_prof_close(c, slot, s);
     k_vjp_prep<<<c->sms * 8, 256, 0, s>>>(c->st, c->cM, cadj);
     k_vjp_leaves<<<c->sms * 8, 256, 0, s>>>(c->st, n, c->leaf_sorted, c->node,

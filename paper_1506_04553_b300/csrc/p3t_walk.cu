@@ -40,7 +40,7 @@ k_walk(int ngroup, const int *__restrict__ gclus,
        const int4 *__restrict__ node, float theta2,
        long long *__restrict__ cnt, const long long *__restrict__ off,
        int *__restrict__ pc_list, int *__restrict__ ppn_list,
-       int *__restrict__ ppf_list, P3TDevState *st)
+       int *__restrict__ ppf_list, P3TDevState *st, long long lim_walk)
 {
     __shared__ int2 stack[WALK_WARPS][WALK_STACK];
     __shared__ int buf[WALK_WARPS][32];
@@ -62,12 +62,12 @@ k_walk(int ngroup, const int *__restrict__ gclus,
         }
         if (lane == 0) stk[0] = make_int2(cl, 1);  // the cluster's root
         int top = 1;
-        bool overflow = false;
-        int iter = 0;
+        bool overflow = false, timeout = false;
+        long long iter = 0;
         __syncwarp();
         while (top > 0) {
-            if (++iter > (1 << 24)) {  // a finite tree never gets here
-                overflow = true;
+            if (++iter > lim_walk) {  // a finite tree stays far below the default
+                timeout = true;
                 break;
             }
             // pop child ranges from the top holding at most 32 cells
@@ -142,8 +142,8 @@ k_walk(int ngroup, const int *__restrict__ gclus,
             if (lane == 0) atomicMax(&st->max_stack, top);
             __syncwarp();
         }
-        if (overflow) {
-            if (lane == 0) p3t_raise(st, P3T_ERR_CAPACITY);
+        if (overflow || timeout) {
+            if (lane == 0) p3t_raise(st, timeout ? P3T_ERR_TIMEOUT : P3T_ERR_CAPACITY);
             npc = nppn = nppf = 0;
         }
         if (!FILL && lane == 0) {
@@ -240,12 +240,12 @@ int p3t_run_walk(p3t_ctx *c, int fill, cudaStream_t s)
         k_walk<true><<<blocks, WALK_WARPS * 32, 0, s>>>(
             G, c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->wmin, c->wmax,
             c->node, theta2, c->lcnt, c->loff, c->list[0], c->list[1],
-            c->list[2], c->st);
+            c->list[2], c->st, c->lim_walk);
     else
         k_walk<false><<<blocks, WALK_WARPS * 32, 0, s>>>(
             G, c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->wmin, c->wmax,
             c->node, theta2, c->lcnt, c->loff, c->list[0], c->list[1],
-            c->list[2], c->st);
+            c->list[2], c->st, c->lim_walk);
     p3t_count_launches(1);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;

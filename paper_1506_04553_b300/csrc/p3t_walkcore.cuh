@@ -129,7 +129,8 @@ __device__ __forceinline__ int pop_batch(Smem &S, int &top, int &total,
 // evaluator supplies
 //   ev.cells(S, take)            tile of `take` cells, ids in S.tj
 //   ev.particles<NEAR>(S, take)  tile of `take` particles, ids in S.tj
-// Returns false when the stack overflowed (the group is left unfinished).
+// Returns P3T_OK, P3T_ERR_CAPACITY when the stack overflowed or
+// P3T_ERR_TIMEOUT after lim iterations (the group is left unfinished).
 // cnt[0..2] receive the numbers of cells, near and far particles met.  The
 // walk is software-pipelined by one batch: the next batch is popped and its
 // box records requested before the full tiles are evaluated (the batches and
@@ -137,17 +138,17 @@ __device__ __forceinline__ int pop_batch(Smem &S, int &top, int &total,
 // A leaf's box records carry its particle range (first particle in
 // wmin.w, minus the count in wmax.w), so no second load is needed.
 template <class Ev>
-__device__ __forceinline__ bool walk_group(
+__device__ __forceinline__ int walk_group(
     Smem &S, float4 gmn, float4 gmx, const float4 *__restrict__ wmin,
     const float4 *__restrict__ wmax, float theta2, float hg2, int root,
-    int lane, Ev &ev, long long cnt[3])
+    int lane, Ev &ev, long long cnt[3], long long lim)
 {
     const unsigned full = 0xffffffffu, lt = lanemask_lt();
     CellRing rc = {0, 0};
     RangeRing rf = {0, 0, 0}, rn = {0, 0, 0};
     if (lane == 0) S.stack[0] = root * 8;  // the group's root, one cell
     int top = 1;
-    int iter = 0;
+    long long iter = 0;
     __syncwarp();
     int total = 0;
     int c = pop_batch(S, top, total, lane);
@@ -157,7 +158,7 @@ __device__ __forceinline__ bool walk_group(
         cmx = wmax[c];
     }
     while (total > 0) {
-        if (++iter > (1 << 24)) return false;  // a finite tree never gets here
+        if (++iter > lim) return P3T_ERR_TIMEOUT;  // a finite tree stays far below
         bool is_pc = false, near = false, farl = false, open = false;
         int child = 0, nchild = 0, pfirst = 0, pcount = 0;
         if (c >= 0) {
@@ -195,7 +196,7 @@ __device__ __forceinline__ bool walk_group(
         {
             unsigned mo = __ballot_sync(full, open);
             int np = __popc(mo);
-            if (top + np > STACK) return false;
+            if (top + np > STACK) return P3T_ERR_CAPACITY;
             if (open) S.stack[top + __popc(mo & lt)] = child * 8 + (nchild - 1);
             top += np;
         }
@@ -233,7 +234,7 @@ __device__ __forceinline__ bool walk_group(
         take_particles(S.pn, rn, t, S.tj, lane);
         ev.template particles<true>(S, t);
     }
-    return true;
+    return P3T_OK;
 }
 
 }  // namespace p3t_walk

@@ -69,6 +69,25 @@ def test_lists_identical(case):
     assert st["list_pp_far"] == L["ppf"].size
 
 
+def test_fused_kernel_lists_identical(case):
+    """The sources the timed walk + force kernel itself evaluates (recorded by
+    an instantiation of the same kernel) are, group by group, the oracle's
+    interaction lists: cells, near-leaf and far-leaf particles."""
+    ctx, tree = case["ctx"], case["tree"]
+    og, gid = compare_structure(ctx, tree)
+    F, Lo = ctx.force_lists(), tree.lists()
+    for g in range(tree.ngroup):
+        q = gid[g]
+        pc_o = og[Lo["pc"][Lo["pc_off"][g]:Lo["pc_off"][g + 1]]]
+        pc_g = F["pc"][F["pc_off"][q]:F["pc_off"][q + 1]]
+        assert sorted(pc_o.tolist()) == pc_g.tolist(), f"cells of group {g}"
+        for name in ("ppn", "ppf"):
+            lo_ = Lo[name][Lo[name + "_off"][g]:Lo[name + "_off"][g + 1]]
+            lg_ = F[name][F[name + "_off"][q]:F[name + "_off"][q + 1]]
+            assert sorted(lo_.tolist()) == lg_.tolist(), f"{name} of group {g}"
+    assert F["pc"].size == Lo["pc"].size and F["ppf"].size == Lo["ppf"].size
+
+
 def test_force_matches_same_tree_oracle(case):
     p = case["p"]
     a_o, p_o = case["tree"].force(G=p.G, eps=p.eps, r_cut=p.r_out,
