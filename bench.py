@@ -55,7 +55,7 @@ B_BUILD_PER_PARTICLE = 32 + 12 + 8 * 24 + 64
 B_BUILD_PER_CELL = 228
 B_KICK = 60
 B_DRIFT = 72
-FLOPS_PC = 49
+FLOPS_PC = 48
 FLOPS_PP_FAR = 18
 FLOPS_PP_NEAR = 31
 # FP32 flops per interaction of the backward kernel (FMA = 2), fixed from its
@@ -1319,10 +1319,11 @@ def run_ensemble(args, dev, sample=False):
     ctx.set_ensemble(off, r_out=r_out, eps=eps)
     pos = torch.tensor(pos_h, device=dev)
     mass = torch.tensor(m_h, device=dev)
-    ng, nl, tune_ms = ctx.autotune(pos, mass, reps=2)
-    acc = torch.empty((3, n), dtype=torch.float32, device=dev)
     w = torch.randn((3, n), dtype=torch.float32, device=dev,
                     generator=torch.Generator(device=dev).manual_seed(41))
+    tune = ctx.autotune(pos, mass, w=w, reps=2)
+    ng, nl = tune["n_group"], tune["n_leaf"]
+    acc = torch.empty((3, n), dtype=torch.float32, device=dev)
     gx = torch.empty((3, n), dtype=torch.float64, device=dev)
     gm = torch.empty((n,), dtype=torch.float64, device=dev)
     ctx.build_tree(pos, mass)
@@ -1362,8 +1363,22 @@ def run_ensemble(args, dev, sample=False):
            "n": n, "clusters": 256, "step": "build + force + backward, "
            "one CUDA graph, one walk+force launch for all clusters",
            "value": n / (ms * 1e-3), "unit": "particles/s (fwd+bwd)",
-           "ms_per_step": ms, "autotuned": {"n_group": ng, "n_leaf": nl,
-                                            "build_force_ms": tune_ms}}
+           "ms_per_step": ms,
+           "autotuned": {"n_group": ng, "n_leaf": nl,
+                         "force_warps": tune["force_warps"],
+                         "vjp_warps": tune["vjp_warps"],
+                         "objective": "build + force + backward (ms, best of 2)",
+                         "ms": tune["ms"],
+                         "err_median": tune["err_median"],
+                         "err_max": tune["err_max"],
+                         "start_err_median": tune["base_err_median"],
+                         "start_err_max": tune["base_err_max"],
+                         "evaluated": tune["evaluated"],
+                         "rejected_by_accuracy": tune["rejected"],
+                         "note": "error: |a - a_ref| / max(|a_ref|, 1e-3 rms) "
+                                 "against the starting configuration at "
+                                 "theta / 2; kept if median <= 1.25x and "
+                                 "max <= 2x the starting configuration's"}}
     if not sample:
         return res, None
     # eight clusters spanning the sizes (smallest and largest included)

@@ -155,17 +155,45 @@ typedef struct p3t_species {
 int p3t_set_species(p3t_ctx *ctx, int64_t n, int64_t n_bh,
                     const p3t_species *sp);
 
-/* Autotuner: times p3t_build_tree + p3t_long_force (best of `reps`) for
- * n_group in {32, 48, 64} and n_leaf in {8, 16, 32} on the given particles
- * and keeps the fastest pair in the context's parameters (the tree is left
- * built with it).  The pair changes which cells are opened, not the
- * accuracy target: every pair satisfies the same opening test.
- *   acc : device float[3][n] scratch.
- * Must not be called with P3T_FLAG_NO_SYNC set (it synchronises).
- * Errors: P3T_ERR_INVALID, P3T_ERR_STATE, and those of the timed calls. */
+/* Autotuner (a service of the library; the paper has none).  Chooses the
+ * group size and leaf size (n_group in {32, 48, 64} x n_leaf in {8, 16, 32})
+ * and then the block shape of the walk kernels (warps per block of the
+ * walk + force kernel in {2, 4, 8} and, with weights, of the backward kernel
+ * in {2, 4}) by timing, on the given particles, the step the workload runs:
+ * p3t_build_tree + p3t_long_force, plus p3t_long_force_vjp with the weights
+ * w when w is not NULL (device float[3][n]); each configuration the best of
+ * `reps` runs after one untimed run.
+ * Accuracy check: the reference is the force of the starting configuration
+ * at half the opening angle theta / 2 (its tree error is several times
+ * smaller).  A (n_group, n_leaf) candidate is kept only if the median and
+ * the maximum over particles of |a - a_ref| / max(|a_ref|, 1e-3 rms|a_ref|)
+ * are at most P3T_TUNE_MEDIAN_FACTOR and P3T_TUNE_MAX_FACTOR times those of
+ * the starting configuration (which is always kept); the block shape changes
+ * no arithmetic.  The fastest kept configuration goes into the context (its
+ * n_group and n_leaf into the parameters) and the tree is left built with it.
+ * Allocates and frees its scratch (3 n floats for the reference and the
+ * candidates' forces, 4 n doubles of gradients with w) and synchronises:
+ * must not be called with P3T_FLAG_NO_SYNC.
+ * Errors: P3T_ERR_INVALID, P3T_ERR_STATE (NO_SYNC; w with species), and
+ * those of the timed calls (the context's parameters are then restored). */
+#define P3T_TUNE_MEDIAN_FACTOR 1.25
+#define P3T_TUNE_MAX_FACTOR 2.0
+typedef struct p3t_tune {
+    int32_t n_group, n_leaf;   /* chosen sizes */
+    int32_t force_warps;       /* chosen warps per block, walk + force */
+    int32_t vjp_warps;         /* chosen warps per block, backward */
+    double ms;                 /* the chosen configuration's time (ms) */
+    double err_median, err_max;          /* its error against the reference */
+    double base_err_median, base_err_max; /* the starting configuration's */
+    int32_t evaluated;         /* configurations timed */
+    int32_t rejected;          /* (n_group, n_leaf) pairs failing the check */
+    double cand_ms[9];         /* per pair (n_group index x 3 + n_leaf index) */
+    double cand_err_median[9];
+    double cand_err_max[9];
+} p3t_tune;
 int p3t_autotune(p3t_ctx *ctx, int64_t n, const double *pos,
-                 const double *mass, float *acc, int reps, void *stream,
-                 int32_t *best_n_group, int32_t *best_n_leaf, double *best_ms);
+                 const double *mass, const float *w, int reps, void *stream,
+                 p3t_tune *out);
 
 /* Long-range acceleration a_soft (Eq. 8) of every particle by the tree.
  *   acc : device, float[3][n] (SoA), written in the caller's order

@@ -72,6 +72,17 @@ class _CHermite(C.Structure):
                 ("kmax", C.c_int32)]
 
 
+class _CTune(C.Structure):
+    _fields_ = [("n_group", C.c_int32), ("n_leaf", C.c_int32),
+                ("force_warps", C.c_int32), ("vjp_warps", C.c_int32),
+                ("ms", C.c_double), ("err_median", C.c_double),
+                ("err_max", C.c_double), ("base_err_median", C.c_double),
+                ("base_err_max", C.c_double), ("evaluated", C.c_int32),
+                ("rejected", C.c_int32), ("cand_ms", C.c_double * 9),
+                ("cand_err_median", C.c_double * 9),
+                ("cand_err_max", C.c_double * 9)]
+
+
 class _CProfile(C.Structure):
     _fields_ = [("build_ms", C.c_double), ("walk_ms", C.c_double),
                 ("force_ms", C.c_double), ("ngb_ms", C.c_double),
@@ -109,7 +120,7 @@ _sigs = {
     "p3t_long_force_vjp": [_vp, _vp, _vp, _vp, _vp],
     "p3t_set_ensemble": [_vp, C.c_int32, _vp, _vp, _vp, _vp],
     "p3t_set_species": [_vp, C.c_int64, C.c_int64, _vp],
-    "p3t_autotune": [_vp, _i64, _vp, _vp, _vp, C.c_int, _vp, _vp, _vp, _vp],
+    "p3t_autotune": [_vp, _i64, _vp, _vp, _vp, C.c_int, _vp, _vp],
     "p3t_get_profile": [_vp, _vp, C.c_int],
     "p3t_alu_peaks": [_vp, _vp, _vp],
     "p3t_fp64_peaks": [_vp, _vp, _vp, _vp],
@@ -253,22 +264,29 @@ class Context:
                                     C.byref(sp) if n_bh else None),
                "p3t_set_species")
 
-    def autotune(self, pos, mass, reps=2, stream=None):
-        """Time build + force for n_group in {32, 48, 64} x n_leaf in
-        {8, 16, 32}; keep the fastest (returns (n_group, n_leaf, ms))."""
+    def autotune(self, pos, mass, w=None, reps=2, stream=None) -> dict:
+        """p3t_autotune: n_group x n_leaf, then the walk kernels' warps per
+        block, timed on build + force (+ backward with weights w, (3, n)
+        float32), keeping only sizes whose force stays within the accuracy
+        check against the theta/2 reference.  Returns the p3t_tune record as
+        a dict; the context keeps the chosen configuration."""
         import torch
         n = int(mass.shape[0])
-        acc = torch.empty((3, n), dtype=torch.float32, device="cuda")
-        bg, bl, bm = C.c_int32(0), C.c_int32(0), C.c_double(0.0)
+        t = _CTune()
+        wp = _dptr(w, torch.float32, (3, n), "w") if w is not None else None
         _check(_lib.p3t_autotune(
             self._h, n, _dptr(pos, torch.float64, (3, n), "pos"),
-            _dptr(mass, torch.float64, (n,), "mass"), C.c_void_p(acc.data_ptr()),
-            reps, _stream(stream), C.byref(bg), C.byref(bl), C.byref(bm)),
-            "p3t_autotune")
-        self.params.n_group, self.params.n_leaf = int(bg.value), int(bl.value)
+            _dptr(mass, torch.float64, (n,), "mass"), wp, reps, _stream(stream),
+            C.byref(t)), "p3t_autotune")
+        self.params.n_group, self.params.n_leaf = int(t.n_group), int(t.n_leaf)
         self.n = n
         self.build_id = getattr(self, "build_id", 0) + 1
-        return int(bg.value), int(bl.value), float(bm.value)
+        out = {}
+        for f, ty in _CTune._fields_:
+            v = getattr(t, f)
+            out[f] = [float(x) for x in v] if f.startswith("cand_") else (
+                float(v) if ty is C.c_double else int(v))
+        return out
 
     # ---- hot path ----
     def build_tree(self, pos, mass, stream=None):

@@ -956,56 +956,151 @@ const char *p3t_status_string(int s)
 }  // extern "C"
 
 // ---- autotuning of the group and leaf sizes --------------------------------
-extern "C" int p3t_autotune(p3t_ctx *c, int64_t n, const double *pos,
-                            const double *mass, float *acc, int reps,
-                            void *stream, int32_t *best_n_group,
-                            int32_t *best_n_leaf, double *best_ms)
+// One timed configuration of the autotuner: the best of `reps` runs of
+// build + force (+ backward with weights w), after one untimed run that
+// sizes every buffer.
+static int tune_time(p3t_ctx *c, int64_t n, const double *pos,
+                     const double *mass, const float *w, float *acc,
+                     double *gpos, double *gmass, int reps, void *stream,
+                     cudaEvent_t e0, cudaEvent_t e1, double *ms)
 {
-    if (!c || n <= 0 || !pos || !mass || !acc || reps < 1) return P3T_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    *ms = 1e300;
+    for (int r = -1; r < reps; ++r) {
+        if (r >= 0) cudaEventRecord(e0, s);
+        P3T_TRY(p3t_build_tree(c, n, pos, mass, stream));
+        P3T_TRY(p3t_long_force(c, acc, nullptr, stream));
+        if (w) P3T_TRY(p3t_long_force_vjp(c, w, gpos, gmass, stream));
+        if (r < 0) {
+            P3T_TRY(p3t_check(c, stream));
+            continue;
+        }
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return P3T_ERR_CUDA;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (t < *ms) *ms = t;
+    }
+    return p3t_check(c, stream);
+}
+
+extern "C" int p3t_autotune(p3t_ctx *c, int64_t n, const double *pos,
+                            const double *mass, const float *w, int reps,
+                            void *stream, p3t_tune *out)
+{
+    if (!c || n <= 0 || !pos || !mass || reps < 1 || !out) return P3T_ERR_INVALID;
     if (c->p.flags & P3T_FLAG_NO_SYNC) return P3T_ERR_STATE;
+    if (w && c->n_bh > 0) return P3T_ERR_STATE;  // no backward with species
     cudaStream_t s = (cudaStream_t)stream;
     static const int groups[] = {32, 48, 64};
     static const int leaves[] = {8, 16, 32};
+    static const int fwarps[] = {2, 4, 8};
+    static const int vwarps[] = {2, 4};
     const p3t_params keep = c->p;
-    cudaEvent_t e0, e1;
-    P3T_CUDA_TRY(cudaEventCreate(&e0));
-    P3T_CUDA_TRY(cudaEventCreate(&e1));
-    double best = 1e300;
-    int bg = keep.n_group, bl = keep.n_leaf;
+    const int keep_fw = c->force_warps, keep_vw = c->vjp_warps;
+    memset(out, 0, sizeof(*out));
+    float *acc = nullptr, *ref = nullptr;
+    double *gpos = nullptr, *gmass = nullptr;
+    void *scr = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = P3T_OK;
+    if (cudaMalloc(&acc, sizeof(float) * 3 * n) != cudaSuccess ||
+        cudaMalloc(&ref, sizeof(float) * 3 * n) != cudaSuccess ||
+        (w && cudaMalloc(&gpos, sizeof(double) * 3 * n) != cudaSuccess) ||
+        (w && cudaMalloc(&gmass, sizeof(double) * n) != cudaSuccess) ||
+        cudaMalloc(&scr, p3t_force_err_scratch(c)) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        rc = P3T_ERR_CUDA;
+    // reference: the starting configuration at half the opening angle
+    if (rc == P3T_OK) {
+        c->p.theta = 0.5 * keep.theta;
+        rc = p3t_build_tree(c, n, pos, mass, stream);
+        if (rc == P3T_OK) rc = p3t_long_force(c, ref, nullptr, stream);
+        if (rc == P3T_OK) rc = p3t_check(c, stream);
+        c->p = keep;
+    }
+    double base_med = 0.0, base_max = 0.0, best = 1e300;
+    int bg = keep.n_group, bl = keep.n_leaf;
+    double best_med = 0.0, best_max = 0.0;
     for (int gi = 0; gi < 3 && rc == P3T_OK; ++gi)
         for (int li = 0; li < 3 && rc == P3T_OK; ++li) {
             c->p.n_group = groups[gi];
             c->p.n_leaf = leaves[li];
-            // one untimed evaluation sizes every buffer
-            rc = p3t_build_tree(c, n, pos, mass, stream);
-            if (rc == P3T_OK) rc = p3t_long_force(c, acc, nullptr, stream);
+            double t = 0.0, med = 0.0, mx = 0.0;
+            rc = tune_time(c, n, pos, mass, w, acc, gpos, gmass, reps, stream, e0,
+                           e1, &t);
+            if (rc == P3T_OK) rc = p3t_force_err(c, n, acc, ref, scr, &med, &mx, s);
             if (rc != P3T_OK) break;
-            double t = 1e300;
-            for (int r = 0; r < reps && rc == P3T_OK; ++r) {
-                cudaEventRecord(e0, s);
-                rc = p3t_build_tree(c, n, pos, mass, stream);
-                if (rc == P3T_OK) rc = p3t_long_force(c, acc, nullptr, stream);
-                cudaEventRecord(e1, s);
-                if (cudaEventSynchronize(e1) != cudaSuccess) rc = P3T_ERR_CUDA;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < t) t = ms;
+            ++out->evaluated;
+            if (groups[gi] == keep.n_group && leaves[li] == keep.n_leaf) {
+                base_med = med;
+                base_max = mx;
             }
-            if (rc == P3T_OK && t < best) {
-                best = t;
-                bg = groups[gi];
-                bl = leaves[li];
-            }
+            out->cand_ms[gi * 3 + li] = t;
+            out->cand_err_median[gi * 3 + li] = med;
+            out->cand_err_max[gi * 3 + li] = mx;
         }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    // the accuracy check: no worse than the starting configuration by more
+    // than the stated factors (the starting configuration always passes)
+    for (int q = 0; q < 9 && rc == P3T_OK; ++q) {
+        const bool start = groups[q / 3] == keep.n_group && leaves[q % 3] == keep.n_leaf;
+        const bool ok = start || (out->cand_err_median[q] <= P3T_TUNE_MEDIAN_FACTOR * base_med &&
+                                  out->cand_err_max[q] <= P3T_TUNE_MAX_FACTOR * base_max);
+        if (!ok) {
+            ++out->rejected;
+            continue;
+        }
+        if (out->cand_ms[q] < best) {
+            best = out->cand_ms[q];
+            bg = groups[q / 3];
+            bl = leaves[q % 3];
+            best_med = out->cand_err_median[q];
+            best_max = out->cand_err_max[q];
+        }
+    }
+    // block shapes of the walk kernels for the chosen sizes (they change no
+    // arithmetic, so no accuracy check)
+    int bfw = keep_fw ? keep_fw : 4, bvw = keep_vw ? keep_vw : 4;
     c->p = keep;
     c->p.n_group = bg;
     c->p.n_leaf = bl;
-    if (rc == P3T_OK) rc = p3t_build_tree(c, n, pos, mass, stream);
-    if (best_n_group) *best_n_group = bg;
-    if (best_n_leaf) *best_n_leaf = bl;
-    if (best_ms) *best_ms = best;
+    for (int fi = 0; fi < 3 && rc == P3T_OK; ++fi)
+        for (int vi = 0; vi < (w ? 2 : 1) && rc == P3T_OK; ++vi) {
+            c->force_warps = fwarps[fi];
+            c->vjp_warps = w ? vwarps[vi] : bvw;
+            double t = 0.0;
+            rc = tune_time(c, n, pos, mass, w, acc, gpos, gmass, reps, stream, e0,
+                           e1, &t);
+            if (rc != P3T_OK) break;
+            ++out->evaluated;
+            if (t < best) {
+                best = t;
+                bfw = c->force_warps;
+                bvw = c->vjp_warps;
+            }
+        }
+    c->force_warps = rc == P3T_OK ? bfw : keep_fw;
+    c->vjp_warps = rc == P3T_OK ? bvw : keep_vw;
+    if (rc != P3T_OK) {
+        c->p = keep;
+    } else {
+        out->n_group = bg;
+        out->n_leaf = bl;
+        out->force_warps = bfw;
+        out->vjp_warps = bvw;
+        out->ms = best;
+        out->err_median = best_med;
+        out->err_max = best_max;
+        out->base_err_median = base_med;
+        out->base_err_max = base_max;
+        rc = p3t_build_tree(c, n, pos, mass, stream);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(acc);
+    cudaFree(ref);
+    cudaFree(gpos);
+    cudaFree(gmass);
+    cudaFree(scr);
     return rc;
 }

@@ -31,7 +31,8 @@
 
 namespace {
 
-constexpr int FW = 4;  // warps (groups in flight) per block
+// Warps (groups in flight) per block of the walk + force kernel: a template
+// parameter (2, 4 or 8), chosen per context by the autotuner; 4 by default.
 
 #ifndef P3T_PC_UNROLL
 #define P3T_PC_UNROLL 4
@@ -103,8 +104,10 @@ __device__ __forceinline__ f2 rsqrt2(f2 a) { return make_float2(rsqrt_ftz(a.x), 
 // centre, mass and the negated traceless quadrupole Q' = -Q.  With Q',
 // q' = Q' d = -Q d and (d.Q'.d) = -(d.Q.d), so
 //   a = M d/s^3 - Q d/s^5 + (5/2)(d.Q.d) d/s^7
-//     = [(-5/2) (d.Q'.d) / s^7 + M / s^3] d + q' / s^5
-// needs no sign flips.  (nx, ny, nz) = minus the particle's coordinates.
+//     = [M / s^3 - (5/2) (d.Q'.d) / s^7] d + q' / s^5
+//     = (1 / s^5) (b d + q'),   b = M s^2 - (5/2) (d.Q'.d) / s^2,
+// which needs no sign flips and no 1/s^7: 30 FP32x2 instructions per pair of
+// cells.  (nx, ny, nz) = minus the particle's coordinates.
 struct CellPair {
     f2 X, Y, Z, M, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz;
 };
@@ -122,16 +125,11 @@ __device__ __forceinline__ void pc_term2(f2 nx, f2 ny, f2 nz,
     const f2 qy = fma2(c.Qxy, dx, fma2(c.Qyy, dy, mul2(c.Qyz, dz)));
     const f2 qz = fma2(c.Qxz, dx, fma2(c.Qyz, dy, mul2(c.Qzz, dz)));
     const f2 dqd = fma2(dx, qx, fma2(dy, qy, mul2(dz, qz)));
-    const f2 ri3 = mul2(ri, ri2);
-    const f2 ri5 = mul2(ri3, ri2);
-    const f2 ri7 = mul2(ri5, ri2);
-    const f2 a = fma2(mul2(dup2(-2.5f), dqd), ri7, mul2(c.M, ri3));
-    ax = fma2(a, dx, ax);
-    ay = fma2(a, dy, ay);
-    az = fma2(a, dz, az);
-    ax = fma2(ri5, qx, ax);
-    ay = fma2(ri5, qy, ay);
-    az = fma2(ri5, qz, az);
+    const f2 ri5 = mul2(mul2(ri, ri2), ri2);
+    const f2 b = fma2(mul2(dup2(-2.5f), dqd), ri2, mul2(c.M, s2));
+    ax = fma2(ri5, fma2(b, dx, qx), ax);
+    ay = fma2(ri5, fma2(b, dy, qy), ay);
+    az = fma2(ri5, fma2(b, dz, qz), az);
     if (POT)  // phi = -(M/s + (1/2)(d.Q.d)/s^5), summed with its sign flipped
         pp = add2(pp, fma2(mul2(dup2(-0.5f), dqd), ri5, mul2(c.M, ri)));
 }
@@ -577,7 +575,7 @@ __device__ __forceinline__ int pop_batch(WarpSmem &S, int &top, int &total,
     return c;
 }
 
-template <bool POT, bool REC>
+template <bool POT, bool REC, int FW>
 __global__ void __launch_bounds__(FW * 32, P3T_FORCE_MIN_BLOCKS)
 k_walk_force(const int *__restrict__ gclus,
              const ClusterConsts *__restrict__ ccs,
@@ -950,19 +948,30 @@ int p3t_run_force(p3t_ctx *c, float *acc, double *pot, cudaStream_t s,
     ForceConsts k = make_consts(c->p);
     float theta2, hg2;
     p3t_mac_constants(&c->p, &theta2, &hg2);
-    int blocks = (int)((G + FW - 1) / FW);
-    if (blocks > c->sms * 16) blocks = c->sms * 16;
+    const int fw = c->force_warps == 2 || c->force_warps == 8 ? c->force_warps : 4;
+    int blocks = (int)((G + fw - 1) / fw);
+    // enough blocks to fill every SM, whatever fits per SM
+    if (blocks > c->sms * 64 / fw) blocks = c->sms * 64 / fw;
 #define P3T_FORCE_ARGS                                                         \
     c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin, c->wmax,   \
         c->node, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2, c->order, n,  \
         k, c->gperm, c->gcost, c->pgroup, acc, pot, c->st, rec, rec_cap,   \
         c->lim_walk
+#define P3T_FORCE_LAUNCH(POT, REC, W)                                          \
+    k_walk_force<POT, REC, W><<<blocks, (W) * 32, 0, s>>>(P3T_FORCE_ARGS)
     if (rec)
-        k_walk_force<false, true><<<blocks, FW * 32, 0, s>>>(P3T_FORCE_ARGS);
-    else if (pot)
-        k_walk_force<true, false><<<blocks, FW * 32, 0, s>>>(P3T_FORCE_ARGS);
-    else
-        k_walk_force<false, false><<<blocks, FW * 32, 0, s>>>(P3T_FORCE_ARGS);
+        P3T_FORCE_LAUNCH(false, true, 4);
+    else if (fw == 2) {
+        if (pot) P3T_FORCE_LAUNCH(true, false, 2);
+        else P3T_FORCE_LAUNCH(false, false, 2);
+    } else if (fw == 8) {
+        if (pot) P3T_FORCE_LAUNCH(true, false, 8);
+        else P3T_FORCE_LAUNCH(false, false, 8);
+    } else {
+        if (pot) P3T_FORCE_LAUNCH(true, false, 4);
+        else P3T_FORCE_LAUNCH(false, false, 4);
+    }
+#undef P3T_FORCE_LAUNCH
 #undef P3T_FORCE_ARGS
     p3t_count_launches(1);
     if (c->n_bh > 0) {

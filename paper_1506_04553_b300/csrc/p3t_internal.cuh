@@ -153,6 +153,8 @@ struct p3t_ctx {
     double *ha, *hj, *hxp, *hvp;
     int64_t cap_herm;
     int herm_pad;            // dynamic shared memory of the Hermite kernel
+    int force_warps;         // warps per block of the walk + force kernel (0: 4)
+    int vjp_warps;           // warps per block of the backward kernel (0: 4)
     // bounds of the kernels' loops and waits (p3t_set_limits)
     long long lim_walk;      // walk iterations per group
     long long lim_uf;        // union-find rounds per edge
@@ -308,6 +310,9 @@ int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,
 int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
                       const double *mass, const long long *off, const int *idx,
                       const p3t_hermite_params *hp, cudaStream_t s); // p3t_hard.cu
+int p3t_force_err(p3t_ctx *c, long long n, const float *a, const float *r,
+                  void *scratch, double *median, double *emax, cudaStream_t s);
+size_t p3t_force_err_scratch(const p3t_ctx *c);               // p3t_misc.cu
 int p3t_energy_launch(p3t_ctx *c, long long n, const double *mass,
                       const double *vel, const double *pot, double *out,
                       cudaStream_t s);                           // p3t_misc.cu

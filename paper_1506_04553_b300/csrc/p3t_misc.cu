@@ -1,5 +1,6 @@
 // Elementwise FP64 updates (kick, drift), energy reductions and the scan that
 // turns per-particle neighbour counts into CSR offsets.
+#include <cstring>
 #include <mutex>
 
 #include <climits>
@@ -226,6 +227,90 @@ int p3t_energy_launch(p3t_ctx *c, long long n, const double *mass,
     p3t_count_launches(2);
     P3T_CUDA_TRY(cudaGetLastError());
     return P3T_OK;
+}
+
+// ---- relative difference of two force fields (the autotuner's accuracy
+// check) ----
+// e_i = |a_i - r_i| / max(|r_i|, 1e-3 rms |r|): its maximum and a histogram
+// of log10 e over [1e-12, 1e4) in 1/128 decade bins, from which the host
+// reads the median (to 2 %).
+constexpr int ERR_BINS = 2048;
+
+__global__ void __launch_bounds__(TB)
+k_err_sumsq(long long n, const float *__restrict__ r, double *__restrict__ part)
+{
+    double q = 0.0;
+    const long long stride = (long long)gridDim.x * TB;
+    for (long long i = (long long)blockIdx.x * TB + threadIdx.x; i < n; i += stride) {
+        const double x = r[i], y = r[n + i], z = r[2 * n + i];
+        q += x * x + y * y + z * z;
+    }
+    q = block_sum(q);
+    if (threadIdx.x == 0) part[blockIdx.x] = q;
+}
+
+__global__ void __launch_bounds__(TB)
+k_err_hist(long long n, const float *__restrict__ a, const float *__restrict__ r,
+           const double *__restrict__ part, int nb,
+           unsigned long long *__restrict__ hist, unsigned long long *__restrict__ emax)
+{
+    __shared__ double floor_s;
+    if (threadIdx.x == 0) {
+        double q = 0.0;
+        for (int b = 0; b < nb; ++b) q += part[b];
+        floor_s = 1e-3 * sqrt(q / (double)n);
+    }
+    __syncthreads();
+    const double fl = floor_s;
+    double mx = 0.0;
+    const long long stride = (long long)gridDim.x * TB;
+    for (long long i = (long long)blockIdx.x * TB + threadIdx.x; i < n; i += stride) {
+        const double rx = r[i], ry = r[n + i], rz = r[2 * n + i];
+        const double dx = (double)a[i] - rx, dy = (double)a[n + i] - ry,
+                     dz = (double)a[2 * n + i] - rz;
+        const double den = fmax(sqrt(rx * rx + ry * ry + rz * rz), fl);
+        const double e = den > 0.0 ? sqrt(dx * dx + dy * dy + dz * dz) / den : 0.0;
+        mx = fmax(mx, e);
+        int b = e > 0.0 ? (int)floor((log10(e) + 12.0) * 128.0) : 0;
+        b = b < 0 ? 0 : (b >= ERR_BINS ? ERR_BINS - 1 : b);
+        atomicAdd(hist + b, 1ull);
+    }
+    // a non-negative double orders like its bit pattern
+    atomicMax(emax, (unsigned long long)__double_as_longlong(mx));
+}
+
+// Median and maximum of e over n particles; scratch: device double[4 x SMs]
+// + ERR_BINS + 1 unsigned long long (allocated by the caller).  Synchronises.
+int p3t_force_err(p3t_ctx *c, long long n, const float *a, const float *r,
+                  void *scratch, double *median, double *emax, cudaStream_t s)
+{
+    double *part = (double *)scratch;
+    const int nb = c->sms * 4;
+    unsigned long long *hist = (unsigned long long *)(part + nb);
+    P3T_CUDA_TRY(cudaMemsetAsync(hist, 0, (ERR_BINS + 1) * sizeof(unsigned long long), s));
+    k_err_sumsq<<<nb, TB, 0, s>>>(n, r, part);
+    k_err_hist<<<nb, TB, 0, s>>>(n, a, r, part, nb, hist, hist + ERR_BINS);
+    p3t_count_launches(2);
+    P3T_CUDA_TRY(cudaGetLastError());
+    unsigned long long h[ERR_BINS + 1];
+    P3T_CUDA_TRY(cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, s));
+    P3T_CUDA_TRY(cudaStreamSynchronize(s));
+    unsigned long long cum = 0;
+    int b = 0;
+    for (; b < ERR_BINS - 1; ++b) {
+        cum += h[b];
+        if (2 * cum >= (unsigned long long)n) break;
+    }
+    *median = pow(10.0, (b + 0.5) / 128.0 - 12.0);
+    double m;
+    memcpy(&m, &h[ERR_BINS], sizeof m);
+    *emax = m;
+    return P3T_OK;
+}
+
+size_t p3t_force_err_scratch(const p3t_ctx *c)
+{
+    return sizeof(double) * 4 * c->sms + sizeof(unsigned long long) * (ERR_BINS + 1);
 }
 
 // ---- energy sums without allocation -------------------------------------

@@ -43,7 +43,8 @@ namespace {
 
 using p3t_walk::Smem;
 
-constexpr int VW = 4;    // warps per block
+// warps per block of k_walk_vjp: a template parameter (2 or 4), chosen per
+// context by the autotuner; 4 by default
 #ifndef P3T_VJP_NSP
 #define P3T_VJP_NSP 4
 #endif
@@ -433,6 +434,7 @@ struct VjpEval {
     }
 };
 
+template <int VW>
 __global__ void __launch_bounds__(VW * 32, P3T_VJP_MIN_BLOCKS)
 k_walk_vjp(const int *__restrict__ gclus,
            const ClusterConsts *__restrict__ ccs,
@@ -634,15 +636,20 @@ int p3t_run_vjp(p3t_ctx *c, const float *w, double *gpos, double *gmass,
     k.kA = (float)(1.0 / ((1.0 - c->p.gamma) * c->p.r_out));
     k.kB = (float)(-c->p.gamma / (1.0 - c->p.gamma));
     k.G = c->p.G;
-    int blocks = (int)((G + VW - 1) / VW);
-    if (blocks > c->sms * 16) blocks = c->sms * 16;
+    const int vw = c->vjp_warps == 2 ? 2 : 4;
+    int blocks = (int)((G + vw - 1) / vw);
+    if (blocks > c->sms * 64 / vw) blocks = c->sms * 64 / vw;
     k_vjp_reset<<<1, 32, 0, s>>>(c->st);
     const int slot = p3t_prof_open(c, P3T_PH_VJPWALK, s);
-    k_walk_vjp<<<blocks, VW * 32, 0, s>>>(
-        c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin,
-        c->wmax, theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2,
-        c->order, n, k, w,
-        gpos, gmass, cadj, c->gperm, c->st, c->lim_walk);
+#define P3T_VJP_ARGS                                                           \
+    c->gclus, c->cc, c->grange, c->gmin, c->gmax, c->gctr, c->wmin, c->wmax,   \
+        theta2, c->phi, c->plo, c->cf0, c->cf1, c->cf2, c->order, n, k, w,     \
+        gpos, gmass, cadj, c->gperm, c->st, c->lim_walk
+    if (vw == 2)
+        k_walk_vjp<2><<<blocks, 2 * 32, 0, s>>>(P3T_VJP_ARGS);
+    else
+        k_walk_vjp<4><<<blocks, 4 * 32, 0, s>>>(P3T_VJP_ARGS);
+#undef P3T_VJP_ARGS
     p3t_prof_close(c, slot, s);
     k_vjp_prep<<<c->sms * 8, 256, 0, s>>>(c->st, c->cM, cadj);
     k_vjp_leaves<<<c->sms * 8, 256, 0, s>>>(c->st, n, c->leaf_sorted, c->node,
