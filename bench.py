@@ -677,6 +677,17 @@ def run_ours(args, world, rank, local):
     hbm = float(peaks.get("hbm_gbs", 6518.0))
     b_build = (B_BUILD_PER_PARTICLE + B_BUILD_PER_CELL * cells_per_particle) * n
     build_ms = prof["build_ms"] / nprof
+    nb_ = max(prof["builds"], 1)
+    cells = cells_per_particle * n
+
+    def sub(name, nbytes, note):
+        ms_ = prof[f"build_{name}_ms"] / nb_
+        out = {"ms": ms_, "share": ms_ / build_ms if build_ms else None,
+               "note": note}
+        if nbytes:
+            out.update(bytes=nbytes, gbs=nbytes / (ms_ * 1e-3) / 1e9,
+                       frac=nbytes / (ms_ * 1e-3) / 1e9 / hbm)
+        return out
     line["hbm"] = {
         "peak_gbs": hbm,
         "build": {"bytes": b_build, "ms": build_ms,
@@ -684,7 +695,26 @@ def run_ours(args, world, rank, local):
                   "frac": b_build / (build_ms * 1e-3) / 1e9 / hbm,
                   "note": f"{B_BUILD_PER_PARTICLE} B/particle + "
                           f"{B_BUILD_PER_CELL} B/cell algorithmic; latency and "
-                          f"FP64 bound, not HBM"},
+                          f"FP64 bound, not HBM",
+                  "phases": {
+                      "keys": sub("keys", 60 * n, "root box (read x) and keys "
+                                  "(read x, write key and index): 60 B/particle"),
+                      "sort": sub("sort", (8 * 32 + 104) * n,
+                                  "8 radix passes (read the key for the "
+                                  "histogram, read and write key and index: "
+                                  "32 B) and the gather of the Morton-ordered "
+                                  "copies (104 B) per particle"),
+                      "split": sub("split", 0, "octree split, one launch per "
+                                   "level (21), and the leaf order: latency "
+                                   "bound, no byte count"),
+                      "moments": sub("moments", 32 * n + 208 * cells,
+                                     "read x and m (32 B/particle), write the "
+                                     "FP64 moments, box and FP32 records "
+                                     "(208 B/cell); one bottom-up launch"),
+                      "groups": sub("groups", 28 * n, "groups, their boxes "
+                                    "(read x and order: 28 B/particle) and "
+                                    "evaluation order"),
+                      "note": "CUDA events per sub-phase in the profiled steps"}},
         "kick": {"bytes_per_particle": B_KICK, "ms": kick_ms,
                  "gbs": B_KICK * n / (kick_ms * 1e-3) / 1e9,
                  "frac": B_KICK * n / (kick_ms * 1e-3) / 1e9 / hbm},

@@ -423,6 +423,11 @@ typedef struct p3t_profile {
     double vjp_walk_ms;  /* the backward's walk + Jacobian kernel alone (part
                             of walk_ms) */
     int64_t vjp_walks;
+    /* parts of build_ms: root box and keys; radix sort and gather of the
+     * Morton-ordered copies; octree split and leaf order; moments; groups,
+     * their boxes and evaluation order */
+    double build_keys_ms, build_sort_ms, build_split_ms, build_moments_ms,
+        build_groups_ms;
 } p3t_profile;
 int p3t_profile_enable(p3t_ctx *ctx, int on);
 int p3t_get_profile(p3t_ctx *ctx, p3t_profile *out, int reset);

@@ -90,7 +90,10 @@ class _CProfile(C.Structure):
                 ("forces", C.c_int64), ("ngbs", C.c_int64),
                 ("int_pc", C.c_int64), ("int_pp", C.c_int64),
                 ("int_pp_near", C.c_int64), ("vjp_walk_ms", C.c_double),
-                ("vjp_walks", C.c_int64)]
+                ("vjp_walks", C.c_int64), ("build_keys_ms", C.c_double),
+                ("build_sort_ms", C.c_double), ("build_split_ms", C.c_double),
+                ("build_moments_ms", C.c_double),
+                ("build_groups_ms", C.c_double)]
 
 
 _lib = _load_lib()

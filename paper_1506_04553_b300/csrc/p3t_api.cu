@@ -916,6 +916,11 @@ int p3t_get_profile(p3t_ctx *c, p3t_profile *o, int reset)
     o->forces = c->prof_calls[P3T_PH_FORCE];
     o->ngbs = c->prof_calls[P3T_PH_NGB];
     o->vjp_walk_ms = c->prof_ms[P3T_PH_VJPWALK];
+    o->build_keys_ms = c->prof_ms[P3T_PH_B_KEYS];
+    o->build_sort_ms = c->prof_ms[P3T_PH_B_SORT];
+    o->build_split_ms = c->prof_ms[P3T_PH_B_SPLIT];
+    o->build_moments_ms = c->prof_ms[P3T_PH_B_MOMENTS];
+    o->build_groups_ms = c->prof_ms[P3T_PH_B_GROUPS];
     o->vjp_walks = c->prof_calls[P3T_PH_VJPWALK];
     if (c->built && c->n > 0) {
         long long cum[3];

@@ -76,7 +76,8 @@ struct P3TDevState {
 
 // Phase timing with CUDA events (resolved lazily at p3t_get_profile).
 enum { P3T_PH_BUILD = 0, P3T_PH_WALK, P3T_PH_FORCE, P3T_PH_NGB,
-       P3T_PH_VJPWALK, P3T_NPH };
+       P3T_PH_VJPWALK, P3T_PH_B_KEYS, P3T_PH_B_SORT, P3T_PH_B_SPLIT,
+       P3T_PH_B_MOMENTS, P3T_PH_B_GROUPS, P3T_NPH };
 struct P3TEvents {
     cudaEvent_t *ev;   // pairs: ev[2k] start, ev[2k+1] stop
     int *phase;

@@ -995,6 +995,8 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     if (nbb < 1) nbb = 1;
     const int nc = c->nclus;
     const long long *off = (const long long *)c->clus_off;
+    // sub-phases timed when profiling is on (p3t_profile.build_*_ms)
+    int slot = p3t_prof_open(c, P3T_PH_B_KEYS, s);
     if (nc == 1) {
         k_bbox_partial<<<nbb, TB, 0, s>>>(n, pos, mass, c->bbox_part, c->st);
         k_bbox_final<<<1, TB, 0, s>>>(nbb, c->bbox_part, c->st, c->clus_box);
@@ -1004,6 +1006,8 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     }
     k_keys<<<nb, TB, 0, s>>>(n, pos, nc, c->pclus, c->clus_box, c->key_a,
                              c->idx_a);
+    p3t_prof_close(c, slot, s);
+    slot = p3t_prof_open(c, P3T_PH_B_SORT, s);
     int rc = p3t_sort_keys(c, n, s);
     if (rc) return rc;
     if (nc > 1) {
@@ -1012,6 +1016,8 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     }
     k_gather<<<nb, TB, 0, s>>>(n, c->idx_a, pos, mass, c->order, c->xs, c->ms,
                                c->phi, c->plo);
+    p3t_prof_close(c, slot, s);
+    slot = p3t_prof_open(c, P3T_PH_B_SPLIT, s);
     k_tree_init<<<(nc + 255) / 256, 256, 0, s>>>(nc, off, c->node, c->parent,
                                                  c->cpend, c->st);
     const int cap = (int)c->cap_cells;
@@ -1023,11 +1029,15 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     k_leaf_hist<<<c->sms * 4, TB, 0, s>>>(c->leaf_list, c->node, c->st);
     k_leaf_scatter<<<c->sms * 4, TB, 0, s>>>(c->leaf_list, c->node,
                                               c->leaf_sorted, c->st);
+    p3t_prof_close(c, slot, s);
+    slot = p3t_prof_open(c, P3T_PH_B_MOMENTS, s);
     k_moments_up<<<c->sms * 8, TB, 0, s>>>(c->xs, c->ms, n, c->node, c->parent,
                                             c->leaf_sorted, c->cpend, c->cM,
                                             c->ccom, c->cQ, c->cbmin, c->cbmax,
                                             c->wmin, c->wmax, c->cf0, c->cf1,
                                             c->cf2, c->st);
+    p3t_prof_close(c, slot, s);
+    slot = p3t_prof_open(c, P3T_PH_B_GROUPS, s);
     k_groups<<<grid_small, TB, 0, s>>>(c->p.n_group, (int)c->cap_groups,
                                         c->node, c->parent, c->grange, c->st);
     k_group_box<<<c->sms * 2, GB, 0, s>>>(c->grange, c->xs, n, nc, c->order,
@@ -1037,6 +1047,7 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
                                             c->gcost, c->st);
     k_group_order<<<grid_small, TB, 0, s>>>(n, c->grange, c->order, c->pgroup,
                                              c->gcost, c->gperm, c->st);
+    p3t_prof_close(c, slot, s);
     // bbox 2, keys, gather, init, 21 splits, leaf order 2, moments, groups,
     // boxes, order 2
     p3t_count_launches(2 + 1 + 1 + 1 + P3T_MAX_LEVEL + 2 + 1 + 4);
