@@ -228,20 +228,23 @@ __device__ __forceinline__ float4 rel4(float4 hi, float4 lo, float4 c)
 #define P3T_FORCE_MIN_BLOCKS 0
 #endif
 constexpr int FSTACK = 768;  // walk stack entries per warp (child ranges)
-constexpr int RING = 64;     // ring capacity (entries); never more than 63 used
+constexpr int RING = 64;     // leaf-range ring capacity; never more than 63 used
+constexpr int CRING = 128;   // cell ring capacity; never more than 95 used
+constexpr int CTILE = 64;    // cells per tile (two staged per lane)
+constexpr int PTILE = 32;    // particles per tile (one staged per lane)
 
 // components of the staged sources (cells use all ten, particles the first
 // four): X Y Z M -Qxx -Qyy -Qzz -Qxy -Qxz -Qyz
 constexpr int NCOMP = 10;
 
 struct __align__(16) WarpSmem {
-    float t[NCOMP][32];             // staged sources, pair-interleaved (see cell_tile)
+    float t[NCOMP][CTILE];          // staged sources, pair-interleaved (see cell_tile)
     int stack[FSTACK];              // packed child ranges: child * 8 + nchild-1
     int cb[32];                     // cells of the current walk batch
-    int pc[RING];                   // accepted cells
+    int pc[CRING];                  // accepted cells
     int2 pf[RING];                  // far leaf ranges (first, count)
     int2 pn[RING];                  // near leaf ranges
-    int tj[32];                     // sorted ids of staged particles
+    int tj[PTILE];                  // sorted ids of staged particles
     float4 gmn, gmx, ct;            // the group's box and centre
 };
 
@@ -319,12 +322,14 @@ struct Rec {
 };
 
 __device__ __forceinline__ void rec_tile(const Rec &R, int take, int lane,
-                                         int kind, int id)
+                                         int kind, int id, int slot0 = 0)
 {
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(R.cnt, (unsigned long long)take);
+    const int nt = take - slot0 < 32 ? take - slot0 : 32;  // this round's sources
+    if (nt <= 0) return;
+    if (lane == 0) base = atomicAdd(R.cnt, (unsigned long long)nt);
     base = __shfl_sync(0xffffffffu, base, 0);
-    if (lane < take && base + lane < (unsigned long long)R.cap)
+    if (lane < nt && base + lane < (unsigned long long)R.cap)
         R.buf[base + lane] = ((long long)R.g << 33) | ((long long)kind << 31) | id;
 }
 
@@ -373,8 +378,10 @@ __device__ __forceinline__ CellPair cell_pair(const WarpSmem &S, int j)
     return c;
 }
 
-// One tile of up to 32 accepted cells.  TWO: the lane holds a second
-// particle (slot 32 + lane); groups of at most 32 particles skip it.
+// One tile of up to CTILE = 64 accepted cells, two staged per lane (slots
+// lane and lane + 32).  TWO: the lane holds a second particle (slot 32 +
+// lane); groups of at most 32 particles skip it.  A tile of at most 32
+// cells evaluates only the first half of the staged pairs.
 template <bool POT, bool TWO, bool REC>
 __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
                                           int take, const float4 *cf0,
@@ -383,49 +390,52 @@ __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
                                           float eps2, GroupAcc<POT> &A, int lane,
                                           const Rec &R)
 {
-    float v[NCOMP];
-    if (REC) rec_tile(R, take, lane, 0, lane < take ? S.pc[(head + lane) & (RING - 1)] : 0);
-    if (lane < take) {
-        int c = S.pc[(head + lane) & (RING - 1)];
-        float4 a = cf0[c], bb = cf1[c], cc = cf2[c];
-        const float4 ct = S.ct;
-        v[0] = __fadd_rn(__fsub_rn(a.x, ct.x), bb.x);
-        v[1] = __fadd_rn(__fsub_rn(a.y, ct.y), bb.y);
-        v[2] = __fadd_rn(__fsub_rn(a.z, ct.z), bb.z);
-        v[3] = a.w;
-        v[4] = -bb.w;          // -Qxx
-        v[5] = -cc.x;          // -Qyy
-        v[6] = bb.w + cc.x;    // -Qzz = Qxx + Qyy (traceless)
-        v[7] = -cc.y;          // -Qxy
-        v[8] = -cc.z;          // -Qxz
-        v[9] = -cc.w;          // -Qyz
-    } else {
-        const float4 fp = far_pad();
-        v[0] = fp.x; v[1] = fp.y; v[2] = fp.z;
+    const float4 ct = S.ct;
 #pragma unroll
-        for (int q = 3; q < NCOMP; ++q) v[q] = 0.0f;
-    }
-    // pair-interleaved: the cells 2p and 2p+1 fill 20 consecutive floats,
-    // components (2k, 2k+1) of both in float4 k, so one 128-bit load gives
-    // two components of the pair
-    {
+    for (int h = 0; h < 2; ++h) {
+        const int slot = lane + 32 * h;
+        const int c = slot < take ? S.pc[(head + slot) & (CRING - 1)] : 0;
+        if (REC) rec_tile(R, take, lane, 0, c, 32 * h);
+        float v[NCOMP];
+        if (slot < take) {
+            float4 a = cf0[c], bb = cf1[c], cc = cf2[c];
+            v[0] = __fadd_rn(__fsub_rn(a.x, ct.x), bb.x);
+            v[1] = __fadd_rn(__fsub_rn(a.y, ct.y), bb.y);
+            v[2] = __fadd_rn(__fsub_rn(a.z, ct.z), bb.z);
+            v[3] = a.w;
+            v[4] = -bb.w;          // -Qxx
+            v[5] = -cc.x;          // -Qyy
+            v[6] = bb.w + cc.x;    // -Qzz = Qxx + Qyy (traceless)
+            v[7] = -cc.y;          // -Qxy
+            v[8] = -cc.z;          // -Qxz
+            v[9] = -cc.w;          // -Qyz
+        } else {
+            const float4 fp = far_pad();
+            v[0] = fp.x; v[1] = fp.y; v[2] = fp.z;
+#pragma unroll
+            for (int q = 3; q < NCOMP; ++q) v[q] = 0.0f;
+        }
+        // pair-interleaved: the cells 2p and 2p+1 fill 20 consecutive floats,
+        // components (2k, 2k+1) of both in float4 k, so one 128-bit load
+        // gives two components of the pair
         float *t = &S.t[0][0];
-        const int pr = lane >> 1, hf = lane & 1;
+        const int pr = slot >> 1, hf = slot & 1;
 #pragma unroll
         for (int k = 0; k < NCOMP / 2; ++k) {
             t[pr * 20 + 4 * k + hf] = v[2 * k];
             t[pr * 20 + 4 * k + 2 + hf] = v[2 * k + 1];
         }
     }
-    head = (head + take) & (RING - 1);
+    head = (head + take) & (CRING - 1);
     n -= take;
     __syncwarp();
     Part3 u, w;
     u.zero();
     w.zero();
     const f2 e2 = dup2(eps2);
+    const int jend = take > 32 ? 64 : 32;  // warp-uniform
 #pragma unroll kPcUnroll
-    for (int j = 0; j < 32; j += 2) {
+    for (int j = 0; j < jend; j += 2) {
         const CellPair c = cell_pair(S, j);
         pc_term2<POT>(P.x0, P.y0, P.z0, c, e2, u.x, u.y, u.z, u.p);
         if (TWO) pc_term2<POT>(P.x1, P.y1, P.z1, c, e2, w.x, w.y, w.z, w.p);
@@ -447,8 +457,8 @@ __device__ __forceinline__ PartPair part_pair(const WarpSmem &S, int j)
     return p;
 }
 
-// One tile of up to 32 particles from a ring of leaf ranges (TWO as for
-// cell_tile).
+// One tile of up to PTILE = 32 particles from a ring of leaf ranges (TWO as
+// for cell_tile).
 template <bool NEAR, bool POT, bool TWO, bool REC>
 __device__ __forceinline__ void particle_tile(
     WarpSmem &S, int2 *ring, RangeRing &r, int take, const float4 *phi,
@@ -481,7 +491,7 @@ __device__ __forceinline__ void particle_tile(
         const f2 kA = dup2(k.kA), kB = dup2(k.kB);
         float tp0 = 0.f, tp1 = 0.f;
 #pragma unroll 2
-        for (int j = 0; j < 32; j += 2) {
+        for (int j = 0; j < PTILE; j += 2) {
             const PartPair p = part_pair(S, j);
             const f2 s0 = pp_near2(P.x0, P.y0, P.z0, p, e2, kA, kB, u.x, u.y, u.z);
             const f2 s1 = TWO ? pp_near2(P.x1, P.y1, P.z1, p, e2, kA, kB, w.x, w.y, w.z)
@@ -503,7 +513,7 @@ __device__ __forceinline__ void particle_tile(
         tile_end<POT>(A, u, w, 1.0f);
     } else {
 #pragma unroll 8
-        for (int j = 0; j < 32; j += 2) {
+        for (int j = 0; j < PTILE; j += 2) {
             const PartPair p = part_pair(S, j);
             pp_far2<POT>(P.x0, P.y0, P.z0, p, e2, u.x, u.y, u.z, u.p);
             if (TWO) pp_far2<POT>(P.x1, P.y1, P.z1, p, e2, w.x, w.y, w.z, w.p);
@@ -513,10 +523,10 @@ __device__ __forceinline__ void particle_tile(
     __syncwarp();
 }
 
-// Evaluates tiles while a ring holds at least `lim` sources: lim = 32 during
-// the walk (full tiles), lim = 1 at its end (the partial tiles left over).
+// Evaluates the full tiles (CTILE sources) of every ring during the walk,
+// and at its end (last) also the partial tiles left over.
 template <bool POT, bool TWO, bool REC>
-__device__ __forceinline__ void drain(WarpSmem &S, int lim, int &pc_head,
+__device__ __forceinline__ void drain(WarpSmem &S, bool last, int &pc_head,
                                       int &pc_n, RangeRing &rf, RangeRing &rn,
                                       const float4 *cf0, const float4 *cf1,
                                       const float4 *cf2, const float4 *phi,
@@ -524,14 +534,14 @@ __device__ __forceinline__ void drain(WarpSmem &S, int lim, int &pc_head,
                                       int k0, int k1, const ForceConsts &kg,
                                       GroupAcc<POT> &A, int lane, const Rec &R)
 {
-    while (pc_n >= lim)
-        cell_tile<POT, TWO, REC>(S, pc_head, pc_n, min(pc_n, 32), cf0, cf1, cf2,
-                                 P, kg.eps2, A, lane, R);
-    while (rf.np >= lim)
-        particle_tile<false, POT, TWO, REC>(S, S.pf, rf, min(rf.np, 32), phi,
+    while (pc_n >= (last ? 1 : CTILE))
+        cell_tile<POT, TWO, REC>(S, pc_head, pc_n, min(pc_n, CTILE), cf0, cf1,
+                                 cf2, P, kg.eps2, A, lane, R);
+    while (rf.np >= (last ? 1 : PTILE))
+        particle_tile<false, POT, TWO, REC>(S, S.pf, rf, min(rf.np, PTILE), phi,
                                             plo, P, k0, k1, kg, A, lane, R);
-    while (rn.np >= lim)
-        particle_tile<true, POT, TWO, REC>(S, S.pn, rn, min(rn.np, 32), phi,
+    while (rn.np >= (last ? 1 : PTILE))
+        particle_tile<true, POT, TWO, REC>(S, S.pn, rn, min(rn.np, PTILE), phi,
                                            plo, P, k0, k1, kg, A, lane, R);
 }
 
@@ -700,7 +710,7 @@ k_walk_force(const int *__restrict__ gclus,
             // accepted cells -> cell ring
             {
                 unsigned m = __ballot_sync(full, is_pc);
-                if (is_pc) S.pc[(pc_head + pc_n + __popc(m & lt)) & (RING - 1)] = c;
+                if (is_pc) S.pc[(pc_head + pc_n + __popc(m & lt)) & (CRING - 1)] = c;
                 pc_n += __popc(m);
                 cnt_pc += __popc(m);
             }
@@ -733,10 +743,10 @@ k_walk_force(const int *__restrict__ gclus,
             }
             // evaluate every full tile
             if (two)
-                drain<POT, true, REC>(S, 32, pc_head, pc_n, rf, rn, cf0, cf1,
+                drain<POT, true, REC>(S, false, pc_head, pc_n, rf, rn, cf0, cf1,
                                       cf2, phi, plo, P, k0, k1, kg, A, lane, R);
             else
-                drain<POT, false, REC>(S, 32, pc_head, pc_n, rf, rn, cf0, cf1,
+                drain<POT, false, REC>(S, false, pc_head, pc_n, rf, rn, cf0, cf1,
                                        cf2, phi, plo, P, k0, k1, kg, A, lane, R);
         }
         if (overflow || timeout) {
@@ -745,10 +755,10 @@ k_walk_force(const int *__restrict__ gclus,
         }
         // the partial tiles left over
         if (two)
-            drain<POT, true, REC>(S, 1, pc_head, pc_n, rf, rn, cf0, cf1, cf2,
+            drain<POT, true, REC>(S, true, pc_head, pc_n, rf, rn, cf0, cf1, cf2,
                                   phi, plo, P, k0, k1, kg, A, lane, R);
         else
-            drain<POT, false, REC>(S, 1, pc_head, pc_n, rf, rn, cf0, cf1, cf2,
+            drain<POT, false, REC>(S, true, pc_head, pc_n, rf, rn, cf0, cf1, cf2,
                                    phi, plo, P, k0, k1, kg, A, lane, R);
         // ---- write back in the caller's order ----
         const float Gc = k.G;
