@@ -228,8 +228,9 @@ __device__ __forceinline__ float4 rel4(float4 hi, float4 lo, float4 c)
 #define P3T_FORCE_MIN_BLOCKS 0
 #endif
 constexpr int FSTACK = 768;  // walk stack entries per warp (child ranges)
-constexpr int RING = 64;     // leaf-range ring capacity; never more than 63 used
-constexpr int CRING = 128;   // cell ring capacity; never more than 95 used
+constexpr int RING = 128;    // leaf-range ring capacity; never more than 95 used
+constexpr int CRING = 128;   // cell ring capacity; never more than 127 used
+constexpr int WB = 64;       // cells per walk batch (two per lane)
 constexpr int CTILE = 64;    // cells per tile (two staged per lane)
 constexpr int PTILE = 32;    // particles per tile (one staged per lane)
 
@@ -240,7 +241,8 @@ constexpr int NCOMP = 10;
 struct __align__(16) WarpSmem {
     float t[NCOMP][CTILE];          // staged sources, pair-interleaved (see cell_tile)
     int stack[FSTACK];              // packed child ranges: child * 8 + nchild-1
-    int cb[32];                     // cells of the current walk batch
+    int cb[WB];                     // cells of the current walk batch
+    float4 box[2][WB];              // their box records (wmin, wmax), by slot
     int pc[CRING];                  // accepted cells
     int2 pf[RING];                  // far leaf ranges (first, count)
     int2 pn[RING];                  // near leaf ranges
@@ -555,17 +557,25 @@ __device__ __forceinline__ void prefetch_l2(const void *ptr, size_t bytes,
         asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
 }
 
+// Asynchronous 16-byte copy global -> shared (cp.async; no register holds
+// the data while it is in flight).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
+}
+
 // Pops child ranges from the top of the walk stack until they hold at most
-// 32 cells and returns this lane's cell of the batch (-1 past its end);
-// total receives the batch size (warp-uniform, 0 when the stack is empty).
-__device__ __forceinline__ int pop_batch(WarpSmem &S, int &top, int &total,
+// WB = 64 cells, lists them in S.cb and requests their box records into
+// S.box with cp.async; returns the batch size (warp-uniform, 0 when the
+// stack is empty).  The lane's cells are slots lane and lane + 32.
+__device__ __forceinline__ int pop_batch(WarpSmem &S, int &top,
+                                         const float4 *__restrict__ wmin,
+                                         const float4 *__restrict__ wmax,
                                          int lane)
 {
     const unsigned full = 0xffffffffu;
-    if (top == 0) {
-        total = 0;
-        return -1;
-    }
+    if (top == 0) return 0;
     int rx = 0, ry = 0;
     if (lane < top) {
         int e = S.stack[top - 1 - lane];
@@ -573,16 +583,24 @@ __device__ __forceinline__ int pop_batch(WarpSmem &S, int &top, int &total,
         ry = (e & 7) + 1;
     }
     int inc = warp_incl_scan(ry);
-    bool take = lane < top && inc <= 32;
+    bool take = lane < top && inc <= WB;
     int ntake = __popc(__ballot_sync(full, take));
-    total = __shfl_sync(full, inc, ntake - 1);
+    const int total = __shfl_sync(full, inc, ntake - 1);
     if (take)
         for (int t = 0; t < ry; ++t) S.cb[inc - ry + t] = rx + t;
     top -= ntake;
     __syncwarp();
-    const int c = lane < total ? S.cb[lane] : -1;
-    __syncwarp();
-    return c;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int slot = lane + 32 * h;
+        if (slot < total) {
+            const int c = S.cb[slot];
+            cp_async16(&S.box[0][slot], wmin + c);
+            cp_async16(&S.box[1][slot], wmax + c);
+        }
+    }
+    asm volatile("cp.async.commit_group;");
+    return total;
 }
 
 template <bool POT, bool REC, int FW>
@@ -670,77 +688,78 @@ k_walk_force(const int *__restrict__ gclus,
         long long iter = 0;
         bool overflow = false, timeout = false;
         __syncwarp();
-        // The walk is software-pipelined by one batch: the next batch is
-        // popped and its box records requested before the full tiles are
-        // evaluated, so the records' latency hides behind the warp's own
-        // arithmetic.  The batches, and so the tiles, are those of the plain
-        // loop (pop, test, push, evaluate), in the same order.
-        int total = 0;
-        int c = pop_batch(S, top, total, lane);
-        float4 cmn = make_float4(0.f, 0.f, 0.f, 0.f), cmx = cmn;
-        if (c >= 0) {
-            cmn = wmin[c];
-            cmx = wmax[c];
-        }
+        // The walk is software-pipelined by one batch: the next batch (up to
+        // 64 cells, two per lane) is popped and its box records copied into
+        // shared memory by cp.async before the full tiles are evaluated, so
+        // the records' latency hides behind the warp's own arithmetic and no
+        // register holds them.  The batches, and so the tiles, are those of
+        // the plain loop (pop, test, push, evaluate), in the same order.
+        int total = pop_batch(S, top, wmin, wmax, lane);
         while (total > 0) {
             if (++iter > lim_walk) {  // a finite tree stays far below the default
                 timeout = true;
                 break;
             }
-            bool is_pc = false, near = false, farl = false, open = false;
-            int child = 0, nchild = 0, pfirst = 0, pcount = 0;
-            if (c >= 0) {
-                float d2 = box_d2(S.gmn, S.gmx, cmn, cmx);
-                float l = box_side(cmn, cmx);
-                if (mac_accept(d2, l, theta2, hg2)) {
-                    is_pc = true;
-                } else {
-                    child = __float_as_int(cmn.w);
-                    nchild = __float_as_int(cmx.w);
-                    if (nchild <= 0) {  // a leaf: first particle, -count
-                        pfirst = child;
-                        pcount = -nchild;
-                        near = d2 <= hg2;
-                        farl = !near;
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncwarp();
+            bool is_pc[2], near[2], farl[2], open[2];
+            int cid[2], child[2], nchild[2], pfirst[2], pcount[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int slot = lane + 32 * h;
+                is_pc[h] = near[h] = farl[h] = open[h] = false;
+                cid[h] = slot < total ? S.cb[slot] : -1;
+                child[h] = nchild[h] = pfirst[h] = pcount[h] = 0;
+                if (cid[h] >= 0) {
+                    const float4 cmn = S.box[0][slot], cmx = S.box[1][slot];
+                    float d2 = box_d2(S.gmn, S.gmx, cmn, cmx);
+                    float l = box_side(cmn, cmx);
+                    if (mac_accept(d2, l, theta2, hg2)) {
+                        is_pc[h] = true;
                     } else {
-                        open = true;
+                        child[h] = __float_as_int(cmn.w);
+                        nchild[h] = __float_as_int(cmx.w);
+                        if (nchild[h] <= 0) {  // a leaf: first particle, -count
+                            pfirst[h] = child[h];
+                            pcount[h] = -nchild[h];
+                            near[h] = d2 <= hg2;
+                            farl[h] = !near[h];
+                        } else {
+                            open[h] = true;
+                        }
                     }
                 }
             }
-            // accepted cells -> cell ring
-            {
-                unsigned m = __ballot_sync(full, is_pc);
-                if (is_pc) S.pc[(pc_head + pc_n + __popc(m & lt)) & (CRING - 1)] = c;
+            // accepted cells -> cell ring, leaves -> particle rings, opened
+            // cells -> stack; slot order (lane, then lane + 32)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                unsigned m = __ballot_sync(full, is_pc[h]);
+                if (is_pc[h]) S.pc[(pc_head + pc_n + __popc(m & lt)) & (CRING - 1)] = cid[h];
                 pc_n += __popc(m);
                 cnt_pc += __popc(m);
-            }
-            // leaves -> particle rings
-            {
                 int before = rn.np;
-                ring_push_ranges(S.pn, rn, near, pfirst, pcount, lane);
+                ring_push_ranges(S.pn, rn, near[h], pfirst[h], pcount[h], lane);
                 cnt_pn += rn.np - before;
                 before = rf.np;
-                ring_push_ranges(S.pf, rf, farl, pfirst, pcount, lane);
+                ring_push_ranges(S.pf, rf, farl[h], pfirst[h], pcount[h], lane);
                 cnt_pf += rf.np - before;
             }
-            // opened cells -> stack
-            {
-                unsigned mo = __ballot_sync(full, open);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                unsigned mo = __ballot_sync(full, open[h]);
                 int np = __popc(mo);
                 if (top + np > FSTACK) {
                     overflow = true;
                     break;
                 }
-                if (open) S.stack[top + __popc(mo & lt)] = child * 8 + (nchild - 1);
+                if (open[h]) S.stack[top + __popc(mo & lt)] = child[h] * 8 + (nchild[h] - 1);
                 top += np;
             }
+            if (overflow) break;
             __syncwarp();
             // the next batch, requested now
-            c = pop_batch(S, top, total, lane);
-            if (c >= 0) {
-                cmn = wmin[c];
-                cmx = wmax[c];
-            }
+            total = pop_batch(S, top, wmin, wmax, lane);
             // evaluate every full tile
             if (two)
                 drain<POT, true, REC>(S, false, pc_head, pc_n, rf, rn, cf0, cf1,
@@ -750,6 +769,9 @@ k_walk_force(const int *__restrict__ gclus,
                                        cf2, phi, plo, P, k0, k1, kg, A, lane, R);
         }
         if (overflow || timeout) {
+            // the abandoned batch's copies land before S.box is reused
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            __syncwarp();
             if (lane == 0) p3t_raise(st, timeout ? P3T_ERR_TIMEOUT : P3T_ERR_CAPACITY);
             continue;
         }
