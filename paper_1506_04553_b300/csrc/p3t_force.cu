@@ -57,6 +57,14 @@ __device__ __forceinline__ float4 far_pad()
 // exact whenever |hi| >= |v|, which holds after a group's first tiles (a
 // tile's partial sum is one of many); the terms themselves carry FP32
 // rounding, so no more exactness is needed.
+// Asynchronous 16-byte copy global -> shared (cp.async; no register holds
+// the data while it is in flight).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
+}
+
 __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float v)
 {
     float s = __fadd_rn(hi, v);
@@ -243,6 +251,7 @@ struct __align__(16) WarpSmem {
     int stack[FSTACK];              // packed child ranges: child * 8 + nchild-1
     int cb[WB];                     // cells of the current walk batch
     float4 box[2][WB];              // their box records (wmin, wmax), by slot
+    float4 raw[3][CTILE];           // force records of a requested cell tile
     int pc[CRING];                  // accepted cells
     int2 pf[RING];                  // far leaf ranges (first, count)
     int2 pn[RING];                  // near leaf ranges
@@ -380,10 +389,67 @@ __device__ __forceinline__ CellPair cell_pair(const WarpSmem &S, int j)
     return c;
 }
 
-// One tile of up to CTILE = 64 accepted cells, two staged per lane (slots
-// lane and lane + 32).  TWO: the lane holds a second particle (slot 32 +
-// lane); groups of at most 32 particles skip it.  A tile of at most 32
-// cells evaluates only the first half of the staged pairs.
+// Staged form of one cell (slot of the tile): position relative to the group
+// centre, mass and -Q, from its force records (hi com + M, lo com + Qxx,
+// Qyy Qxy Qxz Qyz), written pair-interleaved: the cells 2p and 2p+1 fill 20
+// consecutive floats, components (2k, 2k+1) of both in float4 k, so one
+// 128-bit load gives two components of the pair.  Empty slots are far
+// padding with no mass.
+__device__ __forceinline__ void stage_cell(WarpSmem &S, int slot, bool have,
+                                           float4 a, float4 bb, float4 cc)
+{
+    const float4 ct = S.ct;
+    float v[NCOMP];
+    if (have) {
+        v[0] = __fadd_rn(__fsub_rn(a.x, ct.x), bb.x);
+        v[1] = __fadd_rn(__fsub_rn(a.y, ct.y), bb.y);
+        v[2] = __fadd_rn(__fsub_rn(a.z, ct.z), bb.z);
+        v[3] = a.w;
+        v[4] = -bb.w;          // -Qxx
+        v[5] = -cc.x;          // -Qyy
+        v[6] = bb.w + cc.x;    // -Qzz = Qxx + Qyy (traceless)
+        v[7] = -cc.y;          // -Qxy
+        v[8] = -cc.z;          // -Qxz
+        v[9] = -cc.w;          // -Qyz
+    } else {
+        const float4 fp = far_pad();
+        v[0] = fp.x; v[1] = fp.y; v[2] = fp.z;
+#pragma unroll
+        for (int q = 3; q < NCOMP; ++q) v[q] = 0.0f;
+    }
+    float *t = &S.t[0][0];
+    const int pr = slot >> 1, hf = slot & 1;
+#pragma unroll
+    for (int k = 0; k < NCOMP / 2; ++k) {
+        t[pr * 20 + 4 * k + hf] = v[2 * k];
+        t[pr * 20 + 4 * k + 2 + hf] = v[2 * k + 1];
+    }
+}
+
+// Evaluation of the staged cell tile (64 cells, or 32 when jend = 32) for the
+// lane's particles.  TWO: the lane holds a second particle (slot 32 +
+// lane); groups of at most 32 particles skip it.
+template <bool POT, bool TWO>
+__device__ __forceinline__ void cell_eval(const WarpSmem &S, int jend,
+                                          const IPair &P, float eps2,
+                                          GroupAcc<POT> &A)
+{
+    Part3 u, w;
+    u.zero();
+    w.zero();
+    const f2 e2 = dup2(eps2);
+#pragma unroll kPcUnroll
+    for (int j = 0; j < jend; j += 2) {
+        const CellPair c = cell_pair(S, j);
+        pc_term2<POT>(P.x0, P.y0, P.z0, c, e2, u.x, u.y, u.z, u.p);
+        if (TWO) pc_term2<POT>(P.x1, P.y1, P.z1, c, e2, w.x, w.y, w.z, w.p);
+    }
+    tile_end<POT>(A, u, w, -1.0f);
+}
+
+// One tile of up to CTILE = 64 accepted cells from the ring, two per lane
+// (slots lane and lane + 32), loaded and staged at once (the walk's last,
+// partial tiles); a tile of at most 32 cells evaluates only the first half.
 template <bool POT, bool TWO, bool REC>
 __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
                                           int take, const float4 *cf0,
@@ -392,57 +458,64 @@ __device__ __forceinline__ void cell_tile(WarpSmem &S, int &head, int &n,
                                           float eps2, GroupAcc<POT> &A, int lane,
                                           const Rec &R)
 {
-    const float4 ct = S.ct;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int slot = lane + 32 * h;
         const int c = slot < take ? S.pc[(head + slot) & (CRING - 1)] : 0;
         if (REC) rec_tile(R, take, lane, 0, c, 32 * h);
-        float v[NCOMP];
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), bb = a, cc = a;
         if (slot < take) {
-            float4 a = cf0[c], bb = cf1[c], cc = cf2[c];
-            v[0] = __fadd_rn(__fsub_rn(a.x, ct.x), bb.x);
-            v[1] = __fadd_rn(__fsub_rn(a.y, ct.y), bb.y);
-            v[2] = __fadd_rn(__fsub_rn(a.z, ct.z), bb.z);
-            v[3] = a.w;
-            v[4] = -bb.w;          // -Qxx
-            v[5] = -cc.x;          // -Qyy
-            v[6] = bb.w + cc.x;    // -Qzz = Qxx + Qyy (traceless)
-            v[7] = -cc.y;          // -Qxy
-            v[8] = -cc.z;          // -Qxz
-            v[9] = -cc.w;          // -Qyz
-        } else {
-            const float4 fp = far_pad();
-            v[0] = fp.x; v[1] = fp.y; v[2] = fp.z;
-#pragma unroll
-            for (int q = 3; q < NCOMP; ++q) v[q] = 0.0f;
+            a = cf0[c];
+            bb = cf1[c];
+            cc = cf2[c];
         }
-        // pair-interleaved: the cells 2p and 2p+1 fill 20 consecutive floats,
-        // components (2k, 2k+1) of both in float4 k, so one 128-bit load
-        // gives two components of the pair
-        float *t = &S.t[0][0];
-        const int pr = slot >> 1, hf = slot & 1;
-#pragma unroll
-        for (int k = 0; k < NCOMP / 2; ++k) {
-            t[pr * 20 + 4 * k + hf] = v[2 * k];
-            t[pr * 20 + 4 * k + 2 + hf] = v[2 * k + 1];
-        }
+        stage_cell(S, slot, slot < take, a, bb, cc);
     }
     head = (head + take) & (CRING - 1);
     n -= take;
     __syncwarp();
-    Part3 u, w;
-    u.zero();
-    w.zero();
-    const f2 e2 = dup2(eps2);
-    const int jend = take > 32 ? 64 : 32;  // warp-uniform
-#pragma unroll kPcUnroll
-    for (int j = 0; j < jend; j += 2) {
-        const CellPair c = cell_pair(S, j);
-        pc_term2<POT>(P.x0, P.y0, P.z0, c, e2, u.x, u.y, u.z, u.p);
-        if (TWO) pc_term2<POT>(P.x1, P.y1, P.z1, c, e2, w.x, w.y, w.z, w.p);
+    cell_eval<POT, TWO>(S, take > 32 ? 64 : 32, P, eps2, A);
+    __syncwarp();
+}
+
+// A full tile of CTILE cells taken from the ring and its force records
+// requested into S.raw by cp.async; staged and evaluated by cell_raw_tile
+// after the next wait, one walk iteration later, so that the records'
+// latency hides behind the warp's other work.
+template <bool REC>
+__device__ __forceinline__ void cell_request(WarpSmem &S, int &head, int &n,
+                                             const float4 *cf0,
+                                             const float4 *cf1,
+                                             const float4 *cf2, int lane,
+                                             const Rec &R)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int slot = lane + 32 * h;
+        const int c = S.pc[(head + slot) & (CRING - 1)];
+        if (REC) rec_tile(R, CTILE, lane, 0, c, 32 * h);
+        cp_async16(&S.raw[0][slot], cf0 + c);
+        cp_async16(&S.raw[1][slot], cf1 + c);
+        cp_async16(&S.raw[2][slot], cf2 + c);
     }
-    tile_end<POT>(A, u, w, -1.0f);
+    asm volatile("cp.async.commit_group;");
+    head = (head + CTILE) & (CRING - 1);
+    n -= CTILE;
+}
+
+// The requested tile (its copies complete), staged and evaluated.
+template <bool POT, bool TWO>
+__device__ __forceinline__ void cell_raw_tile(WarpSmem &S, const IPair &P,
+                                              float eps2, GroupAcc<POT> &A,
+                                              int lane)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int slot = lane + 32 * h;
+        stage_cell(S, slot, true, S.raw[0][slot], S.raw[1][slot], S.raw[2][slot]);
+    }
+    __syncwarp();
+    cell_eval<POT, TWO>(S, CTILE, P, eps2, A);
     __syncwarp();
 }
 
@@ -525,8 +598,9 @@ __device__ __forceinline__ void particle_tile(
     __syncwarp();
 }
 
-// Evaluates the full tiles (CTILE sources) of every ring during the walk,
-// and at its end (last) also the partial tiles left over.
+// Evaluates the full particle tiles during the walk (the full cell tiles go
+// through cell_request / cell_raw_tile), and at its end (last) every tile
+// left over, partial ones included.
 template <bool POT, bool TWO, bool REC>
 __device__ __forceinline__ void drain(WarpSmem &S, bool last, int &pc_head,
                                       int &pc_n, RangeRing &rf, RangeRing &rn,
@@ -536,7 +610,7 @@ __device__ __forceinline__ void drain(WarpSmem &S, bool last, int &pc_head,
                                       int k0, int k1, const ForceConsts &kg,
                                       GroupAcc<POT> &A, int lane, const Rec &R)
 {
-    while (pc_n >= (last ? 1 : CTILE))
+    while (last && pc_n >= 1)  // during the walk full cell tiles are requested
         cell_tile<POT, TWO, REC>(S, pc_head, pc_n, min(pc_n, CTILE), cf0, cf1,
                                  cf2, P, kg.eps2, A, lane, R);
     while (rf.np >= (last ? 1 : PTILE))
@@ -555,14 +629,6 @@ __device__ __forceinline__ void prefetch_l2(const void *ptr, size_t bytes,
     const char *p = (const char *)ptr;
     for (size_t off = t * 128; off < bytes; off += nt * 128)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
-}
-
-// Asynchronous 16-byte copy global -> shared (cp.async; no register holds
-// the data while it is in flight).
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
 }
 
 // Pops child ranges from the top of the walk stack until they hold at most
@@ -695,6 +761,7 @@ k_walk_force(const int *__restrict__ gclus,
         // register holds them.  The batches, and so the tiles, are those of
         // the plain loop (pop, test, push, evaluate), in the same order.
         int total = pop_batch(S, top, wmin, wmax, lane);
+        bool pend = false;  // a cell tile's records requested into S.raw
         while (total > 0) {
             if (++iter > lim_walk) {  // a finite tree stays far below the default
                 timeout = true;
@@ -760,7 +827,17 @@ k_walk_force(const int *__restrict__ gclus,
             __syncwarp();
             // the next batch, requested now
             total = pop_batch(S, top, wmin, wmax, lane);
-            // evaluate every full tile
+            // the cell tile requested one iteration ago, then the next one
+            if (pend) {
+                if (two) cell_raw_tile<POT, true>(S, P, kg.eps2, A, lane);
+                else cell_raw_tile<POT, false>(S, P, kg.eps2, A, lane);
+                pend = false;
+            }
+            if (pc_n >= CTILE) {
+                cell_request<REC>(S, pc_head, pc_n, cf0, cf1, cf2, lane, R);
+                pend = true;
+            }
+            // evaluate every full particle tile
             if (two)
                 drain<POT, true, REC>(S, false, pc_head, pc_n, rf, rn, cf0, cf1,
                                       cf2, phi, plo, P, k0, k1, kg, A, lane, R);
@@ -775,7 +852,13 @@ k_walk_force(const int *__restrict__ gclus,
             if (lane == 0) p3t_raise(st, timeout ? P3T_ERR_TIMEOUT : P3T_ERR_CAPACITY);
             continue;
         }
-        // the partial tiles left over
+        // the requested tile and the partial tiles left over
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
+        if (pend) {
+            if (two) cell_raw_tile<POT, true>(S, P, kg.eps2, A, lane);
+            else cell_raw_tile<POT, false>(S, P, kg.eps2, A, lane);
+        }
         if (two)
             drain<POT, true, REC>(S, true, pc_head, pc_n, rf, rn, cf0, cf1, cf2,
                                   phi, plo, P, k0, k1, kg, A, lane, R);
