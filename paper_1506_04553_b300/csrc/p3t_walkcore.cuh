@@ -16,11 +16,13 @@
 namespace p3t_walk {
 
 constexpr int STACK = 768;  // child ranges per warp
-constexpr int RING = 64;    // ring capacity; at most 63 entries are held
+constexpr int RING = 128;   // ring capacity; at most 95 entries are held
+constexpr int WB = 64;      // cells per walk batch (two per lane)
 
 struct __align__(16) Smem {
     int stack[STACK];               // packed child ranges: child*8 + nchild-1
-    int cb[32];                     // cells of the current walk batch
+    int cb[WB];                     // cells of the current walk batch
+    float4 box[2][WB];              // their box records (wmin, wmax), by slot
     int pc[RING];                   // accepted cells
     int2 pf[RING];                  // far leaf ranges (first, count)
     int2 pn[RING];                  // near leaf ranges
@@ -95,17 +97,24 @@ __device__ __forceinline__ void take_cells(Smem &S, CellRing &r, int take,
     r.n -= take;
 }
 
-// Pops child ranges from the top of the stack until they hold at most 32
-// cells; returns this lane's cell of the batch (-1 past its end) and the
-// batch size in total (warp-uniform, 0 when the stack is empty).
-__device__ __forceinline__ int pop_batch(Smem &S, int &top, int &total,
+// Asynchronous 16-byte copy global -> shared (cp.async).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
+}
+
+// Pops child ranges from the top of the stack until they hold at most WB =
+// 64 cells, lists them in S.cb and requests their box records into S.box
+// with cp.async; returns the batch size (warp-uniform, 0 when the stack is
+// empty).  The lane's cells are slots lane and lane + 32.
+__device__ __forceinline__ int pop_batch(Smem &S, int &top,
+                                         const float4 *__restrict__ wmin,
+                                         const float4 *__restrict__ wmax,
                                          int lane)
 {
     const unsigned full = 0xffffffffu;
-    if (top == 0) {
-        total = 0;
-        return -1;
-    }
+    if (top == 0) return 0;
     int rx = 0, ry = 0;
     if (lane < top) {
         int e = S.stack[top - 1 - lane];
@@ -113,16 +122,24 @@ __device__ __forceinline__ int pop_batch(Smem &S, int &top, int &total,
         ry = (e & 7) + 1;
     }
     int inc = warp_incl_scan(ry);
-    bool take = lane < top && inc <= 32;
+    bool take = lane < top && inc <= WB;
     int ntake = __popc(__ballot_sync(full, take));
-    total = __shfl_sync(full, inc, ntake - 1);
+    const int total = __shfl_sync(full, inc, ntake - 1);
     if (take)
         for (int t = 0; t < ry; ++t) S.cb[inc - ry + t] = rx + t;
     top -= ntake;
     __syncwarp();
-    const int c = lane < total ? S.cb[lane] : -1;
-    __syncwarp();
-    return c;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int slot = lane + 32 * h;
+        if (slot < total) {
+            const int c = S.cb[slot];
+            cp_async16(&S.box[0][slot], wmin + c);
+            cp_async16(&S.box[1][slot], wmax + c);
+        }
+    }
+    asm volatile("cp.async.commit_group;");
+    return total;
 }
 
 // Walks the tree of cell `root` (the group's cluster) for one group.  The
@@ -132,11 +149,13 @@ __device__ __forceinline__ int pop_batch(Smem &S, int &top, int &total,
 // Returns P3T_OK, P3T_ERR_CAPACITY when the stack overflowed or
 // P3T_ERR_TIMEOUT after lim iterations (the group is left unfinished).
 // cnt[0..2] receive the numbers of cells, near and far particles met.  The
-// walk is software-pipelined by one batch: the next batch is popped and its
-// box records requested before the full tiles are evaluated (the batches and
-// tiles are those of the plain pop-test-push-evaluate loop, in its order).
-// A leaf's box records carry its particle range (first particle in
-// wmin.w, minus the count in wmax.w), so no second load is needed.
+// walk takes batches of up to 64 cells (two per lane) and is
+// software-pipelined by one batch: the next batch is popped and its box
+// records copied into shared memory by cp.async before the full tiles are
+// evaluated (the batches and tiles are those of the plain
+// pop-test-push-evaluate loop, in its order).  A leaf's box records carry
+// its particle range (first particle in wmin.w, minus the count in wmax.w),
+// so no second load is needed.
 template <class Ev>
 __device__ __forceinline__ int walk_group(
     Smem &S, float4 gmn, float4 gmx, const float4 *__restrict__ wmin,
@@ -150,62 +169,70 @@ __device__ __forceinline__ int walk_group(
     int top = 1;
     long long iter = 0;
     __syncwarp();
-    int total = 0;
-    int c = pop_batch(S, top, total, lane);
-    float4 cmn = make_float4(0.f, 0.f, 0.f, 0.f), cmx = cmn;
-    if (c >= 0) {
-        cmn = wmin[c];
-        cmx = wmax[c];
-    }
+    int total = pop_batch(S, top, wmin, wmax, lane);
+    int status = P3T_OK;
     while (total > 0) {
-        if (++iter > lim) return P3T_ERR_TIMEOUT;  // a finite tree stays far below
-        bool is_pc = false, near = false, farl = false, open = false;
-        int child = 0, nchild = 0, pfirst = 0, pcount = 0;
-        if (c >= 0) {
-            float d2 = box_d2(gmn, gmx, cmn, cmx);
-            float l = box_side(cmn, cmx);
-            if (mac_accept(d2, l, theta2, hg2)) {
-                is_pc = true;
-            } else {
-                child = __float_as_int(cmn.w);
-                nchild = __float_as_int(cmx.w);
-                if (nchild <= 0) {  // a leaf: first particle, -count
-                    pfirst = child;
-                    pcount = -nchild;
-                    near = d2 <= hg2;
-                    farl = !near;
+        if (++iter > lim) {  // a finite tree stays far below
+            status = P3T_ERR_TIMEOUT;
+            break;
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
+        bool is_pc[2], near[2], farl[2], open[2];
+        int cid[2], child[2], nchild[2], pfirst[2], pcount[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int slot = lane + 32 * h;
+            is_pc[h] = near[h] = farl[h] = open[h] = false;
+            cid[h] = slot < total ? S.cb[slot] : -1;
+            child[h] = nchild[h] = pfirst[h] = pcount[h] = 0;
+            if (cid[h] >= 0) {
+                const float4 cmn = S.box[0][slot], cmx = S.box[1][slot];
+                float d2 = box_d2(gmn, gmx, cmn, cmx);
+                float l = box_side(cmn, cmx);
+                if (mac_accept(d2, l, theta2, hg2)) {
+                    is_pc[h] = true;
                 } else {
-                    open = true;
+                    child[h] = __float_as_int(cmn.w);
+                    nchild[h] = __float_as_int(cmx.w);
+                    if (nchild[h] <= 0) {  // a leaf: first particle, -count
+                        pfirst[h] = child[h];
+                        pcount[h] = -nchild[h];
+                        near[h] = d2 <= hg2;
+                        farl[h] = !near[h];
+                    } else {
+                        open[h] = true;
+                    }
                 }
             }
         }
-        {
-            unsigned m = __ballot_sync(full, is_pc);
-            if (is_pc) S.pc[(rc.head + rc.n + __popc(m & lt)) & (RING - 1)] = c;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            unsigned m = __ballot_sync(full, is_pc[h]);
+            if (is_pc[h]) S.pc[(rc.head + rc.n + __popc(m & lt)) & (RING - 1)] = cid[h];
             rc.n += __popc(m);
             cnt[0] += __popc(m);
-        }
-        {
             int before = rn.np;
-            push_ranges(S.pn, rn, near, pfirst, pcount);
+            push_ranges(S.pn, rn, near[h], pfirst[h], pcount[h]);
             cnt[1] += rn.np - before;
             before = rf.np;
-            push_ranges(S.pf, rf, farl, pfirst, pcount);
+            push_ranges(S.pf, rf, farl[h], pfirst[h], pcount[h]);
             cnt[2] += rf.np - before;
         }
-        {
-            unsigned mo = __ballot_sync(full, open);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            unsigned mo = __ballot_sync(full, open[h]);
             int np = __popc(mo);
-            if (top + np > STACK) return P3T_ERR_CAPACITY;
-            if (open) S.stack[top + __popc(mo & lt)] = child * 8 + (nchild - 1);
+            if (top + np > STACK) {
+                status = P3T_ERR_CAPACITY;
+                break;
+            }
+            if (open[h]) S.stack[top + __popc(mo & lt)] = child[h] * 8 + (nchild[h] - 1);
             top += np;
         }
+        if (status != P3T_OK) break;
         __syncwarp();
-        c = pop_batch(S, top, total, lane);
-        if (c >= 0) {
-            cmn = wmin[c];
-            cmx = wmax[c];
-        }
+        total = pop_batch(S, top, wmin, wmax, lane);
         while (rc.n >= 32) {
             take_cells(S, rc, 32, lane);
             ev.cells(S, 32);
@@ -218,6 +245,12 @@ __device__ __forceinline__ int walk_group(
             take_particles(S.pn, rn, 32, S.tj, lane);
             ev.template particles<true>(S, 32);
         }
+    }
+    if (status != P3T_OK) {
+        // the abandoned batch's copies land before S.box is reused
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
+        return status;
     }
     if (rc.n > 0) {
         const int t = rc.n;
