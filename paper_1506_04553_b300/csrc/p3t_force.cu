@@ -621,16 +621,6 @@ __device__ __forceinline__ void drain(WarpSmem &S, bool last, int &pc_head,
                                            plo, P, k0, k1, kg, A, lane, R);
 }
 
-// Prefetches [ptr, ptr + bytes) into L2, one 128-byte line per request,
-// lines t, t + nt, ... of the range.
-__device__ __forceinline__ void prefetch_l2(const void *ptr, size_t bytes,
-                                            size_t t, size_t nt)
-{
-    const char *p = (const char *)ptr;
-    for (size_t off = t * 128; off < bytes; off += nt * 128)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
-}
-
 // Pops child ranges from the top of the walk stack until they hold at most
 // WB = 64 cells, lists them in S.cb and requests their box records into
 // S.box with cp.async; returns the batch size (warp-uniform, 0 when the
@@ -692,23 +682,6 @@ k_walk_force(const int *__restrict__ gclus,
     WarpSmem &S = smem[w];
     if (st->error) return;  // no valid tree
     const int G = st->ngroup;
-    {
-        // Warm L2 with the records every walk reads (the cells' box and
-        // force records, the particles' FP32 copies, ~80 B per cell and 32 B
-        // per particle), spread over all threads before the first group:
-        // after a build has streamed other data through L2, the walks' first
-        // touches of a record then hit L2 instead of waiting for HBM.
-        const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-        const size_t nt = (size_t)gridDim.x * blockDim.x;
-        const size_t nc = (size_t)st->ncell;
-        prefetch_l2(wmin, nc * sizeof(float4), t, nt);
-        prefetch_l2(wmax, nc * sizeof(float4), t, nt);
-        prefetch_l2(cf0, nc * sizeof(float4), t, nt);
-        prefetch_l2(cf1, nc * sizeof(float4), t, nt);
-        prefetch_l2(cf2, nc * sizeof(float4), t, nt);
-        prefetch_l2(phi, (size_t)n * sizeof(float4), t, nt);
-        prefetch_l2(plo, (size_t)n * sizeof(float4), t, nt);
-    }
     for (;;) {
         int g = 0;
         if (lane == 0) g = (int)atomicAdd(&st->work, 1u);
