@@ -19,13 +19,16 @@
 //
 // k_walk_vjp walks each group exactly as the force kernel does (shared
 // walk in p3t_walkcore.cuh, so the interaction sets are recomputed, not
-// stored).  For every tile of up to 32 sources each lane owns one source and
-// sweeps the group's particles (staged once per group in shared memory) two
-// at a time with FP32x2 instructions, in group-relative coordinates.  The
-// source's adjoints stay in the lane's registers and go to FP64 atomics once
-// per tile; the particle-side products (3 per particle) are summed over the
-// lanes by a warp reduce-scatter, four particle pairs at a time, and kept by
-// the particle's owner lane in two-sum (hi, lo) FP32 accumulators.
+// stored).  The group's particles are staged once per group in shared
+// memory, in group-relative coordinates.  For a tile of up to 64 sources
+// (cells, or particles of leaves) each lane owns two sources, held as the
+// two halves of every FP32x2 operand, and sweeps the particles one at a time
+// (each broadcast to both halves).  The sources' adjoints stay in the lane's
+// registers and go to FP64 atomics once per tile; the particle-side products
+// (3 per particle, the lane's two sources added) are summed over the lanes
+// by a warp reduce-scatter, four particles at a time, and kept by the
+// particle's owner lane in two-sum (hi, lo) FP32 accumulators.  Two sources
+// per lane halve the reduce-scatter per source and particle.
 // The cell adjoints then reach the member particles in FP64: with
 // T = 3 S - tr(S) I and e = x_k - com (so 6 S e - 2 tr(S) e = 2 T e and
 // 3 e.S.e - |e|^2 tr(S) = e.T.e), the sums over a particle's ancestors are
@@ -43,16 +46,17 @@ namespace {
 
 using p3t_walk::Smem;
 
-// warps per block of k_walk_vjp: a template parameter (2 or 4), chosen per
-// context by the autotuner; 4 by default
-#ifndef P3T_VJP_NSP
-#define P3T_VJP_NSP 4
-#endif
 #ifndef P3T_VJP_MIN_BLOCKS
 #define P3T_VJP_MIN_BLOCKS 0
 #endif
-constexpr int NSP = P3T_VJP_NSP;  // particle pairs per i-side reduce-scatter
-constexpr int GMAX = 64; // particle slots of a group
+// The warps per block of k_walk_vjp are a template parameter (2 or 4),
+// chosen per context by the autotuner; 4 by default.
+// Particles per i-side reduce-scatter.  Eight would save 1.5 instructions
+// per particle, but the eight-fold unrolled tiles no longer fit the
+// instruction cache (stalls for lack of an instruction: 0.35 -> 1.2 per
+// issue, 30.9 -> 33.8 ms at 2^20).
+constexpr int NPC = 4;
+constexpr int GMAX = 64;  // particle slots of a group
 
 struct VjpConsts {
     float eps2, kA, kB;
@@ -144,12 +148,12 @@ __device__ __forceinline__ float pick(const float (&a)[NV], int v)
 }
 
 // The group's particles, staged once per group: negated group-relative
-// positions and weights, slot = particle index in the group, stored
-// pair-interleaved (slots 2p and 2p+1 fill 12 consecutive floats: nx, ny,
-// nz, wx, wy, wz of both), so that three 128-bit loads give a particle
-// pair; and the particle-side tile sums.
+// positions and weights, slot = particle index in the group, each value
+// duplicated (slot p fills 12 floats: nx, nx, ny, ny, ..., wz, wz), so that
+// three 128-bit loads give a particle as broadcast pairs; and the
+// particle-side tile sums.
 struct __align__(16) VjpSmem {
-    float pp[GMAX * 6];
+    float pd[GMAX * 12];
     float ts[3][GMAX];
 };
 
@@ -157,23 +161,20 @@ __device__ __forceinline__ void stage_slot(VjpSmem *V, int slot, float nx,
                                            float ny, float nz, float wx,
                                            float wy, float wz)
 {
-    float *q = V->pp + (slot >> 1) * 12 + (slot & 1);
-    q[0] = nx;
-    q[2] = ny;
-    q[4] = nz;
-    q[6] = wx;
-    q[8] = wy;
-    q[10] = wz;
+    float4 *d = reinterpret_cast<float4 *>(V->pd) + slot * 3;
+    d[0] = make_float4(nx, nx, ny, ny);
+    d[1] = make_float4(nz, nz, wx, wx);
+    d[2] = make_float4(wy, wy, wz, wz);
 }
 
-// Particle pair j, j + 1 (j even) as broadcast-free pairs.
+// A particle as broadcast pairs.
 struct PPair {
     f2 nx, ny, nz, wx, wy, wz;
 };
 
-__device__ __forceinline__ PPair load_pair(const VjpSmem *V, int j)
+__device__ __forceinline__ PPair load_dup(const VjpSmem *V, int j)
 {
-    const float4 *t4 = reinterpret_cast<const float4 *>(V->pp) + (j >> 1) * 3;
+    const float4 *t4 = reinterpret_cast<const float4 *>(V->pd) + j * 3;
     const float4 A = t4[0], B = t4[1], C = t4[2];
     PPair r;
     r.nx = make_float2(A.x, A.y);
@@ -185,13 +186,13 @@ __device__ __forceinline__ PPair load_pair(const VjpSmem *V, int j)
     return r;
 }
 
-// One cell (broadcast pairs) against two particles (the pair's halves).
+// Two cells (the halves) against one particle (broadcast pairs).
 struct CellSrc {
     f2 X, Y, Z, M, M3, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz;  // M3 = -3 M
 };
 
-// J^T w for the pair (jx, jy, jz) and the cell adjoints
-// acc = (dL/dM, dL/dcom xyz, 2S xx yy zz xy xz yz), all without G.
+// J^T w per half (jx, jy, jz) and the cell adjoints
+// acc = (dL/dM, dL/dcom xyz, 2S xx yy zz xy xz yz) per half, all without G.
 __device__ __forceinline__ void cell_pair(const CellSrc &c, f2 nx, f2 ny,
                                           f2 nz, f2 wx, f2 wy, f2 wz, f2 eps2,
                                           f2 (&acc)[10], f2 &jx, f2 &jy,
@@ -240,14 +241,14 @@ __device__ __forceinline__ void cell_pair(const CellSrc &c, f2 nx, f2 ny,
     acc[9] = fma2(dy, uz, fma2(vy, dz, acc[9]));
 }
 
-// One source particle (broadcast pairs) against two particles.
+// Two source particles (the halves) against one particle (broadcast pairs).
 struct PartSrc {
     f2 X, Y, Z, m;
 };
 
-// J w for the pair (jx, jy, jz) and the source adjoints
-// acc = (dL/dx_j xyz, dL/dm_j), all without G.  selfx / selfy: the half's
-// particle is the source itself (contributes 0).
+// J w per half (jx, jy, jz) and the source adjoints acc = (dL/dx_j xyz,
+// dL/dm_j) per half, all without G.  selfx / selfy: the half's source is the
+// particle itself (contributes 0).
 template <bool NEAR>
 __device__ __forceinline__ void pair_pair(const PartSrc &p, f2 nx, f2 ny,
                                           f2 nz, f2 wx, f2 wy, f2 wz,
@@ -301,7 +302,7 @@ __device__ __forceinline__ void pair_pair(const PartSrc &p, f2 nx, f2 ny,
 // Per-lane state of one group.  Lane l owns particle slots l and l + 32.
 struct VjpEval {
     VjpSmem *V;
-    int lane, gfirst, npairs;  // npairs: particle pairs swept (multiple of NSP)
+    int lane, gfirst, npart;  // npart: particles swept (multiple of NPC)
     float4 ct;
     float ih[2][3], il[2][3];  // owner's dL/dx sums (without G, sign: + J w)
     const float4 *phi, *plo, *cf0, *cf1, *cf2;
@@ -310,16 +311,14 @@ struct VjpEval {
     int n;
     VjpConsts k;
 
-    // Particle-side products of NSP pairs starting at pair ch: summed over
-    // the lanes and stored in the tile sums.
-    __device__ __forceinline__ void flush(float (&r)[NSP][6], int ch)
+    // Particle-side products of NPC particles starting at particle ch (the
+    // lane's two sources already added): summed over the lanes and stored
+    // in the tile sums.
+    __device__ __forceinline__ void flush(float (&r)[NPC][3], int ch)
     {
-        reduce_scatter<NSP, 6>(r, lane);
-        const int v = lane & (32 / NSP - 1);
-        if (v < 6) {
-            const int slot = 2 * (ch + src_of<NSP>(lane)) + (v >= 3 ? 1 : 0);
-            V->ts[v % 3][slot] = pick<6>(r[0], v);
-        }
+        reduce_scatter<NPC, 3>(r, lane);
+        const int v = lane & (32 / NPC - 1);
+        if (v < 3) V->ts[v][ch + src_of<NPC>(lane)] = pick<3>(r[0], v);
     }
 
     // The owners add the tile sums of their particles.
@@ -334,102 +333,139 @@ struct VjpEval {
         __syncwarp();
     }
 
-    // Cell tile: ids in S.tj[0..take); lane j owns cell j.
+    // Cell tile: ids in S.tj[0..take), take <= 64; lane l owns cells l and
+    // l + 32, the halves of every FP32x2 operand.
     __device__ __forceinline__ void cells(Smem &S, int take)
     {
-        CellSrc c;
-        int cid = -1;
-        if (lane < take) {
-            cid = S.tj[lane];
-            const float4 a = cf0[cid], bb = cf1[cid], cc = cf2[cid];
-            c.X = dup2(__fadd_rn(__fsub_rn(a.x, ct.x), bb.x));
-            c.Y = dup2(__fadd_rn(__fsub_rn(a.y, ct.y), bb.y));
-            c.Z = dup2(__fadd_rn(__fsub_rn(a.z, ct.z), bb.z));
-            c.M = dup2(a.w);
-            c.M3 = dup2(-3.0f * a.w);
-            c.Qxx = dup2(bb.w);
-            c.Qyy = dup2(cc.x);
-            c.Qzz = dup2(-(bb.w + cc.x));
-            c.Qxy = dup2(cc.y);
-            c.Qxz = dup2(cc.z);
-            c.Qyz = dup2(cc.w);
-        } else {
-            c.X = c.Y = c.Z = dup2(-PAD);
-            c.M = c.M3 = c.Qxx = c.Qyy = c.Qzz = c.Qxy = c.Qxz = c.Qyz = dup2(0.0f);
+        float v[2][11];  // X Y Z M -3M Qxx Qyy Qzz Qxy Qxz Qyz
+        int cid[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int slot = lane + 32 * h;
+            cid[h] = slot < take ? S.tj[slot] : -1;
+            if (cid[h] >= 0) {
+                const float4 a = cf0[cid[h]], bb = cf1[cid[h]], cc = cf2[cid[h]];
+                v[h][0] = __fadd_rn(__fsub_rn(a.x, ct.x), bb.x);
+                v[h][1] = __fadd_rn(__fsub_rn(a.y, ct.y), bb.y);
+                v[h][2] = __fadd_rn(__fsub_rn(a.z, ct.z), bb.z);
+                v[h][3] = a.w;
+                v[h][4] = -3.0f * a.w;
+                v[h][5] = bb.w;
+                v[h][6] = cc.x;
+                v[h][7] = -(bb.w + cc.x);
+                v[h][8] = cc.y;
+                v[h][9] = cc.z;
+                v[h][10] = cc.w;
+            } else {
+                v[h][0] = v[h][1] = v[h][2] = -PAD;
+#pragma unroll
+                for (int q = 3; q < 11; ++q) v[h][q] = 0.0f;
+            }
         }
+        CellSrc c;
+        c.X = make_float2(v[0][0], v[1][0]);
+        c.Y = make_float2(v[0][1], v[1][1]);
+        c.Z = make_float2(v[0][2], v[1][2]);
+        c.M = make_float2(v[0][3], v[1][3]);
+        c.M3 = make_float2(v[0][4], v[1][4]);
+        c.Qxx = make_float2(v[0][5], v[1][5]);
+        c.Qyy = make_float2(v[0][6], v[1][6]);
+        c.Qzz = make_float2(v[0][7], v[1][7]);
+        c.Qxy = make_float2(v[0][8], v[1][8]);
+        c.Qxz = make_float2(v[0][9], v[1][9]);
+        c.Qyz = make_float2(v[0][10], v[1][10]);
         __syncwarp();  // S.tj is rewritten by the walk after the tile
         f2 acc[10];
 #pragma unroll
-        for (int v = 0; v < 10; ++v) acc[v] = dup2(0.0f);
+        for (int q = 0; q < 10; ++q) acc[q] = dup2(0.0f);
         const f2 e2 = dup2(k.eps2);
-        for (int ch = 0; ch < npairs; ch += NSP) {
-            float r[NSP][6];
+        for (int ch = 0; ch < npart; ch += NPC) {
+            float r[NPC][3];
 #pragma unroll
-            for (int u = 0; u < NSP; ++u) {
-                const int j = 2 * (ch + u);
+            for (int u = 0; u < NPC; ++u) {
                 f2 jx, jy, jz;
-                const PPair q = load_pair(V, j);
+                const PPair q = load_dup(V, ch + u);
                 cell_pair(c, q.nx, q.ny, q.nz, q.wx, q.wy, q.wz, e2, acc, jx, jy,
                           jz);
-                r[u][0] = jx.x; r[u][1] = jy.x; r[u][2] = jz.x;
-                r[u][3] = jx.y; r[u][4] = jy.y; r[u][5] = jz.y;
+                r[u][0] = __fadd_rn(jx.x, jx.y);
+                r[u][1] = __fadd_rn(jy.x, jy.y);
+                r[u][2] = __fadd_rn(jz.x, jz.y);
             }
             flush(r, ch);
         }
         tile_end();
-        if (cid >= 0) {
-            double *dst = cadj + (size_t)cid * 10;
 #pragma unroll
-            for (int v = 0; v < 10; ++v)
-                atomicAdd(dst + v, k.G * (double)(acc[v].x + acc[v].y));
+        for (int h = 0; h < 2; ++h) {
+            if (cid[h] >= 0) {
+                double *dst = cadj + (size_t)cid[h] * 10;
+#pragma unroll
+                for (int q = 0; q < 10; ++q)
+                    atomicAdd(dst + q, k.G * (double)(h == 0 ? acc[q].x : acc[q].y));
+            }
         }
     }
 
-    // Particle tile: sorted ids in S.tj[0..take); lane j owns source j.
+    // Particle tile: ids in S.tj[0..take), take <= 64; lane l owns sources
+    // l and l + 32, the halves of every FP32x2 operand.
     template <bool NEAR>
     __device__ __forceinline__ void particles(Smem &S, int take)
     {
-        PartSrc p;
-        int sj = -1;
-        if (lane < take) {
-            sj = S.tj[lane];
-            const float4 a = rel(phi[sj], plo[sj], ct);
-            p.X = dup2(a.x);
-            p.Y = dup2(a.y);
-            p.Z = dup2(a.z);
-            p.m = dup2(a.w);
-        } else {
-            p.X = p.Y = p.Z = dup2(-PAD);
-            p.m = dup2(0.0f);
+        float v[2][4];  // X Y Z m
+        int sj[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int slot = lane + 32 * h;
+            sj[h] = slot < take ? S.tj[slot] : -1;
+            if (sj[h] >= 0) {
+                const float4 a = rel(phi[sj[h]], plo[sj[h]], ct);
+                v[h][0] = a.x;
+                v[h][1] = a.y;
+                v[h][2] = a.z;
+                v[h][3] = a.w;
+            } else {
+                v[h][0] = v[h][1] = v[h][2] = -PAD;
+                v[h][3] = 0.0f;
+            }
         }
-        __syncwarp();
+        PartSrc p;
+        p.X = make_float2(v[0][0], v[1][0]);
+        p.Y = make_float2(v[0][1], v[1][1]);
+        p.Z = make_float2(v[0][2], v[1][2]);
+        p.m = make_float2(v[0][3], v[1][3]);
+        __syncwarp();  // S.tj is rewritten by the walk after the tile
         f2 acc[4];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v] = dup2(0.0f);
+        for (int q = 0; q < 4; ++q) acc[q] = dup2(0.0f);
         const f2 e2 = dup2(k.eps2), kA = dup2(k.kA), kB = dup2(k.kB);
-        const int self = sj - gfirst;  // the source's slot if it is in the group
-        for (int ch = 0; ch < npairs; ch += NSP) {
-            float r[NSP][6];
+        // the sources' slots if they are in the group (else negative)
+        const int self0 = sj[0] - gfirst, self1 = sj[1] - gfirst;
+        for (int ch = 0; ch < npart; ch += NPC) {
+            float r[NPC][3];
 #pragma unroll
-            for (int u = 0; u < NSP; ++u) {
-                const int j = 2 * (ch + u);
+            for (int u = 0; u < NPC; ++u) {
+                const int j = ch + u;
                 f2 jx, jy, jz;
-                const PPair q = load_pair(V, j);
+                const PPair q = load_dup(V, j);
                 pair_pair<NEAR>(p, q.nx, q.ny, q.nz, q.wx, q.wy, q.wz,
-                                self == j, self == j + 1, e2, kA, kB, acc, jx,
+                                self0 == j, self1 == j, e2, kA, kB, acc, jx,
                                 jy, jz);
-                r[u][0] = jx.x; r[u][1] = jy.x; r[u][2] = jz.x;
-                r[u][3] = jx.y; r[u][4] = jy.y; r[u][5] = jz.y;
+                r[u][0] = __fadd_rn(jx.x, jx.y);
+                r[u][1] = __fadd_rn(jy.x, jy.y);
+                r[u][2] = __fadd_rn(jz.x, jz.y);
             }
             flush(r, ch);
         }
         tile_end();
-        if (sj >= 0) {
-            const int o = order[sj];
 #pragma unroll
-            for (int v = 0; v < 3; ++v)
-                atomicAdd(gpos + (size_t)v * n + o, k.G * (double)(acc[v].x + acc[v].y));
-            atomicAdd(gmass + o, k.G * (double)(acc[3].x + acc[3].y));
+        for (int h = 0; h < 2; ++h) {
+            if (sj[h] >= 0) {
+                const int o = order[sj[h]];
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    atomicAdd(gpos + (size_t)q * n + o,
+                              k.G * (double)(h == 0 ? acc[q].x : acc[q].y));
+                atomicAdd(gmass + o, k.G * (double)(h == 0 ? acc[3].x : acc[3].y));
+            }
         }
     }
 };
@@ -469,7 +505,7 @@ k_walk_vjp(const int *__restrict__ gclus,
         ev.V = &vsm[wi];
         ev.lane = lane;
         ev.gfirst = gr.x;
-        ev.npairs = ((gr.y + 2 * NSP - 1) / (2 * NSP)) * NSP;
+        ev.npart = ((gr.y + NPC - 1) / NPC) * NPC;
         ev.ct = gctr[g];
         // stage the group's particles; slots past the group are padding
         __syncwarp();  // the previous group's reads of vsm are done

@@ -3,21 +3,27 @@
 //
 // The warp keeps a stack of child ranges (first child, number of children)
 // in shared memory.  Each iteration pops ranges from the top until they hold
-// at most 32 cells, tests one cell per lane with the opening test of
+// at most 64 cells, tests two cells per lane with the opening test of
 // p3t_internal.cuh, and sends what it finds to three rings in shared memory:
 // accepted cells, far leaf ranges (K = 1) and near leaf ranges (K < 1
-// possible).  Whenever a ring holds 32 sources the caller's evaluator is
-// invoked on a tile of 32; the partial tiles are evaluated when the walk
-// ends.  The traversal and the test are those of the list walk in
-// p3t_walk.cu, so the sources met are the same sets.
+// possible).  Whenever a ring holds a tile (64 cells or 64 particles) the
+// caller's evaluator is invoked on it; the partial tiles are evaluated
+// when the walk ends.  The traversal and the test are those of the list walk
+// in p3t_walk.cu, so the sources met are the same sets.
 #pragma once
 #include "p3t_internal.cuh"
 
 namespace p3t_walk {
 
 constexpr int STACK = 768;  // child ranges per warp
-constexpr int RING = 128;   // ring capacity; at most 95 entries are held
+constexpr int RING = 128;   // ring capacity; at most 127 entries are held
 constexpr int WB = 64;      // cells per walk batch (two per lane)
+constexpr int CTILE = 64;   // cells per tile (two per lane)
+constexpr int PTILE = 64;   // particles per tile (two per lane)
+// A ring holds less than a tile when a batch starts and gains at most one
+// entry per cell of the batch (a leaf range holds at least one particle).
+static_assert(RING >= CTILE - 1 + WB && RING >= PTILE - 1 + WB,
+              "ring too small for a tile plus a batch");
 
 struct __align__(16) Smem {
     int stack[STACK];               // packed child ranges: child*8 + nchild-1
@@ -26,7 +32,7 @@ struct __align__(16) Smem {
     int pc[RING];                   // accepted cells
     int2 pf[RING];                  // far leaf ranges (first, count)
     int2 pn[RING];                  // near leaf ranges
-    int tj[32];                     // ids of the staged sources
+    int tj[64];                     // ids of the sources of a tile
 };
 
 struct RangeRing {
@@ -87,11 +93,26 @@ __device__ __forceinline__ void take_particles(int2 *ring, RangeRing &r,
     r.np -= take;
 }
 
-// Moves the next `take` accepted cells into tj[0..take).
+// Moves the next `take` (<= PTILE) particle ids off the front of a ring of
+// ranges into tj[0..take), in rounds of 32.
+__device__ __forceinline__ void take_tile(int2 *ring, RangeRing &r, int take,
+                                          int *tj, int lane)
+{
+#pragma unroll
+    for (int h = 0; h < PTILE / 32; ++h)
+        if (take > 32 * h)
+            take_particles(ring, r, min(take - 32 * h, 32), tj + 32 * h, lane);
+}
+
+// Moves the next `take` (<= CTILE) accepted cells into tj[0..take).
 __device__ __forceinline__ void take_cells(Smem &S, CellRing &r, int take,
                                            int lane)
 {
-    if (lane < take) S.tj[lane] = S.pc[(r.head + lane) & (RING - 1)];
+#pragma unroll
+    for (int h = 0; h < CTILE / 32; ++h) {
+        const int slot = lane + 32 * h;
+        if (slot < take) S.tj[slot] = S.pc[(r.head + slot) & (RING - 1)];
+    }
     __syncwarp();
     r.head = (r.head + take) & (RING - 1);
     r.n -= take;
@@ -144,8 +165,9 @@ __device__ __forceinline__ int pop_batch(Smem &S, int &top,
 
 // Walks the tree of cell `root` (the group's cluster) for one group.  The
 // evaluator supplies
-//   ev.cells(S, take)            tile of `take` cells, ids in S.tj
-//   ev.particles<NEAR>(S, take)  tile of `take` particles, ids in S.tj
+//   ev.cells(S, take)            tile of `take` (<= CTILE) cells, ids in S.tj
+//   ev.particles<NEAR>(S, take)  tile of `take` (<= PTILE) particles, ids in
+//                                S.tj
 // Returns P3T_OK, P3T_ERR_CAPACITY when the stack overflowed or
 // P3T_ERR_TIMEOUT after lim iterations (the group is left unfinished).
 // cnt[0..2] receive the numbers of cells, near and far particles met.  The
@@ -233,17 +255,17 @@ __device__ __forceinline__ int walk_group(
         if (status != P3T_OK) break;
         __syncwarp();
         total = pop_batch(S, top, wmin, wmax, lane);
-        while (rc.n >= 32) {
-            take_cells(S, rc, 32, lane);
-            ev.cells(S, 32);
+        while (rc.n >= CTILE) {
+            take_cells(S, rc, CTILE, lane);
+            ev.cells(S, CTILE);
         }
-        while (rf.np >= 32) {
-            take_particles(S.pf, rf, 32, S.tj, lane);
-            ev.template particles<false>(S, 32);
+        while (rf.np >= PTILE) {
+            take_tile(S.pf, rf, PTILE, S.tj, lane);
+            ev.template particles<false>(S, PTILE);
         }
-        while (rn.np >= 32) {
-            take_particles(S.pn, rn, 32, S.tj, lane);
-            ev.template particles<true>(S, 32);
+        while (rn.np >= PTILE) {
+            take_tile(S.pn, rn, PTILE, S.tj, lane);
+            ev.template particles<true>(S, PTILE);
         }
     }
     if (status != P3T_OK) {
@@ -259,12 +281,12 @@ __device__ __forceinline__ int walk_group(
     }
     if (rf.np > 0) {
         const int t = rf.np;
-        take_particles(S.pf, rf, t, S.tj, lane);
+        take_tile(S.pf, rf, t, S.tj, lane);
         ev.template particles<false>(S, t);
     }
     if (rn.np > 0) {
         const int t = rn.np;
-        take_particles(S.pn, rn, t, S.tj, lane);
+        take_tile(S.pn, rn, t, S.tj, lane);
         ev.template particles<true>(S, t);
     }
     return P3T_OK;
