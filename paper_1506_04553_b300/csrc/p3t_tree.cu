@@ -424,7 +424,11 @@ __device__ __forceinline__ void emit_children(int c, int L, int cap,
     node[c].w = (L << 8) | k;
 }
 
-constexpr int BIG_CELL = 2048;  // above: 32-ary searches; below: one scan
+// Above BIG_CELL particles a cell's child boundaries come from 32-ary
+// searches (at most 5 rounds of loads at 2^20), below from one coalesced
+// scan (at most 2 rounds of 8 x 32 keys); 512 took the split levels of a
+// 2^20 build from 0.267 to 0.255 ms against 2048 (same-box A/B).
+constexpr int BIG_CELL = 512;
 
 // Level L in two passes over its cells: one thread per cell files the
 // cells holding at most n_leaf particles in the leaf list (one aggregated
@@ -731,7 +735,13 @@ __device__ void cell_moments(int c, int4 nd, const double *__restrict__ xs,
 // computes the parent from all its children, in child order, and climbs on;
 // the others stop.  Every cell is computed once, by whichever thread comes
 // last, with the same arithmetic: the result does not depend on the order.
-__global__ void __launch_bounds__(TB)
+// Threads per block of k_moments_up.  A block stays resident until its
+// slowest thread has climbed, so small blocks let finished threads' slots
+// take new leaves sooner: 64 took the moments of a 2^20 build from 0.308 to
+// 0.280 ms against 256 (same-box A/B).
+constexpr int MB = 64;
+
+__global__ void __launch_bounds__(MB)
 k_moments_up(const double *__restrict__ xs, const double *__restrict__ ms,
              int n, const int4 *__restrict__ node, const int *__restrict__ parent,
              const int *__restrict__ leaf_sorted, int *cpend, double *cM,
@@ -742,7 +752,7 @@ k_moments_up(const double *__restrict__ xs, const double *__restrict__ ms,
 {
     if (st->error) return;
     const int nl = st->nleaf;
-    for (int q = blockIdx.x * TB + threadIdx.x; q < nl; q += gridDim.x * TB) {
+    for (int q = blockIdx.x * MB + threadIdx.x; q < nl; q += gridDim.x * MB) {
         int c = leaf_sorted[q];
         cell_moments(c, node[c], xs, ms, n, cM, ccom, cQ, cbmin, cbmax, wmin,
                      wmax, cf0, cf1, cf2);
@@ -1031,7 +1041,7 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
                                               c->leaf_sorted, c->st);
     p3t_prof_close(c, slot, s);
     slot = p3t_prof_open(c, P3T_PH_B_MOMENTS, s);
-    k_moments_up<<<c->sms * 8, TB, 0, s>>>(c->xs, c->ms, n, c->node, c->parent,
+    k_moments_up<<<c->sms * 8 * (TB / MB), MB, 0, s>>>(c->xs, c->ms, n, c->node, c->parent,
                                             c->leaf_sorted, c->cpend, c->cM,
                                             c->ccom, c->cQ, c->cbmin, c->cbmax,
                                             c->wmin, c->wmax, c->cf0, c->cf1,
