@@ -120,10 +120,10 @@ def force_and_neighbours(ctx, acc, off, idx, side):
     cur.wait_stream(side)
 
 
-def profile_traffic():
-    """Per-launch DRAM bytes of the force kernel from the committed ncu
-    summary (a line 'dram_bytes_per_launch: <float>'), else None."""
-    path = os.path.join(HERE, "profiles", "k_walk_force_plummer_1M.txt")
+def profile_traffic(name="k_walk_force_plummer_1M.txt"):
+    """Per-launch DRAM bytes of a kernel from its committed ncu summary (a
+    line 'dram_bytes_per_launch: <float>'), else None."""
+    path = os.path.join(HERE, "profiles", name)
     try:
         for line in open(path):
             if line.startswith("dram_bytes_per_launch:"):
@@ -763,7 +763,13 @@ def run_ours(args, world, rank, local):
         "kernel": "k_walk_vjp", "bound": "alu", "achieved": ach_b,
         "peak": peak, "unit": "TFLOP/s", "frac": ach_b / peak,
         "frac_of_measured": ach_b / fma_meas, "kernel_ms": vjp_ms,
-        "flops": flops_b, "traffic": None,
+        "flops": flops_b,
+        "traffic": profile_traffic("k_walk_vjp_plummer_1M.txt"),
+        "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one "
+                          "ncu capture of this kernel on this workload, read "
+                          "from the committed summary "
+                          "profiles/k_walk_vjp_plummer_1M.txt (not measured in "
+                          "this run); mostly the FP64 adjoint atomics",
         "note": f"{FLOPS_BWD_PC} / {FLOPS_BWD_PP_FAR} / {FLOPS_BWD_PP_NEAR} "
                 "flops per cell / far / near interaction (FMA = 2) x the "
                 "interaction counts of the same tree, over the kernel's CUDA-"
