@@ -341,13 +341,18 @@ k_comp_fill(int n, const long long *__restrict__ off, int *parent,
 //
 // Each class is a queue.  A component of more than 32 particles is one work
 // item (one warp, lanes over its members).  A class of s <= 32 particles
-// has one work item per floor(32 / s) components: a warp that packs that
-// many components side by side, one lane per particle, and takes the next
+// has work items of floor(32 / s) components: a warp that packs that many
+// components side by side, one lane per particle, and takes the next
 // component of the queue into a slot as soon as the slot's component is
 // done (so a warp stays with a class while its queue lasts, and items that
-// find the queue empty end at once).  The first item of every class is
-// handed out before all others, so that each class's deepest components
-// start at once; the rest follow class by class.
+// find the queue empty end at once).  Items go out in rounds: each round
+// gives every class a share of the warps proportional to its items (at
+// least one), so that the classes run side by side, each from its deepest
+// components on, and a warp meets the end of a queue about once per hard
+// step instead of once per class.  When a queue runs dry its warps' slots
+// idle until the warp's longest component is done; handed out class by
+// class, every warp met that drain at every class (30 % of the lanes of a
+// 2^20 hard step idle in it).
 //
 // FP64 on B300: one warp per SM sub-partition already keeps its FP64 unit
 // busy (a dependent add takes ~63 cycles, about the unit's time for one
@@ -365,12 +370,12 @@ constexpr int NS = 33;   // size classes: more than 32, then s = 32 .. 1
 constexpr int NB = NLB * NS;
 static_assert(NB == P3T_HERM_BUCKETS, "bucket scratch");
 static_assert(NB % 32 == 0, "one-warp scan");
-// bucket scratch (ints): counts, root starts (NB + 1), fill counters, starts
-// of the later items per class (NS + 1), queue heads per class, the classes
-// with a first item and their number (NS + 1), then a 64-bit counter
+// bucket scratch (ints): counts, root starts (NB + 1), fill counters, the
+// classes' shares of a round as exclusive prefix sums (NS + 1), queue heads
+// per class, the number of rounds (NS + 1 reserved), then a 64-bit counter
 constexpr int BK_COUNT = 0, BK_RSTART = NB, BK_RFILL = 2 * NB + 1,
-              BK_ISTART = 3 * NB + 1, BK_NEXT = 3 * NB + NS + 2,
-              BK_FIRST = 3 * NB + 2 * NS + 2,
+              BK_SHARE = 3 * NB + 1, BK_NEXT = 3 * NB + NS + 2,
+              BK_ROUNDS = 3 * NB + 2 * NS + 2,
               BK_WORK = (3 * NB + 3 * NS + 3 + 1) & ~1;
 static_assert(BK_WORK + 2 <= 2 * P3T_HERM_BUCKET_LL, "bucket scratch size");
 
@@ -414,13 +419,16 @@ k_root_hist(int n, const int *__restrict__ parent, const int *__restrict__ csize
         if (h[b]) atomicAdd(bk + BK_COUNT + b, h[b]);
 }
 
-// counts -> root starts and fill counters (exclusive); then the work items:
-// the first item of each nonempty class, then the later ones per class
-__global__ void k_root_scan(int *bk)
+// counts -> root starts and fill counters (exclusive); then the rounds of
+// work items: a class with c items (c components of more than 32
+// particles, else ceil(components / floor(32 / s))) gets
+// max(1, round(warps c / all items)) items per round, and there are as many
+// rounds as the class needing most takes
+__global__ void k_root_scan(int *bk, int warps)
 {
     constexpr int PER = NB / 32;
     const int *bcount = bk + BK_COUNT;
-    int *rstart = bk + BK_RSTART, *rfill = bk + BK_RFILL, *istart = bk + BK_ISTART;
+    int *rstart = bk + BK_RSTART, *rfill = bk + BK_RFILL, *share = bk + BK_SHARE;
     const int lane = threadIdx.x;
     int sr = 0;
     for (int q = 0; q < PER; ++q) sr += bcount[lane * PER + q];
@@ -434,18 +442,27 @@ __global__ void k_root_scan(int *bk)
     if (lane == 31) rstart[NB] = er;
     __syncwarp();
     if (lane == 0) {
-        int *first = bk + BK_FIRST;
-        int later = 0, nfirst = 0;
+        long long all = 0;
         for (int co = 0; co < NS; ++co) {
-            istart[co] = later;
+            const int count = rstart[(co + 1) * NLB] - rstart[co * NLB];
+            const int s = class_size(co);
+            all += s == 0 ? count : (count + 32 / s - 1) / (32 / s);
+        }
+        int run = 0, rounds = 0;
+        for (int co = 0; co < NS; ++co) {
+            share[co] = run;
             const int count = rstart[(co + 1) * NLB] - rstart[co * NLB];
             const int s = class_size(co);
             if (count == 0) continue;
-            first[nfirst++] = co;
-            later += (s == 0 ? count : (count + 32 / s - 1) / (32 / s)) - 1;
+            const int items = s == 0 ? count : (count + 32 / s - 1) / (32 / s);
+            int sh = (int)(((long long)warps * items + all / 2) / all);
+            sh = sh < 1 ? 1 : sh;
+            run += sh;
+            const int need = (items + sh - 1) / sh;
+            rounds = need > rounds ? need : rounds;
         }
-        istart[NS] = later;
-        first[NS] = nfirst;
+        share[NS] = run;
+        bk[BK_ROUNDS] = rounds;
     }
 }
 
@@ -842,27 +859,26 @@ k_herm_pack(int n, double *x, double *v, const double *__restrict__ m,
     if (st->error) return;
     const int lane = threadIdx.x & 31;
     LaneSmem &S = smem[threadIdx.x >> 5];
-    const int *rstart = bk + BK_RSTART, *istart = bk + BK_ISTART, *first = bk + BK_FIRST;
+    const int *rstart = bk + BK_RSTART, *share = bk + BK_SHARE;
     unsigned *next = (unsigned *)(bk + BK_NEXT);
     unsigned long long *work = (unsigned long long *)(bk + BK_WORK);
-    const int nfirst = first[NS], nitems = nfirst + istart[NS];
+    const int per = share[NS];  // items per round (0: no components)
+    const long long nitems = (long long)per * bk[BK_ROUNDS];
     long long nblk = 0, nstep = 0, pairs = 0, capped = 0, ncomp = 0, maxblk = 0;
     int maxsize = 0;
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = (int)atomicAdd(work, 1ull);
+        long long item = 0;
+        if (lane == 0) item = (long long)atomicAdd(work, 1ull);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= nitems) break;
-        int co = 0, k = 0;  // the class and the item's rank in it
-        if (item < nfirst) {
-            co = first[item];
-        } else {
-            const int later = item - nfirst;  // the last class whose later items start at or before
-            while (co + 1 < NS && istart[co + 1] <= later) ++co;
-            k = 1 + later - istart[co];
-        }
+        // the class and the item's rank in it
+        const int round = (int)(item / per), pos = (int)(item - (long long)round * per);
+        int co = 0;
+        while (share[co + 1] <= pos) ++co;
+        const int k = round * (share[co + 1] - share[co]) + pos - share[co];
         const int r0 = rstart[co * NLB], count = rstart[(co + 1) * NLB] - r0;
         if (co == 0) {
+            if (k >= count) continue;
             const int r = roots[r0 + k];
             const int size = csize[r];
             if (lane == 0) {
@@ -1035,7 +1051,7 @@ int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
     k_comp_level<<<g, HB, 0, s>>>(n, off, c->hparent, c->hlev, c->hcfill, c->st,
                                   c->lim_uf);
     k_root_hist<<<g, HB, 0, s>>>(n, c->hparent, c->hcsize, c->hcfill, bk);
-    k_root_scan<<<1, 32, 0, s>>>(bk);
+    k_root_scan<<<1, 32, 0, s>>>(bk, c->sms * HBS * HW);
     k_root_scatter<<<g, HB, 0, s>>>(n, c->hparent, c->hcsize, c->hcfill, bk,
                                     c->hroots);
     // every component, deepest first, from one dynamically shared list
