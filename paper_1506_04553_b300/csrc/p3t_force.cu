@@ -15,10 +15,12 @@
 // group (the same traversal and opening test as the list walk in
 // p3t_walk.cu) and feeds what it finds into three small rings in shared
 // memory: accepted cells, far leaf ranges, near leaf ranges.  Whenever a ring
-// holds 32 sources they are staged in shared memory as group-relative FP32
-// vectors, (x_hi - c) + x_lo, so that no absolute coordinate enters the FP32
-// arithmetic, and every lane applies each staged source (a broadcast read) to
-// both of its particles at once, as one packed FP32x2 pair.  Walking and evaluating in one kernel means the
+// holds a tile (64 cells or 32 particles) its sources are staged in shared
+// memory as group-relative FP32 vectors, (x_hi - c) + x_lo, so that no
+// absolute coordinate enters the FP32 arithmetic, and every lane applies
+// them to each of its particles two sources at a time: one packed FP32x2
+// instruction evaluates a particle against a pair of staged sources (a
+// broadcast read).  Walking and evaluating in one kernel means the
 // interaction lists never go through HBM and the walk's memory latency hides
 // behind other warps' arithmetic; the walk is software-pipelined by one
 // batch, so that a batch's box records are in flight while the previous
@@ -30,9 +32,6 @@
 #include "p3t_internal.cuh"
 
 namespace {
-
-// Warps (groups in flight) per block of the walk + force kernel: a template
-// parameter (2, 4 or 8), chosen per context by the autotuner; 4 by default.
 
 #ifndef P3T_PC_UNROLL
 #define P3T_PC_UNROLL 4
@@ -229,9 +228,10 @@ __device__ __forceinline__ float4 rel4(float4 hi, float4 lo, float4 c)
                        __fadd_rn(__fsub_rn(hi.z, c.z), lo.z), hi.w);
 }
 
-
-// Resident blocks per SM the force kernel's registers are sized for (0: let
-// the compiler choose).
+// Warps (groups in flight) per block of the walk + force kernel are a
+// template parameter (2, 4 or 8), chosen per context by the autotuner; 4 by
+// default.  P3T_FORCE_MIN_BLOCKS: the resident blocks per SM its registers
+// are sized for (0: the compiler chooses).
 #ifndef P3T_FORCE_MIN_BLOCKS
 #define P3T_FORCE_MIN_BLOCKS 0
 #endif
