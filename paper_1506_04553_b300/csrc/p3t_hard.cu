@@ -149,14 +149,16 @@ __device__ __forceinline__ PairPar pair_of(const HardPar &P, int t)
     return q;
 }
 
-// Hard acceleration and jerk of a particle at (xi, vi) from one neighbour at
-// (xj, vj) of mass mj, subtracted into acc and jrk: one square root and one
-// division (1/s, then its powers).
-__device__ __forceinline__ void pair_add(const double xi[3], const double vi[3],
-                                         double xj0, double xj1, double xj2,
-                                         double vj0, double vj1, double vj2,
-                                         double mj, const HardPar &P, int t,
-                                         double acc[3], double jrk[3])
+// The factors of one pair's hard acceleration and jerk, for a particle at
+// (xi, vi) and a neighbour at (xj, vj) of mass mj: with q = xi - xj,
+// u = vi - vj, fa = G mj (1 - K) / s^3, c1 = 3 (q.u) / s^2 and
+// fb = G mj (dK/ds) (q.u) / s^4 (one square root and one division: 1/s,
+// then its powers).
+__device__ __forceinline__ void pair_factors(const double xi[3], const double vi[3],
+                                             double xj0, double xj1, double xj2,
+                                             double vj0, double vj1, double vj2,
+                                             double mj, const HardPar &P, int t,
+                                             double &fa, double &c1, double &fb)
 {
     const PairPar pp = pair_of(P, t);
     const double q[3] = {dsub(xi[0], xj0), dsub(xi[1], xj1), dsub(xi[2], xj2)};
@@ -171,14 +173,39 @@ __device__ __forceinline__ void pair_add(const double xi[3], const double vi[3],
     const double dKds = dmul(dK_of_x(xk), pp.iomgrc);
     const double rv = dot3(q[0], q[1], q[2], u[0], u[1], u[2]);
     const double gm = dmul(P.G, mj);
-    const double fa = dmul(dmul(gm, w), ri3);
-    const double c1 = dmul(dmul(3.0, rv), ri2);
-    const double fb = dmul(dmul(gm, dmul(dmul(dKds, rv), ri)), ri3);
+    fa = dmul(dmul(gm, w), ri3);
+    c1 = dmul(dmul(3.0, rv), ri2);
+    fb = dmul(dmul(gm, dmul(dmul(dKds, rv), ri)), ri3);
+}
+
+// The pair's terms subtracted into acc and jrk:
+//   acc -= fa q,  jrk -= fa (u - c1 q) - fb q.
+__device__ __forceinline__ void pair_apply(const double xi[3], const double vi[3],
+                                           double xj0, double xj1, double xj2,
+                                           double vj0, double vj1, double vj2,
+                                           double fa, double c1, double fb,
+                                           double acc[3], double jrk[3])
+{
+    const double q[3] = {dsub(xi[0], xj0), dsub(xi[1], xj1), dsub(xi[2], xj2)};
+    const double u[3] = {dsub(vi[0], vj0), dsub(vi[1], vj1), dsub(vi[2], vj2)};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         acc[c] = dfma(-fa, q[c], acc[c]);
         jrk[c] = dfma(-fa, dfma(-c1, q[c], u[c]), dfma(fb, q[c], jrk[c]));
     }
+}
+
+// Hard acceleration and jerk of a particle at (xi, vi) from one neighbour at
+// (xj, vj) of mass mj, subtracted into acc and jrk.
+__device__ __forceinline__ void pair_add(const double xi[3], const double vi[3],
+                                         double xj0, double xj1, double xj2,
+                                         double vj0, double vj1, double vj2,
+                                         double mj, const HardPar &P, int t,
+                                         double acc[3], double jrk[3])
+{
+    double fa, c1, fb;
+    pair_factors(xi, vi, xj0, xj1, xj2, vj0, vj1, vj2, mj, P, t, fa, c1, fb);
+    pair_apply(xi, vi, xj0, xj1, xj2, vj0, vj1, vj2, fa, c1, fb, acc, jrk);
 }
 
 __device__ __forceinline__ void load3(const double *p, int n, int i, double r[3])
@@ -717,6 +744,9 @@ struct LaneSmem {
 
 // neighbour rows up to this length are held as lane numbers, 5 bits each
 constexpr int ROW_PACK = 12;
+// pair factors of one block step of a packed warp: with symmetric rows a
+// particle's neighbours are members of its component (at most 31)
+constexpr int FCAP = 32 * 31;
 
 // The queue of one class of components of s <= 32 particles, served by one
 // warp with floor(32 / s) slots: slot q = lane / s holds a component, lane
@@ -740,7 +770,8 @@ __device__ void integrate_class(int s, const int *__restrict__ croots, int count
                                 const double *__restrict__ ga,
                                 const double *__restrict__ gj,
                                 const int *__restrict__ glev, int *loc,
-                                LaneSmem &S, P3TDevState *st, long long &nblk,
+                                LaneSmem &S, double *F, P3TDevState *st,
+                                long long &nblk,
                                 long long &nstep, long long &pairs,
                                 long long &capped, long long &ncomp,
                                 int &maxsize, long long &maxblk)
@@ -812,14 +843,60 @@ __device__ void integrate_class(int s, const int *__restrict__ croots, int count
             }
         }
         __syncwarp();
-        if (have && e == tn) {
+        // The pairs of the due particles, numbered over the warp by a scan
+        // of their row lengths, are spread over all lanes: lane l computes
+        // the factors of pairs l, l + 32, ... (its owner found by a binary
+        // search over the scan) into F.  Each due lane then applies its row
+        // in row order with the same operations as pair_add, so the result
+        // is the per-lane loop's bit for bit, in ceil(pairs / 32) rounds of
+        // the costly part instead of the longest row's length.
+        const bool due = have && e == tn;
+        const int ln = due ? (int)len : 0;
+        const int incl = warp_incl_scan(ln), ex = incl - ln;
+        const int T = __shfl_sync(full, incl, 31);
+        const bool spread = T <= FCAP;  // warp-uniform
+        if (spread) {
+            for (int base = 0; base < T; base += 32) {
+                const int k = base + lane;
+                int o = 0;  // the largest lane whose first pair is at or before k
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int cand = o + step;
+                    if (__shfl_sync(full, ex, cand) <= k) o = cand;
+                }
+                const unsigned long long orow = __shfl_sync(full, row, o);
+                const long long oe0 = __shfl_sync(full, e0, o);
+                const long long olen = __shfl_sync(full, len, o);
+                const int oi = __shfl_sync(full, i, o), oex = __shfl_sync(full, ex, o);
+                if (k < T) {
+                    const int q = k - oex;
+                    const int jl = olen <= ROW_PACK ? (int)((orow >> (5 * q)) & 31)
+                                                    : loc[idx[oe0 + q]] & 31;
+                    const double xo[3] = {S.xp[0][o], S.xp[1][o], S.xp[2][o]};
+                    const double vo[3] = {S.vp[0][o], S.vp[1][o], S.vp[2][o]};
+                    pair_factors(xo, vo, S.xp[0][jl], S.xp[1][jl], S.xp[2][jl],
+                                 S.vp[0][jl], S.vp[1][jl], S.vp[2][jl], S.m[jl],
+                                 H.f, (oi >= H.f.nfs) + (int)((bhm >> jl) & 1u),
+                                 F[k], F[FCAP + k], F[2 * FCAP + k]);
+                }
+            }
+            __syncwarp();
+        }
+        if (due) {
             double a1[3] = {0.0, 0.0, 0.0}, j1[3] = {0.0, 0.0, 0.0};
             for (long long q = 0; q < len; ++q) {
                 const int jl = len <= ROW_PACK ? (int)((row >> (5 * q)) & 31)
                                                : loc[idx[e0 + q]] & 31;
-                pair_add(xp, vp, S.xp[0][jl], S.xp[1][jl], S.xp[2][jl],
-                         S.vp[0][jl], S.vp[1][jl], S.vp[2][jl], S.m[jl], H.f,
-                         (i >= H.f.nfs) + (int)((bhm >> jl) & 1u), a1, j1);
+                if (spread) {
+                    const int k = ex + (int)q;
+                    pair_apply(xp, vp, S.xp[0][jl], S.xp[1][jl], S.xp[2][jl],
+                               S.vp[0][jl], S.vp[1][jl], S.vp[2][jl], F[k],
+                               F[FCAP + k], F[2 * FCAP + k], a1, j1);
+                } else {
+                    pair_add(xp, vp, S.xp[0][jl], S.xp[1][jl], S.xp[2][jl],
+                             S.vp[0][jl], S.vp[1][jl], S.vp[2][jl], S.m[jl], H.f,
+                             (i >= H.f.nfs) + (int)((bhm >> jl) & 1u), a1, j1);
+                }
             }
             pairs += len;
             correct_reg(xs, vs, as, js, xp, vp, a1, j1, mass, i >= H.f.nfs, tn, H,
@@ -840,7 +917,7 @@ __device__ void integrate_class(int s, const int *__restrict__ croots, int count
             if (lane == 0) p3t_raise(st, P3T_ERR_TIMEOUT);
             break;
         }
-        __syncwarp();
+        __syncwarp();  // F and the predictions are rewritten next step
     }
 }
 
@@ -856,9 +933,11 @@ k_herm_pack(int n, double *x, double *v, const double *__restrict__ m,
             long long *t, int *lev, int *loc, P3TDevState *st)
 {
     __shared__ LaneSmem smem[HW];
+    extern __shared__ double hdyn[];  // pair factors, 3 FCAP per warp
     if (st->error) return;
     const int lane = threadIdx.x & 31;
     LaneSmem &S = smem[threadIdx.x >> 5];
+    double *F = hdyn + (size_t)(threadIdx.x >> 5) * 3 * FCAP;
     const int *rstart = bk + BK_RSTART, *share = bk + BK_SHARE;
     unsigned *next = (unsigned *)(bk + BK_NEXT);
     unsigned long long *work = (unsigned long long *)(bk + BK_WORK);
@@ -891,7 +970,7 @@ k_herm_pack(int n, double *x, double *v, const double *__restrict__ m,
         } else {
             integrate_class(class_size(co), roots + r0, count, next + co, lane, n,
                             x, v, m, off, idx, cstart, member, H, a, jk, lev, loc,
-                            S, st, nblk, nstep, pairs, capped, ncomp, maxsize,
+                            S, F, st, nblk, nstep, pairs, capped, ncomp, maxsize,
                             maxblk);
         }
     }
@@ -948,8 +1027,9 @@ int grid_for(long long n, int sms)
 
 // Dynamic shared memory that holds k_herm_pack at HBS blocks per SM: the
 // SM's shared memory split HBS ways, less the per-block reserve and the
-// static part, lowered until the occupancy calculator agrees.  Host only;
-// called where the hard-step scratch is allocated (never under capture).
+// static part, lowered until the occupancy calculator agrees; it also holds
+// the warps' pair factors (3 FCAP doubles per warp).  Host only; called
+// where the hard-step scratch is allocated (never under capture).
 int p3t_hard_setup(p3t_ctx *c)
 {
     int dev = 0, per_sm = 0, reserved = 0, optin = 0;
@@ -969,6 +1049,8 @@ int p3t_hard_setup(p3t_ctx *c)
                                                                    HW * 32, pad));
         if (nb >= HBS) break;
     }
+    // the padding also holds the warps' pair factors
+    if (pad < (int)(HW * 3 * FCAP * sizeof(double))) return P3T_ERR_STATE;
     c->herm_pad = pad;
     return P3T_OK;
 }
