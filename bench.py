@@ -1394,12 +1394,36 @@ def run_ensemble(args, dev, sample=False):
     torch.cuda.synchronize()
     ctx.check()
     ms = e0.elapsed_time(e1) / k
+    # phases, in uncaptured steps: the library's event profile for the build
+    # and the walk + force kernel, events around the whole backward
+    ctx.profile(reset=True)
+    ctx.profile_enable(True)
+    tb = []
+    for _ in range(3):
+        ctx.build_tree(pos, mass)
+        ctx.long_force(acc, check=False)
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        ctx.long_force_vjp(w, gx, gm, check=False)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        tb.append(b0.elapsed_time(b1))
+    ctx.profile_enable(False)
+    pr = ctx.profile(reset=True)
+    ctx.check()
+    phases = {"build": pr["build_ms"] / max(pr["builds"], 1),
+              "walk_and_force": pr["force_ms"] / max(pr["forces"], 1),
+              "backward": float(np.median(tb)),
+              "backward_walk_kernel": pr["vjp_walk_ms"] / max(pr["vjp_walks"], 1),
+              "note": "CUDA events, three uncaptured steps (medians / means)"}
     res = {"workload": "256 Plummer clusters, N_c log-uniform in [1024, 65536], "
                        "theta 0.4, r_out 0.01 (N_c/8192)^(-1/3), eps 4/N_c",
            "n": n, "clusters": 256, "step": "build + force + backward, "
            "one CUDA graph, one walk+force launch for all clusters",
            "value": n / (ms * 1e-3), "unit": "particles/s (fwd+bwd)",
            "ms_per_step": ms,
+           "phase_ms_per_step": phases,
            "autotuned": {"n_group": ng, "n_leaf": nl,
                          "force_warps": tune["force_warps"],
                          "vjp_warps": tune["vjp_warps"],
