@@ -120,6 +120,15 @@ def force_and_neighbours(ctx, acc, off, idx, side):
     cur.wait_stream(side)
 
 
+def fp32_peak_tflops(dev):
+    """Nominal FP32 FMA peak: SMs x 128 lanes x 2 flops x the maximum SM
+    clock recorded in MEASURED_PEAKS.json (2032 MHz if absent)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = float(measured_peaks().get("sm_max_mhz", 2032.0))
+    return sms * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+
+
 def profile_traffic(name="k_walk_force_plummer_1M.txt"):
     """Per-launch DRAM bytes of a kernel from its committed ncu summary (a
     line 'dram_bytes_per_launch: <float>'), else None."""
@@ -623,7 +632,7 @@ def run_ours(args, world, rank, local):
     peaks = measured_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clk = float(peaks.get("sm_max_mhz", 2032.0))
-    peak = sms * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+    peak = fp32_peak_tflops(dev)
     traffic = profile_traffic()
     gint = world * (int_pc + int_pp) / nprof / (ms_step * 1e-3) / 1e9
 
@@ -1412,11 +1421,25 @@ def run_ensemble(args, dev, sample=False):
     ctx.profile_enable(False)
     pr = ctx.profile(reset=True)
     ctx.check()
+    f_ms = pr["force_ms"] / max(pr["forces"], 1)
+    b_ms = pr["vjp_walk_ms"] / max(pr["vjp_walks"], 1)
+    nf = max(pr["forces"], 1)
+    ipc, ipp, ippn = pr["int_pc"] / nf, pr["int_pp"] / nf, pr["int_pp_near"] / nf
+    fl_f = FLOPS_PC * ipc + FLOPS_PP_NEAR * ippn + FLOPS_PP_FAR * (ipp - ippn)
+    fl_b = (FLOPS_BWD_PC * ipc + FLOPS_BWD_PP_NEAR * ippn
+            + FLOPS_BWD_PP_FAR * (ipp - ippn))
+    peak = fp32_peak_tflops(dev)
     phases = {"build": pr["build_ms"] / max(pr["builds"], 1),
-              "walk_and_force": pr["force_ms"] / max(pr["forces"], 1),
+              "walk_and_force": f_ms,
               "backward": float(np.median(tb)),
-              "backward_walk_kernel": pr["vjp_walk_ms"] / max(pr["vjp_walks"], 1),
-              "note": "CUDA events, three uncaptured steps (medians / means)"}
+              "backward_walk_kernel": b_ms,
+              "force_frac_of_fp32_peak": fl_f / (f_ms * 1e-3) / 1e12 / peak,
+              "backward_frac_of_fp32_peak": fl_b / (b_ms * 1e-3) / 1e12 / peak,
+              "note": "CUDA events, three uncaptured steps (medians / means); "
+                      "fractions: the forward's and backward's flops per "
+                      "interaction (as in roofline and roofline_bwd) times "
+                      "the kernel's own interaction counts, over its time, "
+                      "of the nominal FP32 peak"}
     res = {"workload": "256 Plummer clusters, N_c log-uniform in [1024, 65536], "
                        "theta 0.4, r_out 0.01 (N_c/8192)^(-1/3), eps 4/N_c",
            "n": n, "clusters": 256, "step": "build + force + backward, "
