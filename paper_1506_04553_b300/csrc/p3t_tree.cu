@@ -429,6 +429,11 @@ __device__ __forceinline__ void emit_children(int c, int L, int cap,
 // scan (at most 2 rounds of 8 x 32 keys); 512 took the split levels of a
 // 2^20 build from 0.267 to 0.255 ms against 2048 (same-box A/B).
 constexpr int BIG_CELL = 512;
+// Blocks per SM of a split level: as many as stay resident (58 registers
+// at 256 threads), so that a level runs in one wave; 4 took the split
+// levels of a 2^20 build from 0.256 to 0.244 ms against 8 (2: 0.262, 3:
+// 0.246, 16: 0.272; same-box A/B).
+constexpr int SPLIT_BLOCKS_PER_SM = 4;
 
 // Level L in two passes over its cells: one thread per cell files the
 // cells holding at most n_leaf particles in the leaf list (one aggregated
@@ -1033,7 +1038,7 @@ int p3t_build_levels(p3t_ctx *c, int n, cudaStream_t s, const double *pos,
     const int cap = (int)c->cap_cells;
     // one warp per cell: enough warps to fill every SM once
     for (int L = 0; L < P3T_MAX_LEVEL; ++L)
-        k_tree_split<<<c->sms * 8, TB, 0, s>>>(L, c->p.n_leaf, cap, c->key_a,
+        k_tree_split<<<c->sms * SPLIT_BLOCKS_PER_SM, TB, 0, s>>>(L, c->p.n_leaf, cap, c->key_a,
                                                 c->node, c->parent, c->cpend,
                                                 c->leaf_list, c->st);
     k_leaf_hist<<<c->sms * 4, TB, 0, s>>>(c->leaf_list, c->node, c->st);
