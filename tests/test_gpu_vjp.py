@@ -106,3 +106,53 @@ def test_autograd_function(cuda):
     ox, _ = t.vjp(w, eps=kw["eps"], r_cut=kw["r_out"])
     ex = rel_err(pd.grad.cpu().numpy().T, ox)
     assert np.median(ex) <= MED
+
+
+def _vjp_vs_oracle(pos, m, w, p):
+    _, gx, gm = _gpu_vjp(pos, m, w, p)
+    t = oracle.Tree(pos, m, n_leaf=p.n_leaf, n_group=p.n_group)
+    t.walk(p.theta, p.r_out, p.r_out)
+    ox, om = t.vjp(w, G=p.G, eps=p.eps, r_cut=p.r_out, gamma=p.gamma)
+    return gx, gm, ox, om
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 65, 300, 4099])
+def test_vjp_small_and_ragged_sizes(cuda, n):
+    """Groups, source tiles (64 per lane pair of a warp) and particle sweeps
+    (four at a time) all partial: a few particles in a tight clump, every
+    pair near, and a size that leaves a ragged tail at every level."""
+    from paper_1506_04553_b300 import Params
+    rng = np.random.default_rng(500 + n)
+    pos = rng.normal(size=(n, 3)) * 0.01
+    m = rng.uniform(0.5, 1.5, n) / n
+    w = rng.normal(size=(n, 3))
+    p = Params(theta=0.5, r_out=0.005, eps=1e-4, gamma=GAMMA)
+    gx, gm, ox, om = _vjp_vs_oracle(pos, m, w, p)
+    if n == 1:  # no pair at all
+        assert np.all(gx == 0.0) and np.all(gm == 0.0)
+        assert np.all(ox == 0.0) and np.all(om == 0.0)
+        return
+    ex = rel_err(gx, ox)
+    em = _scalar_err(gm, om)
+    assert np.median(ex) <= MED and ex.max() <= MAX_X, (np.median(ex), ex.max())
+    assert np.median(em) <= MED and em.max() <= MAX_M, (np.median(em), em.max())
+
+
+def test_vjp_coincident_particles(cuda):
+    """Coincident particles with eps = 0 inside a Plummer sphere: their pairs
+    have K(0) = 0, so they add nothing to the force or its derivative (the
+    backward's near terms must not form 0 * inf); the rest matches the
+    oracle."""
+    from paper_1506_04553_b300 import Params
+    n = 4096
+    pos, _, m = ics.plummer(n, 21)
+    pos = pos.T.copy()
+    pos[:80] = pos[0]  # a leaf of 80 coincident particles, a chain above it
+    w = np.random.default_rng(22).normal(size=(n, 3))
+    p = Params(theta=0.4, r_out=0.01, eps=0.0, gamma=GAMMA)
+    gx, gm, ox, om = _vjp_vs_oracle(pos, m, w, p)
+    assert np.all(np.isfinite(gx)) and np.all(np.isfinite(gm))
+    ex = rel_err(gx, ox)
+    em = _scalar_err(gm, om)
+    assert np.median(ex) <= MED and ex.max() <= MAX_X, (np.median(ex), ex.max())
+    assert np.median(em) <= MED and em.max() <= MAX_M, (np.median(em), em.max())
