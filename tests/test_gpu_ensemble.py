@@ -1,8 +1,9 @@
 """Ensembles of independent clusters (p3t_set_ensemble): every cluster must
 give what the oracle gives for that cluster alone (structure and lists
-bit-exact, forces and gradients within the usual tolerances, neighbour lists
-bit-exact), including a one-particle and a two-particle cluster; and a step
-captured in a CUDA graph must replay to the same forces."""
+bit-exact, forces within the usual tolerances, gradients within about three
+times the largest errors measured, neighbour lists bit-exact), including a
+one-particle and a two-particle cluster; and a step captured in a CUDA graph
+must replay to the same forces."""
 import numpy as np
 import pytest
 
@@ -85,7 +86,13 @@ def test_each_cluster_matches_its_own_oracle(ens):
         ox, om = t.vjp(ens["w"][b:e], eps=ens["eps"][k], r_cut=ens["r_out"][k])
         if e - b > 1:
             ex = rel_err(ens["gx"][b:e], ox)
-            assert np.median(ex) <= 1e-5 and ex.max() <= 1e-3, (k, ex.max())
+            floor = 1e-3 * np.sqrt(np.mean(om ** 2))
+            em = np.abs(ens["gm"][b:e] - om) / np.maximum(np.abs(om), floor)
+            print(f"cluster {k} (N = {e - b}): dL/dx max {ex.max():.2e}, "
+                  f"dL/dm max {em.max():.2e}")
+            # about three times the largest measured (7.3e-5 and 4.4e-4)
+            assert np.median(ex) <= 1e-5 and ex.max() <= 2e-4, (k, ex.max())
+            assert np.median(em) <= 1e-5 and em.max() <= 1.5e-3, (k, em.max())
 
 
 def test_graph_capture_replays_the_step(ens):
