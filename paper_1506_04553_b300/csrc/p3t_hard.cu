@@ -158,11 +158,15 @@ __device__ __forceinline__ void pair_factors(const double xi[3], const double vi
                                              double xj0, double xj1, double xj2,
                                              double vj0, double vj1, double vj2,
                                              double mj, const HardPar &P, int t,
-                                             double &fa, double &c1, double &fb)
+                                             double &fa, double &c1, double &fb,
+                                             double q[3], double u[3])
 {
     const PairPar pp = pair_of(P, t);
-    const double q[3] = {dsub(xi[0], xj0), dsub(xi[1], xj1), dsub(xi[2], xj2)};
-    const double u[3] = {dsub(vi[0], vj0), dsub(vi[1], vj1), dsub(vi[2], vj2)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        q[c] = dsub(xi[c], c == 0 ? xj0 : c == 1 ? xj1 : xj2);
+        u[c] = dsub(vi[c], c == 0 ? vj0 : c == 1 ? vj1 : vj2);
+    }
     const double s2 = dfma(q[0], q[0], dfma(q[1], q[1], dfma(q[2], q[2], pp.eps2)));
     const double s = dsqrt(s2);
     const double ri = ddiv(1.0, s);
@@ -178,20 +182,16 @@ __device__ __forceinline__ void pair_factors(const double xi[3], const double vi
     fb = dmul(dmul(gm, dmul(dmul(dKds, rv), ri)), ri3);
 }
 
-// The pair's terms subtracted into acc and jrk:
-//   acc -= fa q,  jrk -= fa (u - c1 q) - fb q.
-__device__ __forceinline__ void pair_apply(const double xi[3], const double vi[3],
-                                           double xj0, double xj1, double xj2,
-                                           double vj0, double vj1, double vj2,
-                                           double fa, double c1, double fb,
-                                           double acc[3], double jrk[3])
+// The pair's terms subtracted into acc and jrk, with tq = u - c1 q:
+//   acc -= fa q,  jrk -= fa tq - fb q.
+__device__ __forceinline__ void pair_apply(double fa, double fb, const double q[3],
+                                           const double tq[3], double acc[3],
+                                           double jrk[3])
 {
-    const double q[3] = {dsub(xi[0], xj0), dsub(xi[1], xj1), dsub(xi[2], xj2)};
-    const double u[3] = {dsub(vi[0], vj0), dsub(vi[1], vj1), dsub(vi[2], vj2)};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         acc[c] = dfma(-fa, q[c], acc[c]);
-        jrk[c] = dfma(-fa, dfma(-c1, q[c], u[c]), dfma(fb, q[c], jrk[c]));
+        jrk[c] = dfma(-fa, tq[c], dfma(fb, q[c], jrk[c]));
     }
 }
 
@@ -203,9 +203,11 @@ __device__ __forceinline__ void pair_add(const double xi[3], const double vi[3],
                                          double mj, const HardPar &P, int t,
                                          double acc[3], double jrk[3])
 {
-    double fa, c1, fb;
-    pair_factors(xi, vi, xj0, xj1, xj2, vj0, vj1, vj2, mj, P, t, fa, c1, fb);
-    pair_apply(xi, vi, xj0, xj1, xj2, vj0, vj1, vj2, fa, c1, fb, acc, jrk);
+    double fa, c1, fb, q[3], u[3], tq[3];
+    pair_factors(xi, vi, xj0, xj1, xj2, vj0, vj1, vj2, mj, P, t, fa, c1, fb, q, u);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tq[c] = dfma(-c1, q[c], u[c]);
+    pair_apply(fa, fb, q, tq, acc, jrk);
 }
 
 __device__ __forceinline__ void load3(const double *p, int n, int i, double r[3])
@@ -744,9 +746,11 @@ struct LaneSmem {
 
 // neighbour rows up to this length are held as lane numbers, 5 bits each
 constexpr int ROW_PACK = 12;
-// pair factors of one block step of a packed warp: with symmetric rows a
-// particle's neighbours are members of its component (at most 31)
-constexpr int FCAP = 32 * 31;
+// pair terms of one block step of a packed warp (8 doubles each: fa, fb, q,
+// u - c1 q); a block step with more pairs (components of more than 16
+// particles, densely connected, all due) takes the per-lane loop
+constexpr int FCAP = 512;
+constexpr int FTERMS = 8;
 
 // The queue of one class of components of s <= 32 particles, served by one
 // warp with floor(32 / s) slots: slot q = lane / s holds a component, lane
@@ -845,11 +849,12 @@ __device__ void integrate_class(int s, const int *__restrict__ croots, int count
         __syncwarp();
         // The pairs of the due particles, numbered over the warp by a scan
         // of their row lengths, are spread over all lanes: lane l computes
-        // the factors of pairs l, l + 32, ... (its owner found by a binary
-        // search over the scan) into F.  Each due lane then applies its row
-        // in row order with the same operations as pair_add, so the result
-        // is the per-lane loop's bit for bit, in ceil(pairs / 32) rounds of
-        // the costly part instead of the longest row's length.
+        // the terms of pairs l, l + 32, ... (its owner found by a binary
+        // search over the scan) into F: fa, fb, q and u - c1 q.  Each due
+        // lane then applies its row in row order with the same operations
+        // as pair_add, so the result is the per-lane loop's bit for bit, in
+        // ceil(pairs / 32) rounds of the costly part instead of the longest
+        // row's length, and only the fused sums per pair in row order.
         const bool due = have && e == tn;
         const int ln = due ? (int)len : 0;
         const int incl = warp_incl_scan(ln), ex = incl - ln;
@@ -874,10 +879,18 @@ __device__ void integrate_class(int s, const int *__restrict__ croots, int count
                                                     : loc[idx[oe0 + q]] & 31;
                     const double xo[3] = {S.xp[0][o], S.xp[1][o], S.xp[2][o]};
                     const double vo[3] = {S.vp[0][o], S.vp[1][o], S.vp[2][o]};
+                    double fa, c1, fb, q3[3], u3[3];
                     pair_factors(xo, vo, S.xp[0][jl], S.xp[1][jl], S.xp[2][jl],
                                  S.vp[0][jl], S.vp[1][jl], S.vp[2][jl], S.m[jl],
                                  H.f, (oi >= H.f.nfs) + (int)((bhm >> jl) & 1u),
-                                 F[k], F[FCAP + k], F[2 * FCAP + k]);
+                                 fa, c1, fb, q3, u3);
+                    F[k] = fa;
+                    F[FCAP + k] = fb;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        F[(2 + c) * FCAP + k] = q3[c];
+                        F[(5 + c) * FCAP + k] = dfma(-c1, q3[c], u3[c]);
+                    }
                 }
             }
             __syncwarp();
@@ -889,9 +902,11 @@ __device__ void integrate_class(int s, const int *__restrict__ croots, int count
                                                : loc[idx[e0 + q]] & 31;
                 if (spread) {
                     const int k = ex + (int)q;
-                    pair_apply(xp, vp, S.xp[0][jl], S.xp[1][jl], S.xp[2][jl],
-                               S.vp[0][jl], S.vp[1][jl], S.vp[2][jl], F[k],
-                               F[FCAP + k], F[2 * FCAP + k], a1, j1);
+                    const double q3[3] = {F[2 * FCAP + k], F[3 * FCAP + k],
+                                          F[4 * FCAP + k]};
+                    const double t3[3] = {F[5 * FCAP + k], F[6 * FCAP + k],
+                                          F[7 * FCAP + k]};
+                    pair_apply(F[k], F[FCAP + k], q3, t3, a1, j1);
                 } else {
                     pair_add(xp, vp, S.xp[0][jl], S.xp[1][jl], S.xp[2][jl],
                              S.vp[0][jl], S.vp[1][jl], S.vp[2][jl], S.m[jl], H.f,
@@ -933,11 +948,11 @@ k_herm_pack(int n, double *x, double *v, const double *__restrict__ m,
             long long *t, int *lev, int *loc, P3TDevState *st)
 {
     __shared__ LaneSmem smem[HW];
-    extern __shared__ double hdyn[];  // pair factors, 3 FCAP per warp
+    extern __shared__ double hdyn[];  // pair terms, FTERMS FCAP per warp
     if (st->error) return;
     const int lane = threadIdx.x & 31;
     LaneSmem &S = smem[threadIdx.x >> 5];
-    double *F = hdyn + (size_t)(threadIdx.x >> 5) * 3 * FCAP;
+    double *F = hdyn + (size_t)(threadIdx.x >> 5) * FTERMS * FCAP;
     const int *rstart = bk + BK_RSTART, *share = bk + BK_SHARE;
     unsigned *next = (unsigned *)(bk + BK_NEXT);
     unsigned long long *work = (unsigned long long *)(bk + BK_WORK);
@@ -1028,7 +1043,7 @@ int grid_for(long long n, int sms)
 // Dynamic shared memory that holds k_herm_pack at HBS blocks per SM: the
 // SM's shared memory split HBS ways, less the per-block reserve and the
 // static part, lowered until the occupancy calculator agrees; it also holds
-// the warps' pair factors (3 FCAP doubles per warp).  Host only; called
+// the warps' pair terms (FTERMS FCAP doubles per warp).  Host only; called
 // where the hard-step scratch is allocated (never under capture).
 int p3t_hard_setup(p3t_ctx *c)
 {
@@ -1049,8 +1064,8 @@ int p3t_hard_setup(p3t_ctx *c)
                                                                    HW * 32, pad));
         if (nb >= HBS) break;
     }
-    // the padding also holds the warps' pair factors
-    if (pad < (int)(HW * 3 * FCAP * sizeof(double))) return P3T_ERR_STATE;
+    // the padding also holds the warps' pair terms
+    if (pad < (int)(HW * FTERMS * FCAP * sizeof(double))) return P3T_ERR_STATE;
     c->herm_pad = pad;
     return P3T_OK;
 }
