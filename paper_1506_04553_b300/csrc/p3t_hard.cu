@@ -45,6 +45,7 @@
 //   a2 = (-6 (a0 - a1) - h (4 j0 + 2 j1)) / h^2
 //   a3 = (12 (a0 - a1) + 6 h (j0 + j1)) / h^3
 //   x = xp + a2 h^4 / 24 + a3 h^5 / 120,  v = vp + a2 h^3 / 6 + a3 h^4 / 24.
+#include <float.h>
 #include <math.h>
 
 #include "p3t_internal.cuh"
@@ -515,10 +516,24 @@ struct HermPar {
     double idt_max;        // 1 / dt_max: 1 / h = 2^k / dt_max exactly
     double a0c[2];         // per species: alpha G / r_cut^2, a_0 = a0c m_i
     double c6, c24, c120;  // 1/6, 1/24, 1/120
+    // Products of dt_max (or 1/dt_max) and the constants in the order the
+    // corrector forms them at level 0: (1/dt_max)^2, (1/dt_max)^3,
+    // dt_max^3/6, dt_max^4/24, dt_max^5/120 and 6 dt_max.  At level k each
+    // is the level-0 value times an exact power of two, so when every one
+    // stays normal over [0, kmax] (fast) the corrector takes them by
+    // exponent arithmetic, bit for bit the rounded products.
+    double ih2_0, ih3_0, h3c6_0, h4c24_0, h5c120_0, h6_0;
     long long T;  // dt_soft in ticks
     long long max_block;  // block steps allowed per component
     int kmax;
+    int fast;
 };
+
+// x 2^n for x and x 2^n normal: the exponent field moved.
+__device__ __forceinline__ double scale2n(double x, int n)
+{
+    return __longlong_as_double(__double_as_longlong(x) + ((long long)n << 52));
+}
 
 // Level of a step dt of at most eta sqrt(num / den), tested in squares (no
 // division, no outer square root): dt^2 den <= e with e = eta^2 num.  The
@@ -527,6 +542,27 @@ struct HermPar {
 __device__ __forceinline__ int level_sq(double den, double e, const HermPar &H,
                                         int kmin, long long &capped)
 {
+    // (dt_max 2^-k)^2 den is P 4^-k with P = dt_max^2 den when every
+    // dt_max^2 4^-k stays normal (fast), and P 4^-k <= e is a comparison of
+    // exponents and mantissas: with d the exponent difference of P and e,
+    // it holds for 2k > d, and for 2k = d when P's mantissa is at most e's
+    if (H.fast) {
+        const double P = dmul(H.dm2, den);
+        if (P == 0.0) return kmin;  // no hard force: no limit
+        const long long bp = __double_as_longlong(P), be = __double_as_longlong(e);
+        const int ep = (int)((bp >> 52) & 0x7ff), ee = (int)((be >> 52) & 0x7ff);
+        if (bp > 0 && be > 0 && ep > 0 && ep < 0x7ff && ee > 0 && ee < 0x7ff) {
+            const long long mm = (1LL << 52) - 1;
+            const int d = ep - ee + ((bp & mm) > (be & mm) ? 1 : 0);
+            int k = (d + 1) >> 1;  // ceil(d / 2)
+            k = k > kmin ? k : kmin;
+            if (k > H.kmax) {
+                ++capped;
+                k = H.kmax;
+            }
+            return k;
+        }
+    }
     int k = kmin;
     double q = scale2(H.dm2, -2 * k);
     while (k < H.kmax && dmul(q, den) > e) {
@@ -608,19 +644,32 @@ __device__ __forceinline__ void correct_reg(double x[3], double v[3], double a[3
     // both exact scalings (the parameter checks keep them normal), so they
     // equal the rounded product and quotient
     const double h = scale2(H.dt_max, -lev);
-    const double ih = scale2(H.idt_max, lev);
-    const double ih2 = dmul(ih, ih), ih3 = dmul(ih2, ih);
-    const double h2 = dmul(h, h), h3 = dmul(h2, h), h4 = dmul(h3, h),
-                 h5 = dmul(h4, h);
-    const double h3c6 = dmul(h3, H.c6), h4c24 = dmul(h4, H.c24),
-                 h5c120 = dmul(h5, H.c120);
+    double ih2, ih3, h3c6, h4c24, h5c120, h6;
+    if (H.fast) {  // the same products, by exponent arithmetic
+        ih2 = scale2n(H.ih2_0, 2 * lev);
+        ih3 = scale2n(H.ih3_0, 3 * lev);
+        h3c6 = scale2n(H.h3c6_0, -3 * lev);
+        h4c24 = scale2n(H.h4c24_0, -4 * lev);
+        h5c120 = scale2n(H.h5c120_0, -5 * lev);
+        h6 = scale2n(H.h6_0, -lev);
+    } else {
+        const double ih = scale2(H.idt_max, lev);
+        ih2 = dmul(ih, ih);
+        ih3 = dmul(ih2, ih);
+        const double h2 = dmul(h, h), h3 = dmul(h2, h), h4 = dmul(h3, h),
+                     h5 = dmul(h4, h);
+        h3c6 = dmul(h3, H.c6);
+        h4c24 = dmul(h4, H.c24);
+        h5c120 = dmul(h5, H.c120);
+        h6 = dmul(6.0, h);
+    }
     double a2[3], a3[3], a2e[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const double j0 = jk[c];
         const double da = dsub(a[c], a1[c]);
         a2[c] = dmul(dfma(-h, dfma(4.0, j0, dmul(2.0, j1[c])), dmul(-6.0, da)), ih2);
-        a3[c] = dmul(dfma(dmul(6.0, h), dadd(j0, j1[c]), dmul(12.0, da)), ih3);
+        a3[c] = dmul(dfma(h6, dadd(j0, j1[c]), dmul(12.0, da)), ih3);
         x[c] = dfma(a3[c], h5c120, dfma(a2[c], h4c24, xp[c]));
         v[c] = dfma(a3[c], h4c24, dfma(a2[c], h3c6, vp[c]));
         a[c] = a1[c];
@@ -1125,6 +1174,31 @@ int p3t_run_hard_step(p3t_ctx *c, int n, double *pos, double *vel,
     H.idt_max = 1.0 / H.dt_max;
     H.T = 1LL << (hp->log2_soft_over_max + hp->kmax);
     H.kmax = hp->kmax;
+    {
+        // the corrector's products at level 0, formed as the kernel forms
+        // them at any level; fast when all of them, and dt_max^2 4^-k,
+        // stay normal over [0, kmax]
+        const double dt = H.dt_max, ih = H.idt_max;
+        const double h2 = dt * dt, h3 = h2 * dt, h4 = h3 * dt, h5 = h4 * dt;
+        H.ih2_0 = ih * ih;
+        H.ih3_0 = H.ih2_0 * ih;
+        H.h3c6_0 = h3 * H.c6;
+        H.h4c24_0 = h4 * H.c24;
+        H.h5c120_0 = h5 * H.c120;
+        H.h6_0 = 6.0 * dt;
+        const int K = H.kmax;
+        const double lo[] = {ldexp(dt, -K), ldexp(h2, -2 * K), ldexp(h3, -3 * K),
+                             ldexp(h4, -4 * K), ldexp(h5, -5 * K),
+                             ldexp(H.h3c6_0, -3 * K), ldexp(H.h4c24_0, -4 * K),
+                             ldexp(H.h5c120_0, -5 * K), ldexp(H.h6_0, -K),
+                             ldexp(H.dm2, -2 * K), ih, H.ih2_0, H.ih3_0};
+        const double hi[] = {dt, h2, h3, h4, h5, H.h3c6_0, H.h4c24_0, H.h5c120_0,
+                             H.h6_0, H.dm2, ldexp(ih, K), ldexp(H.ih2_0, 2 * K),
+                             ldexp(H.ih3_0, 3 * K)};
+        H.fast = 1;
+        for (int q = 0; q < (int)(sizeof(lo) / sizeof(lo[0])); ++q)
+            if (!(lo[q] >= DBL_MIN && hi[q] <= DBL_MAX)) H.fast = 0;
+    }
     H.max_block = c->lim_block;
     const int g = grid_for(n, c->sms);
     k_herm_reset<<<1, 32, 0, s>>>(c->st);
